@@ -1,0 +1,45 @@
+"""Paper-level pins for the oracle (CPU only, ~90 s).
+
+Reproduces Table DropImpactParameters (Sec. IV): planar interface on a
+(Nx, Ny) = (2, 200) periodic lattice, initial tanh profile of width W = 10
+between the Maxwell densities (Eq. PlanarIntDensity), all relaxation times 1,
+Li forcing with sigma from Eq. VaporLiqEq, run until the convergence criterion
+of Sec. III.A drops below 1e-6. Checks the vapour-density error
+(Eq. DensityError), the interface width and the surface tension
+(Eq. SurfaceTension) against the printed values.
+"""
+import json
+import os
+
+import pytest
+
+import lbm_inputs as I
+from oracle import eos as E
+from oracle import lbm as L
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+CASES = GOLD["table_drop_impact_parameters"]["cases"]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
+def test_planar_interface_reproduces_table(case):
+    mode = E.MODE_SMOOTH if case["mode"] == "SMOOTH" else E.MODE_CS
+    eos = E.make_eos(mode, case["Tr"], case["a_l"], case["a_v"], case["alpha"])
+    lat = L.Lattice(2, 200, L.BC_PERIODIC_X | L.BC_PERIODIC_Y, eos, L.Relax(sigma=eos.sigma()))
+    f = lat.init_equilibrium(I.planar(2, 200, eos.rho_v, eos.rho_l, W=10.0))
+    prev = f.sum(axis=0)
+    for _ in range(2000):
+        f = lat.step(f, 100)
+        rho = f.sum(axis=0)
+        r = L.convergence_residual(rho, prev)
+        prev = rho
+        if r < 1e-6:
+            break
+    else:
+        pytest.fail("no convergence")
+    rho_v, rho_l = rho[0, 0], rho[100, 0]
+    err = L.vapor_density_error(rho_v, eos.rho_v)
+    assert err == pytest.approx(case["E_percent"], rel=0.01)
+    assert L.interface_width(rho[:, 0], rho_v, rho_l) == case["w"]
+    gamma = L.surface_tension_planar(eos.psi(rho[:, 0]), eos.G)
+    assert gamma * 1e3 == pytest.approx(case["gamma_e3"], rel=0.06)
