@@ -1,0 +1,327 @@
+"""Benchmark of the pseudopotential D2Q9 LBM step on GB300.
+
+Default workload (one bench step = one LBM time step of all four lattices):
+four 512 x 512 periodic static droplets, radii 32, 48, 64, 96, reduced
+temperature 0.6, Smooth C-S EOS (a_l = 0.387, a_v = 2, alpha = 0.834),
+all relaxation times 1, Li forcing with sigma from the mechanical-stability
+condition; initial tanh profiles of width 8. The four lattices' buffers
+(f in/out, psi, moments: ~180 MB per step) exceed the 126 MB L2, so the state
+streams from HBM every step (no explicit flush).
+
+Prints one JSON line: MLUPS (million lattice-node updates per second) over all
+ranks, the roofline of the dominant kernel, an end-to-end figure through the
+host-buffer C-ABI call, clocks sampled during the timed region and the oracle
+timed on the host cores (rank 0 only).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RADII = (32, 48, 64, 96)
+NX = NY = 512
+TR, A_L, A_V, ALPHA = 0.6, 0.387, 2.0, 0.834
+METRIC = "D2Q9 pseudopotential MLUPS (4 x 512^2 static droplets, T_r=0.6, Smooth C-S, FP64)"
+WORKLOAD = "static droplets 512x512 periodic, R in {32,48,64,96}, T_r=0.6, Smooth C-S (a_l=0.387, a_v=2, alpha=0.834), tau=1, Li forcing"
+E2E_INNER = 100  # LBM steps per end-to-end call
+
+# FP64 arithmetic instructions of one node update (density/psi pass + collision pass),
+# counted from the kernels' arithmetic; see DESIGN.md "Roofline".
+FP64_OPS_PER_NODE = {"rho_psi": 36, "collide": 67}
+BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_lib():
+    from paper_2107_06355_gb300 import build
+    build.build()
+
+
+def make_droplets(torch, stream):
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    eos = P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA)
+    relax = P.Relax()
+    sims, rho0s = [], []
+    for R in RADII:
+        s = P.Simulation(NX, NY, P.BC_PERIODIC, eos, relax, stream=stream)
+        d = s.derived()
+        rho0 = I.droplet(NX, NY, R, d["rho_v"], d["rho_l"], W=8.0)
+        s.init_equilibrium(rho0)
+        sims.append(s)
+        rho0s.append(rho0)
+    return sims, rho0s
+
+
+def time_oracle_sample(max_seconds=20.0):
+    """The oracle (numpy, as it stands) on one 512^2 droplet lattice of the workload."""
+    import lbm_inputs as I
+    from oracle import eos as E
+    from oracle import lbm as L
+
+    e = E.make_eos(E.MODE_SMOOTH, TR, A_L, A_V, ALPHA)
+    lat = L.Lattice(NX, NY, L.BC_PERIODIC_X | L.BC_PERIODIC_Y, e, L.Relax(sigma=e.sigma()))
+    f = lat.init_equilibrium(I.droplet(NX, NY, RADII[1], e.rho_v, e.rho_l, W=8.0))
+    f = lat.step(f, 1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        f = lat.step(f, 1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt > max_seconds or n >= 200:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = _numpy_threads()
+    return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": threads, "host_cores": cores,
+            "kind": "oracle",
+            "sample": f"{n} LBM steps of one 512x512 droplet lattice (R=48) of the workload, {dt:.1f} s"}
+
+
+def _numpy_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        return 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    steps_done, t_all = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        r = time_oracle_sample(max_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if k >= args.warmup:
+            t_all += 1.0
+            steps_done += 1
+            last = r
+    val = last["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or ws == 1:
+        build_lib()
+    if ws > 1:
+        torch.distributed.barrier()
+        build_lib()  # no-op after rank 0 (up to date)
+
+    stream = torch.cuda.current_stream()
+    sims, rho0s = make_droplets(torch, stream)
+    nodes = NX * NY * len(sims)
+
+    def step_all():
+        for s in sims:
+            s.step(1)
+
+    for _ in range(args.warmup):
+        step_all()
+    torch.cuda.synchronize()
+    for s in sims:
+        s.enable_kernel_timing(True)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_all()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    k_ms = [0.0, 0.0]
+    k_n = [0, 0]
+    for s in sims:
+        t, n = s.kernel_times()
+        s.enable_kernel_timing(False)
+        for i in range(2):
+            k_ms[i] += t[i]
+            k_n[i] += n[i]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    for s in sims:
+        m, umax, bad = s.guard()
+        if bad:
+            raise RuntimeError("benchmark state diverged")
+
+    # end to end: host density in (pinned), f = f_eq, E2E_INNER steps, host density out
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import _lib as L
+    import ctypes as C
+
+    pin_in = [torch.from_numpy(r).pin_memory() for r in rho0s]
+    pin_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in sims]
+    lib = L.lib()
+
+    def e2e_call():
+        for s, pi, po in zip(sims, pin_in, pin_out):
+            st = lib.pplbm_run_host(s.ctx, C.c_void_p(pi.data_ptr()), None, None, E2E_INNER,
+                                    C.c_void_p(po.data_ptr()))
+            L.check(st, s.ctx)
+
+    e2e_call()
+    e2e_steps = max(2, min(5, args.steps // 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_call()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_mlups = nodes * E2E_INNER / e2e_s / 1e6 * ws
+
+    hbm_gbs, sm_max, peak_src = load_peaks()
+    ms_per_step = ms / args.steps
+    mlups = nodes * args.steps / (ms / 1e3) / 1e6 * ws
+    # dominant kernel: the collision/streaming pass
+    dom = 1 if k_ms[1] >= k_ms[0] else 0
+    dom_name = ["rho_psi", "collide"][dom]
+    per_launch_s = k_ms[dom] / max(1, k_n[dom]) / 1e3
+    ops = FP64_OPS_PER_NODE[dom_name] * NX * NY
+    fp64_peak = 2 * 152 * sm_max * 1e6  # FP64 instructions/s: 2 per SM per clock
+    achieved = ops / per_launch_s
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattices": len(sims), "nx": NX, "ny": NY, "nodes_per_step": nodes,
+                   "parallelism": f"replicas{ws}", "l2": "state > L2 (about 180 MB per step), no flush"},
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12,
+                     "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": None, "flop_convention": "1 per FP64 add/mul/fma instruction",
+                     "peak_source": f"2 FP64 instr/clk/SM x 152 SMs x {sm_max:.0f} MHz",
+                     "launch_ms": per_launch_s * 1e3},
+        "roofline_hbm": {"kernel": dom_name, "achieved": BYTES_PER_NODE[dom_name] * NX * NY / per_launch_s / 1e9,
+                         "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": BYTES_PER_NODE[dom_name] * NX * NY / per_launch_s / 1e9 / hbm_gbs,
+                         "peak_source": peak_src},
+        "kernel_ms": {"rho_psi": k_ms[0] / max(1, k_n[0]), "collide": k_ms[1] / max(1, k_n[1])},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS",
+                "h2d_bytes_per_step": 8 * NX * NY * len(sims), "d2h_bytes_per_step": 8 * NX * NY * len(sims),
+                "call": f"pplbm_run_host per lattice: H2D rho0 (pinned), f=f_eq, {E2E_INNER} steps, D2H rho"},
+        "gpu_launches": 2 * len(sims) * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

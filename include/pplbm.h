@@ -1,0 +1,212 @@
+/*
+ * pplbm.h -- C ABI of the GB300 pseudopotential D2Q9 lattice Boltzmann step.
+ *
+ * One time step of the method of Czelusniak, Mapelli, Cabezas Gomez and Wagner,
+ * "Shaping the equation of state to improve numerical accuracy and stability of
+ * the pseudopotential lattice Boltzmann method":
+ *   density moment (Eq. Density) -> shaped equation of state (Sec. III.D, the
+ *   "Smooth C-S" EOS, or plain Carnahan-Starling, Eq. CS) -> psi(rho)
+ *   (Eq. InteractionPotential) -> Shan-Chen force (Eq. ShanChenForce) ->
+ *   MRT collision (Eqs. OperatorMRT, MatrixMRT, RelaxationMatrix) with the Li
+ *   forcing scheme (Eq. LiFS; sigma = 0 is the Guo scheme, Eq. GFS) ->
+ *   streaming (Eq. LBE), periodic or half-way bounce-back walls (Sec. IV).
+ * All arithmetic is IEEE double precision.
+ *
+ * Conventions
+ *   - Fields are row-major, x fastest: element (x, y) of an nx-by-ny field is at
+ *     index y*nx + x. Distributions f are 9 such planes (i = 0..8, the D2Q9
+ *     order of Eq. VelocitySet), plane i at offset i*nx*ny.
+ *   - The stored distribution is the pre-collision f(t) of Eq. LBE.
+ *   - Every call returns a pplbm_status; PPLBM_OK is 0. On error the context
+ *     (if any) keeps a message readable with pplbm_last_error(). Errors raised
+ *     by kernels (non-finite or non-positive density, psi^2 <= 0) are sticky:
+ *     they are read by pplbm_sync() / pplbm_guard() and returned by every later
+ *     call until pplbm_destroy().
+ *   - Device work is issued on the context's CUDA stream and is asynchronous
+ *     unless a call says otherwise. Pointers named "device or host" are checked
+ *     with cudaPointerGetAttributes: device memory is used in place; host memory
+ *     is staged through the workspace and the call synchronises the stream.
+ *   - Memory: the caller allocates the workspace (pplbm_workspace_bytes) and
+ *     every input/output buffer; the library never frees caller memory. The
+ *     context owns only a small device block for the error word and reduction
+ *     partials, allocated in pplbm_create and freed in pplbm_destroy.
+ */
+#ifndef PPLBM_H
+#define PPLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPLBM_API_VERSION 1
+
+typedef enum pplbm_status {
+  PPLBM_OK = 0,
+  PPLBM_ERR_ARG = 1,        /* invalid argument (size, flag, tau <= 1/2, null pointer ...) */
+  PPLBM_ERR_EOS_SETUP = 2,  /* no Maxwell root, a_1^2 or a_3^2 <= 0, psi^2 <= 0 at set-up */
+  PPLBM_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+  PPLBM_ERR_DIVERGED = 4,   /* a kernel met a non-finite or non-positive density or psi^2 <= 0 */
+  PPLBM_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+  PPLBM_ERR_STATE = 6       /* call not valid in the context's state */
+} pplbm_status;
+
+/* Boundary flags (Sec. III.A: periodic planar tests; Sec. IV: periodic in x,
+ * half-way bounce-back walls at bottom and top). x must be periodic; y is either
+ * periodic or walled on both sides. */
+#define PPLBM_BC_PERIODIC_X 1u
+#define PPLBM_BC_PERIODIC_Y 2u
+#define PPLBM_BC_WALL_BOTTOM 4u
+#define PPLBM_BC_WALL_TOP 8u
+
+/* Equation of state in use. */
+#define PPLBM_EOS_CS 0      /* Carnahan-Starling with a_liq everywhere (Eq. CS) */
+#define PPLBM_EOS_SMOOTH 1  /* Smooth C-S of Sec. III.D: vapour branch C-S(a_vap),
+                               liquid branch C-S(a_liq) + Delta P (Sec. III.D, last part) */
+
+/* Relaxation set. */
+#define PPLBM_RELAX_MRT 0        /* six constant relaxation times, Eq. RelaxationMatrix */
+#define PPLBM_RELAX_TWO_PHASE 1  /* Lambda = diag(1,1,1,1,1,1,1,1/tau,1/tau) with tau(rho) of
+                                    Eq. RelaxationTime, tau_v = 1/2 + v_r (tau_l - 1/2) (Sec. IV) */
+
+/* Forcing scheme. */
+#define PPLBM_FORCING_GUO 0  /* Eq. GFS (the Li scheme with sigma = 0) */
+#define PPLBM_FORCING_LI 1   /* Eq. LiFS */
+
+typedef struct pplbm_lattice {
+  int32_t nx, ny;   /* nodes along x and y, each >= 1; 9*nx*ny < 2^31 */
+  uint32_t bc;      /* PPLBM_BC_* flags */
+  int32_t reserved; /* must be 0 */
+} pplbm_lattice;
+
+typedef struct pplbm_eos_params {
+  int32_t mode;     /* PPLBM_EOS_* */
+  int32_t reserved; /* must be 0 */
+  double Tr;        /* reduced temperature T/T_c, 0 < Tr < 1 */
+  double a_liq;     /* C-S attraction a of the liquid branch (and of the whole EOS for PPLBM_EOS_CS) */
+  double a_vap;     /* C-S attraction a of the vapour branch (PPLBM_EOS_SMOOTH) */
+  double b, R;      /* C-S co-volume and gas constant (paper: b = 4, R = 1) */
+  double alpha;     /* shaping parameter: p_min = p_sat - alpha (p_sat^CS - p_min^CS) (Sec. III.D) */
+} pplbm_eos_params;
+
+typedef struct pplbm_relax {
+  int32_t kind;     /* PPLBM_RELAX_* */
+  int32_t forcing;  /* PPLBM_FORCING_* */
+  /* PPLBM_RELAX_MRT: tau_rho, tau_e, tau_zeta (varsigma), tau_j, tau_q, tau_nu, each > 1/2 */
+  double tau_rho, tau_e, tau_zeta, tau_j, tau_q, tau_nu;
+  /* PPLBM_RELAX_TWO_PHASE: liquid relaxation time (> 1/2) and kinematic viscosity ratio v_r (> 0) */
+  double tau_l, visc_ratio;
+  double sigma;        /* Li forcing parameter, used when sigma_auto == 0 */
+  int32_t sigma_auto;  /* 1: sigma = -eps/(16 G) with eps solving Eq. VaporLiqEq at the
+                          Maxwell densities for the EOS in use (Sec. III.A) */
+  int32_t reserved;    /* must be 0 */
+} pplbm_relax;
+
+/* Everything the device needs about the EOS, computed by pplbm_eos_setup. */
+typedef struct pplbm_eos_derived {
+  int32_t mode, reserved;
+  double G;                  /* interaction parameter (paper: -1) */
+  double b, R;
+  double a_l, a_v;           /* C-S a of the liquid / vapour branch */
+  double Tc_l, Tc_v;         /* exact C-S critical temperatures for a_l, a_v */
+  double T_l, T_v;           /* Tr * Tc_l, Tr * Tc_v */
+  double rho_v, rho_l;       /* Maxwell coexistence densities (Eq. MaxwellRule) */
+  double p_sat;              /* saturation pressure of the EOS in use */
+  double p_sat_cs;           /* Maxwell pressure of C-S(a_l) */
+  double rho_max, rho_min;   /* C-S spinodal densities (extrema of the vdW loop) */
+  double p_min_cs;           /* C-S(a_l) pressure at rho_min */
+  double p_max, p_min;       /* shaped-loop extrema (Sec. III.D) */
+  double dP;                 /* liquid-branch shift p_sat(a_v) - p_sat(a_l) */
+  double dpdrho_v, dpdrho_l; /* bulk-branch slopes at rho_v and rho_l */
+  double a1sq, b1;           /* region-1 ellipse */
+  double a3sq, b3;           /* region-3 ellipse */
+  double eps;                /* mechanical-stability exponent solving Eq. VaporLiqEq */
+  double psi_v, psi_l;       /* psi(rho_v), psi(rho_l): wall ghost values (Sec. IV) */
+} pplbm_eos_derived;
+
+typedef struct pplbm_ctx pplbm_ctx;
+
+/* Host-only, pure. Builds the EOS at one reduced temperature: exact critical
+ * point of Eq. CS, Maxwell densities (Eq. MaxwellRule), spinodal densities,
+ * p_min from alpha and p_max from the Maxwell rule of the shaped EOS
+ * (Sec. III.D), and eps of Eq. VaporLiqEq by Newton's method from eps = 2
+ * (Sec. III.A). G must be negative (Sec. II.B). Returns PPLBM_ERR_EOS_SETUP if
+ * any step has no solution. */
+pplbm_status pplbm_eos_setup(const pplbm_eos_params* params, double G, pplbm_eos_derived* out);
+
+/* Bytes of caller-owned device workspace a lattice needs with the given
+ * relaxation set: two distribution buffers (9 planes each), psi (1 plane) and the
+ * moments the collision pass reads (3, 5 or 9 planes). 0 on invalid input. */
+size_t pplbm_workspace_bytes(const pplbm_lattice* lattice, const pplbm_relax* relax);
+
+/* Creates a context for one lattice. `workspace` is device memory of at least
+ * pplbm_workspace_bytes() bytes, 16-byte aligned, owned by the caller and kept
+ * alive until pplbm_destroy. `stream` is a cudaStream_t (NULL = legacy default
+ * stream). The distributions are undefined until pplbm_init_equilibrium or
+ * pplbm_set_f. On error *out is NULL. */
+pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos,
+                          const pplbm_relax* relax, double G, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Replaces the stream later calls are issued on. */
+pplbm_status pplbm_set_stream(pplbm_ctx* ctx, void* stream);
+
+/* f_i = f_i^eq(rho0, u0) (Sec. III.A, Eq. EquilibriumDistribution). rho0 (nx*ny
+ * values, > 0) is device or host memory; ux0, uy0 likewise or NULL for zero. */
+pplbm_status pplbm_init_equilibrium(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0);
+
+/* Advances nsteps >= 0 time steps of Eq. LBE on the stream (asynchronous). */
+pplbm_status pplbm_step(pplbm_ctx* ctx, int64_t nsteps);
+
+/* Macroscopic fields of the current state: rho (Eq. Density), u with the F/2
+ * correction (Eq. Momentum) and psi (Eq. InteractionPotential). Each output
+ * (nx*ny values) is device or host memory, or NULL to skip. Overwrites the
+ * moment planes of the workspace (they are rebuilt by the next step). */
+pplbm_status pplbm_get_fields(pplbm_ctx* ctx, double* rho, double* ux, double* uy, double* psi);
+
+/* Copies the current distributions (9*nx*ny values, plane-major) out of / into
+ * the context; device or host memory. For checkpoint/resume. */
+pplbm_status pplbm_get_f(pplbm_ctx* ctx, double* f);
+pplbm_status pplbm_set_f(pplbm_ctx* ctx, const double* f);
+
+/* Synchronises the stream, then reports the sticky device error and the number
+ * of steps issued so far (steps_done may be NULL). */
+pplbm_status pplbm_sync(pplbm_ctx* ctx, int64_t* steps_done);
+
+/* Per-step guard (Sec. III.A convergence check and mass): writes to host
+ * out[0] = total mass sum(rho), out[1] = max |u|, out[2] = number of nodes with a
+ * non-finite or non-positive density. Deterministic two-pass reduction.
+ * Synchronises the stream. */
+pplbm_status pplbm_guard(pplbm_ctx* ctx, double out[3]);
+
+/* The EOS block the context uses. */
+pplbm_status pplbm_get_derived(const pplbm_ctx* ctx, pplbm_eos_derived* out);
+
+/* One call from host data to host data: rho0 (and optional ux0, uy0) are host
+ * arrays; initialises f = f^eq, advances nsteps and writes the final density to
+ * the host array rho_out. Synchronous. */
+pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0,
+                            int64_t nsteps, double* rho_out);
+
+/* Kernel timing, a profiling aid. While enabled, pplbm_step records a CUDA event
+ * pair around every launch of the two step kernels on the context's stream
+ * (events are created here, outside any timed region). pplbm_kernel_times
+ * synchronises the stream and returns, since the previous call, the summed
+ * device durations in milliseconds and the launch counts of the density/psi pass
+ * (index 0) and the collision/streaming pass (index 1), then resets them. */
+pplbm_status pplbm_enable_kernel_timing(pplbm_ctx* ctx, int enable);
+pplbm_status pplbm_kernel_times(pplbm_ctx* ctx, double ms[2], int64_t launches[2]);
+
+/* Message of the last error on this context ("" if none); valid until the next call. */
+const char* pplbm_last_error(const pplbm_ctx* ctx);
+const char* pplbm_status_string(pplbm_status status);
+
+/* Frees the context's own device block. Does not touch caller memory. */
+void pplbm_destroy(pplbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPLBM_H */

@@ -1,0 +1,57 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pplbm.h"
+#include "eos.cuh"
+
+namespace pplbm {
+
+EosConst make_eos_const(const pplbm_eos_derived& d);
+
+// Collision variants, chosen on the host from the relaxation set.
+enum CollideKind : int {
+  kUnitTau = 0,   // every relaxation time 1 (Lambda = I)
+  kShearTau = 1,  // Lambda = diag(1,...,1, omega_nu, omega_nu), omega_nu constant or from tau(rho)
+  kFullMrt = 2    // six independent relaxation times
+};
+
+// Number of moment planes K1 hands to K2 for each collision kind.
+inline int moment_planes(int kind) { return kind == kUnitTau ? 3 : (kind == kShearTau ? 5 : 9); }
+
+// Arguments of one lattice's step kernels (passed by value).
+struct StepArgs {
+  const double* f_in;   // 9 planes, pre-collision f(t)
+  double* f_out;        // 9 planes, f(t+1)
+  double* psi;          // 1 plane
+  double* mom;          // moment planes (3, 5 or 9)
+  int* err;             // sticky error word
+  int nx, ny;
+  int64_t n;            // nx * ny
+  int walls;            // 1: bounce-back walls at y = -1/2 and y = ny - 1/2; 0: periodic y
+  int kind;             // CollideKind
+  EosConst eos;
+  double G;
+  double psi_ghost_bottom, psi_ghost_top;
+  // kShearTau: omega = 1/tau with tau = tau_a + tau_b * rho (Eq. RelaxationTime); constant if tau_b == 0
+  double tau_a, tau_b;
+  // Li forcing, scaled: sigma * G^2 / (432 tau_e) (kUnitTau / kShearTau, tau_e = tau_zeta = 1)
+  double zz_scale;
+  // kFullMrt: relaxation rates for the 9 moments and the Li sigma terms 12 sigma/(tau - 1/2)
+  double omega[9];
+  double li_e, li_z;
+};
+
+// Launchers (step_kernels.cu); all asynchronous on `stream`.
+void launch_rho_psi(const StepArgs& a, void* stream);
+void launch_collide(const StepArgs& a, void* stream);
+void launch_fields(const StepArgs& a, double* rho, double* ux, double* uy, double* psi_out, void* stream);
+void launch_init_eq(const StepArgs& a, double* f, const double* rho0, const double* ux0, const double* uy0,
+                    void* stream);
+// deterministic guard reduction over f: partials has room for guard_blocks()*3 doubles; out gets 3
+int guard_blocks();
+void launch_guard(const StepArgs& a, const double* f, double* partials, double* out, void* stream);
+
+}  // namespace pplbm

@@ -1,0 +1,51 @@
+"""Shared set-up for the GPU parity tests: one configuration is built twice, once
+as an oracle lattice and once as a CUDA simulation, from the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import eos as E
+from oracle import lbm as L
+
+BC_PER = L.BC_PERIODIC_X | L.BC_PERIODIC_Y
+BC_WALLS = L.BC_PERIODIC_X | L.BC_WALL_BOTTOM | L.BC_WALL_TOP
+
+_EOS_CACHE = {}
+
+
+def oracle_eos(mode, Tr, a_l, a_v, alpha):
+    key = (mode, Tr, a_l, a_v, alpha)
+    if key not in _EOS_CACHE:
+        e = E.make_eos(mode, Tr, a_l, a_v if mode == E.MODE_SMOOTH else a_l, alpha)
+        e.solve_eps()
+        _EOS_CACHE[key] = e
+    return _EOS_CACHE[key]
+
+
+def make_pair(nx, ny, bc, eos_case, relax_kw, forcing_li=True):
+    """(oracle Lattice, gpu Simulation) for the same parameters.
+
+    eos_case = (mode, Tr, a_l, a_v, alpha); relax_kw: keyword arguments of the
+    library's Relax (kind, tau_*, tau_l, visc_ratio)."""
+    import paper_2107_06355_gb300 as P
+
+    mode, Tr, a_l, a_v, alpha = eos_case
+    oe = oracle_eos(*eos_case)
+    sigma = oe.sigma() if forcing_li else 0.0
+    kind = relax_kw.get("kind", P.RELAX_MRT)
+    orelax = L.Relax(kind=kind, tau_rho=relax_kw.get("tau_rho", 1.0), tau_e=relax_kw.get("tau_e", 1.0),
+                     tau_zeta=relax_kw.get("tau_zeta", 1.0), tau_j=relax_kw.get("tau_j", 1.0),
+                     tau_q=relax_kw.get("tau_q", 1.0), tau_nu=relax_kw.get("tau_nu", 1.0),
+                     tau_l=relax_kw.get("tau_l", 1.0), visc_ratio=relax_kw.get("visc_ratio", 1.0), sigma=sigma)
+    olat = L.Lattice(nx, ny, bc, oe, orelax)
+    gp = P.EOSParams(mode=mode, Tr=Tr, a_liq=a_l, a_vap=a_v if mode == E.MODE_SMOOTH else a_l,
+                     alpha=alpha if alpha > 0 else 0.5)
+    grelax = P.Relax(forcing=P.FORCING_LI if forcing_li else P.FORCING_GUO, sigma_auto=True, **relax_kw)
+    sim = P.Simulation(nx, ny, bc, gp, grelax)
+    return olat, sim
+
+
+def normwise(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))

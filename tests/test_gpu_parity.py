@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA step (through the C ABI) against the oracle.
+
+Per-step bar: max |f_gpu - f_oracle| / max |f_oracle| <= 1e-12 (normwise; the
+populations of vapour nodes are ~1e-7 of the liquid ones, so elementwise
+relative error is not meaningful there). Coexistence densities after
+equilibration agree to 1e-8 relative. Lattice sizes span several 32 x 8 tiles
+with ragged tails, plus degenerate 1 x 1 and 3 x 3 lattices.
+"""
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from gpu_helpers import BC_PER, BC_WALLS, make_pair, normwise
+from oracle import eos as E
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMOOTH06 = (E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+SMOOTH05 = (E.MODE_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+SMOOTH035 = (E.MODE_SMOOTH, 0.35, 0.363, 2.0, 0.775)
+SMOOTH08 = (E.MODE_SMOOTH, 0.8, 0.5, 0.5, 0.342)
+CS08 = (E.MODE_CS, 0.8, 0.5, 0.5, 0.0)
+CS06 = (E.MODE_CS, 0.6, 0.387, 0.387, 0.0)
+
+RELAX = {
+    "unit": {},
+    "shear_const": {"tau_nu": 0.7},
+    "two_phase": {"kind": 1, "tau_l": 0.6, "visc_ratio": 3.0},
+    "full_mrt": {"tau_rho": 1.0, "tau_e": 0.8, "tau_zeta": 1.1, "tau_j": 1.0, "tau_q": 1.2, "tau_nu": 0.7},
+}
+
+
+def _state(nx, ny, bc, eos, seed):
+    e = eos
+    if bc == BC_WALLS:
+        R = max(2.0, min(nx, ny) / 6)
+        rho, ux, uy = I.impact(nx, ny, R, max(2, ny // 6), e.rho_v, e.rho_l, 0.03, W=5.0)
+    else:
+        rho = I.droplet(nx, ny, max(1.5, min(nx, ny) / 4), e.rho_v, e.rho_l, W=5.0)
+        ux, uy = I.random_velocity((ny, nx), 0.01, seed + 1)
+    rho = I.perturbed(rho, 0.01, seed)
+    return rho, ux, uy
+
+
+@pytest.mark.parametrize("relax", list(RELAX))
+@pytest.mark.parametrize("shape,bc", [((70, 19), BC_PER), ((70, 27), BC_WALLS), ((3, 3), BC_PER),
+                                      ((33, 9), BC_WALLS), ((1, 1), BC_PER), ((5, 2), BC_WALLS)])
+@pytest.mark.parametrize("eos_case", [SMOOTH06, CS08], ids=["smooth06", "cs08"])
+def test_step_parity_small(relax, shape, bc, eos_case):
+    nx, ny = shape
+    olat, sim = make_pair(nx, ny, bc, eos_case, RELAX[relax])
+    rho, ux, uy = _state(nx, ny, bc, olat.eos, 17)
+    f = olat.init_equilibrium(rho, ux, uy)
+    sim.init_equilibrium(rho, ux, uy)
+    assert normwise(sim.get_f().cpu().numpy(), f) < 1e-15
+    for nsteps in (1, 9):
+        f = olat.step(f, nsteps)
+        sim.step(nsteps)
+        sim.sync()
+        err = normwise(sim.get_f().cpu().numpy(), f)
+        assert err < 1e-12 * max(1, nsteps / 2), (nsteps, err)
+    # macroscopic fields at the same state (Eqs. Density, Momentum, InteractionPotential)
+    r, u, v, p = [t.cpu().numpy() for t in sim.fields()]
+    orho, oux, ouy, opsi, _, _ = olat.macroscopic(f)
+    assert normwise(r, orho) < 1e-12
+    assert normwise(p, opsi) < 1e-12
+    umax = max(np.max(np.abs(oux)), np.max(np.abs(ouy)), 1e-30)
+    assert np.max(np.abs(u - oux)) < 1e-10 * umax + 1e-15
+    assert np.max(np.abs(v - ouy)) < 1e-10 * umax + 1e-15
+    sim.close()
+
+
+def test_guo_forcing_parity():
+    # Guo forcing with plain C-S is stable only for T_r >~ 0.8 (Sec. III.A)
+    olat, sim = make_pair(40, 24, BC_PER, CS08, {}, forcing_li=False)
+    rho, ux, uy = _state(40, 24, BC_PER, olat.eos, 5)
+    f = olat.init_equilibrium(rho, ux, uy)
+    sim.init_equilibrium(rho, ux, uy)
+    f = olat.step(f, 5)
+    sim.step(5)
+    assert normwise(sim.get_f().cpu().numpy(), f) < 5e-12
+
+
+def test_low_temperature_walls_parity():
+    """T_r = 0.35 (density ratio ~7.9e4) with walls and the two-phase relaxation."""
+    olat, sim = make_pair(64, 48, BC_WALLS, SMOOTH035, {"kind": 1, "tau_l": 0.6, "visc_ratio": 1.0})
+    rho, ux, uy = I.impact(64, 48, 8, 8, olat.eos.rho_v, olat.eos.rho_l, 0.05, W=8.0)
+    f = olat.init_equilibrium(rho, ux, uy)
+    sim.init_equilibrium(rho, ux, uy)
+    for _ in range(3):
+        f = olat.step(f, 5)
+        sim.step(5)
+        assert normwise(sim.get_f().cpu().numpy(), f) < 1e-11
+
+
+def test_mass_conservation_and_guard():
+    olat, sim = make_pair(96, 40, BC_WALLS, SMOOTH05, {"kind": 1, "tau_l": 0.7, "visc_ratio": 2.0})
+    rho, ux, uy = I.impact(96, 40, 8, 6, olat.eos.rho_v, olat.eos.rho_l, 0.03, W=7.0)
+    sim.init_equilibrium(rho, ux, uy)
+    m0, _, bad0 = sim.guard()
+    sim.step(300)
+    m1, umax, bad1 = sim.guard()
+    assert bad0 == 0 and bad1 == 0
+    assert abs(m1 - m0) < 1e-12 * m0
+    assert abs(m0 - olat.init_equilibrium(rho, ux, uy).sum()) < 1e-12 * m0
+    assert 0 < umax < 0.3
+
+
+def test_uniform_rest_state_fixed_point():
+    olat, sim = make_pair(40, 17, BC_PER, SMOOTH06, RELAX["full_mrt"])
+    rho = np.full((17, 40), olat.eos.rho_l)
+    sim.init_equilibrium(rho)
+    f0 = sim.get_f().cpu().numpy()
+    sim.step(50)
+    assert normwise(sim.get_f().cpu().numpy(), f0) < 1e-13
+
+
+def test_set_get_f_roundtrip_and_resume_bit_identical():
+    olat, sim = make_pair(50, 30, BC_PER, SMOOTH06, {})
+    rho, ux, uy = _state(50, 30, BC_PER, olat.eos, 3)
+    sim.init_equilibrium(rho, ux, uy)
+    sim.step(20)
+    ck = sim.get_f().clone()
+    sim.step(30)
+    a = sim.get_f().clone()
+    sim.set_f(ck)
+    sim.step(30)
+    b = sim.get_f()
+    assert torch.equal(a, b)
+    host = ck.cpu().numpy()
+    sim.set_f(host)   # host pointer path
+    assert torch.equal(sim.get_f(), ck)
+
+
+def test_host_and_device_pointer_paths_agree():
+    olat, sim = make_pair(64, 20, BC_PER, SMOOTH06, {})
+    rho, ux, uy = _state(64, 20, BC_PER, olat.eos, 9)
+    out_host = sim.run_host(rho, 7, ux, uy)
+    sim.init_equilibrium(torch.tensor(rho, device="cuda"), torch.tensor(ux, device="cuda"),
+                         torch.tensor(uy, device="cuda"))
+    sim.step(7)
+    r = sim.fields()[0].cpu().numpy()
+    assert np.array_equal(out_host, r)
+
+
+def test_divergence_is_reported_not_faulted():
+    """A non-physical state (negative density) sets the sticky error word; the
+    context reports PPLBM_ERR_DIVERGED and the GPU stays usable."""
+    import paper_2107_06355_gb300 as P
+
+    olat, sim = make_pair(32, 8, BC_PER, SMOOTH06, {})
+    rho = np.full((8, 32), olat.eos.rho_l)
+    rho[3, 5] = -0.1
+    with pytest.raises(P.PPLBMError) as ei:
+        sim.init_equilibrium(rho)
+    assert ei.value.status == 4
+    with pytest.raises(P.PPLBMError):
+        sim.step(1)
+    sim.close()
+    # a fresh context works
+    olat, sim = make_pair(32, 8, BC_PER, SMOOTH06, {})
+    sim.init_equilibrium(np.full((8, 32), olat.eos.rho_l))
+    sim.step(3)
+    assert sim.sync() == 3
+
+
+# --- full-size workloads, in the configuration the benchmark times -----------------
+def test_planar_256x4_coexistence_after_10000_steps():
+    """Planar interface, 256 x 4 periodic, T_r = 0.8, Smooth C-S (a = 0.5, alpha = 0.342),
+    tau = 1, tanh profile of width 8 along the 256 axis: vapour and liquid densities
+    after 10,000 steps agree with the oracle to 1e-8."""
+    olat, sim = make_pair(4, 256, BC_PER, SMOOTH08, {})
+    rho0 = I.planar(4, 256, olat.eos.rho_v, olat.eos.rho_l, W=8.0)
+    f = olat.init_equilibrium(rho0)
+    sim.init_equilibrium(rho0)
+    f = olat.step(f, 10000)
+    sim.step(10000)
+    r = sim.fields()[0].cpu().numpy()
+    orho = f.sum(axis=0)
+    assert abs(r[0, 0] - orho[0, 0]) < 1e-8 * orho[0, 0]
+    assert abs(r[128, 0] - orho[128, 0]) < 1e-8 * orho[128, 0]
+    assert normwise(r, orho) < 1e-10
+
+
+def test_droplet_512_full_field_parity():
+    """512 x 512 periodic droplet (R = 48, T_r = 0.6, Smooth C-S): full-field parity over 3 steps."""
+    olat, sim = make_pair(512, 512, BC_PER, SMOOTH06, {})
+    rho0 = I.droplet(512, 512, 48, olat.eos.rho_v, olat.eos.rho_l, W=8.0)
+    f = olat.init_equilibrium(rho0)
+    sim.init_equilibrium(rho0)
+    f = olat.step(f, 3)
+    sim.step(3)
+    assert normwise(sim.get_f().cpu().numpy(), f) < 3e-12
+
+
+def test_impact_2048x1024_full_field_parity():
+    """Droplet impact lattice 2048 x 1024, walls in y, T_r = 0.35, Re = 300 (tau_l = 0.6,
+    v_r = 1, V_d = 0.05, R = 100, film 102): full-field parity after 2 steps."""
+    olat, sim = make_pair(2048, 1024, BC_WALLS, SMOOTH035, {"kind": 1, "tau_l": 0.6, "visc_ratio": 1.0})
+    rho0, ux0, uy0 = I.impact(2048, 1024, 100, 102, olat.eos.rho_v, olat.eos.rho_l, 0.05, W=8.0)
+    f = olat.init_equilibrium(rho0, ux0, uy0)
+    sim.init_equilibrium(rho0, ux0, uy0)
+    f = olat.step(f, 2)
+    sim.step(2)
+    assert normwise(sim.get_f().cpu().numpy(), f) < 2e-12

@@ -1,0 +1,105 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol include/pplbm.h
+declares, and its host-only entry points (EOS set-up, workspace sizing, argument
+checks) agree with the oracle. No CUDA call is made here."""
+import ctypes as C
+import subprocess
+
+import pytest
+
+from oracle import eos as E
+
+P = pytest.importorskip("paper_2107_06355_gb300")
+from paper_2107_06355_gb300 import _lib as L  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_06355_gb300 import build
+    build.build()
+    return L.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    declared = L.declared_symbols()
+    assert len(declared) >= 16
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    for s in declared:
+        assert hasattr(lib, s)
+
+
+CASES = [(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), (E.MODE_SMOOTH, 0.5, 0.363, 2.0, 0.775),
+         (E.MODE_SMOOTH, 0.35, 0.363, 2.0, 0.775), (E.MODE_SMOOTH, 0.8, 0.5, 0.5, 0.342),
+         (E.MODE_SMOOTH, 0.95, 0.363, 2.0, 0.775), (E.MODE_CS, 0.6, 0.387, 0.387, 0.0),
+         (E.MODE_CS, 0.5, 0.363, 0.363, 0.0), (E.MODE_CS, 0.8, 0.5, 0.5, 0.0)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "m%d_Tr%.2f_al%.3f_av%.3f_al%.3f" % c)
+def test_eos_setup_matches_oracle(lib, case):
+    mode, Tr, al, av, alpha = case
+    d = P.eos_setup(P.EOSParams(mode, Tr, al, av, alpha if alpha > 0 else 0.5))
+    o = E.make_eos(mode, Tr, al, av, alpha)
+    o.solve_eps()
+    keys = ["Tc_l", "Tc_v", "T_l", "T_v", "rho_v", "rho_l", "p_sat", "p_sat_cs", "rho_max", "rho_min", "p_min_cs"]
+    if mode == E.MODE_SMOOTH:
+        keys += ["p_max", "p_min", "dP", "dpdrho_v", "dpdrho_l", "a1sq", "b1", "a3sq", "b3"]
+    for k in keys:
+        want = getattr(o, k)
+        assert d[k] == pytest.approx(want, rel=2e-12, abs=1e-300), k
+    # the oracle's Simpson estimate of eps carries ~1e-11 rounding (large cancelling terms)
+    assert d["eps"] == pytest.approx(o.eps, rel=5e-11)
+    assert d["psi_l"] == pytest.approx(float(o.psi(o.rho_l)), rel=1e-12)
+    assert d["psi_v"] == pytest.approx(float(o.psi(o.rho_v)), rel=1e-12)
+
+
+def test_eos_setup_rejects_bad_arguments(lib):
+    out = L.pplbm_eos_derived()
+    for p, G in [(L.pplbm_eos_params(1, 0, 1.2, 0.5, 0.5, 4, 1, 0.3), -1.0),   # Tr >= 1
+                 (L.pplbm_eos_params(1, 0, 0.6, 0.5, 0.5, 4, 1, 0.3), 1.0),    # G > 0
+                 (L.pplbm_eos_params(7, 0, 0.6, 0.5, 0.5, 4, 1, 0.3), -1.0),   # mode
+                 (L.pplbm_eos_params(1, 0, 0.6, -0.5, 0.5, 4, 1, 0.3), -1.0)]:  # a < 0
+        assert lib.pplbm_eos_setup(C.byref(p), G, C.byref(out)) == L.PPLBM_ERR_ARG
+    assert lib.pplbm_eos_setup(None, -1.0, C.byref(out)) == L.PPLBM_ERR_ARG
+
+
+def test_eos_setup_reports_unshapeable_loop(lib):
+    # alpha so large that the liquid-side ellipse has no real a_3 (Sec. III.D condition)
+    out = L.pplbm_eos_derived()
+    p = L.pplbm_eos_params(1, 0, 0.6, 0.387, 2.0, 4, 1, 40.0)
+    assert lib.pplbm_eos_setup(C.byref(p), -1.0, C.byref(out)) == L.PPLBM_ERR_EOS_SETUP
+
+
+def test_workspace_bytes_and_lattice_validation(lib):
+    relax = P.Relax().c()
+    two = P.Relax(kind=L.RELAX_TWO_PHASE, tau_l=0.6, visc_ratio=2.0).c()
+    full = P.Relax(tau_e=0.8).c()
+    lat = L.pplbm_lattice(256, 4, L.BC_PERIODIC, 0)
+    n = 256 * 4
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(relax)) == 8 * n * (19 + 3)
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(two)) == 8 * n * (19 + 5)
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(full)) == 8 * n * (19 + 9)
+    for bad in [L.pplbm_lattice(0, 4, L.BC_PERIODIC, 0), L.pplbm_lattice(4, 0, L.BC_PERIODIC, 0),
+                L.pplbm_lattice(4, 4, L.BC_PERIODIC_Y, 0),                       # x not periodic
+                L.pplbm_lattice(4, 4, L.BC_PERIODIC_X | L.BC_WALL_BOTTOM, 0),    # one wall only
+                L.pplbm_lattice(4, 4, L.BC_PERIODIC | L.BC_WALL_TOP, 0),         # periodic and wall
+                L.pplbm_lattice(20000, 20000, L.BC_PERIODIC, 0),                 # 9 n >= 2^31
+                L.pplbm_lattice(4, 4, L.BC_PERIODIC, 1)]:                        # reserved
+        assert lib.pplbm_workspace_bytes(C.byref(bad), C.byref(relax)) == 0
+    bad_tau = P.Relax(tau_nu=0.5).c()
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(bad_tau)) == 0
+
+
+def test_create_rejects_without_touching_the_gpu(lib):
+    ctx = C.c_void_p()
+    lat = L.pplbm_lattice(8, 8, L.BC_PERIODIC, 0)
+    eos = P.EOSParams().c()
+    relax = P.Relax().c()
+    # workspace too small, or NULL: rejected before any CUDA call
+    assert lib.pplbm_create(C.byref(ctx), C.byref(lat), C.byref(eos), C.byref(relax), -1.0,
+                            C.c_void_p(16), 8, None) == L.PPLBM_ERR_ARG
+    assert lib.pplbm_create(C.byref(ctx), C.byref(lat), C.byref(eos), C.byref(relax), -1.0,
+                            None, 1 << 20, None) == L.PPLBM_ERR_ARG
+    assert ctx.value is None
+    assert lib.pplbm_status_string(L.PPLBM_ERR_DIVERGED) == b"simulation diverged"
