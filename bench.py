@@ -162,6 +162,23 @@ def _numpy_threads():
         return 1
 
 
+def profile_case():
+    """One 2048 x 1024 periodic droplet lattice (R = 100) of the workload's EOS, 3 steps:
+    369 MB of workspace (larger than L2), 3 launches of each step kernel."""
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    s = P.Simulation(2048, 1024, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA), P.Relax())
+    d = s.derived()
+    s.init_equilibrium(I.droplet(2048, 1024, 100, d["rho_v"], d["rho_l"], W=8.0))
+    s.step(3)
+    s.sync()
+    torch.cuda.synchronize()
+    print("profile case done")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -190,7 +207,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
