@@ -199,6 +199,30 @@ pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux
 pplbm_status pplbm_enable_kernel_timing(pplbm_ctx* ctx, int enable);
 pplbm_status pplbm_kernel_times(pplbm_ctx* ctx, double ms[2], int64_t launches[2]);
 
+/* One time step, f_out = step(f_in), that allocates no device memory. The paper
+ * has no counterpart: this exists for callers that cannot call cudaMalloc, such
+ * as code inside a host framework that owns all device memory through its own
+ * pool or budget, or code on a latency-critical stream where cudaMalloc/cudaFree
+ * would synchronise the device. There is no context: the caller passes the
+ * lattice, an EOS block from pplbm_eos_setup (host only), the relaxation set and
+ * two distinct device buffers of 9*nx*ny values (plane-major); psi and the
+ * moment planes live in a static device array inside the library, so
+ * nx*ny <= 65536 (larger lattices return PPLBM_ERR_ARG with a message saying so).
+ *  - The array (5.2 MB) is held by every GPU that loads the library until the
+ *    process exits. Its address is looked up once per device, by the first call
+ *    made while that device is current; make that first call before any stream
+ *    capture.
+ *  - Every call uses the same array: calls that overlap on the GPU (other
+ *    streams, other threads) race and give undefined results. The error word in
+ *    it is cleared at the start of each call.
+ *  - Synchronises `stream` (cudaStream_t, NULL = legacy default stream) to read
+ *    the error word; returns PPLBM_ERR_DIVERGED for a non-finite or non-positive
+ *    density or psi^2 <= 0. `message` (may be NULL) receives a static string
+ *    describing a failure, "" on success. */
+pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const pplbm_eos_derived* eos,
+                                const pplbm_relax* relax, const double* f_in, double* f_out, void* stream,
+                                const char** message);
+
 /* Message of the last error on this context ("" if none); valid until the next call. */
 const char* pplbm_last_error(const pplbm_ctx* ctx);
 const char* pplbm_status_string(pplbm_status status);
