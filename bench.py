@@ -36,9 +36,9 @@ METRIC = "D2Q9 pseudopotential MLUPS (4 x 512^2 static droplets, T_r=0.6, Smooth
 WORKLOAD = "static droplets 512x512 periodic, R in {32,48,64,96}, T_r=0.6, Smooth C-S (a_l=0.387, a_v=2, alpha=0.834), tau=1, Li forcing"
 E2E_INNER = 100  # LBM steps per end-to-end call
 
-# FP64 arithmetic instructions of one node update (density/psi pass + collision pass),
-# counted from the kernels' arithmetic; see DESIGN.md "Roofline".
-FP64_OPS_PER_NODE = {"rho_psi": 36, "collide": 67}
+# FP64 instructions of one node update per kernel (unit relaxation times, Li forcing,
+# bulk nodes), counted from the kernels' arithmetic; ncu's FP64-pipe cycles agree.
+FP64_OPS_PER_NODE = {"rho_psi": 33, "collide": 51}
 BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
 
 
@@ -203,7 +203,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=12000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -242,7 +242,7 @@ def main():
         step_all()
     torch.cuda.synchronize()
     for s in sims:
-        s.enable_kernel_timing(True)
+        s.enable_kernel_timing(args.steps)
 
     def barrier():
         if ws > 1:
@@ -264,7 +264,7 @@ def main():
     k_n = [0, 0]
     for s in sims:
         t, n = s.kernel_times()
-        s.enable_kernel_timing(False)
+        s.enable_kernel_timing(0)
         for i in range(2):
             k_ms[i] += t[i]
             k_n[i] += n[i]
@@ -293,7 +293,7 @@ def main():
             L.check(st, s.ctx)
 
     e2e_call()
-    e2e_steps = max(2, min(5, args.steps // 50))
+    e2e_steps = 5
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):

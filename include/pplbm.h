@@ -190,13 +190,23 @@ pplbm_status pplbm_get_derived(const pplbm_ctx* ctx, pplbm_eos_derived* out);
 pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0,
                             int64_t nsteps, double* rho_out);
 
-/* Kernel timing, a profiling aid. While enabled, pplbm_step records a CUDA event
- * pair around every launch of the two step kernels on the context's stream
- * (events are created here, outside any timed region). pplbm_kernel_times
- * synchronises the stream and returns, since the previous call, the summed
- * device durations in milliseconds and the launch counts of the density/psi pass
- * (index 0) and the collision/streaming pass (index 1), then resets them. */
-pplbm_status pplbm_enable_kernel_timing(pplbm_ctx* ctx, int enable);
+/* Self-test of the double-precision reciprocal and square root the step kernels
+ * use in place of IEEE division and sqrt (a hardware seed refined by one
+ * third-order series step). Evaluates n pseudo-random x = m 2^k (m in [1, 2),
+ * |k| <= 60) and writes to the device array out[2] the largest relative error
+ * against CUDA's correctly rounded 1/x (out[0]) and sqrt(x) (out[1]).
+ * Asynchronous on `stream`. */
+pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed, double* out, void* stream);
+
+/* Kernel timing, a profiling aid. With capacity > 0, pplbm_step records a CUDA
+ * event pair around every launch of the two step kernels on the context's
+ * stream; events for `capacity` launches of each kernel are created here, outside
+ * any timed region (more are created on demand). capacity = 0 disables timing.
+ * pplbm_kernel_times synchronises the stream and returns, since the previous
+ * call, the summed device durations in milliseconds and the launch counts of the
+ * density/psi pass (index 0) and the collision/streaming pass (index 1), then
+ * resets them. */
+pplbm_status pplbm_enable_kernel_timing(pplbm_ctx* ctx, int64_t capacity);
 pplbm_status pplbm_kernel_times(pplbm_ctx* ctx, double ms[2], int64_t launches[2]);
 
 /* One time step, f_out = step(f_in), that allocates no device memory. The paper

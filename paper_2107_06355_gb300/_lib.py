@@ -83,10 +83,11 @@ _SIGS = {
     "pplbm_guard": (C.c_int, [_P, _D]),
     "pplbm_get_derived": (C.c_int, [_P, C.POINTER(pplbm_eos_derived)]),
     "pplbm_run_host": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P]),
-    "pplbm_enable_kernel_timing": (C.c_int, [_P, C.c_int]),
+    "pplbm_enable_kernel_timing": (C.c_int, [_P, C.c_int64]),
     "pplbm_kernel_times": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
     "pplbm_step_noalloc": (C.c_int, [C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_derived),
                                      C.POINTER(pplbm_relax), _P, _P, _P, C.POINTER(C.c_char_p)]),
+    "pplbm_fp64_selftest": (C.c_int, [C.c_longlong, C.c_ulonglong, _P, _P]),
     "pplbm_last_error": (C.c_char_p, [_P]),
     "pplbm_status_string": (C.c_char_p, [C.c_int]),
     "pplbm_destroy": (None, [_P]),

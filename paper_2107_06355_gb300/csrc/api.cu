@@ -243,6 +243,7 @@ pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const p
   a.kind = kind;
   a.eos = make_eos_const(d);
   a.G = G;
+  a.half_force = -G / 24.0;
   a.psi_ghost_bottom = d.psi_l;  // liquid below the bottom wall (Sec. IV)
   a.psi_ghost_top = d.psi_v;     // vapour above the top wall
   const double sigma = relax->forcing == PPLBM_FORCING_GUO ? 0.0
@@ -380,12 +381,12 @@ pplbm_status pplbm_run_host(pplbm_ctx* c, const double* rho0, const double* ux0,
   return pplbm_get_fields(c, rho_out, nullptr, nullptr, nullptr);
 }
 
-pplbm_status pplbm_enable_kernel_timing(pplbm_ctx* c, int enable) {
-  if (!c) return PPLBM_ERR_ARG;
-  c->timing = enable != 0;
+pplbm_status pplbm_enable_kernel_timing(pplbm_ctx* c, int64_t capacity) {
+  if (!c || capacity < 0) return PPLBM_ERR_ARG;
+  c->timing = capacity > 0;
   if (c->timing) {
     for (int k = 0; k < 2; ++k)
-      if (pplbm_status s = grow_events(c, k, 4096)) return s;
+      if (pplbm_status s = grow_events(c, k, 2 * (size_t)capacity)) return s;
   }
   c->ev_used[0] = c->ev_used[1] = 0;
   return PPLBM_OK;

@@ -34,6 +34,13 @@ struct EosConst {
   double p_min, b3, inv_a3sq;
   double inv_span, a2, b2;
   double psi2_scale;   // 2 / G: psi^2 = psi2_scale * (p - rho/3)
+  // C-S branches folded into psi^2 (kernels): with s = 2/G,
+  // psi^2 = rho (k1 num/(1 - eta)^3 + k2 rho + k3) + k4, k1 = s R T, k2 = -s a, k3 = -s/3, k4 = s dP
+  double k1_v, k2_v, k4_v;
+  double k1_l, k2_l, k4_l;
+  double k3;
+  // bit patterns of the branch densities (positive doubles order like their bits)
+  long long bits_rho_v, bits_rho_max, bits_rho_min, bits_rho_l;
 };
 
 PPLBM_HD inline double cs_pressure(double rho, double b4, double RT, double a) {

@@ -243,6 +243,18 @@ EosConst make_eos_const(const pplbm_eos_derived& d) {
   e.a2 = 2.0 * (d.p_max - d.p_min);
   e.b2 = 3.0 * (d.p_min - d.p_max);
   e.psi2_scale = 2.0 / d.G;
+  const double sc = e.psi2_scale;
+  e.k1_v = sc * e.RT_v;
+  e.k2_v = -sc * e.a_v;
+  e.k4_v = 0.0;
+  e.k1_l = sc * e.RT_l;
+  e.k2_l = -sc * e.a_l;
+  e.k4_l = sc * e.dP;
+  e.k3 = -sc / 3.0;
+  std::memcpy(&e.bits_rho_v, &e.rho_v, 8);
+  std::memcpy(&e.bits_rho_max, &e.rho_max, 8);
+  std::memcpy(&e.bits_rho_min, &e.rho_min, 8);
+  std::memcpy(&e.bits_rho_l, &e.rho_l, 8);
   return e;
 }
 

@@ -34,6 +34,7 @@ struct StepArgs {
   int kind;             // CollideKind
   EosConst eos;
   double G;
+  double half_force;    // -G / 24: F/2 = half_force * psi(x) * g, g = 12 sum_i w_i psi(x + c_i) c_i
   double psi_ghost_bottom, psi_ghost_top;
   // kShearTau: omega = 1/tau with tau = tau_a + tau_b * rho (Eq. RelaxationTime); constant if tau_b == 0
   double tau_a, tau_b;

@@ -108,6 +108,7 @@ extern "C" pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const p
   a.kind = kind;
   a.eos = make_eos_const(*eos);
   a.G = eos->G;
+  a.half_force = -eos->G / 24.0;
   a.psi_ghost_bottom = eos->psi_l;
   a.psi_ghost_top = eos->psi_v;
   const double G = eos->G;

@@ -26,6 +26,8 @@
 //    Li term needs no division by psi^2.
 #include <cuda_runtime.h>
 
+#include "eos_dev.cuh"
+#include "fp64.cuh"
 #include "internal.h"
 
 namespace pplbm {
@@ -54,9 +56,11 @@ __global__ void __launch_bounds__(256) k_rho_psi(const StepArgs a) {
   const double rho = (f0 + f2 + f4) + (sxp + sxm);
   const double jx = sxp - sxm;
   const double jy = (f2 + f5 + f6) - (f4 + f7 + f8);
-  const double psi2 = eos_psi2(a.eos, rho);
-  if (!(rho > 0.0 && rho < 1e300 && psi2 > 0.0)) atomicOr(a.err, 1);
-  a.psi[i] = sqrt(psi2);
+  const double psi2 = eos_psi2_dev(a.eos, rho);
+  // 0 < rho < 1e300 and 0 < psi^2 < inf, tested on the bit patterns (integer pipe)
+  const long long rb = dbits(rho), pb = dbits(psi2);
+  if (!(rb > 0 && rb < 0x7E37E43C8800759CLL && pb > 0 && pb < 0x7FF0000000000000LL)) atomicOr(a.err, 1);
+  a.psi[i] = fast_sqrt(psi2);
   double* __restrict__ m = a.mom;
   m[i] = rho;
   m[N + i] = jx;
@@ -101,53 +105,64 @@ struct Post {
 };
 
 // Collision for Lambda = I (KIND kUnitTau) or shear-only relaxation (kShearTau).
+//
+// With h = F/2: J = j + h = rho u (Eq. Momentum), P = j + 2h (momentum after the
+// step), and the post-collision second moments (Lambda = I)
+//   Pi_xx = rho ux^2 + ux Fx = ux (P_x + h_x),  Pi_yy = uy (P_y + h_y),
+//   Pi_xy = rho ux uy + (ux Fy + uy Fx)/2 = ux P_y + uy h_x.
+// These are rows 1, 7, 8 of m* = m_eq + S/2 (Eqs. LiFS, GFS with tau = 1);
+// kShearTau relaxes rows 7, 8 with omega = 1/tau instead. Then
+//   f*_i = w_i [rho + 3 c_i.P + 4.5 (c_i c_i - I/3) : Pi] + z_i,
+// z_i = zz (-8, 1, 1, 1, 1, 1, 1, 1, 1) being M^-1 applied to the Li sigma terms
+// +-12 sigma |F|^2 / psi^2 of rows 1 and 2 (tau_e = tau_zeta = 1), zz = sigma |F|^2 / (3 psi^2).
 template <int KIND>
 __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node, double rho, double jx, double jy,
                                                 double psi0, double gx, double gy, Post& out, double* ux_o,
                                                 double* uy_o) {
-  const double cF = -a.G * psi0 * (1.0 / 12.0);
-  const double Fx = cF * gx, Fy = cF * gy;
-  const double Jx = fma(0.5, Fx, jx), Jy = fma(0.5, Fy, jy);  // rho u (Eq. Momentum)
-  const double inv_rho = 1.0 / rho;
-  const double ux = Jx * inv_rho, uy = Jy * inv_rho;
+  const double cH = a.half_force * psi0;  // h = cH g, cH = -G psi / 24
+  const double hx = cH * gx, hy = cH * gy;
+  const double inv_rho = fast_rcp(rho);
+  const double ux = (jx + hx) * inv_rho, uy = (jy + hy) * inv_rho;
   *ux_o = ux;
   *uy_o = uy;
-  const double Px = jx + Fx, Py = jy + Fy;  // momentum after collision and forcing
-  const double Pxx = ux * (Jx + Fx);        // rho ux^2 + ux Fx
-  const double Pyy = uy * (Jy + Fy);
-  double tr = Pxx + Pyy;
-  double Dxy, Pxy;
-  if (KIND == kUnitTau) {
-    Dxy = Pxx - Pyy;
-    Pxy = fma(ux, Jy, 0.5 * fma(ux, Fy, uy * Fx));
-  } else {
-    // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S
-    const double tau = fma(a.tau_b, rho, a.tau_a);
-    const double om = 1.0 / tau;
-    const double m7 = a.mom[3 * a.n + node], m8 = a.mom[4 * a.n + node];
-    const double meq7 = fma(ux, Jx, -uy * Jy), meq8 = ux * Jy;
-    const double s7 = 2.0 * fma(ux, Fx, -uy * Fy), s8 = fma(ux, Fy, uy * Fx);
-    const double h = fma(-0.5, om, 1.0);
-    Dxy = fma(h, s7, fma(-om, m7 - meq7, m7));
-    Pxy = fma(h, s8, fma(-om, m8 - meq8, m8));
-  }
-  const double Pxx2 = 0.5 * (tr + Dxy), Pyy2 = 0.5 * (tr - Dxy);
-  // Li term: M^-1 of (12 sigma |F|^2/(psi^2 tau_e)) e_1 - (12 sigma |F|^2/(psi^2 tau_z)) e_2
+  const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
+  const double Pxx = ux * (Px + hx), Pyy = uy * (Py + hy);
+  const double tr = Pxx + Pyy;
+  const double Pxy_eq = fma(ux, Py, uy * hx);
   const double zz = a.zz_scale * fma(gx, gx, gy * gy);
   const double B0 = fma(-1.5, tr, rho);
+  const double Q = fma(B0, 1.0 / 9.0, zz);
+  double axp, ayp, Pxy;
+  if (KIND == kUnitTau) {
+    axp = fma(0.5, Pxx, Q);
+    ayp = fma(0.5, Pyy, Q);
+    Pxy = Pxy_eq;
+  } else {
+    // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S, with m_eq + S/2 = Pi above
+    const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
+    const double m7 = a.mom[3 * a.n + node], m8 = a.mom[4 * a.n + node];
+    const double Jx = jx + hx, Jy = jy + hy;
+    const double meq7 = fma(ux, Jx, -uy * Jy), meq8 = ux * Jy;
+    const double s7 = 4.0 * fma(ux, hx, -uy * hy), s8 = 2.0 * fma(ux, hy, uy * hx);
+    const double hw = fma(-0.5, om, 1.0);
+    const double m7s = fma(hw, s7, fma(-om, m7 - meq7, m7));
+    Pxy = fma(hw, s8, fma(-om, m8 - meq8, m8));
+    const double T4 = fma(0.25, tr, Q);
+    axp = fma(0.25, m7s, T4);  // Q + Pi_xx/2 with Pi_xx = (tr + m7*)/2
+    ayp = fma(-0.25, m7s, T4);
+  }
   out.f[0] = fma(4.0 / 9.0, B0, -8.0 * zz);
-  const double ax = fma(4.5, Pxx2, B0), ay = fma(4.5, Pyy2, B0);
-  out.f[1] = fma(1.0 / 9.0, fma(3.0, Px, ax), zz);
-  out.f[3] = fma(1.0 / 9.0, fma(-3.0, Px, ax), zz);
-  out.f[2] = fma(1.0 / 9.0, fma(3.0, Py, ay), zz);
-  out.f[4] = fma(1.0 / 9.0, fma(-3.0, Py, ay), zz);
-  const double D = fma(3.0, tr, rho);
-  const double dp = fma(9.0, Pxy, D), dm = fma(-9.0, Pxy, D);
+  out.f[1] = fma(Px, 1.0 / 3.0, axp);
+  out.f[3] = fma(-Px, 1.0 / 3.0, axp);
+  out.f[2] = fma(Py, 1.0 / 3.0, ayp);
+  out.f[4] = fma(-Py, 1.0 / 3.0, ayp);
+  const double Dq = fma(fma(3.0, tr, rho), 1.0 / 36.0, zz);
+  const double dp = fma(0.25, Pxy, Dq), dm = fma(-0.25, Pxy, Dq);
   const double ps = Px + Py, pd = Py - Px;
-  out.f[5] = fma(1.0 / 36.0, fma(3.0, ps, dp), zz);
-  out.f[7] = fma(1.0 / 36.0, fma(-3.0, ps, dp), zz);
-  out.f[6] = fma(1.0 / 36.0, fma(3.0, pd, dm), zz);
-  out.f[8] = fma(1.0 / 36.0, fma(-3.0, pd, dm), zz);
+  out.f[5] = fma(ps, 1.0 / 12.0, dp);
+  out.f[7] = fma(-ps, 1.0 / 12.0, dp);
+  out.f[6] = fma(pd, 1.0 / 12.0, dm);
+  out.f[8] = fma(-pd, 1.0 / 12.0, dm);
 }
 
 // General MRT collision in moment space (six relaxation times).
@@ -165,10 +180,10 @@ __device__ __forceinline__ void collide_full(const StepArgs& a, int64_t node, do
   m[7] = a.mom[7 * N + node];
   m[8] = a.mom[8 * N + node];
   const double rho = m[0];
-  const double cF = -a.G * psi0 * (1.0 / 12.0);
+  const double cF = 2.0 * a.half_force * psi0;
   const double Fx = cF * gx, Fy = cF * gy;
   const double Jx = fma(0.5, Fx, m[3]), Jy = fma(0.5, Fy, m[5]);
-  const double inv_rho = 1.0 / rho;
+  const double inv_rho = fast_rcp(rho);
   const double ux = Jx * inv_rho, uy = Jy * inv_rho;
   *rho_o = rho;
   *ux_o = ux;

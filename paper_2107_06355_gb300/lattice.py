@@ -159,8 +159,9 @@ class Simulation:
         self._check(L.lib().pplbm_guard(self.ctx, out))
         return out[0], out[1], int(out[2])
 
-    def enable_kernel_timing(self, on=True):
-        self._check(L.lib().pplbm_enable_kernel_timing(self.ctx, 1 if on else 0))
+    def enable_kernel_timing(self, capacity=4096):
+        """Record per-launch device times of the two step kernels (capacity 0 disables)."""
+        self._check(L.lib().pplbm_enable_kernel_timing(self.ctx, int(capacity)))
 
     def kernel_times(self):
         """((ms_rho_psi, ms_collide), (launches_rho_psi, launches_collide)) since the last call."""
