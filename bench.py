@@ -200,6 +200,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serial_sims(torch, stream):
+    sims, rho0s = make_droplets(torch, stream)
+    return sims, rho0s
+
+
+def make_batch(P, I, specs, stream):
+    """A Batch over `specs` (dicts with nx, ny, Tr, kind, R) with tanh initial fields."""
+    eos = [P.EOSParams(P.EOS_SMOOTH, s["Tr"], s.get("a_l", A_L), s.get("a_v", A_V), s.get("alpha", ALPHA))
+           for s in specs]
+    relax = [P.Relax() for _ in specs]
+    b = P.Batch([(s["nx"], s["ny"], P.BC_PERIODIC) for s in specs], eos, relax, stream=stream)
+    inits = []
+    for k, s in enumerate(specs):
+        d = b.derived(k)
+        if s["kind"] == "planar":
+            rho = I.planar(s["nx"], s["ny"], d["rho_v"], d["rho_l"], W=8.0)
+        else:
+            rho = I.droplet(s["nx"], s["ny"], s["R"], d["rho_v"], d["rho_l"], W=8.0)
+        b.init_equilibrium(k, rho)
+        inits.append(rho)
+    return b, eos, relax, inits
+
+
+def time_device(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def sweep_comparison(torch, stream, steps):
+    """64-lattice sweep (seed 210706355): batched engine vs one context per lattice."""
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    specs = I.batch_specs()
+    for s in specs:
+        s["a_l"], s["a_v"], s["alpha"] = 0.363, 2.0, 0.775
+    nodes = sum(s["nx"] * s["ny"] for s in specs)
+    b, eos, relax, inits = make_batch(P, I, specs, stream)
+    plan = b.autotune(trial_steps=4)
+    b.step(2)
+    ms_b = time_device(torch, stream, lambda: b.step(steps))
+    b.sync()
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    sims = []
+    for k, s in enumerate(specs):
+        sim = P.Simulation(s["nx"], s["ny"], P.BC_PERIODIC, eos[k], relax[k], stream=stream)
+        sim.init_equilibrium(inits[k])
+        sims.append(sim)
+
+    def serial():
+        for _ in range(steps):
+            for sim in sims:
+                sim.step(1)
+
+    for sim in sims:
+        sim.step(2)
+    ms_s = time_device(torch, stream, serial)
+    for sim in sims:
+        sim.sync()
+        sim.close()
+    mode = {0: "launches", 1: "graph", 2: "persistent"}[plan["mode"]]
+    return {"instances": len(specs), "nodes": nodes, "steps": steps, "plan": mode,
+            "tile_width": plan["tile_width"] or "per-instance",
+            "batched_instance_steps_per_s": len(specs) * steps / (ms_b / 1e3),
+            "serial_instance_steps_per_s": len(specs) * steps / (ms_s / 1e3),
+            "batched_mlups": nodes * steps / (ms_b / 1e3) / 1e6,
+            "serial_mlups": nodes * steps / (ms_s / 1e3) / 1e6,
+            "speedup": ms_s / ms_b}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +284,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
     args = ap.parse_args()
@@ -218,6 +296,8 @@ def main():
         return run_reference(args)
 
     import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -231,18 +311,13 @@ def main():
         build_lib()  # no-op after rank 0 (up to date)
 
     stream = torch.cuda.current_stream()
-    sims, rho0s = make_droplets(torch, stream)
-    nodes = NX * NY * len(sims)
-
-    def step_all():
-        for s in sims:
-            s.step(1)
-
-    for _ in range(args.warmup):
-        step_all()
+    specs = [dict(kind="droplet", nx=NX, ny=NY, R=R, Tr=TR) for R in RADII]
+    batch, _, _, rho0s = make_batch(P, I, specs, stream)
+    nodes = NX * NY * len(specs)
+    plan = batch.autotune(trial_steps=20)
+    batch.step(args.warmup)
     torch.cuda.synchronize()
-    for s in sims:
-        s.enable_kernel_timing(args.steps)
+    batch.enable_timing(4)
 
     def barrier():
         if ws > 1:
@@ -254,31 +329,42 @@ def main():
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step_all()
+    batch.step(args.steps)
     e1.record(stream)
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    k_ms = [0.0, 0.0]
-    k_n = [0, 0]
+    call_ms, call_steps = batch.times()
+    batch.enable_timing(0)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    batch.sync()
+
+    # the same four lattices stepped one context at a time (two launches per lattice per step)
+    sims, _ = serial_sims(torch, stream)
+    for s in sims:
+        s.step(args.warmup)
+    serial_steps = min(args.steps, 2000)
+    for s in sims:
+        s.enable_kernel_timing(serial_steps)
+
+    def serial():
+        for _ in range(serial_steps):
+            for s in sims:
+                s.step(1)
+
+    ms_serial = time_device(torch, stream, serial)
+    k_ms, k_n = [0.0, 0.0], [0, 0]
     for s in sims:
         t, n = s.kernel_times()
         s.enable_kernel_timing(0)
         for i in range(2):
             k_ms[i] += t[i]
             k_n[i] += n[i]
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    for s in sims:
-        m, umax, bad = s.guard()
-        if bad:
-            raise RuntimeError("benchmark state diverged")
 
     # end to end: host density in (pinned), f = f_eq, E2E_INNER steps, host density out
-    import paper_2107_06355_gb300 as P
     from paper_2107_06355_gb300 import _lib as L
     import ctypes as C
 
@@ -301,45 +387,56 @@ def main():
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_mlups = nodes * E2E_INNER / e2e_s / 1e6 * ws
+    for s in sims:
+        m, umax, bad = s.guard()
+        if bad:
+            raise RuntimeError("benchmark state diverged")
+        s.close()
 
     hbm_gbs, sm_max, peak_src = load_peaks()
     ms_per_step = ms / args.steps
     mlups = nodes * args.steps / (ms / 1e3) / 1e6 * ws
-    # dominant kernel: the collision/streaming pass
-    dom = 1 if k_ms[1] >= k_ms[0] else 0
-    dom_name = ["rho_psi", "collide"][dom]
-    per_launch_s = k_ms[dom] / max(1, k_n[dom]) / 1e3
-    ops = FP64_OPS_PER_NODE[dom_name] * NX * NY
     fp64_peak = 2 * 152 * sm_max * 1e6  # FP64 instructions/s: 2 per SM per clock
-    achieved = ops / per_launch_s
+    ops_per_node = FP64_OPS_PER_NODE["rho_psi"] + FP64_OPS_PER_NODE["collide"]
+    bytes_per_node = BYTES_PER_NODE["rho_psi"] + BYTES_PER_NODE["collide"]
+    step_s = call_ms / max(1, call_steps) / 1e3
+    achieved = ops_per_node * nodes / step_s
+    mode = {0: "launches", 1: "graph", 2: "persistent"}[plan["mode"]]
+    launches_per_step = 0 if plan["mode"] == 2 else 2
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattices": len(sims), "nx": NX, "ny": NY, "nodes_per_step": nodes,
+        "config": {"workload": WORKLOAD, "lattices": len(specs), "nx": NX, "ny": NY, "nodes_per_step": nodes,
+                   "engine": f"batched ({mode}, tiles {plan['tile_width'] or 'per-instance'})",
                    "parallelism": f"replicas{ws}", "l2": "state > L2 (about 180 MB per step), no flush"},
-        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12,
-                     "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "traffic": None, "flop_convention": "1 per FP64 add/mul/fma instruction",
+        "roofline": {"bound": "alu", "kernel": f"batched step: density/psi + collision passes ({mode})",
+                     "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": None,
+                     "flop_convention": "1 per FP64 add/mul/fma instruction; 84 per node update",
                      "peak_source": f"2 FP64 instr/clk/SM x 152 SMs x {sm_max:.0f} MHz",
-                     "launch_ms": per_launch_s * 1e3},
-        "roofline_hbm": {"kernel": dom_name, "achieved": BYTES_PER_NODE[dom_name] * NX * NY / per_launch_s / 1e9,
-                         "peak": hbm_gbs, "unit": "GB/s",
-                         "frac": BYTES_PER_NODE[dom_name] * NX * NY / per_launch_s / 1e9 / hbm_gbs,
-                         "peak_source": peak_src},
-        "kernel_ms": {"rho_psi": k_ms[0] / max(1, k_n[0]), "collide": k_ms[1] / max(1, k_n[1])},
+                     "launch_ms": step_s * 1e3},
+        "roofline_hbm": {"achieved": bytes_per_node * nodes / step_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": bytes_per_node * nodes / step_s / 1e9 / hbm_gbs,
+                         "bytes_per_node": bytes_per_node, "peak_source": peak_src},
+        "autotune_ms_per_step": {"launches": plan["ms_launches"], "graph": plan["ms_graph"],
+                                 "persistent": plan["ms_persistent"]},
+        "serial_contexts": {"mlups": nodes * serial_steps / (ms_serial / 1e3) / 1e6, "steps": serial_steps,
+                            "kernel_ms": {"rho_psi": k_ms[0] / max(1, k_n[0]),
+                                          "collide": k_ms[1] / max(1, k_n[1])}},
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
-                "h2d_bytes_per_step": 8 * NX * NY * len(sims), "d2h_bytes_per_step": 8 * NX * NY * len(sims),
+                "h2d_bytes_per_step": 8 * NX * NY * len(specs), "d2h_bytes_per_step": 8 * NX * NY * len(specs),
                 "call": f"pplbm_run_host per lattice: H2D rho0 (pinned), f=f_eq, {E2E_INNER} steps, D2H rho"},
-        "gpu_launches": 2 * len(sims) * args.steps,
+        "gpu_launches": launches_per_step * args.steps + (1 if plan["mode"] == 2 else 0),
         "clocks": clk,
     }
+    if rank == 0 and ws == 1 and not args.no_sweep:
+        line["batch_sweep"] = sweep_comparison(torch, stream, 100)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for s in sims:
-        s.close()
+    batch.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 

@@ -190,6 +190,76 @@ pplbm_status pplbm_get_derived(const pplbm_ctx* ctx, pplbm_eos_derived* out);
 pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0,
                             int64_t nsteps, double* rho_out);
 
+/* ---- Batched engine: many independent lattices advanced together ----------
+ * The instances may differ in size, boundary flags, EOS parameters (e.g. a sweep
+ * of reduced temperatures) and relaxation times, but must share one collision
+ * kind (all tau = 1; only tau_nu or the two-phase tau(rho) relaxing; or general
+ * MRT). Work is partitioned by 256-node blocks and 256-thread tiles across all
+ * instances, so one launch per pass covers the whole batch; the per-node
+ * arithmetic is the single-lattice step's, and a batched step is bitwise equal
+ * to stepping each lattice alone. */
+typedef struct pplbm_batch pplbm_batch;
+
+#define PPLBM_PLAN_LAUNCHES 0    /* two launches per step covering all instances */
+#define PPLBM_PLAN_GRAPH 1       /* the same launches, two steps per replayed CUDA graph */
+#define PPLBM_PLAN_PERSISTENT 2  /* one cooperative launch per call; bounded grid barriers
+                                    between the passes (PPLBM_ERR_TIMEOUT if a wait gives up) */
+
+typedef struct pplbm_batch_plan {
+  int32_t mode;        /* PPLBM_PLAN_* */
+  int32_t tile_width;  /* collision tile width; 0 = per instance, the power of two in [4, 256]
+                          wasting the fewest threads on partial tiles */
+  int32_t k1_blocks;   /* work items of the density/psi pass */
+  int32_t k2_tiles;    /* work items of the collision pass */
+  double ms_launches, ms_graph, ms_persistent;  /* per-step times measured by the autotuner (0 if not) */
+  double ms_chosen;
+} pplbm_batch_plan;
+
+/* Workspace bytes for n instances (each instance's block is 256-byte aligned);
+ * 0 if any lattice or relaxation set is invalid or the collision kinds differ. */
+size_t pplbm_batch_workspace_bytes(int32_t n, const pplbm_lattice* lattices, const pplbm_relax* relax);
+
+/* Creates a batch over caller-owned device workspace (256-byte aligned). eos and
+ * relax are arrays of n; each EOS is set up as in pplbm_eos_setup. The batch owns
+ * a small device block (instance table, work-item tables, barrier, error word)
+ * and a capture stream. Initial plan: PPLBM_PLAN_LAUNCHES, per-instance tiles. */
+pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattice* lattices,
+                                const pplbm_eos_params* eos, const pplbm_relax* relax, double G, void* workspace,
+                                size_t workspace_bytes, void* stream);
+/* As pplbm_init_equilibrium, for instance i. Synchronises. */
+pplbm_status pplbm_batch_init_equilibrium(pplbm_batch* b, int32_t i, const double* rho0, const double* ux0,
+                                          const double* uy0);
+/* Advances every instance by nsteps (asynchronous). */
+pplbm_status pplbm_batch_step(pplbm_batch* b, int64_t nsteps);
+/* As pplbm_get_fields / pplbm_get_f / pplbm_set_f, for instance i. */
+pplbm_status pplbm_batch_get_fields(pplbm_batch* b, int32_t i, double* rho, double* ux, double* uy, double* psi);
+pplbm_status pplbm_batch_get_f(pplbm_batch* b, int32_t i, double* f);
+pplbm_status pplbm_batch_set_f(pplbm_batch* b, int32_t i, const double* f);
+/* Fixes the plan: mode PPLBM_PLAN_*, tile_width 0 (per instance) or a power of two in [4, 256]. */
+pplbm_status pplbm_batch_set_plan(pplbm_batch* b, int32_t mode, int32_t tile_width);
+pplbm_status pplbm_batch_get_plan(const pplbm_batch* b, pplbm_batch_plan* out);
+/* Times trial_steps (>= 2) steps of each mode with per-instance and width-32 tiles
+ * on the current state, keeps the fastest plan and restores the state (it
+ * allocates a temporary copy of every instance's distributions). Synchronises. */
+pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_batch_plan* chosen);
+/* Synchronises; sticky device error (PPLBM_ERR_DIVERGED / PPLBM_ERR_TIMEOUT) and steps issued. */
+pplbm_status pplbm_batch_sync(pplbm_batch* b, int64_t* steps_done);
+pplbm_status pplbm_batch_get_derived(const pplbm_batch* b, int32_t i, pplbm_eos_derived* out);
+/* Timing aid: with capacity > 0, each pplbm_batch_step call is bracketed by CUDA
+ * events; pplbm_batch_times synchronises and returns the summed milliseconds and
+ * steps since the previous call, then resets. */
+pplbm_status pplbm_batch_enable_timing(pplbm_batch* b, int64_t capacity);
+pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps);
+/* Failure-detection self-test of the persistent kernel's bounded grid barrier:
+ * launches one step in which one block leaves without arriving, with waits
+ * limited to spin_limit sleeps of ~100 ns; returns PPLBM_ERR_TIMEOUT when the
+ * others' waits ran out and were reported (the expected outcome). The waits give
+ * up before the collision pass, so the distributions are not touched; the error
+ * word is cleared and the batch stays usable. Synchronises. */
+pplbm_status pplbm_batch_barrier_selftest(pplbm_batch* b, uint32_t spin_limit);
+const char* pplbm_batch_last_error(const pplbm_batch* b);
+void pplbm_batch_destroy(pplbm_batch* b);
+
 /* Self-test of the double-precision reciprocal and square root the step kernels
  * use in place of IEEE division and sqrt (a hardware seed refined by one
  * third-order series step). Evaluates n pseudo-random x = m 2^k (m in [1, 2),

@@ -66,6 +66,19 @@ class pplbm_eos_derived(C.Structure):
         return d
 
 
+class pplbm_batch_plan(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("tile_width", C.c_int32), ("k1_blocks", C.c_int32), ("k2_tiles", C.c_int32),
+                ("ms_launches", C.c_double), ("ms_graph", C.c_double), ("ms_persistent", C.c_double),
+                ("ms_chosen", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+PLAN_LAUNCHES = 0
+PLAN_GRAPH = 1
+PLAN_PERSISTENT = 2
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _SIGS = {
@@ -88,6 +101,24 @@ _SIGS = {
     "pplbm_step_noalloc": (C.c_int, [C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_derived),
                                      C.POINTER(pplbm_relax), _P, _P, _P, C.POINTER(C.c_char_p)]),
     "pplbm_fp64_selftest": (C.c_int, [C.c_longlong, C.c_ulonglong, _P, _P]),
+    "pplbm_batch_workspace_bytes": (C.c_size_t, [C.c_int32, C.POINTER(pplbm_lattice), C.POINTER(pplbm_relax)]),
+    "pplbm_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),
+                                     C.POINTER(pplbm_relax), C.c_double, _P, C.c_size_t, _P]),
+    "pplbm_batch_init_equilibrium": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "pplbm_batch_step": (C.c_int, [_P, C.c_int64]),
+    "pplbm_batch_get_fields": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "pplbm_batch_get_f": (C.c_int, [_P, C.c_int32, _P]),
+    "pplbm_batch_set_f": (C.c_int, [_P, C.c_int32, _P]),
+    "pplbm_batch_set_plan": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "pplbm_batch_get_plan": (C.c_int, [_P, C.POINTER(pplbm_batch_plan)]),
+    "pplbm_batch_autotune": (C.c_int, [_P, C.c_int32, C.POINTER(pplbm_batch_plan)]),
+    "pplbm_batch_sync": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "pplbm_batch_get_derived": (C.c_int, [_P, C.c_int32, C.POINTER(pplbm_eos_derived)]),
+    "pplbm_batch_enable_timing": (C.c_int, [_P, C.c_int64]),
+    "pplbm_batch_times": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
+    "pplbm_batch_barrier_selftest": (C.c_int, [_P, C.c_uint32]),
+    "pplbm_batch_last_error": (C.c_char_p, [_P]),
+    "pplbm_batch_destroy": (None, [_P]),
     "pplbm_last_error": (C.c_char_p, [_P]),
     "pplbm_status_string": (C.c_char_p, [C.c_int]),
     "pplbm_destroy": (None, [_P]),
@@ -126,7 +157,10 @@ class PPLBMError(RuntimeError):
         super().__init__(f"pplbm status {status} ({s}){': ' + msg if msg else ''}")
 
 
-def check(status, ctx=None):
+def check(status, ctx=None, batch=None):
     if status != PPLBM_OK:
-        msg = lib().pplbm_last_error(ctx).decode() if ctx else ""
+        if batch:
+            msg = lib().pplbm_batch_last_error(batch).decode()
+        else:
+            msg = lib().pplbm_last_error(ctx).decode() if ctx else ""
         raise PPLBMError(status, msg)

@@ -1,0 +1,784 @@
+// Batched engine: many independent lattices (uneven sizes, their own EOS and
+// relaxation times, one collision kind) advanced together.
+//
+// Work is partitioned by blocks, not by instances: the density/psi pass runs one
+// 256-node block per work item; the collision pass runs one 256-thread tile per
+// work item, with a tile shape (tw x th, tw*th = 256) chosen per instance so that
+// narrow lattices (the 4-wide planar ones) do not leave threads idle. A
+// device-resident table maps each work item to its instance. Three ways to run a
+// step, chosen by the autotuner:
+//   PLAN_LAUNCHES   two launches per step covering every instance;
+//   PLAN_GRAPH      the same two launches, two steps captured in a CUDA graph that
+//                   is replayed;
+//   PLAN_PERSISTENT one cooperative launch for all steps of a call: a grid-stride
+//                   loop over work items with a grid barrier between the passes.
+//                   Every barrier wait is bounded: after the spin limit the block
+//                   sets the error word (PPLBM_ERR_TIMEOUT) and returns.
+// The per-node arithmetic is the single-lattice kernels' (step_device.cuh), so a
+// batched step is bitwise identical to stepping each lattice alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pplbm.h"
+#include "step_device.cuh"
+
+namespace pplbm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxTileSmem = (256 + 2) * (1 + 2);  // largest (tw + 2)(th + 2) over tw*th = 256
+constexpr unsigned kSpinLimit = 1u << 24;           // x ~100 ns sleeps: ~1.7 s per barrier wait
+constexpr int kErrDiverged = 1;
+constexpr int kErrTimeout = 2;
+
+struct BatchInst {
+  StepArgs a[2];  // a[p] reads f from buffer p and writes buffer 1 - p
+  int tw, th, log2tw, tiles_x;
+  int k1_start, k2_start;
+};
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int generation;
+};
+
+// Bounded grid-wide barrier for a cooperative launch; false if a wait gave up.
+__device__ bool grid_barrier(GridBarrier* b, int* err, unsigned spin_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &b->generation;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&b->count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      b->count = 0u;
+      __threadfence();
+      atomicAdd(&b->generation, 1u);
+    } else {
+      unsigned int it = 0;
+      while (*gen == g) {
+        if (++it > spin_limit) {
+          atomicOr(err, kErrTimeout);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return (*(volatile int*)err & kErrTimeout) == 0;
+}
+
+// Copies instance id's StepArgs for `parity` into shared memory (uniform across
+// the block, so every later field read is a shared-memory broadcast).
+__device__ __forceinline__ void stage_args(const BatchInst* __restrict__ inst, int id, int parity, StepArgs* sa) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&inst[id].a[parity]);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(sa);
+  for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / 8); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+}
+
+template <int KIND>
+__device__ __forceinline__ void batch_rho_psi_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
+                                                   int w, int parity, StepArgs* sa) {
+  const int id = owner[w];
+  stage_args(inst, id, parity, sa);
+  const int64_t i = (int64_t)(w - inst[id].k1_start) * kThreads + threadIdx.x;
+  if (i < sa->n) rho_psi_node<KIND>(*sa, sa->f_in, i);
+  __syncthreads();
+}
+
+template <int KIND>
+__device__ __forceinline__ void batch_collide_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
+                                                   int w, int parity, double* sp, StepArgs* sa) {
+  const int id = owner[w];
+  stage_args(inst, id, parity, sa);
+  const StepArgs& a = *sa;
+  const BatchInst& I = inst[id];
+  const int tw = I.tw, th = I.th, log2tw = I.log2tw, tiles_x = I.tiles_x;
+  const int t = w - I.k2_start;
+  const int tyi = t / tiles_x;
+  const int x0 = (t - tyi * tiles_x) * tw, y0 = tyi * th;
+  load_psi_tile(a, sp, x0, y0, tw, th, threadIdx.x, kThreads);
+  __syncthreads();
+  const int lx = threadIdx.x & (tw - 1), ly = threadIdx.x >> log2tw;
+  const int x = x0 + lx, y = y0 + ly;
+  if (x < a.nx && y < a.ny)
+    collide_node<KIND, false>(a, x, y, sp, (ly + 1) * (tw + 2) + lx + 1, tw + 2, nullptr, nullptr, nullptr, nullptr);
+  __syncthreads();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_batch_rho_psi(const BatchInst* inst, const int* owner, int parity) {
+  __shared__ StepArgs sa;
+  batch_rho_psi_item<KIND>(inst, owner, blockIdx.x, parity, &sa);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_batch_collide(const BatchInst* inst, const int* owner, int parity) {
+  __shared__ double sp[kMaxTileSmem];
+  __shared__ StepArgs sa;
+  batch_collide_item<KIND>(inst, owner, blockIdx.x, parity, sp, &sa);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* inst, const int* owner1, int n1,
+                                                               const int* owner2, int n2, int parity0, long long nsteps,
+                                                               GridBarrier* bar, int* err, unsigned spin_limit,
+                                                               int absent_block) {
+  __shared__ double sp[kMaxTileSmem];
+  __shared__ StepArgs sa;
+  // barrier self-test only: one block leaves without arriving, so the others' waits run out
+  if ((int)blockIdx.x == absent_block) return;
+  for (long long s = 0; s < nsteps; ++s) {
+    const int parity = (int)((parity0 + s) & 1);
+    for (int w = blockIdx.x; w < n1; w += gridDim.x) batch_rho_psi_item<KIND>(inst, owner1, w, parity, &sa);
+    if (!grid_barrier(bar, err, spin_limit)) return;
+    for (int w = blockIdx.x; w < n2; w += gridDim.x) batch_collide_item<KIND>(inst, owner2, w, parity, sp, &sa);
+    if (!grid_barrier(bar, err, spin_limit)) return;
+  }
+}
+
+const void* persistent_kernel(int kind) {
+  switch (kind) {
+    case kUnitTau: return (const void*)k_batch_persistent<kUnitTau>;
+    case kShearTau: return (const void*)k_batch_persistent<kShearTau>;
+    default: return (const void*)k_batch_persistent<kFullMrt>;
+  }
+}
+
+void launch_pair(int kind, const BatchInst* inst, const int* o1, int n1, const int* o2, int n2, int parity,
+                 cudaStream_t s) {
+  switch (kind) {
+    case kUnitTau:
+      k_batch_rho_psi<kUnitTau><<<n1, kThreads, 0, s>>>(inst, o1, parity);
+      k_batch_collide<kUnitTau><<<n2, kThreads, 0, s>>>(inst, o2, parity);
+      break;
+    case kShearTau:
+      k_batch_rho_psi<kShearTau><<<n1, kThreads, 0, s>>>(inst, o1, parity);
+      k_batch_collide<kShearTau><<<n2, kThreads, 0, s>>>(inst, o2, parity);
+      break;
+    default:
+      k_batch_rho_psi<kFullMrt><<<n1, kThreads, 0, s>>>(inst, o1, parity);
+      k_batch_collide<kFullMrt><<<n2, kThreads, 0, s>>>(inst, o2, parity);
+      break;
+  }
+}
+
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+// collision kind and validity, as pplbm_create
+int kind_of(const pplbm_relax* r) {
+  if (!r || r->reserved != 0) return -1;
+  if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
+  if (r->kind == PPLBM_RELAX_TWO_PHASE) return (r->tau_l > 0.5 && r->visc_ratio > 0.0) ? kShearTau : -1;
+  if (r->kind != PPLBM_RELAX_MRT) return -1;
+  const double t[6] = {r->tau_rho, r->tau_e, r->tau_zeta, r->tau_j, r->tau_q, r->tau_nu};
+  for (double v : t)
+    if (!(v > 0.5) || !std::isfinite(v)) return -1;
+  if (r->tau_rho == 1.0 && r->tau_e == 1.0 && r->tau_zeta == 1.0 && r->tau_j == 1.0 && r->tau_q == 1.0)
+    return r->tau_nu == 1.0 ? kUnitTau : kShearTau;
+  return kFullMrt;
+}
+
+bool lattice_ok(const pplbm_lattice* l) {
+  if (!l || l->nx < 1 || l->ny < 1 || l->reserved != 0) return false;
+  if (9 * (int64_t)l->nx * l->ny >= ((int64_t)1 << 31)) return false;
+  if (!(l->bc & PPLBM_BC_PERIODIC_X)) return false;
+  const uint32_t walls = l->bc & (PPLBM_BC_WALL_BOTTOM | PPLBM_BC_WALL_TOP);
+  if (l->bc & PPLBM_BC_PERIODIC_Y) return walls == 0;
+  return walls == (PPLBM_BC_WALL_BOTTOM | PPLBM_BC_WALL_TOP);
+}
+
+size_t inst_doubles(const pplbm_lattice& l, int kind) {
+  const size_t n = (size_t)l.nx * l.ny;
+  const size_t d = n * (19 + (size_t)moment_planes(kind));
+  return (d + 31) & ~(size_t)31;  // 256-byte aligned instances
+}
+
+// tile width for a lattice: the power of two in [4, 256] that wastes the fewest
+// threads on partial tiles (ties go to the width closest to 32)
+int model_tile_width(int nx, int ny) {
+  int best = 32;
+  long long best_waste = -1;
+  for (int tw = 4; tw <= 256; tw *= 2) {
+    const int th = 256 / tw;
+    const long long tiles = (long long)((nx + tw - 1) / tw) * ((ny + th - 1) / th);
+    const long long waste = tiles * 256 - (long long)nx * ny;
+    const int dist = std::abs(ilog2(tw) - 5);
+    if (best_waste < 0 || waste < best_waste || (waste == best_waste && dist < std::abs(ilog2(best) - 5))) {
+      best = tw;
+      best_waste = waste;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+}  // namespace pplbm
+
+using namespace pplbm;
+
+struct pplbm_batch {
+  int n;
+  int kind;
+  std::vector<pplbm_lattice> lat;
+  std::vector<pplbm_relax> relax;
+  std::vector<pplbm_eos_derived> eos;
+  std::vector<BatchInst> host_inst;
+  std::vector<double*> bufA, bufB;  // per instance: the two f buffers
+  int parity;                       // state of every instance is in buffer `parity`
+  cudaStream_t stream;
+  cudaStream_t capture_stream;
+  void* dev_block;                  // owned: instance table, owners, barrier, error word
+  BatchInst* d_inst;
+  int* d_owner1;
+  int* d_owner2;
+  int n1, n2;
+  GridBarrier* d_bar;
+  int* d_err;
+  int persistent_grid;
+  pplbm_batch_plan plan;
+  cudaGraphExec_t graph[2];  // graph[p]: two steps starting from parity p
+  int64_t steps;
+  pplbm_status sticky;
+  std::string msg;
+  bool timing;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used;
+  int64_t timed_steps;
+};
+
+namespace {
+
+pplbm_status bfail(pplbm_batch* b, pplbm_status s, const char* fmt, ...) {
+  if (b) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    b->msg = buf;
+  }
+  return s;
+}
+
+#define BTRY(b, call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return bfail((b), PPLBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_dev(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// rebuild the per-instance tile shapes and the owner tables for a tile-width policy
+pplbm_status build_tables(pplbm_batch* b, int tile_width) {
+  std::vector<int> o1, o2;
+  for (int i = 0; i < b->n; ++i) {
+    BatchInst& I = b->host_inst[i];
+    const int nx = b->lat[i].nx, ny = b->lat[i].ny;
+    const int tw = tile_width > 0 ? tile_width : model_tile_width(nx, ny);
+    I.tw = tw;
+    I.th = 256 / tw;
+    I.log2tw = ilog2(tw);
+    I.tiles_x = (nx + tw - 1) / tw;
+    const int tiles = I.tiles_x * ((ny + I.th - 1) / I.th);
+    const int64_t n = (int64_t)nx * ny;
+    I.k1_start = (int)o1.size();
+    for (int64_t k = 0; k < (n + kThreads - 1) / kThreads; ++k) o1.push_back(i);
+    I.k2_start = (int)o2.size();
+    for (int k = 0; k < tiles; ++k) o2.push_back(i);
+  }
+  if (o1.size() > (size_t)INT32_MAX / 2 || o2.size() > (size_t)INT32_MAX / 2)
+    return bfail(b, PPLBM_ERR_ARG, "batch too large");
+  b->n1 = (int)o1.size();
+  b->n2 = (int)o2.size();
+  // owner tables live in a device block sized at create for the worst case (tw = 4 or 256)
+  BTRY(b, cudaMemcpyAsync(b->d_inst, b->host_inst.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice,
+                          b->stream));
+  BTRY(b, cudaMemcpyAsync(b->d_owner1, o1.data(), sizeof(int) * o1.size(), cudaMemcpyHostToDevice, b->stream));
+  BTRY(b, cudaMemcpyAsync(b->d_owner2, o2.data(), sizeof(int) * o2.size(), cudaMemcpyHostToDevice, b->stream));
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  return PPLBM_OK;
+}
+
+void destroy_graphs(pplbm_batch* b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->graph[p]) {
+      cudaGraphExecDestroy(b->graph[p]);
+      b->graph[p] = nullptr;
+    }
+}
+
+pplbm_status build_graphs(pplbm_batch* b) {
+  destroy_graphs(b);
+  for (int p = 0; p < 2; ++p) {
+    cudaGraph_t g;
+    BTRY(b, cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+    launch_pair(b->kind, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, p, b->capture_stream);
+    launch_pair(b->kind, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, 1 - p, b->capture_stream);
+    BTRY(b, cudaStreamEndCapture(b->capture_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&b->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, PPLBM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  return PPLBM_OK;
+}
+
+pplbm_status apply_plan(pplbm_batch* b, int mode, int tile_width) {
+  if (mode != PPLBM_PLAN_LAUNCHES && mode != PPLBM_PLAN_GRAPH && mode != PPLBM_PLAN_PERSISTENT)
+    return bfail(b, PPLBM_ERR_ARG, "unknown plan mode %d", mode);
+  if (tile_width != 0 && (tile_width < 4 || tile_width > 256 || (tile_width & (tile_width - 1))))
+    return bfail(b, PPLBM_ERR_ARG, "tile width must be 0 or a power of two in [4, 256]");
+  if (pplbm_status s = build_tables(b, tile_width)) return s;
+  destroy_graphs(b);
+  if (mode == PPLBM_PLAN_GRAPH)
+    if (pplbm_status s = build_graphs(b)) return s;
+  b->plan.mode = mode;
+  b->plan.tile_width = tile_width;
+  b->plan.k1_blocks = b->n1;
+  b->plan.k2_tiles = b->n2;
+  return PPLBM_OK;
+}
+
+pplbm_status poll(pplbm_batch* b) {
+  int h = 0;
+  BTRY(b, cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  if (h != 0 && b->sticky == PPLBM_OK) {
+    if (h & kErrTimeout) {
+      b->sticky = PPLBM_ERR_TIMEOUT;
+      b->msg = "a grid-barrier wait of the persistent kernel gave up";
+    } else {
+      b->sticky = PPLBM_ERR_DIVERGED;
+      b->msg = "a kernel met a non-finite or non-positive density, or psi^2 <= 0";
+    }
+  }
+  return b->sticky;
+}
+
+pplbm_status launch_persistent(pplbm_batch* b, int64_t nsteps, cudaStream_t s, unsigned spin_limit, int absent) {
+  BTRY(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), s));
+  int parity0 = b->parity;
+  long long ns = nsteps;
+  void* args[] = {(void*)&b->d_inst, (void*)&b->d_owner1, (void*)&b->n1,     (void*)&b->d_owner2,
+                  (void*)&b->n2,     (void*)&parity0,     (void*)&ns,        (void*)&b->d_bar,
+                  (void*)&b->d_err,  (void*)&spin_limit,  (void*)&absent};
+  BTRY(b, cudaLaunchCooperativeKernel(persistent_kernel(b->kind), dim3(b->persistent_grid), dim3(kThreads), args, 0,
+                                      s));
+  return PPLBM_OK;
+}
+
+pplbm_status issue_steps(pplbm_batch* b, int64_t nsteps, cudaStream_t s) {
+  int64_t k = 0;
+  if (b->plan.mode == PPLBM_PLAN_PERSISTENT && nsteps > 0) {
+    if (pplbm_status st = launch_persistent(b, nsteps, s, kSpinLimit, -1)) return st;
+    b->parity = (int)((b->parity + nsteps) & 1);
+    return PPLBM_OK;
+  }
+  if (b->plan.mode == PPLBM_PLAN_GRAPH) {
+    for (; k + 2 <= nsteps; k += 2) BTRY(b, cudaGraphLaunch(b->graph[b->parity], s));
+  }
+  for (; k < nsteps; ++k) {
+    launch_pair(b->kind, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, b->parity, s);
+    b->parity ^= 1;
+  }
+  BTRY(b, cudaGetLastError());
+  return PPLBM_OK;
+}
+
+// StepArgs of instance i reading buffer `parity`
+StepArgs& args_of(pplbm_batch* b, int i) { return b->host_inst[i].a[b->parity]; }
+
+}  // namespace
+
+extern "C" {
+
+size_t pplbm_batch_workspace_bytes(int32_t n, const pplbm_lattice* lattices, const pplbm_relax* relax) {
+  if (n < 1 || !lattices || !relax) return 0;
+  size_t total = 0;
+  const int k0 = kind_of(&relax[0]);
+  for (int i = 0; i < n; ++i) {
+    const int k = kind_of(&relax[i]);
+    if (k < 0 || k != k0 || !lattice_ok(&lattices[i])) return 0;
+    total += inst_doubles(lattices[i], k);
+  }
+  return total * sizeof(double);
+}
+
+pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattice* lattices,
+                                const pplbm_eos_params* eos, const pplbm_relax* relax, double G, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+  if (!out) return PPLBM_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || !lattices || !eos || !relax || !workspace) return PPLBM_ERR_ARG;
+  const size_t need = pplbm_batch_workspace_bytes(n, lattices, relax);
+  if (need == 0 || workspace_bytes < need || ((uintptr_t)workspace & 255u)) return PPLBM_ERR_ARG;
+  pplbm_batch* b = new (std::nothrow) pplbm_batch();
+  if (!b) return PPLBM_ERR_ARG;
+  b->n = n;
+  b->kind = kind_of(&relax[0]);
+  b->lat.assign(lattices, lattices + n);
+  b->relax.assign(relax, relax + n);
+  b->eos.resize(n);
+  b->host_inst.resize(n);
+  b->bufA.resize(n);
+  b->bufB.resize(n);
+  b->stream = (cudaStream_t)stream;
+  b->sticky = PPLBM_OK;
+  for (int i = 0; i < n; ++i) {
+    const pplbm_status st = pplbm_eos_setup(&eos[i], G, &b->eos[i]);
+    if (st != PPLBM_OK) {
+      delete b;
+      return st;
+    }
+  }
+  // the largest owner tables any tile width can produce
+  size_t max1 = 0, max2 = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t nn = (int64_t)lattices[i].nx * lattices[i].ny;
+    max1 += (nn + kThreads - 1) / kThreads;
+    size_t worst = 0;
+    for (int tw = 4; tw <= 256; tw *= 2)
+      worst = std::max(worst, (size_t)((lattices[i].nx + tw - 1) / tw) * ((lattices[i].ny + 256 / tw - 1) / (256 / tw)));
+    max2 += worst;
+  }
+  const size_t inst_bytes = ((sizeof(BatchInst) * n + 255) / 256) * 256;
+  const size_t o1_bytes = ((sizeof(int) * max1 + 255) / 256) * 256;
+  const size_t o2_bytes = ((sizeof(int) * max2 + 255) / 256) * 256;
+  const size_t block = inst_bytes + o1_bytes + o2_bytes + 256 + 256;
+  if (cudaMalloc(&b->dev_block, block) != cudaSuccess) {
+    delete b;
+    return PPLBM_ERR_CUDA;
+  }
+  char* p = (char*)b->dev_block;
+  b->d_inst = (BatchInst*)p;
+  b->d_owner1 = (int*)(p + inst_bytes);
+  b->d_owner2 = (int*)(p + inst_bytes + o1_bytes);
+  b->d_bar = (GridBarrier*)(p + inst_bytes + o1_bytes + o2_bytes);
+  b->d_err = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 256);
+  if (cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(b->dev_block);
+    delete b;
+    return PPLBM_ERR_CUDA;
+  }
+  cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  double* w = (double*)workspace;
+  for (int i = 0; i < n; ++i) {
+    const pplbm_lattice& L = lattices[i];
+    const pplbm_relax& r = relax[i];
+    const pplbm_eos_derived& d = b->eos[i];
+    const int64_t nn = (int64_t)L.nx * L.ny;
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = w + 18 * nn;
+    a.mom = w + 19 * nn;
+    a.err = b->d_err;
+    a.nx = L.nx;
+    a.ny = L.ny;
+    a.n = nn;
+    a.walls = (L.bc & PPLBM_BC_PERIODIC_Y) ? 0 : 1;
+    a.kind = b->kind;
+    a.eos = make_eos_const(d);
+    a.G = G;
+    a.half_force = -G / 24.0;
+    a.psi_ghost_bottom = d.psi_l;
+    a.psi_ghost_top = d.psi_v;
+    const double sigma = r.forcing == PPLBM_FORCING_GUO ? 0.0 : r.sigma_auto ? -d.eps / (16.0 * G) : r.sigma;
+    if (b->kind == kShearTau) {
+      if (r.kind == PPLBM_RELAX_TWO_PHASE) {
+        const double tv = 0.5 + r.visc_ratio * (r.tau_l - 0.5);
+        a.tau_b = (r.tau_l - tv) / (d.rho_l - d.rho_v);
+        a.tau_a = r.tau_l - a.tau_b * d.rho_l;
+      } else {
+        a.tau_a = r.tau_nu;
+        a.tau_b = 0.0;
+      }
+    }
+    a.zz_scale = sigma * G * G / 432.0;
+    if (b->kind == kFullMrt) {
+      const double t[9] = {r.tau_rho, r.tau_e, r.tau_zeta, r.tau_j, r.tau_q, r.tau_j, r.tau_q, r.tau_nu, r.tau_nu};
+      for (int k = 0; k < 9; ++k) a.omega[k] = 1.0 / t[k];
+      a.li_e = 12.0 * sigma / (r.tau_e - 0.5);
+      a.li_z = 12.0 * sigma / (r.tau_zeta - 0.5);
+    }
+    b->bufA[i] = w;
+    b->bufB[i] = w + 9 * nn;
+    BatchInst& I = b->host_inst[i];
+    I.a[0] = a;
+    I.a[0].f_in = b->bufA[i];
+    I.a[0].f_out = b->bufB[i];
+    I.a[1] = a;
+    I.a[1].f_in = b->bufB[i];
+    I.a[1].f_out = b->bufA[i];
+    w += inst_doubles(L, b->kind);
+  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel(b->kind), kThreads, 0);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->persistent_grid = std::max(1, occ * sms);
+  pplbm_status s = apply_plan(b, PPLBM_PLAN_LAUNCHES, 0);
+  if (s != PPLBM_OK) {
+    pplbm_batch_destroy(b);
+    return s;
+  }
+  b->persistent_grid = std::min(b->persistent_grid, std::max(b->n1, b->n2));
+  *out = b;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_init_equilibrium(pplbm_batch* b, int32_t i, const double* rho0, const double* ux0,
+                                          const double* uy0) {
+  if (!b || i < 0 || i >= b->n || !rho0) return bfail(b, PPLBM_ERR_ARG, "bad instance or NULL rho0");
+  if (b->sticky) return b->sticky;
+  StepArgs& a = args_of(b, i);
+  const double* src[3] = {rho0, ux0, uy0};
+  const double* dev[3];
+  for (int k = 0; k < 3; ++k) {
+    if (!src[k] || is_dev(src[k])) {
+      dev[k] = src[k];
+    } else {  // stage host data in the other f buffer, unused between steps
+      double* dst = const_cast<double*>(a.f_out) + (int64_t)k * a.n;
+      BTRY(b, cudaMemcpyAsync(dst, src[k], sizeof(double) * a.n, cudaMemcpyHostToDevice, b->stream));
+      dev[k] = dst;
+    }
+  }
+  launch_init_eq(a, const_cast<double*>(a.f_in), dev[0], dev[1], dev[2], b->stream);
+  BTRY(b, cudaGetLastError());
+  return poll(b);
+}
+
+pplbm_status pplbm_batch_step(pplbm_batch* b, int64_t nsteps) {
+  if (!b || nsteps < 0) return bfail(b, PPLBM_ERR_ARG, "nsteps < 0");
+  if (b->sticky) return b->sticky;
+  if (b->timing) {
+    while (b->ev.size() < b->ev_used + 2) {
+      cudaEvent_t e;
+      BTRY(b, cudaEventCreate(&e));
+      b->ev.push_back(e);
+    }
+    BTRY(b, cudaEventRecord(b->ev[b->ev_used], b->stream));
+  }
+  if (pplbm_status s = issue_steps(b, nsteps, b->stream)) return s;
+  if (b->timing) {
+    BTRY(b, cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
+    b->ev_used += 2;
+    b->timed_steps += nsteps;
+  }
+  b->steps += nsteps;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_get_fields(pplbm_batch* b, int32_t i, double* rho, double* ux, double* uy, double* psi) {
+  if (!b || i < 0 || i >= b->n) return bfail(b, PPLBM_ERR_ARG, "bad instance");
+  if (b->sticky) return b->sticky;
+  StepArgs a = args_of(b, i);
+  launch_rho_psi(a, b->stream);
+  double* outs[4] = {rho, ux, uy, psi};
+  double* dst[4];
+  bool host[4];
+  for (int k = 0; k < 4; ++k) {
+    host[k] = outs[k] && !is_dev(outs[k]);
+    dst[k] = host[k] ? a.f_out + (int64_t)k * a.n : outs[k];
+  }
+  launch_fields(a, dst[0], dst[1], dst[2], dst[3], b->stream);
+  BTRY(b, cudaGetLastError());
+  for (int k = 0; k < 4; ++k)
+    if (host[k]) BTRY(b, cudaMemcpyAsync(outs[k], dst[k], sizeof(double) * a.n, cudaMemcpyDeviceToHost, b->stream));
+  return poll(b);
+}
+
+pplbm_status pplbm_batch_get_f(pplbm_batch* b, int32_t i, double* f) {
+  if (!b || i < 0 || i >= b->n || !f) return bfail(b, PPLBM_ERR_ARG, "bad instance or NULL f");
+  const StepArgs& a = args_of(b, i);
+  BTRY(b, cudaMemcpyAsync(f, a.f_in, sizeof(double) * 9 * a.n, cudaMemcpyDefault, b->stream));
+  if (!is_dev(f)) BTRY(b, cudaStreamSynchronize(b->stream));
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_set_f(pplbm_batch* b, int32_t i, const double* f) {
+  if (!b || i < 0 || i >= b->n || !f) return bfail(b, PPLBM_ERR_ARG, "bad instance or NULL f");
+  if (b->sticky) return b->sticky;
+  const StepArgs& a = args_of(b, i);
+  BTRY(b, cudaMemcpyAsync(const_cast<double*>(a.f_in), f, sizeof(double) * 9 * a.n, cudaMemcpyDefault, b->stream));
+  if (!is_dev(f)) BTRY(b, cudaStreamSynchronize(b->stream));
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_set_plan(pplbm_batch* b, int32_t mode, int32_t tile_width) {
+  if (!b) return PPLBM_ERR_ARG;
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  return apply_plan(b, mode, tile_width);
+}
+
+pplbm_status pplbm_batch_get_plan(const pplbm_batch* b, pplbm_batch_plan* out) {
+  if (!b || !out) return PPLBM_ERR_ARG;
+  *out = b->plan;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_batch_plan* chosen) {
+  if (!b || trial_steps < 2) return bfail(b, PPLBM_ERR_ARG, "trial_steps < 2");
+  if (b->sticky) return b->sticky;
+  // keep the state: copy every instance's current f aside, restore it afterwards
+  size_t total = 0;
+  for (int i = 0; i < b->n; ++i) total += 9 * (size_t)b->lat[i].nx * b->lat[i].ny;
+  double* backup = nullptr;
+  BTRY(b, cudaMalloc(&backup, total * sizeof(double)));
+  const int parity0 = b->parity;
+  size_t off = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const StepArgs& a = args_of(b, i);
+    cudaMemcpyAsync(backup + off, a.f_in, sizeof(double) * 9 * a.n, cudaMemcpyDeviceToDevice, b->stream);
+    off += 9 * (size_t)a.n;
+  }
+  const int modes[3] = {PPLBM_PLAN_LAUNCHES, PPLBM_PLAN_GRAPH, PPLBM_PLAN_PERSISTENT};
+  const int widths[2] = {0, 32};
+  double best = 1e300;
+  int best_mode = PPLBM_PLAN_LAUNCHES, best_w = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  pplbm_status st = PPLBM_OK;
+  for (int m : modes) {
+    for (int wd : widths) {
+      if ((st = apply_plan(b, m, wd)) != PPLBM_OK) break;
+      if ((st = issue_steps(b, 2, b->stream)) != PPLBM_OK) break;  // warm-up
+      cudaEventRecord(e0, b->stream);
+      if ((st = issue_steps(b, trial_steps, b->stream)) != PPLBM_OK) break;
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = bfail(b, PPLBM_ERR_CUDA, "autotune timing failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = ms / trial_steps;
+      if (m == PPLBM_PLAN_LAUNCHES) b->plan.ms_launches = per;
+      if (m == PPLBM_PLAN_GRAPH) b->plan.ms_graph = per;
+      if (m == PPLBM_PLAN_PERSISTENT) b->plan.ms_persistent = per;
+      if (per < best) {
+        best = per;
+        best_mode = m;
+        best_w = wd;
+      }
+    }
+    if (st != PPLBM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the state into buffer parity0
+  b->parity = parity0;
+  off = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const StepArgs& a = args_of(b, i);
+    cudaMemcpyAsync(const_cast<double*>(a.f_in), backup + off, sizeof(double) * 9 * a.n, cudaMemcpyDeviceToDevice,
+                    b->stream);
+    off += 9 * (size_t)a.n;
+  }
+  cudaStreamSynchronize(b->stream);
+  cudaFree(backup);
+  if (st != PPLBM_OK) return st;
+  if (pplbm_status s = poll(b)) return s;
+  const double keep_l = b->plan.ms_launches, keep_g = b->plan.ms_graph, keep_p = b->plan.ms_persistent;
+  if (pplbm_status s = apply_plan(b, best_mode, best_w)) return s;
+  b->plan.ms_launches = keep_l;
+  b->plan.ms_graph = keep_g;
+  b->plan.ms_persistent = keep_p;
+  b->plan.ms_chosen = best;
+  if (chosen) *chosen = b->plan;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_sync(pplbm_batch* b, int64_t* steps_done) {
+  if (!b) return PPLBM_ERR_ARG;
+  const pplbm_status s = poll(b);
+  if (steps_done) *steps_done = b->steps;
+  return s;
+}
+
+pplbm_status pplbm_batch_get_derived(const pplbm_batch* b, int32_t i, pplbm_eos_derived* out) {
+  if (!b || i < 0 || i >= b->n || !out) return PPLBM_ERR_ARG;
+  *out = b->eos[i];
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_enable_timing(pplbm_batch* b, int64_t capacity) {
+  if (!b || capacity < 0) return PPLBM_ERR_ARG;
+  b->timing = capacity > 0;
+  while (b->ev.size() < 2 * (size_t)capacity) {
+    cudaEvent_t e;
+    BTRY(b, cudaEventCreate(&e));
+    b->ev.push_back(e);
+  }
+  b->ev_used = 0;
+  b->timed_steps = 0;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps) {
+  if (!b || !ms || !steps) return PPLBM_ERR_ARG;
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  double acc = 0.0;
+  for (size_t k = 0; k + 1 < b->ev_used; k += 2) {
+    float t = 0.f;
+    BTRY(b, cudaEventElapsedTime(&t, b->ev[k], b->ev[k + 1]));
+    acc += t;
+  }
+  *ms = acc;
+  *steps = b->timed_steps;
+  b->ev_used = 0;
+  b->timed_steps = 0;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_barrier_selftest(pplbm_batch* b, uint32_t spin_limit) {
+  if (!b || spin_limit < 1) return PPLBM_ERR_ARG;
+  if (b->sticky) return b->sticky;
+  if (b->persistent_grid < 2) return bfail(b, PPLBM_ERR_STATE, "barrier self-test needs at least two blocks");
+  if (pplbm_status s = launch_persistent(b, 1, b->stream, spin_limit, b->persistent_grid - 1)) return s;
+  int h = 0;
+  BTRY(b, cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  // the waits gave up before the collision pass, so no distribution was written:
+  // clear the word and keep the batch usable
+  BTRY(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  return (h & kErrTimeout) ? PPLBM_ERR_TIMEOUT : PPLBM_OK;
+}
+
+const char* pplbm_batch_last_error(const pplbm_batch* b) { return b ? b->msg.c_str() : ""; }
+
+void pplbm_batch_destroy(pplbm_batch* b) {
+  if (!b) return;
+  destroy_graphs(b);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->dev_block) cudaFree(b->dev_block);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+// Per-node device code of the two step kernels, shared by the single-lattice
+// kernels (step_kernels.cu) and the batched multi-lattice kernels (batch.cu) so
+// that both perform identical arithmetic.
+//
+// The GB300 FP64 pipe issues about 0.6e12 instructions/s, some 60x below FP32,
+// so these kernels are bound by FP64 issue rather than HBM: the arithmetic is
+// arranged to minimise FP64 instructions per node.
+//  * K1 hands K2 the moments instead of the populations, so K2 never re-sums f.
+//  * With Lambda = I or with only the shear rates relaxing, f* is rebuilt
+//    directly as w_i [rho + 3 c.P + 4.5 (c c - I/3) : Pi] plus the sigma term of
+//    the Li scheme, which M^-1 maps onto (-8, 1, ..., 1) z. This equals
+//    M^-1 m* for the moment vector m* of Eq. LiFS / GFS.
+//  * |F|^2 / psi^2 is (G^2/144) |g|^2 with g the weighted psi differences, so the
+//    Li term needs no division by psi^2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "eos_dev.cuh"
+#include "fp64.cuh"
+#include "internal.h"
+
+namespace pplbm {
+
+// K1 body for node i: moments, EOS, psi (Eqs. Density, Momentum, CS, Sec. III.D,
+// InteractionPotential); error word on a non-finite or non-positive density or psi^2.
+template <int KIND>
+__device__ __forceinline__ void rho_psi_node(const StepArgs& a, const double* __restrict__ f, int64_t i) {
+  const int64_t N = a.n;
+  const double f0 = f[i], f1 = f[N + i], f2 = f[2 * N + i], f3 = f[3 * N + i], f4 = f[4 * N + i];
+  const double f5 = f[5 * N + i], f6 = f[6 * N + i], f7 = f[7 * N + i], f8 = f[8 * N + i];
+  const double sxp = f1 + f5 + f8;  // populations with c_x = +1
+  const double sxm = f3 + f6 + f7;  // c_x = -1
+  const double rho = (f0 + f2 + f4) + (sxp + sxm);
+  const double jx = sxp - sxm;
+  const double jy = (f2 + f5 + f6) - (f4 + f7 + f8);
+  const double psi2 = eos_psi2_dev(a.eos, rho);
+  // 0 < rho < 1e300 and 0 < psi^2 < inf, tested on the bit patterns (integer pipe)
+  const long long rb = dbits(rho), pb = dbits(psi2);
+  if (!(rb > 0 && rb < 0x7E37E43C8800759CLL && pb > 0 && pb < 0x7FF0000000000000LL)) atomicOr(a.err, 1);
+  a.psi[i] = fast_sqrt(psi2);
+  double* __restrict__ m = a.mom;
+  m[i] = rho;
+  m[N + i] = jx;
+  m[2 * N + i] = jy;
+  if (KIND == kShearTau) {
+    m[3 * N + i] = (f1 + f3) - (f2 + f4);  // row 7 of Eq. MatrixMRT
+    m[4 * N + i] = (f5 + f7) - (f6 + f8);  // row 8
+  } else if (KIND == kFullMrt) {
+    const double ax = f1 + f2 + f3 + f4, dg = f5 + f6 + f7 + f8;
+    m[3 * N + i] = -4.0 * f0 - ax + 2.0 * dg;                    // row 1 (e)
+    m[4 * N + i] = 4.0 * f0 - 2.0 * ax + dg;                     // row 2 (varsigma)
+    m[5 * N + i] = -2.0 * (f1 - f3) + ((f5 - f6) - (f7 - f8));   // row 4 (q_x)
+    m[6 * N + i] = -2.0 * (f2 - f4) + ((f5 + f6) - (f7 + f8));   // row 6 (q_y)
+    m[7 * N + i] = (f1 + f3) - (f2 + f4);                        // row 7
+    m[8 * N + i] = (f5 + f7) - (f6 + f8);                        // row 8
+  }
+}
+
+__device__ __forceinline__ int wrap_index(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// psi of the tile [x0 - 1, x0 + tw] x [y0 - 1, y0 + th] into sp (row stride tw + 2):
+// periodic wrap in x; periodic in y, or the wall ghost values beyond the walls.
+__device__ __forceinline__ void load_psi_tile(const StepArgs& a, double* sp, int x0, int y0, int tw, int th,
+                                              int tid, int nthreads) {
+  const int sw = tw + 2;
+  for (int k = tid; k < (th + 2) * sw; k += nthreads) {
+    const int ty = k / sw, tx = k - ty * sw;
+    const int gx = wrap_index(x0 + tx - 1, a.nx);
+    int gy = y0 + ty - 1;
+    double v;
+    if (a.walls) {
+      if (gy < 0) v = a.psi_ghost_bottom;
+      else if (gy >= a.ny) v = a.psi_ghost_top;
+      else v = a.psi[(int64_t)gy * a.nx + gx];
+    } else {
+      gy = wrap_index(gy, a.ny);
+      v = a.psi[(int64_t)gy * a.nx + gx];
+    }
+    sp[k] = v;
+  }
+}
+
+struct Post {
+  double f[9];
+};
+
+// Collision for Lambda = I (KIND kUnitTau) or shear-only relaxation (kShearTau).
+//
+// With h = F/2: J = j + h = rho u (Eq. Momentum), P = j + 2h (momentum after the
+// step), and the post-collision second moments (Lambda = I)
+//   Pi_xx = rho ux^2 + ux Fx = ux (P_x + h_x),  Pi_yy = uy (P_y + h_y),
+//   Pi_xy = rho ux uy + (ux Fy + uy Fx)/2 = ux P_y + uy h_x.
+// These are rows 1, 7, 8 of m* = m_eq + S/2 (Eqs. LiFS, GFS with tau = 1);
+// kShearTau relaxes rows 7, 8 with omega = 1/tau instead. Then
+//   f*_i = w_i [rho + 3 c_i.P + 4.5 (c_i c_i - I/3) : Pi] + z_i,
+// z_i = zz (-8, 1, 1, 1, 1, 1, 1, 1, 1) being M^-1 applied to the Li sigma terms
+// +-12 sigma |F|^2 / psi^2 of rows 1 and 2 (tau_e = tau_zeta = 1), zz = sigma |F|^2 / (3 psi^2).
+template <int KIND>
+__device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node, double rho, double jx, double jy,
+                                                double psi0, double gx, double gy, Post& out, double* ux_o,
+                                                double* uy_o) {
+  const double cH = a.half_force * psi0;  // h = cH g, cH = -G psi / 24
+  const double hx = cH * gx, hy = cH * gy;
+  const double inv_rho = fast_rcp(rho);
+  const double ux = (jx + hx) * inv_rho, uy = (jy + hy) * inv_rho;
+  *ux_o = ux;
+  *uy_o = uy;
+  const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
+  const double Pxx = ux * (Px + hx), Pyy = uy * (Py + hy);
+  const double tr = Pxx + Pyy;
+  const double Pxy_eq = fma(ux, Py, uy * hx);
+  const double zz = a.zz_scale * fma(gx, gx, gy * gy);
+  const double B0 = fma(-1.5, tr, rho);
+  const double Q = fma(B0, 1.0 / 9.0, zz);
+  double axp, ayp, Pxy;
+  if (KIND == kUnitTau) {
+    axp = fma(0.5, Pxx, Q);
+    ayp = fma(0.5, Pyy, Q);
+    Pxy = Pxy_eq;
+  } else {
+    // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S, with m_eq + S/2 = Pi above
+    const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
+    const double m7 = a.mom[3 * a.n + node], m8 = a.mom[4 * a.n + node];
+    const double Jx = jx + hx, Jy = jy + hy;
+    const double meq7 = fma(ux, Jx, -uy * Jy), meq8 = ux * Jy;
+    const double s7 = 4.0 * fma(ux, hx, -uy * hy), s8 = 2.0 * fma(ux, hy, uy * hx);
+    const double hw = fma(-0.5, om, 1.0);
+    const double m7s = fma(hw, s7, fma(-om, m7 - meq7, m7));
+    Pxy = fma(hw, s8, fma(-om, m8 - meq8, m8));
+    const double T4 = fma(0.25, tr, Q);
+    axp = fma(0.25, m7s, T4);  // Q + Pi_xx/2 with Pi_xx = (tr + m7*)/2
+    ayp = fma(-0.25, m7s, T4);
+  }
+  out.f[0] = fma(4.0 / 9.0, B0, -8.0 * zz);
+  out.f[1] = fma(Px, 1.0 / 3.0, axp);
+  out.f[3] = fma(-Px, 1.0 / 3.0, axp);
+  out.f[2] = fma(Py, 1.0 / 3.0, ayp);
+  out.f[4] = fma(-Py, 1.0 / 3.0, ayp);
+  const double Dq = fma(fma(3.0, tr, rho), 1.0 / 36.0, zz);
+  const double dp = fma(0.25, Pxy, Dq), dm = fma(-0.25, Pxy, Dq);
+  const double ps = Px + Py, pd = Py - Px;
+  out.f[5] = fma(ps, 1.0 / 12.0, dp);
+  out.f[7] = fma(-ps, 1.0 / 12.0, dp);
+  out.f[6] = fma(pd, 1.0 / 12.0, dm);
+  out.f[8] = fma(-pd, 1.0 / 12.0, dm);
+}
+
+// General MRT collision in moment space (six relaxation times).
+__device__ __forceinline__ void collide_full(const StepArgs& a, int64_t node, double psi0, double gx, double gy,
+                                             Post& out, double* rho_o, double* ux_o, double* uy_o) {
+  const int64_t N = a.n;
+  double m[9];
+  m[0] = a.mom[node];
+  m[3] = a.mom[N + node];
+  m[5] = a.mom[2 * N + node];
+  m[1] = a.mom[3 * N + node];
+  m[2] = a.mom[4 * N + node];
+  m[4] = a.mom[5 * N + node];
+  m[6] = a.mom[6 * N + node];
+  m[7] = a.mom[7 * N + node];
+  m[8] = a.mom[8 * N + node];
+  const double rho = m[0];
+  const double cF = 2.0 * a.half_force * psi0;
+  const double Fx = cF * gx, Fy = cF * gy;
+  const double Jx = fma(0.5, Fx, m[3]), Jy = fma(0.5, Fy, m[5]);
+  const double inv_rho = fast_rcp(rho);
+  const double ux = Jx * inv_rho, uy = Jy * inv_rho;
+  *rho_o = rho;
+  *ux_o = ux;
+  *uy_o = uy;
+  const double ru2 = fma(ux, Jx, uy * Jy);
+  const double uF = fma(ux, Fx, uy * Fy);
+  const double F2p = a.G * a.G * (1.0 / 144.0) * fma(gx, gx, gy * gy);  // |F|^2 / psi^2
+  double meq[9], S[9];
+  meq[0] = rho;                   S[0] = 0.0;
+  meq[1] = fma(3.0, ru2, -2.0 * rho); S[1] = fma(6.0, uF, a.li_e * F2p);
+  meq[2] = fma(-3.0, ru2, rho);   S[2] = -fma(6.0, uF, a.li_z * F2p);
+  meq[3] = Jx;                    S[3] = Fx;
+  meq[4] = -Jx;                   S[4] = -Fx;
+  meq[5] = Jy;                    S[5] = Fy;
+  meq[6] = -Jy;                   S[6] = -Fy;
+  meq[7] = fma(ux, Jx, -uy * Jy); S[7] = 2.0 * fma(ux, Fx, -uy * Fy);
+  meq[8] = ux * Jy;               S[8] = fma(ux, Fy, uy * Fx);
+  double n[9];
+  const double inv_norm[9] = {1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 6.0, 1.0 / 12.0,
+                              1.0 / 6.0, 1.0 / 12.0, 1.0 / 4.0,  1.0 / 4.0};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double om = a.omega[k];
+    const double ms = fma(fma(-0.5, om, 1.0), S[k], fma(-om, m[k] - meq[k], m[k]));
+    n[k] = ms * inv_norm[k];
+  }
+  // f* = M^T n (M^-1 = M^T diag(1/|row|^2))
+  out.f[0] = n[0] - 4.0 * n[1] + 4.0 * n[2];
+  const double A = n[0] - n[1] - 2.0 * n[2];
+  const double X = n[3] - 2.0 * n[4], Y = n[5] - 2.0 * n[6];
+  out.f[1] = A + X + n[7];
+  out.f[3] = A - X + n[7];
+  out.f[2] = A + Y - n[7];
+  out.f[4] = A - Y - n[7];
+  const double B = n[0] + 2.0 * n[1] + n[2];
+  const double Px = n[3] + n[4], Py = n[5] + n[6];
+  const double bp = B + n[8], bm = B - n[8];
+  out.f[5] = bp + (Px + Py);
+  out.f[7] = bp - (Px + Py);
+  out.f[6] = bm + (Py - Px);
+  out.f[8] = bm - (Py - Px);
+}
+
+// K2 body for node (x, y), whose psi sits at sp[c] of a tile with row stride sw:
+// force, collision, then push streaming (or the macroscopic fields when FIELDS).
+template <int KIND, bool FIELDS>
+__device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, const double* sp, int c, int sw,
+                                             double* rho_o, double* ux_o, double* uy_o, double* psi_o) {
+  const double p0 = sp[c];
+  const double pE = sp[c + 1], pW = sp[c - 1], pN = sp[c + sw], pS = sp[c - sw];
+  const double pNE = sp[c + sw + 1], pNW = sp[c + sw - 1], pSW = sp[c - sw - 1], pSE = sp[c - sw + 1];
+  // 12 * sum_i w(|c_i|^2) psi(x + c_i) c_i  (w = 1/3 axis, 1/12 diagonal)
+  const double d1 = pNE - pSW, d2 = pSE - pNW;
+  const double gx = fma(4.0, pE - pW, d1 + d2);
+  const double gy = fma(4.0, pN - pS, d1 - d2);
+  const int64_t N = a.n;
+  const int64_t node = (int64_t)y * a.nx + x;
+  Post o;
+  double rho, ux, uy;
+  if (KIND == kFullMrt) {
+    collide_full(a, node, p0, gx, gy, o, &rho, &ux, &uy);
+  } else {
+    rho = a.mom[node];
+    collide_reduced<KIND>(a, node, rho, a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, o, &ux, &uy);
+  }
+  if (FIELDS) {
+    if (rho_o) rho_o[node] = rho;
+    if (ux_o) ux_o[node] = ux;
+    if (uy_o) uy_o[node] = uy;
+    if (psi_o) psi_o[node] = p0;
+    return;
+  }
+  // push streaming: f_i(x + c_i, t + 1) = f*_i(x, t); bounce-back into the opposite
+  // population of the same node when x + c_i lies in a wall
+  double* __restrict__ out = a.f_out;
+  const int nx = a.nx, ny = a.ny;
+  const int xe = (x + 1 == nx) ? 0 : x + 1;
+  const int xw = (x == 0) ? nx - 1 : x - 1;
+  const int64_t row = (int64_t)y * nx;
+  out[node] = o.f[0];
+  out[N + row + xe] = o.f[1];
+  out[3 * N + row + xw] = o.f[3];
+  bool up_wall = false, down_wall = false;
+  int yn = y + 1, ys = y - 1;
+  if (a.walls) {
+    up_wall = (yn == ny);
+    down_wall = (ys < 0);
+  } else {
+    if (yn == ny) yn = 0;
+    if (ys < 0) ys = ny - 1;
+  }
+  const int64_t rn = (int64_t)yn * nx, rs = (int64_t)ys * nx;
+  if (up_wall) {
+    out[4 * N + node] = o.f[2];
+    out[7 * N + node] = o.f[5];
+    out[8 * N + node] = o.f[6];
+  } else {
+    out[2 * N + rn + x] = o.f[2];
+    out[5 * N + rn + xe] = o.f[5];
+    out[6 * N + rn + xw] = o.f[6];
+  }
+  if (down_wall) {
+    out[2 * N + node] = o.f[4];
+    out[5 * N + node] = o.f[7];
+    out[6 * N + node] = o.f[8];
+  } else {
+    out[4 * N + rs + x] = o.f[4];
+    out[7 * N + rs + xw] = o.f[7];
+    out[8 * N + rs + xe] = o.f[8];
+  }
+}
+
+}  // namespace pplbm

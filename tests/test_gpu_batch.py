@@ -1,0 +1,162 @@
+"""Batched engine: many uneven lattices advanced by one launch per pass (or one
+persistent cooperative launch). The per-node arithmetic is the single-lattice
+step's, so every plan must give distributions bitwise equal to stepping each
+lattice alone through pplbm_create/pplbm_step; that path in turn matches the
+oracle (test_gpu_parity.py), and one batch instance is checked against the
+oracle directly here."""
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from gpu_helpers import BC_PER, BC_WALLS, make_pair, normwise
+from oracle import eos as E
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2107_06355_gb300")
+
+
+def _instances():
+    # (nx, ny, bc, Tr, init kind)
+    return [(4, 90, BC_PER, 0.8, "planar"), (70, 45, BC_PER, 0.6, "droplet"), (4, 37, BC_PER, 0.5, "planar"),
+            (33, 33, BC_PER, 0.35, "droplet"), (48, 40, BC_WALLS, 0.6, "impact"), (3, 5, BC_PER, 0.6, "droplet"),
+            (1, 1, BC_PER, 0.7, "uniform"), (130, 9, BC_WALLS, 0.5, "impact")]
+
+
+def _init_fields(kind, nx, ny, d, seed):
+    if kind == "planar":
+        return I.planar(nx, ny, d["rho_v"], d["rho_l"], W=6.0), None, None
+    if kind == "droplet":
+        rho = I.perturbed(I.droplet(nx, ny, max(1.0, min(nx, ny) / 4), d["rho_v"], d["rho_l"], W=5.0), 0.01, seed)
+        ux, uy = I.random_velocity((ny, nx), 0.01, seed + 1)
+        return rho, ux, uy
+    if kind == "impact":
+        return I.impact(nx, ny, max(2.0, min(nx, ny) / 6), max(2, ny // 6), d["rho_v"], d["rho_l"], 0.03, W=5.0)
+    return np.full((ny, nx), d["rho_l"]), None, None
+
+
+def _build(relax_kw):
+    inst = _instances()
+    eos = [P.EOSParams(P.EOS_SMOOTH, Tr, 0.363, 2.0, 0.775) for (_, _, _, Tr, _) in inst]
+    relax = [P.Relax(**relax_kw) for _ in inst]
+    b = P.Batch([(nx, ny, bc) for (nx, ny, bc, _, _) in inst], eos, relax)
+    sims = []
+    for k, (nx, ny, bc, Tr, kind) in enumerate(inst):
+        s = P.Simulation(nx, ny, bc, eos[k], relax[k])
+        rho, ux, uy = _init_fields(kind, nx, ny, s.derived(), 100 + k)
+        s.init_equilibrium(rho, ux, uy)
+        b.init_equilibrium(k, rho, ux, uy)
+        sims.append(s)
+    return b, sims
+
+
+@pytest.mark.parametrize("relax_kw", [{}, {"kind": 1, "tau_l": 0.6, "visc_ratio": 2.0}], ids=["unit", "two_phase"])
+@pytest.mark.parametrize("mode,width", [(0, 0), (0, 4), (0, 32), (0, 256), (1, 0), (2, 0), (2, 8)])
+def test_batch_bitwise_equals_single_lattice(relax_kw, mode, width):
+    b, sims = _build(relax_kw)
+    b.set_plan(mode, width)
+    for nsteps in (1, 6, 7):
+        b.step(nsteps)
+        for s in sims:
+            s.step(nsteps)
+        assert b.sync() > 0
+        for k, s in enumerate(sims):
+            assert torch.equal(b.get_f(k), s.get_f()), (k, nsteps)
+    for k, s in enumerate(sims):
+        rb = b.fields(k)
+        rs = s.fields()
+        for x, y in zip(rb, rs):
+            assert torch.equal(x, y)
+    b.close()
+
+
+def test_batch_instance_matches_oracle():
+    inst = [(4, 64, BC_PER, 0.5), (40, 24, BC_WALLS, 0.6)]
+    eos = [P.EOSParams(P.EOS_SMOOTH, Tr, 0.363, 2.0, 0.775) for (_, _, _, Tr) in inst]
+    relax = [P.Relax(kind=1, tau_l=0.6, visc_ratio=2.0) for _ in inst]
+    b = P.Batch([(nx, ny, bc) for (nx, ny, bc, _) in inst], eos, relax)
+    b.set_plan(P.PLAN_PERSISTENT, 0)
+    olat, _ = make_pair(40, 24, BC_WALLS, (E.MODE_SMOOTH, 0.6, 0.363, 2.0, 0.775),
+                        {"kind": 1, "tau_l": 0.6, "visc_ratio": 2.0})
+    e = olat.eos
+    rho, ux, uy = I.impact(40, 24, 4, 4, e.rho_v, e.rho_l, 0.03, W=5.0)
+    d0 = b.derived(0)
+    b.init_equilibrium(0, I.planar(4, 64, d0["rho_v"], d0["rho_l"], W=6.0))
+    b.init_equilibrium(1, rho, ux, uy)
+    f = olat.init_equilibrium(rho, ux, uy)
+    f = olat.step(f, 12)
+    b.step(12)
+    assert normwise(b.get_f(1).cpu().numpy(), f) < 1e-11
+
+
+def test_autotune_keeps_state_and_reports_plan():
+    b, sims = _build({})
+    b.step(3)
+    before = [b.get_f(k).clone() for k in range(len(sims))]
+    plan = b.autotune(trial_steps=6)
+    assert plan["mode"] in (0, 1, 2)
+    assert plan["ms_launches"] > 0 and plan["ms_graph"] > 0 and plan["ms_persistent"] > 0
+    for k in range(len(sims)):
+        assert torch.equal(b.get_f(k), before[k])
+    # stepping after tuning still matches the single-lattice path
+    b.step(5)
+    for s in sims:
+        s.step(8)
+    for k, s in enumerate(sims):
+        assert torch.equal(b.get_f(k), s.get_f())
+
+
+def test_persistent_barrier_wait_runs_out_and_is_reported():
+    """Failure detection without a GPU fault: one block leaves without arriving,
+    the others' bounded waits run out, the status is PPLBM_ERR_TIMEOUT, and the
+    batch (whose distributions the test run did not touch) keeps working."""
+    b, sims = _build({})
+    b.set_plan(P.PLAN_PERSISTENT, 0)
+    b.step(2)
+    for s in sims:
+        s.step(2)
+    assert b.barrier_selftest(spin_limit=1 << 12) == 5
+    b.step(3)
+    for s in sims:
+        s.step(3)
+    assert b.sync() == 5
+    for k, s in enumerate(sims):
+        assert torch.equal(b.get_f(k), s.get_f())
+
+
+def test_sweep_64_instances_full_size_sampled():
+    """The 64-lattice sweep (seed 210706355, planar L x 4 and droplets L x L, L in
+    64..1024, T_r 0.35..0.95; ~12.9 M nodes) in the autotuned plan: sampled small
+    instances against the oracle, large ones bitwise against single-lattice steps."""
+    specs = I.batch_specs()
+    eos = [P.EOSParams(P.EOS_SMOOTH, s["Tr"], 0.363, 2.0, 0.775) for s in specs]
+    relax = [P.Relax() for _ in specs]
+    b = P.Batch([(s["nx"], s["ny"], BC_PER) for s in specs], eos, relax)
+    inits = []
+    for k, s in enumerate(specs):
+        d = b.derived(k)
+        if s["kind"] == "planar":
+            rho = I.planar(s["nx"], s["ny"], d["rho_v"], d["rho_l"], W=8.0)
+        else:
+            rho = I.droplet(s["nx"], s["ny"], s["R"], d["rho_v"], d["rho_l"], W=8.0)
+        b.init_equilibrium(k, rho)
+        inits.append(rho)
+    plan = b.autotune(trial_steps=4)
+    b.step(5)
+    b.sync()
+    # small planar instances against the oracle
+    for k in (0, 6, 62):
+        s = specs[k]
+        olat, _ = make_pair(s["nx"], s["ny"], BC_PER, (E.MODE_SMOOTH, s["Tr"], 0.363, 2.0, 0.775), {})
+        f = olat.step(olat.init_equilibrium(inits[k]), 5)
+        assert normwise(b.get_f(k).cpu().numpy(), f) < 1e-12, (k, plan)
+    # large droplets bitwise against the single-lattice path
+    for k in (1, 33, 63):
+        s = specs[k]
+        sim = P.Simulation(s["nx"], s["ny"], BC_PER, eos[k], relax[k])
+        sim.init_equilibrium(inits[k])
+        sim.step(5)
+        assert torch.equal(b.get_f(k), sim.get_f()), (k, plan)
+        sim.close()
+    b.close()
