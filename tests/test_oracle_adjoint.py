@@ -1,0 +1,95 @@
+"""Pins for the oracle's reference adjoint (CPU only): the torch restatement of
+the step equals the numpy oracle step, and its reverse-mode gradients agree with
+central finite differences of the numpy oracle (w.r.t. the initial field and the
+shaping parameter alpha)."""
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from oracle import adjoint as A
+from oracle import eos as E
+from oracle import lbm as L
+
+torch = pytest.importorskip("torch")
+
+CASE = (E.MODE_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+PER = L.BC_PERIODIC_X | L.BC_PERIODIC_Y
+WALLS = L.BC_PERIODIC_X | L.BC_WALL_BOTTOM | L.BC_WALL_TOP
+
+
+def lattice(nx, ny, bc, alpha=CASE[4]):
+    e = E.make_eos(CASE[0], CASE[1], CASE[2], CASE[3], alpha)
+    e.solve_eps(n=40000)
+    return L.Lattice(nx, ny, bc, e, L.Relax(sigma=e.sigma()))
+
+
+def initial(lat, nx, ny, bc):
+    e = lat.eos
+    if bc == WALLS:
+        rho, ux, uy = I.impact(nx, ny, 3, 4, e.rho_v, e.rho_l, 0.01, W=6.0)
+    else:
+        rho = I.perturbed(I.droplet(nx, ny, min(nx, ny) / 4, e.rho_v, e.rho_l, W=4.0), 0.01, 1)
+        ux, uy = I.random_velocity((ny, nx), 0.005, 2)
+    return lat.init_equilibrium(rho, ux, uy)
+
+
+@pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
+def test_torch_step_equals_numpy_oracle(bc):
+    lat = lattice(12, 10, bc)
+    f = initial(lat, 12, 10, bc)
+    c = A.constants_as_tensors(lat.eos, requires_grad=False)
+    g = torch.tensor(f)
+    for _ in range(4):
+        f = lat.step(f, 1)
+        g = A.step(g, lat, c)
+    assert np.max(np.abs(g.numpy() - f)) < 1e-14 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
+def test_gradient_wrt_initial_field_matches_finite_differences(bc):
+    nx, ny, steps = 10, 12, 5
+    lat = lattice(nx, ny, bc)
+    e = lat.eos
+    f0 = initial(lat, nx, ny, bc)
+    c = A.constants_as_tensors(e, requires_grad=False)
+    x = torch.tensor(f0, requires_grad=True)
+    g = x
+    for _ in range(steps):
+        g = A.step(g, lat, c)
+    loss = A.droplet_loss(g.sum(0), e.rho_v, e.rho_l, 2.5)
+    loss.backward()
+    v = np.random.default_rng(3).standard_normal(f0.shape) * f0
+    h = 1e-6
+
+    def Lnp(f):
+        rho = lat.step(f, steps).sum(0)
+        return float(A.droplet_loss(torch.tensor(rho), e.rho_v, e.rho_l, 2.5))
+
+    fd = (Lnp(f0 + h * v) - Lnp(f0 - h * v)) / (2 * h)
+    ad = float((x.grad.numpy() * v).sum())
+    assert ad == pytest.approx(fd, rel=1e-6)
+
+
+def test_gradient_wrt_alpha_matches_finite_differences():
+    nx, ny, steps = 12, 12, 6
+    alpha = CASE[4]
+    lat = lattice(nx, ny, PER, alpha)
+    e = lat.eos
+    rho0 = I.droplet(nx, ny, 3.0, e.rho_v, e.rho_l, W=4.0)
+    c = A.constants_as_tensors(e)
+    g = torch.tensor(lat.init_equilibrium(rho0))
+    for _ in range(steps):
+        g = A.step(g, lat, c)
+    loss = A.droplet_loss(g.sum(0), e.rho_v, e.rho_l, 3.0)
+    loss.backward()
+    dc = A.constants_derivative(*CASE[:4], alpha)
+    ad = sum(float(c[k].grad) * dc[k] for k in A.CONST_NAMES)
+
+    def Lalpha(al):
+        lt = lattice(nx, ny, PER, al)
+        rho = lt.step(lt.init_equilibrium(rho0), steps).sum(0)
+        return float(A.droplet_loss(torch.tensor(rho), e.rho_v, e.rho_l, 3.0))
+
+    h = 1e-4
+    fd = (Lalpha(alpha + h) - Lalpha(alpha - h)) / (2 * h)
+    assert ad == pytest.approx(fd, rel=1e-5)
