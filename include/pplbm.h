@@ -190,6 +190,45 @@ pplbm_status pplbm_get_derived(const pplbm_ctx* ctx, pplbm_eos_derived* out);
 pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0,
                             int64_t nsteps, double* rho_out);
 
+/* ---- Adjoint (reverse-mode gradients), unit relaxation times (Sec. III.A) -----
+ * A hand-written adjoint of pplbm_step for contexts whose relaxation times are
+ * all 1 (other sets return PPLBM_ERR_STATE). Gradients flow to the state and to
+ * the EOS constants that depend on the shaping parameter alpha (Sec. III.D):
+ * grad[PPLBM_NGRAD] = dL/d{p_max, b1, 1/a1^2, a2, b2, p_min, b3, 1/a3^2, z},
+ * with a2, b2 the cubic's coefficients and z = sigma G^2/432 the Li term's scale
+ * (Eq. LiFS). pplbm_eos_constant_sensitivity gives their alpha-derivatives, so
+ * dL/dalpha = sum_k grad[k] dc[k]. All pointers are device memory unless noted. */
+#define PPLBM_NGRAD 9
+
+/* Bytes of the adjoint workspace (adjoint planes, lambda ping-pong, per-block partials). */
+size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice);
+/* One adjoint step at the state f_t (9 planes): lambda_t = (d f^{t+1}/d f^t)^T lambda_next,
+ * grad += (d f^{t+1}/d constants)^T lambda_next. Uses the context's psi/moment planes.
+ * Asynchronous; the reduction into grad is deterministic. */
+pplbm_status pplbm_adjoint_step(pplbm_ctx* ctx, const double* f_t, const double* lambda_next, double* lambda_t,
+                                double* grad, void* adj_workspace, size_t adj_workspace_bytes);
+/* Advances nsteps from the current state, copying f into checkpoints[k] (9*nx*ny
+ * values each) before steps k*interval; ceil(nsteps/interval) slots. */
+pplbm_status pplbm_forward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t interval, double* checkpoints);
+/* Reverse pass of a checkpointed rollout: for each segment, last first, recomputes
+ * its states from the checkpoint into `segment` (interval slots of 9*nx*ny) and runs
+ * the adjoint steps back through it. lambda_N = dL/df^nsteps (device or host),
+ * lambda_0 = dL/df^0 (device or host); grad accumulates. sqrt(N) checkpointing:
+ * interval ~ sqrt(nsteps) keeps 2 sqrt(nsteps) states and costs one extra forward pass. */
+pplbm_status pplbm_backward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t interval, const double* checkpoints,
+                                         double* segment, const double* lambda_N, double* lambda_0, double* grad,
+                                         void* adj_workspace, size_t adj_workspace_bytes);
+/* rho0_bar = sum_i w_i lambda_0[i]: the gradient w.r.t. the initial density of
+ * f^0 = f^eq(rho0, u = 0) (Sec. III.A). */
+pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* ctx, const double* lambda_0, double* rho0_bar);
+/* Host only: the values of the PPLBM_NGRAD constants (z left 0). */
+pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* eos, double c[PPLBM_NGRAD]);
+/* Host only: dc/dalpha (which = 0) of the PPLBM_NGRAD constants, including z through
+ * sigma(alpha) when relax->sigma_auto, by central differences of pplbm_eos_setup at
+ * steps h and h/2 combined by Richardson extrapolation (error O(h^4)). */
+pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* params, double G, const pplbm_relax* relax,
+                                            int32_t which, double h, double dc[PPLBM_NGRAD]);
+
 /* ---- Batched engine: many independent lattices advanced together ----------
  * The instances may differ in size, boundary flags, EOS parameters (e.g. a sweep
  * of reduced temperatures) and relaxation times, but must share one collision

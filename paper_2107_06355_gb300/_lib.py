@@ -75,6 +75,9 @@ class pplbm_batch_plan(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+NGRAD = 9
+GRAD_NAMES = ("p_max", "b1", "inv_a1sq", "a2", "b2", "p_min", "b3", "inv_a3sq", "zz_scale")
+
 PLAN_LAUNCHES = 0
 PLAN_GRAPH = 1
 PLAN_PERSISTENT = 2
@@ -119,6 +122,14 @@ _SIGS = {
     "pplbm_batch_barrier_selftest": (C.c_int, [_P, C.c_uint32]),
     "pplbm_batch_last_error": (C.c_char_p, [_P]),
     "pplbm_batch_destroy": (None, [_P]),
+    "pplbm_adjoint_workspace_bytes": (C.c_size_t, [C.POINTER(pplbm_lattice)]),
+    "pplbm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_size_t]),
+    "pplbm_forward_checkpointed": (C.c_int, [_P, C.c_int64, C.c_int64, _P]),
+    "pplbm_backward_checkpointed": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_size_t]),
+    "pplbm_adjoint_initial_density": (C.c_int, [_P, _P, _P]),
+    "pplbm_eos_grad_constants": (C.c_int, [C.POINTER(pplbm_eos_derived), _D]),
+    "pplbm_eos_constant_sensitivity": (C.c_int, [C.POINTER(pplbm_eos_params), C.c_double, C.POINTER(pplbm_relax),
+                                                 C.c_int32, C.c_double, _D]),
     "pplbm_last_error": (C.c_char_p, [_P]),
     "pplbm_status_string": (C.c_char_p, [C.c_int]),
     "pplbm_destroy": (None, [_P]),

@@ -1,0 +1,495 @@
+// Hand-written adjoint of the step (unit relaxation times), sqrt(N) checkpointed
+// rollouts, and the EOS-constant sensitivities that chain the gradient to the
+// shaping parameter alpha (Sec. III.D).
+//
+// Forward step at time t (step_device.cuh): rho, j, psi per node; g = 12 sum_i
+// w_i psi(x + c_i) c_i; f*(x) = Phi(rho, j, psi(x), g; constants); push
+// f^{t+1}_i(x + c_i) = f*_i(x) (bounce-back at walls). Given lambda^{t+1} =
+// dL/df^{t+1}, one adjoint step is:
+//   A1 (per node): mu_i(x) = lambda^{t+1}_i(x + c_i), or lambda^{t+1}_opp(i)(x)
+//      beyond a wall (the transpose of the push, a gather); reverse mode through
+//      Phi gives rho_bar, j_bar, psi_bar (own node), g_bar and the Li-term scale's
+//      adjoint;
+//   A2 (per node): psi_bar(y) += sum_c W_c (c_x gx_bar(y - c) + c_y gy_bar(y - c)),
+//      the transpose of the psi stencil written as a gather (W = 4 axis, 1
+//      diagonal; neighbours beyond a wall are ghosts with no adjoint); then
+//      through psi = sqrt(psi^2(rho; constants)) to rho_bar and the constants'
+//      adjoints; lambda^t_i = rho_bar + c_i . j_bar.
+// Constant adjoints are reduced per block and summed in a fixed order
+// (deterministic). The host maps them to d/d alpha with dconstants/dalpha.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/pplbm.h"
+#include "ctx.h"
+#include "step_device.cuh"
+
+namespace pplbm {
+namespace {
+
+constexpr int kTX = 32, kTY = 8, kNT = kTX * kTY;
+// gradient slots (the alpha-dependent constants of EosConst, then the Li-term scale)
+enum { G_PMAX = 0, G_B1, G_IA1, G_A2, G_B2, G_PMIN, G_B3, G_IA3, G_ZZ, kNGrad };
+static_assert(kNGrad == PPLBM_NGRAD, "gradient slot count");
+
+struct AdjArgs {
+  StepArgs a;            // forward arguments of step t (psi, mom filled by K1 on f^t)
+  const double* lam1;    // lambda^{t+1}, 9 planes
+  double* lam0;          // lambda^t, 9 planes
+  double* bar;           // 6 planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar
+  double* partial1;      // per A1 block: zz-scale adjoint
+  double* partial2;      // per A2 block: kNGrad - 1 constant adjoints
+};
+
+// reverse mode of collide_reduced<kUnitTau> (see its comments for the forward)
+__device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double rho, double jx, double jy, double psi0,
+                                                     double gx, double gy, const double* mu, double* rho_b,
+                                                     double* jx_b, double* jy_b, double* psi_b, double* gx_b,
+                                                     double* gy_b, double* zs_b) {
+  // forward recompute
+  const double cH = a.half_force * psi0;
+  const double hx = cH * gx, hy = cH * gy;
+  const double inv = fast_rcp(rho);
+  const double Jx = jx + hx, Jy = jy + hy;
+  const double ux = Jx * inv, uy = Jy * inv;
+  const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
+  const double g2 = fma(gx, gx, gy * gy);
+  // reverse
+  const double dp_b = mu[5] + mu[7], ps_b = (mu[5] - mu[7]) * (1.0 / 12.0);
+  const double dm_b = mu[6] + mu[8], pd_b = (mu[6] - mu[8]) * (1.0 / 12.0);
+  const double Dq_b = dp_b + dm_b;
+  const double Pxy_b = 0.25 * (dp_b - dm_b);
+  const double D_b = Dq_b * (1.0 / 36.0);
+  double zz_b = Dq_b;
+  double r_b = D_b;
+  double tr_b = 3.0 * D_b;
+  const double axp_b = mu[1] + mu[3], ayp_b = mu[2] + mu[4];
+  double Px_b = (mu[1] - mu[3]) * (1.0 / 3.0) + (ps_b - pd_b);
+  double Py_b = (mu[2] - mu[4]) * (1.0 / 3.0) + (ps_b + pd_b);
+  const double Q_b = axp_b + ayp_b;
+  double Pxx_b = 0.5 * axp_b, Pyy_b = 0.5 * ayp_b;
+  const double B0_b = (4.0 / 9.0) * mu[0] + Q_b * (1.0 / 9.0);
+  zz_b += Q_b - 8.0 * mu[0];
+  r_b += B0_b;
+  tr_b += -1.5 * B0_b;
+  Pxx_b += tr_b;
+  Pyy_b += tr_b;
+  // Pxy = ux Py + uy hx
+  double ux_b = Pxy_b * Py, uy_b = Pxy_b * hx, hx_b = Pxy_b * uy;
+  Py_b += Pxy_b * ux;
+  // Pxx = ux (Px + hx), Pyy = uy (Py + hy)
+  ux_b += Pxx_b * (Px + hx);
+  Px_b += Pxx_b * ux;
+  hx_b += Pxx_b * ux;
+  uy_b += Pyy_b * (Py + hy);
+  Py_b += Pyy_b * uy;
+  double hy_b = Pyy_b * uy;
+  // Px = jx + 2 hx, Py = jy + 2 hy
+  double jx_bb = Px_b, jy_bb = Py_b;
+  hx_b += 2.0 * Px_b;
+  hy_b += 2.0 * Py_b;
+  // ux = Jx inv, uy = Jy inv
+  const double Jx_b = ux_b * inv, Jy_b = uy_b * inv;
+  const double inv_b = ux_b * Jx + uy_b * Jy;
+  jx_bb += Jx_b;
+  hx_b += Jx_b;
+  jy_bb += Jy_b;
+  hy_b += Jy_b;
+  r_b += -inv_b * inv * inv;
+  // zz = zs g2
+  const double zs = a.zz_scale;
+  double gx_bb = 2.0 * zs * gx * zz_b, gy_bb = 2.0 * zs * gy * zz_b;
+  *zs_b = zz_b * g2;
+  // hx = cH gx, hy = cH gy, cH = hf psi0
+  const double cH_b = hx_b * gx + hy_b * gy;
+  gx_bb += hx_b * cH;
+  gy_bb += hy_b * cH;
+  *psi_b = cH_b * a.half_force;
+  *rho_b = r_b;
+  *jx_b = jx_bb;
+  *jy_b = jy_bb;
+  *gx_b = gx_bb;
+  *gy_b = gy_bb;
+}
+
+// psi^2(rho) and its derivatives w.r.t. rho and the alpha-dependent constants (eos_dev.cuh)
+__device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, double* dc) {
+  for (int k = 0; k < kNGrad - 1; ++k) dc[k] = 0.0;
+  const long long rb = dbits(rho);
+  const bool vap = rb <= e.bits_rho_v, liq = rb >= e.bits_rho_l;
+  if (e.mode == 0 || vap || liq) {
+    const bool use_v = (e.mode != 0) && vap;
+    const double k1 = use_v ? e.k1_v : e.k1_l, k2 = use_v ? e.k2_v : e.k2_l;
+    const double eta = e.b4 * rho, om = 1.0 - eta;
+    const double num = fma(eta, fma(eta, om, 1.0), 1.0);
+    const double r = fast_rcp(om);
+    const double r3 = r * r * r;
+    const double Z = num * r3;
+    const double dZ = e.b4 * (4.0 + eta * (4.0 - 2.0 * eta)) * r3 * r;
+    return fma(k1, Z, fma(k2, rho, e.k3)) + rho * fma(k1, dZ, k2);
+  }
+  const double s = e.psi2_scale;
+  double dp;
+  if (rb <= e.bits_rho_max) {
+    const double d = rho - e.rho_max;
+    const double s1 = sqrt(fma(-d * d, e.inv_a1sq, 1.0));
+    dp = -e.b1 * d * e.inv_a1sq / s1;
+    dc[G_PMAX] = s;
+    dc[G_B1] = s * (s1 - 1.0);
+    dc[G_IA1] = s * (-e.b1 * d * d / (2.0 * s1));
+  } else if (rb < e.bits_rho_min) {
+    const double t = (rho - e.rho_max) * e.inv_span;
+    dp = (3.0 * e.a2 * t + 2.0 * e.b2) * t * e.inv_span;
+    dc[G_PMAX] = s;
+    dc[G_A2] = s * t * t * t;
+    dc[G_B2] = s * t * t;
+  } else {
+    const double d = rho - e.rho_min;
+    const double s3 = sqrt(fma(-d * d, e.inv_a3sq, 1.0));
+    dp = e.b3 * d * e.inv_a3sq / s3;
+    dc[G_PMIN] = s;
+    dc[G_B3] = s * (1.0 - s3);
+    dc[G_IA3] = s * (e.b3 * d * d / (2.0 * s3));
+  }
+  return s * (dp - 1.0 / 3.0);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  red[threadIdx.y * kTX + threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kNT / 2; w > 0; w >>= 1) {
+    const int t = threadIdx.y * kTX + threadIdx.x;
+    if (t < w) red[t] += red[t + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
+  __shared__ double sp[(kTY + 2) * (kTX + 2)];
+  __shared__ double red[kNT];
+  const StepArgs& a = g.a;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  load_psi_tile(a, sp, x0, y0, kTX, kTY, threadIdx.y * kTX + threadIdx.x, kNT);
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  double zs_b = 0.0;
+  if (x < a.nx && y < a.ny) {
+    const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
+    const double p0 = sp[c];
+    const double d1 = sp[c + sw + 1] - sp[c - sw - 1], d2 = sp[c - sw + 1] - sp[c + sw - 1];
+    const double gx = fma(4.0, sp[c + 1] - sp[c - 1], d1 + d2);
+    const double gy = fma(4.0, sp[c + sw] - sp[c - sw], d1 - d2);
+    const int64_t N = a.n, node = (int64_t)y * a.nx + x;
+    const int nx = a.nx, ny = a.ny;
+    const int xe = (x + 1 == nx) ? 0 : x + 1, xw = (x == 0) ? nx - 1 : x - 1;
+    int yn = y + 1, ys = y - 1;
+    bool up = false, down = false;
+    if (a.walls) {
+      up = (yn == ny);
+      down = (ys < 0);
+    } else {
+      if (yn == ny) yn = 0;
+      if (ys < 0) ys = ny - 1;
+    }
+    const int64_t row = (int64_t)y * nx, rn = (int64_t)yn * nx, rs = (int64_t)ys * nx;
+    const double* L1 = g.lam1;
+    // mu_i(x) = lambda^{t+1} at the node the push sent f*_i to
+    double mu[9];
+    mu[0] = L1[node];
+    mu[1] = L1[N + row + xe];
+    mu[3] = L1[3 * N + row + xw];
+    mu[2] = up ? L1[4 * N + node] : L1[2 * N + rn + x];
+    mu[5] = up ? L1[7 * N + node] : L1[5 * N + rn + xe];
+    mu[6] = up ? L1[8 * N + node] : L1[6 * N + rn + xw];
+    mu[4] = down ? L1[2 * N + node] : L1[4 * N + rs + x];
+    mu[7] = down ? L1[5 * N + node] : L1[7 * N + rs + xw];
+    mu[8] = down ? L1[6 * N + node] : L1[8 * N + rs + xe];
+    double rb, jxb, jyb, pb, gxb, gyb;
+    collide_unit_reverse(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, mu, &rb, &jxb, &jyb, &pb,
+                         &gxb, &gyb, &zs_b);
+    double* B = g.bar;
+    B[node] = rb;
+    B[N + node] = jxb;
+    B[2 * N + node] = jyb;
+    B[3 * N + node] = pb;
+    B[4 * N + node] = gxb;
+    B[5 * N + node] = gyb;
+  }
+  const double s = block_sum(zs_b, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) g.partial1[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// gx_bar, gy_bar tile with a one-node halo (zero beyond a wall: ghosts carry no adjoint)
+__device__ __forceinline__ void load_gbar_tile(const AdjArgs& g, double* sx, double* sy, int x0, int y0) {
+  const StepArgs& a = g.a;
+  const int sw = kTX + 2;
+  for (int k = threadIdx.y * kTX + threadIdx.x; k < (kTY + 2) * sw; k += kNT) {
+    const int ty = k / sw, tx = k - ty * sw;
+    const int gx = wrap_index(x0 + tx - 1, a.nx);
+    int gy = y0 + ty - 1;
+    double vx = 0.0, vy = 0.0;
+    if (a.walls) {
+      if (gy >= 0 && gy < a.ny) {
+        vx = g.bar[4 * a.n + (int64_t)gy * a.nx + gx];
+        vy = g.bar[5 * a.n + (int64_t)gy * a.nx + gx];
+      }
+    } else {
+      gy = wrap_index(gy, a.ny);
+      vx = g.bar[4 * a.n + (int64_t)gy * a.nx + gx];
+      vy = g.bar[5 * a.n + (int64_t)gy * a.nx + gx];
+    }
+    sx[k] = vx;
+    sy[k] = vy;
+  }
+}
+
+__global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
+  __shared__ double sx[(kTY + 2) * (kTX + 2)], sy[(kTY + 2) * (kTX + 2)];
+  __shared__ double red[kNT];
+  const StepArgs& a = g.a;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  load_gbar_tile(g, sx, sy, x0, y0);
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  double dcsum[kNGrad - 1];
+  for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = 0.0;
+  if (x < a.nx && y < a.ny) {
+    const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
+    // transpose of g = 12 sum_c w_c psi(x + c) c, gathered at this node y
+    const double pg = 4.0 * (sx[c - 1] - sx[c + 1]) + 4.0 * (sy[c - sw] - sy[c + sw]) +
+                      (sx[c - sw - 1] + sy[c - sw - 1]) - (sx[c + sw + 1] + sy[c + sw + 1]) +
+                      (sx[c + sw - 1] - sy[c + sw - 1]) - (sx[c - sw + 1] - sy[c - sw + 1]);
+    const int64_t N = a.n, node = (int64_t)y * a.nx + x;
+    const double psi_b = g.bar[3 * N + node] + pg;
+    const double rho = a.mom[node];
+    const double psi = a.psi[node];
+    double dc[kNGrad - 1];
+    const double dpsi2 = psi2_grad(a.eos, rho, dc);
+    const double psi2_b = psi_b * 0.5 / psi;
+    const double rho_b = g.bar[node] + psi2_b * dpsi2;
+    for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = psi2_b * dc[k];
+    const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
+    double* L0 = g.lam0;
+    L0[node] = rho_b;
+    L0[N + node] = rho_b + jxb;
+    L0[2 * N + node] = rho_b + jyb;
+    L0[3 * N + node] = rho_b - jxb;
+    L0[4 * N + node] = rho_b - jyb;
+    L0[5 * N + node] = rho_b + jxb + jyb;
+    L0[6 * N + node] = rho_b - jxb + jyb;
+    L0[7 * N + node] = rho_b - jxb - jyb;
+    L0[8 * N + node] = rho_b + jxb - jyb;
+  }
+  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  for (int k = 0; k < kNGrad - 1; ++k) {
+    const double s = block_sum(dcsum[k], red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) g.partial2[(int64_t)blk * (kNGrad - 1) + k] = s;
+  }
+}
+
+// grad[k] += sum over blocks, in a fixed order
+__global__ void k_adj_reduce(const double* partial1, const double* partial2, int nblocks, double* grad) {
+  __shared__ double red[kNGrad][256];
+  double acc[kNGrad];
+  for (int k = 0; k < kNGrad; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) {
+    for (int k = 0; k < kNGrad - 1; ++k) acc[k] += partial2[(int64_t)b * (kNGrad - 1) + k];
+    acc[G_ZZ] += partial1[b];
+  }
+  for (int k = 0; k < kNGrad; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < kNGrad; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < kNGrad) grad[threadIdx.x] += red[threadIdx.x][0];
+}
+
+// f_i = w_i rho0 is f^eq at rest; its transpose: rho0_bar = sum_i w_i lambda_i
+__global__ void k_adj_init(int64_t n, const double* lam, double* rho_bar) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  double s = 0.0;
+  for (int k = 0; k < 9; ++k) s += w[k] * lam[k * n + i];
+  rho_bar[i] = s;
+}
+
+int nblocks(const StepArgs& a) { return ((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY); }
+
+}  // namespace
+}  // namespace pplbm
+
+using namespace pplbm;
+
+namespace {
+
+size_t adj_bytes(const pplbm_lattice* l) {
+  const size_t n = (size_t)l->nx * l->ny;
+  const size_t nb = (size_t)((l->nx + kTX - 1) / kTX) * ((l->ny + kTY - 1) / kTY);
+  return sizeof(double) * (6 * n + 18 * n + nb * kNGrad + 64);
+}
+
+// one adjoint step at state f_t (device), lambda_next -> lambda_t, grad += ...
+pplbm_status adjoint_step(pplbm_ctx* c, const double* f_t, const double* lam1, double* lam0, double* grad,
+                          double* ws) {
+  StepArgs a = c->args;
+  a.f_in = f_t;
+  a.f_out = nullptr;
+  launch_rho_psi(a, c->stream);  // psi, moments of f^t
+  AdjArgs g;
+  g.a = a;
+  g.lam1 = lam1;
+  g.lam0 = lam0;
+  g.bar = ws;
+  const int nb = nblocks(a);
+  g.partial1 = ws + 24 * c->n;
+  g.partial2 = g.partial1 + nb;
+  const dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY), block(kTX, kTY);
+  k_adj_collide<<<grid, block, 0, c->stream>>>(g);
+  k_adj_rho_psi<<<grid, block, 0, c->stream>>>(g);
+  k_adj_reduce<<<1, 256, 0, c->stream>>>(g.partial1, g.partial2, nb, grad);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->msg = cudaGetErrorString(e);
+    return PPLBM_ERR_CUDA;
+  }
+  return PPLBM_OK;
+}
+
+pplbm_status forward_into(pplbm_ctx* c, const double* fin, double* fout) {
+  StepArgs a = c->args;
+  a.f_in = fin;
+  a.f_out = fout;
+  launch_rho_psi(a, c->stream);
+  launch_collide(a, c->stream);
+  return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice) {
+  if (!lattice || lattice->nx < 1 || lattice->ny < 1) return 0;
+  return adj_bytes(lattice);
+}
+
+pplbm_status pplbm_adjoint_step(pplbm_ctx* c, const double* f_t, const double* lambda_next, double* lambda_t,
+                                double* grad, void* adj_workspace, size_t adj_workspace_bytes) {
+  if (!c || !f_t || !lambda_next || !lambda_t || !grad || !adj_workspace) return PPLBM_ERR_ARG;
+  if (c->args.kind != kUnitTau) {
+    c->msg = "the adjoint covers unit relaxation times only";
+    return PPLBM_ERR_STATE;
+  }
+  if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
+  return adjoint_step(c, f_t, lambda_next, lambda_t, grad, (double*)adj_workspace);
+}
+
+pplbm_status pplbm_forward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t interval, double* checkpoints) {
+  if (!c || nsteps < 0 || interval < 1 || !checkpoints) return PPLBM_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  const int64_t stride = 9 * c->n;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (t % interval == 0) {
+      if (cudaMemcpyAsync(checkpoints + (t / interval) * stride, c->fA, sizeof(double) * stride,
+                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return PPLBM_ERR_CUDA;
+    }
+    if (pplbm_status s = pplbm_step(c, 1)) return s;
+  }
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t interval, const double* checkpoints,
+                                         double* segment, const double* lambda_N, double* lambda_0, double* grad,
+                                         void* adj_workspace, size_t adj_workspace_bytes) {
+  if (!c || nsteps < 0 || interval < 1 || !checkpoints || !segment || !lambda_N || !lambda_0 || !grad ||
+      !adj_workspace)
+    return PPLBM_ERR_ARG;
+  if (c->args.kind != kUnitTau) {
+    c->msg = "the adjoint covers unit relaxation times only";
+    return PPLBM_ERR_STATE;
+  }
+  if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  const int64_t stride = 9 * c->n;
+  double* ws = (double*)adj_workspace;
+  double* lamA = ws + 6 * c->n;       // lambda ping-pong inside the adjoint workspace
+  double* lamB = lamA + stride;
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(lamA, lambda_N, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
+    return PPLBM_ERR_CUDA;
+  double* cur = lamA;
+  double* nxt = lamB;
+  if (nsteps > 0) {
+    const int64_t nseg = (nsteps + interval - 1) / interval;
+    for (int64_t j = nseg - 1; j >= 0; --j) {
+      const int64_t t0 = j * interval, t1 = std::min(nsteps, t0 + interval);
+      // recompute f^{t0} .. f^{t1 - 1} from the checkpoint
+      if (cudaMemcpyAsync(segment, checkpoints + j * stride, sizeof(double) * stride, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+        return PPLBM_ERR_CUDA;
+      for (int64_t t = t0; t + 1 < t1; ++t)
+        if (pplbm_status st = forward_into(c, segment + (t - t0) * stride, segment + (t - t0 + 1) * stride)) return st;
+      for (int64_t t = t1 - 1; t >= t0; --t) {
+        if (pplbm_status st = adjoint_step(c, segment + (t - t0) * stride, cur, nxt, grad, ws)) return st;
+        std::swap(cur, nxt);
+      }
+    }
+  }
+  if (cudaMemcpyAsync(lambda_0, cur, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
+    return PPLBM_ERR_CUDA;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* c, const double* lambda_0, double* rho0_bar) {
+  if (!c || !lambda_0 || !rho0_bar) return PPLBM_ERR_ARG;
+  k_adj_init<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(c->n, lambda_0, rho0_bar);
+  return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
+}
+
+pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* d, double c[PPLBM_NGRAD]) {
+  if (!d || !c) return PPLBM_ERR_ARG;
+  const EosConst e = make_eos_const(*d);
+  const double vals[PPLBM_NGRAD] = {e.p_max, e.b1, e.inv_a1sq, e.a2, e.b2, e.p_min, e.b3, e.inv_a3sq, 0.0};
+  std::memcpy(c, vals, sizeof(vals));
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* p, double G, const pplbm_relax* relax,
+                                            int32_t which, double h, double dc[PPLBM_NGRAD]) {
+  if (!p || !relax || !dc || which != 0 || !(h > 0.0)) return PPLBM_ERR_ARG;
+  auto at = [&](double alpha, double* out) -> pplbm_status {
+    pplbm_eos_params q = *p;
+    q.alpha = alpha;
+    pplbm_eos_derived d;
+    if (pplbm_status s = pplbm_eos_setup(&q, G, &d)) return s;
+    pplbm_eos_grad_constants(&d, out);
+    const double sigma = relax->forcing == PPLBM_FORCING_GUO ? 0.0
+                         : relax->sigma_auto               ? -d.eps / (16.0 * G)
+                                                           : relax->sigma;
+    out[G_ZZ] = sigma * G * G / 432.0;
+    return PPLBM_OK;
+  };
+  double a1[PPLBM_NGRAD], a2[PPLBM_NGRAD], b1[PPLBM_NGRAD], b2[PPLBM_NGRAD];
+  const double a0 = p->alpha;
+  if (pplbm_status s = at(a0 + h, a1)) return s;
+  if (pplbm_status s = at(a0 - h, a2)) return s;
+  if (pplbm_status s = at(a0 + h / 2, b1)) return s;
+  if (pplbm_status s = at(a0 - h / 2, b2)) return s;
+  for (int k = 0; k < PPLBM_NGRAD; ++k) {
+    const double d1 = (a1[k] - a2[k]) / (2 * h), d2 = (b1[k] - b2[k]) / h;
+    dc[k] = (4 * d2 - d1) / 3;  // Richardson: O(h^4)
+  }
+  return PPLBM_OK;
+}
+
+}  // extern "C"

@@ -8,38 +8,13 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include <vector>
 
 #include "../../include/pplbm.h"
 #include "internal.h"
 
 using namespace pplbm;
 
-struct pplbm_ctx {
-  pplbm_lattice lat;
-  pplbm_relax relax;
-  pplbm_eos_derived eos;
-  double G;
-  int64_t n;
-  int nmom;
-  double* fA;  // current f(t)
-  double* fB;  // next f(t+1); scratch between steps (host staging)
-  double* psi;
-  double* mom;
-  cudaStream_t stream;
-  void* dev_block;  // owned: error word + guard partials + guard output
-  int* d_err;
-  double* d_partials;
-  double* d_guard;
-  int64_t steps;
-  pplbm_status sticky;
-  std::string msg;
-  StepArgs args;
-  // kernel timing: event pairs recorded around each launch while enabled
-  bool timing;
-  std::vector<cudaEvent_t> ev[2];  // per kernel: start/stop interleaved
-  size_t ev_used[2];
-};
+#include "ctx.h"
 
 namespace {
 

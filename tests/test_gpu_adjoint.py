@@ -1,0 +1,132 @@
+"""GPU adjoint: one adjoint step against the oracle's reverse-mode autograd, a
+small checkpointed rollout against the oracle, and the 256 x 256 droplet
+rollout of 2,000 steps (R = 48, T_r = 0.5, sqrt(N) checkpoints) against central
+finite differences (h = 1e-6) in alpha and in the initial density."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from gpu_helpers import BC_PER, BC_WALLS, make_pair, normwise
+from oracle import adjoint as A
+from oracle import eos as E
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2107_06355_gb300")
+from paper_2107_06355_gb300 import _lib as L  # noqa: E402
+from paper_2107_06355_gb300 import adjoint as AD  # noqa: E402
+
+CASE = (E.MODE_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+
+
+def _state(olat, nx, ny, bc):
+    e = olat.eos
+    if bc == BC_WALLS:
+        rho, ux, uy = I.impact(nx, ny, 3, 4, e.rho_v, e.rho_l, 0.01, W=6.0)
+    else:
+        rho = I.perturbed(I.droplet(nx, ny, min(nx, ny) / 4, e.rho_v, e.rho_l, W=5.0), 0.01, 5)
+        ux, uy = I.random_velocity((ny, nx), 0.005, 6)
+    return olat.step(olat.init_equilibrium(rho, ux, uy), 3)
+
+
+def _gpu_alpha_grad(grad, spec_eos, relax):
+    dc = (C.c_double * L.NGRAD)()
+    p = spec_eos.c()
+    r = relax.c()
+    assert L.lib().pplbm_eos_constant_sensitivity(C.byref(p), -1.0, C.byref(r), 0, 1e-4, dc) == 0
+    return float(sum(g * d for g, d in zip(grad, dc)))
+
+
+@pytest.mark.parametrize("shape,bc", [((40, 18), BC_PER), ((37, 22), BC_WALLS)], ids=["periodic", "walls"])
+def test_adjoint_step_matches_oracle_autograd(shape, bc):
+    nx, ny = shape
+    olat, sim = make_pair(nx, ny, bc, CASE, {})
+    f = _state(olat, nx, ny, bc)
+    lam1 = np.random.default_rng(11).standard_normal((9, ny, nx))
+    # oracle: reverse mode through the torch restatement
+    c = A.constants_as_tensors(olat.eos)
+    x = torch.tensor(f, requires_grad=True)
+    (A.step(x, olat, c) * torch.tensor(lam1)).sum().backward()
+    dc_cpu = A.constants_derivative(*CASE[:4], CASE[4])
+    galpha_cpu = sum(float(c[k].grad) * dc_cpu[k] for k in A.CONST_NAMES)
+    # GPU
+    fd = torch.tensor(f, device="cuda")
+    l1 = torch.tensor(lam1, device="cuda")
+    l0 = torch.empty_like(l1)
+    grad = torch.zeros(L.NGRAD, dtype=torch.float64, device="cuda")
+    nbytes = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
+    ws = torch.empty(nbytes // 8 + 1, dtype=torch.float64, device="cuda")
+    p = lambda t: C.c_void_p(t.data_ptr())
+    assert L.lib().pplbm_adjoint_step(sim.ctx, p(fd), p(l1), p(l0), p(grad), p(ws), nbytes) == 0
+    torch.cuda.synchronize()
+    assert normwise(l0.cpu().numpy(), x.grad.numpy()) < 1e-12
+    galpha_gpu = _gpu_alpha_grad(grad.tolist(), sim.eos_params, sim.relax)
+    assert galpha_gpu == pytest.approx(galpha_cpu, rel=1e-6)
+
+
+def test_small_rollout_matches_oracle_reference_adjoint():
+    nx, ny, nsteps = 24, 24, 30
+    olat, _ = make_pair(nx, ny, BC_PER, CASE, {})
+    e = olat.eos
+    rho0 = I.droplet(nx, ny, 6.0, e.rho_v, e.rho_l, W=5.0)
+    # oracle reference adjoint
+    c = A.constants_as_tensors(e)
+    r0 = torch.tensor(rho0, requires_grad=True)
+    g = torch.stack([float(w) * r0 for w in A._W])
+    for _ in range(nsteps):
+        g = A.step(g, olat, c)
+    loss = A.droplet_loss(g.sum(0), e.rho_v, e.rho_l, 6.0)
+    loss.backward()
+    dc_cpu = A.constants_derivative(*CASE[:4], CASE[4])
+    galpha_cpu = sum(float(c[k].grad) * dc_cpu[k] for k in A.CONST_NAMES)
+    # GPU rollout through the autograd Function
+    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775), P.Relax(),
+                          nsteps, interval=7)
+    rho0_t = torch.tensor(rho0, device="cuda", requires_grad=True)
+    alpha = torch.tensor(0.775, dtype=torch.float64, requires_grad=True)
+    rhoN = AD.rollout(rho0_t, alpha, spec)
+    lg = A.droplet_loss(rhoN, e.rho_v, e.rho_l, 6.0)
+    lg.backward()
+    # the vapour term divides by rho_v ~ 6e-4, which amplifies 1e-13 differences in rho
+    assert float(lg.detach()) == pytest.approx(float(loss.detach()), rel=1e-8)
+    assert normwise(rho0_t.grad.cpu().numpy(), r0.grad.numpy()) < 1e-8
+    assert float(alpha.grad) == pytest.approx(galpha_cpu, rel=1e-6)
+
+
+def test_droplet_256_rollout_2000_steps_against_finite_differences():
+    """The adjoint configuration: 256 x 256 periodic droplet, R = 48, T_r = 0.5
+    (a_l = 0.363, a_v = 2, alpha = 0.775), tau = 1, 2,000 steps, checkpoint every
+    45 steps; loss = squared vapour-density error vs Maxwell + radius mismatch."""
+    nx = ny = 256
+    nsteps, R0 = 2000, 48.0
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    d = P.eos_setup(eosp)
+    rv, rl = d["rho_v"], d["rho_l"]
+    rho0 = torch.tensor(I.droplet(nx, ny, R0, rv, rl, W=7.0), device="cuda")
+    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps, interval=45)
+
+    def loss_of(rho):
+        phi = (rho - rv) / (rl - rv)
+        reff = torch.sqrt(phi.sum() / math.pi)
+        return ((rho[0, 0] - rv) / rv) ** 2 + ((reff - R0) / R0) ** 2
+
+    r0 = rho0.clone().requires_grad_(True)
+    alpha = torch.tensor(0.775, dtype=torch.float64, requires_grad=True)
+    L0 = loss_of(AD.rollout(r0, alpha, spec))
+    L0.backward()
+
+    def loss_at(al, rho):
+        with torch.no_grad():
+            return float(loss_of(AD.rollout(rho, torch.tensor(al, dtype=torch.float64), spec)))
+
+    h = 1e-6
+    fd_alpha = (loss_at(0.775 + h, rho0) - loss_at(0.775 - h, rho0)) / (2 * h)
+    assert float(alpha.grad) == pytest.approx(fd_alpha, rel=1e-6)
+    v = torch.tensor(np.random.default_rng(7).standard_normal((ny, nx)), device="cuda") * rho0
+    hv = 1e-6
+    fd_rho = (loss_at(0.775, rho0 + hv * v) - loss_at(0.775, rho0 - hv * v)) / (2 * hv)
+    assert float((r0.grad * v).sum()) == pytest.approx(fd_rho, rel=1e-6)
