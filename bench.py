@@ -179,6 +179,23 @@ def profile_case():
     print("profile case done")
 
 
+def profile_batch():
+    """The benchmark's four 512 x 512 droplets in one batch, launches plan, 3 steps:
+    3 launches of each batched pass over 1,048,576 nodes (184 MB of state, > L2)."""
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    specs = [dict(kind="droplet", nx=NX, ny=NY, R=R, Tr=TR) for R in RADII]
+    b, _, _, _ = make_batch(P, I, specs, torch.cuda.current_stream())
+    b.set_plan(P.PLAN_LAUNCHES, 0)
+    b.step(3)
+    b.sync()
+    torch.cuda.synchronize()
+    print("profile batch done")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -277,6 +294,46 @@ def sweep_comparison(torch, stream, steps):
             "speedup": ms_s / ms_b}
 
 
+def adjoint_cost(torch, steps=400, interval=20):
+    """Adjoint configuration (256 x 256 droplet, R = 48, T_r = 0.5, tau = 1): time of a
+    checkpointed forward rollout vs its reverse pass (recomputation + adjoint kernels)."""
+    import ctypes as C
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import _lib as L
+
+    nx = ny = 256
+    eos = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    sim = P.Simulation(nx, ny, P.BC_PERIODIC, eos, P.Relax())
+    d = sim.derived()
+    rho0 = I.droplet(nx, ny, 48.0, d["rho_v"], d["rho_l"], W=7.0)
+    nseg = -(-steps // interval)
+    dev = sim.device
+    ckpt = torch.empty((nseg, 9, ny, nx), dtype=torch.float64, device=dev)
+    seg = torch.empty((interval, 9, ny, nx), dtype=torch.float64, device=dev)
+    lam = torch.ones((9, ny, nx), dtype=torch.float64, device=dev)
+    lam0 = torch.empty_like(lam)
+    grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
+    nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
+    ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
+    p = lambda t: C.c_void_p(t.data_ptr())
+    lib = L.lib()
+    res = []
+    for _ in range(2):  # second round is timed
+        sim.init_equilibrium(rho0)
+        t_f = time_device(torch, torch.cuda.current_stream(),
+                          lambda: L.check(lib.pplbm_forward_checkpointed(sim.ctx, steps, interval, p(ckpt)), sim.ctx))
+        t_b = time_device(torch, torch.cuda.current_stream(),
+                          lambda: L.check(lib.pplbm_backward_checkpointed(sim.ctx, steps, interval, p(ckpt), p(seg),
+                                                                          p(lam), p(lam0), p(grad), p(ws), nb),
+                                          sim.ctx))
+        res = (t_f, t_b)
+    sim.close()
+    return {"config": f"256x256 droplet R=48, T_r=0.5, {steps} steps, checkpoint interval {interval}",
+            "forward_ms": res[0], "backward_ms": res[1], "adjoint_over_forward": res[1] / res[0],
+            "forward_mlups": nx * ny * steps / (res[0] / 1e3) / 1e6}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,11 +342,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--plan", default="auto", choices=["auto", "launches", "graph", "persistent"],
+                    help="batched-engine plan for the timed run (auto: autotuned)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run the four 512x512 droplets through the batched engine (launches plan) for 3 steps and exit")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
+    if args.profile_batch:
+        return profile_batch()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -314,7 +377,11 @@ def main():
     specs = [dict(kind="droplet", nx=NX, ny=NY, R=R, Tr=TR) for R in RADII]
     batch, _, _, rho0s = make_batch(P, I, specs, stream)
     nodes = NX * NY * len(specs)
-    plan = batch.autotune(trial_steps=20)
+    if args.plan == "auto":
+        plan = batch.autotune(trial_steps=20)
+    else:
+        batch.set_plan({"launches": P.PLAN_LAUNCHES, "graph": P.PLAN_GRAPH, "persistent": P.PLAN_PERSISTENT}[args.plan], 0)
+        plan = batch.plan()
     batch.step(args.warmup)
     torch.cuda.synchronize()
     batch.enable_timing(4)
@@ -432,6 +499,7 @@ def main():
     }
     if rank == 0 and ws == 1 and not args.no_sweep:
         line["batch_sweep"] = sweep_comparison(torch, stream, 100)
+        line["adjoint"] = adjoint_cost(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle_sample()
     if rank == 0:
