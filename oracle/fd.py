@@ -1,0 +1,112 @@
+"""Oracle: the finite-difference (MacCormack) solver of App. A, periodic domains.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``). It integrates the
+macroscopic equations the lattice Boltzmann method recovers, written as in
+App. A:
+
+  d_t rho   = -(rho d_g u_g + u_g d_g rho)
+  d_t u_a   = -u_g d_g u_a - (1/rho) d_a p_EOS - (1/rho) d_b p'_ab + (1/rho) d_b sigma'_ab
+
+with the viscous stress of Eq. StressTensor expanded as Eq. FDstressTensor
+(mu = rho c_s^2 (tau_nu - 1/2), mu_B = rho c_s^2 (tau_e - tau_nu), Eq.
+DynamicViscosity; their gradients through d mu/d rho, Eq. FDviscosityDerivative)
+and d_b p'_ab of Eq. FDforce,
+
+  d_b p'_ab = -eps (G c^4/4) (d_g psi)(d_a d_g psi) + (G c^4/12)(d_a psi)(d_g d_g psi)
+              + (G c^4/6)(d_g psi)(d_a d_g psi) + (G c^4/4) psi d_a d_g d_g psi.
+
+MacCormack predictor/corrector: first derivatives of rho, u, p_EOS and mu in the
+advective, pressure and viscous terms are forward differences in the predictor
+and backward differences in the corrector; second derivatives are central in
+both; every derivative in d_b p'_ab is a second-order central difference.
+Periodic boundaries only (the wall conditions of App. B are not restated).
+Lengths are in lattice units; dx is the FD grid spacing, c = 1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _sh(a, dy, dx):
+    """a(y + dy, x + dx) on a periodic grid (a has shape (ny, nx))."""
+    return np.roll(a, shift=(-dy, -dx), axis=(0, 1))
+
+
+class FDSolver:
+    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0):
+        self.eos = eos
+        self.eps = eps
+        self.G = eos.G
+        self.dx = dx
+        self.tau_nu = tau_nu
+        self.tau_e = tau_e
+
+    # difference operators (axis 0 = y, axis 1 = x)
+    def d1(self, a, axis, kind):
+        h = self.dx
+        dy, dx = (1, 0) if axis == 0 else (0, 1)
+        if kind == "f":
+            return (_sh(a, dy, dx) - a) / h
+        if kind == "b":
+            return (a - _sh(a, -dy, -dx)) / h
+        return (_sh(a, dy, dx) - _sh(a, -dy, -dx)) / (2 * h)
+
+    def d2(self, a, ax1, ax2):
+        h = self.dx
+        if ax1 == ax2:
+            dy, dx = (1, 0) if ax1 == 0 else (0, 1)
+            return (_sh(a, dy, dx) - 2 * a + _sh(a, -dy, -dx)) / h**2
+        return (_sh(a, 1, 1) - _sh(a, 1, -1) - _sh(a, -1, 1) + _sh(a, -1, -1)) / (4 * h**2)
+
+    def rhs(self, rho, u, kind):
+        """Time derivatives (d_t rho, d_t u_x, d_t u_y); kind 'f' (predictor) or 'b' (corrector)."""
+        G, eps = self.G, self.eps
+        cs2 = 1.0 / 3.0
+        axes = (1, 0)  # alpha = x -> axis 1, alpha = y -> axis 0
+        p = self.eos.pressure(rho)
+        psi = self.eos.psi(rho)
+        # mass
+        div = sum(self.d1(u[a], axes[a], kind) for a in range(2))
+        drho = -(rho * div + sum(u[a] * self.d1(rho, axes[a], kind) for a in range(2)))
+        # psi derivatives (central)
+        dpsi = [self.d1(psi, axes[a], "c") for a in range(2)]
+        ddpsi = [[self.d2(psi, axes[a], axes[b]) for b in range(2)] for a in range(2)]
+        lap = ddpsi[0][0] + ddpsi[1][1]
+        dlap = [self.d1(lap, axes[a], "c") for a in range(2)]
+        # viscosity and its density derivative (constant relaxation times)
+        mu = rho * cs2 * (self.tau_nu - 0.5)
+        muB = rho * cs2 * (self.tau_e - self.tau_nu)
+        dmu_drho = cs2 * (self.tau_nu - 0.5)
+        dmuB_drho = cs2 * (self.tau_e - self.tau_nu)
+        drho_1 = [self.d1(rho, axes[a], kind) for a in range(2)]
+        du = [[self.d1(u[b], axes[a], kind) for b in range(2)] for a in range(2)]  # du[a][b] = d_a u_b
+        ddu = [[[self.d2(u[c], axes[a], axes[b]) for c in range(2)] for b in range(2)] for a in range(2)]
+        dpdx = [self.d1(p, axes[a], kind) for a in range(2)]
+        dgu = du[0][0] + du[1][1]
+        out = []
+        for a in range(2):
+            adv = sum(u[g] * du[g][a] for g in range(2))
+            s = sum(dpsi[g] * ddpsi[a][g] for g in range(2))
+            dpprime = (-eps * G / 4.0 * s + G / 12.0 * dpsi[a] * lap + G / 6.0 * s + G / 4.0 * psi * dlap[a])
+            visc = (sum(dmu_drho * drho_1[b] * (du[a][b] + du[b][a]) for b in range(2))
+                    + mu * sum(ddu[a][b][b] + ddu[b][b][a] for b in range(2))
+                    + dmuB_drho * drho_1[a] * dgu
+                    + muB * sum(ddu[a][b][b] for b in range(2)))
+            out.append(-adv - dpdx[a] / rho - dpprime / rho + visc / rho)
+        return drho, out
+
+    def step(self, rho, u, dt):
+        """One MacCormack step; u = [u_x, u_y]."""
+        r1, du1 = self.rhs(rho, u, "f")
+        rho_p = rho + dt * r1
+        u_p = [u[a] + dt * du1[a] for a in range(2)]
+        r2, du2 = self.rhs(rho_p, u_p, "b")
+        rho_n = 0.5 * (rho + rho_p + dt * r2)
+        u_n = [0.5 * (u[a] + u_p[a] + dt * du2[a]) for a in range(2)]
+        return rho_n, u_n
+
+    def run(self, rho, u, t_end, dt):
+        n = int(round(t_end / dt))
+        for _ in range(n):
+            rho, u = self.step(rho, u, dt)
+        return rho, u
