@@ -403,10 +403,9 @@ def main():
     ms = e0.elapsed_time(e1)
     call_ms, call_steps = batch.times()
     batch.enable_timing(0)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2107_06355_gb300.replicas import max_over_ranks
+
+    ms = max_over_ranks(ms, device="cuda")  # each rank runs its own replica; slowest rank sets the time
     batch.sync()
 
     # the same four lattices stepped one context at a time (two launches per lattice per step)
