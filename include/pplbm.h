@@ -65,6 +65,12 @@ typedef enum pplbm_status {
 #define PPLBM_EOS_CS 0      /* Carnahan-Starling with a_liq everywhere (Eq. CS) */
 #define PPLBM_EOS_SMOOTH 1  /* Smooth C-S of Sec. III.D: vapour branch C-S(a_vap),
                                liquid branch C-S(a_liq) + Delta P (Sec. III.D, last part) */
+#define PPLBM_EOS_PENG 2    /* Peng et al. loop (Eqs. PengEOS, PengTheta) on C-S(a_liq): the cubic
+                               p_sat + theta (rho - rho_v)(rho - rho_l)(rho - rho_m), rho_m from Eq.
+                               VaporLiqEq with eps = 0, theta from r_theta; meant for Guo forcing */
+#define PPLBM_EOS_SMOOTH_MOD 3  /* "Modified Smooth" (Sec. IV.C): the Smooth C-S shape with p_max
+                                   from Eq. VaporLiqEq with eps = 0 instead of the Maxwell rule;
+                                   meant for Guo forcing */
 
 /* Relaxation set. */
 #define PPLBM_RELAX_MRT 0        /* six constant relaxation times, Eq. RelaxationMatrix */
@@ -89,6 +95,7 @@ typedef struct pplbm_eos_params {
   double a_vap;     /* C-S attraction a of the vapour branch (PPLBM_EOS_SMOOTH) */
   double b, R;      /* C-S co-volume and gas constant (paper: b = 4, R = 1) */
   double alpha;     /* shaping parameter: p_min = p_sat - alpha (p_sat^CS - p_min^CS) (Sec. III.D) */
+  double r_theta;   /* PPLBM_EOS_PENG: weight of the liquid slope in theta (Eq. PengTheta) */
 } pplbm_eos_params;
 
 typedef struct pplbm_relax {
@@ -122,8 +129,10 @@ typedef struct pplbm_eos_derived {
   double dpdrho_v, dpdrho_l; /* bulk-branch slopes at rho_v and rho_l */
   double a1sq, b1;           /* region-1 ellipse */
   double a3sq, b3;           /* region-3 ellipse */
-  double eps;                /* mechanical-stability exponent solving Eq. VaporLiqEq */
+  double eps;                /* mechanical-stability exponent solving Eq. VaporLiqEq (0 for the
+                                Peng and Modified Smooth EOS, built for eps = 0) */
   double psi_v, psi_l;       /* psi(rho_v), psi(rho_l): wall ghost values (Sec. IV) */
+  double rho_m, theta;       /* PPLBM_EOS_PENG: cubic root and coefficient */
 } pplbm_eos_derived;
 
 typedef struct pplbm_ctx pplbm_ctx;

@@ -44,8 +44,10 @@ import numpy as np
 from scipy import integrate, optimize
 
 # Coexistence EOS modes.
-MODE_CS = 0       # plain Carnahan-Starling (the "standard procedure", Sec. III.B)
-MODE_SMOOTH = 1   # Smooth C-S (Sec. III.D)
+MODE_CS = 0           # plain Carnahan-Starling (the "standard procedure", Sec. III.B)
+MODE_SMOOTH = 1       # Smooth C-S (Sec. III.D)
+MODE_PENG = 2         # Peng et al. cubic loop (Sec. II.D, Eqs. PengEOS, PengTheta), Guo forcing
+MODE_SMOOTH_MOD = 3   # "Modified Smooth" (Sec. IV.C): p_max from Eq. VaporLiqEq with eps = 0
 
 
 # ---------------------------------------------------------------------------
@@ -166,6 +168,7 @@ class EOS:
     b: float = 4.0
     R: float = 1.0
     G: float = -1.0
+    r_theta: float = 0.0   # MODE_PENG: theta from Eq. PengTheta
 
     def __post_init__(self):
         b, R = self.b, self.R
@@ -179,7 +182,14 @@ class EOS:
         if self.mode == MODE_CS:
             self.p_sat = self.p_sat_cs
             self.dP = 0.0
-        elif self.mode == MODE_SMOOTH:
+        elif self.mode == MODE_PENG:
+            self.p_sat = self.p_sat_cs
+            self.dP = 0.0
+            self.dpdrho_v = cs_dpdrho(self.rho_v, self.a_l, b, R, self.T_l)
+            self.dpdrho_l = cs_dpdrho(self.rho_l, self.a_l, b, R, self.T_l)
+            self.rho_m = self._solve_rho_m()
+            self._peng_theta(self.rho_m)
+        elif self.mode in (MODE_SMOOTH, MODE_SMOOTH_MOD):
             # saturation pressure of the vapour-branch EOS at the same reduced temperature
             _, _, p_sat_v = maxwell(self.a_v, b, R, self.T_v)
             self.p_sat = p_sat_v
@@ -190,6 +200,8 @@ class EOS:
             self._region3()
             self.p_max = self._solve_p_max()
             self._region1(self.p_max)
+            if self.mode == MODE_SMOOTH_MOD:
+                self.eps = 0.0
         else:
             raise ValueError("unknown EOS mode")
         self.eps = None
@@ -219,9 +231,53 @@ class EOS:
 
         def residual(pm):
             self._region1(pm)
+            if self.mode == MODE_SMOOTH_MOD:
+                return self.mech_stability_quad(0.0)
             return self.maxwell_residual()
 
         return optimize.brentq(residual, lo, hi, **kw)
+
+    def mech_stability_quad(self, eps):
+        """Eq. VaporLiqEq by adaptive quadrature over the three regions (set-up root finding)."""
+        f = lambda r: (self.p_sat - float(self.pressure(r))) * float(self.dpsidrho(r)) / float(self.psi(r)) ** (1.0 + eps)
+        total = 0.0
+        for lo, hi in self._regions():
+            val, _ = integrate.quad(f, lo, hi, epsabs=0.0, epsrel=1e-13, limit=500)
+            total += val
+        return total
+
+    def _regions(self):
+        if self.mode == MODE_PENG:
+            return ((self.rho_v, self.rho_l),)
+        return ((self.rho_v, self.rho_max), (self.rho_max, self.rho_min), (self.rho_min, self.rho_l))
+
+    # -- Peng et al. loop, Eqs. PengEOS and PengTheta ---------------------------------
+    def _peng_theta(self, rho_m):
+        rv, rl = self.rho_v, self.rho_l
+        self.theta = ((1.0 - self.r_theta) / ((rv - rho_m) * (rv - rl)) * self.dpdrho_v
+                      + self.r_theta / ((rl - rho_m) * (rl - rv)) * self.dpdrho_l)
+
+    def _solve_rho_m(self):
+        """rho_m such that Eq. ShanVaporLiqEq (eps = 0) holds at the Maxwell densities."""
+        kw = dict(xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=500)
+
+        def residual(rm):
+            self.rho_m = rm
+            self._peng_theta(rm)
+            return self.mech_stability_quad(0.0)
+
+        d = self.rho_l - self.rho_v
+        grid = np.linspace(self.rho_v + 1e-3 * d, self.rho_l - 1e-3 * d, 60)
+        vals = []
+        for rm in grid:
+            try:
+                vals.append(residual(rm))
+            except (ValueError, ZeroDivisionError, FloatingPointError):
+                vals.append(np.nan)
+        for (a, fa), (b_, fb) in zip(zip(grid[:-1], vals[:-1]), zip(grid[1:], vals[1:])):
+            if np.isfinite(fa) and np.isfinite(fb) and fa * fb < 0:
+                return optimize.brentq(residual, a, b_, **kw)
+        raise RuntimeError("no rho_m solves the mechanical stability condition")
 
     def maxwell_residual(self):
         f = lambda r: (self.p_sat - self.pressure(r)) / r**2
@@ -238,6 +294,15 @@ class EOS:
         b, R = self.b, self.R
         if self.mode == MODE_CS:
             return cs_pressure(rho, self.a_l, b, R, self.T_l)
+        if self.mode == MODE_PENG:
+            p = cs_pressure(rho, self.a_l, b, R, self.T_l)
+            m = (rho > self.rho_v) & (rho < self.rho_l)
+            x = rho[m] if p.ndim else rho
+            loop = self.p_sat + self.theta * (x - self.rho_v) * (x - self.rho_l) * (x - self.rho_m)
+            if p.ndim:
+                p[m] = loop
+                return p
+            return float(loop) if m else float(p)
         p = np.empty_like(rho)
         r1 = rho <= self.rho_v
         r2 = (rho > self.rho_v) & (rho <= self.rho_max)
@@ -261,6 +326,16 @@ class EOS:
         b, R = self.b, self.R
         if self.mode == MODE_CS:
             return cs_dpdrho(rho, self.a_l, b, R, self.T_l)
+        if self.mode == MODE_PENG:
+            d = cs_dpdrho(rho, self.a_l, b, R, self.T_l)
+            m = (rho > self.rho_v) & (rho < self.rho_l)
+            x = rho[m] if d.ndim else rho
+            rv, rl, rm = self.rho_v, self.rho_l, self.rho_m
+            loop = self.theta * ((x - rl) * (x - rm) + (x - rv) * (x - rm) + (x - rv) * (x - rl))
+            if d.ndim:
+                d[m] = loop
+                return d
+            return float(loop) if m else float(d)
         d = np.empty_like(rho)
         r1 = rho <= self.rho_v
         r2 = (rho > self.rho_v) & (rho <= self.rho_max)
@@ -290,7 +365,7 @@ class EOS:
     # -- mechanical stability, Eq. VaporLiqEq --------------------------------------
     def _simpson_nodes(self, n):
         """Composite-Simpson nodes and weights over [rho_v, rho_l] in s = ln rho, per region."""
-        edges = [self.rho_v, self.rho_max, self.rho_min, self.rho_l]
+        edges = [self.rho_v, self.rho_l] if self.mode == MODE_PENG else [self.rho_v, self.rho_max, self.rho_min, self.rho_l]
         rs, ws = [], []
         for lo, hi in zip(edges[:-1], edges[1:]):
             s = np.linspace(math.log(lo), math.log(hi), 2 * n + 1)
@@ -331,12 +406,16 @@ class EOS:
         return eps
 
     def sigma(self):
-        """sigma of the Li forcing scheme from eps = -16 G sigma (Sec. II.C)."""
+        """sigma of the Li forcing scheme from eps = -16 G sigma (Sec. II.C); the Peng and
+        Modified Smooth EOS are used with the Guo scheme (sigma = 0, Sec. II.D, IV.C)."""
+        if self.mode in (MODE_PENG, MODE_SMOOTH_MOD):
+            return 0.0
         if self.eps is None:
             self.solve_eps()
         return -self.eps / (16.0 * self.G)
 
 
-def make_eos(mode, Tr, a_l, a_v=None, alpha=0.0, b=4.0, R=1.0, G=-1.0):
+def make_eos(mode, Tr, a_l, a_v=None, alpha=0.0, b=4.0, R=1.0, G=-1.0, r_theta=0.0):
     """Convenience constructor; a_v defaults to a_l."""
-    return EOS(mode=mode, Tr=Tr, a_l=a_l, a_v=a_l if a_v is None else a_v, alpha=alpha, b=b, R=R, G=G)
+    return EOS(mode=mode, Tr=Tr, a_l=a_l, a_v=a_l if a_v is None else a_v, alpha=alpha, b=b, R=R, G=G,
+               r_theta=r_theta)

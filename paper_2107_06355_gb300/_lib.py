@@ -29,6 +29,8 @@ BC_WALLS_Y = BC_PERIODIC_X | BC_WALL_BOTTOM | BC_WALL_TOP
 
 EOS_CS = 0
 EOS_SMOOTH = 1
+EOS_PENG = 2
+EOS_SMOOTH_MOD = 3
 RELAX_MRT = 0
 RELAX_TWO_PHASE = 1
 FORCING_GUO = 0
@@ -41,7 +43,8 @@ class pplbm_lattice(C.Structure):
 
 class pplbm_eos_params(C.Structure):
     _fields_ = [("mode", C.c_int32), ("reserved", C.c_int32), ("Tr", C.c_double), ("a_liq", C.c_double),
-                ("a_vap", C.c_double), ("b", C.c_double), ("R", C.c_double), ("alpha", C.c_double)]
+                ("a_vap", C.c_double), ("b", C.c_double), ("R", C.c_double), ("alpha", C.c_double),
+                ("r_theta", C.c_double)]
 
 
 class pplbm_relax(C.Structure):
@@ -54,7 +57,7 @@ class pplbm_relax(C.Structure):
 
 _DERIVED_DOUBLES = ["G", "b", "R", "a_l", "a_v", "Tc_l", "Tc_v", "T_l", "T_v", "rho_v", "rho_l", "p_sat",
                     "p_sat_cs", "rho_max", "rho_min", "p_min_cs", "p_max", "p_min", "dP", "dpdrho_v",
-                    "dpdrho_l", "a1sq", "b1", "a3sq", "b3", "eps", "psi_v", "psi_l"]
+                    "dpdrho_l", "a1sq", "b1", "a3sq", "b3", "eps", "psi_v", "psi_l", "rho_m", "theta"]
 
 
 class pplbm_eos_derived(C.Structure):

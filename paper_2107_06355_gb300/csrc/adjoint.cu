@@ -120,8 +120,13 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
   for (int k = 0; k < kNGrad - 1; ++k) dc[k] = 0.0;
   const long long rb = dbits(rho);
   const bool vap = rb <= e.bits_rho_v, liq = rb >= e.bits_rho_l;
-  if (e.mode == 0 || vap || liq) {
-    const bool use_v = (e.mode != 0) && vap;
+  if (e.mode == 2 && !vap && !liq) {  // Peng cubic loop: no alpha-dependent constants
+    const double dv = rho - e.rho_v, dl = rho - e.rho_l, dm = rho - e.rho_m;
+    const double dp = e.theta * (dl * dm + dv * dm + dv * dl);
+    return e.psi2_scale * (dp - 1.0 / 3.0);
+  }
+  if (e.mode != 1 || vap || liq) {
+    const bool use_v = (e.mode == 1) && vap;
     const double k1 = use_v ? e.k1_v : e.k1_l, k2 = use_v ? e.k2_v : e.k2_l;
     const double eta = e.b4 * rho, om = 1.0 - eta;
     const double num = fma(eta, fma(eta, om, 1.0), 1.0);

@@ -24,7 +24,7 @@ namespace pplbm {
 
 // Constants for fast evaluation, built once from pplbm_eos_derived.
 struct EosConst {
-  int mode;            // PPLBM_EOS_*
+  int mode;            // shape of p(rho): 0 C-S everywhere, 1 Smooth C-S regions, 2 Peng cubic loop
   int pad;
   double b4;           // b / 4
   double RT_v, a_v;    // vapour branch (mode SMOOTH); equals the liquid branch for mode CS
@@ -41,6 +41,7 @@ struct EosConst {
   double k3;
   // bit patterns of the branch densities (positive doubles order like their bits)
   long long bits_rho_v, bits_rho_max, bits_rho_min, bits_rho_l;
+  double p_sat, theta, rho_m;  // Peng loop: p_sat + theta (rho - rho_v)(rho - rho_l)(rho - rho_m)
 };
 
 PPLBM_HD inline double cs_pressure(double rho, double b4, double RT, double a) {
@@ -52,6 +53,10 @@ PPLBM_HD inline double cs_pressure(double rho, double b4, double RT, double a) {
 
 PPLBM_HD inline double eos_pressure(const EosConst& e, double rho) {
   if (e.mode == 0) return cs_pressure(rho, e.b4, e.RT_l, e.a_l);
+  if (e.mode == 2) {
+    if (rho > e.rho_v && rho < e.rho_l) return e.p_sat + e.theta * (rho - e.rho_v) * (rho - e.rho_l) * (rho - e.rho_m);
+    return cs_pressure(rho, e.b4, e.RT_l, e.a_l);
+  }
   if (rho <= e.rho_v) return cs_pressure(rho, e.b4, e.RT_v, e.a_v);
   if (rho <= e.rho_max) {
     const double d = rho - e.rho_max;

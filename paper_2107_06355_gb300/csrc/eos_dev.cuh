@@ -18,8 +18,12 @@ __device__ __forceinline__ double eos_psi2_dev(const EosConst& e, double rho) {
   const long long rb = dbits(rho);
   const bool vap = rb <= e.bits_rho_v;
   const bool liq = rb >= e.bits_rho_l;
-  if (e.mode == 0 || vap || liq) {
-    const bool use_v = (e.mode != 0) && vap;
+  if (e.mode == 2 && !vap && !liq) {  // Peng cubic loop (Eq. PengEOS)
+    const double p = fma(e.theta * (rho - e.rho_v), (rho - e.rho_l) * (rho - e.rho_m), e.p_sat);
+    return e.psi2_scale * fma(-rho, 1.0 / 3.0, p);
+  }
+  if (e.mode != 1 || vap || liq) {
+    const bool use_v = (e.mode == 1) && vap;
     const double k1 = use_v ? e.k1_v : e.k1_l;
     const double k2 = use_v ? e.k2_v : e.k2_l;
     const double k4 = use_v ? e.k4_v : e.k4_l;

@@ -217,11 +217,12 @@ bool ellipse(double dp_dr, double delta, double dpress, double& asq, double& bb)
 
 EosConst make_eos_const(const pplbm_eos_derived& d) {
   EosConst e{};
-  e.mode = d.mode;
+  // shape of p(rho): the Modified Smooth EOS has the Smooth C-S shape
+  e.mode = d.mode == PPLBM_EOS_SMOOTH_MOD ? PPLBM_EOS_SMOOTH : d.mode;
   e.b4 = d.b / 4.0;
   e.RT_l = d.R * d.T_l;
   e.a_l = d.a_l;
-  if (d.mode == PPLBM_EOS_SMOOTH) {
+  if (d.mode == PPLBM_EOS_SMOOTH || d.mode == PPLBM_EOS_SMOOTH_MOD) {
     e.RT_v = d.R * d.T_v;
     e.a_v = d.a_v;
   } else {
@@ -255,47 +256,68 @@ EosConst make_eos_const(const pplbm_eos_derived& d) {
   std::memcpy(&e.bits_rho_max, &e.rho_max, 8);
   std::memcpy(&e.bits_rho_min, &e.rho_min, 8);
   std::memcpy(&e.bits_rho_l, &e.rho_l, 8);
+  e.p_sat = d.p_sat;
+  e.theta = d.theta;
+  e.rho_m = d.rho_m;
   return e;
 }
 
-// Newton from eps = 2 on g(eps) = int (p_sat - p) psi'/psi^(1+eps) d rho (Eq. VaporLiqEq).
-// With psi^2 = (2/G)(p - rho/3): psi'/psi = (p' - 1/3)/(G psi^2), with p' the closed-form
-// derivative of the piece containing rho; dg/deps = -int ln(psi) (...) d rho.
-bool solve_eps(const pplbm_eos_derived& d, double& eps_out) {
-  const EosConst e = make_eos_const(d);
-  auto dp = [&](double r) {
-    // derivative of the piece containing r, from its closed form
-    if (e.mode == PPLBM_EOS_CS) return cs_dp(r, d.a_l, d.b, d.R, d.T_l);
-    if (r <= e.rho_v) return cs_dp(r, d.a_v, d.b, d.R, d.T_v);
-    if (r <= e.rho_max) {
-      const double x = r - e.rho_max;
-      return -e.b1 * x * e.inv_a1sq / std::sqrt(1.0 - x * x * e.inv_a1sq);
-    }
-    if (r < e.rho_min) {
-      const double t = (r - e.rho_max) * e.inv_span;
-      return (3.0 * e.a2 * t + 2.0 * e.b2) * t * e.inv_span;
-    }
-    if (r < e.rho_l) {
-      const double x = r - e.rho_min;
-      return e.b3 * x * e.inv_a3sq / std::sqrt(1.0 - x * x * e.inv_a3sq);
-    }
+// dp/drho of the piece containing rho, from its closed form
+static double eos_dpdrho(const EosConst& e, const pplbm_eos_derived& d, double r) {
+  if (e.mode == PPLBM_EOS_CS) return cs_dp(r, d.a_l, d.b, d.R, d.T_l);
+  if (e.mode == PPLBM_EOS_PENG) {
+    if (r > e.rho_v && r < e.rho_l)
+      return e.theta * ((r - e.rho_l) * (r - e.rho_m) + (r - e.rho_v) * (r - e.rho_m) + (r - e.rho_v) * (r - e.rho_l));
     return cs_dp(r, d.a_l, d.b, d.R, d.T_l);
-  };
-  double eps = 2.0;
-  for (int it = 0; it < 100; ++it) {
-    double g = 0.0, dg = 0.0;
-    const double edges[4] = {e.rho_v, e.rho_max, e.rho_min, e.rho_l};
-    for (int r = 0; r < 3; ++r) {
-      auto base = [&](double rho) {
-        const double psi2 = eos_psi2(e, rho);
-        const double psi = std::sqrt(psi2);
-        const double dpsi_over_psi = (dp(rho) - 1.0 / 3.0) / (d.G * psi2);
-        return (d.p_sat - eos_pressure(e, rho)) * dpsi_over_psi * std::pow(psi, -eps);
-      };
-      g += integrate_log(base, edges[r], edges[r + 1], kPanels);
+  }
+  if (r <= e.rho_v) return cs_dp(r, d.a_v, d.b, d.R, d.T_v);
+  if (r <= e.rho_max) {
+    const double x = r - e.rho_max;
+    return -e.b1 * x * e.inv_a1sq / std::sqrt(1.0 - x * x * e.inv_a1sq);
+  }
+  if (r < e.rho_min) {
+    const double t = (r - e.rho_max) * e.inv_span;
+    return (3.0 * e.a2 * t + 2.0 * e.b2) * t * e.inv_span;
+  }
+  if (r < e.rho_l) {
+    const double x = r - e.rho_min;
+    return e.b3 * x * e.inv_a3sq / std::sqrt(1.0 - x * x * e.inv_a3sq);
+  }
+  return cs_dp(r, d.a_l, d.b, d.R, d.T_l);
+}
+
+// g(eps) = int_{rho_v}^{rho_l} (p_sat - p) psi'/psi^(1+eps) d rho (Eq. VaporLiqEq) and dg/deps,
+// with psi^2 = (2/G)(p - rho/3): psi'/psi = (p' - 1/3)/(G psi^2); split where p is only C^1.
+static void mech_integral(const pplbm_eos_derived& d, double eps, double* g_out, double* dg_out) {
+  const EosConst e = make_eos_const(d);
+  double edges[4] = {e.rho_v, e.rho_max, e.rho_min, e.rho_l};
+  int nreg = 3;
+  if (e.mode == PPLBM_EOS_PENG) {
+    edges[1] = e.rho_l;
+    nreg = 1;
+  }
+  double g = 0.0, dg = 0.0;
+  for (int r = 0; r < nreg; ++r) {
+    auto base = [&](double rho) {
+      const double psi2 = eos_psi2(e, rho);
+      const double dpsi_over_psi = (eos_dpdrho(e, d, rho) - 1.0 / 3.0) / (d.G * psi2);
+      return (d.p_sat - eos_pressure(e, rho)) * dpsi_over_psi * std::pow(psi2, -0.5 * eps);
+    };
+    g += integrate_log(base, edges[r], edges[r + 1], kPanels);
+    if (dg_out)
       dg += integrate_log([&](double rho) { return -0.5 * std::log(eos_psi2(e, rho)) * base(rho); }, edges[r],
                           edges[r + 1], kPanels);
-    }
+  }
+  *g_out = g;
+  if (dg_out) *dg_out = dg;
+}
+
+// Newton from eps = 2 on g(eps) = 0 (Sec. III.A)
+bool solve_eps(const pplbm_eos_derived& d, double& eps_out) {
+  double eps = 2.0;
+  for (int it = 0; it < 100; ++it) {
+    double g, dg;
+    mech_integral(d, eps, &g, &dg);
     if (!std::isfinite(g) || !std::isfinite(dg) || dg == 0.0) return false;
     const double step = g / dg;
     eps -= step;
@@ -313,10 +335,12 @@ using namespace pplbm;
 
 extern "C" pplbm_status pplbm_eos_setup(const pplbm_eos_params* p, double G, pplbm_eos_derived* out) {
   if (!p || !out) return PPLBM_ERR_ARG;
-  if (p->mode != PPLBM_EOS_CS && p->mode != PPLBM_EOS_SMOOTH) return PPLBM_ERR_ARG;
+  if (p->mode < PPLBM_EOS_CS || p->mode > PPLBM_EOS_SMOOTH_MOD) return PPLBM_ERR_ARG;
   if (!(p->Tr > 0.0 && p->Tr < 1.0) || !(p->a_liq > 0) || !(p->b > 0) || !(p->R > 0) || !(G < 0.0))
     return PPLBM_ERR_ARG;
-  if (p->mode == PPLBM_EOS_SMOOTH && (!(p->a_vap > 0) || !(p->alpha > 0.0))) return PPLBM_ERR_ARG;
+  const bool smooth = p->mode == PPLBM_EOS_SMOOTH || p->mode == PPLBM_EOS_SMOOTH_MOD;
+  if (smooth && (!(p->a_vap > 0) || !(p->alpha > 0.0))) return PPLBM_ERR_ARG;
+  if (p->mode == PPLBM_EOS_PENG && !(p->r_theta >= 0.0 && p->r_theta <= 1.0)) return PPLBM_ERR_ARG;
   pplbm_eos_derived d;
   std::memset(&d, 0, sizeof(d));
   d.mode = p->mode;
@@ -324,7 +348,7 @@ extern "C" pplbm_status pplbm_eos_setup(const pplbm_eos_params* p, double G, ppl
   d.b = p->b;
   d.R = p->R;
   d.a_l = p->a_liq;
-  d.a_v = p->mode == PPLBM_EOS_SMOOTH ? p->a_vap : p->a_liq;
+  d.a_v = smooth ? p->a_vap : p->a_liq;
   double rho_c_l, rho_c_v;
   if (!critical_temperature(d.a_l, d.b, d.R, d.Tc_l, rho_c_l)) return PPLBM_ERR_EOS_SETUP;
   if (!critical_temperature(d.a_v, d.b, d.R, d.Tc_v, rho_c_v)) return PPLBM_ERR_EOS_SETUP;
@@ -339,6 +363,47 @@ extern "C" pplbm_status pplbm_eos_setup(const pplbm_eos_params* p, double G, ppl
     d.p_sat = d.p_sat_cs;
     d.p_max = liq.p(d.rho_max);
     d.p_min = d.p_min_cs;
+  } else if (p->mode == PPLBM_EOS_PENG) {
+    // Eq. PengEOS: cubic through (rho_v, p_sat), (rho_l, p_sat); rho_m from Eq. VaporLiqEq with
+    // eps = 0 at the Maxwell densities; theta from r_theta (Eq. PengTheta), a function of rho_m
+    d.p_sat = d.p_sat_cs;
+    d.p_max = liq.p(d.rho_max);
+    d.p_min = d.p_min_cs;
+    d.dpdrho_v = liq.dp(d.rho_v);
+    d.dpdrho_l = liq.dp(d.rho_l);
+    const double rt = p->r_theta;
+    auto with_rho_m = [&](double rm) {
+      pplbm_eos_derived t = d;
+      t.rho_m = rm;
+      t.theta = (1.0 - rt) / ((t.rho_v - rm) * (t.rho_v - t.rho_l)) * t.dpdrho_v +
+                rt / ((t.rho_l - rm) * (t.rho_l - t.rho_v)) * t.dpdrho_l;
+      return t;
+    };
+    auto resid = [&](double rm) {
+      const pplbm_eos_derived t = with_rho_m(rm);
+      const EosConst e = make_eos_const(t);
+      for (int k = 0; k <= 64; ++k)  // psi^2 must stay positive on the loop
+        if (!(eos_psi2(e, t.rho_v + (t.rho_l - t.rho_v) * k / 64.0) > 0.0)) return (double)NAN;
+      double g;
+      mech_integral(t, 0.0, &g, nullptr);
+      return g;
+    };
+    const double span = d.rho_l - d.rho_v;
+    double prev_x = d.rho_v + 1e-3 * span, prev_f = resid(prev_x), rm = NAN;
+    for (int k = 1; k <= 120 && std::isnan(rm); ++k) {
+      const double x = d.rho_v + span * (1e-3 + (1.0 - 2e-3) * k / 120.0);
+      const double fx = resid(x);
+      if (std::isfinite(prev_f) && std::isfinite(fx) && (prev_f > 0) != (fx > 0)) {
+        double root;
+        if (ridders(resid, prev_x, x, root)) rm = root;
+      }
+      prev_x = x;
+      prev_f = fx;
+    }
+    if (std::isnan(rm)) return PPLBM_ERR_EOS_SETUP;
+    const pplbm_eos_derived t = with_rho_m(rm);
+    d.rho_m = t.rho_m;
+    d.theta = t.theta;
   } else {
     // vapour branch: its own Maxwell construction (Eq. CS scales with a at fixed Tr, so its
     // coexistence densities coincide with the liquid branch's); p_sat is its Maxwell pressure
@@ -354,10 +419,19 @@ extern "C" pplbm_status pplbm_eos_setup(const pplbm_eos_params* p, double G, ppl
     const double delta1 = d.rho_max - d.rho_v;
     const double hi = d.p_sat + 0.5 * d.dpdrho_v * delta1 * (1.0 - 1e-12);
     const double lo = d.p_sat + 1e-9 * (hi - d.p_sat);
+    const bool modified = p->mode == PPLBM_EOS_SMOOTH_MOD;
     auto resid = [&](double pm) {
       pplbm_eos_derived t = d;
       t.p_max = pm;
       if (!ellipse(t.dpdrho_v, delta1, pm - t.p_sat, t.a1sq, t.b1)) return (double)NAN;
+      if (modified) {  // Sec. IV.C: Eq. VaporLiqEq with eps = 0 instead of the Maxwell rule
+        const EosConst e = make_eos_const(t);
+        for (int k = 0; k <= 64; ++k)
+          if (!(eos_psi2(e, t.rho_v * std::pow(t.rho_l / t.rho_v, k / 64.0)) > 0.0)) return (double)NAN;
+        double g;
+        mech_integral(t, 0.0, &g, nullptr);
+        return g;
+      }
       return maxwell_residual(make_eos_const(t), t.p_sat);
     };
     double pm;
@@ -379,7 +453,11 @@ extern "C" pplbm_status pplbm_eos_setup(const pplbm_eos_params* p, double G, ppl
     const double r = d.rho_v * std::pow(1.2 * d.rho_l / d.rho_v, k / 2000.0);
     if (!(eos_psi2(e, r) > 0.0)) return PPLBM_ERR_EOS_SETUP;
   }
-  if (!solve_eps(d, d.eps)) return PPLBM_ERR_EOS_SETUP;
+  if (p->mode == PPLBM_EOS_PENG || p->mode == PPLBM_EOS_SMOOTH_MOD) {
+    d.eps = 0.0;  // built for the Guo scheme
+  } else if (!solve_eps(d, d.eps)) {
+    return PPLBM_ERR_EOS_SETUP;
+  }
   *out = d;
   return PPLBM_OK;
 }

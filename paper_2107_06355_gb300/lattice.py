@@ -21,9 +21,11 @@ class EOSParams:
     alpha: float = 0.834
     b: float = 4.0
     R: float = 1.0
+    r_theta: float = 0.0
 
     def c(self):
-        return L.pplbm_eos_params(self.mode, 0, self.Tr, self.a_liq, self.a_vap, self.b, self.R, self.alpha)
+        return L.pplbm_eos_params(self.mode, 0, self.Tr, self.a_liq, self.a_vap, self.b, self.R, self.alpha,
+                                  self.r_theta)
 
 
 @dataclass

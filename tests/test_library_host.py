@@ -36,6 +36,23 @@ CASES = [(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), (E.MODE_SMOOTH, 0.5, 0.363, 2.
          (E.MODE_CS, 0.5, 0.363, 0.363, 0.0), (E.MODE_CS, 0.8, 0.5, 0.5, 0.0)]
 
 
+def test_peng_and_modified_smooth_setup_match_oracle(lib):
+    for mode, Tr, al, av, alpha, rt in [(E.MODE_PENG, 0.6, 0.387, 0.387, 0.0, 0.45),
+                                        (E.MODE_PENG, 0.5, 0.363, 0.363, 0.0, 0.44),
+                                        (E.MODE_PENG, 0.7, 0.5, 0.5, 0.0, 0.122),
+                                        (E.MODE_SMOOTH_MOD, 0.6, 0.387, 2.0, 0.446, 0.0)]:
+        d = P.eos_setup(P.EOSParams(mode, Tr, al, av, alpha if alpha > 0 else 0.5, r_theta=rt))
+        o = E.make_eos(mode, Tr, al, av, alpha, r_theta=rt)
+        if mode == E.MODE_PENG:
+            assert d["rho_m"] == pytest.approx(o.rho_m, rel=1e-11)
+            assert d["theta"] == pytest.approx(o.theta, rel=1e-11)
+        else:
+            for k in ("p_max", "a1sq", "b1", "p_min", "a3sq", "b3"):
+                assert d[k] == pytest.approx(getattr(o, k), rel=1e-11), k
+        assert d["eps"] == 0.0
+        assert d["psi_l"] == pytest.approx(float(o.psi(o.rho_l)), rel=1e-12)
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "m%d_Tr%.2f_al%.3f_av%.3f_al%.3f" % c)
 def test_eos_setup_matches_oracle(lib, case):
     mode, Tr, al, av, alpha = case
