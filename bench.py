@@ -334,6 +334,40 @@ def adjoint_cost(torch, steps=400, interval=20):
             "forward_mlups": nx * ny * steps / (res[0] / 1e3) / 1e6}
 
 
+def eos_variant_throughput(torch, steps=1000):
+    """The bench workload (4 x 512^2 droplets, tau = 1) with each EOS the kernels
+    support (T_r = 0.6; the two Guo-forced EOS at 0.7), batched graph plan: MLUPS per EOS."""
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    variants = {
+        "cs_a0.387_li": (P.EOSParams(P.EOS_CS, 0.6, 0.387, 0.387, 0.5), P.Relax()),
+        "smooth_alpha0.834_li": (P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax()),
+        # Peng + Guo droplets diverge below T_r ~ 0.65 (the paper's minimum for that method)
+        "peng_r0.45_Tr0.7_guo": (P.EOSParams(P.EOS_PENG, 0.7, 0.387, 0.387, 0.5, r_theta=0.45),
+                                 P.Relax(forcing=P.FORCING_GUO)),
+        # Modified Smooth + Guo droplets also diverge at T_r = 0.6 (the oracle agrees); 0.7 is stable
+        "modsmooth_alpha0.446_Tr0.7_guo": (P.EOSParams(P.EOS_SMOOTH_MOD, 0.7, 0.387, 2.0, 0.446),
+                                           P.Relax(forcing=P.FORCING_GUO)),
+    }
+    out = {}
+    for name, (eos, relax) in variants.items():
+        b = P.Batch([(NX, NY, P.BC_PERIODIC)] * 4, [eos] * 4, [relax] * 4)
+        d = b.derived(0)
+        for k, R in enumerate(RADII):
+            b.init_equilibrium(k, I.droplet(NX, NY, R, d["rho_v"], d["rho_l"], W=8.0))
+        b.set_plan(P.PLAN_GRAPH, 0)
+        b.step(20)
+        ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
+        try:
+            b.sync()
+            out[name] = 4 * NX * NY * steps / (ms / 1e3) / 1e6
+        except P.PPLBMError as e:
+            out[name] = f"diverged ({e})"
+        b.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,6 +533,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_sweep:
         line["batch_sweep"] = sweep_comparison(torch, stream, 100)
         line["adjoint"] = adjoint_cost(torch)
+        line["eos_variants_mlups"] = eos_variant_throughput(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle_sample()
     if rank == 0:

@@ -238,6 +238,29 @@ pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* eos, double c[PPL
 pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* params, double G, const pplbm_relax* relax,
                                             int32_t which, double h, double dc[PPLBM_NGRAD]);
 
+/* ---- Finite-difference solver of the same macroscopic equations (App. A) ----
+ * The MacCormack scheme the paper uses as its reference for dynamics: predictor
+ * with forward, corrector with backward first differences; central second
+ * differences and central differences for every derivative of psi (Eqs.
+ * FDmomentum, FDstressTensor, FDviscosityDerivative, FDforce). Periodic grids
+ * only (App. B's wall conditions are not provided). State: rho, u_x, u_y planes
+ * (x fastest); grid spacing dx in lattice units; eps is the EOS set-up's. */
+typedef struct pplbm_fd pplbm_fd;
+/* Caller-owned device workspace: 8 planes (state, predictor state, psi, p). */
+size_t pplbm_fd_workspace_bytes(const pplbm_lattice* lattice);
+/* lattice->bc must be PPLBM_BC_PERIODIC_X | PPLBM_BC_PERIODIC_Y; tau_nu > 1/2 and
+ * tau_e > 0 give mu = rho (tau_nu - 1/2)/3 and mu_B = rho (tau_e - tau_nu)/3. */
+pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos, double G,
+                             double tau_nu, double tau_e, double dx, void* workspace, size_t workspace_bytes,
+                             void* stream);
+/* Copies the state in / out (device or host pointers; NULL skips an output). Synchronous. */
+pplbm_status pplbm_fd_set_state(pplbm_fd* fd, const double* rho, const double* ux, const double* uy);
+pplbm_status pplbm_fd_get_state(pplbm_fd* fd, double* rho, double* ux, double* uy);
+/* nsteps MacCormack steps of size dt (the paper uses dt = 0.8 dx^2 for v_r = 1). Asynchronous. */
+pplbm_status pplbm_fd_step(pplbm_fd* fd, int64_t nsteps, double dt);
+pplbm_status pplbm_fd_sync(pplbm_fd* fd);
+void pplbm_fd_destroy(pplbm_fd* fd);
+
 /* ---- Batched engine: many independent lattices advanced together ----------
  * The instances may differ in size, boundary flags, EOS parameters (e.g. a sweep
  * of reduced temperatures) and relaxation times, but must share one collision

@@ -11,4 +11,5 @@ from ._lib import (BC_PERIODIC, BC_PERIODIC_X, BC_PERIODIC_Y, BC_WALL_BOTTOM, BC
                    lib)
 from ._lib import PLAN_GRAPH, PLAN_LAUNCHES, PLAN_PERSISTENT  # noqa: F401
 from .batch import Batch  # noqa: F401
+from .fd import FDSolver  # noqa: F401
 from .lattice import EOSParams, Relax, Simulation, eos_setup  # noqa: F401

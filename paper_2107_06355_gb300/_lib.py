@@ -133,6 +133,14 @@ _SIGS = {
     "pplbm_eos_grad_constants": (C.c_int, [C.POINTER(pplbm_eos_derived), _D]),
     "pplbm_eos_constant_sensitivity": (C.c_int, [C.POINTER(pplbm_eos_params), C.c_double, C.POINTER(pplbm_relax),
                                                  C.c_int32, C.c_double, _D]),
+    "pplbm_fd_workspace_bytes": (C.c_size_t, [C.POINTER(pplbm_lattice)]),
+    "pplbm_fd_create": (C.c_int, [C.POINTER(_P), C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params), C.c_double,
+                                  C.c_double, C.c_double, C.c_double, _P, C.c_size_t, _P]),
+    "pplbm_fd_set_state": (C.c_int, [_P, _P, _P, _P]),
+    "pplbm_fd_get_state": (C.c_int, [_P, _P, _P, _P]),
+    "pplbm_fd_step": (C.c_int, [_P, C.c_int64, C.c_double]),
+    "pplbm_fd_sync": (C.c_int, [_P]),
+    "pplbm_fd_destroy": (None, [_P]),
     "pplbm_last_error": (C.c_char_p, [_P]),
     "pplbm_status_string": (C.c_char_p, [C.c_int]),
     "pplbm_destroy": (None, [_P]),
