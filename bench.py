@@ -368,6 +368,30 @@ def eos_variant_throughput(torch, steps=1000):
     return out
 
 
+def fd_throughput(torch, steps=200):
+    """The finite-difference solver (App. A) on a 2048 x 1024 periodic droplet grid
+    (dx = 1, Smooth C-S at T_r = 0.6): grid-point updates per second. dt = 0.4: with
+    the paper's 0.8 dx^2 the static droplet diverges in this scheme (CPU oracle too)."""
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    nx, ny = 2048, 1024
+    eos = P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA)
+    d = P.eos_setup(eos)
+    fd = P.FDSolver(nx, ny, eos, dx=1.0)
+    rho = I.droplet(nx, ny, 100, d["rho_v"], d["rho_l"], W=8.0)
+    z = torch.zeros((ny, nx), dtype=torch.float64)
+    fd.set_state(rho, z, z)
+    fd.step(5, 0.4)
+    ms = time_device(torch, torch.cuda.current_stream(), lambda: fd.step(steps, 0.4))
+    fd.sync()
+    r = fd.get_state()[0]
+    ok = bool(torch.isfinite(r).all())
+    fd.close()
+    return {"grid": f"{nx}x{ny}, dx=1, dt=0.4", "mlups": nx * ny * steps / (ms / 1e3) / 1e6,
+            "ms_per_step": ms / steps, "finite": ok, "launches_per_step": 4}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,6 +558,7 @@ def main():
         line["batch_sweep"] = sweep_comparison(torch, stream, 100)
         line["adjoint"] = adjoint_cost(torch)
         line["eos_variants_mlups"] = eos_variant_throughput(torch)
+        line["fd_solver"] = fd_throughput(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle_sample()
     if rank == 0:
