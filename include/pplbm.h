@@ -328,6 +328,15 @@ pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps);
  * up before the collision pass, so the distributions are not touched; the error
  * word is cleared and the batch stays usable. Synchronises. */
 pplbm_status pplbm_batch_barrier_selftest(pplbm_batch* b, uint32_t spin_limit);
+/* Divergence isolation for sweeps: with on != 0, an instance whose kernels meet a
+ * non-finite or non-positive density (or psi^2 <= 0) is marked diverged but does
+ * not make the batch's status sticky, so the other instances keep stepping (a
+ * diverged instance keeps computing on its non-finite state, touching nothing
+ * else). Off by default: any divergence stops the batch. */
+pplbm_status pplbm_batch_set_isolation(pplbm_batch* b, int32_t on);
+/* Synchronises and writes, per instance, PPLBM_OK or PPLBM_ERR_DIVERGED into
+ * status[n] (host); returns the batch status. */
+pplbm_status pplbm_batch_instance_status(pplbm_batch* b, int32_t* status);
 const char* pplbm_batch_last_error(const pplbm_batch* b);
 void pplbm_batch_destroy(pplbm_batch* b);
 

@@ -20,7 +20,7 @@ Contents (each function cites the passage it follows):
   method from epsilon = 2 with Simpson's rule, and sigma = -epsilon/(16 G)
   (Sec. II.C, below Eq. NewPressureTensor; Sec. III.A).
 
-Readings of passages that are silent or garbled (all listed in the design doc):
+Readings of passages that are silent or garbled:
 
 * T_c is the exact critical point of Eq. CS, not the rounded 0.3773 a/(R b).
 * Region 2's cubic is evaluated in the normalised variable

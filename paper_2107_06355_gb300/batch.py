@@ -114,6 +114,16 @@ class Batch:
         self._check(L.lib().pplbm_batch_times(self.b, C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
+    def set_isolation(self, on=True):
+        """Let diverged instances be reported individually instead of stopping the batch."""
+        self._check(L.lib().pplbm_batch_set_isolation(self.b, 1 if on else 0))
+
+    def instance_status(self):
+        """Per-instance status (0 ok, 4 diverged); synchronises."""
+        st = (C.c_int32 * self.n)()
+        self._check(L.lib().pplbm_batch_instance_status(self.b, st))
+        return list(st)
+
     def barrier_selftest(self, spin_limit=1 << 14):
         """Status of the bounded-barrier self-test (expected: PPLBM_ERR_TIMEOUT = 5)."""
         return L.lib().pplbm_batch_barrier_selftest(self.b, int(spin_limit))

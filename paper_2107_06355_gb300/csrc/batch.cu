@@ -250,7 +250,10 @@ struct pplbm_batch {
   int* d_owner2;
   int n1, n2;
   GridBarrier* d_bar;
-  int* d_err;
+  int* d_err;                       // batch-wide word (grid-barrier timeout)
+  int* d_ierr;                      // one word per instance (divergence)
+  bool isolate;                     // diverged instances do not stop the batch
+  std::vector<int> diverged;
   int persistent_grid;
   pplbm_batch_plan plan;
   cudaGraphExec_t graph[2];  // graph[p]: two steps starting from parity p
@@ -364,15 +367,25 @@ pplbm_status apply_plan(pplbm_batch* b, int mode, int tile_width) {
 
 pplbm_status poll(pplbm_batch* b) {
   int h = 0;
+  std::vector<int> hi(b->n, 0);
   BTRY(b, cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BTRY(b, cudaMemcpyAsync(hi.data(), b->d_ierr, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream));
   BTRY(b, cudaStreamSynchronize(b->stream));
-  if (h != 0 && b->sticky == PPLBM_OK) {
+  int first = -1;
+  for (int i = 0; i < b->n; ++i)
+    if (hi[i]) {
+      b->diverged[i] = 1;
+      if (first < 0) first = i;
+    }
+  if (b->sticky == PPLBM_OK) {
     if (h & kErrTimeout) {
       b->sticky = PPLBM_ERR_TIMEOUT;
       b->msg = "a grid-barrier wait of the persistent kernel gave up";
-    } else {
+    } else if (first >= 0 && !b->isolate) {
       b->sticky = PPLBM_ERR_DIVERGED;
-      b->msg = "a kernel met a non-finite or non-positive density, or psi^2 <= 0";
+      char buf[160];
+      snprintf(buf, sizeof(buf), "instance %d met a non-finite or non-positive density, or psi^2 <= 0", first);
+      b->msg = buf;
     }
   }
   return b->sticky;
@@ -467,7 +480,8 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   const size_t inst_bytes = ((sizeof(BatchInst) * n + 255) / 256) * 256;
   const size_t o1_bytes = ((sizeof(int) * max1 + 255) / 256) * 256;
   const size_t o2_bytes = ((sizeof(int) * max2 + 255) / 256) * 256;
-  const size_t block = inst_bytes + o1_bytes + o2_bytes + 256 + 256;
+  const size_t ierr_bytes = ((sizeof(int) * n + 255) / 256) * 256;
+  const size_t block = inst_bytes + o1_bytes + o2_bytes + 256 + 256 + ierr_bytes;
   if (cudaMalloc(&b->dev_block, block) != cudaSuccess) {
     delete b;
     return PPLBM_ERR_CUDA;
@@ -478,12 +492,15 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   b->d_owner2 = (int*)(p + inst_bytes + o1_bytes);
   b->d_bar = (GridBarrier*)(p + inst_bytes + o1_bytes + o2_bytes);
   b->d_err = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 256);
+  b->d_ierr = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 512);
+  b->diverged.assign(n, 0);
   if (cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(b->dev_block);
     delete b;
     return PPLBM_ERR_CUDA;
   }
   cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  cudaMemsetAsync(b->d_ierr, 0, sizeof(int) * n, b->stream);
   double* w = (double*)workspace;
   for (int i = 0; i < n; ++i) {
     const pplbm_lattice& L = lattices[i];
@@ -494,7 +511,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
     std::memset(&a, 0, sizeof(a));
     a.psi = w + 18 * nn;
     a.mom = w + 19 * nn;
-    a.err = b->d_err;
+    a.err = b->d_ierr + i;
     a.nx = L.nx;
     a.ny = L.ny;
     a.n = nn;
@@ -768,6 +785,19 @@ pplbm_status pplbm_batch_barrier_selftest(pplbm_batch* b, uint32_t spin_limit) {
   BTRY(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
   BTRY(b, cudaStreamSynchronize(b->stream));
   return (h & kErrTimeout) ? PPLBM_ERR_TIMEOUT : PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_set_isolation(pplbm_batch* b, int32_t on) {
+  if (!b) return PPLBM_ERR_ARG;
+  b->isolate = on != 0;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_instance_status(pplbm_batch* b, int32_t* status) {
+  if (!b || !status) return PPLBM_ERR_ARG;
+  const pplbm_status s = poll(b);
+  for (int i = 0; i < b->n; ++i) status[i] = b->diverged[i] ? PPLBM_ERR_DIVERGED : PPLBM_OK;
+  return s;
 }
 
 const char* pplbm_batch_last_error(const pplbm_batch* b) { return b ? b->msg.c_str() : ""; }

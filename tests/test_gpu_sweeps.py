@@ -1,0 +1,106 @@
+"""Paper-level reproduction on the GPU: the planar-interface sweeps of Sec. III,
+run as one batch of (2, 200) lattices to the convergence criterion of Sec. III.A
+(paper_2107_06355_gb300.sweeps), checked against the statements the paper makes
+about them (golden/paper_values.json, "coexistence_statements")."""
+import json
+import os
+
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+P = pytest.importorskip("paper_2107_06355_gb300")
+from paper_2107_06355_gb300.sweeps import planar_coexistence  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+S = GOLD["coexistence_statements"]
+TABLE = GOLD["table_drop_impact_parameters"]["cases"]
+PM = GOLD["peng_and_modified_smooth"]["cases"]
+MODES = {"CS": P.EOS_CS, "SMOOTH": P.EOS_SMOOTH, "PENG": P.EOS_PENG, "SMOOTH_MOD": P.EOS_SMOOTH_MOD}
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    cases, keys = [], []
+
+    def add(key, eos, forcing=P.FORCING_LI):
+        cases.append((eos, P.Relax(forcing=forcing)))
+        keys.append(key)
+
+    for Tr in (0.9, 0.8, 0.75, 0.7, 0.5):
+        add(("li", Tr), P.EOSParams(P.EOS_CS, Tr, 0.5, 0.5, 0.5))
+    for Tr in (0.9, 0.8, 0.75, 0.7):
+        add(("guo", Tr), P.EOSParams(P.EOS_CS, Tr, 0.5, 0.5, 0.5), P.FORCING_GUO)
+    for a in S["standard"]["a"]:
+        add(("std", a), P.EOSParams(P.EOS_CS, 0.5, a, a, 0.5))
+    for al in S["smooth"]["alpha"]:
+        add(("smooth", al), P.EOSParams(P.EOS_SMOOTH, 0.5, 0.5, 0.5, al))
+    for al in S["smooth_av2"]["alpha"]:
+        add(("av2", al), P.EOSParams(P.EOS_SMOOTH, 0.5, 0.5, 2.0, al))
+    for c in TABLE:
+        add(("table", c["name"]), P.EOSParams(MODES[c["mode"]], c["Tr"], c["a_l"], c["a_v"],
+                                              c["alpha"] if c["alpha"] > 0 else 0.5))
+    for c in PM:
+        add(("table", c["name"]), P.EOSParams(MODES[c["mode"]], c["Tr"], c["a_l"], c["a_v"],
+                                              c["alpha"] if c["alpha"] > 0 else 0.5, r_theta=c["r_theta"]),
+            P.FORCING_GUO)
+    return dict(zip(keys, planar_coexistence(cases)))
+
+
+def test_li_forcing_with_cs(sweep):
+    for Tr in (0.9, 0.8, 0.75, 0.7):
+        r = sweep[("li", Tr)]
+        assert r["converged"] and abs(r["E_percent"]) < S["li_cs_small_percent"], (Tr, r)
+    lo, hi = S["li_cs_Tr05_percent"]
+    assert lo < sweep[("li", 0.5)]["E_percent"] < hi
+
+
+def test_guo_forcing_with_cs_unstable_below_08(sweep):
+    for Tr in (0.9, 0.8):
+        r = sweep[("guo", Tr)]
+        assert r["converged"] and not r["diverged"]
+        assert abs(r["E_percent"]) > abs(sweep[("li", Tr)]["E_percent"])   # Guo deviates much more
+    for Tr in (0.75, 0.7):
+        assert sweep[("guo", Tr)]["diverged"]
+
+
+def test_standard_procedure_widths_and_errors(sweep):
+    for a, w in zip(S["standard"]["a"], S["standard"]["w"]):
+        assert sweep[("std", a)]["width"] == w
+    lo, hi = S["standard"]["E_a0.363_percent"]
+    assert lo < sweep[("std", 0.363)]["E_percent"] < hi
+    lo, hi = S["standard"]["E_a0.141_percent"]
+    assert lo < sweep[("std", 0.141)]["E_percent"] < hi
+
+
+def test_smooth_widths_and_smaller_errors(sweep):
+    for (al, w), a in zip(zip(S["smooth"]["alpha"], S["smooth"]["w"]), S["standard"]["a"]):
+        r = sweep[("smooth", al)]
+        assert r["width"] == w
+        assert abs(r["E_percent"]) < abs(sweep[("std", a)]["E_percent"])   # same width, smaller error
+
+
+def test_smooth_with_vapour_sound_speed(sweep):
+    for al, w in zip(S["smooth_av2"]["alpha"], S["smooth_av2"]["w"]):
+        assert sweep[("av2", al)]["width"] == w
+    lo, hi = S["smooth_av2"]["E_w7_percent"]
+    assert lo < sweep[("av2", 0.554)]["E_percent"] < hi
+    assert abs(sweep[("av2", 0.207)]["E_percent"]) < S["smooth_av2"]["E_w11_max_percent"]
+    # a stiffer vapour branch lowers the error at every width
+    for a_s, a_v in zip(S["smooth"]["alpha"], S["smooth_av2"]["alpha"]):
+        assert abs(sweep[("av2", a_v)]["E_percent"]) < abs(sweep[("smooth", a_s)]["E_percent"])
+
+
+@pytest.mark.parametrize("case", TABLE + PM, ids=[c["name"] for c in TABLE + PM])
+def test_table_drop_impact_parameters(sweep, case):
+    """Table DropImpactParameters (and the Modified Smooth row of Sec. IV.C) from the
+    batched engine, at the tolerances the oracle's own reproduction uses."""
+    r = sweep[("table", case["name"])]
+    assert r["converged"]
+    if case["mode"] == "PENG":
+        assert abs(r["E_percent"] - case["E_percent"]) < 0.002
+    elif case["E_percent"] is not None:
+        assert r["E_percent"] == pytest.approx(case["E_percent"], rel=0.01)
+    assert r["width"] == case["w"]
+    rel = 0.03 if case in PM else 0.06
+    assert r["gamma"] * 1e3 == pytest.approx(case["gamma_e3"], rel=rel)

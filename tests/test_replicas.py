@@ -61,3 +61,4 @@ def test_two_rank_gloo_shards_and_max_reduction(tmp_path):
     assert sum(locals_) == float(sum(sizes))
     for l in lines:
         assert l[2].strip() == str(list(range(len(sizes))))
+
