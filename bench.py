@@ -41,6 +41,34 @@ E2E_INNER = 100  # LBM steps per end-to-end call
 FP64_OPS_PER_NODE = {"rho_psi": 33, "collide": 51}
 BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
+# batched pass on this workload, averaged over three launches of an ncu capture of
+# `bench.py --profile-batch` (profiles/k_batch_collide_k_batch_rho_psi_droplets512.md).
+# They hold for the kernel sources whose digest is recorded with them; once those
+# sources change, traffic is reported as null until the capture is repeated.
+TRAFFIC = {"sources": "3caf2a342cf98ce0", "rho_psi": 75540565 + 2426624, "collide": 33615104 + 13665109}
+KERNEL_SOURCES = ("batch.cu", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
+
+
+def kernel_sources_digest():
+    """sha256 (first 16 hex digits) over the sources the batched step kernels are
+    compiled from, in a fixed order, each preceded by its file name."""
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_2107_06355_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def step_traffic():
+    if TRAFFIC["sources"] is None or TRAFFIC["sources"] != kernel_sources_digest():
+        return None
+    return TRAFFIC["rho_psi"] + TRAFFIC["collide"]
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -368,6 +396,42 @@ def eos_variant_throughput(torch, steps=1000):
     return out
 
 
+def impact_sweep_throughput(torch, steps=2000):
+    """A slice of the stability study (Sec. IV.D) on the batched engine: droplet
+    impact at Re = 300 on (600, 250) lattices with walls, C-S a = 0.363, Li forcing,
+    two-phase tau(rho), T_r in {0.45, ..., 0.75} x v_r in {2, ..., 10}: 35 instances,
+    5.25 M nodes, graph plan with divergence isolation. Every run is stable here, so
+    all nodes count."""
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import sweeps as SW
+
+    # initial interface widths: the planar C-S (a = 0.363) widths at each T_r
+    width = {0.45: 6.0, 0.50: 7.0, 0.55: 7.0, 0.60: 9.0, 0.65: 9.0, 0.70: 10.0, 0.75: 11.0}
+    Trs = sorted(width)
+    vrs = [2, 4, 6, 8, 10]
+    lats, eoss, relaxes, Ws = [], [], [], []
+    for Tr in Trs:
+        for vr in vrs:
+            lats.append((600, 250, P.BC_WALLS_Y))
+            eoss.append(P.EOSParams(P.EOS_CS, Tr, 0.363, 0.363, 0.5))
+            relaxes.append(P.Relax(kind=P.RELAX_TWO_PHASE, tau_l=0.6, visc_ratio=float(vr)))
+            Ws.append(width[Tr])
+    b = P.Batch(lats, eoss, relaxes)
+    b.set_isolation(True)
+    for i in range(len(lats)):
+        d = b.derived(i)
+        b.init_equilibrium(i, *SW._impact_profile(600, 250, 50, 25, d["rho_v"], d["rho_l"], 0.1, Ws[i]))
+    b.set_plan(P.PLAN_GRAPH, 0)
+    b.step(20)
+    ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
+    g = b.guard()
+    stable = int(((np.asarray(b.instance_status()) == 0) & (g[:, 2] == 0)).sum())
+    b.close()
+    nodes = 600 * 250 * len(lats)
+    return {"instances": len(lats), "stable": stable, "nodes": nodes, "steps": steps,
+            "mlups": nodes * steps / (ms / 1e3) / 1e6 if stable == len(lats) else None}
+
+
 def fd_throughput(torch, steps=200):
     """The finite-difference solver (App. A) on a 2048 x 1024 periodic droplet grid
     (dx = 1, Smooth C-S at T_r = 0.6): grid-point updates per second. dt = 0.4: with
@@ -536,7 +600,8 @@ def main():
                    "parallelism": f"replicas{ws}", "l2": "state > L2 (about 180 MB per step), no flush"},
         "roofline": {"bound": "alu", "kernel": f"batched step: density/psi + collision passes ({mode})",
                      "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": None,
+                     "frac": achieved / fp64_peak, "traffic": step_traffic(),
+                     "traffic_unit": "DRAM bytes per step (both passes; ncu, same kernel sources)",
                      "flop_convention": "1 per FP64 add/mul/fma instruction; 84 per node update",
                      "peak_source": f"2 FP64 instr/clk/SM x 152 SMs x {sm_max:.0f} MHz",
                      "launch_ms": step_s * 1e3},
@@ -559,6 +624,7 @@ def main():
         line["adjoint"] = adjoint_cost(torch)
         line["eos_variants_mlups"] = eos_variant_throughput(torch)
         line["fd_solver"] = fd_throughput(torch)
+        line["impact_sweep"] = impact_sweep_throughput(torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle_sample()
     if rank == 0:

@@ -286,7 +286,9 @@ typedef struct pplbm_batch_plan {
   double ms_chosen;
 } pplbm_batch_plan;
 
-/* Workspace bytes for n instances (each instance's block is 256-byte aligned);
+/* Workspace bytes for n instances: per instance two f buffers, psi, the moment
+ * planes of the collision kind and a density snapshot for pplbm_batch_guard
+ * (each instance's block is 256-byte aligned);
  * 0 if any lattice or relaxation set is invalid or the collision kinds differ. */
 size_t pplbm_batch_workspace_bytes(int32_t n, const pplbm_lattice* lattices, const pplbm_relax* relax);
 
@@ -337,6 +339,20 @@ pplbm_status pplbm_batch_set_isolation(pplbm_batch* b, int32_t on);
 /* Synchronises and writes, per instance, PPLBM_OK or PPLBM_ERR_DIVERGED into
  * status[n] (host); returns the batch status. */
 pplbm_status pplbm_batch_instance_status(pplbm_batch* b, int32_t* status);
+/* Per-instance guard (Sec. III.A convergence check, mass and the stability test of
+ * the dynamic runs, Sec. IV). First runs the density/psi pass over every
+ * instance's current state (as the next step would), then writes to the host
+ * array out[4 n], for instance i, out[4i] = mass sum(rho), out[4i+1] = max |u|
+ * with u = (j + F/2)/rho the fluid velocity (Eq. Momentum; F the Shan-Chen force
+ * of the collision pass), out[4i+2] = number of nodes with a non-finite or
+ * non-positive density (excluded from the other three; such a node also marks
+ * the instance diverged, as a step would), and
+ * out[4i+3] = sum |rho - rho'| / sum rho, where rho' is the density at the
+ * previous pplbm_batch_guard call, or -1 on the first call for the instance and
+ * after its pplbm_batch_init_equilibrium / pplbm_batch_set_f. rho' lives in the
+ * instance's workspace block. Deterministic (fixed-order) reduction; runs in the
+ * batch's stream and synchronises it. Returns the batch status. */
+pplbm_status pplbm_batch_guard(pplbm_batch* b, double* out);
 const char* pplbm_batch_last_error(const pplbm_batch* b);
 void pplbm_batch_destroy(pplbm_batch* b);
 

@@ -124,6 +124,15 @@ class Batch:
         self._check(L.lib().pplbm_batch_instance_status(self.b, st))
         return list(st)
 
+    def guard(self):
+        """(n, 4) array per instance: mass, max |j|/rho, bad-node count, residual
+        against the previous guard call (-1 when there is none); synchronises."""
+        import numpy as np
+
+        out = np.empty(4 * self.n, dtype=np.float64)
+        self._check(L.lib().pplbm_batch_guard(self.b, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(self.n, 4)
+
     def barrier_selftest(self, spin_limit=1 << 14):
         """Status of the bounded-barrier self-test (expected: PPLBM_ERR_TIMEOUT = 5)."""
         return L.lib().pplbm_batch_barrier_selftest(self.b, int(spin_limit))

@@ -42,6 +42,7 @@ constexpr int kErrTimeout = 2;
 
 struct BatchInst {
   StepArgs a[2];  // a[p] reads f from buffer p and writes buffer 1 - p
+  double* snap;   // density at the previous guard call (one plane)
   int tw, th, log2tw, tiles_x;
   int k1_start, k2_start;
 };
@@ -149,6 +150,99 @@ __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* 
   }
 }
 
+// Guard, pass 1: one block per 256-node work item of the density pass; per block
+// (mass, max |u|, bad count, sum |rho - rho'|), reduced in a fixed tree order.
+// Runs after a density pass over the current state, so rho, j and psi are those
+// the next step starts from; u = (j + F/2)/rho is the fluid velocity of Eq.
+// Momentum, with the Shan-Chen force evaluated as in the collision pass (same
+// stencil, periodic wrap, wall ghost values). Refreshes the snapshot rho'.
+constexpr int kGuardQ = 4;
+
+__device__ __forceinline__ void block_reduce4(double v[kGuardQ], double (*s)[kThreads]) {
+  for (int q = 0; q < kGuardQ; ++q) s[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + w];
+      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
+      s[2][threadIdx.x] += s[2][threadIdx.x + w];
+      s[3][threadIdx.x] += s[3][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+}
+
+// psi at (x + dx, y + dy) for 0 <= x < nx, 0 <= y < ny, |dx|, |dy| <= 1
+__device__ __forceinline__ double psi_near(const StepArgs& a, int x, int y, int dx, int dy) {
+  const int gx = wrap_index(x + dx, a.nx);
+  int gy = y + dy;
+  if (a.walls) {
+    if (gy < 0) return a.psi_ghost_bottom;
+    if (gy >= a.ny) return a.psi_ghost_top;
+  } else {
+    gy = wrap_index(gy, a.ny);
+  }
+  return a.psi[(int64_t)gy * a.nx + gx];
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch_guard_partial(const BatchInst* inst, const int* owner, int parity,
+                                                                  const int* snap_valid, double* partials) {
+  __shared__ double s[kGuardQ][kThreads];
+  const int w = blockIdx.x;
+  const int id = owner[w];
+  const BatchInst& I = inst[id];
+  const StepArgs& a = I.a[parity];
+  const int64_t n = a.n;
+  const int64_t i = (int64_t)(w - I.k1_start) * kThreads + threadIdx.x;
+  double v[kGuardQ] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    const double rho = a.mom[i];
+    if (!(rho > 0.0 && rho < 1e300)) {
+      v[2] = 1.0;
+    } else {
+      const int y = (int)(i / a.nx), x = (int)(i - (int64_t)y * a.nx);
+      const double pE = psi_near(a, x, y, 1, 0), pW = psi_near(a, x, y, -1, 0);
+      const double pN = psi_near(a, x, y, 0, 1), pS = psi_near(a, x, y, 0, -1);
+      const double d1 = psi_near(a, x, y, 1, 1) - psi_near(a, x, y, -1, -1);
+      const double d2 = psi_near(a, x, y, 1, -1) - psi_near(a, x, y, -1, 1);
+      const double gx = 4.0 * (pE - pW) + (d1 + d2), gy = 4.0 * (pN - pS) + (d1 - d2);
+      const double cH = a.half_force * a.psi[i];
+      const double ux = (a.mom[n + i] + cH * gx) / rho, uy = (a.mom[2 * n + i] + cH * gy) / rho;
+      v[0] = rho;
+      v[1] = sqrt(ux * ux + uy * uy);
+      if (snap_valid[id]) v[3] = fabs(rho - I.snap[i]);
+    }
+    I.snap[i] = rho;
+  }
+  block_reduce4(v, s);
+  if (threadIdx.x < kGuardQ) partials[kGuardQ * (int64_t)w + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Guard, pass 2: one block per instance over its work items, in a fixed order.
+__global__ void __launch_bounds__(kThreads) k_batch_guard_final(const BatchInst* inst, const double* partials,
+                                                                int* snap_valid, double* out) {
+  __shared__ double s[kGuardQ][kThreads];
+  const int id = blockIdx.x;
+  const BatchInst& I = inst[id];
+  const int nb = (int)((I.a[0].n + kThreads - 1) / kThreads);
+  double v[kGuardQ] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < nb; k += kThreads) {
+    const double* p = partials + kGuardQ * (int64_t)(I.k1_start + k);
+    v[0] += p[0];
+    v[1] = fmax(v[1], p[1]);
+    v[2] += p[2];
+    v[3] += p[3];
+  }
+  block_reduce4(v, s);
+  if (threadIdx.x == 0) {
+    out[kGuardQ * id + 0] = s[0][0];
+    out[kGuardQ * id + 1] = s[1][0];
+    out[kGuardQ * id + 2] = s[2][0];
+    out[kGuardQ * id + 3] = snap_valid[id] ? s[3][0] / s[0][0] : -1.0;
+    snap_valid[id] = 1;
+  }
+}
+
 const void* persistent_kernel(int kind) {
   switch (kind) {
     case kUnitTau: return (const void*)k_batch_persistent<kUnitTau>;
@@ -172,6 +266,15 @@ void launch_pair(int kind, const BatchInst* inst, const int* o1, int n1, const i
       k_batch_rho_psi<kFullMrt><<<n1, kThreads, 0, s>>>(inst, o1, parity);
       k_batch_collide<kFullMrt><<<n2, kThreads, 0, s>>>(inst, o2, parity);
       break;
+  }
+}
+
+// the density/psi pass alone, over every instance (refreshes psi and the moments)
+void launch_density_pass(int kind, const BatchInst* inst, const int* o1, int n1, int parity, cudaStream_t s) {
+  switch (kind) {
+    case kUnitTau: k_batch_rho_psi<kUnitTau><<<n1, kThreads, 0, s>>>(inst, o1, parity); break;
+    case kShearTau: k_batch_rho_psi<kShearTau><<<n1, kThreads, 0, s>>>(inst, o1, parity); break;
+    default: k_batch_rho_psi<kFullMrt><<<n1, kThreads, 0, s>>>(inst, o1, parity); break;
   }
 }
 
@@ -206,7 +309,7 @@ bool lattice_ok(const pplbm_lattice* l) {
 
 size_t inst_doubles(const pplbm_lattice& l, int kind) {
   const size_t n = (size_t)l.nx * l.ny;
-  const size_t d = n * (19 + (size_t)moment_planes(kind));
+  const size_t d = n * (20 + (size_t)moment_planes(kind));  // f x 2, psi, moments, guard snapshot
   return (d + 31) & ~(size_t)31;  // 256-byte aligned instances
 }
 
@@ -252,6 +355,9 @@ struct pplbm_batch {
   GridBarrier* d_bar;
   int* d_err;                       // batch-wide word (grid-barrier timeout)
   int* d_ierr;                      // one word per instance (divergence)
+  int* d_snap_valid;                // one word per instance: guard snapshot holds a density
+  double* d_gpart;                  // guard partials, 4 per density-pass work item
+  double* d_gout;                   // guard output, 4 per instance
   bool isolate;                     // diverged instances do not stop the batch
   std::vector<int> diverged;
   int persistent_grid;
@@ -481,7 +587,9 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   const size_t o1_bytes = ((sizeof(int) * max1 + 255) / 256) * 256;
   const size_t o2_bytes = ((sizeof(int) * max2 + 255) / 256) * 256;
   const size_t ierr_bytes = ((sizeof(int) * n + 255) / 256) * 256;
-  const size_t block = inst_bytes + o1_bytes + o2_bytes + 256 + 256 + ierr_bytes;
+  const size_t gpart_bytes = ((sizeof(double) * kGuardQ * max1 + 255) / 256) * 256;
+  const size_t gout_bytes = ((sizeof(double) * kGuardQ * n + 255) / 256) * 256;
+  const size_t block = inst_bytes + o1_bytes + o2_bytes + 256 + 256 + 2 * ierr_bytes + gpart_bytes + gout_bytes;
   if (cudaMalloc(&b->dev_block, block) != cudaSuccess) {
     delete b;
     return PPLBM_ERR_CUDA;
@@ -493,6 +601,9 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   b->d_bar = (GridBarrier*)(p + inst_bytes + o1_bytes + o2_bytes);
   b->d_err = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 256);
   b->d_ierr = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 512);
+  b->d_snap_valid = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + ierr_bytes);
+  b->d_gpart = (double*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes);
+  b->d_gout = (double*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes);
   b->diverged.assign(n, 0);
   if (cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(b->dev_block);
@@ -501,6 +612,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   }
   cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   cudaMemsetAsync(b->d_ierr, 0, sizeof(int) * n, b->stream);
+  cudaMemsetAsync(b->d_snap_valid, 0, sizeof(int) * n, b->stream);
   double* w = (double*)workspace;
   for (int i = 0; i < n; ++i) {
     const pplbm_lattice& L = lattices[i];
@@ -543,6 +655,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
     b->bufA[i] = w;
     b->bufB[i] = w + 9 * nn;
     BatchInst& I = b->host_inst[i];
+    I.snap = w + (19 + moment_planes(b->kind)) * nn;
     I.a[0] = a;
     I.a[0].f_in = b->bufA[i];
     I.a[0].f_out = b->bufB[i];
@@ -585,6 +698,7 @@ pplbm_status pplbm_batch_init_equilibrium(pplbm_batch* b, int32_t i, const doubl
   }
   launch_init_eq(a, const_cast<double*>(a.f_in), dev[0], dev[1], dev[2], b->stream);
   BTRY(b, cudaGetLastError());
+  BTRY(b, cudaMemsetAsync(b->d_snap_valid + i, 0, sizeof(int), b->stream));
   return poll(b);
 }
 
@@ -641,6 +755,7 @@ pplbm_status pplbm_batch_set_f(pplbm_batch* b, int32_t i, const double* f) {
   if (b->sticky) return b->sticky;
   const StepArgs& a = args_of(b, i);
   BTRY(b, cudaMemcpyAsync(const_cast<double*>(a.f_in), f, sizeof(double) * 9 * a.n, cudaMemcpyDefault, b->stream));
+  BTRY(b, cudaMemsetAsync(b->d_snap_valid + i, 0, sizeof(int), b->stream));
   if (!is_dev(f)) BTRY(b, cudaStreamSynchronize(b->stream));
   return PPLBM_OK;
 }
@@ -791,6 +906,19 @@ pplbm_status pplbm_batch_set_isolation(pplbm_batch* b, int32_t on) {
   if (!b) return PPLBM_ERR_ARG;
   b->isolate = on != 0;
   return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_guard(pplbm_batch* b, double* out) {
+  if (!b || !out) return bfail(b, PPLBM_ERR_ARG, "NULL batch or output");
+  if (b->sticky) return b->sticky;
+  launch_density_pass(b->kind, b->d_inst, b->d_owner1, b->n1, b->parity, b->stream);
+  k_batch_guard_partial<<<b->n1, kThreads, 0, b->stream>>>(b->d_inst, b->d_owner1, b->parity, b->d_snap_valid,
+                                                            b->d_gpart);
+  k_batch_guard_final<<<b->n, kThreads, 0, b->stream>>>(b->d_inst, b->d_gpart, b->d_snap_valid, b->d_gout);
+  BTRY(b, cudaGetLastError());
+  BTRY(b, cudaMemcpyAsync(out, b->d_gout, sizeof(double) * kGuardQ * b->n, cudaMemcpyDefault, b->stream));
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  return poll(b);
 }
 
 pplbm_status pplbm_batch_instance_status(pplbm_batch* b, int32_t* status) {

@@ -104,3 +104,45 @@ def test_table_drop_impact_parameters(sweep, case):
     assert r["width"] == case["w"]
     rel = 0.03 if case in PM else 0.06
     assert r["gamma"] * 1e3 == pytest.approx(case["gamma_e3"], rel=rel)
+
+
+ST = GOLD["stability_statements"]
+
+
+@pytest.fixture(scope="module")
+def study():
+    from paper_2107_06355_gb300.sweeps import stability_study
+
+    # t* = steps V_d / D = 10: long enough that every run below has met its fate
+    return stability_study([0.35, 0.40, 0.60, 0.65], [4, 8], steps=10000, a_cs=ST["cs_a"])
+
+
+def test_stability_study_density_ratios(study):
+    """Simulated planar density ratios of the study's parameter sets (Sec. IV.D, V)."""
+    pl = study["planar"]
+    ratio = lambda r: r["rho_l"] / r["rho_v"]  # noqa: E731
+    assert ratio(pl["C-S"][0.35]) == pytest.approx(ST["ratio_cs_Tr035"], rel=0.02)
+    assert pl["Smooth C-S"][0.35]["ok"]
+    assert ratio(pl["Smooth C-S"][0.35]) == pytest.approx(ST["ratio_smooth_Tr035"], rel=0.03)
+    assert ratio(pl["Peng C-S"][0.65]) == pytest.approx(ST["ratio_peng_Tr065"], rel=0.02)
+    for Tr in (0.35, 0.40, 0.60, 0.65):   # tuned widths equal the C-S widths
+        assert pl["Smooth C-S"][Tr]["width_interp"] == pytest.approx(pl["C-S"][Tr]["width_interp"], abs=0.02)
+
+
+def test_stability_study_peng_range(study):
+    """Peng: no interface of the C-S width below T_r = 0.65; stable impacts at 0.65."""
+    assert set(study["tuned"]["Peng C-S"]) == {0.65}
+    for Tr in (0.35, 0.40, 0.60):
+        assert not any(study["map"][("Peng C-S", Tr, vr)]["run"] for vr in (4, 8))
+    assert study["map"][("Peng C-S", ST["peng_min_Tr"], 8)]["stable"]
+
+
+def test_stability_study_smooth_extends_range(study):
+    """The Smooth C-S is stable at a T_r where the C-S EOS of the same width is not."""
+    m = study["map"]
+    assert not any(m[("C-S", 0.40, vr)]["stable"] for vr in (4, 8))
+    assert m[("Smooth C-S", 0.40, 4)]["stable"]
+    for name in ("C-S", "Smooth C-S"):
+        for vr in (4, 8):
+            r = m[(name, 0.60, vr)]
+            assert r["stable"] and r["mass_drift"] < 1e-10   # walls and periodic x conserve mass
