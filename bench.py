@@ -46,7 +46,7 @@ BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
 # `bench.py --profile-batch` (profiles/k_batch_collide_k_batch_rho_psi_droplets512.md).
 # They hold for the kernel sources whose digest is recorded with them; once those
 # sources change, traffic is reported as null until the capture is repeated.
-TRAFFIC = {"sources": "3caf2a342cf98ce0", "rho_psi": 75540565 + 2426624, "collide": 33615104 + 13665109}
+TRAFFIC = {"sources": "8755dcebd31f9e70", "rho_psi": 75532373 + 2554965, "collide": 33625429 + 14029824}
 KERNEL_SOURCES = ("batch.cu", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
 
 

@@ -185,7 +185,9 @@ pplbm_status pplbm_set_f(pplbm_ctx* ctx, const double* f);
 pplbm_status pplbm_sync(pplbm_ctx* ctx, int64_t* steps_done);
 
 /* Per-step guard (Sec. III.A convergence check and mass): writes to host
- * out[0] = total mass sum(rho), out[1] = max |u|, out[2] = number of nodes with a
+ * out[0] = total mass sum(rho), out[1] = max |j|/rho with j = sum_i f_i c_i (the
+ * momentum before the half-force shift of Eq. Momentum; the fluid velocity is in
+ * pplbm_get_fields and pplbm_batch_guard), out[2] = number of nodes with a
  * non-finite or non-positive density. Deterministic two-pass reduction.
  * Synchronises the stream. */
 pplbm_status pplbm_guard(pplbm_ctx* ctx, double out[3]);
