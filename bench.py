@@ -40,6 +40,10 @@ E2E_INNER = 100  # LBM steps per end-to-end call
 # bulk nodes), counted from the kernels' arithmetic; ncu's FP64-pipe cycles agree.
 FP64_OPS_PER_NODE = {"rho_psi": 33, "collide": 51}
 BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
+# FP64 instructions of one MacCormack step per grid point: predictor 113, corrector
+# 119, two EOS passes of 27 (the kernels' arithmetic; ncu's sm__inst_executed_pipe_fp64
+# on the 2048 x 1024 grid, profiles/k_fd_update_k_fd_eos_2048x1024.md)
+FD_FP64_PER_POINT = 113 + 119 + 2 * 27
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
 # batched pass on this workload, averaged over three launches of an ncu capture of
@@ -222,6 +226,24 @@ def profile_batch():
     b.sync()
     torch.cuda.synchronize()
     print("profile batch done")
+
+
+def profile_fd():
+    """The finite-difference solver on the 2048 x 1024 droplet grid of fd_throughput,
+    3 steps: 3 launches of each of its two kernels per half-step pair."""
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    eos = P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA)
+    d = P.eos_setup(eos)
+    fd = P.FDSolver(2048, 1024, eos, dx=1.0)
+    rho = I.droplet(2048, 1024, 100, d["rho_v"], d["rho_l"], W=8.0)
+    fd.set_state(rho, np.zeros_like(rho), np.zeros_like(rho))
+    fd.step(3, 0.4)
+    torch.cuda.synchronize()
+    print("profile fd done")
 
 
 def run_reference(args):
@@ -452,8 +474,14 @@ def fd_throughput(torch, steps=200):
     r = fd.get_state()[0]
     ok = bool(torch.isfinite(r).all())
     fd.close()
+    _, sm_max, _ = load_peaks()
+    peak = 2 * 152 * sm_max * 1e6
+    achieved = FD_FP64_PER_POINT * nx * ny * steps / (ms / 1e3)
     return {"grid": f"{nx}x{ny}, dx=1, dt=0.4", "mlups": nx * ny * steps / (ms / 1e3) / 1e6,
-            "ms_per_step": ms / steps, "finite": ok, "launches_per_step": 4}
+            "ms_per_step": ms / steps, "finite": ok, "launches_per_step": 4,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "fp64_per_point_step": FD_FP64_PER_POINT,
+                         "peak_source": f"2 FP64 instr/clk/SM x 152 SMs x {sm_max:.0f} MHz"}}
 
 
 def main():
@@ -468,6 +496,7 @@ def main():
                     help="batched-engine plan for the timed run (auto: autotuned)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
+    ap.add_argument("--profile-fd", action="store_true", help="3 steps of the FD solver on 2048 x 1024 (for ncu)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run the four 512x512 droplets through the batched engine (launches plan) for 3 steps and exit")
     args = ap.parse_args()
@@ -475,6 +504,8 @@ def main():
         return profile_case()
     if args.profile_batch:
         return profile_batch()
+    if args.profile_fd:
+        return profile_fd()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -552,19 +583,13 @@ def main():
             k_ms[i] += t[i]
             k_n[i] += n[i]
 
-    # end to end: host density in (pinned), f = f_eq, E2E_INNER steps, host density out
-    from paper_2107_06355_gb300 import _lib as L
-    import ctypes as C
-
-    pin_in = [torch.from_numpy(r).pin_memory() for r in rho0s]
-    pin_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in sims]
-    lib = L.lib()
+    # end to end through the batch's host-to-host call: the four host densities in
+    # (pinned), f = f_eq, E2E_INNER steps with the tuned plan, the four densities out
+    pin_in = [torch.from_numpy(np.ascontiguousarray(r)).pin_memory() for r in rho0s]
+    pin_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in specs]
 
     def e2e_call():
-        for s, pi, po in zip(sims, pin_in, pin_out):
-            st = lib.pplbm_run_host(s.ctx, C.c_void_p(pi.data_ptr()), None, None, E2E_INNER,
-                                    C.c_void_p(po.data_ptr()))
-            L.check(st, s.ctx)
+        batch.run_host(pin_in, E2E_INNER, pin_out)
 
     e2e_call()
     e2e_steps = 5
@@ -575,6 +600,8 @@ def main():
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_mlups = nodes * E2E_INNER / e2e_s / 1e6 * ws
+    if not all(bool(torch.isfinite(po).all()) for po in pin_out):
+        raise RuntimeError("end-to-end densities are not finite")
     for s in sims:
         m, umax, bad = s.guard()
         if bad:
@@ -614,8 +641,12 @@ def main():
                             "kernel_ms": {"rho_psi": k_ms[0] / max(1, k_n[0]),
                                           "collide": k_ms[1] / max(1, k_n[1])}},
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
-                "h2d_bytes_per_step": 8 * NX * NY * len(specs), "d2h_bytes_per_step": 8 * NX * NY * len(specs),
-                "call": f"pplbm_run_host per lattice: H2D rho0 (pinned), f=f_eq, {E2E_INNER} steps, D2H rho"},
+                "h2d_bytes_per_step": 8 * NX * NY * len(specs) // E2E_INNER,
+                "d2h_bytes_per_step": 8 * NX * NY * len(specs) // E2E_INNER,
+                "steps_per_call": E2E_INNER, "h2d_bytes_per_call": 8 * NX * NY * len(specs),
+                "d2h_bytes_per_call": 8 * NX * NY * len(specs),
+                "call": f"pplbm_batch_run_host: H2D of the four rho0 (pinned), f=f_eq, {E2E_INNER} steps "
+                        "(tuned plan), D2H of the four rho"},
         "gpu_launches": launches_per_step * args.steps + (1 if plan["mode"] == 2 else 0),
         "clocks": clk,
     }

@@ -341,6 +341,13 @@ pplbm_status pplbm_batch_set_isolation(pplbm_batch* b, int32_t on);
 /* Synchronises and writes, per instance, PPLBM_OK or PPLBM_ERR_DIVERGED into
  * status[n] (host); returns the batch status. */
 pplbm_status pplbm_batch_instance_status(pplbm_batch* b, int32_t* status);
+/* One call from host data to host data for the whole batch: rho0[i] and
+ * rho_out[i] are host arrays of instance i's nx*ny densities (pinned memory gives
+ * the fastest copies). Sets f = f^eq(rho0[i], 0) for every instance, advances
+ * nsteps with the current plan and writes the final densities (the density
+ * pass's rho, Eq. Density) to rho_out. Synchronous; returns the batch status. */
+pplbm_status pplbm_batch_run_host(pplbm_batch* b, const double* const* rho0, int64_t nsteps,
+                                  double* const* rho_out);
 /* Per-instance guard (Sec. III.A convergence check, mass and the stability test of
  * the dynamic runs, Sec. IV). First runs the density/psi pass over every
  * instance's current state (as the next step would), then writes to the host

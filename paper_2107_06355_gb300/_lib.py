@@ -126,6 +126,7 @@ _SIGS = {
     "pplbm_batch_set_isolation": (C.c_int, [_P, C.c_int32]),
     "pplbm_batch_instance_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "pplbm_batch_guard": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "pplbm_batch_run_host": (C.c_int, [_P, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_void_p)]),
     "pplbm_batch_last_error": (C.c_char_p, [_P]),
     "pplbm_batch_destroy": (None, [_P]),
     "pplbm_adjoint_workspace_bytes": (C.c_size_t, [C.POINTER(pplbm_lattice)]),

@@ -124,6 +124,29 @@ class Batch:
         self._check(L.lib().pplbm_batch_instance_status(self.b, st))
         return list(st)
 
+    def run_host(self, rho0s, nsteps, outs):
+        """pplbm_batch_run_host: host densities in (one contiguous float64 (ny, nx)
+        array or CPU tensor per instance), nsteps, host densities out (same kind)."""
+        def addr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        import numpy as np
+
+        if len(rho0s) != self.n or len(outs) != self.n:
+            raise ValueError("one input and one output array per instance")
+        for k, (a, o) in enumerate(zip(rho0s, outs)):
+            nx, ny = self.shapes[k]
+            for t in (a, o):
+                if hasattr(t, "is_cuda"):
+                    ok = (not t.is_cuda) and t.dtype == self.torch.float64 and t.is_contiguous() and t.numel() == nx * ny
+                else:
+                    ok = isinstance(t, np.ndarray) and t.dtype == np.float64 and t.flags.c_contiguous and t.size == nx * ny
+                if not ok:
+                    raise ValueError(f"instance {k}: need a contiguous float64 host array of {ny} x {nx}")
+        src = (C.c_void_p * self.n)(*[addr(a) for a in rho0s])
+        dst = (C.c_void_p * self.n)(*[addr(a) for a in outs])
+        self._check(L.lib().pplbm_batch_run_host(self.b, src, int(nsteps), dst))
+
     def guard(self):
         """(n, 4) array per instance: mass, max |j|/rho, bad-node count, residual
         against the previous guard call (-1 when there is none); synchronises."""

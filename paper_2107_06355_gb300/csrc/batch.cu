@@ -742,6 +742,33 @@ pplbm_status pplbm_batch_get_fields(pplbm_batch* b, int32_t i, double* rho, doub
   return poll(b);
 }
 
+pplbm_status pplbm_batch_run_host(pplbm_batch* b, const double* const* rho0, int64_t nsteps,
+                                  double* const* rho_out) {
+  if (!b || !rho0 || !rho_out || nsteps < 0) return bfail(b, PPLBM_ERR_ARG, "NULL arrays or nsteps < 0");
+  if (b->sticky) return b->sticky;
+  for (int i = 0; i < b->n; ++i)
+    if (!rho0[i] || !rho_out[i]) return bfail(b, PPLBM_ERR_ARG, "NULL density array for instance %d", i);
+  // host densities in: staged in each instance's second f buffer, then f = f^eq
+  for (int i = 0; i < b->n; ++i) {
+    StepArgs& a = args_of(b, i);
+    double* stage = const_cast<double*>(a.f_out);
+    BTRY(b, cudaMemcpyAsync(stage, rho0[i], sizeof(double) * a.n, cudaMemcpyHostToDevice, b->stream));
+    launch_init_eq(a, const_cast<double*>(a.f_in), stage, nullptr, nullptr, b->stream);
+  }
+  BTRY(b, cudaGetLastError());
+  BTRY(b, cudaMemsetAsync(b->d_snap_valid, 0, sizeof(int) * b->n, b->stream));
+  if (pplbm_status st = issue_steps(b, nsteps, b->stream)) return st;
+  b->steps += nsteps;
+  // densities out: the density pass over the final state, one copy per instance
+  launch_density_pass(b->kind, b->d_inst, b->d_owner1, b->n1, b->parity, b->stream);
+  for (int i = 0; i < b->n; ++i) {
+    const StepArgs& a = args_of(b, i);
+    BTRY(b, cudaMemcpyAsync(rho_out[i], a.mom, sizeof(double) * a.n, cudaMemcpyDeviceToHost, b->stream));
+  }
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  return poll(b);
+}
+
 pplbm_status pplbm_batch_get_f(pplbm_batch* b, int32_t i, double* f) {
   if (!b || i < 0 || i >= b->n || !f) return bfail(b, PPLBM_ERR_ARG, "bad instance or NULL f");
   const StepArgs& a = args_of(b, i);

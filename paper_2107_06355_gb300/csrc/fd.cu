@@ -40,9 +40,12 @@ struct FDArgs {
   double* oux;
   double* ouy;
   int nx, ny;
-  double inv_dx, inv_dx2, dt;
-  double G, eps;
-  double mu_c, muB_c;  // mu = mu_c rho, mu_B = muB_c rho
+  // Every derivative is formed from raw stencil differences; the powers of
+  // h = 1/dx, the time step and the force and viscosity coefficients are folded
+  // into these constants on the host (mu = mu_c rho, mu_B = muB_c rho):
+  double cA;              // dt h: advection, mass flux, pressure gradient
+  double kS, kL, kD;      // dt (h^3/2) (G/6 - eps G/4), dt (h^3/2) G/12, dt (h^3/2) G/4
+  double v1, v2, v3, v4;  // dt h^2 mu_c, dt h^2 muB_c, dt h^2 (2 mu_c + muB_c), dt h^2 (mu_c + muB_c)/4
 };
 
 __global__ void k_fd_eos(const EosConst e, const double* __restrict__ rho, double* __restrict__ psi,
@@ -52,7 +55,8 @@ __global__ void k_fd_eos(const EosConst e, const double* __restrict__ rho, doubl
   const double r = rho[i];
   const double pr = eos_pressure(e, r);
   p[i] = pr;
-  psi[i] = sqrt(e.psi2_scale * (pr - r * (1.0 / 3.0)));
+  const double psi2 = e.psi2_scale * (pr - r * (1.0 / 3.0));
+  psi[i] = psi2 > 0.0 ? fast_sqrt(psi2) : sqrt(psi2);  // IEEE result at 0, below 0 and NaN
 }
 
 template <bool PRED>
@@ -61,74 +65,80 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   const int y = blockIdx.y * 8 + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const int nx = a.nx, ny = a.ny;
-  auto X = [&](int dx) { int v = x + dx; v %= nx; return v < 0 ? v + nx : v; };
-  auto Y = [&](int dy) { int v = y + dy; v %= ny; return v < 0 ? v + ny : v; };
-  auto at = [&](const double* f, int dx, int dy) { return f[(int64_t)Y(dy) * nx + X(dx)]; };
-  const double h = a.inv_dx, h2 = a.inv_dx2;
-  // one-sided first derivative along x (axis 0) or y (axis 1)
-  auto d1 = [&](const double* f, int axis) {
-    const double c = at(f, 0, 0);
-    if (PRED) return (axis == 0 ? at(f, 1, 0) - c : at(f, 0, 1) - c) * h;
-    return (axis == 0 ? c - at(f, -1, 0) : c - at(f, 0, -1)) * h;
+  // periodic columns and row offsets of the 5 x 5 neighbourhood, wrapped once
+  // (offsets reach +-2, so a grid of width 1 or 2 wraps twice)
+  auto wrap = [](int v, int n) {
+    if (v < 0) v += n;
+    if (v < 0) v += n;
+    if (v >= n) v -= n;
+    if (v >= n) v -= n;
+    return v;
   };
-  auto dc = [&](const double* f, int axis, int ox, int oy) {  // central first derivative at (x+ox, y+oy)
-    return (axis == 0 ? at(f, ox + 1, oy) - at(f, ox - 1, oy) : at(f, ox, oy + 1) - at(f, ox, oy - 1)) * (0.5 * h);
-  };
-  auto d2 = [&](const double* f, int ax1, int ax2, int ox, int oy) {  // central second derivatives
-    if (ax1 == ax2) {
-      if (ax1 == 0) return (at(f, ox + 1, oy) - 2.0 * at(f, ox, oy) + at(f, ox - 1, oy)) * h2;
-      return (at(f, ox, oy + 1) - 2.0 * at(f, ox, oy) + at(f, ox, oy - 1)) * h2;
-    }
-    return (at(f, ox + 1, oy + 1) - at(f, ox + 1, oy - 1) - at(f, ox - 1, oy + 1) + at(f, ox - 1, oy - 1)) *
-           (0.25 * h2);
-  };
-  const double rho = at(a.rho, 0, 0);
-  const double u[2] = {at(a.ux, 0, 0), at(a.uy, 0, 0)};
-  const double* uf[2] = {a.ux, a.uy};
-  // mass
-  const double drho_1[2] = {d1(a.rho, 0), d1(a.rho, 1)};
-  double du[2][2];  // du[a][b] = d_a u_b (one-sided)
-  for (int ax = 0; ax < 2; ++ax)
-    for (int b = 0; b < 2; ++b) du[ax][b] = d1(uf[b], ax);
-  const double div = du[0][0] + du[1][1];
-  const double rhs_rho = -(rho * div + (u[0] * drho_1[0] + u[1] * drho_1[1]));
-  // psi derivatives (central)
-  const double psi = at(a.psi, 0, 0);
-  const double dpsi[2] = {dc(a.psi, 0, 0, 0), dc(a.psi, 1, 0, 0)};
-  double ddpsi[2][2];
-  ddpsi[0][0] = d2(a.psi, 0, 0, 0, 0);
-  ddpsi[1][1] = d2(a.psi, 1, 1, 0, 0);
-  ddpsi[0][1] = ddpsi[1][0] = d2(a.psi, 0, 1, 0, 0);
-  const double lap = ddpsi[0][0] + ddpsi[1][1];
-  auto lap_at = [&](int ox, int oy) { return d2(a.psi, 0, 0, ox, oy) + d2(a.psi, 1, 1, ox, oy); };
-  const double dlap[2] = {(lap_at(1, 0) - lap_at(-1, 0)) * (0.5 * h), (lap_at(0, 1) - lap_at(0, -1)) * (0.5 * h)};
-  const double dp_1[2] = {d1(a.p, 0), d1(a.p, 1)};
-  double out[2];
-  for (int al = 0; al < 2; ++al) {
-    const double adv = u[0] * du[0][al] + u[1] * du[1][al];
-    const double s = dpsi[0] * ddpsi[al][0] + dpsi[1] * ddpsi[al][1];
-    const double dpp = -a.eps * a.G * 0.25 * s + a.G * (1.0 / 12.0) * dpsi[al] * lap + a.G * (1.0 / 6.0) * s +
-                       a.G * 0.25 * psi * dlap[al];
-    double visc = 0.0;
-    for (int b = 0; b < 2; ++b) visc += a.mu_c * drho_1[b] * (du[al][b] + du[b][al]);
-    double lapu = 0.0;
-    for (int b = 0; b < 2; ++b) lapu += d2(uf[b], al, b, 0, 0) + d2(uf[al], b, b, 0, 0);
-    visc += a.mu_c * rho * lapu;
-    visc += a.muB_c * drho_1[al] * div;
-    double gdiv = 0.0;
-    for (int b = 0; b < 2; ++b) gdiv += d2(uf[b], al, b, 0, 0);
-    visc += a.muB_c * rho * gdiv;
-    out[al] = -adv - dp_1[al] / rho - dpp / rho + visc / rho;
+  int cx[5];
+  int64_t ry[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    cx[k] = wrap(x + k - 2, nx);
+    ry[k] = (int64_t)wrap(y + k - 2, ny) * nx;
   }
+  auto at = [&](const double* f, int dx, int dy) { return f[ry[dy + 2] + cx[dx + 2]]; };
+  // one-sided first difference along x (axis 0) or y (axis 1): forward in the
+  // predictor, backward in the corrector; true derivative = h D
+  auto D1 = [&](const double* f, int axis) {
+    const double c = at(f, 0, 0);
+    if (PRED) return axis == 0 ? at(f, 1, 0) - c : at(f, 0, 1) - c;
+    return axis == 0 ? c - at(f, -1, 0) : c - at(f, 0, -1);
+  };
+  // central second differences: d_xx = h^2 Dxx, d_xy = (h^2/4) Dxy
+  auto Dxx = [&](const double* f) { return (at(f, 1, 0) + at(f, -1, 0)) - 2.0 * at(f, 0, 0); };
+  auto Dyy = [&](const double* f) { return (at(f, 0, 1) + at(f, 0, -1)) - 2.0 * at(f, 0, 0); };
+  auto Dxy = [&](const double* f) { return (at(f, 1, 1) - at(f, 1, -1)) - (at(f, -1, 1) - at(f, -1, -1)); };
+  const double rho = at(a.rho, 0, 0), ux = at(a.ux, 0, 0), uy = at(a.uy, 0, 0);
+  // mass: d_t rho = -(rho div u + u . grad rho)
+  const double Dr0 = D1(a.rho, 0), Dr1 = D1(a.rho, 1);
+  const double Du00 = D1(a.ux, 0), Du01 = D1(a.uy, 0);  // Du_ab: d_a u_b
+  const double Du10 = D1(a.ux, 1), Du11 = D1(a.uy, 1);
+  const double Dv = Du00 + Du11, Sh = Du01 + Du10;
+  const double drho = -a.cA * fma(rho, Dv, fma(ux, Dr0, uy * Dr1));
+  // psi: dpsi = (h/2) Pd, d_ab psi from Dxx, Dyy, Dxy, lap = h^2 Lc, and the
+  // derivative of lap psi = (h^3/2) DL from the 5-point sums at +-1
+  const double* ps = a.psi;
+  const double psi = at(ps, 0, 0);
+  const double Pd0 = at(ps, 1, 0) - at(ps, -1, 0), Pd1 = at(ps, 0, 1) - at(ps, 0, -1);
+  const double Pxx = Dxx(ps), Pyy = Dyy(ps), q = 0.25 * Dxy(ps);
+  const double Lc = Pxx + Pyy;
+  auto L5 = [&](int ox, int oy) {
+    return ((at(ps, ox + 1, oy) + at(ps, ox - 1, oy)) + (at(ps, ox, oy + 1) + at(ps, ox, oy - 1))) -
+           4.0 * at(ps, ox, oy);
+  };
+  const double DL0 = L5(1, 0) - L5(-1, 0), DL1 = L5(0, 1) - L5(0, -1);
+  // d_b p'_ab (Eq. FDforce) = (h^3/2) [(G/6 - eps G/4) S_a + (G/12) Pd_a Lc + (G/4) psi DL_a],
+  // S_a = sum_g Pd_g (d_a d_g psi in the same units)
+  const double S0 = fma(Pd0, Pxx, q * Pd1), S1 = fma(Pd1, Pyy, q * Pd0);
+  const double kDpsi = a.kD * psi;
+  const double F0 = fma(a.kS, S0, fma(a.kL * Pd0, Lc, kDpsi * DL0));
+  const double F1 = fma(a.kS, S1, fma(a.kL * Pd1, Lc, kDpsi * DL1));
+  // d_b sigma'_ab (Eqs. FDstressTensor, FDviscosityDerivative) with one-sided grad rho, grad u
+  // and central second derivatives of u
+  const double U0xx = Dxx(a.ux), U0yy = Dyy(a.ux), U1xx = Dxx(a.uy), U1yy = Dyy(a.uy);
+  const double U0xy = Dxy(a.ux), U1xy = Dxy(a.uy);
+  const double V0 = fma(a.v1, fma(2.0 * Dr0, Du00, Dr1 * Sh),
+                        fma(a.v2 * Dr0, Dv, rho * fma(a.v3, U0xx, fma(a.v4, U1xy, a.v1 * U0yy))));
+  const double V1 = fma(a.v1, fma(2.0 * Dr1, Du11, Dr0 * Sh),
+                        fma(a.v2 * Dr1, Dv, rho * fma(a.v3, U1yy, fma(a.v4, U0xy, a.v1 * U1xx))));
+  // dt d_t u_a = -dt u . grad u_a + (dt/rho)(d_b sigma'_ab - d_a p_EOS - d_b p'_ab)
+  const double inv_rho = fast_rcp(rho);
+  const double dux = fma(V0 - F0 - a.cA * D1(a.p, 0), inv_rho, -a.cA * fma(ux, Du00, uy * Du10));
+  const double duy = fma(V1 - F1 - a.cA * D1(a.p, 1), inv_rho, -a.cA * fma(ux, Du01, uy * Du11));
   const int64_t i = (int64_t)y * nx + x;
   if (PRED) {
-    a.orho[i] = rho + a.dt * rhs_rho;
-    a.oux[i] = u[0] + a.dt * out[0];
-    a.ouy[i] = u[1] + a.dt * out[1];
+    a.orho[i] = rho + drho;
+    a.oux[i] = ux + dux;
+    a.ouy[i] = uy + duy;
   } else {
-    a.orho[i] = 0.5 * (a.rho0[i] + rho + a.dt * rhs_rho);
-    a.oux[i] = 0.5 * (a.ux0[i] + u[0] + a.dt * out[0]);
-    a.ouy[i] = 0.5 * (a.uy0[i] + u[1] + a.dt * out[1]);
+    a.orho[i] = 0.5 * (a.rho0[i] + (rho + drho));
+    a.oux[i] = 0.5 * (a.ux0[i] + (ux + dux));
+    a.ouy[i] = 0.5 * (a.uy0[i] + (uy + duy));
   }
 }
 
@@ -219,13 +229,15 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   std::memset(&a, 0, sizeof(a));
   a.nx = f->nx;
   a.ny = f->ny;
-  a.inv_dx = 1.0 / f->dx;
-  a.inv_dx2 = a.inv_dx * a.inv_dx;
-  a.dt = dt;
-  a.G = f->G;
-  a.eps = f->eps;
-  a.mu_c = f->mu_c;
-  a.muB_c = f->muB_c;
+  const double h = 1.0 / f->dx, h2 = h * h, h3 = h2 * h;
+  a.cA = dt * h;
+  a.kS = dt * 0.5 * h3 * (f->G / 6.0 - f->eps * f->G / 4.0);
+  a.kL = dt * 0.5 * h3 * (f->G / 12.0);
+  a.kD = dt * 0.5 * h3 * (f->G / 4.0);
+  a.v1 = dt * h2 * f->mu_c;
+  a.v2 = dt * h2 * f->muB_c;
+  a.v3 = dt * h2 * (2.0 * f->mu_c + f->muB_c);
+  a.v4 = dt * h2 * (f->mu_c + f->muB_c) * 0.25;
   a.psi = f->psi;
   a.p = f->p;
   const int64_t n = f->n;

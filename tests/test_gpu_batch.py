@@ -212,3 +212,31 @@ def test_batch_guard_matches_host_reduction():
     assert b.instance_status()[1] == L.PPLBM_ERR_DIVERGED
     assert [st for k, st in enumerate(b.instance_status()) if k != 1] == [0] * (b.n - 1)
     b.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batch_run_host_equals_init_step_fields(mode):
+    """pplbm_batch_run_host (host in, nsteps, host out) gives the densities of
+    init_equilibrium + step + get_fields, bit for bit, in every plan."""
+    inst = _instances()
+    eos = [P.EOSParams(P.EOS_SMOOTH, Tr, 0.363, 2.0, 0.775) for (_, _, _, Tr, _) in inst]
+    lats = [(nx, ny, bc) for (nx, ny, bc, _, _) in inst]
+    relax = [P.Relax() for _ in inst]
+    b1 = P.Batch(lats, eos, relax)
+    b2 = P.Batch(lats, eos, relax)
+    b1.set_plan(mode, 0)
+    b2.set_plan(mode, 0)
+    rho0s = []
+    for k, (nx, ny, bc, Tr, kind) in enumerate(inst):
+        rho, _, _ = _init_fields(kind, nx, ny, b1.derived(k), 300 + k)
+        rho0s.append(np.ascontiguousarray(rho, dtype=np.float64))
+        b2.init_equilibrium(k, rho)
+    outs = [np.empty_like(r) for r in rho0s]
+    b1.run_host(rho0s, 9, outs)
+    b2.step(9)
+    for k in range(len(inst)):
+        assert np.array_equal(outs[k], b2.fields(k)[0].cpu().numpy())
+    with pytest.raises(ValueError):
+        b1.run_host(rho0s[:-1], 1, outs)
+    b1.close()
+    b2.close()
