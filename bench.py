@@ -246,6 +246,39 @@ def profile_fd():
     print("profile fd done")
 
 
+def profile_adjoint():
+    """Checkpointed forward and reverse pass on a 1024 x 1024 droplet (T_r = 0.5,
+    tau = 1), 12 steps with interval 4: 12 launches of each adjoint kernel on
+    75 MB states (> L2 with the adjoint planes)."""
+    import ctypes as C
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import _lib as L
+
+    build_lib()
+    nx = ny = 1024
+    steps, interval = 12, 4
+    sim = P.Simulation(nx, ny, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775), P.Relax())
+    d = sim.derived()
+    sim.init_equilibrium(I.droplet(nx, ny, 192.0, d["rho_v"], d["rho_l"], W=7.0))
+    dev = sim.device
+    ckpt = torch.empty((steps // interval, 9, ny, nx), dtype=torch.float64, device=dev)
+    seg = torch.empty((interval, 9, ny, nx), dtype=torch.float64, device=dev)
+    lam = torch.ones((9, ny, nx), dtype=torch.float64, device=dev)
+    lam0 = torch.empty_like(lam)
+    grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
+    nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
+    ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
+    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    L.check(L.lib().pplbm_forward_checkpointed(sim.ctx, steps, interval, p(ckpt)), sim.ctx)
+    L.check(L.lib().pplbm_backward_checkpointed(sim.ctx, steps, interval, p(ckpt), p(seg), p(lam), p(lam0), p(grad),
+                                                p(ws), nb), sim.ctx)
+    torch.cuda.synchronize()
+    sim.close()
+    print("profile adjoint done")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -344,7 +377,7 @@ def sweep_comparison(torch, stream, steps):
             "speedup": ms_s / ms_b}
 
 
-def adjoint_cost(torch, steps=400, interval=20):
+def adjoint_cost(torch, steps=2000, interval=45):
     """Adjoint configuration (256 x 256 droplet, R = 48, T_r = 0.5, tau = 1): time of a
     checkpointed forward rollout vs its reverse pass (recomputation + adjoint kernels)."""
     import ctypes as C
@@ -496,6 +529,7 @@ def main():
                     help="batched-engine plan for the timed run (auto: autotuned)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
+    ap.add_argument("--profile-adjoint", action="store_true", help="checkpointed adjoint on 1024 x 1024 (for ncu)")
     ap.add_argument("--profile-fd", action="store_true", help="3 steps of the FD solver on 2048 x 1024 (for ncu)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run the four 512x512 droplets through the batched engine (launches plan) for 3 steps and exit")
@@ -506,6 +540,8 @@ def main():
         return profile_batch()
     if args.profile_fd:
         return profile_fd()
+    if args.profile_adjoint:
+        return profile_adjoint()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

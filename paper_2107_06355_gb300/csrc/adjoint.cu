@@ -16,7 +16,10 @@
 //      through psi = sqrt(psi^2(rho; constants)) to rho_bar and the constants'
 //      adjoints; lambda^t_i = rho_bar + c_i . j_bar.
 // Constant adjoints are reduced per block and summed in a fixed order
-// (deterministic). The host maps them to d/d alpha with dconstants/dalpha.
+// (deterministic); over a checkpointed rollout each block's sums accumulate
+// across the steps and are reduced once at the end. Blocks with no node on a
+// branch whose constants depend on alpha skip those reductions. The host maps
+// the adjoints to d/d alpha with dconstants/dalpha.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,6 +45,7 @@ struct AdjArgs {
   double* bar;           // 6 planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar
   double* partial1;      // per A1 block: zz-scale adjoint
   double* partial2;      // per A2 block: kNGrad - 1 constant adjoints
+  int accumulate;        // add this step's block sums to the partials (a rollout) instead of storing them
 };
 
 // reverse mode of collide_reduced<kUnitTau> (see its comments for the forward)
@@ -140,11 +144,12 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
   double dp;
   if (rb <= e.bits_rho_max) {
     const double d = rho - e.rho_max;
-    const double s1 = sqrt(fma(-d * d, e.inv_a1sq, 1.0));
-    dp = -e.b1 * d * e.inv_a1sq / s1;
+    const double s1 = fast_sqrt(fma(-d * d, e.inv_a1sq, 1.0));
+    const double q = e.b1 * d * fast_rcp(s1);
+    dp = -q * e.inv_a1sq;
     dc[G_PMAX] = s;
     dc[G_B1] = s * (s1 - 1.0);
-    dc[G_IA1] = s * (-e.b1 * d * d / (2.0 * s1));
+    dc[G_IA1] = -0.5 * s * q * d;
   } else if (rb < e.bits_rho_min) {
     const double t = (rho - e.rho_max) * e.inv_span;
     dp = (3.0 * e.a2 * t + 2.0 * e.b2) * t * e.inv_span;
@@ -153,11 +158,12 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
     dc[G_B2] = s * t * t;
   } else {
     const double d = rho - e.rho_min;
-    const double s3 = sqrt(fma(-d * d, e.inv_a3sq, 1.0));
-    dp = e.b3 * d * e.inv_a3sq / s3;
+    const double s3 = fast_sqrt(fma(-d * d, e.inv_a3sq, 1.0));
+    const double q = e.b3 * d * fast_rcp(s3);
+    dp = q * e.inv_a3sq;
     dc[G_PMIN] = s;
     dc[G_B3] = s * (1.0 - s3);
-    dc[G_IA3] = s * (e.b3 * d * d / (2.0 * s3));
+    dc[G_IA3] = 0.5 * s * q * d;
   }
   return s * (dp - 1.0 / 3.0);
 }
@@ -227,7 +233,10 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
     B[5 * N + node] = gyb;
   }
   const double s = block_sum(zs_b, red);
-  if (threadIdx.x == 0 && threadIdx.y == 0) g.partial1[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double* dst = g.partial1 + blockIdx.y * gridDim.x + blockIdx.x;
+    *dst = g.accumulate ? *dst + s : s;
+  }
 }
 
 // gx_bar, gy_bar tile with a one-node halo (zero beyond a wall: ghosts carry no adjoint)
@@ -264,6 +273,7 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   double dcsum[kNGrad - 1];
   for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = 0.0;
+  bool shaped = false;  // this node's density lies on a branch with alpha-dependent constants
   if (x < a.nx && y < a.ny) {
     const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
     // transpose of g = 12 sum_c w_c psi(x + c) c, gathered at this node y
@@ -276,9 +286,12 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     const double psi = a.psi[node];
     double dc[kNGrad - 1];
     const double dpsi2 = psi2_grad(a.eos, rho, dc);
-    const double psi2_b = psi_b * 0.5 / psi;
+    const double psi2_b = 0.5 * psi_b * fast_rcp(psi);  // psi = sqrt(psi^2) > 0 (checked by the step)
     const double rho_b = g.bar[node] + psi2_b * dpsi2;
-    for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = psi2_b * dc[k];
+    const long long rb = dbits(rho);
+    shaped = a.eos.mode == 1 && rb > a.eos.bits_rho_v && rb < a.eos.bits_rho_l;
+    if (shaped)
+      for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
     double* L0 = g.lam0;
     L0[node] = rho_b;
@@ -292,29 +305,34 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     L0[8 * N + node] = rho_b + jxb - jyb;
   }
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  double* dst = g.partial2 + (int64_t)blk * (kNGrad - 1);
+  // block-uniform: a block with no node on a shaped branch adds exact zeros
+  if (!__syncthreads_or(shaped)) {
+    if (!g.accumulate && threadIdx.x == 0 && threadIdx.y == 0)
+      for (int k = 0; k < kNGrad - 1; ++k) dst[k] = 0.0;
+    return;
+  }
   for (int k = 0; k < kNGrad - 1; ++k) {
     const double s = block_sum(dcsum[k], red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) g.partial2[(int64_t)blk * (kNGrad - 1) + k] = s;
+    if (threadIdx.x == 0 && threadIdx.y == 0) dst[k] = g.accumulate ? dst[k] + s : s;
   }
 }
 
-// grad[k] += sum over blocks, in a fixed order
-__global__ void k_adj_reduce(const double* partial1, const double* partial2, int nblocks, double* grad) {
-  __shared__ double red[kNGrad][256];
-  double acc[kNGrad];
-  for (int k = 0; k < kNGrad; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += 256) {
-    for (int k = 0; k < kNGrad - 1; ++k) acc[k] += partial2[(int64_t)b * (kNGrad - 1) + k];
-    acc[G_ZZ] += partial1[b];
-  }
-  for (int k = 0; k < kNGrad; ++k) red[k][threadIdx.x] = acc[k];
+// grad[k] += sum over blocks, in a fixed order; one block per gradient slot
+__global__ void __launch_bounds__(256) k_adj_reduce(const double* partial1, const double* partial2, int nblocks,
+                                                    double* grad) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256)
+    acc += k == G_ZZ ? partial1[b] : partial2[(int64_t)b * (kNGrad - 1) + k];
+  red[threadIdx.x] = acc;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-      for (int k = 0; k < kNGrad; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < kNGrad) grad[threadIdx.x] += red[threadIdx.x][0];
+  if (threadIdx.x == 0) grad[k] += red[0];
 }
 
 // f_i = w_i rho0 is f^eq at rest; its transpose: rho0_bar = sum_i w_i lambda_i
@@ -342,13 +360,10 @@ size_t adj_bytes(const pplbm_lattice* l) {
   return sizeof(double) * (6 * n + 18 * n + nb * kNGrad + 64);
 }
 
-// one adjoint step at state f_t (device), lambda_next -> lambda_t, grad += ...
-pplbm_status adjoint_step(pplbm_ctx* c, const double* f_t, const double* lam1, double* lam0, double* grad,
-                          double* ws) {
-  StepArgs a = c->args;
-  a.f_in = f_t;
-  a.f_out = nullptr;
-  launch_rho_psi(a, c->stream);  // psi, moments of f^t
+// one adjoint step given the forward arguments of step t whose psi and moment
+// planes hold psi(f^t) and the moments of f^t: lambda_next -> lambda_t, grad += ...
+pplbm_status adjoint_core(pplbm_ctx* c, const StepArgs& a, const double* lam1, double* lam0, double* grad,
+                          double* ws, bool accumulate, bool reduce) {
   AdjArgs g;
   g.a = a;
   g.lam1 = lam1;
@@ -357,16 +372,28 @@ pplbm_status adjoint_step(pplbm_ctx* c, const double* f_t, const double* lam1, d
   const int nb = nblocks(a);
   g.partial1 = ws + 24 * c->n;
   g.partial2 = g.partial1 + nb;
+  g.accumulate = accumulate ? 1 : 0;
   const dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY), block(kTX, kTY);
   k_adj_collide<<<grid, block, 0, c->stream>>>(g);
   k_adj_rho_psi<<<grid, block, 0, c->stream>>>(g);
-  k_adj_reduce<<<1, 256, 0, c->stream>>>(g.partial1, g.partial2, nb, grad);
+  if (reduce) k_adj_reduce<<<kNGrad, 256, 0, c->stream>>>(g.partial1, g.partial2, nb, grad);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     c->msg = cudaGetErrorString(e);
     return PPLBM_ERR_CUDA;
   }
   return PPLBM_OK;
+}
+
+// one adjoint step at state f_t (device): the density pass fills the context's
+// psi and moment planes first
+pplbm_status adjoint_step(pplbm_ctx* c, const double* f_t, const double* lam1, double* lam0, double* grad,
+                          double* ws, bool accumulate, bool reduce) {
+  StepArgs a = c->args;
+  a.f_in = f_t;
+  a.f_out = nullptr;
+  launch_rho_psi(a, c->stream);
+  return adjoint_core(c, a, lam1, lam0, grad, ws, accumulate, reduce);
 }
 
 pplbm_status forward_into(pplbm_ctx* c, const double* fin, double* fout) {
@@ -395,7 +422,7 @@ pplbm_status pplbm_adjoint_step(pplbm_ctx* c, const double* f_t, const double* l
     return PPLBM_ERR_STATE;
   }
   if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
-  return adjoint_step(c, f_t, lambda_next, lambda_t, grad, (double*)adj_workspace);
+  return adjoint_step(c, f_t, lambda_next, lambda_t, grad, (double*)adj_workspace, false, true);
 }
 
 pplbm_status pplbm_forward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t interval, double* checkpoints) {
@@ -434,22 +461,57 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
     return PPLBM_ERR_CUDA;
   double* cur = lamA;
   double* nxt = lamB;
+  // per-block constant adjoints are summed over the whole rollout, then reduced once
+  const size_t nb = (size_t)nblocks(c->args);
+  double* partials = ws + 24 * c->n;
+  if (cudaMemsetAsync(partials, 0, sizeof(double) * nb * kNGrad, s) != cudaSuccess) return PPLBM_ERR_CUDA;
   if (nsteps > 0) {
     const int64_t nseg = (nsteps + interval - 1) / interval;
+    // With interval >= 4 the segment buffer (interval x 9 planes) holds two f
+    // buffers plus psi and the three moments of every state of the segment: the
+    // recomputation keeps what its density passes produce and the adjoint steps
+    // reuse it. Shorter intervals store the states themselves.
+    const bool keep_fields = 9 * interval >= 18 + 4 * interval;
+    const int64_t n = c->n;
     for (int64_t j = nseg - 1; j >= 0; --j) {
       const int64_t t0 = j * interval, t1 = std::min(nsteps, t0 + interval);
-      // recompute f^{t0} .. f^{t1 - 1} from the checkpoint
       if (cudaMemcpyAsync(segment, checkpoints + j * stride, sizeof(double) * stride, cudaMemcpyDeviceToDevice, s) !=
           cudaSuccess)
         return PPLBM_ERR_CUDA;
-      for (int64_t t = t0; t + 1 < t1; ++t)
-        if (pplbm_status st = forward_into(c, segment + (t - t0) * stride, segment + (t - t0 + 1) * stride)) return st;
-      for (int64_t t = t1 - 1; t >= t0; --t) {
-        if (pplbm_status st = adjoint_step(c, segment + (t - t0) * stride, cur, nxt, grad, ws)) return st;
-        std::swap(cur, nxt);
+      if (keep_fields) {
+        double* fb[2] = {segment, segment + stride};
+        double* fields = segment + 2 * stride;  // per state: psi, rho, jx, jy
+        for (int64_t t = t0; t < t1; ++t) {
+          StepArgs a = c->args;
+          a.f_in = fb[(t - t0) & 1];
+          a.f_out = fb[(t - t0 + 1) & 1];
+          a.psi = fields + (t - t0) * 4 * n;
+          a.mom = a.psi + n;
+          launch_rho_psi(a, s);
+          if (t + 1 < t1) launch_collide(a, s);
+        }
+        if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+          StepArgs a = c->args;
+          a.psi = fields + (t - t0) * 4 * n;
+          a.mom = a.psi + n;
+          if (pplbm_status st = adjoint_core(c, a, cur, nxt, grad, ws, true, false)) return st;
+          std::swap(cur, nxt);
+        }
+      } else {
+        for (int64_t t = t0; t + 1 < t1; ++t)
+          if (pplbm_status st = forward_into(c, segment + (t - t0) * stride, segment + (t - t0 + 1) * stride))
+            return st;
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+          if (pplbm_status st = adjoint_step(c, segment + (t - t0) * stride, cur, nxt, grad, ws, true, false))
+            return st;
+          std::swap(cur, nxt);
+        }
       }
     }
   }
+  k_adj_reduce<<<kNGrad, 256, 0, s>>>(partials, partials + nb, (int)nb, grad);
+  if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   if (cudaMemcpyAsync(lambda_0, cur, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
     return PPLBM_ERR_CUDA;
   return PPLBM_OK;

@@ -130,3 +130,24 @@ def test_droplet_256_rollout_2000_steps_against_finite_differences():
     hv = 1e-6
     fd_rho = (loss_at(0.775, rho0 + hv * v) - loss_at(0.775, rho0 - hv * v)) / (2 * hv)
     assert float((r0.grad * v).sum()) == pytest.approx(fd_rho, rel=1e-6)
+
+
+def test_rollout_gradients_do_not_depend_on_the_checkpoint_interval():
+    """Intervals below 4 store the recomputed states, longer ones keep only psi and
+    the moments of each state: both feed the adjoint kernels the same values in the
+    same order, so the gradients are bitwise equal across intervals."""
+    nx, ny, nsteps = 40, 36, 30
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    d = P.eos_setup(eosp)
+    rho0 = I.perturbed(I.droplet(nx, ny, 10.0, d["rho_v"], d["rho_l"], W=6.0), 0.002, 11)
+    grads = []
+    for interval in (1, 2, 3, 7, 30):
+        spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps, interval=interval)
+        r0 = torch.tensor(rho0, device="cuda", requires_grad=True)
+        alpha = torch.tensor(0.775, dtype=torch.float64, requires_grad=True)
+        rhoN = AD.rollout(r0, alpha, spec)
+        (rhoN ** 2).sum().backward()
+        grads.append((r0.grad.cpu().numpy(), float(alpha.grad)))
+    for g in grads[1:]:
+        assert np.array_equal(g[0], grads[0][0])
+        assert g[1] == grads[0][1]
