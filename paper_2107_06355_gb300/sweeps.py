@@ -68,7 +68,8 @@ def surface_tension(psi_profile, G=-1.0):
 
 
 def planar_coexistence(cases, nx=2, ny=200, W=10.0, tol=1e-6, check_every=100, max_steps=300000, G=-1.0):
-    """cases: list of (EOSParams, Relax). Returns one dict per case with keys
+    """cases: list of (EOSParams, Relax) or (EOSParams, Relax, W) (W: that case's
+    initial width; otherwise `W`). Returns one dict per case with keys
     converged, diverged, steps and, unless the case diverged, rho_v, rho_l,
     E_percent, width, width_interp, gamma and the density profile along y.
     The Sec. III.A residual and the divergence test run in the library's guard."""
@@ -81,7 +82,7 @@ def planar_coexistence(cases, nx=2, ny=200, W=10.0, tol=1e-6, check_every=100, m
     for i in range(n):
         d = b.derived(i)
         maxwell.append((d["rho_v"], d["rho_l"]))
-        prof = planar_profile(ny, d["rho_v"], d["rho_l"], W)
+        prof = planar_profile(ny, d["rho_v"], d["rho_l"], cases[i][2] if len(cases[i]) > 2 else W)
         b.init_equilibrium(i, np.repeat(prof[:, None], nx, axis=1))
     b.set_plan(L.PLAN_GRAPH, 0)
     b.guard()   # first snapshot
@@ -118,6 +119,28 @@ def planar_coexistence(cases, nx=2, ny=200, W=10.0, tol=1e-6, check_every=100, m
     return out
 
 
+def planar_coexistence_started(cases, widths=(10.0, 18.0, 22.0, 25.0), **kw):
+    """planar_coexistence, retrying every case that diverges from the next, wider
+    initial profile in `widths`. From the W = 10 tanh between the Maxwell densities,
+    the Peng loop at T_r <= 0.55 drives the vapour-side node negative within a few
+    hundred steps although wider starts converge (Table ParamPeng's interfaces).
+    Each result records the initial width W it converged from."""
+    out = [None] * len(cases)
+    todo = list(range(len(cases)))
+    for W in widths:
+        if not todo:
+            break
+        res = planar_coexistence([(cases[i][0], cases[i][1], W) for i in todo], **kw)
+        left = []
+        for i, r in zip(todo, res):
+            r["W"] = W
+            out[i] = r
+            if r["diverged"]:
+                left.append(i)
+        todo = left
+    return out
+
+
 def _settable(eos, G=-1.0):
     """True if the library's EOS set-up accepts these parameters (host only)."""
     from .lattice import eos_setup
@@ -138,8 +161,10 @@ def tune_to_width(families, grid=8, rounds=3, **planar_kw):
     The width is taken to be monotone in p. Each round evaluates `grid` geometrically
     spaced values of every family in one batch, keeps the adjacent pair whose widths
     straddle the target and refines inside it; the answer is the linear interpolation
-    of the last pair, verified by one more batched run. Candidates the EOS set-up
-    rejects, and runs that diverge, count as having no width.
+    of the last pair, verified by one more batched run. Each run starts from
+    W = 10 and, if it diverges, from wider profiles (`planar_coexistence_started`).
+    Candidates the EOS set-up rejects, and runs that diverge from every start,
+    count as having no width.
 
     Returns one dict per family: ok, param, and the verification run's result
     (width, width_interp, E_percent, rho_v, rho_l, gamma) when ok."""
@@ -158,7 +183,7 @@ def tune_to_width(families, grid=8, rounds=3, **planar_kw):
                     cases.append((eos, relax))
                     owner.append(k)
                     params.append(float(p))
-        res = planar_coexistence(cases, **planar_kw) if cases else []
+        res = planar_coexistence_started(cases, **planar_kw) if cases else []
         for k, f in enumerate(families):
             if not alive[k]:
                 continue
@@ -184,7 +209,7 @@ def tune_to_width(families, grid=8, rounds=3, **planar_kw):
         out.append(dict(ok=True, param=float(p)))
         cases.append(f["make"](float(p)))
         owner.append(k)
-    for k, r in zip(owner, planar_coexistence(cases, **planar_kw) if cases else []):
+    for k, r in zip(owner, planar_coexistence_started(cases, **planar_kw) if cases else []):
         r = dict(r)
         r.pop("profile", None)
         out[k].update(r)
@@ -300,7 +325,7 @@ def stability_study(Trs, vrs, steps=4000, a_cs=0.363, a_v=2.0, check_every=500):
     from .lattice import EOSParams, Relax
 
     cs_cases = [(EOSParams(L.EOS_CS, Tr, a_cs, a_cs, 0.5), Relax()) for Tr in Trs]
-    cs = planar_coexistence(cs_cases)
+    cs = planar_coexistence_started(cs_cases)
     fams, owners = [], []
     for Tr, r in zip(Trs, cs):
         if not r["converged"]:
