@@ -166,6 +166,14 @@ pplbm_status pplbm_set_stream(pplbm_ctx* ctx, void* stream);
  * values, > 0) is device or host memory; ux0, uy0 likewise or NULL for zero. */
 pplbm_status pplbm_init_equilibrium(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0);
 
+/* One call for the set-up of Sec. III.A: pplbm_create followed by
+ * pplbm_init_equilibrium(rho0, ux0, uy0) (rho0 required; ux0, uy0 may be NULL;
+ * host or device arrays of nx*ny). On failure nothing is left allocated and *out
+ * is NULL. The workspace rules are those of pplbm_create. */
+pplbm_status pplbm_init(pplbm_ctx** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos,
+                        const pplbm_relax* relax, double G, const double* rho0, const double* ux0, const double* uy0,
+                        void* f_workspace, size_t workspace_bytes, void* stream);
+
 /* Advances nsteps >= 0 time steps of Eq. LBE on the stream (asynchronous). */
 pplbm_status pplbm_step(pplbm_ctx* ctx, int64_t nsteps);
 
@@ -229,6 +237,14 @@ pplbm_status pplbm_forward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t 
 pplbm_status pplbm_backward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t interval, const double* checkpoints,
                                          double* segment, const double* lambda_N, double* lambda_0, double* grad,
                                          void* adj_workspace, size_t adj_workspace_bytes);
+/* The adjoint over one segment of a checkpointed rollout: from the segment's first
+ * state f_start (device, 9 planes), recomputes its nsteps states into `states`
+ * (nsteps slots of 9*nx*ny, device) and runs the adjoint steps back through them:
+ * lambda_start = (d f^{t0+nsteps} / d f^{t0})^T lambda_end, grad += the constants'
+ * adjoints. Equal to pplbm_backward_checkpointed with interval = nsteps. */
+pplbm_status pplbm_adjoint_segment(pplbm_ctx* ctx, const double* f_start, int64_t nsteps, double* states,
+                                   const double* lambda_end, double* lambda_start, double* grad,
+                                   void* adj_workspace, size_t adj_workspace_bytes);
 /* rho0_bar = sum_i w_i lambda_0[i]: the gradient w.r.t. the initial density of
  * f^0 = f^eq(rho0, u = 0) (Sec. III.A). */
 pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* ctx, const double* lambda_0, double* rho0_bar);
@@ -304,6 +320,13 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
 /* As pplbm_init_equilibrium, for instance i. Synchronises. */
 pplbm_status pplbm_batch_init_equilibrium(pplbm_batch* b, int32_t i, const double* rho0, const double* ux0,
                                           const double* uy0);
+/* pplbm_batch_create followed by pplbm_batch_init_equilibrium for every instance:
+ * rho0[i] (required), ux0[i], uy0[i] (ux0, uy0 or their entries may be NULL) are
+ * instance i's arrays. On failure nothing is left allocated and *out is NULL. */
+pplbm_status pplbm_batch_init(pplbm_batch** out, int32_t n, const pplbm_lattice* lattices,
+                              const pplbm_eos_params* eos, const pplbm_relax* relax, double G,
+                              const double* const* rho0, const double* const* ux0, const double* const* uy0,
+                              void* workspace, size_t workspace_bytes, void* stream);
 /* Advances every instance by nsteps (asynchronous). */
 pplbm_status pplbm_batch_step(pplbm_batch* b, int64_t nsteps);
 /* As pplbm_get_fields / pplbm_get_f / pplbm_set_f, for instance i. */

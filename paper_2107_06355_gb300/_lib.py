@@ -126,6 +126,12 @@ _SIGS = {
     "pplbm_batch_set_isolation": (C.c_int, [_P, C.c_int32]),
     "pplbm_batch_instance_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "pplbm_batch_guard": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "pplbm_init": (C.c_int, [C.POINTER(_P), C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),
+                             C.POINTER(pplbm_relax), C.c_double, _P, _P, _P, _P, C.c_size_t, _P]),
+    "pplbm_batch_init": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),
+                                   C.POINTER(pplbm_relax), C.c_double, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                   _P, C.c_size_t, _P]),
+    "pplbm_adjoint_segment": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P, _P, _P, C.c_size_t]),
     "pplbm_batch_run_host": (C.c_int, [_P, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_void_p)]),
     "pplbm_batch_last_error": (C.c_char_p, [_P]),
     "pplbm_batch_destroy": (None, [_P]),

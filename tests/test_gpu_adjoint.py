@@ -151,3 +151,32 @@ def test_rollout_gradients_do_not_depend_on_the_checkpoint_interval():
     for g in grads[1:]:
         assert np.array_equal(g[0], grads[0][0])
         assert g[1] == grads[0][1]
+
+
+def test_adjoint_segment_equals_one_segment_backward():
+    """pplbm_adjoint_segment(f_start, n) = pplbm_backward_checkpointed with interval n."""
+    nx, ny, nsteps = 40, 36, 12
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    sim = P.Simulation(nx, ny, P.BC_PERIODIC, eosp, P.Relax())
+    d = sim.derived()
+    sim.init_equilibrium(I.perturbed(I.droplet(nx, ny, 10.0, d["rho_v"], d["rho_l"], W=6.0), 0.002, 5))
+    f0 = sim.get_f().clone()
+    lam = torch.as_tensor(np.random.default_rng(3).standard_normal((9, ny, nx)), device="cuda")
+    nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
+    out = []
+    for which in range(2):
+        ws = torch.zeros(nb // 8 + 1, dtype=torch.float64, device="cuda")
+        states = torch.empty((nsteps, 9, ny, nx), dtype=torch.float64, device="cuda")
+        lam0 = torch.empty_like(lam)
+        grad = torch.zeros(L.NGRAD, dtype=torch.float64, device="cuda")
+        p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+        if which == 0:
+            st = L.lib().pplbm_adjoint_segment(sim.ctx, p(f0), nsteps, p(states), p(lam), p(lam0), p(grad), p(ws), nb)
+        else:
+            st = L.lib().pplbm_backward_checkpointed(sim.ctx, nsteps, nsteps, p(f0), p(states), p(lam), p(lam0),
+                                                     p(grad), p(ws), nb)
+        L.check(st, sim.ctx)
+        torch.cuda.synchronize()
+        out.append((lam0.cpu(), grad.cpu()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    sim.close()

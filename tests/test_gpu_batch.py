@@ -240,3 +240,35 @@ def test_batch_run_host_equals_init_step_fields(mode):
         b1.run_host(rho0s[:-1], 1, outs)
     b1.close()
     b2.close()
+
+
+def test_one_call_batch_init_equals_create_then_init():
+    import ctypes as C
+
+    inst = _instances()
+    eos = [P.EOSParams(P.EOS_SMOOTH, Tr, 0.363, 2.0, 0.775) for (_, _, _, Tr, _) in inst]
+    relax = [P.Relax() for _ in inst]
+    ref = P.Batch([(nx, ny, bc) for (nx, ny, bc, _, _) in inst], eos, relax)
+    fields = []
+    for k, (nx, ny, bc, Tr, kind) in enumerate(inst):
+        rho, ux, uy = _init_fields(kind, nx, ny, ref.derived(k), 500 + k)
+        fields.append(tuple(None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy)))
+        ref.init_equilibrium(k, *fields[-1])
+    n = len(inst)
+    ptrs = [(C.c_void_p * n)(*[None if f[j] is None else f[j].ctypes.data for f in fields]) for j in range(3)]
+    ws = torch.empty(ref.workspace.numel(), dtype=torch.float64, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    nbytes = L.lib().pplbm_batch_workspace_bytes(n, ref._lat, ref._relax)
+    b = C.c_void_p()
+    st = L.lib().pplbm_batch_init(C.byref(b), n, ref._lat, ref._eos, ref._relax, -1.0, *ptrs, C.c_void_p(base),
+                                  nbytes, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == L.PPLBM_OK
+    L.check(L.lib().pplbm_batch_step(b, 4), batch=b)
+    ref.step(4)
+    for k, (nx, ny, _, _, _) in enumerate(inst):
+        f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+        L.check(L.lib().pplbm_batch_get_f(b, k, C.c_void_p(f.data_ptr())), batch=b)
+        torch.cuda.synchronize()
+        assert torch.equal(f, ref.get_f(k))
+    L.lib().pplbm_batch_destroy(b)
+    ref.close()

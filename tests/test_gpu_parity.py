@@ -260,3 +260,38 @@ def test_impact_2048x1024_100000_steps_stable_and_conserves_mass():
     vapour = float(np.median(rho[600:1000]))
     assert film == pytest.approx(d["rho_l"], rel=0.01)
     assert film / vapour > 2e4
+
+
+def test_one_call_init_equals_create_then_init_equilibrium():
+    """pplbm_init (Sec. III.A set-up in one call) leaves the same distributions as
+    pplbm_create + pplbm_init_equilibrium, and steps identically."""
+    import ctypes as C
+    import torch
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import _lib as L
+
+    nx, ny = 48, 40
+    eos, relax = P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax()
+    ref = P.Simulation(nx, ny, BC_WALLS, eos, relax)
+    d = ref.derived()
+    rho0, ux0, uy0 = I.impact(nx, ny, 8, 8, d["rho_v"], d["rho_l"], 0.02, W=5.0)
+    ref.init_equilibrium(rho0, ux0, uy0)
+    lat, ce, cr = L.pplbm_lattice(nx, ny, BC_WALLS, 0), eos.c(), relax.c()
+    nbytes = L.lib().pplbm_workspace_bytes(C.byref(lat), C.byref(cr))
+    ws = torch.empty(nbytes // 8 + 32, dtype=torch.float64, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    hosts = [np.ascontiguousarray(a) for a in (rho0, ux0, uy0)]
+    ctx = C.c_void_p()
+    st = L.lib().pplbm_init(C.byref(ctx), C.byref(lat), C.byref(ce), C.byref(cr), -1.0,
+                            *[C.c_void_p(h.ctypes.data) for h in hosts], C.c_void_p(base), nbytes,
+                            C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == L.PPLBM_OK
+    f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+    for nsteps in (0, 5):
+        L.check(L.lib().pplbm_step(ctx, nsteps), ctx)
+        ref.step(nsteps)
+        L.check(L.lib().pplbm_get_f(ctx, C.c_void_p(f.data_ptr())), ctx)
+        torch.cuda.synchronize()
+        assert torch.equal(f, ref.get_f())
+    L.lib().pplbm_destroy(ctx)
+    ref.close()

@@ -120,3 +120,22 @@ def test_create_rejects_without_touching_the_gpu(lib):
                             None, 1 << 20, None) == L.PPLBM_ERR_ARG
     assert ctx.value is None
     assert lib.pplbm_status_string(L.PPLBM_ERR_DIVERGED) == b"simulation diverged"
+
+
+def test_one_call_setups_reject_missing_fields_without_touching_the_gpu(lib):
+    lat = L.pplbm_lattice(8, 8, L.BC_PERIODIC, 0)
+    eos = P.EOSParams().c()
+    relax = P.Relax().c()
+    ctx = C.c_void_p(1)
+    assert lib.pplbm_init(C.byref(ctx), C.byref(lat), C.byref(eos), C.byref(relax), -1.0, None, None, None,
+                          C.c_void_p(256), 1 << 20, None) == L.PPLBM_ERR_ARG
+    assert ctx.value is None
+    b = C.c_void_p(1)
+    lats = (L.pplbm_lattice * 1)(lat)
+    eoss = (L.pplbm_eos_params * 1)(eos)
+    rels = (L.pplbm_relax * 1)(relax)
+    rho = (C.c_void_p * 1)(None)
+    assert lib.pplbm_batch_init(C.byref(b), 1, lats, eoss, rels, -1.0, rho, None, None, C.c_void_p(256), 1 << 20,
+                                None) == L.PPLBM_ERR_ARG
+    assert b.value is None
+    assert lib.pplbm_adjoint_segment(None, None, 0, None, None, None, None, None, 0) == L.PPLBM_ERR_ARG
