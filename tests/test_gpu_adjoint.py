@@ -180,3 +180,34 @@ def test_adjoint_segment_equals_one_segment_backward():
         out.append((lam0.cpu(), grad.cpu()))
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
     sim.close()
+
+
+def test_planar_vapour_density_error_gradient_against_finite_differences():
+    """The planar-interface loss: E^2 with E = (rho_v(sim) - rho_v^M)/rho_v^M the
+    vapour-density error of Eq. DensityError, after 3,000 steps of the (4, 200)
+    planar interface at T_r = 0.5 (Smooth C-S, a = 0.5, a_v = 0.5, alpha = 0.610,
+    the w = 7 row of Table ParamSmooth; tau = 1, Li forcing). d(E^2)/d alpha from
+    the adjoint (sqrt(N) checkpoints) against central differences, h = 1e-6."""
+    nx, ny, nsteps = 4, 200, 3000
+    al0 = 0.610
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.5, 0.5, al0)
+    d = P.eos_setup(eosp)
+    rv, rl = d["rho_v"], d["rho_l"]   # the Maxwell densities do not depend on alpha
+    rho0 = torch.tensor(I.planar(nx, ny, rv, rl, W=10.0), device="cuda")
+    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps)
+
+    def loss_of(rho):
+        return ((rho[0, :].mean() - rv) / rv) ** 2
+
+    alpha = torch.tensor(al0, dtype=torch.float64, requires_grad=True)
+    L0 = loss_of(AD.rollout(rho0, alpha, spec))
+    L0.backward()
+
+    def loss_at(al):
+        with torch.no_grad():
+            return float(loss_of(AD.rollout(rho0, torch.tensor(al, dtype=torch.float64), spec)))
+
+    h = 1e-6
+    fd_alpha = (loss_at(al0 + h) - loss_at(al0 - h)) / (2 * h)
+    assert abs(float(alpha.grad)) > 0
+    assert float(alpha.grad) == pytest.approx(fd_alpha, rel=1e-6)
