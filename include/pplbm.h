@@ -212,12 +212,18 @@ pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux
 /* ---- Adjoint (reverse-mode gradients), unit relaxation times (Sec. III.A) -----
  * A hand-written adjoint of pplbm_step for contexts whose relaxation times are
  * all 1 (other sets return PPLBM_ERR_STATE). Gradients flow to the state and to
- * the EOS constants that depend on the shaping parameter alpha (Sec. III.D):
- * grad[PPLBM_NGRAD] = dL/d{p_max, b1, 1/a1^2, a2, b2, p_min, b3, 1/a3^2, z},
- * with a2, b2 the cubic's coefficients and z = sigma G^2/432 the Li term's scale
- * (Eq. LiFS). pplbm_eos_constant_sensitivity gives their alpha-derivatives, so
- * dL/dalpha = sum_k grad[k] dc[k]. All pointers are device memory unless noted. */
-#define PPLBM_NGRAD 9
+ * the EOS constants that the shaping parameters move (Sec. III.D):
+ * grad[PPLBM_NGRAD] = dL/d{p_max, b1, 1/a1^2, a2, b2, p_min, b3, 1/a3^2, z,
+ *                          k1_v, k2_v, k1_l, k2_l, k4_l},
+ * with a2, b2 the cubic's coefficients, z = sigma G^2/432 the Li term's scale
+ * (Eq. LiFS), and k1 = (2/G) R T, k2 = -(2/G) a, k4 = (2/G) Delta P the constants of
+ * psi^2 = rho (k1 Z(rho) + k2 rho - 2/(3G)) + k4 on the vapour (v) and liquid (l)
+ * C-S branches (Eq. CS, Eq. InteractionPotential). pplbm_eos_constant_sensitivity
+ * gives their derivatives with respect to alpha, a_vap or a_liq, so dL/dtheta =
+ * sum_k grad[k] dc[k]. At fixed T_r the branch boundaries (rho_v, rho_l, rho_max,
+ * rho_min) do not depend on these parameters, so the chain is exact. All pointers
+ * are device memory unless noted. */
+#define PPLBM_NGRAD 14
 
 /* Bytes of the adjoint workspace (adjoint planes, lambda ping-pong, per-block partials). */
 size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice);
@@ -250,9 +256,10 @@ pplbm_status pplbm_adjoint_segment(pplbm_ctx* ctx, const double* f_start, int64_
 pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* ctx, const double* lambda_0, double* rho0_bar);
 /* Host only: the values of the PPLBM_NGRAD constants (z left 0). */
 pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* eos, double c[PPLBM_NGRAD]);
-/* Host only: dc/dalpha (which = 0) of the PPLBM_NGRAD constants, including z through
- * sigma(alpha) when relax->sigma_auto, by central differences of pplbm_eos_setup at
- * steps h and h/2 combined by Richardson extrapolation (error O(h^4)). */
+/* Host only: dc/dtheta of the PPLBM_NGRAD constants for theta = alpha (which = 0),
+ * a_vap (1) or a_liq (2), including z through sigma(theta) when relax->sigma_auto,
+ * by central differences of pplbm_eos_setup at steps h and h/2 combined by
+ * Richardson extrapolation (error O(h^4)). PPLBM_ERR_ARG for another `which`. */
 pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* params, double G, const pplbm_relax* relax,
                                             int32_t which, double h, double dc[PPLBM_NGRAD]);
 

@@ -6,9 +6,10 @@ in the same order (rho, psi, Shan-Chen force, u, m = M f, m_eq, Li source S,
 m* = m - Lambda (m - m_eq) + (I - Lambda/2) S, f* = M^-1 m*, streaming with
 half-way bounce-back), and torch.autograd supplies the exact reverse-mode
 derivatives of that arithmetic. The EOS enters through its derived constants
-(p_max, b1, a1^2, p_min, b3, a3^2 of Sec. III.D and sigma), which are inputs here;
-their dependence on the shaping parameter alpha is taken from the numpy oracle by
-central differences with Richardson extrapolation.
+(p_max, b1, a1^2, p_min, b3, a3^2 of Sec. III.D, sigma, and the C-S parameters
+a, T of the vapour and liquid branches with the liquid shift Delta P), which are
+inputs here; their dependence on a parameter (alpha, a_v or a_l) is taken from the
+numpy oracle by central differences with Richardson extrapolation.
 
 Only the unit-relaxation-time set (Lambda = I, Sec. III.A) is restated.
 """
@@ -20,7 +21,7 @@ import torch
 from . import eos as E
 from . import lbm as L
 
-CONST_NAMES = ("p_max", "b1", "a1sq", "p_min", "b3", "a3sq", "sigma")
+CONST_NAMES = ("p_max", "b1", "a1sq", "p_min", "b3", "a3sq", "sigma", "a_v", "T_v", "a_l", "T_l", "dP")
 
 _C = torch.tensor(L.C, dtype=torch.float64)
 _W = torch.tensor(L.W, dtype=torch.float64)
@@ -30,21 +31,27 @@ _WSC = torch.tensor(L.W_SC, dtype=torch.float64)
 
 
 def eos_constants(eos):
-    """The alpha-dependent constants of a Smooth C-S oracle EOS (and sigma)."""
+    """The constants of a Smooth C-S oracle EOS that its parameters move: those of
+    the shaped branches, sigma, and the C-S parameters of both bulk branches."""
     return {"p_max": eos.p_max, "b1": eos.b1, "a1sq": eos.a1sq, "p_min": eos.p_min, "b3": eos.b3,
-            "a3sq": eos.a3sq, "sigma": eos.sigma()}
+            "a3sq": eos.a3sq, "sigma": eos.sigma(), "a_v": eos.a_v, "T_v": eos.T_v, "a_l": eos.a_l,
+            "T_l": eos.T_l, "dP": eos.dP}
 
 
-def constants_derivative(mode, Tr, a_l, a_v, alpha, h=1e-3):
-    """d(constant)/d(alpha) for each of CONST_NAMES: central differences of the oracle's
-    set-up at steps h and h/2 combined by Richardson extrapolation."""
-    def at(al):
-        e = E.make_eos(mode, Tr, a_l, a_v, al)
+def constants_derivative(mode, Tr, a_l, a_v, alpha, h=1e-3, wrt="alpha"):
+    """d(constant)/d(theta), theta = alpha, a_v or a_l (`wrt`), for each of CONST_NAMES:
+    central differences of the oracle's set-up at steps h and h/2 combined by
+    Richardson extrapolation."""
+    def at(v):
+        args = {"alpha": alpha, "a_v": a_v, "a_l": a_l}
+        args[wrt] = v
+        e = E.make_eos(mode, Tr, args["a_l"], args["a_v"], args["alpha"])
         e.solve_eps(n=40000)
         return np.array([eos_constants(e)[k] for k in CONST_NAMES])
 
-    d1 = (at(alpha + h) - at(alpha - h)) / (2 * h)
-    d2 = (at(alpha + h / 2) - at(alpha - h / 2)) / h
+    x = {"alpha": alpha, "a_v": a_v, "a_l": a_l}[wrt]
+    d1 = (at(x + h) - at(x - h)) / (2 * h)
+    d2 = (at(x + h / 2) - at(x - h / 2)) / h
     return dict(zip(CONST_NAMES, (4 * d2 - d1) / 3))
 
 
@@ -61,7 +68,7 @@ def pressure(rho, eos, c):
     m3 = (rho > eos.rho_max) & (rho < eos.rho_min)
     m4 = (rho >= eos.rho_min) & (rho < eos.rho_l)
     m5 = rho >= eos.rho_l
-    p = p.index_put((m1,), _cs_pressure(rho[m1], eos.a_v, eos.b, eos.R, eos.T_v))
+    p = p.index_put((m1,), _cs_pressure(rho[m1], c["a_v"], eos.b, eos.R, c["T_v"]))
     x = rho[m2]
     p = p.index_put((m2,), c["p_max"] - c["b1"] + c["b1"] * torch.sqrt(1.0 - (x - eos.rho_max) ** 2 / c["a1sq"]))
     t = (rho[m3] - eos.rho_max) / (eos.rho_min - eos.rho_max)
@@ -70,7 +77,7 @@ def pressure(rho, eos, c):
     p = p.index_put((m3,), a2 * t**3 + b2 * t**2 + c["p_max"])
     x = rho[m4]
     p = p.index_put((m4,), c["p_min"] + c["b3"] - c["b3"] * torch.sqrt(1.0 - (x - eos.rho_min) ** 2 / c["a3sq"]))
-    p = p.index_put((m5,), _cs_pressure(rho[m5], eos.a_l, eos.b, eos.R, eos.T_l) + eos.dP)
+    p = p.index_put((m5,), _cs_pressure(rho[m5], c["a_l"], eos.b, eos.R, c["T_l"]) + c["dP"])
     return p
 
 

@@ -4,9 +4,10 @@ Forward: f^0 = f^eq(rho0, 0), nsteps steps through pplbm_forward_checkpointed
 (checkpoints every `interval` steps, ~sqrt(nsteps)), output rho^N. Backward:
 pplbm_backward_checkpointed (segment recomputation + hand-written adjoint
 kernels) gives dL/df^0 and dL/d(EOS constants); the initial-density gradient is
-sum_i w_i dL/df^0_i and the alpha gradient chains the constants' gradients with
-their alpha-derivatives (pplbm_eos_constant_sensitivity). Argument marshalling
-only: every step runs in the library's kernels.
+sum_i w_i dL/df^0_i and the parameter gradient (alpha, a_vap or a_liq, chosen by
+RolloutSpec.param) chains the constants' gradients with their derivatives
+(pplbm_eos_constant_sensitivity). Argument marshalling only: every step runs in
+the library's kernels.
 """
 from __future__ import annotations
 
@@ -23,29 +24,42 @@ class RolloutSpec:
     nx: int
     ny: int
     bc: int
-    eos: EOSParams          # alpha is taken from the Function's input
+    eos: EOSParams          # the differentiated parameter is taken from the Function's input
     relax: Relax
     nsteps: int
     interval: int = 0       # 0: ceil(sqrt(nsteps))
     G: float = -1.0
+    param: str = "alpha"    # "alpha", "a_vap" or "a_liq"
 
     def k(self):
         return self.interval if self.interval > 0 else max(1, math.ceil(math.sqrt(self.nsteps)))
 
 
-def alpha_sensitivity(spec: RolloutSpec, alpha: float, h: float = 1e-4):
-    """d(EOS constants)/d(alpha), PPLBM_NGRAD values (host)."""
+def param_sensitivity(spec: RolloutSpec, value: float, h: float = 1e-4):
+    """d(EOS constants)/d(spec.param) at spec.param = value, PPLBM_NGRAD values (host)."""
     dc = (C.c_double * L.NGRAD)()
-    p = replace(spec.eos, alpha=alpha).c()
+    p = _with_param(spec, value).c()
     r = spec.relax.c()
-    L.check(L.lib().pplbm_eos_constant_sensitivity(C.byref(p), spec.G, C.byref(r), 0, h, dc))
+    L.check(L.lib().pplbm_eos_constant_sensitivity(C.byref(p), spec.G, C.byref(r), L.SENS_PARAMS[spec.param], h,
+                                                   dc))
     return list(dc)
 
 
-def _rollout_forward(spec: RolloutSpec, rho0, alpha: float):
+def alpha_sensitivity(spec: RolloutSpec, alpha: float, h: float = 1e-4):
+    """d(EOS constants)/d(alpha), PPLBM_NGRAD values (host)."""
+    return param_sensitivity(replace(spec, param="alpha"), alpha, h)
+
+
+def _with_param(spec: RolloutSpec, value: float) -> EOSParams:
+    if spec.param not in L.SENS_PARAMS:
+        raise ValueError(f"unknown parameter {spec.param!r}")
+    return replace(spec.eos, **{spec.param: value})
+
+
+def _rollout_forward(spec: RolloutSpec, rho0, value: float):
     import torch
 
-    sim = Simulation(spec.nx, spec.ny, spec.bc, replace(spec.eos, alpha=alpha), spec.relax, G=spec.G)
+    sim = Simulation(spec.nx, spec.ny, spec.bc, _with_param(spec, value), spec.relax, G=spec.G)
     sim.init_equilibrium(rho0)
     K = spec.k()
     nseg = max(1, -(-spec.nsteps // K))
@@ -78,22 +92,22 @@ def _make_function():
     import torch
 
     class Rollout(torch.autograd.Function):
-        """rho^N = rollout(rho0, alpha); gradients w.r.t. rho0 and alpha."""
+        """rho^N = rollout(rho0, theta); gradients w.r.t. rho0 and theta = spec.param."""
 
         @staticmethod
-        def forward(ctx, rho0, alpha, spec):
-            sim, ckpt, rhoN = _rollout_forward(spec, rho0.detach(), float(alpha))
-            ctx.spec, ctx.sim, ctx.ckpt, ctx.alpha = spec, sim, ckpt, float(alpha)
+        def forward(ctx, rho0, theta, spec):
+            sim, ckpt, rhoN = _rollout_forward(spec, rho0.detach(), float(theta))
+            ctx.spec, ctx.sim, ctx.ckpt, ctx.theta = spec, sim, ckpt, float(theta)
             return rhoN
 
         @staticmethod
         def backward(ctx, grad_rhoN):
             spec = ctx.spec
             rho0_bar, grad, _ = _rollout_backward(spec, ctx.sim, ctx.ckpt, grad_rhoN.contiguous())
-            dc = torch.tensor(alpha_sensitivity(spec, ctx.alpha), dtype=torch.float64, device=grad.device)
-            galpha = (grad * dc).sum()
+            dc = torch.tensor(param_sensitivity(spec, ctx.theta), dtype=torch.float64, device=grad.device)
+            gtheta = (grad * dc).sum()
             ctx.sim.close()
-            return rho0_bar, galpha.to(grad_rhoN.dtype), None
+            return rho0_bar, gtheta.to(grad_rhoN.dtype), None
 
     return Rollout
 
@@ -101,9 +115,10 @@ def _make_function():
 _FN = None
 
 
-def rollout(rho0, alpha, spec: RolloutSpec):
-    """Differentiable rollout: rho0 (ny, nx) CUDA float64 tensor, alpha a 0-d tensor."""
+def rollout(rho0, theta, spec: RolloutSpec):
+    """Differentiable rollout: rho0 (ny, nx) CUDA float64 tensor, theta a 0-d tensor
+    holding the value of spec.param (alpha by default)."""
     global _FN
     if _FN is None:
         _FN = _make_function()
-    return _FN.apply(rho0, alpha, spec)
+    return _FN.apply(rho0, theta, spec)

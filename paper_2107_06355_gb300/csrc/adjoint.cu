@@ -34,9 +34,13 @@ namespace pplbm {
 namespace {
 
 constexpr int kTX = 32, kTY = 8, kNT = kTX * kTY;
-// gradient slots (the alpha-dependent constants of EosConst, then the Li-term scale)
-enum { G_PMAX = 0, G_B1, G_IA1, G_A2, G_B2, G_PMIN, G_B3, G_IA3, G_ZZ, kNGrad };
+// gradient slots: the constants of the shaped branches (which alpha moves), the
+// Li-term scale, then the bulk C-S constants the parameters a_vap and a_liq move
+enum { G_PMAX = 0, G_B1, G_IA1, G_A2, G_B2, G_PMIN, G_B3, G_IA3, G_ZZ, G_K1V, G_K2V, G_K1L, G_K2L, G_K4L, kNGrad };
 static_assert(kNGrad == PPLBM_NGRAD, "gradient slot count");
+// A2 reduces every slot but G_ZZ (A1's); its local index of slot k
+constexpr int kA2 = kNGrad - 1;
+__host__ __device__ constexpr int a2_index(int k) { return k < G_ZZ ? k : k - 1; }
 
 struct AdjArgs {
   StepArgs a;            // forward arguments of step t (psi, mom filled by K1 on f^t)
@@ -44,7 +48,7 @@ struct AdjArgs {
   double* lam0;          // lambda^t, 9 planes
   double* bar;           // 6 planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar
   double* partial1;      // per A1 block: zz-scale adjoint
-  double* partial2;      // per A2 block: kNGrad - 1 constant adjoints
+  double* partial2;      // per A2 block: kA2 constant adjoints (slot order without G_ZZ)
   int accumulate;        // add this step's block sums to the partials (a rollout) instead of storing them
 };
 
@@ -121,7 +125,7 @@ __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double r
 
 // psi^2(rho) and its derivatives w.r.t. rho and the alpha-dependent constants (eos_dev.cuh)
 __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, double* dc) {
-  for (int k = 0; k < kNGrad - 1; ++k) dc[k] = 0.0;
+  for (int k = 0; k < kA2; ++k) dc[k] = 0.0;
   const long long rb = dbits(rho);
   const bool vap = rb <= e.bits_rho_v, liq = rb >= e.bits_rho_l;
   if (e.mode == 2 && !vap && !liq) {  // Peng cubic loop: no alpha-dependent constants
@@ -138,6 +142,10 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
     const double r3 = r * r * r;
     const double Z = num * r3;
     const double dZ = e.b4 * (4.0 + eta * (4.0 - 2.0 * eta)) * r3 * r;
+    // psi^2 = rho (k1 Z + k2 rho + k3) + k4 (k4 of the vapour branch is 0)
+    dc[a2_index(use_v ? G_K1V : G_K1L)] = rho * Z;
+    dc[a2_index(use_v ? G_K2V : G_K2L)] = rho * rho;
+    if (!use_v) dc[a2_index(G_K4L)] = 1.0;
     return fma(k1, Z, fma(k2, rho, e.k3)) + rho * fma(k1, dZ, k2);
   }
   const double s = e.psi2_scale;
@@ -147,23 +155,23 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
     const double s1 = fast_sqrt(fma(-d * d, e.inv_a1sq, 1.0));
     const double q = e.b1 * d * fast_rcp(s1);
     dp = -q * e.inv_a1sq;
-    dc[G_PMAX] = s;
-    dc[G_B1] = s * (s1 - 1.0);
-    dc[G_IA1] = -0.5 * s * q * d;
+    dc[a2_index(G_PMAX)] = s;
+    dc[a2_index(G_B1)] = s * (s1 - 1.0);
+    dc[a2_index(G_IA1)] = -0.5 * s * q * d;
   } else if (rb < e.bits_rho_min) {
     const double t = (rho - e.rho_max) * e.inv_span;
     dp = (3.0 * e.a2 * t + 2.0 * e.b2) * t * e.inv_span;
-    dc[G_PMAX] = s;
-    dc[G_A2] = s * t * t * t;
-    dc[G_B2] = s * t * t;
+    dc[a2_index(G_PMAX)] = s;
+    dc[a2_index(G_A2)] = s * t * t * t;
+    dc[a2_index(G_B2)] = s * t * t;
   } else {
     const double d = rho - e.rho_min;
     const double s3 = fast_sqrt(fma(-d * d, e.inv_a3sq, 1.0));
     const double q = e.b3 * d * fast_rcp(s3);
     dp = q * e.inv_a3sq;
-    dc[G_PMIN] = s;
-    dc[G_B3] = s * (1.0 - s3);
-    dc[G_IA3] = 0.5 * s * q * d;
+    dc[a2_index(G_PMIN)] = s;
+    dc[a2_index(G_B3)] = s * (1.0 - s3);
+    dc[a2_index(G_IA3)] = 0.5 * s * q * d;
   }
   return s * (dp - 1.0 / 3.0);
 }
@@ -271,9 +279,11 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
   load_gbar_tile(g, sx, sy, x0, y0);
   __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  double dcsum[kNGrad - 1];
-  for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = 0.0;
-  bool shaped = false;  // this node's density lies on a branch with alpha-dependent constants
+  double dcsum[kA2];
+  for (int k = 0; k < kA2; ++k) dcsum[k] = 0.0;
+  // which constants this node's branch uses: the shaped loop's, the vapour C-S's
+  // or the liquid C-S's
+  bool shaped = false, vap_side = false, liq_side = false;
   if (x < a.nx && y < a.ny) {
     const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
     // transpose of g = 12 sum_c w_c psi(x + c) c, gathered at this node y
@@ -284,14 +294,19 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     const double psi_b = g.bar[3 * N + node] + pg;
     const double rho = a.mom[node];
     const double psi = a.psi[node];
-    double dc[kNGrad - 1];
+    double dc[kA2];
     const double dpsi2 = psi2_grad(a.eos, rho, dc);
     const double psi2_b = 0.5 * psi_b * fast_rcp(psi);  // psi = sqrt(psi^2) > 0 (checked by the step)
     const double rho_b = g.bar[node] + psi2_b * dpsi2;
     const long long rb = dbits(rho);
-    shaped = a.eos.mode == 1 && rb > a.eos.bits_rho_v && rb < a.eos.bits_rho_l;
-    if (shaped)
-      for (int k = 0; k < kNGrad - 1; ++k) dcsum[k] = psi2_b * dc[k];
+    const bool vap = rb <= a.eos.bits_rho_v, liq = rb >= a.eos.bits_rho_l;
+    // as in psi2_grad: C-S (shape 0) uses the liquid constants everywhere, the Peng
+    // loop (2) outside (rho_v, rho_l), the shaped EOS (1) on its liquid branch
+    const int m = a.eos.mode;
+    shaped = m == 1 && !vap && !liq;
+    vap_side = m == 1 && vap;
+    liq_side = m == 0 || (m == 2 && (vap || liq)) || (m == 1 && liq);
+    for (int k = 0; k < kA2; ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
     double* L0 = g.lam0;
     L0[node] = rho_b;
@@ -305,17 +320,21 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     L0[8 * N + node] = rho_b + jxb - jyb;
   }
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-  double* dst = g.partial2 + (int64_t)blk * (kNGrad - 1);
-  // block-uniform: a block with no node on a shaped branch adds exact zeros
-  if (!__syncthreads_or(shaped)) {
-    if (!g.accumulate && threadIdx.x == 0 && threadIdx.y == 0)
-      for (int k = 0; k < kNGrad - 1; ++k) dst[k] = 0.0;
-    return;
-  }
-  for (int k = 0; k < kNGrad - 1; ++k) {
-    const double s = block_sum(dcsum[k], red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) dst[k] = g.accumulate ? dst[k] + s : s;
-  }
+  double* dst = g.partial2 + (int64_t)blk * kA2;
+  // Block-uniform tests: a group of constants that no node of the block uses adds
+  // exact zeros, so its reductions are skipped.
+  const bool any_shaped = __syncthreads_or(shaped);
+  const bool any_vap = __syncthreads_or(vap_side);
+  const bool any_liq = __syncthreads_or(liq_side);
+  auto group = [&](int k0, int k1, bool used) {
+    for (int k = k0; k < k1; ++k) {
+      const double s = used ? block_sum(dcsum[k], red) : 0.0;
+      if (threadIdx.x == 0 && threadIdx.y == 0) dst[k] = g.accumulate ? dst[k] + s : s;
+    }
+  };
+  group(a2_index(G_PMAX), a2_index(G_IA3) + 1, any_shaped);
+  group(a2_index(G_K1V), a2_index(G_K2V) + 1, any_vap);
+  group(a2_index(G_K1L), a2_index(G_K4L) + 1, any_liq);
 }
 
 // grad[k] += sum over blocks, in a fixed order; one block per gradient slot
@@ -325,7 +344,7 @@ __global__ void __launch_bounds__(256) k_adj_reduce(const double* partial1, cons
   const int k = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += 256)
-    acc += k == G_ZZ ? partial1[b] : partial2[(int64_t)b * (kNGrad - 1) + k];
+    acc += k == G_ZZ ? partial1[b] : partial2[(int64_t)b * kA2 + a2_index(k)];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -526,17 +545,18 @@ pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* c, const double* lambda_0,
 pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* d, double c[PPLBM_NGRAD]) {
   if (!d || !c) return PPLBM_ERR_ARG;
   const EosConst e = make_eos_const(*d);
-  const double vals[PPLBM_NGRAD] = {e.p_max, e.b1, e.inv_a1sq, e.a2, e.b2, e.p_min, e.b3, e.inv_a3sq, 0.0};
+  const double vals[PPLBM_NGRAD] = {e.p_max, e.b1, e.inv_a1sq, e.a2, e.b2, e.p_min, e.b3,
+                                    e.inv_a3sq, 0.0, e.k1_v, e.k2_v, e.k1_l, e.k2_l, e.k4_l};
   std::memcpy(c, vals, sizeof(vals));
   return PPLBM_OK;
 }
 
 pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* p, double G, const pplbm_relax* relax,
                                             int32_t which, double h, double dc[PPLBM_NGRAD]) {
-  if (!p || !relax || !dc || which != 0 || !(h > 0.0)) return PPLBM_ERR_ARG;
-  auto at = [&](double alpha, double* out) -> pplbm_status {
+  if (!p || !relax || !dc || which < 0 || which > 2 || !(h > 0.0)) return PPLBM_ERR_ARG;
+  auto at = [&](double v, double* out) -> pplbm_status {
     pplbm_eos_params q = *p;
-    q.alpha = alpha;
+    (which == 0 ? q.alpha : which == 1 ? q.a_vap : q.a_liq) = v;
     pplbm_eos_derived d;
     if (pplbm_status s = pplbm_eos_setup(&q, G, &d)) return s;
     pplbm_eos_grad_constants(&d, out);
@@ -547,7 +567,7 @@ pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* p, double G,
     return PPLBM_OK;
   };
   double a1[PPLBM_NGRAD], a2[PPLBM_NGRAD], b1[PPLBM_NGRAD], b2[PPLBM_NGRAD];
-  const double a0 = p->alpha;
+  const double a0 = which == 0 ? p->alpha : which == 1 ? p->a_vap : p->a_liq;
   if (pplbm_status s = at(a0 + h, a1)) return s;
   if (pplbm_status s = at(a0 - h, a2)) return s;
   if (pplbm_status s = at(a0 + h / 2, b1)) return s;

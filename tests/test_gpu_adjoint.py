@@ -33,11 +33,11 @@ def _state(olat, nx, ny, bc):
     return olat.step(olat.init_equilibrium(rho, ux, uy), 3)
 
 
-def _gpu_alpha_grad(grad, spec_eos, relax):
+def _gpu_alpha_grad(grad, spec_eos, relax, which=0):
     dc = (C.c_double * L.NGRAD)()
     p = spec_eos.c()
     r = relax.c()
-    assert L.lib().pplbm_eos_constant_sensitivity(C.byref(p), -1.0, C.byref(r), 0, 1e-4, dc) == 0
+    assert L.lib().pplbm_eos_constant_sensitivity(C.byref(p), -1.0, C.byref(r), which, 1e-4, dc) == 0
     return float(sum(g * d for g, d in zip(grad, dc)))
 
 
@@ -66,6 +66,13 @@ def test_adjoint_step_matches_oracle_autograd(shape, bc):
     assert normwise(l0.cpu().numpy(), x.grad.numpy()) < 1e-12
     galpha_gpu = _gpu_alpha_grad(grad.tolist(), sim.eos_params, sim.relax)
     assert galpha_gpu == pytest.approx(galpha_cpu, rel=1e-6)
+    # the branch parameters: the GPU's k1, k2, k4 slots against the oracle's a, T, Delta P
+    for wrt, which in (("a_v", 1), ("a_l", 2)):
+        dc_w = A.constants_derivative(*CASE[:4], CASE[4], wrt=wrt)
+        g_cpu = sum(float(c[k].grad) * dc_w[k] for k in A.CONST_NAMES)
+        g_gpu = _gpu_alpha_grad(grad.tolist(), sim.eos_params, sim.relax, which)
+        assert g_cpu != 0.0
+        assert g_gpu == pytest.approx(g_cpu, rel=1e-6), wrt
 
 
 def test_small_rollout_matches_oracle_reference_adjoint():
@@ -182,32 +189,34 @@ def test_adjoint_segment_equals_one_segment_backward():
     sim.close()
 
 
-def test_planar_vapour_density_error_gradient_against_finite_differences():
+@pytest.mark.parametrize("param", ["alpha", "a_vap", "a_liq"])
+def test_planar_vapour_density_error_gradient_against_finite_differences(param):
     """The planar-interface loss: E^2 with E = (rho_v(sim) - rho_v^M)/rho_v^M the
     vapour-density error of Eq. DensityError, after 3,000 steps of the (4, 200)
     planar interface at T_r = 0.5 (Smooth C-S, a = 0.5, a_v = 0.5, alpha = 0.610,
-    the w = 7 row of Table ParamSmooth; tau = 1, Li forcing). d(E^2)/d alpha from
-    the adjoint (sqrt(N) checkpoints) against central differences, h = 1e-6."""
+    the w = 7 row of Table ParamSmooth; tau = 1, Li forcing). d(E^2)/d theta for
+    theta = alpha, a_vap, a_liq from the adjoint (sqrt(N) checkpoints) against
+    central differences, h = 1e-6."""
     nx, ny, nsteps = 4, 200, 3000
-    al0 = 0.610
-    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.5, 0.5, al0)
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.5, 0.5, 0.610)
+    th0 = getattr(eosp, param)
     d = P.eos_setup(eosp)
-    rv, rl = d["rho_v"], d["rho_l"]   # the Maxwell densities do not depend on alpha
+    rv, rl = d["rho_v"], d["rho_l"]   # the Maxwell densities do not depend on theta (fixed T_r)
     rho0 = torch.tensor(I.planar(nx, ny, rv, rl, W=10.0), device="cuda")
-    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps)
+    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps, param=param)
 
     def loss_of(rho):
         return ((rho[0, :].mean() - rv) / rv) ** 2
 
-    alpha = torch.tensor(al0, dtype=torch.float64, requires_grad=True)
-    L0 = loss_of(AD.rollout(rho0, alpha, spec))
+    theta = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    L0 = loss_of(AD.rollout(rho0, theta, spec))
     L0.backward()
 
-    def loss_at(al):
+    def loss_at(v):
         with torch.no_grad():
-            return float(loss_of(AD.rollout(rho0, torch.tensor(al, dtype=torch.float64), spec)))
+            return float(loss_of(AD.rollout(rho0, torch.tensor(v, dtype=torch.float64), spec)))
 
     h = 1e-6
-    fd_alpha = (loss_at(al0 + h) - loss_at(al0 - h)) / (2 * h)
-    assert abs(float(alpha.grad)) > 0
-    assert float(alpha.grad) == pytest.approx(fd_alpha, rel=1e-6)
+    fd = (loss_at(th0 + h) - loss_at(th0 - h)) / (2 * h)
+    assert abs(float(theta.grad)) > 0
+    assert float(theta.grad) == pytest.approx(fd, rel=1e-6)

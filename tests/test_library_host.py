@@ -139,3 +139,37 @@ def test_one_call_setups_reject_missing_fields_without_touching_the_gpu(lib):
                                 None) == L.PPLBM_ERR_ARG
     assert b.value is None
     assert lib.pplbm_adjoint_segment(None, None, 0, None, None, None, None, None, 0) == L.PPLBM_ERR_ARG
+
+
+def test_constant_sensitivity_of_the_bulk_branches_has_closed_forms(lib):
+    """k2 = -(2/G) a and k1 = (2/G) R T with T = T_r T_c(a), T_c proportional to a
+    (Eq. CS, Sec. III.D): dk2/da = -2/G, dk1/da = k1/a on the branch the parameter
+    owns and 0 on the other; alpha moves no bulk constant."""
+    G = -1.0
+    eos = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    relax = P.Relax().c()
+    p = eos.c()
+    d = L.pplbm_eos_derived()
+    assert lib.pplbm_eos_setup(C.byref(p), G, C.byref(d)) == L.PPLBM_OK
+    c = (C.c_double * L.NGRAD)()
+    assert lib.pplbm_eos_grad_constants(C.byref(d), c) == L.PPLBM_OK
+    idx = {n: k for k, n in enumerate(L.GRAD_NAMES)}
+    sens = {}
+    for name, which in L.SENS_PARAMS.items():
+        dc = (C.c_double * L.NGRAD)()
+        assert lib.pplbm_eos_constant_sensitivity(C.byref(p), G, C.byref(relax), which, 1e-4, dc) == L.PPLBM_OK
+        sens[name] = list(dc)
+    assert sens["a_vap"][idx["k2_v"]] == pytest.approx(-2.0 / G, rel=1e-9)
+    assert sens["a_vap"][idx["k1_v"]] == pytest.approx(c[idx["k1_v"]] / eos.a_vap, rel=1e-9)
+    assert sens["a_liq"][idx["k2_l"]] == pytest.approx(-2.0 / G, rel=1e-9)
+    assert sens["a_liq"][idx["k1_l"]] == pytest.approx(c[idx["k1_l"]] / eos.a_liq, rel=1e-9)
+    for k in ("k1_l", "k2_l"):
+        assert abs(sens["a_vap"][idx[k]]) < 1e-9
+    for k in ("k1_v", "k2_v"):
+        assert abs(sens["a_liq"][idx[k]]) < 1e-9
+    for k in ("k1_v", "k2_v", "k1_l", "k2_l", "k4_l"):
+        assert abs(sens["alpha"][idx[k]]) < 1e-9
+    # Delta P = p_sat(a_v) - p_sat(a_l): both parameters move the liquid shift
+    assert abs(sens["a_vap"][idx["k4_l"]]) > 0 and abs(sens["a_liq"][idx["k4_l"]]) > 0
+    dc = (C.c_double * L.NGRAD)()
+    assert lib.pplbm_eos_constant_sensitivity(C.byref(p), G, C.byref(relax), 3, 1e-4, dc) == L.PPLBM_ERR_ARG

@@ -93,3 +93,42 @@ def test_gradient_wrt_alpha_matches_finite_differences():
     h = 1e-4
     fd = (Lalpha(alpha + h) - Lalpha(alpha - h)) / (2 * h)
     assert ad == pytest.approx(fd, rel=1e-5)
+
+
+@pytest.mark.parametrize("wrt", ["a_v", "a_l"])
+def test_gradient_wrt_branch_parameters_matches_finite_differences(wrt):
+    """d loss / d a_v and d a_l: the vapour branch C-S(a_v, T_v), the liquid branch
+    C-S(a_l, T_l) + Delta P and the shaped loop all move with them (Sec. III.D, the
+    higher vapour sound speed variant); the Maxwell densities do not (fixed T_r)."""
+    nx, ny, steps = 12, 12, 6
+    base = {"a_l": CASE[2], "a_v": CASE[3]}
+
+    def make(v):
+        args = dict(base)
+        args[wrt] = v
+        e = E.make_eos(CASE[0], CASE[1], args["a_l"], args["a_v"], CASE[4])
+        e.solve_eps(n=40000)
+        return L.Lattice(nx, ny, PER, e, L.Relax(sigma=e.sigma()))
+
+    lat = make(base[wrt])
+    e = lat.eos
+    rho0 = I.perturbed(I.droplet(nx, ny, 3.0, e.rho_v, e.rho_l, W=4.0), 0.01, 4)
+    c = A.constants_as_tensors(e)
+    g = torch.tensor(lat.init_equilibrium(rho0))
+    for _ in range(steps):
+        g = A.step(g, lat, c)
+    loss = A.droplet_loss(g.sum(0), e.rho_v, e.rho_l, 3.0)
+    loss.backward()
+    dc = A.constants_derivative(CASE[0], CASE[1], base["a_l"], base["a_v"], CASE[4], wrt=wrt)
+    ad = sum(float(c[k].grad) * dc[k] for k in A.CONST_NAMES)
+
+    def Lv(v):
+        lt = make(v)
+        assert lt.eos.rho_v == pytest.approx(e.rho_v, rel=1e-12)
+        rho = lt.step(lt.init_equilibrium(rho0), steps).sum(0)
+        return float(A.droplet_loss(torch.tensor(rho), e.rho_v, e.rho_l, 3.0))
+
+    h = 1e-4
+    fd = (Lv(base[wrt] + h) - Lv(base[wrt] - h)) / (2 * h)
+    assert ad != 0.0
+    assert ad == pytest.approx(fd, rel=1e-5)
