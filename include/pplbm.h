@@ -251,6 +251,12 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t
 pplbm_status pplbm_adjoint_segment(pplbm_ctx* ctx, const double* f_start, int64_t nsteps, double* states,
                                    const double* lambda_end, double* lambda_start, double* grad,
                                    void* adj_workspace, size_t adj_workspace_bytes);
+/* Selects the gradient slots the adjoint calls accumulate: bit k of mask set =
+ * slot k (of PPLBM_NGRAD) is computed; the others are left unchanged (0 when grad
+ * starts at 0). Default: all slots. A caller that chains to one parameter can
+ * clear the slots whose dc/dtheta is 0 (for alpha: the five C-S branch constants)
+ * and skip their reductions. PPLBM_ERR_ARG for bits at or above PPLBM_NGRAD. */
+pplbm_status pplbm_adjoint_set_slots(pplbm_ctx* ctx, uint32_t mask);
 /* rho0_bar = sum_i w_i lambda_0[i]: the gradient w.r.t. the initial density of
  * f^0 = f^eq(rho0, u = 0) (Sec. III.A). */
 pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* ctx, const double* lambda_0, double* rho0_bar);

@@ -69,9 +69,12 @@ def _rollout_forward(spec: RolloutSpec, rho0, value: float):
     return sim, ckpt, rhoN
 
 
-def _rollout_backward(spec: RolloutSpec, sim: Simulation, ckpt, grad_rhoN):
+def _rollout_backward(spec: RolloutSpec, sim: Simulation, ckpt, grad_rhoN, slots=None):
+    """Reverse pass; slots: the gradient slots to accumulate (bit mask), None = all."""
     import torch
 
+    if slots is not None:
+        sim._check(L.lib().pplbm_adjoint_set_slots(sim.ctx, int(slots)))
     K = spec.k()
     dev = sim.device
     lamN = grad_rhoN.to(dev, torch.float64).reshape(1, spec.ny, spec.nx).expand(9, spec.ny, spec.nx).contiguous()
@@ -103,8 +106,10 @@ def _make_function():
         @staticmethod
         def backward(ctx, grad_rhoN):
             spec = ctx.spec
-            rho0_bar, grad, _ = _rollout_backward(spec, ctx.sim, ctx.ckpt, grad_rhoN.contiguous())
-            dc = torch.tensor(param_sensitivity(spec, ctx.theta), dtype=torch.float64, device=grad.device)
+            dc_list = param_sensitivity(spec, ctx.theta)
+            mask = sum(1 << k for k, v in enumerate(dc_list) if v != 0.0)  # slots theta moves
+            rho0_bar, grad, _ = _rollout_backward(spec, ctx.sim, ctx.ckpt, grad_rhoN.contiguous(), mask)
+            dc = torch.tensor(dc_list, dtype=torch.float64, device=grad.device)
             gtheta = (grad * dc).sum()
             ctx.sim.close()
             return rho0_bar, gtheta.to(grad_rhoN.dtype), None

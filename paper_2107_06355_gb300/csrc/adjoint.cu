@@ -50,7 +50,11 @@ struct AdjArgs {
   double* partial1;      // per A1 block: zz-scale adjoint
   double* partial2;      // per A2 block: kA2 constant adjoints (slot order without G_ZZ)
   int accumulate;        // add this step's block sums to the partials (a rollout) instead of storing them
+  unsigned slots;        // bit k set: gradient slot k is accumulated (others stay 0)
 };
+
+// bits of the slots [k0, k1] of a group
+__host__ __device__ constexpr unsigned slot_bits(int k0, int k1) { return ((2u << k1) - 1u) & ~((1u << k0) - 1u); }
 
 // reverse mode of collide_reduced<kUnitTau> (see its comments for the forward)
 __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double rho, double jx, double jy, double psi0,
@@ -142,10 +146,14 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
     const double r3 = r * r * r;
     const double Z = num * r3;
     const double dZ = e.b4 * (4.0 + eta * (4.0 - 2.0 * eta)) * r3 * r;
-    // psi^2 = rho (k1 Z + k2 rho + k3) + k4 (k4 of the vapour branch is 0)
-    dc[a2_index(use_v ? G_K1V : G_K1L)] = rho * Z;
-    dc[a2_index(use_v ? G_K2V : G_K2L)] = rho * rho;
-    if (!use_v) dc[a2_index(G_K4L)] = 1.0;
+    // psi^2 = rho (k1 Z + k2 rho + k3) + k4 (k4 of the vapour branch is 0); constant
+    // indices only, so dc stays in registers
+    const double rz = rho * Z, rr = rho * rho;
+    dc[a2_index(G_K1V)] = use_v ? rz : 0.0;
+    dc[a2_index(G_K2V)] = use_v ? rr : 0.0;
+    dc[a2_index(G_K1L)] = use_v ? 0.0 : rz;
+    dc[a2_index(G_K2L)] = use_v ? 0.0 : rr;
+    dc[a2_index(G_K4L)] = use_v ? 0.0 : 1.0;
     return fma(k1, Z, fma(k2, rho, e.k3)) + rho * fma(k1, dZ, k2);
   }
   const double s = e.psi2_scale;
@@ -240,7 +248,7 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
     B[4 * N + node] = gxb;
     B[5 * N + node] = gyb;
   }
-  const double s = block_sum(zs_b, red);
+  const double s = (g.slots >> G_ZZ) & 1u ? block_sum(zs_b, red) : 0.0;  // grid-uniform test
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     double* dst = g.partial1 + blockIdx.y * gridDim.x + blockIdx.x;
     *dst = g.accumulate ? *dst + s : s;
@@ -303,10 +311,16 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     // as in psi2_grad: C-S (shape 0) uses the liquid constants everywhere, the Peng
     // loop (2) outside (rho_v, rho_l), the shaped EOS (1) on its liquid branch
     const int m = a.eos.mode;
-    shaped = m == 1 && !vap && !liq;
-    vap_side = m == 1 && vap;
-    liq_side = m == 0 || (m == 2 && (vap || liq)) || (m == 1 && liq);
-    for (int k = 0; k < kA2; ++k) dcsum[k] = psi2_b * dc[k];
+    shaped = m == 1 && !vap && !liq && (g.slots & slot_bits(G_PMAX, G_IA3));
+    vap_side = m == 1 && vap && (g.slots & slot_bits(G_K1V, G_K2V));
+    liq_side = (m == 0 || (m == 2 && (vap || liq)) || (m == 1 && liq)) && (g.slots & slot_bits(G_K1L, G_K4L));
+    // only the group this node's branch uses is non-zero (constant loop bounds)
+    if (shaped)
+      for (int k = a2_index(G_PMAX); k <= a2_index(G_IA3); ++k) dcsum[k] = psi2_b * dc[k];
+    if (vap_side)
+      for (int k = a2_index(G_K1V); k <= a2_index(G_K2V); ++k) dcsum[k] = psi2_b * dc[k];
+    if (liq_side)
+      for (int k = a2_index(G_K1L); k <= a2_index(G_K4L); ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
     double* L0 = g.lam0;
     L0[node] = rho_b;
@@ -328,7 +342,8 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
   const bool any_liq = __syncthreads_or(liq_side);
   auto group = [&](int k0, int k1, bool used) {
     for (int k = k0; k < k1; ++k) {
-      const double s = used ? block_sum(dcsum[k], red) : 0.0;
+      const int slot = k < G_ZZ ? k : k + 1;
+      const double s = used && ((g.slots >> slot) & 1u) ? block_sum(dcsum[k], red) : 0.0;
       if (threadIdx.x == 0 && threadIdx.y == 0) dst[k] = g.accumulate ? dst[k] + s : s;
     }
   };
@@ -392,6 +407,7 @@ pplbm_status adjoint_core(pplbm_ctx* c, const StepArgs& a, const double* lam1, d
   g.partial1 = ws + 24 * c->n;
   g.partial2 = g.partial1 + nb;
   g.accumulate = accumulate ? 1 : 0;
+  g.slots = c->adj_slots;
   const dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY), block(kTX, kTY);
   k_adj_collide<<<grid, block, 0, c->stream>>>(g);
   k_adj_rho_psi<<<grid, block, 0, c->stream>>>(g);
@@ -533,6 +549,12 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
   if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   if (cudaMemcpyAsync(lambda_0, cur, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
     return PPLBM_ERR_CUDA;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_adjoint_set_slots(pplbm_ctx* c, uint32_t mask) {
+  if (!c || (mask >> kNGrad) != 0u) return PPLBM_ERR_ARG;
+  c->adj_slots = mask;
   return PPLBM_OK;
 }
 

@@ -34,4 +34,5 @@ struct pplbm_ctx {
   bool timing;
   std::vector<cudaEvent_t> ev[2];  // per kernel: start/stop interleaved
   size_t ev_used[2];
+  uint32_t adj_slots = ~0u;  // adjoint: bit k set = gradient slot k is accumulated
 };

@@ -220,3 +220,28 @@ def test_planar_vapour_density_error_gradient_against_finite_differences(param):
     fd = (loss_at(th0 + h) - loss_at(th0 - h)) / (2 * h)
     assert abs(float(theta.grad)) > 0
     assert float(theta.grad) == pytest.approx(fd, rel=1e-6)
+
+
+def test_slot_mask_skips_only_the_deselected_gradients():
+    """pplbm_adjoint_set_slots: the selected slots are bitwise those of the full
+    computation, the others stay 0; lambda does not depend on the mask."""
+    nx, ny = 40, 18
+    olat, sim = make_pair(nx, ny, BC_PER, CASE, {})
+    f = torch.tensor(_state(olat, nx, ny, BC_PER), device="cuda")
+    l1 = torch.tensor(np.random.default_rng(12).standard_normal((9, ny, nx)), device="cuda")
+    nbytes = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
+    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    alpha_slots = sum(1 << k for k in range(9))
+    res = []
+    for mask in ((1 << L.NGRAD) - 1, alpha_slots):
+        assert L.lib().pplbm_adjoint_set_slots(sim.ctx, mask) == 0
+        l0 = torch.empty_like(l1)
+        grad = torch.zeros(L.NGRAD, dtype=torch.float64, device="cuda")
+        ws = torch.empty(nbytes // 8 + 1, dtype=torch.float64, device="cuda")
+        assert L.lib().pplbm_adjoint_step(sim.ctx, p(f), p(l1), p(l0), p(grad), p(ws), nbytes) == 0
+        torch.cuda.synchronize()
+        res.append((l0.cpu(), grad.cpu()))
+    assert torch.equal(res[0][0], res[1][0])
+    assert torch.equal(res[0][1][:9], res[1][1][:9])
+    assert torch.all(res[1][1][9:] == 0) and torch.any(res[0][1][9:] != 0)
+    assert L.lib().pplbm_adjoint_set_slots(sim.ctx, 1 << L.NGRAD) == L.PPLBM_ERR_ARG
