@@ -417,13 +417,31 @@ def adjoint_cost(torch, steps=2000, interval=45):
                                                                               nb), sim.ctx))
             res = (t_f, t_b)
         out[label] = res
+    # the same rollout with every step's psi and moments kept (4 planes x 2,000 steps =
+    # 4.2 GB): no recomputation in the reverse pass
+    L.check(lib.pplbm_adjoint_set_slots(sim.ctx, alpha_slots), sim.ctx)
+    fields = torch.empty((steps, 4, ny, nx), dtype=torch.float64, device=dev)
+    res = []
+    for _ in range(2):
+        sim.init_equilibrium(rho0)
+        t_f = time_device(torch, torch.cuda.current_stream(),
+                          lambda: L.check(lib.pplbm_forward_stored(sim.ctx, steps, p(fields)), sim.ctx))
+        t_b = time_device(torch, torch.cuda.current_stream(),
+                          lambda: L.check(lib.pplbm_backward_stored(sim.ctx, steps, p(fields), p(lam), p(lam0),
+                                                                    p(grad), p(ws), nb), sim.ctx))
+        res = (t_f, t_b)
+    out["stored"] = res
+    del fields
     sim.close()
     f_ms, b_ms = out["alpha"]
     return {"config": f"256x256 droplet R=48, T_r=0.5, {steps} steps, checkpoint interval {interval}, "
                       "gradients w.r.t. rho0 and alpha",
             "forward_ms": f_ms, "backward_ms": b_ms, "adjoint_over_forward": b_ms / f_ms,
             "forward_mlups": nx * ny * steps / (f_ms / 1e3) / 1e6,
-            "adjoint_over_forward_all_slots": out["all_slots"][1] / out["all_slots"][0]}
+            "adjoint_over_forward_all_slots": out["all_slots"][1] / out["all_slots"][0],
+            "stored_fields": {"forward_ms": out["stored"][0], "backward_ms": out["stored"][1],
+                              "adjoint_over_forward": out["stored"][1] / out["stored"][0],
+                              "bytes": 32 * nx * ny * steps}}
 
 
 def eos_variant_throughput(torch, steps=1000):

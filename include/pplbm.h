@@ -251,6 +251,15 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t
 pplbm_status pplbm_adjoint_segment(pplbm_ctx* ctx, const double* f_start, int64_t nsteps, double* states,
                                    const double* lambda_end, double* lambda_start, double* grad,
                                    void* adj_workspace, size_t adj_workspace_bytes);
+/* Rollouts whose fields fit in device memory (4 planes per step: psi, rho, jx, jy;
+ * 2,000 steps of a 256^2 lattice take 4.2 GB): pplbm_forward_stored advances nsteps
+ * like pplbm_step, its density passes writing psi and the moments of f^t into
+ * fields + 4*nx*ny*t (nsteps slots, device); pplbm_backward_stored then runs the
+ * adjoint steps t = nsteps-1 ... 0 from those slots, with no recomputation and no
+ * density pass of its own. Results are bitwise those of the checkpointed pair. */
+pplbm_status pplbm_forward_stored(pplbm_ctx* ctx, int64_t nsteps, double* fields);
+pplbm_status pplbm_backward_stored(pplbm_ctx* ctx, int64_t nsteps, const double* fields, const double* lambda_N,
+                                   double* lambda_0, double* grad, void* adj_workspace, size_t adj_workspace_bytes);
 /* Selects the gradient slots the adjoint calls accumulate: bit k of mask set =
  * slot k (of PPLBM_NGRAD) is computed; the others are left unchanged (0 when grad
  * starts at 0). Default: all slots. A caller that chains to one parameter can

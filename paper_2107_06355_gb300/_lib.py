@@ -130,6 +130,8 @@ _SIGS = {
     "pplbm_batch_instance_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "pplbm_batch_guard": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "pplbm_adjoint_set_slots": (C.c_int, [_P, C.c_uint32]),
+    "pplbm_forward_stored": (C.c_int, [_P, C.c_int64, _P]),
+    "pplbm_backward_stored": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_size_t]),
     "pplbm_init": (C.c_int, [C.POINTER(_P), C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),
                              C.POINTER(pplbm_relax), C.c_double, _P, _P, _P, _P, C.c_size_t, _P]),
     "pplbm_batch_init": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),

@@ -1,9 +1,11 @@
 """torch.autograd.Function over a checkpointed rollout of the CUDA step.
 
-Forward: f^0 = f^eq(rho0, 0), nsteps steps through pplbm_forward_checkpointed
-(checkpoints every `interval` steps, ~sqrt(nsteps)), output rho^N. Backward:
-pplbm_backward_checkpointed (segment recomputation + hand-written adjoint
-kernels) gives dL/df^0 and dL/d(EOS constants); the initial-density gradient is
+Forward: f^0 = f^eq(rho0, 0), nsteps steps through pplbm_forward_stored (every
+step's psi and moments kept, when they fit in device memory) or
+pplbm_forward_checkpointed (checkpoints every `interval` steps, ~sqrt(nsteps)),
+output rho^N. Backward: pplbm_backward_stored, or pplbm_backward_checkpointed
+(segment recomputation), then the hand-written adjoint kernels give dL/df^0 and
+dL/d(EOS constants); the initial-density gradient is
 sum_i w_i dL/df^0_i and the parameter gradient (alpha, a_vap or a_liq, chosen by
 RolloutSpec.param) chains the constants' gradients with their derivatives
 (pplbm_eos_constant_sensitivity). Argument marshalling only: every step runs in
@@ -27,12 +29,24 @@ class RolloutSpec:
     eos: EOSParams          # the differentiated parameter is taken from the Function's input
     relax: Relax
     nsteps: int
-    interval: int = 0       # 0: ceil(sqrt(nsteps))
+    interval: int = 0       # > 0: checkpoints every `interval` steps; 0: automatic (see `stored`)
     G: float = -1.0
     param: str = "alpha"    # "alpha", "a_vap" or "a_liq"
+    memory_fraction: float = 0.25  # automatic mode: share of free device memory the stored fields may take
 
     def k(self):
         return self.interval if self.interval > 0 else max(1, math.ceil(math.sqrt(self.nsteps)))
+
+    def stored(self):
+        """Keep every step's psi and moments (no recomputation) when the interval is
+        automatic and 4 nx ny nsteps doubles fit in memory_fraction of the free device
+        memory; otherwise sqrt(N) checkpointing with recomputation."""
+        if self.interval > 0:
+            return False
+        import torch
+
+        free, _ = torch.cuda.mem_get_info()
+        return 32 * self.nx * self.ny * max(1, self.nsteps) <= self.memory_fraction * free
 
 
 def param_sensitivity(spec: RolloutSpec, value: float, h: float = 1e-4):
@@ -61,10 +75,15 @@ def _rollout_forward(spec: RolloutSpec, rho0, value: float):
 
     sim = Simulation(spec.nx, spec.ny, spec.bc, _with_param(spec, value), spec.relax, G=spec.G)
     sim.init_equilibrium(rho0)
-    K = spec.k()
-    nseg = max(1, -(-spec.nsteps // K))
-    ckpt = torch.empty((nseg, 9, spec.ny, spec.nx), dtype=torch.float64, device=sim.device)
-    sim._check(L.lib().pplbm_forward_checkpointed(sim.ctx, spec.nsteps, K, _ptr(ckpt)))
+    if spec.stored():
+        # ckpt holds every step's psi and moments
+        ckpt = torch.empty((max(1, spec.nsteps), 4, spec.ny, spec.nx), dtype=torch.float64, device=sim.device)
+        sim._check(L.lib().pplbm_forward_stored(sim.ctx, spec.nsteps, _ptr(ckpt)))
+    else:
+        K = spec.k()
+        nseg = max(1, -(-spec.nsteps // K))
+        ckpt = torch.empty((nseg, 9, spec.ny, spec.nx), dtype=torch.float64, device=sim.device)
+        sim._check(L.lib().pplbm_forward_checkpointed(sim.ctx, spec.nsteps, K, _ptr(ckpt)))
     rhoN = sim.fields()[0]
     return sim, ckpt, rhoN
 
@@ -75,16 +94,20 @@ def _rollout_backward(spec: RolloutSpec, sim: Simulation, ckpt, grad_rhoN, slots
 
     if slots is not None:
         sim._check(L.lib().pplbm_adjoint_set_slots(sim.ctx, int(slots)))
-    K = spec.k()
     dev = sim.device
     lamN = grad_rhoN.to(dev, torch.float64).reshape(1, spec.ny, spec.nx).expand(9, spec.ny, spec.nx).contiguous()
-    seg = torch.empty((K, 9, spec.ny, spec.nx), dtype=torch.float64, device=dev)
     lam0 = torch.empty((9, spec.ny, spec.nx), dtype=torch.float64, device=dev)
     grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
     nbytes = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
     ws = torch.empty(nbytes // 8 + 1, dtype=torch.float64, device=dev)
-    sim._check(L.lib().pplbm_backward_checkpointed(sim.ctx, spec.nsteps, K, _ptr(ckpt), _ptr(seg), _ptr(lamN),
-                                                   _ptr(lam0), _ptr(grad), _ptr(ws), nbytes))
+    if ckpt.shape[1] == 4:   # stored fields of every step
+        sim._check(L.lib().pplbm_backward_stored(sim.ctx, spec.nsteps, _ptr(ckpt), _ptr(lamN), _ptr(lam0),
+                                                 _ptr(grad), _ptr(ws), nbytes))
+    else:
+        K = spec.k()
+        seg = torch.empty((K, 9, spec.ny, spec.nx), dtype=torch.float64, device=dev)
+        sim._check(L.lib().pplbm_backward_checkpointed(sim.ctx, spec.nsteps, K, _ptr(ckpt), _ptr(seg), _ptr(lamN),
+                                                       _ptr(lam0), _ptr(grad), _ptr(ws), nbytes))
     rho0_bar = torch.empty((spec.ny, spec.nx), dtype=torch.float64, device=dev)
     sim._check(L.lib().pplbm_adjoint_initial_density(sim.ctx, _ptr(lam0), _ptr(rho0_bar)))
     sim.sync()

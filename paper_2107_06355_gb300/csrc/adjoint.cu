@@ -552,6 +552,64 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
   return PPLBM_OK;
 }
 
+pplbm_status pplbm_forward_stored(pplbm_ctx* c, int64_t nsteps, double* fields) {
+  if (!c || nsteps < 0 || !fields) return PPLBM_ERR_ARG;
+  if (c->args.kind != kUnitTau) {
+    c->msg = "the adjoint covers unit relaxation times only";
+    return PPLBM_ERR_STATE;
+  }
+  if (c->sticky) return c->sticky;
+  const int64_t n = c->n;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    // the density pass of step t writes psi, rho, j of f^t into slot t, which the
+    // collision pass reads: the same arithmetic as pplbm_step, kept per step
+    StepArgs a = c->args;
+    a.f_in = c->fA;
+    a.f_out = c->fB;
+    a.psi = fields + t * 4 * n;
+    a.mom = a.psi + n;
+    launch_rho_psi(a, c->stream);
+    launch_collide(a, c->stream);
+    std::swap(c->fA, c->fB);
+  }
+  if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
+  c->steps += nsteps;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_backward_stored(pplbm_ctx* c, int64_t nsteps, const double* fields, const double* lambda_N,
+                                   double* lambda_0, double* grad, void* adj_workspace, size_t adj_workspace_bytes) {
+  if (!c || nsteps < 0 || !fields || !lambda_N || !lambda_0 || !grad || !adj_workspace) return PPLBM_ERR_ARG;
+  if (c->args.kind != kUnitTau) {
+    c->msg = "the adjoint covers unit relaxation times only";
+    return PPLBM_ERR_STATE;
+  }
+  if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  const int64_t n = c->n, stride = 9 * n;
+  double* ws = (double*)adj_workspace;
+  double* cur = ws + 6 * n;
+  double* nxt = cur + stride;
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(cur, lambda_N, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
+    return PPLBM_ERR_CUDA;
+  const size_t nb = (size_t)nblocks(c->args);
+  double* partials = ws + 24 * n;
+  if (cudaMemsetAsync(partials, 0, sizeof(double) * nb * kNGrad, s) != cudaSuccess) return PPLBM_ERR_CUDA;
+  for (int64_t t = nsteps - 1; t >= 0; --t) {
+    StepArgs a = c->args;
+    a.psi = const_cast<double*>(fields) + t * 4 * n;
+    a.mom = a.psi + n;
+    if (pplbm_status st = adjoint_core(c, a, cur, nxt, grad, ws, true, false)) return st;
+    std::swap(cur, nxt);
+  }
+  k_adj_reduce<<<kNGrad, 256, 0, s>>>(partials, partials + nb, (int)nb, grad);
+  if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
+  if (cudaMemcpyAsync(lambda_0, cur, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
+    return PPLBM_ERR_CUDA;
+  return PPLBM_OK;
+}
+
 pplbm_status pplbm_adjoint_set_slots(pplbm_ctx* c, uint32_t mask) {
   if (!c || (mask >> kNGrad) != 0u) return PPLBM_ERR_ARG;
   c->adj_slots = mask;

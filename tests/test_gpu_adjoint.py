@@ -245,3 +245,25 @@ def test_slot_mask_skips_only_the_deselected_gradients():
     assert torch.equal(res[0][1][:9], res[1][1][:9])
     assert torch.all(res[1][1][9:] == 0) and torch.any(res[0][1][9:] != 0)
     assert L.lib().pplbm_adjoint_set_slots(sim.ctx, 1 << L.NGRAD) == L.PPLBM_ERR_ARG
+
+
+def test_stored_rollout_equals_checkpointed_rollout_bitwise():
+    """pplbm_forward_stored / pplbm_backward_stored keep every step's psi and
+    moments instead of recomputing them: the gradients are bitwise those of the
+    sqrt(N)-checkpointed pair (the Python rollout picks the stored mode when the
+    interval is automatic and the fields fit)."""
+    nx, ny, nsteps = 40, 36, 30
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    d = P.eos_setup(eosp)
+    rho0 = I.perturbed(I.droplet(nx, ny, 10.0, d["rho_v"], d["rho_l"], W=6.0), 0.002, 21)
+    out = []
+    for interval in (0, 6):
+        spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps, interval=interval)
+        assert spec.stored() == (interval == 0)
+        r0 = torch.tensor(rho0, device="cuda", requires_grad=True)
+        alpha = torch.tensor(0.775, dtype=torch.float64, requires_grad=True)
+        rhoN = AD.rollout(r0, alpha, spec)
+        (rhoN ** 2).sum().backward()
+        out.append((rhoN.detach().cpu(), r0.grad.cpu(), float(alpha.grad)))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
