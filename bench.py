@@ -283,16 +283,18 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    steps_done, t_all = 0, 0.0
+    timed = []
     for k in range(args.warmup + args.steps):
         r = time_oracle_sample(max_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
         if k >= args.warmup:
-            t_all += 1.0
-            steps_done += 1
-            last = r
-    val = last["value"]
+            timed.append(r)
+    last = timed[-1]
+    val = sum(r["value"] for r in timed) / len(timed)   # mean rate over the timed samples
+    nodes = NX * NY * len(RADII)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": nodes / (val * 1e6) * 1e3,   # one step of the whole 4-lattice workload at this rate
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
