@@ -248,8 +248,8 @@ def profile_fd():
 
 def profile_adjoint():
     """Checkpointed forward and reverse pass on a 1024 x 1024 droplet (T_r = 0.5,
-    tau = 1), 12 steps with interval 4: 12 launches of each adjoint kernel on
-    75 MB states (> L2 with the adjoint planes)."""
+    tau = 1), 12 steps with interval 4, gradient slots of alpha: 12 launches of each
+    adjoint kernel on 75 MB states (> L2 with the adjoint planes)."""
     import ctypes as C
     import torch
     import lbm_inputs as I
@@ -271,6 +271,7 @@ def profile_adjoint():
     nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
     ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
     p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    L.check(L.lib().pplbm_adjoint_set_slots(sim.ctx, (1 << 9) - 1), sim.ctx)  # alpha's slots, as in adjoint_cost
     L.check(L.lib().pplbm_forward_checkpointed(sim.ctx, steps, interval, p(ckpt)), sim.ctx)
     L.check(L.lib().pplbm_backward_checkpointed(sim.ctx, steps, interval, p(ckpt), p(seg), p(lam), p(lam0), p(grad),
                                                 p(ws), nb), sim.ctx)
