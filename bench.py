@@ -44,6 +44,9 @@ BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
 # 119, two EOS passes of 27 (the kernels' arithmetic; ncu's sm__inst_executed_pipe_fp64
 # on the 2048 x 1024 grid, profiles/k_fd_update_k_fd_eos_2048x1024.md)
 FD_FP64_PER_POINT = 113 + 119 + 2 * 27
+# FP64 instructions per node of the two-phase (tau(rho), walls) batched passes of the
+# impact sweep (ncu sm__inst_executed_pipe_fp64, profiles/k_batch_shear_tau_impact_sweep.md)
+IMPACT_FP64_PER_NODE = 42.0 + 67.5
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
 # batched pass on this workload, averaged over three launches of an ncu capture of
@@ -487,6 +490,26 @@ def impact_sweep_throughput(torch, steps=2000):
     two-phase tau(rho), T_r in {0.45, ..., 0.75} x v_r in {2, ..., 10}: 35 instances,
     5.25 M nodes, graph plan with divergence isolation. Every run is stable here, so
     all nodes count."""
+    b, n_inst = impact_sweep_batch()
+    b.step(20)
+    ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
+    g = b.guard()
+    stable = int(((np.asarray(b.instance_status()) == 0) & (g[:, 2] == 0)).sum())
+    b.close()
+    nodes = 600 * 250 * n_inst
+    mlups = nodes * steps / (ms / 1e3) / 1e6 if stable == n_inst else None
+    out = {"instances": n_inst, "stable": stable, "nodes": nodes, "steps": steps, "mlups": mlups}
+    if mlups is not None and IMPACT_FP64_PER_NODE is not None:
+        _, sm_max, _ = load_peaks()
+        peak = 2 * 152 * sm_max * 1e6
+        achieved = IMPACT_FP64_PER_NODE * mlups * 1e6
+        out["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "fp64_per_node": IMPACT_FP64_PER_NODE}
+    return out
+
+
+def impact_sweep_batch():
+    """The impact-sweep batch, initialised, on the graph plan: (Batch, instances)."""
     import paper_2107_06355_gb300 as P
     from paper_2107_06355_gb300 import sweeps as SW
 
@@ -507,14 +530,23 @@ def impact_sweep_throughput(torch, steps=2000):
         d = b.derived(i)
         b.init_equilibrium(i, *SW._impact_profile(600, 250, 50, 25, d["rho_v"], d["rho_l"], 0.1, Ws[i]))
     b.set_plan(P.PLAN_GRAPH, 0)
-    b.step(20)
-    ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
-    g = b.guard()
-    stable = int(((np.asarray(b.instance_status()) == 0) & (g[:, 2] == 0)).sum())
+    return b, len(lats)
+
+
+def profile_impact():
+    """The impact-sweep batch (35 lattices 600 x 250, two-phase tau, walls), launches
+    plan, 3 steps: 3 launches of each two-phase batched pass over 5.25 M nodes."""
+    import torch
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    b, _ = impact_sweep_batch()
+    b.set_plan(P.PLAN_LAUNCHES, 0)
+    b.step(3)
+    b.sync()
+    torch.cuda.synchronize()
     b.close()
-    nodes = 600 * 250 * len(lats)
-    return {"instances": len(lats), "stable": stable, "nodes": nodes, "steps": steps,
-            "mlups": nodes * steps / (ms / 1e3) / 1e6 if stable == len(lats) else None}
+    print("profile impact done")
 
 
 def fd_throughput(torch, steps=200):
@@ -560,6 +592,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
     ap.add_argument("--profile-adjoint", action="store_true", help="checkpointed adjoint on 1024 x 1024 (for ncu)")
+    ap.add_argument("--profile-impact", action="store_true", help="3 steps of the impact-sweep batch (for ncu)")
     ap.add_argument("--profile-fd", action="store_true", help="3 steps of the FD solver on 2048 x 1024 (for ncu)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run the four 512x512 droplets through the batched engine (launches plan) for 3 steps and exit")
@@ -570,6 +603,8 @@ def main():
         return profile_batch()
     if args.profile_fd:
         return profile_fd()
+    if args.profile_impact:
+        return profile_impact()
     if args.profile_adjoint:
         return profile_adjoint()
     if args.warmup < 3:
