@@ -340,7 +340,8 @@ def time_device(torch, stream, fn):
 
 
 def sweep_comparison(torch, stream, steps):
-    """64-lattice sweep (seed 210706355): batched engine vs one context per lattice."""
+    """64-lattice sweep (seed 210706355): batched engine vs one context per lattice,
+    the latter as per-instance CUDA graphs (the baseline) and as plain launches."""
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
 
@@ -370,6 +371,34 @@ def sweep_comparison(torch, stream, steps):
     for sim in sims:
         sim.step(2)
     ms_s = time_device(torch, stream, serial)
+
+    # the baseline the batch is measured against: per-instance CUDA graphs of two
+    # steps (pplbm_step only enqueues kernels), replayed one instance after another
+    import ctypes as C
+    from paper_2107_06355_gb300 import _lib as L
+
+    for sim in sims:
+        sim.sync()
+    cs = torch.cuda.Stream()
+    graphs = []
+    for sim in sims:
+        L.check(L.lib().pplbm_set_stream(sim.ctx, C.c_void_p(cs.cuda_stream)), sim.ctx)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cs):
+            sim.step(2)
+        graphs.append(g)
+
+    def serial_graphs():
+        for _ in range(steps // 2):
+            for g in graphs:
+                g.replay()
+
+    cur = torch.cuda.current_stream()
+    for g in graphs:
+        g.replay()
+    ms_g = time_device(torch, cur, serial_graphs) * steps / (2 * (steps // 2))
+    torch.cuda.synchronize()
+    del graphs
     for sim in sims:
         sim.sync()
         sim.close()
@@ -377,10 +406,12 @@ def sweep_comparison(torch, stream, steps):
     return {"instances": len(specs), "nodes": nodes, "steps": steps, "plan": mode,
             "tile_width": plan["tile_width"] or "per-instance",
             "batched_instance_steps_per_s": len(specs) * steps / (ms_b / 1e3),
-            "serial_instance_steps_per_s": len(specs) * steps / (ms_s / 1e3),
+            "serial_instance_steps_per_s": len(specs) * steps / (ms_g / 1e3),
             "batched_mlups": nodes * steps / (ms_b / 1e3) / 1e6,
-            "serial_mlups": nodes * steps / (ms_s / 1e3) / 1e6,
-            "speedup": ms_s / ms_b}
+            "serial_mlups": nodes * steps / (ms_g / 1e3) / 1e6,
+            "serial_baseline": "64 per-instance CUDA graphs of 2 steps, replayed serially",
+            "speedup": ms_g / ms_b,
+            "serial_plain_launches_mlups": nodes * steps / (ms_s / 1e3) / 1e6}
 
 
 def adjoint_cost(torch, steps=2000, interval=45):
