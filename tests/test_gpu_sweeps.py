@@ -104,6 +104,9 @@ def test_table_drop_impact_parameters(sweep, case):
     assert r["width"] == case["w"]
     rel = 0.03 if case in PM else 0.06
     assert r["gamma"] * 1e3 == pytest.approx(case["gamma_e3"], rel=rel)
+    ratio = GOLD["density_ratio_Tr05"].get(case["name"])
+    if ratio is not None:   # Sec. IV.B's simulated density ratios at T_r = 0.5
+        assert r["rho_l"] / r["rho_v"] == pytest.approx(ratio["ratio"], rel=ratio["rel"])
 
 
 ST = GOLD["stability_statements"]

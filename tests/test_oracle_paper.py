@@ -43,6 +43,9 @@ def test_planar_interface_reproduces_table(case):
     assert L.interface_width(rho[:, 0], rho_v, rho_l) == case["w"]
     gamma = L.surface_tension_planar(eos.psi(rho[:, 0]), eos.G)
     assert gamma * 1e3 == pytest.approx(case["gamma_e3"], rel=0.06)
+    ratio = GOLD["density_ratio_Tr05"].get(case["name"])
+    if ratio is not None:   # Sec. IV.B's simulated density ratios at T_r = 0.5
+        assert rho_l / rho_v == pytest.approx(ratio["ratio"], rel=ratio["rel"])
 
 
 PM = GOLD["peng_and_modified_smooth"]["cases"]
