@@ -172,6 +172,7 @@ def tune_to_width(families, grid=8, rounds=3, **planar_kw):
     lo = [float(f["lo"]) for f in families]
     hi = [float(f["hi"]) for f in families]
     alive = [True] * nf
+    brackets = [None] * nf   # (p0, w0, p1, w1) of the last round, per family
     for _ in range(rounds):
         cases, owner, params = [], [], []
         for k, f in enumerate(families):
@@ -198,13 +199,13 @@ def tune_to_width(families, grid=8, rounds=3, **planar_kw):
                 alive[k] = False
                 continue
             lo[k], hi[k] = bracket[0], bracket[2]
-            f["_bracket"] = bracket
+            brackets[k] = bracket
     out, cases, owner = [], [], []
     for k, f in enumerate(families):
         if not alive[k]:
             out.append(dict(ok=False))
             continue
-        p0, w0, p1, w1 = f["_bracket"]
+        p0, w0, p1, w1 = brackets[k]
         p = p0 if w1 == w0 else p0 + (f["target"] - w0) * (p1 - p0) / (w1 - w0)
         out.append(dict(ok=True, param=float(p)))
         cases.append(f["make"](float(p)))
@@ -270,6 +271,7 @@ def stability_map(cases, Trs, vrs, steps=4000, check_every=500, u_limit=float("i
         b.init_equilibrium(i, rho, ux, uy)
     b.set_plan(L.PLAN_GRAPH, 0)
     g0 = b.guard()
+    g = g0
     alive = np.ones(len(keys), dtype=bool)
     reason = [None] * len(keys)
     fail_step = [None] * len(keys)
