@@ -173,3 +173,28 @@ def test_constant_sensitivity_of_the_bulk_branches_has_closed_forms(lib):
     assert abs(sens["a_vap"][idx["k4_l"]]) > 0 and abs(sens["a_liq"][idx["k4_l"]]) > 0
     dc = (C.c_double * L.NGRAD)()
     assert lib.pplbm_eos_constant_sensitivity(C.byref(p), G, C.byref(relax), 3, 1e-4, dc) == L.PPLBM_ERR_ARG
+
+
+def _declarations():
+    """{name: parameter count} of every function include/pplbm.h declares."""
+    import os
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(L.HERE), "include", "pplbm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(pplbm_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", hdr):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_bindings_match_the_header_parameter_counts(lib):
+    """Every declared entry point has a ctypes signature with the header's number
+    of parameters, so no call passes its arguments shifted."""
+    decl = _declarations()
+    assert len(decl) >= 60
+    missing = sorted(set(decl) - set(L._SIGS))
+    assert not missing, missing
+    wrong = {n: (k, len(L._SIGS[n][1])) for n, k in decl.items() if len(L._SIGS[n][1]) != k}
+    assert not wrong, wrong
