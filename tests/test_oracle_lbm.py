@@ -179,3 +179,22 @@ def test_two_phase_tau_endpoints():
     assert lam[7, 0] == pytest.approx(1 / (0.5 + 5.0 * 0.1), rel=1e-14)
     assert lam[7, 1] == pytest.approx(1 / 0.6, rel=1e-14)
     assert np.all(lam[:7] == 1.0)
+
+
+@pytest.mark.parametrize("i", [2, 5, 6])
+def test_bounce_back_is_no_slip_for_free_streaming_packets(eos06, i):
+    """Half-way bounce-back (Sec. IV) reverses the whole velocity at a wall, the
+    tangential part included (no slip): a packet streaming freely between the walls
+    is back at its starting node with its starting direction after 2 ny steps,
+    having moved along x and back. (A specular, free-slip wall would carry a
+    diagonal packet 2 ny nodes along x.)"""
+    nx, ny, x0, y0 = 16, 5, 3, 1
+    lat = L.Lattice(nx, ny, WALLS, eos06, L.Relax())
+    f = np.zeros((9, ny, nx))
+    f[i, y0, x0] = 1.0
+    for _ in range(2 * ny):
+        f = lat.stream(f)
+        assert f.sum() == 1.0
+    want = np.zeros_like(f)
+    want[i, y0, x0] = 1.0
+    assert np.array_equal(f, want)

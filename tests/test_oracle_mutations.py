@@ -1,0 +1,152 @@
+"""The oracle's pins, tested against planted mistakes (CPU only).
+
+Each case below plants one plausible error in the oracle with monkeypatch -- a
+dropped term, a wrong sign, a swapped index or weight, a misread formula -- and
+checks that at least one of the oracle's pins then fails. A pin that passes for
+the right and for the wrong arithmetic pins nothing; these cases show the pins
+cover each part of the method (Eq. CS, the Maxwell rule, the shaped EOS, the
+equilibrium, the MRT moments, the Shan-Chen force, the Li and Guo forcing,
+the two-phase relaxation time, the walls)."""
+import numpy as np
+import pytest
+
+from oracle import eos as E
+from oracle import lbm as L
+
+import test_oracle_eos as TE  # noqa: E402
+import test_oracle_fd as TF  # noqa: E402
+import test_oracle_lbm as TL  # noqa: E402
+
+
+def _eos06():
+    e = E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    e.solve_eps()
+    return e
+
+
+def some_pin_fails(*pins):
+    """True if any of the pins fails its assertion (other exceptions propagate, so a
+    mutant that merely breaks is not counted as caught)."""
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            return True
+    return False
+
+
+def test_pins_pass_unmutated():
+    """The same pins pass on the oracle as it stands (the baseline of every case)."""
+    e = _eos06()
+    assert not some_pin_fails(TE.test_critical_point_matches_printed_constants,
+                              lambda: TE.test_maxwell_equals_equal_chemical_potential(0.6),
+                              lambda: TE.test_smooth_junctions_are_C1(e),
+                              TL.test_equilibrium_moments_closed_form,
+                              TL.test_mrt_rows_are_the_velocity_moments,
+                              lambda: TL.test_collision_sigma0_equals_guo_in_population_space(e, (1, 1, 1, 1, 1, 1)),
+                              TL.test_two_phase_tau_endpoints,
+                              lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 5))
+
+
+def test_cs_without_the_cubic_term(monkeypatch):
+    """Eq. CS with (1 + eta + eta^2) instead of (1 + eta + eta^2 - eta^3)."""
+    monkeypatch.setattr(E, "_cs_Z", lambda eta: (1.0 + eta + eta**2) / (1.0 - eta) ** 3)
+    assert some_pin_fails(TE.test_critical_point_matches_printed_constants,
+                          TE.test_cs_derivative_against_central_differences,
+                          TE.test_maxwell_density_ratios_and_psat_match_paper)
+
+
+def test_maxwell_densities_off_by_1e4(monkeypatch):
+    """A Maxwell construction that lands 1e-4 off (e.g. a loose root tolerance)."""
+    orig = E.maxwell
+    monkeypatch.setattr(E, "maxwell", lambda a, b, R, T: (lambda r: (r[0] * (1 + 1e-4), r[1], r[2]))(orig(a, b, R, T)))
+    assert some_pin_fails(lambda: TE.test_maxwell_equals_equal_chemical_potential(0.6))
+
+
+def test_cubic_of_the_shaped_eos_in_unnormalised_rho(monkeypatch):
+    """Region 2's cubic evaluated in rho - rho_max instead of the normalised t."""
+    orig = E.EOS.pressure
+
+    def pressure(self, rho):
+        p = np.atleast_1d(np.array(orig(self, rho), dtype=np.float64))
+        r = np.atleast_1d(np.asarray(rho, dtype=np.float64))
+        if self.mode in (E.MODE_SMOOTH,):
+            m = (r > self.rho_max) & (r < self.rho_min)
+            d = r[m] - self.rho_max
+            p[m] = 2.0 * (self.p_max - self.p_min) * d**3 + 3.0 * (self.p_min - self.p_max) * d**2 + self.p_max
+        return p if np.ndim(rho) else float(p[0])
+
+    monkeypatch.setattr(E.EOS, "pressure", pressure)
+    assert some_pin_fails(lambda: TE.test_smooth_junctions_are_C1(E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)),
+                          lambda: TE.test_smooth_obeys_maxwell_rule_independent_quadrature(
+                              E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)))
+
+
+def test_equilibrium_second_order_coefficient(monkeypatch):
+    """f_eq with 4 instead of 1/(2 c_s^4) = 4.5 in front of (c.u)^2."""
+    def equilibrium(rho, ux, uy):
+        feq = np.empty((9,) + np.shape(rho))
+        for i in range(9):
+            cu = L.C[i, 0] * ux + L.C[i, 1] * uy
+            feq[i] = L.W[i] * rho * (1.0 + 3.0 * cu + 4.0 * cu * cu - 1.5 * (ux * ux + uy * uy))
+        return feq
+
+    monkeypatch.setattr(L, "equilibrium", equilibrium)
+    assert some_pin_fails(TL.test_equilibrium_moments_closed_form)
+
+
+def test_mrt_shear_rows_swapped(monkeypatch):
+    """Rows 7 and 8 of Eq. MatrixMRT exchanged."""
+    M = L.M.copy()
+    M[[7, 8]] = M[[8, 7]]
+    monkeypatch.setattr(L, "M", M)
+    monkeypatch.setattr(L, "MINV", np.linalg.inv(M))
+    assert some_pin_fails(TL.test_mrt_rows_are_the_velocity_moments)
+
+
+def test_shan_chen_weights_swapped(monkeypatch):
+    """w(1) = 1/12, w(2) = 1/3 instead of w(1) = 1/3, w(2) = 1/12 in Eq. ShanChenForce."""
+    w = L.W_SC.copy()
+    w[1:5], w[5:9] = 1.0 / 12.0, 1.0 / 3.0
+    monkeypatch.setattr(L, "W_SC", w)
+    assert some_pin_fails(lambda: TF.test_interface_response_matches_fd((0.8, 0.5, 0.5, 0.342), 0.03))
+
+
+def test_shan_chen_force_sign(monkeypatch):
+    """F = +G psi sum ... instead of -G psi sum ... (Eq. ShanChenForce)."""
+    orig = L.shan_chen_force
+    monkeypatch.setattr(L, "shan_chen_force", lambda *a, **k: tuple(-v for v in orig(*a, **k)))
+    assert some_pin_fails(lambda: TF.test_interface_response_matches_fd((0.8, 0.5, 0.5, 0.342), 0.03))
+
+
+def test_li_term_sign(monkeypatch):
+    """The sigma terms of Eq. LiFS with the opposite sign."""
+    orig = L.li_source
+    monkeypatch.setattr(L, "li_source", lambda ux, uy, Fx, Fy, psi, sigma, te, tz:
+                        orig(ux, uy, Fx, Fy, psi, -sigma, te, tz))
+    assert some_pin_fails(lambda: TF.test_interface_response_matches_fd((0.6, 0.387, 2.0, 0.834), 0.10))
+
+
+def test_forcing_without_the_half_factor(monkeypatch):
+    """m* = m - Lambda (m - m_eq) + S instead of + (I - Lambda/2) S: with Lambda = I
+    this doubles the source (Eq. GFS)."""
+    orig = L.li_source
+    monkeypatch.setattr(L, "li_source", lambda *a: 2.0 * orig(*a))
+    e = _eos06()
+    assert some_pin_fails(lambda: TL.test_collision_sigma0_equals_guo_in_population_space(e, (1, 1, 1, 1, 1, 1)))
+
+
+def test_two_phase_relaxation_times_swapped(monkeypatch):
+    """tau(rho) of Eq. RelaxationTime with tau_v at rho_l and tau_l at rho_v."""
+    orig = L.relaxation_rates
+    monkeypatch.setattr(L, "relaxation_rates", lambda relax, rho, rv, rl: orig(relax, rho, rl, rv))
+    assert some_pin_fails(TL.test_two_phase_tau_endpoints)
+
+
+def test_specular_walls_instead_of_bounce_back(monkeypatch):
+    """Walls that reflect only the normal velocity (free slip) instead of bouncing the
+    populations back (Sec. IV)."""
+    monkeypatch.setattr(L, "OPP", np.array([0, 3, 4, 1, 2, 8, 7, 6, 5]))
+    e = _eos06()
+    assert some_pin_fails(lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 5),
+                          lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 6))
