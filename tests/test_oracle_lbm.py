@@ -198,3 +198,18 @@ def test_bounce_back_is_no_slip_for_free_streaming_packets(eos06, i):
     want = np.zeros_like(f)
     want[i, y0, x0] = 1.0
     assert np.array_equal(f, want)
+
+
+def test_wall_ghosts_exert_no_force_on_their_own_phase(eos06):
+    """Sec. IV: nodes inside the bottom wall carry the saturated liquid density and
+    those inside the top wall the saturated vapour density. A liquid layer on the
+    bottom wall and a vapour layer under the top wall then feel no Shan-Chen force
+    in the rows next to the walls (their stencils see only their own phase)."""
+    nx, ny = 6, 12
+    lat = L.Lattice(nx, ny, WALLS, eos06, L.Relax(sigma=eos06.sigma()))
+    rho = np.full((ny, nx), eos06.rho_v)
+    rho[: ny // 2] = eos06.rho_l
+    *_, Fx, Fy = lat.macroscopic(lat.init_equilibrium(rho))
+    for row in (0, 1, ny - 2, ny - 1):
+        assert np.max(np.abs(Fx[row])) == 0.0 and np.max(np.abs(Fy[row])) < 1e-15 * eos06.rho_l
+    assert np.max(np.abs(Fy[ny // 2 - 1])) > 1e-3   # at the interface the force is not zero

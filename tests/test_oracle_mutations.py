@@ -6,7 +6,7 @@ checks that at least one of the oracle's pins then fails. A pin that passes for
 the right and for the wrong arithmetic pins nothing; these cases show the pins
 cover each part of the method (Eq. CS, the Maxwell rule, the shaped EOS, the
 equilibrium, the MRT moments, the Shan-Chen force, the Li and Guo forcing,
-the two-phase relaxation time, the walls)."""
+the two-phase relaxation time, the walls and their ghost densities)."""
 import numpy as np
 import pytest
 
@@ -45,7 +45,8 @@ def test_pins_pass_unmutated():
                               TL.test_mrt_rows_are_the_velocity_moments,
                               lambda: TL.test_collision_sigma0_equals_guo_in_population_space(e, (1, 1, 1, 1, 1, 1)),
                               TL.test_two_phase_tau_endpoints,
-                              lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 5))
+                              lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 5),
+                              lambda: TL.test_wall_ghosts_exert_no_force_on_their_own_phase(e))
 
 
 def test_cs_without_the_cubic_term(monkeypatch):
@@ -150,3 +151,17 @@ def test_specular_walls_instead_of_bounce_back(monkeypatch):
     e = _eos06()
     assert some_pin_fails(lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 5),
                           lambda: TL.test_bounce_back_is_no_slip_for_free_streaming_packets(e, 6))
+
+
+def test_wall_ghost_densities_swapped(monkeypatch):
+    """The vapour density inside the bottom wall and the liquid density inside the top
+    wall (Sec. IV states the opposite)."""
+    orig = L.Lattice.__post_init__
+
+    def post_init(self):
+        orig(self)
+        self.psi_ghost_bottom, self.psi_ghost_top = self.psi_ghost_top, self.psi_ghost_bottom
+
+    monkeypatch.setattr(L.Lattice, "__post_init__", post_init)
+    e = _eos06()
+    assert some_pin_fails(lambda: TL.test_wall_ghosts_exert_no_force_on_their_own_phase(e))
