@@ -165,3 +165,29 @@ def test_wall_ghost_densities_swapped(monkeypatch):
     monkeypatch.setattr(L.Lattice, "__post_init__", post_init)
     e = _eos06()
     assert some_pin_fails(lambda: TL.test_wall_ghosts_exert_no_force_on_their_own_phase(e))
+
+
+def test_fd_pressure_tensor_epsilon_sign(monkeypatch):
+    """The finite-difference scheme's eps term (App. A, Eq. FDforce) with the wrong sign."""
+    from oracle import fd as F
+
+    class Mutant(F.FDSolver):
+        def __init__(self, eos, eps, *a, **k):
+            super().__init__(eos, -eps, *a, **k)
+
+    monkeypatch.setattr(F, "FDSolver", Mutant)
+    assert some_pin_fails(lambda: TF.test_interface_response_matches_fd((0.6, 0.387, 2.0, 0.834), 0.10),
+                          lambda: TF.test_interface_response_matches_fd((0.8, 0.5, 0.5, 0.342), 0.03))
+
+
+def test_fd_maccormack_with_forward_differences_only(monkeypatch):
+    """A MacCormack corrector that reuses the predictor's forward differences (App. A)."""
+    from oracle import fd as F
+
+    class Mutant(F.FDSolver):
+        def d1(self, a, axis, kind):
+            return super().d1(a, axis, "f" if kind == "b" else kind)
+
+    monkeypatch.setattr(F, "FDSolver", Mutant)
+    assert some_pin_fails(lambda: TF.test_sound_wave_single_phase_matches_fd("liquid"),
+                          lambda: TF.test_interface_response_matches_fd((0.8, 0.5, 0.5, 0.342), 0.03))
