@@ -82,7 +82,9 @@ typedef enum pplbm_status {
 #define PPLBM_FORCING_LI 1   /* Eq. LiFS */
 
 typedef struct pplbm_lattice {
-  int32_t nx, ny;   /* nodes along x and y, each >= 1; 9*nx*ny < 2^31 */
+  int32_t nx, ny;   /* nodes along x and y, each >= 1; 9*nx*ny < 2^31; a single
+                       lattice (pplbm_create) and the FD solver also need
+                       ny <= 524,280 (their 2-D grids); a batch does not */
   uint32_t bc;      /* PPLBM_BC_* flags */
   int32_t reserved; /* must be 0 */
 } pplbm_lattice;

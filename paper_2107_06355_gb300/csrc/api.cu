@@ -50,10 +50,14 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// 8-node rows of tiles on a grid's y axis, at most 65,535 of them
+constexpr int kMaxRows = 65535 * 8;
+
 bool valid_lattice(const pplbm_lattice* l) {
   if (!l || l->nx < 1 || l->ny < 1 || l->reserved != 0) return false;
   const int64_t n = (int64_t)l->nx * l->ny;
   if (9 * n >= (int64_t)1 << 31) return false;
+  if (l->ny > kMaxRows) return false;  // the 2-D grids of the collision and adjoint passes
   if (!(l->bc & PPLBM_BC_PERIODIC_X)) return false;
   const uint32_t walls = l->bc & (PPLBM_BC_WALL_BOTTOM | PPLBM_BC_WALL_TOP);
   if (l->bc & PPLBM_BC_PERIODIC_Y) return walls == 0;

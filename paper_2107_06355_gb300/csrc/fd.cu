@@ -164,7 +164,7 @@ struct pplbm_fd {
 extern "C" {
 
 size_t pplbm_fd_workspace_bytes(const pplbm_lattice* lattice) {
-  if (!lattice || lattice->nx < 1 || lattice->ny < 1) return 0;
+  if (!lattice || lattice->nx < 1 || lattice->ny < 1 || lattice->ny > 65535 * 8) return 0;
   return sizeof(double) * 8 * (size_t)lattice->nx * lattice->ny;
 }
 
@@ -174,6 +174,7 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
   if (!out) return PPLBM_ERR_ARG;
   *out = nullptr;
   if (!lattice || !eos || !workspace || lattice->nx < 1 || lattice->ny < 1 || lattice->reserved != 0) return PPLBM_ERR_ARG;
+  if (lattice->ny > 65535 * 8) return PPLBM_ERR_ARG;  // the update pass's grid: 8-row tiles on its y axis
   if (lattice->bc != (PPLBM_BC_PERIODIC_X | PPLBM_BC_PERIODIC_Y)) return PPLBM_ERR_ARG;
   if (!(tau_nu > 0.5) || !(tau_e > 0.0) || !(dx > 0.0)) return PPLBM_ERR_ARG;
   if (workspace_bytes < pplbm_fd_workspace_bytes(lattice)) return PPLBM_ERR_ARG;

@@ -198,3 +198,17 @@ def test_bindings_match_the_header_parameter_counts(lib):
     assert not missing, missing
     wrong = {n: (k, len(L._SIGS[n][1])) for n, k in decl.items() if len(L._SIGS[n][1]) != k}
     assert not wrong, wrong
+
+
+def test_tall_lattices_are_rejected_where_the_grids_are_two_dimensional(lib):
+    """A single lattice and the FD solver launch 2-D grids with 8-row tiles on the y
+    axis (at most 65,535): ny <= 524,280 there; the batch's 1-D grids take any ny."""
+    relax = P.Relax().c()
+    ok = L.pplbm_lattice(4, 524280, L.BC_PERIODIC, 0)
+    tall = L.pplbm_lattice(4, 524288, L.BC_PERIODIC, 0)
+    assert lib.pplbm_workspace_bytes(C.byref(ok), C.byref(relax)) > 0
+    assert lib.pplbm_workspace_bytes(C.byref(tall), C.byref(relax)) == 0
+    assert lib.pplbm_fd_workspace_bytes(C.byref(ok)) > 0
+    assert lib.pplbm_fd_workspace_bytes(C.byref(tall)) == 0
+    rel = (L.pplbm_relax * 1)(relax)
+    assert lib.pplbm_batch_workspace_bytes(1, (L.pplbm_lattice * 1)(tall), rel) > 0
