@@ -295,3 +295,36 @@ def test_one_call_init_equals_create_then_init_equilibrium():
         assert torch.equal(f, ref.get_f())
     L.lib().pplbm_destroy(ctx)
     ref.close()
+
+
+def test_largest_lattice_matches_the_oracle_on_a_tiled_field():
+    """The largest lattice the library accepts in one context: 16384 x 14560, so that
+    9 nx ny is just below 2^31 (every plane offset past 2^31 bytes; 42 GB of
+    workspace). The initial field repeats one 32 x 32 tile (a perturbed droplet with
+    random velocities), so after three steps every tile equals the oracle's
+    32 x 32 periodic lattice; 4,096 sampled nodes, all nine populations, to 1e-12."""
+    import torch
+    import paper_2107_06355_gb300 as P
+
+    nx, ny, T = 16384, 14560, 32
+    assert 9 * nx * ny < 2**31 <= 9 * nx * (ny + T)
+    olat, _ = make_pair(T, T, BC_PER, SMOOTH06, {})
+    e = olat.eos
+    rho = I.perturbed(I.droplet(T, T, 8.0, e.rho_v, e.rho_l, W=5.0), 0.01, 41)
+    ux, uy = I.random_velocity((T, T), 0.01, 42)
+    fo = olat.step(olat.init_equilibrium(rho, ux, uy), 3)
+    sim = P.Simulation(nx, ny, BC_PER, P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax())
+    tile = lambda a: torch.tensor(a, device="cuda").repeat(ny // T, nx // T)  # noqa: E731
+    sim.init_equilibrium(tile(rho), tile(ux), tile(uy))
+    sim.step(3)
+    f = sim.get_f()
+    g = np.random.default_rng(43)
+    # random nodes plus the first and the last node (the largest plane offsets)
+    ys_h = np.concatenate([g.integers(0, ny, 4094), [0, ny - 1]])
+    xs_h = np.concatenate([g.integers(0, nx, 4094), [0, nx - 1]])
+    got = f[:, torch.tensor(ys_h, device="cuda"), torch.tensor(xs_h, device="cuda")].cpu().numpy()
+    del f
+    sim.close()
+    want = fo[:, ys_h % T, xs_h % T]
+    assert np.isfinite(got).all()
+    assert normwise(got, want) < 1e-12
