@@ -52,7 +52,9 @@ def _build(relax_kw):
     return b, sims
 
 
-@pytest.mark.parametrize("relax_kw", [{}, {"kind": 1, "tau_l": 0.6, "visc_ratio": 2.0}], ids=["unit", "two_phase"])
+@pytest.mark.parametrize("relax_kw", [{}, {"kind": 1, "tau_l": 0.6, "visc_ratio": 2.0},
+                                      {"tau_e": 0.8, "tau_zeta": 1.1, "tau_q": 1.2, "tau_nu": 0.9}],
+                         ids=["unit", "two_phase", "full_mrt"])
 @pytest.mark.parametrize("mode,width", [(0, 0), (0, 4), (0, 32), (0, 256), (1, 0), (2, 0), (2, 8)])
 def test_batch_bitwise_equals_single_lattice(relax_kw, mode, width):
     b, sims = _build(relax_kw)
