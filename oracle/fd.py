@@ -19,8 +19,14 @@ MacCormack predictor/corrector: first derivatives of rho, u, p_EOS and mu in the
 advective, pressure and viscous terms are forward differences in the predictor
 and backward differences in the corrector; second derivatives are central in
 both; every derivative in d_b p'_ab is a second-order central difference.
-Periodic boundaries only (the wall conditions of App. B are not restated).
-Lengths are in lattice units; dx is the FD grid spacing, c = 1.
+Periodic in x; in y periodic, or walls as in the grid-dependency appendix
+(Eqs. B1, B2): at the bottom a layer b1 on the wall with no slip, its density and
+psi extrapolated linearly from the first two fluid rows (rho_b1 = 2 rho_0 - rho_1,
+psi_b1 = 2 psi_0 - psi_1, U = V = 0), and a layer b2 inside the solid with
+psi_b2 = psi_b1 + 2 dy (psi_l - psi_b1); at the top reflexive layers
+(rho_t1 = rho_{N-1}, psi_t1 = psi_{N-1}, U_t1 = -U_{N-1}, V_t1 = -V_{N-1},
+rho_t2 = rho_{N-2} and likewise psi_t2). p_EOS on b1 and t1 is that of their
+density. Lengths are in lattice units; dx is the FD grid spacing, c = 1.
 """
 from __future__ import annotations
 
@@ -33,13 +39,34 @@ def _sh(a, dy, dx):
 
 
 class FDSolver:
-    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0):
+    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0, walls=False):
         self.eos = eos
         self.eps = eps
         self.G = eos.G
         self.dx = dx
         self.tau_nu = tau_nu
         self.tau_e = tau_e
+        self.walls = walls
+
+    def _padded(self, rho, u):
+        """rho, u, psi, p with two ghost rows below and above (Eqs. B1, B2 and the
+        reflexive top layers); rows 2 .. ny+1 are the fluid rows."""
+        psi = self.eos.psi(rho)
+        pad = lambda a: np.concatenate([np.zeros((2,) + a.shape[1:]), a, np.zeros((2,) + a.shape[1:])])  # noqa: E731
+        R, X, Y, S = pad(rho), pad(u[0]), pad(u[1]), pad(psi)
+        psi_l = float(self.eos.psi(self.eos.rho_l))
+        # bottom: b1 (row 1) on the wall, b2 (row 0) inside the solid
+        R[1] = 2.0 * rho[0] - rho[1]
+        S[1] = 2.0 * psi[0] - psi[1]
+        X[1] = 0.0
+        Y[1] = 0.0
+        S[0] = S[1] + 2.0 * self.dx * (psi_l - S[1])
+        R[0] = R[1]        # not used by any stencil
+        # top: reflexive layers t1 (row ny+2) and t2 (row ny+3)
+        R[-2], S[-2], X[-2], Y[-2] = rho[-1], psi[-1], -u[0][-1], -u[1][-1]
+        R[-1], S[-1] = rho[-2], psi[-2]
+        P = self.eos.pressure(R)
+        return R, [X, Y], S, P
 
     # difference operators (axis 0 = y, axis 1 = x)
     def d1(self, a, axis, kind):
@@ -60,11 +87,18 @@ class FDSolver:
 
     def rhs(self, rho, u, kind):
         """Time derivatives (d_t rho, d_t u_x, d_t u_y); kind 'f' (predictor) or 'b' (corrector)."""
+        if self.walls:
+            # derivatives on the padded arrays (np.roll's wrap in y only touches the
+            # ghost rows, whose results are dropped); the fluid rows are kept
+            R, U, S, P = self._padded(rho, u)
+            dr, du = self._rhs(R, U, kind, S, P)
+            return dr[2:-2], [d[2:-2] for d in du]
+        return self._rhs(rho, u, kind, self.eos.psi(rho), self.eos.pressure(rho))
+
+    def _rhs(self, rho, u, kind, psi, p):
         G, eps = self.G, self.eps
         cs2 = 1.0 / 3.0
         axes = (1, 0)  # alpha = x -> axis 1, alpha = y -> axis 0
-        p = self.eos.pressure(rho)
-        psi = self.eos.psi(rho)
         # mass
         div = sum(self.d1(u[a], axes[a], kind) for a in range(2))
         drho = -(rho * div + sum(u[a] * self.d1(rho, axes[a], kind) for a in range(2)))

@@ -79,3 +79,35 @@ def test_interface_response_matches_fd(case, tol):
     mf = rho_eq[:, 0] * (ufp - ufb)
     assert np.max(np.abs(dl - df)) < tol * np.max(np.abs(dl))
     assert np.max(np.abs(ml - mf)) < tol * np.max(np.abs(ml))
+
+
+def test_fd_walls_keep_liquid_at_rest():
+    """With the wall layers of Eqs. B1, B2 and the reflexive top, uniform liquid at
+    rest is a fixed point (every ghost value equals the fluid's, psi_b2 = psi_l)."""
+    e = E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    for dx in (1.0, 0.5):
+        fds = F.FDSolver(e, e.solve_eps(), dx=dx, walls=True)
+        r, u = fds.run(np.full((24, 3), e.rho_l), [np.zeros((24, 3)), np.zeros((24, 3))], 5, 0.2 * dx * dx)
+        assert np.max(np.abs(r - e.rho_l)) == 0.0 and np.max(np.abs(u[0])) == 0.0 and np.max(np.abs(u[1])) == 0.0
+
+
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_fd_walls_are_no_slip_shear_mode_decays_at_the_viscous_rate(dx):
+    """No slip at the bottom layer b1 (y = -dx) and, through the reflexive layer, at
+    (N - 1/2) dx on top: in uniform liquid the shear mode U = sin(pi (y + dx) / L),
+    L = (N + 1/2) dx, decays at nu (pi / L)^2 with nu = (tau_nu - 1/2)/3 (Eq.
+    DynamicViscosity). Liquid next to the walls feels no force (psi is uniform, ghost
+    layers included)."""
+    e = E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    N = int(round(32 / dx))
+    y = np.arange(N) * dx
+    L_ = (N + 0.5) * dx
+    mode = np.sin(np.pi * (y + dx) / L_)
+    fds = F.FDSolver(e, e.solve_eps(), tau_nu=1.0, dx=dx, walls=True)
+    dt = 0.2 * dx * dx
+    U0 = 1e-4 * np.repeat(mode[:, None], 2, axis=1)
+    r, u = fds.run(np.full((N, 2), e.rho_l), [U0, np.zeros((N, 2))], 200, dt)
+    amp = (u[0][:, 0] * mode).sum() / (mode * mode).sum()
+    rate = -np.log(amp / 1e-4) / 200
+    nu = (1.0 - 0.5) / 3.0
+    assert rate == pytest.approx(nu * (np.pi / L_) ** 2, rel=5e-3)

@@ -191,3 +191,19 @@ def test_fd_maccormack_with_forward_differences_only(monkeypatch):
     monkeypatch.setattr(F, "FDSolver", Mutant)
     assert some_pin_fails(lambda: TF.test_sound_wave_single_phase_matches_fd("liquid"),
                           lambda: TF.test_interface_response_matches_fd((0.8, 0.5, 0.5, 0.342), 0.03))
+
+
+def test_fd_bottom_wall_without_no_slip(monkeypatch):
+    """The FD bottom layer b1 keeping the fluid's tangential velocity (a free-slip
+    wall) instead of U_b1 = 0 (Eq. B1)."""
+    from oracle import fd as F
+
+    orig = F.FDSolver._padded
+
+    def padded(self, rho, u):
+        R, U, S, P = orig(self, rho, u)
+        U[0][1] = u[0][0]
+        return R, U, S, P
+
+    monkeypatch.setattr(F.FDSolver, "_padded", padded)
+    assert some_pin_fails(lambda: TF.test_fd_walls_are_no_slip_shear_mode_decays_at_the_viscous_rate(1.0))
