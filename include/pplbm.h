@@ -288,10 +288,18 @@ pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* params, doub
  * only (App. B's wall conditions are not provided). State: rho, u_x, u_y planes
  * (x fastest); grid spacing dx in lattice units; eps is the EOS set-up's. */
 typedef struct pplbm_fd pplbm_fd;
-/* Caller-owned device workspace: 8 planes (state, predictor state, psi, p). */
+/* Caller-owned device workspace: 8 planes (state, predictor state, psi, p) of nx*ny
+ * values, nx*(ny + 4) with walls; 0 for a grid or boundary flags pplbm_fd_create rejects. */
 size_t pplbm_fd_workspace_bytes(const pplbm_lattice* lattice);
-/* lattice->bc must be PPLBM_BC_PERIODIC_X | PPLBM_BC_PERIODIC_Y; tau_nu > 1/2 and
- * tau_e > 0 give mu = rho (tau_nu - 1/2)/3 and mu_B = rho (tau_e - tau_nu)/3. */
+/* lattice->bc is PPLBM_BC_PERIODIC_X | PPLBM_BC_PERIODIC_Y, or PPLBM_BC_PERIODIC_X
+ * with both walls (ny >= 2): the wall layers of the grid-dependency appendix (Eqs.
+ * B1, B2) -- at the bottom a no-slip layer on the wall whose density and psi are
+ * extrapolated linearly from the first two fluid rows and a layer in the solid with
+ * psi_b2 = psi_b1 + 2 dx (psi_l - psi_b1); at the top reflexive layers (density and
+ * psi mirrored, velocity reversed). The fluid rows are at y = 0, dx, ..., and the
+ * bottom wall at y = -dx. tau_nu > 1/2 and tau_e > 0 give mu = rho (tau_nu - 1/2)/3
+ * and mu_B = rho (tau_e - tau_nu)/3. The workspace holds 8 planes of nx*ny values,
+ * nx*(ny + 4) with walls (pplbm_fd_workspace_bytes). */
 pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos, double G,
                              double tau_nu, double tau_e, double dx, void* workspace, size_t workspace_bytes,
                              void* stream);

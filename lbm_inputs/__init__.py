@@ -39,14 +39,15 @@ def droplet(nx, ny, R, rho_v, rho_l, W=8.0, center=None):
     return rho_v + (rho_l - rho_v) * phi
 
 
-def impact(nx, ny, R, film_h, rho_v, rho_l, V_d, W=8.0):
+def impact(nx, ny, R, film_h, rho_v, rho_l, V_d, W=8.0, dx=1.0):
     """Droplet above a liquid film on the bottom wall (Sec. IV set-up).
 
     rho = rho_v + (rho_l - rho_v) max(phi_drop, phi_film); the drop centre is at
-    (nx/2, film_h + R + W); the drop moves with (0, -V_d) weighted by phi_drop.
-    Returns (rho, ux, uy)."""
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
-    cx, cy = nx / 2.0, film_h + R + W
+    (nx dx/2, film_h + R + W); the drop moves with (0, -V_d) weighted by phi_drop.
+    Lengths are in lattice units; node (i, j) sits at (i dx, j dx), so dx < 1 samples
+    the same field on a finer grid. Returns (rho, ux, uy)."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64) * dx
+    cx, cy = nx * dx / 2.0, film_h + R + W
     r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
     phi_d = 0.5 * (1.0 - np.tanh(4.6 * (r - R) / W))
     phi_f = 0.5 * (1.0 - np.tanh(4.6 * (y - film_h) / W))

@@ -14,6 +14,9 @@
 // One MacCormack step = EOS pass (psi, p of U) + predictor pass (U* = U + dt R_f(U))
 // + EOS pass (of U*) + corrector pass (U <- (U + U* + dt R_b(U*)) / 2, in place:
 // the corrector reads U only at its own node).
+// x is periodic; y is periodic or bounded by the wall layers of the grid-dependency
+// appendix (Eqs. B1, B2): every plane then carries two ghost rows below and above
+// the fluid rows, which a boundary pass fills after each EOS pass.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -40,6 +43,7 @@ struct FDArgs {
   double* oux;
   double* ouy;
   int nx, ny;
+  int walls;  // 1: planes hold ghost rows (fluid row y at row y + 2), y not periodic
   // Every derivative is formed from raw stencil differences; the powers of
   // h = 1/dx, the time step and the force and viscosity coefficients are folded
   // into these constants on the host (mu = mu_c rho, mu_B = muB_c rho):
@@ -57,6 +61,42 @@ __global__ void k_fd_eos(const EosConst e, const double* __restrict__ rho, doubl
   p[i] = pr;
   const double psi2 = e.psi2_scale * (pr - r * (1.0 / 3.0));
   psi[i] = psi2 > 0.0 ? fast_sqrt(psi2) : sqrt(psi2);  // IEEE result at 0, below 0 and NaN
+}
+
+// Wall layers (Eqs. B1, B2), one thread per column of a padded plane set: b1 (row
+// 1) on the bottom wall, no slip, density and psi extrapolated from the first two
+// fluid rows, p of that density; b2 (row 0) in the solid, psi_b2 = psi_b1 + 2 dy
+// (psi_l - psi_b1); top rows mirror the last fluid rows with the velocity
+// reversed (reflexive layers t1 = row ny + 2, t2 = row ny + 3).
+__global__ void k_fd_walls(const EosConst e, double* rho, double* ux, double* uy, double* psi, double* p, int nx,
+                           int ny, double two_dy, double psi_l) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  auto at = [&](int row) { return (int64_t)row * nx + x; };
+  const double rb1 = 2.0 * rho[at(2)] - rho[at(3)];
+  const double sb1 = 2.0 * psi[at(2)] - psi[at(3)];
+  const double pb1 = eos_pressure(e, rb1);
+  rho[at(1)] = rb1;
+  psi[at(1)] = sb1;
+  p[at(1)] = pb1;
+  ux[at(1)] = 0.0;
+  uy[at(1)] = 0.0;
+  rho[at(0)] = rb1;
+  psi[at(0)] = fma(two_dy, psi_l - sb1, sb1);
+  p[at(0)] = pb1;
+  ux[at(0)] = 0.0;
+  uy[at(0)] = 0.0;
+  const int t1 = ny + 2, t2 = ny + 3, f1 = ny + 1, f2 = ny;
+  rho[at(t1)] = rho[at(f1)];
+  psi[at(t1)] = psi[at(f1)];
+  p[at(t1)] = p[at(f1)];
+  ux[at(t1)] = -ux[at(f1)];
+  uy[at(t1)] = -uy[at(f1)];
+  rho[at(t2)] = rho[at(f2)];
+  psi[at(t2)] = psi[at(f2)];
+  p[at(t2)] = p[at(f2)];
+  ux[at(t2)] = 0.0;
+  uy[at(t2)] = 0.0;
 }
 
 template <bool PRED>
@@ -79,7 +119,7 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     cx[k] = wrap(x + k - 2, nx);
-    ry[k] = (int64_t)wrap(y + k - 2, ny) * nx;
+    ry[k] = (int64_t)(a.walls ? y + k : wrap(y + k - 2, ny)) * nx;  // walls: padded rows, no wrap
   }
   auto at = [&](const double* f, int dx, int dy) { return f[ry[dy + 2] + cx[dx + 2]]; };
   // one-sided first difference along x (axis 0) or y (axis 1): forward in the
@@ -130,7 +170,7 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   const double inv_rho = fast_rcp(rho);
   const double dux = fma(V0 - F0 - a.cA * D1(a.p, 0), inv_rho, -a.cA * fma(ux, Du00, uy * Du10));
   const double duy = fma(V1 - F1 - a.cA * D1(a.p, 1), inv_rho, -a.cA * fma(ux, Du01, uy * Du11));
-  const int64_t i = (int64_t)y * nx + x;
+  const int64_t i = (int64_t)(a.walls ? y + 2 : y) * nx + x;
   if (PRED) {
     a.orho[i] = rho + drho;
     a.oux[i] = ux + dux;
@@ -149,7 +189,10 @@ using namespace pplbm;
 
 struct pplbm_fd {
   int nx, ny;
-  int64_t n;
+  int64_t n;     // fluid nodes
+  bool walls;
+  int64_t np;    // values per plane: n, or nx (ny + 4) with walls
+  int64_t off;   // first fluid value of a plane: 0, or 2 nx with walls
   EosConst eos;
   pplbm_eos_derived derived;
   double G, eps, dx, mu_c, muB_c;
@@ -163,9 +206,20 @@ struct pplbm_fd {
 
 extern "C" {
 
+namespace {
+// 0: periodic y, 1: walls, -1: not accepted
+int fd_walls(const pplbm_lattice* l) {
+  if (l->bc == (PPLBM_BC_PERIODIC_X | PPLBM_BC_PERIODIC_Y)) return 0;
+  if (l->bc == (PPLBM_BC_PERIODIC_X | PPLBM_BC_WALL_BOTTOM | PPLBM_BC_WALL_TOP) && l->ny >= 2) return 1;
+  return -1;
+}
+}  // namespace
+
 size_t pplbm_fd_workspace_bytes(const pplbm_lattice* lattice) {
   if (!lattice || lattice->nx < 1 || lattice->ny < 1 || lattice->ny > 65535 * 8) return 0;
-  return sizeof(double) * 8 * (size_t)lattice->nx * lattice->ny;
+  const int w = fd_walls(lattice);
+  if (w < 0) return 0;
+  return sizeof(double) * 8 * (size_t)lattice->nx * (size_t)(lattice->ny + 4 * w);
 }
 
 pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos, double G,
@@ -175,7 +229,7 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
   *out = nullptr;
   if (!lattice || !eos || !workspace || lattice->nx < 1 || lattice->ny < 1 || lattice->reserved != 0) return PPLBM_ERR_ARG;
   if (lattice->ny > 65535 * 8) return PPLBM_ERR_ARG;  // the update pass's grid: 8-row tiles on its y axis
-  if (lattice->bc != (PPLBM_BC_PERIODIC_X | PPLBM_BC_PERIODIC_Y)) return PPLBM_ERR_ARG;
+  if (fd_walls(lattice) < 0) return PPLBM_ERR_ARG;
   if (!(tau_nu > 0.5) || !(tau_e > 0.0) || !(dx > 0.0)) return PPLBM_ERR_ARG;
   if (workspace_bytes < pplbm_fd_workspace_bytes(lattice)) return PPLBM_ERR_ARG;
   pplbm_eos_derived d;
@@ -186,6 +240,9 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
   f->nx = lattice->nx;
   f->ny = lattice->ny;
   f->n = (int64_t)f->nx * f->ny;
+  f->walls = fd_walls(lattice) == 1;
+  f->np = (int64_t)f->nx * (f->ny + (f->walls ? 4 : 0));
+  f->off = f->walls ? 2 * (int64_t)f->nx : 0;
   f->derived = d;
   f->eos = make_eos_const(d);
   f->G = G;
@@ -195,9 +252,9 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
   f->muB_c = (tau_e - tau_nu) / 3.0;
   double* w = (double*)workspace;
   f->U = w;
-  f->S = w + 3 * f->n;
-  f->psi = w + 6 * f->n;
-  f->p = w + 7 * f->n;
+  f->S = w + 3 * f->np;
+  f->psi = w + 6 * f->np;
+  f->p = w + 7 * f->np;
   f->stream = (cudaStream_t)stream;
   *out = f;
   return PPLBM_OK;
@@ -207,7 +264,8 @@ pplbm_status pplbm_fd_set_state(pplbm_fd* f, const double* rho, const double* ux
   if (!f || !rho || !ux || !uy) return PPLBM_ERR_ARG;
   const double* src[3] = {rho, ux, uy};
   for (int k = 0; k < 3; ++k)
-    if (cudaMemcpyAsync(f->U + k * f->n, src[k], sizeof(double) * f->n, cudaMemcpyDefault, f->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(f->U + k * f->np + f->off, src[k], sizeof(double) * f->n, cudaMemcpyDefault, f->stream) !=
+        cudaSuccess)
       return PPLBM_ERR_CUDA;
   return cudaStreamSynchronize(f->stream) == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
 }
@@ -217,7 +275,8 @@ pplbm_status pplbm_fd_get_state(pplbm_fd* f, double* rho, double* ux, double* uy
   double* dst[3] = {rho, ux, uy};
   for (int k = 0; k < 3; ++k)
     if (dst[k] &&
-        cudaMemcpyAsync(dst[k], f->U + k * f->n, sizeof(double) * f->n, cudaMemcpyDefault, f->stream) != cudaSuccess)
+        cudaMemcpyAsync(dst[k], f->U + k * f->np + f->off, sizeof(double) * f->n, cudaMemcpyDefault, f->stream) !=
+            cudaSuccess)
       return PPLBM_ERR_CUDA;
   return cudaStreamSynchronize(f->stream) == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
 }
@@ -230,6 +289,7 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   std::memset(&a, 0, sizeof(a));
   a.nx = f->nx;
   a.ny = f->ny;
+  a.walls = f->walls ? 1 : 0;
   const double h = 1.0 / f->dx, h2 = h * h, h3 = h2 * h;
   a.cA = dt * h;
   a.kS = dt * 0.5 * h3 * (f->G / 6.0 - f->eps * f->G / 4.0);
@@ -241,28 +301,37 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   a.v4 = dt * h2 * (f->mu_c + f->muB_c) * 0.25;
   a.psi = f->psi;
   a.p = f->p;
-  const int64_t n = f->n;
+  const int64_t n = f->n, np = f->np, off = f->off;
+  const unsigned wb = (unsigned)((f->nx + 255) / 256);
+  const double two_dy = 2.0 * f->dx, psi_l = f->derived.psi_l;
+  // psi and p of the state in X, then its wall layers
+  auto eos_pass = [&](double* X) {
+    k_fd_eos<<<eb, 256, 0, f->stream>>>(f->eos, X + off, f->psi + off, f->p + off, n);
+    if (f->walls)
+      k_fd_walls<<<wb, 256, 0, f->stream>>>(f->eos, X, X + np, X + 2 * np, f->psi, f->p, f->nx, f->ny, two_dy,
+                                           psi_l);
+  };
   for (int64_t s = 0; s < nsteps; ++s) {
     // predictor: U* = U + dt R_f(U)
-    k_fd_eos<<<eb, 256, 0, f->stream>>>(f->eos, f->U, f->psi, f->p, n);
+    eos_pass(f->U);
     a.rho = f->U;
-    a.ux = f->U + n;
-    a.uy = f->U + 2 * n;
+    a.ux = f->U + np;
+    a.uy = f->U + 2 * np;
     a.orho = f->S;
-    a.oux = f->S + n;
-    a.ouy = f->S + 2 * n;
+    a.oux = f->S + np;
+    a.ouy = f->S + 2 * np;
     k_fd_update<true><<<grid, block, 0, f->stream>>>(a);
     // corrector: U <- (U + U* + dt R_b(U*)) / 2
-    k_fd_eos<<<eb, 256, 0, f->stream>>>(f->eos, f->S, f->psi, f->p, n);
+    eos_pass(f->S);
     a.rho = f->S;
-    a.ux = f->S + n;
-    a.uy = f->S + 2 * n;
+    a.ux = f->S + np;
+    a.uy = f->S + 2 * np;
     a.rho0 = f->U;
-    a.ux0 = f->U + n;
-    a.uy0 = f->U + 2 * n;
+    a.ux0 = f->U + np;
+    a.uy0 = f->U + 2 * np;
     a.orho = f->U;
-    a.oux = f->U + n;
-    a.ouy = f->U + 2 * n;
+    a.oux = f->U + np;
+    a.ouy = f->U + 2 * np;
     k_fd_update<false><<<grid, block, 0, f->stream>>>(a);
   }
   f->steps += nsteps;

@@ -8,15 +8,20 @@ from .lattice import EOSParams, _ptr
 
 
 class FDSolver:
-    """MacCormack solver of App. A on a periodic nx x ny grid of spacing dx (CUDA)."""
+    """MacCormack solver of App. A on an nx x ny grid of spacing dx (CUDA): periodic
+    (bc = BC_PERIODIC), or periodic in x with the wall layers of Eqs. B1, B2 at the
+    bottom and reflexive layers at the top (bc = BC_WALLS_Y)."""
 
-    def __init__(self, nx, ny, eos: EOSParams, tau_nu=1.0, tau_e=1.0, dx=1.0, G=-1.0, device="cuda", stream=None):
+    def __init__(self, nx, ny, eos: EOSParams, tau_nu=1.0, tau_e=1.0, dx=1.0, G=-1.0, device="cuda", stream=None,
+                 bc=L.BC_PERIODIC):
         import torch
 
         self.torch = torch
         self.nx, self.ny = int(nx), int(ny)
-        self.lattice = L.pplbm_lattice(self.nx, self.ny, L.BC_PERIODIC, 0)
+        self.lattice = L.pplbm_lattice(self.nx, self.ny, int(bc), 0)
         nbytes = L.lib().pplbm_fd_workspace_bytes(C.byref(self.lattice))
+        if nbytes == 0:
+            raise L.PPLBMError(L.PPLBM_ERR_ARG, "invalid FD grid or boundary flags")
         self.device = torch.device(device)
         self.workspace = torch.empty(nbytes // 8, dtype=torch.float64, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -106,3 +106,26 @@ def test_oscillating_droplet_lbm_agrees_with_fd_and_fd_refines_toward_it():
     cl, cf = crossings(lbm), crossings(fd[0.5])
     assert len(cl) == len(cf) >= 2
     assert np.max(np.abs(cl - cf)) < 200.0
+
+
+@pytest.mark.parametrize("shape,dx", [((48, 40), 1.0), ((48, 80), 0.5)])
+def test_fd_with_walls_matches_cpu_oracle(shape, dx):
+    """The wall layers of Eqs. B1, B2 and the reflexive top on the GPU against the CPU
+    FD oracle: a drop (R = 8, W = 8 in lattice units) moving towards a liquid film of
+    height 6 on the bottom wall, 40 steps, at grid spacings 1 and 1/2."""
+    nx, ny = shape
+    oe = E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    eps = oe.solve_eps(n=40000)
+    rho, ux, uy = I.impact(nx, ny, 8.0, 6.0, oe.rho_v, oe.rho_l, 0.02, W=8.0, dx=dx)
+    dt = 0.4 * dx * dx
+    cpu = F.FDSolver(oe, eps, tau_nu=0.8, tau_e=1.0, dx=dx, walls=True)
+    r, u = cpu.run(rho.copy(), [ux.copy(), uy.copy()], 40 * dt, dt)
+    gpu = P.FDSolver(nx, ny, P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), tau_nu=0.8, tau_e=1.0, dx=dx,
+                     bc=P.BC_WALLS_Y)
+    gpu.set_state(rho, ux, uy)
+    gpu.step(40, dt)
+    gr, gux, guy = [t.cpu().numpy() for t in gpu.get_state()]
+    assert np.isfinite(r).all()
+    assert normwise(gr, r) < 1e-10
+    umax = max(np.abs(u[0]).max(), np.abs(u[1]).max())
+    assert np.max(np.abs(gux - u[0])) < 1e-9 * umax and np.max(np.abs(guy - u[1])) < 1e-9 * umax
