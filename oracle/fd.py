@@ -39,7 +39,10 @@ def _sh(a, dy, dx):
 
 
 class FDSolver:
-    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0, walls=False):
+    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0, walls=False, tau_l=None, visc_ratio=None):
+        """tau_l, visc_ratio: the relaxation time of Eq. RelaxationTime, linear in rho
+        between tau_v = 1/2 + v_r (tau_l - 1/2) at rho_v and tau_l at rho_l, in place of
+        the constant tau_nu (Eqs. DynamicViscosity, FDviscosityDerivative)."""
         self.eos = eos
         self.eps = eps
         self.G = eos.G
@@ -47,6 +50,17 @@ class FDSolver:
         self.tau_nu = tau_nu
         self.tau_e = tau_e
         self.walls = walls
+        self.tau_l = tau_l
+        self.visc_ratio = visc_ratio
+
+    def _tau_nu(self, rho):
+        """(tau_nu(rho), d tau_nu / d rho)."""
+        if self.tau_l is None:
+            return self.tau_nu, 0.0
+        e = self.eos
+        tau_v = 0.5 + self.visc_ratio * (self.tau_l - 0.5)
+        tau = self.tau_l * (rho - e.rho_v) / (e.rho_l - e.rho_v) + tau_v * (rho - e.rho_l) / (e.rho_v - e.rho_l)
+        return tau, (self.tau_l - tau_v) / (e.rho_l - e.rho_v)
 
     def _padded(self, rho, u):
         """rho, u, psi, p with two ghost rows below and above (Eqs. B1, B2 and the
@@ -107,11 +121,13 @@ class FDSolver:
         ddpsi = [[self.d2(psi, axes[a], axes[b]) for b in range(2)] for a in range(2)]
         lap = ddpsi[0][0] + ddpsi[1][1]
         dlap = [self.d1(lap, axes[a], "c") for a in range(2)]
-        # viscosity and its density derivative (constant relaxation times)
-        mu = rho * cs2 * (self.tau_nu - 0.5)
-        muB = rho * cs2 * (self.tau_e - self.tau_nu)
-        dmu_drho = cs2 * (self.tau_nu - 0.5)
-        dmuB_drho = cs2 * (self.tau_e - self.tau_nu)
+        # dynamic viscosities (Eq. DynamicViscosity) and their density derivatives
+        # (Eq. FDviscosityDerivative), with tau_nu constant or tau_nu(rho)
+        tau, dtau = self._tau_nu(rho)
+        mu = rho * cs2 * (tau - 0.5)
+        muB = rho * cs2 * (self.tau_e - tau)
+        dmu_drho = cs2 * (tau - 0.5) + rho * cs2 * dtau
+        dmuB_drho = cs2 * (self.tau_e - tau) - rho * cs2 * dtau
         drho_1 = [self.d1(rho, axes[a], kind) for a in range(2)]
         du = [[self.d1(u[b], axes[a], kind) for b in range(2)] for a in range(2)]  # du[a][b] = d_a u_b
         ddu = [[[self.d2(u[c], axes[a], axes[b]) for c in range(2)] for b in range(2)] for a in range(2)]

@@ -111,3 +111,21 @@ def test_fd_walls_are_no_slip_shear_mode_decays_at_the_viscous_rate(dx):
     rate = -np.log(amp / 1e-4) / 200
     nu = (1.0 - 0.5) / 3.0
     assert rate == pytest.approx(nu * (np.pi / L_) ** 2, rel=5e-3)
+
+
+@pytest.mark.parametrize("phase", ["liquid", "vapour"])
+def test_fd_two_phase_viscosity_shear_waves_decay_at_each_phase_rate(phase):
+    """tau_nu(rho) of Eq. RelaxationTime in the FD viscosities (Eq.
+    FDviscosityDerivative): a periodic shear wave in uniform liquid decays at
+    nu_l k^2, in uniform vapour at nu_v k^2, nu = (tau - 1/2)/3, with tau_l = 0.7
+    and tau_v = 1/2 + v_r (tau_l - 1/2) for v_r = 5."""
+    e = E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    tau_l, vr = 0.7, 5.0
+    fds = F.FDSolver(e, e.solve_eps(), tau_e=1.0, dx=1.0, tau_l=tau_l, visc_ratio=vr)
+    rho = e.rho_l if phase == "liquid" else e.rho_v
+    tau = tau_l if phase == "liquid" else 0.5 + vr * (tau_l - 0.5)
+    n, k = 64, 2 * np.pi / 64
+    mode = np.sin(k * np.arange(n))
+    r, u = fds.run(np.full((n, 2), rho), [1e-5 * np.repeat(mode[:, None], 2, axis=1), np.zeros((n, 2))], 100, 0.1)
+    amp = (u[0][:, 0] * mode).sum() / (mode * mode).sum()
+    assert -np.log(amp / 1e-5) / 100 == pytest.approx((tau - 0.5) / 3.0 * k * k, rel=2e-3)
