@@ -303,6 +303,11 @@ size_t pplbm_fd_workspace_bytes(const pplbm_lattice* lattice);
 pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos, double G,
                              double tau_nu, double tau_e, double dx, void* workspace, size_t workspace_bytes,
                              void* stream);
+/* Replaces the constant tau_nu by tau_nu(rho) of Eq. RelaxationTime, linear in rho
+ * from tau_v = 1/2 + visc_ratio (tau_l - 1/2) at rho_v to tau_l at rho_l (the Maxwell
+ * densities), in the viscosities of Eq. DynamicViscosity and their density
+ * derivatives (Eq. FDviscosityDerivative); tau_e stays. tau_l > 1/2, visc_ratio > 0. */
+pplbm_status pplbm_fd_set_two_phase_viscosity(pplbm_fd* fd, double tau_l, double visc_ratio);
 /* Copies the state in / out (device or host pointers; NULL skips an output). Synchronous. */
 pplbm_status pplbm_fd_set_state(pplbm_fd* fd, const double* rho, const double* ux, const double* uy);
 pplbm_status pplbm_fd_get_state(pplbm_fd* fd, double* rho, double* ux, double* uy);

@@ -130,6 +130,7 @@ _SIGS = {
     "pplbm_batch_instance_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "pplbm_batch_guard": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "pplbm_adjoint_set_slots": (C.c_int, [_P, C.c_uint32]),
+    "pplbm_fd_set_two_phase_viscosity": (C.c_int, [_P, C.c_double, C.c_double]),
     "pplbm_forward_stored": (C.c_int, [_P, C.c_int64, _P]),
     "pplbm_backward_stored": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_size_t]),
     "pplbm_init": (C.c_int, [C.POINTER(_P), C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),

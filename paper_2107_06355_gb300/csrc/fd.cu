@@ -50,6 +50,10 @@ struct FDArgs {
   double cA;              // dt h: advection, mass flux, pressure gradient
   double kS, kL, kD;      // dt (h^3/2) (G/6 - eps G/4), dt (h^3/2) G/12, dt (h^3/2) G/4
   double v1, v2, v3, v4;  // dt h^2 mu_c, dt h^2 muB_c, dt h^2 (2 mu_c + muB_c), dt h^2 (mu_c + muB_c)/4
+  // tau_nu(rho) = ta + tb rho (Eq. RelaxationTime) when var_visc: mu = dt h^2 rho (g0 + g1 rho),
+  // mu_B = dt h^2 rho (e0 - g1 rho), and d/drho of both (Eq. FDviscosityDerivative)
+  int var_visc;
+  double g0, g1, e0;
 };
 
 __global__ void k_fd_eos(const EosConst e, const double* __restrict__ rho, double* __restrict__ psi,
@@ -162,10 +166,19 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   // and central second derivatives of u
   const double U0xx = Dxx(a.ux), U0yy = Dyy(a.ux), U1xx = Dxx(a.uy), U1yy = Dyy(a.uy);
   const double U0xy = Dxy(a.ux), U1xy = Dxy(a.uy);
-  const double V0 = fma(a.v1, fma(2.0 * Dr0, Du00, Dr1 * Sh),
-                        fma(a.v2 * Dr0, Dv, rho * fma(a.v3, U0xx, fma(a.v4, U1xy, a.v1 * U0yy))));
-  const double V1 = fma(a.v1, fma(2.0 * Dr1, Du11, Dr0 * Sh),
-                        fma(a.v2 * Dr1, Dv, rho * fma(a.v3, U1yy, fma(a.v4, U0xy, a.v1 * U1xx))));
+  double V0, V1;
+  if (!a.var_visc) {
+    V0 = fma(a.v1, fma(2.0 * Dr0, Du00, Dr1 * Sh),
+             fma(a.v2 * Dr0, Dv, rho * fma(a.v3, U0xx, fma(a.v4, U1xy, a.v1 * U0yy))));
+    V1 = fma(a.v1, fma(2.0 * Dr1, Du11, Dr0 * Sh),
+             fma(a.v2 * Dr1, Dv, rho * fma(a.v3, U1yy, fma(a.v4, U0xy, a.v1 * U1xx))));
+  } else {
+    const double mu = rho * fma(a.g1, rho, a.g0), muB = rho * fma(-a.g1, rho, a.e0);
+    const double dmu = fma(2.0 * a.g1, rho, a.g0), dmuB = fma(-2.0 * a.g1, rho, a.e0);
+    const double c2 = 2.0 * mu + muB, c4 = 0.25 * (mu + muB);
+    V0 = fma(dmu, fma(2.0 * Dr0, Du00, Dr1 * Sh), fma(dmuB * Dr0, Dv, fma(c2, U0xx, fma(c4, U1xy, mu * U0yy))));
+    V1 = fma(dmu, fma(2.0 * Dr1, Du11, Dr0 * Sh), fma(dmuB * Dr1, Dv, fma(c2, U1yy, fma(c4, U0xy, mu * U1xx))));
+  }
   // dt d_t u_a = -dt u . grad u_a + (dt/rho)(d_b sigma'_ab - d_a p_EOS - d_b p'_ab)
   const double inv_rho = fast_rcp(rho);
   const double dux = fma(V0 - F0 - a.cA * D1(a.p, 0), inv_rho, -a.cA * fma(ux, Du00, uy * Du10));
@@ -195,7 +208,9 @@ struct pplbm_fd {
   int64_t off;   // first fluid value of a plane: 0, or 2 nx with walls
   EosConst eos;
   pplbm_eos_derived derived;
-  double G, eps, dx, mu_c, muB_c;
+  double G, eps, dx, mu_c, muB_c, tau_e;
+  bool var_visc;  // tau_nu(rho) = ta + tb rho instead of a constant
+  double ta, tb;
   double* U;   // rho, ux, uy
   double* S;   // predictor state
   double* psi;
@@ -250,6 +265,8 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
   f->dx = dx;
   f->mu_c = (tau_nu - 0.5) / 3.0;
   f->muB_c = (tau_e - tau_nu) / 3.0;
+  f->tau_e = tau_e;
+  f->var_visc = false;
   double* w = (double*)workspace;
   f->U = w;
   f->S = w + 3 * f->np;
@@ -299,6 +316,12 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   a.v2 = dt * h2 * f->muB_c;
   a.v3 = dt * h2 * (2.0 * f->mu_c + f->muB_c);
   a.v4 = dt * h2 * (f->mu_c + f->muB_c) * 0.25;
+  if (f->var_visc) {
+    a.var_visc = 1;
+    a.g0 = dt * h2 * (f->ta - 0.5) / 3.0;
+    a.g1 = dt * h2 * f->tb / 3.0;
+    a.e0 = dt * h2 * (f->tau_e - f->ta) / 3.0;
+  }
   a.psi = f->psi;
   a.p = f->p;
   const int64_t n = f->n, np = f->np, off = f->off;
@@ -336,6 +359,16 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   }
   f->steps += nsteps;
   return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
+}
+
+pplbm_status pplbm_fd_set_two_phase_viscosity(pplbm_fd* f, double tau_l, double visc_ratio) {
+  if (!f || !(tau_l > 0.5) || !(visc_ratio > 0.0)) return PPLBM_ERR_ARG;
+  const double tau_v = 0.5 + visc_ratio * (tau_l - 0.5);
+  const double rv = f->derived.rho_v, rl = f->derived.rho_l;
+  f->tb = (tau_l - tau_v) / (rl - rv);
+  f->ta = tau_l - f->tb * rl;
+  f->var_visc = true;
+  return PPLBM_OK;
 }
 
 pplbm_status pplbm_fd_sync(pplbm_fd* f) {

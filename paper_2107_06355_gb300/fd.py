@@ -13,7 +13,7 @@ class FDSolver:
     bottom and reflexive layers at the top (bc = BC_WALLS_Y)."""
 
     def __init__(self, nx, ny, eos: EOSParams, tau_nu=1.0, tau_e=1.0, dx=1.0, G=-1.0, device="cuda", stream=None,
-                 bc=L.BC_PERIODIC):
+                 bc=L.BC_PERIODIC, tau_l=None, visc_ratio=None):
         import torch
 
         self.torch = torch
@@ -30,6 +30,8 @@ class FDSolver:
         L.check(L.lib().pplbm_fd_create(C.byref(h), C.byref(self.lattice), C.byref(p), G, tau_nu, tau_e, dx,
                                         _ptr(self.workspace), nbytes, C.c_void_p(self.stream.cuda_stream)))
         self.h = h
+        if tau_l is not None:   # tau_nu(rho) of Eq. RelaxationTime instead of the constant tau_nu
+            L.check(L.lib().pplbm_fd_set_two_phase_viscosity(h, float(tau_l), float(visc_ratio)))
 
     def close(self):
         if getattr(self, "h", None):

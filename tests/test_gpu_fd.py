@@ -131,31 +131,40 @@ def test_fd_with_walls_matches_cpu_oracle(shape, dx):
     assert np.max(np.abs(gux - u[0])) < 1e-9 * umax and np.max(np.abs(guy - u[1])) < 1e-9 * umax
 
 
-def test_droplet_impact_lbm_agrees_with_the_fd_reference():
-    """The paper's dynamic comparison (Sec. IV.B, App. C): a drop (R = 50) hitting a
-    liquid film (height 25) on a wall at Re = 112.5 (V_d = 0.075, tau_l = 0.7, v_r = 1),
-    T_r = 0.5, Smooth C-S (a_l = 0.363, a_v = 2, alpha = 0.775), 600 x 250 lattice,
-    against the FD scheme on the same domain at dx = 1/2 with the wall layers of Eqs.
-    B1, B2 and dt = 0.8 dx^2. Up to t* = t V_d / D = 1.5 the liquid half-width on
-    the row just above the film agrees within 2 nodes (of 60-180) and the phase
-    fields differ by less than 3 % of the liquid area; at t* = 2 the phase fields
-    still do."""
-    nx, ny, R, film, V, tau_l, W = 600, 250, 50.0, 25.0, 0.075, 0.7, 7.0
-    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+IMPACT_CASES = {
+    # T_r, a_l, alpha, W (planar width), v_r, FD dt / dx^2 (App. C: 0.8 for v_r = 1, 0.2 otherwise), t* checked
+    "Tr0.5_vr1": (0.5, 0.363, 0.775, 7.0, 1.0, 0.8, (0.25, 0.5, 1.0, 1.5, 2.0)),
+    "Tr0.6_vr5": (0.6, 0.387, 0.834, 8.0, 5.0, 0.2, (0.25, 0.5, 1.0, 1.5)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(IMPACT_CASES))
+def test_droplet_impact_lbm_agrees_with_the_fd_reference(case):
+    """The paper's dynamic comparisons (Sec. IV.B, App. C): a drop (R = 50) hitting a
+    liquid film (height 25) on a wall at Re = 112.5 (V_d = 0.075, tau_l = 0.7), Smooth
+    C-S with a_v = 2, 600 x 250 lattice, at T_r = 0.5 with v_r = 1 and at T_r = 0.6
+    with v_r = 5 (tau(rho) of Eq. RelaxationTime in both methods), against the FD
+    scheme on the same domain at dx = 1/2 with the wall layers of Eqs. B1, B2. Up
+    to t* = t V_d / D = 1.5 the liquid half-width on the row just above the film
+    agrees within 2 nodes (of 60-180) and the phase fields differ by less than 3 %
+    of the liquid area; at t* = 2 the phase fields still do."""
+    Tr, al, alpha, W, vr, dtf, tstars = IMPACT_CASES[case]
+    nx, ny, R, film, V, tau_l = 600, 250, 50.0, 25.0, 0.075, 0.7
+    eosp = P.EOSParams(P.EOS_SMOOTH, Tr, al, 2.0, alpha)
     d = P.eos_setup(eosp)
     rv, rl = d["rho_v"], d["rho_l"]
-    times = [int(round(ts * 2 * R / V)) for ts in (0.25, 0.5, 1.0, 1.5, 2.0)]
+    times = [int(round(ts * 2 * R / V)) for ts in tstars]
 
     def phase(rho, dx):
         phi = np.clip((rho - rv) / (rl - rv), 0.0, 1.0)
         return phi, (phi[int(round(30.0 / dx))] > 0.5).sum() * dx / 2.0
 
-    sim = P.Simulation(nx, ny, P.BC_WALLS_Y, eosp, P.Relax(kind=P.RELAX_TWO_PHASE, tau_l=tau_l, visc_ratio=1.0))
+    sim = P.Simulation(nx, ny, P.BC_WALLS_Y, eosp, P.Relax(kind=P.RELAX_TWO_PHASE, tau_l=tau_l, visc_ratio=vr))
     sim.init_equilibrium(*I.impact(nx, ny, R, film, rv, rl, V, W=W))
-    fd = P.FDSolver(2 * nx, 2 * ny, eosp, tau_nu=tau_l, tau_e=1.0, dx=0.5, bc=P.BC_WALLS_Y)
+    fd = P.FDSolver(2 * nx, 2 * ny, eosp, tau_e=1.0, dx=0.5, bc=P.BC_WALLS_Y, tau_l=tau_l, visc_ratio=vr)
     fd.set_state(*I.impact(2 * nx, 2 * ny, R, film, rv, rl, V, W=W, dx=0.5))
-    dt, t = 0.2, 0
-    for k, T in enumerate(times):
+    dt, t = dtf * 0.25, 0
+    for ts, T in zip(tstars, times):
         sim.step(T - t)
         fd.step(int(round((T - t) / dt)), dt)
         t = T
@@ -163,7 +172,28 @@ def test_droplet_impact_lbm_agrees_with_the_fd_reference():
         phi_f, half_f = phase(fd.get_state()[0].cpu().numpy(), 0.5)
         assert np.isfinite(phi_f).all()
         assert np.abs(phi_f[::2, ::2] - phi_l).sum() < 0.03 * phi_l.sum()
-        if k < 4:
+        if ts <= 1.5:
             assert abs(half_l - half_f) <= 2.0
     sim.close()
     fd.close()
+
+
+def test_fd_two_phase_viscosity_with_walls_matches_cpu_oracle():
+    """tau_nu(rho) of Eq. RelaxationTime (tau_l = 0.7, v_r = 5) in the FD viscosities,
+    with walls, on the GPU against the CPU oracle: 40 steps at dx = 1/2, dt = 0.2 dx^2."""
+    nx, ny, dx = 48, 80, 0.5
+    oe = E.make_eos(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    eps = oe.solve_eps(n=40000)
+    rho, ux, uy = I.impact(nx, ny, 8.0, 6.0, oe.rho_v, oe.rho_l, 0.02, W=8.0, dx=dx)
+    dt = 0.2 * dx * dx
+    cpu = F.FDSolver(oe, eps, tau_e=1.0, dx=dx, walls=True, tau_l=0.7, visc_ratio=5.0)
+    r, u = cpu.run(rho.copy(), [ux.copy(), uy.copy()], 40 * dt, dt)
+    gpu = P.FDSolver(nx, ny, P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), tau_e=1.0, dx=dx,
+                     bc=P.BC_WALLS_Y, tau_l=0.7, visc_ratio=5.0)
+    gpu.set_state(rho, ux, uy)
+    gpu.step(40, dt)
+    gr, gux, guy = [t.cpu().numpy() for t in gpu.get_state()]
+    assert np.isfinite(r).all()
+    assert normwise(gr, r) < 1e-10
+    umax = max(np.abs(u[0]).max(), np.abs(u[1]).max())
+    assert np.max(np.abs(gux - u[0])) < 1e-9 * umax and np.max(np.abs(guy - u[1])) < 1e-9 * umax
