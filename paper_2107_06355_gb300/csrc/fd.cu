@@ -50,9 +50,8 @@ struct FDArgs {
   double cA;              // dt h: advection, mass flux, pressure gradient
   double kS, kL, kD;      // dt (h^3/2) (G/6 - eps G/4), dt (h^3/2) G/12, dt (h^3/2) G/4
   double v1, v2, v3, v4;  // dt h^2 mu_c, dt h^2 muB_c, dt h^2 (2 mu_c + muB_c), dt h^2 (mu_c + muB_c)/4
-  // tau_nu(rho) = ta + tb rho (Eq. RelaxationTime) when var_visc: mu = dt h^2 rho (g0 + g1 rho),
+  // tau_nu(rho) = ta + tb rho (Eq. RelaxationTime) in the VV kernels: mu = dt h^2 rho (g0 + g1 rho),
   // mu_B = dt h^2 rho (e0 - g1 rho), and d/drho of both (Eq. FDviscosityDerivative)
-  int var_visc;
   double g0, g1, e0;
 };
 
@@ -103,7 +102,10 @@ __global__ void k_fd_walls(const EosConst e, double* rho, double* ux, double* uy
   uy[at(t2)] = 0.0;
 }
 
-template <bool PRED>
+// PRED: predictor (forward differences) or corrector (backward); VV: tau_nu(rho)
+// viscosities, a compile-time choice so the constant-viscosity kernel carries none
+// of their arithmetic
+template <bool PRED, bool VV>
 __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   const double U0xx = Dxx(a.ux), U0yy = Dyy(a.ux), U1xx = Dxx(a.uy), U1yy = Dyy(a.uy);
   const double U0xy = Dxy(a.ux), U1xy = Dxy(a.uy);
   double V0, V1;
-  if (!a.var_visc) {
+  if (!VV) {
     V0 = fma(a.v1, fma(2.0 * Dr0, Du00, Dr1 * Sh),
              fma(a.v2 * Dr0, Dv, rho * fma(a.v3, U0xx, fma(a.v4, U1xy, a.v1 * U0yy))));
     V1 = fma(a.v1, fma(2.0 * Dr1, Du11, Dr0 * Sh),
@@ -317,7 +319,6 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   a.v3 = dt * h2 * (2.0 * f->mu_c + f->muB_c);
   a.v4 = dt * h2 * (f->mu_c + f->muB_c) * 0.25;
   if (f->var_visc) {
-    a.var_visc = 1;
     a.g0 = dt * h2 * (f->ta - 0.5) / 3.0;
     a.g1 = dt * h2 * f->tb / 3.0;
     a.e0 = dt * h2 * (f->tau_e - f->ta) / 3.0;
@@ -343,7 +344,10 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
     a.orho = f->S;
     a.oux = f->S + np;
     a.ouy = f->S + 2 * np;
-    k_fd_update<true><<<grid, block, 0, f->stream>>>(a);
+    if (f->var_visc)
+      k_fd_update<true, true><<<grid, block, 0, f->stream>>>(a);
+    else
+      k_fd_update<true, false><<<grid, block, 0, f->stream>>>(a);
     // corrector: U <- (U + U* + dt R_b(U*)) / 2
     eos_pass(f->S);
     a.rho = f->S;
@@ -355,7 +359,10 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
     a.orho = f->U;
     a.oux = f->U + np;
     a.ouy = f->U + 2 * np;
-    k_fd_update<false><<<grid, block, 0, f->stream>>>(a);
+    if (f->var_visc)
+      k_fd_update<false, true><<<grid, block, 0, f->stream>>>(a);
+    else
+      k_fd_update<false, false><<<grid, block, 0, f->stream>>>(a);
   }
   f->steps += nsteps;
   return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
