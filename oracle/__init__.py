@@ -11,5 +11,6 @@ library under ``paper_2107_06355_gb300/`` and never imports it.
 Modules:
   eos  -- Carnahan-Starling EOS, Maxwell rule, Smooth C-S shaping, epsilon/sigma.
   lbm  -- one time step of the D2Q9 MRT lattice Boltzmann equation with the
-          Shan-Chen force and the Guo / Li forcing schemes.
+          Shan-Chen force and the Guo / Li forcing schemes, and the optional
+          surface-tension control the paper's Sec. V names (Li & Luo 2013).
 """

@@ -15,6 +15,16 @@ and d_b p'_ab of Eq. FDforce,
   d_b p'_ab = -eps (G c^4/4) (d_g psi)(d_a d_g psi) + (G c^4/12)(d_a psi)(d_g d_g psi)
               + (G c^4/6)(d_g psi)(d_a d_g psi) + (G c^4/4) psi d_a d_g d_g psi.
 
+With the surface-tension control of the paper's Sec. V (``kappa``; Li & Luo
+2013) the lattice Boltzmann method's momentum flux gains
+-Q + (3/4) tr(Q) I with Q_ab = kappa (G c^4/12) psi (delta_ab lap psi + 2 d_a d_b psi)
+to second order, i.e. p'_ab gains (kappa G c^4/6) psi (delta_ab lap psi - d_a d_b psi):
+the coefficient of psi d_a d_b psi in Eq. GeneralPressureTensor falls by 2 kappa and
+that of psi lap psi delta_ab rises by 2 kappa, so the normal component of a planar
+interface is unchanged and the surface tension of Eq. IntegralSurfaceTension
+becomes (1 - kappa) times its value. Its divergence adds
+(kappa G c^4/6) [(d_a psi)(d_g d_g psi) - (d_g psi)(d_a d_g psi)] to d_b p'_ab.
+
 MacCormack predictor/corrector: first derivatives of rho, u, p_EOS and mu in the
 advective, pressure and viscous terms are forward differences in the predictor
 and backward differences in the corrector; second derivatives are central in
@@ -39,10 +49,12 @@ def _sh(a, dy, dx):
 
 
 class FDSolver:
-    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0, walls=False, tau_l=None, visc_ratio=None):
+    def __init__(self, eos, eps, tau_nu=1.0, tau_e=1.0, dx=1.0, walls=False, tau_l=None, visc_ratio=None,
+                 kappa=0.0):
         """tau_l, visc_ratio: the relaxation time of Eq. RelaxationTime, linear in rho
         between tau_v = 1/2 + v_r (tau_l - 1/2) at rho_v and tau_l at rho_l, in place of
-        the constant tau_nu (Eqs. DynamicViscosity, FDviscosityDerivative)."""
+        the constant tau_nu (Eqs. DynamicViscosity, FDviscosityDerivative). kappa: the
+        surface-tension control (module docstring)."""
         self.eos = eos
         self.eps = eps
         self.G = eos.G
@@ -52,6 +64,7 @@ class FDSolver:
         self.walls = walls
         self.tau_l = tau_l
         self.visc_ratio = visc_ratio
+        self.kappa = kappa
 
     def _tau_nu(self, rho):
         """(tau_nu(rho), d tau_nu / d rho)."""
@@ -138,6 +151,8 @@ class FDSolver:
             adv = sum(u[g] * du[g][a] for g in range(2))
             s = sum(dpsi[g] * ddpsi[a][g] for g in range(2))
             dpprime = (-eps * G / 4.0 * s + G / 12.0 * dpsi[a] * lap + G / 6.0 * s + G / 4.0 * psi * dlap[a])
+            if self.kappa != 0.0:
+                dpprime = dpprime + self.kappa * G / 6.0 * (dpsi[a] * lap - s)
             visc = (sum(dmu_drho * drho_1[b] * (du[a][b] + du[b][a]) for b in range(2))
                     + mu * sum(ddu[a][b][b] + ddu[b][b][a] for b in range(2))
                     + dmuB_drho * drho_1[a] * dgu

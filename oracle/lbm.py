@@ -18,6 +18,11 @@ equations in the paper's order:
 5. streaming f_i(x + c_i, t + 1) = f*_i(x, t) (Eq. LBE), periodic, or half-way
    bounce-back at the walls (Sec. IV, App. B).
 
+Optional surface-tension control (``Relax.kappa``, 0 = off): the technique the
+paper's discussion (Sec. V) names for keeping the Weber number when alpha lowers
+the surface tension, Li & Luo's source term (Phys. Rev. E 88, 053307, 2013),
+added to m* in step 4; see ``surface_tension_source``.
+
 Array layout: f has shape (9, ny, nx); index [i, y, x]; x is the fastest axis.
 Relaxation: ``Relax`` holds either six constant relaxation times (Eq.
 RelaxationMatrix) or the density-dependent two-phase form of Sec. IV
@@ -77,6 +82,7 @@ class Relax:
     tau_l: float = 1.0
     visc_ratio: float = 1.0
     sigma: float = 0.0   # Li forcing parameter; 0 = Guo forcing
+    kappa: float = 0.0   # surface-tension control (Sec. V; Li & Luo 2013); 0 = off
 
 
 def equilibrium(rho, ux, uy):
@@ -154,6 +160,36 @@ def li_source(ux, uy, Fx, Fy, psi, sigma, tau_e, tau_zeta):
     return S
 
 
+def surface_tension_q(psi, G, kappa, bc, psi_ghost_bottom=0.0, psi_ghost_top=0.0):
+    """Q_ab = kappa (G/2) psi(x) sum_i w(|c_i|^2) [psi(x + c_i) - psi(x)] c_ia c_ib, the
+    tensor of the surface-tension control the paper's Sec. V names (Li & Luo 2013),
+    with the Shan-Chen weights of Eq. ShanChenForce and the same wall ghosts.
+    Returns Q_xx, Q_yy, Q_xy."""
+    qxx = np.zeros_like(psi)
+    qyy = np.zeros_like(psi)
+    qxy = np.zeros_like(psi)
+    for i in range(1, 9):
+        d = _neighbour(psi, C[i, 0], C[i, 1], bc, psi_ghost_bottom, psi_ghost_top) - psi
+        qxx += W_SC[i] * d * C[i, 0] * C[i, 0]
+        qyy += W_SC[i] * d * C[i, 1] * C[i, 1]
+        qxy += W_SC[i] * d * C[i, 0] * C[i, 1]
+    k = kappa * G / 2.0 * psi
+    return k * qxx, k * qyy, k * qxy
+
+
+def surface_tension_source(qxx, qyy, qxy, lam):
+    """Moment-space source added to m* by the surface-tension control (Li & Luo 2013):
+    C = [0, 1.5 l_e (Q_xx + Q_yy), -1.5 l_zeta (Q_xx + Q_yy), 0, 0, 0, 0,
+    -l_nu (Q_xx - Q_yy), -l_nu Q_xy] with l_k the diagonal of Lambda (Eq. RelaxationMatrix)
+    for the rows of Eq. MatrixMRT."""
+    Cs = np.zeros((9,) + qxx.shape)
+    Cs[1] = 1.5 * lam[1] * (qxx + qyy)
+    Cs[2] = -1.5 * lam[2] * (qxx + qyy)
+    Cs[7] = -lam[7] * (qxx - qyy)
+    Cs[8] = -lam[8] * qxy
+    return Cs
+
+
 @dataclass
 class Lattice:
     nx: int
@@ -195,6 +231,10 @@ class Lattice:
         S = li_source(ux, uy, Fx, Fy, psi, self.relax.sigma, te, tz)
         lam = relaxation_rates(self.relax, rho, self.eos.rho_v, self.eos.rho_l)
         mstar = m - lam * (m - meq) + (1.0 - lam / 2.0) * S
+        if self.relax.kappa != 0.0:
+            q = surface_tension_q(psi, self.eos.G, self.relax.kappa, self.bc, self.psi_ghost_bottom,
+                                  self.psi_ghost_top)
+            mstar = mstar + surface_tension_source(*q, lam)
         return np.einsum("ik,kyx->iyx", MINV, mstar)
 
     def stream(self, fstar):

@@ -6,7 +6,8 @@ checks that at least one of the oracle's pins then fails. A pin that passes for
 the right and for the wrong arithmetic pins nothing; these cases show the pins
 cover each part of the method (Eq. CS, the Maxwell rule, the shaped EOS, the
 equilibrium, the MRT moments, the Shan-Chen force, the Li and Guo forcing,
-the two-phase relaxation time, the walls and their ghost densities)."""
+the two-phase relaxation time, the walls and their ghost densities, the
+surface-tension control)."""
 import numpy as np
 import pytest
 
@@ -16,6 +17,7 @@ from oracle import lbm as L
 import test_oracle_eos as TE  # noqa: E402
 import test_oracle_fd as TF  # noqa: E402
 import test_oracle_lbm as TL  # noqa: E402
+import test_oracle_surface_tension as TS  # noqa: E402
 
 
 def _eos06():
@@ -207,3 +209,44 @@ def test_fd_bottom_wall_without_no_slip(monkeypatch):
 
     monkeypatch.setattr(F.FDSolver, "_padded", padded)
     assert some_pin_fails(lambda: TF.test_fd_walls_are_no_slip_shear_mode_decays_at_the_viscous_rate(1.0))
+
+
+def test_surface_tension_source_row7_sign(monkeypatch):
+    """The surface-tension source with +l_nu (Q_xx - Q_yy) in row 7."""
+    orig = L.surface_tension_source
+
+    def src(qxx, qyy, qxy, lam):
+        c = orig(qxx, qyy, qxy, lam)
+        c[7] = -c[7]
+        return c
+
+    monkeypatch.setattr(L, "surface_tension_source", src)
+    assert some_pin_fails(TS.test_unit_tau_second_moments_shift_by_minus_q_plus_three_quarters_trace,
+                          TS.test_planar_interface_evolves_identically_at_unit_tau)
+
+
+def test_surface_tension_q_without_the_centre_subtraction(monkeypatch):
+    """Q from sum_i w_i psi(x + c_i) c_i c_i instead of the differences psi(x + c_i) - psi(x)."""
+    orig = L.surface_tension_q
+
+    def q(psi, G, kappa, bc, *ghosts):
+        qxx, qyy, qxy = orig(psi, G, kappa, bc, *ghosts)
+        k = kappa * G / 2.0 * psi * psi
+        return qxx + k, qyy + k, qxy
+
+    monkeypatch.setattr(L, "surface_tension_q", q)
+    assert some_pin_fails(TS.test_q_is_exact_for_a_quadratic_psi, TS.test_planar_interface_evolves_identically_at_unit_tau)
+
+
+def test_fd_surface_tension_term_sign(monkeypatch):
+    """The finite-difference pressure tensor with the surface-tension term's sign reversed."""
+    from oracle import fd as F
+
+    orig = F.FDSolver.__init__
+
+    def init(self, *args, **kw):
+        orig(self, *args, **kw)
+        self.kappa = -self.kappa
+
+    monkeypatch.setattr(F.FDSolver, "__init__", init)
+    assert some_pin_fails(TS.test_droplet_response_to_kappa_matches_fd)
