@@ -53,7 +53,7 @@ IMPACT_FP64_PER_NODE = 42.0 + 67.5
 # `bench.py --profile-batch` (profiles/k_batch_collide_k_batch_rho_psi_droplets512.md).
 # They hold for the kernel sources whose digest is recorded with them; once those
 # sources change, traffic is reported as null until the capture is repeated.
-TRAFFIC = {"sources": "5b2e7c5d79b6e03b", "rho_psi": 75532459 + 2572117, "collide": 33606571 + 13751979}
+TRAFFIC = {"sources": "b30298601f1ce61b", "rho_psi": 75536384 + 2682880, "collide": 33605291 + 13938005}
 KERNEL_SOURCES = ("batch.cu", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
 
 
@@ -483,13 +483,16 @@ def adjoint_cost(torch, steps=2000, interval=45):
 
 def eos_variant_throughput(torch, steps=1000):
     """The bench workload (4 x 512^2 droplets, tau = 1) with each EOS the kernels
-    support (T_r = 0.6; the two Guo-forced EOS at 0.7), batched graph plan: MLUPS per EOS."""
+    support (T_r = 0.6; the two Guo-forced EOS at 0.7), and the Smooth C-S with the
+    surface-tension control, batched graph plan: MLUPS per variant."""
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
 
     variants = {
         "cs_a0.387_li": (P.EOSParams(P.EOS_CS, 0.6, 0.387, 0.387, 0.5), P.Relax()),
         "smooth_alpha0.834_li": (P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax()),
+        # the same with the surface-tension control (Sec. V's technique): its cost per step
+        "smooth_alpha0.834_li_kappa0.5": (P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax(kappa=0.5)),
         # Peng + Guo droplets diverge below T_r ~ 0.65 (the paper's minimum for that method)
         "peng_r0.45_Tr0.7_guo": (P.EOSParams(P.EOS_PENG, 0.7, 0.387, 0.387, 0.5, r_theta=0.45),
                                  P.Relax(forcing=P.FORCING_GUO)),

@@ -111,6 +111,18 @@ typedef struct pplbm_relax {
   int32_t sigma_auto;  /* 1: sigma = -eps/(16 G) with eps solving Eq. VaporLiqEq at the
                           Maxwell densities for the EOS in use (Sec. III.A) */
   int32_t reserved;    /* must be 0 */
+  /* Surface-tension control, the technique the discussion (Sec. V) names for
+     keeping the Weber number when alpha lowers the surface tension (Li & Luo,
+     Phys. Rev. E 88, 053307, 2013): the source
+       C = [0, 1.5 l_e tr Q, -1.5 l_zeta tr Q, 0, 0, 0, 0, -l_nu (Q_xx - Q_yy), -l_nu Q_xy]
+     (rows of Eq. MatrixMRT, l_k the relaxation rates of Eq. RelaxationMatrix) is
+     added to m*, with Q_ab = kappa (G/2) psi(x) sum_i w_i [psi(x + c_i) - psi(x)] c_ia c_ib
+     over the Shan-Chen stencil (wall ghosts as for the force). The coexistence
+     densities (Eq. VaporLiqEq) are unchanged and the surface tension of Eq.
+     IntegralSurfaceTension scales by (1 - kappa). 0 = off (the step is then
+     bitwise the plain one); finite and < 1, else PPLBM_ERR_ARG. Not covered by
+     the adjoint (PPLBM_ERR_STATE there). */
+  double kappa;
 } pplbm_relax;
 
 /* Everything the device needs about the EOS, computed by pplbm_eos_setup. */
@@ -308,6 +320,13 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
  * densities), in the viscosities of Eq. DynamicViscosity and their density
  * derivatives (Eq. FDviscosityDerivative); tau_e stays. tau_l > 1/2, visc_ratio > 0. */
 pplbm_status pplbm_fd_set_two_phase_viscosity(pplbm_fd* fd, double tau_l, double visc_ratio);
+/* The surface-tension control of pplbm_relax.kappa, as the macroscopic equations
+ * see it: the pressure tensor of Eq. FDforce gains its second-order counterpart
+ * (kappa G/6) psi (delta_ab lap psi - d_a d_b psi), whose divergence
+ * (kappa G/6) [(d_a psi) lap psi - (d_g psi)(d_a d_g psi)] has no third
+ * derivative. kappa finite and < 1 (0 = off), else PPLBM_ERR_ARG. Applies from the
+ * next pplbm_fd_step. */
+pplbm_status pplbm_fd_set_surface_tension(pplbm_fd* fd, double kappa);
 /* Copies the state in / out (device or host pointers; NULL skips an output). Synchronous. */
 pplbm_status pplbm_fd_set_state(pplbm_fd* fd, const double* rho, const double* ux, const double* uy);
 pplbm_status pplbm_fd_get_state(pplbm_fd* fd, double* rho, double* ux, double* uy);

@@ -52,7 +52,8 @@ class pplbm_relax(C.Structure):
                 ("tau_rho", C.c_double), ("tau_e", C.c_double), ("tau_zeta", C.c_double),
                 ("tau_j", C.c_double), ("tau_q", C.c_double), ("tau_nu", C.c_double),
                 ("tau_l", C.c_double), ("visc_ratio", C.c_double),
-                ("sigma", C.c_double), ("sigma_auto", C.c_int32), ("reserved", C.c_int32)]
+                ("sigma", C.c_double), ("sigma_auto", C.c_int32), ("reserved", C.c_int32),
+                ("kappa", C.c_double)]
 
 
 _DERIVED_DOUBLES = ["G", "b", "R", "a_l", "a_v", "Tc_l", "Tc_v", "T_l", "T_v", "rho_v", "rho_l", "p_sat",
@@ -131,6 +132,7 @@ _SIGS = {
     "pplbm_batch_guard": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "pplbm_adjoint_set_slots": (C.c_int, [_P, C.c_uint32]),
     "pplbm_fd_set_two_phase_viscosity": (C.c_int, [_P, C.c_double, C.c_double]),
+    "pplbm_fd_set_surface_tension": (C.c_int, [_P, C.c_double]),
     "pplbm_forward_stored": (C.c_int, [_P, C.c_int64, _P]),
     "pplbm_backward_stored": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_size_t]),
     "pplbm_init": (C.c_int, [C.POINTER(_P), C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),

@@ -449,13 +449,23 @@ size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice) {
   return adj_bytes(lattice);
 }
 
-pplbm_status pplbm_adjoint_step(pplbm_ctx* c, const double* f_t, const double* lambda_next, double* lambda_t,
-                                double* grad, void* adj_workspace, size_t adj_workspace_bytes) {
-  if (!c || !f_t || !lambda_next || !lambda_t || !grad || !adj_workspace) return PPLBM_ERR_ARG;
+// the adjoint differentiates collide_reduced<kUnitTau> without the surface-tension source
+static pplbm_status adjoint_supported(pplbm_ctx* c) {
   if (c->args.kind != kUnitTau) {
     c->msg = "the adjoint covers unit relaxation times only";
     return PPLBM_ERR_STATE;
   }
+  if (c->args.kappa_q != 0.0) {
+    c->msg = "the adjoint does not cover the surface-tension source (kappa != 0)";
+    return PPLBM_ERR_STATE;
+  }
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_adjoint_step(pplbm_ctx* c, const double* f_t, const double* lambda_next, double* lambda_t,
+                                double* grad, void* adj_workspace, size_t adj_workspace_bytes) {
+  if (!c || !f_t || !lambda_next || !lambda_t || !grad || !adj_workspace) return PPLBM_ERR_ARG;
+  if (pplbm_status s = adjoint_supported(c)) return s;
   if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
   return adjoint_step(c, f_t, lambda_next, lambda_t, grad, (double*)adj_workspace, false, true);
 }
@@ -481,10 +491,7 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
   if (!c || nsteps < 0 || interval < 1 || !checkpoints || !segment || !lambda_N || !lambda_0 || !grad ||
       !adj_workspace)
     return PPLBM_ERR_ARG;
-  if (c->args.kind != kUnitTau) {
-    c->msg = "the adjoint covers unit relaxation times only";
-    return PPLBM_ERR_STATE;
-  }
+  if (pplbm_status s = adjoint_supported(c)) return s;
   if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
   if (c->sticky) return c->sticky;
   const int64_t stride = 9 * c->n;
@@ -554,10 +561,7 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
 
 pplbm_status pplbm_forward_stored(pplbm_ctx* c, int64_t nsteps, double* fields) {
   if (!c || nsteps < 0 || !fields) return PPLBM_ERR_ARG;
-  if (c->args.kind != kUnitTau) {
-    c->msg = "the adjoint covers unit relaxation times only";
-    return PPLBM_ERR_STATE;
-  }
+  if (pplbm_status s = adjoint_supported(c)) return s;
   if (c->sticky) return c->sticky;
   const int64_t n = c->n;
   for (int64_t t = 0; t < nsteps; ++t) {
@@ -580,10 +584,7 @@ pplbm_status pplbm_forward_stored(pplbm_ctx* c, int64_t nsteps, double* fields) 
 pplbm_status pplbm_backward_stored(pplbm_ctx* c, int64_t nsteps, const double* fields, const double* lambda_N,
                                    double* lambda_0, double* grad, void* adj_workspace, size_t adj_workspace_bytes) {
   if (!c || nsteps < 0 || !fields || !lambda_N || !lambda_0 || !grad || !adj_workspace) return PPLBM_ERR_ARG;
-  if (c->args.kind != kUnitTau) {
-    c->msg = "the adjoint covers unit relaxation times only";
-    return PPLBM_ERR_STATE;
-  }
+  if (pplbm_status s = adjoint_supported(c)) return s;
   if (adj_workspace_bytes < adj_bytes(&c->lat)) return PPLBM_ERR_ARG;
   if (c->sticky) return c->sticky;
   const int64_t n = c->n, stride = 9 * n;

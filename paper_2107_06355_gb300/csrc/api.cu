@@ -67,6 +67,7 @@ bool valid_lattice(const pplbm_lattice* l) {
 // Collision kind from the relaxation set; -1 if invalid.
 int relax_kind(const pplbm_relax* r) {
   if (!r || r->reserved != 0) return -1;
+  if (!std::isfinite(r->kappa) || !(r->kappa < 1.0)) return -1;
   if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
   if (r->kind == PPLBM_RELAX_TWO_PHASE) {
     if (!(r->tau_l > 0.5) || !(r->visc_ratio > 0.0)) return -1;
@@ -240,6 +241,7 @@ pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const p
     }
   }
   a.zz_scale = sigma * G * G / 432.0;
+  a.kappa_q = relax->kappa * G / 24.0;
   if (kind == kFullMrt) {
     const double t[9] = {relax->tau_rho, relax->tau_e, relax->tau_zeta, relax->tau_j, relax->tau_q,
                          relax->tau_j,   relax->tau_q, relax->tau_nu,   relax->tau_nu};

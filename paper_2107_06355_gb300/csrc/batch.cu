@@ -99,7 +99,7 @@ __device__ __forceinline__ void batch_rho_psi_item(const BatchInst* __restrict__
   __syncthreads();
 }
 
-template <int KIND>
+template <int KIND, bool ST>
 __device__ __forceinline__ void batch_collide_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
                                                    int w, int parity, double* sp, StepArgs* sa) {
   const int id = owner[w];
@@ -115,7 +115,8 @@ __device__ __forceinline__ void batch_collide_item(const BatchInst* __restrict__
   const int lx = threadIdx.x & (tw - 1), ly = threadIdx.x >> log2tw;
   const int x = x0 + lx, y = y0 + ly;
   if (x < a.nx && y < a.ny)
-    collide_node<KIND, false>(a, x, y, sp, (ly + 1) * (tw + 2) + lx + 1, tw + 2, nullptr, nullptr, nullptr, nullptr);
+    collide_node<KIND, false, ST>(a, x, y, sp, (ly + 1) * (tw + 2) + lx + 1, tw + 2, nullptr, nullptr, nullptr,
+                                  nullptr);
   __syncthreads();
 }
 
@@ -125,14 +126,16 @@ __global__ void __launch_bounds__(kThreads) k_batch_rho_psi(const BatchInst* ins
   batch_rho_psi_item<KIND>(inst, owner, blockIdx.x, parity, &sa);
 }
 
-template <int KIND>
+// ST: some instance has the surface-tension source (kappa != 0); for the others
+// kappa_q = 0 makes the source exactly zero, so their results do not change
+template <int KIND, bool ST>
 __global__ void __launch_bounds__(kThreads) k_batch_collide(const BatchInst* inst, const int* owner, int parity) {
   __shared__ double sp[kMaxTileSmem];
   __shared__ StepArgs sa;
-  batch_collide_item<KIND>(inst, owner, blockIdx.x, parity, sp, &sa);
+  batch_collide_item<KIND, ST>(inst, owner, blockIdx.x, parity, sp, &sa);
 }
 
-template <int KIND>
+template <int KIND, bool ST>
 __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* inst, const int* owner1, int n1,
                                                                const int* owner2, int n2, int parity0, long long nsteps,
                                                                GridBarrier* bar, int* err, unsigned spin_limit,
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* 
     const int parity = (int)((parity0 + s) & 1);
     for (int w = blockIdx.x; w < n1; w += gridDim.x) batch_rho_psi_item<KIND>(inst, owner1, w, parity, &sa);
     if (!grid_barrier(bar, err, spin_limit)) return;
-    for (int w = blockIdx.x; w < n2; w += gridDim.x) batch_collide_item<KIND>(inst, owner2, w, parity, sp, &sa);
+    for (int w = blockIdx.x; w < n2; w += gridDim.x) batch_collide_item<KIND, ST>(inst, owner2, w, parity, sp, &sa);
     if (!grid_barrier(bar, err, spin_limit)) return;
   }
 }
@@ -243,30 +246,44 @@ __global__ void __launch_bounds__(kThreads) k_batch_guard_final(const BatchInst*
   }
 }
 
-const void* persistent_kernel(int kind) {
+template <bool ST>
+const void* persistent_kernel_t(int kind) {
   switch (kind) {
-    case kUnitTau: return (const void*)k_batch_persistent<kUnitTau>;
-    case kShearTau: return (const void*)k_batch_persistent<kShearTau>;
-    default: return (const void*)k_batch_persistent<kFullMrt>;
+    case kUnitTau: return (const void*)k_batch_persistent<kUnitTau, ST>;
+    case kShearTau: return (const void*)k_batch_persistent<kShearTau, ST>;
+    default: return (const void*)k_batch_persistent<kFullMrt, ST>;
   }
 }
 
-void launch_pair(int kind, const BatchInst* inst, const int* o1, int n1, const int* o2, int n2, int parity,
-                 cudaStream_t s) {
+const void* persistent_kernel(int kind, bool st) {
+  return st ? persistent_kernel_t<true>(kind) : persistent_kernel_t<false>(kind);
+}
+
+template <bool ST>
+void launch_pair_t(int kind, const BatchInst* inst, const int* o1, int n1, const int* o2, int n2, int parity,
+                   cudaStream_t s) {
   switch (kind) {
     case kUnitTau:
       k_batch_rho_psi<kUnitTau><<<n1, kThreads, 0, s>>>(inst, o1, parity);
-      k_batch_collide<kUnitTau><<<n2, kThreads, 0, s>>>(inst, o2, parity);
+      k_batch_collide<kUnitTau, ST><<<n2, kThreads, 0, s>>>(inst, o2, parity);
       break;
     case kShearTau:
       k_batch_rho_psi<kShearTau><<<n1, kThreads, 0, s>>>(inst, o1, parity);
-      k_batch_collide<kShearTau><<<n2, kThreads, 0, s>>>(inst, o2, parity);
+      k_batch_collide<kShearTau, ST><<<n2, kThreads, 0, s>>>(inst, o2, parity);
       break;
     default:
       k_batch_rho_psi<kFullMrt><<<n1, kThreads, 0, s>>>(inst, o1, parity);
-      k_batch_collide<kFullMrt><<<n2, kThreads, 0, s>>>(inst, o2, parity);
+      k_batch_collide<kFullMrt, ST><<<n2, kThreads, 0, s>>>(inst, o2, parity);
       break;
   }
+}
+
+void launch_pair(int kind, bool st, const BatchInst* inst, const int* o1, int n1, const int* o2, int n2, int parity,
+                 cudaStream_t s) {
+  if (st)
+    launch_pair_t<true>(kind, inst, o1, n1, o2, n2, parity, s);
+  else
+    launch_pair_t<false>(kind, inst, o1, n1, o2, n2, parity, s);
 }
 
 // the density/psi pass alone, over every instance (refreshes psi and the moments)
@@ -287,6 +304,7 @@ int ilog2(int v) {
 // collision kind and validity, as pplbm_create
 int kind_of(const pplbm_relax* r) {
   if (!r || r->reserved != 0) return -1;
+  if (!std::isfinite(r->kappa) || !(r->kappa < 1.0)) return -1;
   if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
   if (r->kind == PPLBM_RELAX_TWO_PHASE) return (r->tau_l > 0.5 && r->visc_ratio > 0.0) ? kShearTau : -1;
   if (r->kind != PPLBM_RELAX_MRT) return -1;
@@ -339,6 +357,7 @@ using namespace pplbm;
 struct pplbm_batch {
   int n;
   int kind;
+  bool st;  // some instance has the surface-tension source
   std::vector<pplbm_lattice> lat;
   std::vector<pplbm_relax> relax;
   std::vector<pplbm_eos_derived> eos;
@@ -445,8 +464,8 @@ pplbm_status build_graphs(pplbm_batch* b) {
   for (int p = 0; p < 2; ++p) {
     cudaGraph_t g;
     BTRY(b, cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
-    launch_pair(b->kind, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, p, b->capture_stream);
-    launch_pair(b->kind, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, 1 - p, b->capture_stream);
+    launch_pair(b->kind, b->st, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, p, b->capture_stream);
+    launch_pair(b->kind, b->st, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, 1 - p, b->capture_stream);
     BTRY(b, cudaStreamEndCapture(b->capture_stream, &g));
     cudaError_t e = cudaGraphInstantiate(&b->graph[p], g, 0);
     cudaGraphDestroy(g);
@@ -504,7 +523,7 @@ pplbm_status launch_persistent(pplbm_batch* b, int64_t nsteps, cudaStream_t s, u
   void* args[] = {(void*)&b->d_inst, (void*)&b->d_owner1, (void*)&b->n1,     (void*)&b->d_owner2,
                   (void*)&b->n2,     (void*)&parity0,     (void*)&ns,        (void*)&b->d_bar,
                   (void*)&b->d_err,  (void*)&spin_limit,  (void*)&absent};
-  BTRY(b, cudaLaunchCooperativeKernel(persistent_kernel(b->kind), dim3(b->persistent_grid), dim3(kThreads), args, 0,
+  BTRY(b, cudaLaunchCooperativeKernel(persistent_kernel(b->kind, b->st), dim3(b->persistent_grid), dim3(kThreads), args, 0,
                                       s));
   return PPLBM_OK;
 }
@@ -520,7 +539,7 @@ pplbm_status issue_steps(pplbm_batch* b, int64_t nsteps, cudaStream_t s) {
     for (; k + 2 <= nsteps; k += 2) BTRY(b, cudaGraphLaunch(b->graph[b->parity], s));
   }
   for (; k < nsteps; ++k) {
-    launch_pair(b->kind, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, b->parity, s);
+    launch_pair(b->kind, b->st, b->d_inst, b->d_owner1, b->n1, b->d_owner2, b->n2, b->parity, s);
     b->parity ^= 1;
   }
   BTRY(b, cudaGetLastError());
@@ -558,6 +577,8 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   if (!b) return PPLBM_ERR_ARG;
   b->n = n;
   b->kind = kind_of(&relax[0]);
+  b->st = false;
+  for (int i = 0; i < n; ++i) b->st = b->st || relax[i].kappa != 0.0;
   b->lat.assign(lattices, lattices + n);
   b->relax.assign(relax, relax + n);
   b->eos.resize(n);
@@ -646,6 +667,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
       }
     }
     a.zz_scale = sigma * G * G / 432.0;
+    a.kappa_q = r.kappa * G / 24.0;
     if (b->kind == kFullMrt) {
       const double t[9] = {r.tau_rho, r.tau_e, r.tau_zeta, r.tau_j, r.tau_q, r.tau_j, r.tau_q, r.tau_nu, r.tau_nu};
       for (int k = 0; k < 9; ++k) a.omega[k] = 1.0 / t[k];
@@ -665,7 +687,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
     w += inst_doubles(L, b->kind);
   }
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel(b->kind), kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel(b->kind, b->st), kThreads, 0);
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

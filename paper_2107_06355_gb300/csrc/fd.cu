@@ -7,7 +7,11 @@
 // (tau_nu - 1/2), mu_B = rho/3 (tau_e - tau_nu), Eq. DynamicViscosity; gradients
 // via dmu/drho, Eq. FDviscosityDerivative) and d_b p'_ab of Eq. FDforce
 //   -eps (G/4)(d_g psi)(d_a d_g psi) + (G/12)(d_a psi) lap psi + (G/6)(d_g psi)(d_a d_g psi)
-//   + (G/4) psi d_a lap psi          (c = 1).
+//   + (G/4) psi d_a lap psi          (c = 1),
+// plus, with the surface-tension control of Sec. V's technique (kappa), the
+// divergence of its second-order pressure tensor (kappa G/6) psi (delta lap psi -
+// d_a d_b psi): (kappa G/6) [(d_a psi) lap psi - (d_g psi)(d_a d_g psi)], which only
+// changes the coefficients of the first and third terms above.
 // Predictor: first derivatives of rho, u, p_EOS and rho in the viscous terms are
 // forward differences; corrector: backward; second derivatives central; every
 // derivative of psi central (the third derivative through lap psi at +-1).
@@ -19,6 +23,7 @@
 // the fluid rows, which a boundary pass fills after each EOS pass.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -211,6 +216,7 @@ struct pplbm_fd {
   EosConst eos;
   pplbm_eos_derived derived;
   double G, eps, dx, mu_c, muB_c, tau_e;
+  double kappa;   // surface-tension control, 0 = off
   bool var_visc;  // tau_nu(rho) = ta + tb rho instead of a constant
   double ta, tb;
   double* U;   // rho, ux, uy
@@ -268,6 +274,7 @@ pplbm_status pplbm_fd_create(pplbm_fd** out, const pplbm_lattice* lattice, const
   f->mu_c = (tau_nu - 0.5) / 3.0;
   f->muB_c = (tau_e - tau_nu) / 3.0;
   f->tau_e = tau_e;
+  f->kappa = 0.0;
   f->var_visc = false;
   double* w = (double*)workspace;
   f->U = w;
@@ -311,8 +318,8 @@ pplbm_status pplbm_fd_step(pplbm_fd* f, int64_t nsteps, double dt) {
   a.walls = f->walls ? 1 : 0;
   const double h = 1.0 / f->dx, h2 = h * h, h3 = h2 * h;
   a.cA = dt * h;
-  a.kS = dt * 0.5 * h3 * (f->G / 6.0 - f->eps * f->G / 4.0);
-  a.kL = dt * 0.5 * h3 * (f->G / 12.0);
+  a.kS = dt * 0.5 * h3 * (f->G / 6.0 - f->eps * f->G / 4.0 - f->kappa * f->G / 6.0);
+  a.kL = dt * 0.5 * h3 * (f->G / 12.0 + f->kappa * f->G / 6.0);
   a.kD = dt * 0.5 * h3 * (f->G / 4.0);
   a.v1 = dt * h2 * f->mu_c;
   a.v2 = dt * h2 * f->muB_c;
@@ -375,6 +382,12 @@ pplbm_status pplbm_fd_set_two_phase_viscosity(pplbm_fd* f, double tau_l, double 
   f->tb = (tau_l - tau_v) / (rl - rv);
   f->ta = tau_l - f->tb * rl;
   f->var_visc = true;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_fd_set_surface_tension(pplbm_fd* f, double kappa) {
+  if (!f || !std::isfinite(kappa) || !(kappa < 1.0)) return PPLBM_ERR_ARG;
+  f->kappa = kappa;
   return PPLBM_OK;
 }
 

@@ -43,6 +43,9 @@ struct StepArgs {
   // kFullMrt: relaxation rates for the 9 moments and the Li sigma terms 12 sigma/(tau - 1/2)
   double omega[9];
   double li_e, li_z;
+  // surface-tension control: kappa G / 24, so Q = kappa_q psi(x) q with
+  // q = 12 sum_i w_i [psi(x + c_i) - psi(x)] c_i c_i; 0 when off
+  double kappa_q;
 };
 
 // Launchers (step_kernels.cu); all asynchronous on `stream`.

@@ -46,6 +46,7 @@ pplbm_status noalloc_fail(const char** message, pplbm_status s, const char* text
 // collision kind of a relaxation set (same rules as pplbm_create); -1 if invalid
 int noalloc_kind(const pplbm_relax* r) {
   if (!r || r->reserved != 0) return -1;
+  if (!std::isfinite(r->kappa) || !(r->kappa < 1.0)) return -1;
   if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
   if (r->kind == PPLBM_RELAX_TWO_PHASE) return (r->tau_l > 0.5 && r->visc_ratio > 0.0) ? kShearTau : -1;
   if (r->kind != PPLBM_RELAX_MRT) return -1;
@@ -126,6 +127,7 @@ extern "C" pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const p
     }
   }
   a.zz_scale = sigma * G * G / 432.0;
+  a.kappa_q = relax->kappa * G / 24.0;
   if (kind == kFullMrt) {
     const double t[9] = {relax->tau_rho, relax->tau_e, relax->tau_zeta, relax->tau_j, relax->tau_q,
                          relax->tau_j,   relax->tau_q, relax->tau_nu,   relax->tau_nu};

@@ -12,6 +12,10 @@
 //    M^-1 m* for the moment vector m* of Eq. LiFS / GFS.
 //  * |F|^2 / psi^2 is (G^2/144) |g|^2 with g the weighted psi differences, so the
 //    Li term needs no division by psi^2.
+//  * The optional surface-tension control (template flag ST) adds Li & Luo's
+//    source C to m*; in population space it joins the Li term's z and the rows
+//    7, 8 terms, so it costs about 20 FP64 instructions per node, and nothing when
+//    the flag is off.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -88,6 +92,28 @@ struct Post {
   double f[9];
 };
 
+// Surface-tension control (the technique of the paper's Sec. V; Li & Luo 2013):
+// tr = Q_xx + Q_yy, df = Q_xx - Q_yy, xy = Q_xy with
+// Q_ab = kappa (G/2) psi(x) sum_i w(|c_i|^2) [psi(x + c_i) - psi(x)] c_ia c_ib.
+struct SurfQ {
+  double tr, df, xy;
+};
+
+// Q from the psi stencil: 12 sum_i w_i [psi_i - psi] c_x^2 = 4 (pE + pW) + dg - 12 psi with
+// dg the four diagonal neighbours, likewise in y, and 12 sum_i w_i psi_i c_x c_y =
+// (pNE + pSW) - (pNW + pSE); kappa_q = kappa G / 24.
+__device__ __forceinline__ SurfQ surface_q(const StepArgs& a, double p0, double pE, double pW, double pN, double pS,
+                                           double pNE, double pNW, double pSW, double pSE) {
+  const double kq = a.kappa_q * p0;
+  const double sA = pE + pW, sB = pN + pS;
+  const double dP = pNE + pSW, dM = pNW + pSE;
+  SurfQ q;
+  q.tr = kq * fma(4.0, sA + sB, 2.0 * fma(-12.0, p0, dP + dM));
+  q.df = kq * (4.0 * (sA - sB));
+  q.xy = kq * (dP - dM);
+  return q;
+}
+
 // Collision for Lambda = I (KIND kUnitTau) or shear-only relaxation (kShearTau).
 //
 // With h = F/2: J = j + h = rho u (Eq. Momentum), P = j + 2h (momentum after the
@@ -99,10 +125,13 @@ struct Post {
 //   f*_i = w_i [rho + 3 c_i.P + 4.5 (c_i c_i - I/3) : Pi] + z_i,
 // z_i = zz (-8, 1, 1, 1, 1, 1, 1, 1, 1) being M^-1 applied to the Li sigma terms
 // +-12 sigma |F|^2 / psi^2 of rows 1 and 2 (tau_e = tau_zeta = 1), zz = sigma |F|^2 / (3 psi^2).
-template <int KIND>
+// With ST, the surface-tension source's rows 1, 2 (+-1.5 tr Q) map onto the same
+// shape with zz += tr Q / 24, and rows 7, 8 (-l_nu (Q_xx - Q_yy), -l_nu Q_xy) add to
+// the post-collision m_7, m_8 (l_nu = 1, or omega for kShearTau).
+template <int KIND, bool ST = false>
 __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node, double rho, double jx, double jy,
-                                                double psi0, double gx, double gy, Post& out, double* ux_o,
-                                                double* uy_o) {
+                                                double psi0, double gx, double gy, const SurfQ& sq, Post& out,
+                                                double* ux_o, double* uy_o) {
   const double cH = a.half_force * psi0;  // h = cH g, cH = -G psi / 24
   const double hx = cH * gx, hy = cH * gy;
   const double inv_rho = fast_rcp(rho);
@@ -113,7 +142,8 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
   const double Pxx = ux * (Px + hx), Pyy = uy * (Py + hy);
   const double tr = Pxx + Pyy;
   const double Pxy_eq = fma(ux, Py, uy * hx);
-  const double zz = a.zz_scale * fma(gx, gx, gy * gy);
+  double zz = a.zz_scale * fma(gx, gx, gy * gy);
+  if (ST) zz = fma(sq.tr, 1.0 / 24.0, zz);
   const double B0 = fma(-1.5, tr, rho);
   const double Q = fma(B0, 1.0 / 9.0, zz);
   double axp, ayp, Pxy;
@@ -121,6 +151,11 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
     axp = fma(0.5, Pxx, Q);
     ayp = fma(0.5, Pyy, Q);
     Pxy = Pxy_eq;
+    if (ST) {
+      axp = fma(-0.25, sq.df, axp);  // m_7* -= Q_xx - Q_yy, n_7 = m_7 / 4
+      ayp = fma(0.25, sq.df, ayp);
+      Pxy -= sq.xy;
+    }
   } else {
     // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S, with m_eq + S/2 = Pi above
     const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
@@ -129,8 +164,12 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
     const double meq7 = fma(ux, Jx, -uy * Jy), meq8 = ux * Jy;
     const double s7 = 4.0 * fma(ux, hx, -uy * hy), s8 = 2.0 * fma(ux, hy, uy * hx);
     const double hw = fma(-0.5, om, 1.0);
-    const double m7s = fma(hw, s7, fma(-om, m7 - meq7, m7));
+    double m7s = fma(hw, s7, fma(-om, m7 - meq7, m7));
     Pxy = fma(hw, s8, fma(-om, m8 - meq8, m8));
+    if (ST) {
+      m7s = fma(-om, sq.df, m7s);
+      Pxy = fma(-om, sq.xy, Pxy);
+    }
     const double T4 = fma(0.25, tr, Q);
     axp = fma(0.25, m7s, T4);  // Q + Pi_xx/2 with Pi_xx = (tr + m7*)/2
     ayp = fma(-0.25, m7s, T4);
@@ -149,9 +188,14 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
   out.f[8] = fma(-pd, 1.0 / 12.0, dm);
 }
 
-// General MRT collision in moment space (six relaxation times).
+// General MRT collision in moment space (six relaxation times). With ST the
+// surface-tension source C_k = l_k D_k enters as the shift D of m_eq in rows 1, 2,
+// 7, 8 (+1.5 tr Q, -1.5 tr Q, -(Q_xx - Q_yy), -Q_xy), since m - l (m - m_eq - D) =
+// m - l (m - m_eq) + l D.
+template <bool ST = false>
 __device__ __forceinline__ void collide_full(const StepArgs& a, int64_t node, double psi0, double gx, double gy,
-                                             Post& out, double* rho_o, double* ux_o, double* uy_o) {
+                                             const SurfQ& sq, Post& out, double* rho_o, double* ux_o,
+                                             double* uy_o) {
   const int64_t N = a.n;
   double m[9];
   m[0] = a.mom[node];
@@ -185,6 +229,12 @@ __device__ __forceinline__ void collide_full(const StepArgs& a, int64_t node, do
   meq[6] = -Jy;                   S[6] = -Fy;
   meq[7] = fma(ux, Jx, -uy * Jy); S[7] = 2.0 * fma(ux, Fx, -uy * Fy);
   meq[8] = ux * Jy;               S[8] = fma(ux, Fy, uy * Fx);
+  if (ST) {
+    meq[1] = fma(1.5, sq.tr, meq[1]);
+    meq[2] = fma(-1.5, sq.tr, meq[2]);
+    meq[7] -= sq.df;
+    meq[8] -= sq.xy;
+  }
   double n[9];
   const double inv_norm[9] = {1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 6.0, 1.0 / 12.0,
                               1.0 / 6.0, 1.0 / 12.0, 1.0 / 4.0,  1.0 / 4.0};
@@ -212,8 +262,9 @@ __device__ __forceinline__ void collide_full(const StepArgs& a, int64_t node, do
 }
 
 // K2 body for node (x, y), whose psi sits at sp[c] of a tile with row stride sw:
-// force, collision, then push streaming (or the macroscopic fields when FIELDS).
-template <int KIND, bool FIELDS>
+// force, collision (with the surface-tension source when ST), then push streaming
+// (or the macroscopic fields when FIELDS, which the source does not change).
+template <int KIND, bool FIELDS, bool ST = false>
 __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, const double* sp, int c, int sw,
                                              double* rho_o, double* ux_o, double* uy_o, double* psi_o) {
   const double p0 = sp[c];
@@ -227,11 +278,14 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   const int64_t node = (int64_t)y * a.nx + x;
   Post o;
   double rho, ux, uy;
+  SurfQ sq = {0.0, 0.0, 0.0};
+  if (ST && !FIELDS) sq = surface_q(a, p0, pE, pW, pN, pS, pNE, pNW, pSW, pSE);
+  constexpr bool kST = ST && !FIELDS;
   if (KIND == kFullMrt) {
-    collide_full(a, node, p0, gx, gy, o, &rho, &ux, &uy);
+    collide_full<kST>(a, node, p0, gx, gy, sq, o, &rho, &ux, &uy);
   } else {
     rho = a.mom[node];
-    collide_reduced<KIND>(a, node, rho, a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, o, &ux, &uy);
+    collide_reduced<KIND, kST>(a, node, rho, a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, sq, o, &ux, &uy);
   }
   if (FIELDS) {
     if (rho_o) rho_o[node] = rho;

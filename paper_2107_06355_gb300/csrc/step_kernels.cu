@@ -11,8 +11,9 @@
 //              x, periodic or wall ghost rows in y), computes the Shan-Chen force
 //              (Eq. ShanChenForce), the velocity with the F/2 shift (Eq. Momentum),
 //              the MRT collision with the Li source (Eqs. OperatorMRT, LiFS,
-//              GFS) and pushes f* to the neighbours (streaming, Eq. LBE), with
-//              half-way bounce-back at walls (Sec. IV).
+//              GFS), optionally the surface-tension source of Sec. V's
+//              technique, and pushes f* to the neighbours (streaming, Eq. LBE),
+//              with half-way bounce-back at walls (Sec. IV).
 #include <cuda_runtime.h>
 
 #include "step_device.cuh"
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(256) k_rho_psi(const StepArgs a) {
   rho_psi_node<KIND>(a, a.f_in, i);
 }
 
-template <int KIND, bool FIELDS>
+template <int KIND, bool FIELDS, bool ST = false>
 __global__ void __launch_bounds__(kTX* kTY) k_collide(const StepArgs a, double* rho_o, double* ux_o, double* uy_o,
                                                       double* psi_o) {
   __shared__ double sp[(kTY + 2) * (kTX + 2)];
@@ -40,8 +41,8 @@ __global__ void __launch_bounds__(kTX* kTY) k_collide(const StepArgs a, double* 
   __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
-  collide_node<KIND, FIELDS>(a, x, y, sp, (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, kTX + 2, rho_o, ux_o,
-                             uy_o, psi_o);
+  collide_node<KIND, FIELDS, ST>(a, x, y, sp, (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, kTX + 2, rho_o, ux_o,
+                                 uy_o, psi_o);
 }
 
 // f_i = f_i^eq(rho0, u0), Eq. EquilibriumDistribution (c_s^2 = 1/3)
@@ -151,6 +152,14 @@ void launch_rho_psi(const StepArgs& a, void* stream) {
 void launch_collide(const StepArgs& a, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const dim3 block(kTX, kTY);
+  if (a.kappa_q != 0.0) {  // with the surface-tension source
+    switch (a.kind) {
+      case kUnitTau: k_collide<kUnitTau, false, true><<<collide_grid(a), block, 0, s>>>(a, 0, 0, 0, 0); break;
+      case kShearTau: k_collide<kShearTau, false, true><<<collide_grid(a), block, 0, s>>>(a, 0, 0, 0, 0); break;
+      default: k_collide<kFullMrt, false, true><<<collide_grid(a), block, 0, s>>>(a, 0, 0, 0, 0); break;
+    }
+    return;
+  }
   switch (a.kind) {
     case kUnitTau: k_collide<kUnitTau, false><<<collide_grid(a), block, 0, s>>>(a, 0, 0, 0, 0); break;
     case kShearTau: k_collide<kShearTau, false><<<collide_grid(a), block, 0, s>>>(a, 0, 0, 0, 0); break;

@@ -13,7 +13,7 @@ class FDSolver:
     bottom and reflexive layers at the top (bc = BC_WALLS_Y)."""
 
     def __init__(self, nx, ny, eos: EOSParams, tau_nu=1.0, tau_e=1.0, dx=1.0, G=-1.0, device="cuda", stream=None,
-                 bc=L.BC_PERIODIC, tau_l=None, visc_ratio=None):
+                 bc=L.BC_PERIODIC, tau_l=None, visc_ratio=None, kappa=0.0):
         import torch
 
         self.torch = torch
@@ -32,6 +32,8 @@ class FDSolver:
         self.h = h
         if tau_l is not None:   # tau_nu(rho) of Eq. RelaxationTime instead of the constant tau_nu
             L.check(L.lib().pplbm_fd_set_two_phase_viscosity(h, float(tau_l), float(visc_ratio)))
+        if kappa != 0.0:        # the surface-tension control's pressure-tensor term
+            L.check(L.lib().pplbm_fd_set_surface_tension(h, float(kappa)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -43,11 +43,12 @@ class Relax:
     visc_ratio: float = 1.0
     sigma: float = 0.0
     sigma_auto: bool = True
+    kappa: float = 0.0  # surface-tension control (Sec. V's technique, Li & Luo 2013); 0 = off
 
     def c(self):
         return L.pplbm_relax(self.kind, self.forcing, self.tau_rho, self.tau_e, self.tau_zeta, self.tau_j,
                              self.tau_q, self.tau_nu, self.tau_l, self.visc_ratio, self.sigma,
-                             1 if self.sigma_auto else 0, 0)
+                             1 if self.sigma_auto else 0, 0, self.kappa)
 
 
 def eos_setup(params: EOSParams, G: float = -1.0) -> dict:

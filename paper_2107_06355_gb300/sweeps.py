@@ -10,6 +10,10 @@ Simpson's rule). Instances are isolated: one that diverges is reported as such
 and the others continue. Stepping and the per-check guard (residual, bad nodes)
 run in the library's kernels; the host evaluates the observables on the
 returned fields at the end.
+
+`laplace_law` fits the 2-D Laplace law on static droplets; with
+`kappa_for_surface_tension` it sets the surface-tension control that the
+paper's Sec. V proposes for keeping the Weber number when alpha changes.
 """
 from __future__ import annotations
 
@@ -72,7 +76,10 @@ def planar_coexistence(cases, nx=2, ny=200, W=10.0, tol=1e-6, check_every=100, m
     initial width; otherwise `W`). Returns one dict per case with keys
     converged, diverged, steps and, unless the case diverged, rho_v, rho_l,
     E_percent, width, width_interp, gamma and the density profile along y.
-    The Sec. III.A residual and the divergence test run in the library's guard."""
+    The Sec. III.A residual and the divergence test run in the library's guard.
+    gamma is Eq. IntegralSurfaceTension of the case's pressure tensor: with the
+    surface-tension control (Relax.kappa) the planar profile does not change and
+    gamma is (1 - kappa) times Eq. SurfaceTension."""
     import torch
 
     n = len(cases)
@@ -113,7 +120,7 @@ def planar_coexistence(cases, nx=2, ny=200, W=10.0, tol=1e-6, check_every=100, m
         rv, rl = float(col_r[0]), float(col_r[ny // 2])
         out[i].update(rho_v=rv, rho_l=rl, E_percent=density_error(rv, maxwell[i][0]),
                       width=interface_width(col_r, rv, rl), width_interp=interface_width_interp(col_r, rv, rl),
-                      gamma=surface_tension(col_p, G), profile=col_r.copy())
+                      gamma=(1.0 - cases[i][1].kappa) * surface_tension(col_p, G), profile=col_r.copy())
     b.close()
     torch.cuda.synchronize()
     return out
@@ -294,6 +301,67 @@ def stability_map(cases, Trs, vrs, steps=4000, check_every=500, u_limit=float("i
         out[key] = dict(run=True, stable=bool(alive[i]), fail_step=fail_step[i], reason=reason[i],
                         umax=float(umax[i]),
                         mass_drift=float(abs(g[i, 0] - g0[i, 0]) / g0[i, 0]) if alive[i] else float("nan"))
+    b.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def kappa_for_surface_tension(gamma_target, gamma_at_kappa0):
+    """kappa of the surface-tension control that turns a surface tension gamma_0
+    (kappa = 0) into gamma_target, from gamma = (1 - kappa) gamma_0: the use the
+    paper's Sec. V proposes, keeping the Weber number (and so the impact velocity)
+    when a smaller alpha lowers the surface tension."""
+    if not (gamma_target > 0 and gamma_at_kappa0 > 0):
+        raise ValueError("surface tensions must be positive")
+    return 1.0 - gamma_target / gamma_at_kappa0
+
+
+def _droplet_profile(n, R, rho_v, rho_l, W):
+    """Centred tanh droplet of radius R on an n x n lattice (the planar profile's form)."""
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    r = np.hypot(x - n / 2.0, y - n / 2.0)
+    return rho_v + (rho_l - rho_v) * 0.5 * (1.0 - np.tanh(4.6 * (r - R) / W))
+
+
+def laplace_law(cases, radii, n=256, steps=40000, W=8.0, G=-1.0):
+    """Static droplets: for each (EOSParams, Relax) case and radius R a centred
+    droplet on a periodic n x n lattice, all advanced together in one batch for
+    `steps` steps. Per droplet: dp = p_EOS(centre) - p_EOS(corner), with p_EOS =
+    rho/3 + G psi^2/2 from the library's psi (Eq. InteractionPotential), and the
+    equimolar radius; per case the 2-D Laplace law dp R = gamma + b/R fitted over the
+    radii. Returns one dict per case: dpR (list), radius (list), gamma, b, diverged."""
+    import torch
+
+    m = len(cases) * len(radii)
+    b = Batch([(n, n, L.BC_PERIODIC)] * m, [c[0] for c in cases for _ in radii],
+              [c[1] for c in cases for _ in radii], G=G)
+    b.set_isolation(True)
+    for k in range(m):
+        d = b.derived(k)
+        b.init_equilibrium(k, _droplet_profile(n, radii[k % len(radii)], d["rho_v"], d["rho_l"], W))
+    b.autotune(trial_steps=4)
+    b.step(steps)
+    b.sync()
+    status = b.instance_status()
+    out = []
+    for c in range(len(cases)):
+        dpR, req, bad = [], [], False
+        for j in range(len(radii)):
+            k = c * len(radii) + j
+            rho, _, _, psi = [t.cpu().numpy() for t in b.fields(k)]
+            if status[k] != 0 or not np.all(np.isfinite(rho)):
+                bad = True
+                break
+            p = rho / 3.0 + G * psi * psi / 2.0
+            rin, rout = rho[n // 2, n // 2], rho[0, 0]
+            Re = float(np.sqrt(((rho - rout) / (rin - rout)).sum() / np.pi))
+            dpR.append(float(p[n // 2, n // 2] - p[0, 0]) * Re)
+            req.append(Re)
+        if bad:
+            out.append(dict(diverged=True))
+            continue
+        slope, gamma = np.polyfit(1.0 / np.array(req), np.array(dpR), 1)
+        out.append(dict(diverged=False, dpR=dpR, radius=req, gamma=float(gamma), b=float(slope)))
     b.close()
     torch.cuda.synchronize()
     return out

@@ -30,7 +30,7 @@ def make_pair(nx, ny, bc, eos_case, relax_kw, forcing_li=True):
     """(oracle Lattice, gpu Simulation) for the same parameters.
 
     eos_case = (mode, Tr, a_l, a_v, alpha); relax_kw: keyword arguments of the
-    library's Relax (kind, tau_*, tau_l, visc_ratio)."""
+    library's Relax (kind, tau_*, tau_l, visc_ratio, kappa)."""
     import paper_2107_06355_gb300 as P
 
     mode, Tr, a_l, a_v, alpha = eos_case[:5]
@@ -41,7 +41,8 @@ def make_pair(nx, ny, bc, eos_case, relax_kw, forcing_li=True):
     orelax = L.Relax(kind=kind, tau_rho=relax_kw.get("tau_rho", 1.0), tau_e=relax_kw.get("tau_e", 1.0),
                      tau_zeta=relax_kw.get("tau_zeta", 1.0), tau_j=relax_kw.get("tau_j", 1.0),
                      tau_q=relax_kw.get("tau_q", 1.0), tau_nu=relax_kw.get("tau_nu", 1.0),
-                     tau_l=relax_kw.get("tau_l", 1.0), visc_ratio=relax_kw.get("visc_ratio", 1.0), sigma=sigma)
+                     tau_l=relax_kw.get("tau_l", 1.0), visc_ratio=relax_kw.get("visc_ratio", 1.0), sigma=sigma,
+                     kappa=relax_kw.get("kappa", 0.0))
     olat = L.Lattice(nx, ny, bc, oe, orelax)
     gp = P.EOSParams(mode=mode, Tr=Tr, a_liq=a_l, a_vap=a_v if mode in SMOOTH_MODES else a_l,
                      alpha=alpha if alpha > 0 else 0.5, r_theta=r_theta)

@@ -212,3 +212,20 @@ def test_tall_lattices_are_rejected_where_the_grids_are_two_dimensional(lib):
     assert lib.pplbm_fd_workspace_bytes(C.byref(tall)) == 0
     rel = (L.pplbm_relax * 1)(relax)
     assert lib.pplbm_batch_workspace_bytes(1, (L.pplbm_lattice * 1)(tall), rel) > 0
+
+
+def test_surface_tension_kappa_is_validated_at_set_up(lib):
+    """kappa (the surface-tension control) must be finite and below 1, where the
+    surface tension (1 - kappa) gamma would vanish or change sign; the check runs in
+    the single-lattice and batched set-ups before any CUDA call. The relax struct's
+    layout in the binding matches the header (kappa after the reserved word)."""
+    lat = L.pplbm_lattice(16, 16, L.BC_PERIODIC, 0)
+    for kind in ({}, {"kind": L.RELAX_TWO_PHASE, "tau_l": 0.7, "visc_ratio": 5.0}, {"tau_e": 0.8}):
+        for kappa, ok in ((0.0, True), (0.5, True), (-2.0, True), (0.999, True), (1.0, False), (3.0, False),
+                          (float("nan"), False), (float("inf"), False)):
+            r = P.Relax(kappa=kappa, **kind).c()
+            assert (lib.pplbm_workspace_bytes(C.byref(lat), C.byref(r)) > 0) == ok, (kind, kappa)
+            arr = (L.pplbm_relax * 1)(r)
+            assert (lib.pplbm_batch_workspace_bytes(1, (L.pplbm_lattice * 1)(lat), arr) > 0) == ok, (kind, kappa)
+    assert C.sizeof(L.pplbm_relax) == 8 + 8 * 9 + 8 + 8
+    assert L.pplbm_relax.kappa.offset == C.sizeof(L.pplbm_relax) - 8
