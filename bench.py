@@ -53,7 +53,7 @@ IMPACT_FP64_PER_NODE = 42.0 + 67.5
 # `bench.py --profile-batch` (profiles/k_batch_collide_k_batch_rho_psi_droplets512.md).
 # They hold for the kernel sources whose digest is recorded with them; once those
 # sources change, traffic is reported as null until the capture is repeated.
-TRAFFIC = {"sources": "b30298601f1ce61b", "rho_psi": 75536384 + 2682880, "collide": 33605291 + 13938005}
+TRAFFIC = {"sources": "1b65f9f3df6d2772", "rho_psi": 75533483 + 2519979, "collide": 33615104 + 13852245}
 KERNEL_SOURCES = ("batch.cu", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
 
 
@@ -214,16 +214,17 @@ def profile_case():
     print("profile case done")
 
 
-def profile_batch():
+def profile_batch(kappa=0.0):
     """The benchmark's four 512 x 512 droplets in one batch, launches plan, 3 steps:
-    3 launches of each batched pass over 1,048,576 nodes (184 MB of state, > L2)."""
+    3 launches of each batched pass over 1,048,576 nodes (184 MB of state, > L2);
+    kappa != 0 runs them with the surface-tension control."""
     import torch
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
 
     build_lib()
     specs = [dict(kind="droplet", nx=NX, ny=NY, R=R, Tr=TR) for R in RADII]
-    b, _, _, _ = make_batch(P, I, specs, torch.cuda.current_stream())
+    b, _, _, _ = make_batch(P, I, specs, torch.cuda.current_stream(), kappa=kappa)
     b.set_plan(P.PLAN_LAUNCHES, 0)
     b.step(3)
     b.sync()
@@ -311,11 +312,12 @@ def serial_sims(torch, stream):
     return sims, rho0s
 
 
-def make_batch(P, I, specs, stream):
-    """A Batch over `specs` (dicts with nx, ny, Tr, kind, R) with tanh initial fields."""
+def make_batch(P, I, specs, stream, kappa=0.0):
+    """A Batch over `specs` (dicts with nx, ny, Tr, kind, R) with tanh initial fields;
+    kappa: the surface-tension control of every instance (0 = off)."""
     eos = [P.EOSParams(P.EOS_SMOOTH, s["Tr"], s.get("a_l", A_L), s.get("a_v", A_V), s.get("alpha", ALPHA))
            for s in specs]
-    relax = [P.Relax() for _ in specs]
+    relax = [P.Relax(kappa=kappa) for _ in specs]
     b = P.Batch([(s["nx"], s["ny"], P.BC_PERIODIC) for s in specs], eos, relax, stream=stream)
     inits = []
     for k, s in enumerate(specs):
@@ -630,11 +632,15 @@ def main():
     ap.add_argument("--profile-fd", action="store_true", help="3 steps of the FD solver on 2048 x 1024 (for ncu)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run the four 512x512 droplets through the batched engine (launches plan) for 3 steps and exit")
+    ap.add_argument("--profile-kappa", type=float, default=None,
+                    help="as --profile-batch, with the surface-tension control at this kappa")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
     if args.profile_batch:
         return profile_batch()
+    if args.profile_kappa is not None:
+        return profile_batch(args.profile_kappa)
     if args.profile_fd:
         return profile_fd()
     if args.profile_impact:

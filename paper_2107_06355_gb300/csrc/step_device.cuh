@@ -14,7 +14,7 @@
 //    Li term needs no division by psi^2.
 //  * The optional surface-tension control (template flag ST) adds Li & Luo's
 //    source C to m*; in population space it joins the Li term's z and the rows
-//    7, 8 terms, so it costs about 20 FP64 instructions per node, and nothing when
+//    7, 8 terms, so it costs about 15 FP64 instructions per node, and nothing when
 //    the flag is off.
 #pragma once
 
@@ -93,24 +93,26 @@ struct Post {
 };
 
 // Surface-tension control (the technique of the paper's Sec. V; Li & Luo 2013):
-// tr = Q_xx + Q_yy, df = Q_xx - Q_yy, xy = Q_xy with
-// Q_ab = kappa (G/2) psi(x) sum_i w(|c_i|^2) [psi(x + c_i) - psi(x)] c_ia c_ib.
+// Q_ab = kappa (G/2) psi(x) sum_i w(|c_i|^2) [psi(x + c_i) - psi(x)] c_ia c_ib, kept as
+// raw stencil sums with the scale k = kappa_q psi(x) (kappa_q = kappa G / 24), so that
+// each use is one FMA:
+//   (Q_xx + Q_yy) / 24 = k t,  t = (pE + pW + pN + pS)/6 + (four diagonals)/12 - psi,
+//   Q_xx - Q_yy = 4 k sd,     sd = (pE + pW) - (pN + pS),
+//   Q_xy = k xd,              xd = (pNE + pSW) - (pNW + pSE)
+// (12 sum_i w_i [psi_i - psi] c_x^2 = 4 (pE + pW) + diagonals - 12 psi, likewise in y).
 struct SurfQ {
-  double tr, df, xy;
+  double k, t, sd, xd;
 };
 
-// Q from the psi stencil: 12 sum_i w_i [psi_i - psi] c_x^2 = 4 (pE + pW) + dg - 12 psi with
-// dg the four diagonal neighbours, likewise in y, and 12 sum_i w_i psi_i c_x c_y =
-// (pNE + pSW) - (pNW + pSE); kappa_q = kappa G / 24.
 __device__ __forceinline__ SurfQ surface_q(const StepArgs& a, double p0, double pE, double pW, double pN, double pS,
                                            double pNE, double pNW, double pSW, double pSE) {
-  const double kq = a.kappa_q * p0;
   const double sA = pE + pW, sB = pN + pS;
   const double dP = pNE + pSW, dM = pNW + pSE;
   SurfQ q;
-  q.tr = kq * fma(4.0, sA + sB, 2.0 * fma(-12.0, p0, dP + dM));
-  q.df = kq * (4.0 * (sA - sB));
-  q.xy = kq * (dP - dM);
+  q.k = a.kappa_q * p0;
+  q.t = fma(1.0 / 6.0, sA + sB, fma(1.0 / 12.0, dP + dM, -p0));
+  q.sd = sA - sB;
+  q.xd = dP - dM;
   return q;
 }
 
@@ -143,7 +145,7 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
   const double tr = Pxx + Pyy;
   const double Pxy_eq = fma(ux, Py, uy * hx);
   double zz = a.zz_scale * fma(gx, gx, gy * gy);
-  if (ST) zz = fma(sq.tr, 1.0 / 24.0, zz);
+  if (ST) zz = fma(sq.k, sq.t, zz);  // + tr Q / 24
   const double B0 = fma(-1.5, tr, rho);
   const double Q = fma(B0, 1.0 / 9.0, zz);
   double axp, ayp, Pxy;
@@ -152,9 +154,9 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
     ayp = fma(0.5, Pyy, Q);
     Pxy = Pxy_eq;
     if (ST) {
-      axp = fma(-0.25, sq.df, axp);  // m_7* -= Q_xx - Q_yy, n_7 = m_7 / 4
-      ayp = fma(0.25, sq.df, ayp);
-      Pxy -= sq.xy;
+      axp = fma(-sq.k, sq.sd, axp);  // m_7* -= Q_xx - Q_yy, n_7 = m_7 / 4
+      ayp = fma(sq.k, sq.sd, ayp);
+      Pxy = fma(-sq.k, sq.xd, Pxy);  // m_8* -= Q_xy
     }
   } else {
     // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S, with m_eq + S/2 = Pi above
@@ -167,8 +169,9 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
     double m7s = fma(hw, s7, fma(-om, m7 - meq7, m7));
     Pxy = fma(hw, s8, fma(-om, m8 - meq8, m8));
     if (ST) {
-      m7s = fma(-om, sq.df, m7s);
-      Pxy = fma(-om, sq.xy, Pxy);
+      const double ok = om * sq.k;
+      m7s = fma(-4.0 * ok, sq.sd, m7s);  // -omega (Q_xx - Q_yy)
+      Pxy = fma(-ok, sq.xd, Pxy);        // -omega Q_xy
     }
     const double T4 = fma(0.25, tr, Q);
     axp = fma(0.25, m7s, T4);  // Q + Pi_xx/2 with Pi_xx = (tr + m7*)/2
@@ -230,10 +233,11 @@ __device__ __forceinline__ void collide_full(const StepArgs& a, int64_t node, do
   meq[7] = fma(ux, Jx, -uy * Jy); S[7] = 2.0 * fma(ux, Fx, -uy * Fy);
   meq[8] = ux * Jy;               S[8] = fma(ux, Fy, uy * Fx);
   if (ST) {
-    meq[1] = fma(1.5, sq.tr, meq[1]);
-    meq[2] = fma(-1.5, sq.tr, meq[2]);
-    meq[7] -= sq.df;
-    meq[8] -= sq.xy;
+    const double k36 = 36.0 * sq.k;  // 1.5 tr Q = 36 k t
+    meq[1] = fma(k36, sq.t, meq[1]);
+    meq[2] = fma(-k36, sq.t, meq[2]);
+    meq[7] = fma(-4.0 * sq.k, sq.sd, meq[7]);
+    meq[8] = fma(-sq.k, sq.xd, meq[8]);
   }
   double n[9];
   const double inv_norm[9] = {1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 6.0, 1.0 / 12.0,
@@ -278,7 +282,7 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   const int64_t node = (int64_t)y * a.nx + x;
   Post o;
   double rho, ux, uy;
-  SurfQ sq = {0.0, 0.0, 0.0};
+  SurfQ sq = {0.0, 0.0, 0.0, 0.0};
   if (ST && !FIELDS) sq = surface_q(a, p0, pE, pW, pN, pS, pNE, pNW, pSW, pSE);
   constexpr bool kST = ST && !FIELDS;
   if (KIND == kFullMrt) {

@@ -201,10 +201,13 @@ def _crossings(h, times):
 
 def test_oscillating_droplet_period_and_fd_agreement_with_kappa():
     """An elliptic droplet (R = 30, semi-axes R (1 +- 0.15), T_r = 0.6 Smooth C-S,
-    tau = 1, 128^2) oscillates with a period ~ sqrt(rho R^3 / gamma): with kappa = 0.5
-    the time between zero crossings of the deformation grows by 1/sqrt(1 - kappa)
-    (within 8 %), and the LBM history agrees with the FD solver (dx = 1/2) carrying
-    the same term to 0.02 in deformation (amplitude 0.14)."""
+    tau = 1, 128^2) oscillates with an undamped frequency ~ sqrt(gamma / (rho R^3)):
+    with kappa = 0.5 it falls by sqrt(1 - kappa). Viscous damping (beta, the same for
+    both) lowers the observed frequency sqrt(w0^2 - beta^2) more for the slower
+    oscillation, so the half period between zero crossings grows by at least
+    1/sqrt(1 - kappa) = 1.414 (measured 1.50); the test takes that bound and at most
+    10 % above it. The LBM history agrees with the FD solver (dx = 1/2) carrying the
+    same term to 0.02 in deformation (amplitude 0.14; measured 0.015)."""
     L_, R, ecc, W, T, every = 128, 30.0, 0.15, 8.0, 6000, 100
     eosp = P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834)
     d = P.eos_setup(eosp)
@@ -239,4 +242,5 @@ def test_oscillating_droplet_period_and_fd_agreement_with_kappa():
     assert len(c0) >= 3 and len(ck) >= 2
     half0 = np.mean(np.diff(c0[:3]))
     halfk = np.mean(np.diff(ck[:2])) if len(ck) < 3 else np.mean(np.diff(ck[:3]))
-    assert abs(halfk / half0 * np.sqrt(1 - 0.5) - 1) < 0.08, (half0, halfk)
+    r = halfk / half0 * np.sqrt(1 - 0.5)
+    assert 1.0 <= r < 1.1, (half0, halfk)
