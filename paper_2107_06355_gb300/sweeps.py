@@ -426,9 +426,53 @@ def stability_study(Trs, vrs, steps=4000, a_cs=0.363, a_v=2.0, check_every=500):
     return dict(planar=planar, tuned=params, map=m)
 
 
+def weber_matching(Trs, a_cs=0.363, a_v=2.0, verify=True, radii=(24.0, 32.0, 48.0), n=192, steps=60000):
+    """Sec. V's proposal across T_r: the Smooth C-S EOS is set to the C-S interface
+    width (alpha tuned as in the stability study, `tune_to_width`), which changes
+    its surface tension; the surface-tension control with
+    kappa = 1 - gamma_CS / gamma_alpha (planar Eq. SurfaceTension values) gives it
+    the C-S surface tension back, so impacts keep their Weber number at an unchanged
+    impact velocity. With `verify`, static droplets of both (C-S, and Smooth C-S
+    with that kappa) at every T_r run in one batch and their Laplace fits
+    (`laplace_law`) are returned beside the planar values.
+
+    Returns {T_r: dict(alpha, width, gamma_cs, gamma_alpha, kappa[, laplace_cs,
+    laplace_matched])}; a T_r whose C-S interface or width tuning fails is absent."""
+    from .lattice import EOSParams, Relax
+
+    cs_cases = [(EOSParams(L.EOS_CS, Tr, a_cs, a_cs, 0.5), Relax()) for Tr in Trs]
+    cs = planar_coexistence_started(cs_cases)
+    fams, keep = [], []
+    for Tr, r in zip(Trs, cs):
+        if r["converged"]:
+            fams.append(dict(target=r["width_interp"], lo=0.02, hi=2.0,
+                             make=lambda p, Tr=Tr: (EOSParams(L.EOS_SMOOTH, Tr, a_cs, a_v, p), Relax())))
+            keep.append((Tr, r))
+    tuned = tune_to_width(fams) if fams else []
+    out = {}
+    for (Tr, r), t in zip(keep, tuned):
+        if not t.get("ok") or not t.get("converged", True):
+            continue
+        k = kappa_for_surface_tension(r["gamma"], t["gamma"])
+        out[Tr] = dict(alpha=t["param"], width=r["width_interp"], gamma_cs=r["gamma"], gamma_alpha=t["gamma"],
+                       kappa=k)
+    if verify and out:
+        cases = []
+        for Tr, v in out.items():
+            cases.append((EOSParams(L.EOS_CS, Tr, a_cs, a_cs, 0.5), Relax()))
+            cases.append((EOSParams(L.EOS_SMOOTH, Tr, a_cs, a_v, v["alpha"]), Relax(kappa=v["kappa"])))
+        lap = laplace_law(cases, radii, n=n, steps=steps)
+        for j, Tr in enumerate(out):
+            c, m = lap[2 * j], lap[2 * j + 1]
+            out[Tr]["laplace_cs"] = None if c["diverged"] else c["gamma"]
+            out[Tr]["laplace_matched"] = None if m["diverged"] else m["gamma"]
+    return out
+
+
 def _main(argv=None):
     """Command line: the stability study over T_r in [0.35, 0.75] (step 0.05) and
-    v_r in 2..24 (step 2), printed as a map and as JSON."""
+    v_r in 2..24 (step 2), printed as a map and as JSON; or, with --weber, the
+    surface-tension control that keeps the C-S surface tension at each T_r."""
     import argparse
     import json
     import time
@@ -436,7 +480,25 @@ def _main(argv=None):
     ap = argparse.ArgumentParser(description=_main.__doc__)
     ap.add_argument("--steps", type=int, default=4000, help="impact steps per run (t* = steps V_d / D)")
     ap.add_argument("--json", default=None, help="write the full result to this file")
+    ap.add_argument("--weber", action="store_true",
+                    help="instead: the surface-tension control that keeps the C-S surface tension for the "
+                         "width-matched Smooth C-S at each T_r, with Laplace-law checks (Sec. V)")
     args = ap.parse_args(argv)
+    if args.weber:
+        Trs = [round(0.35 + 0.05 * k, 2) for k in range(9)]
+        t0 = time.perf_counter()
+        res = weber_matching(Trs)
+        print("  T_r   alpha   gamma_CS   gamma_alpha   kappa    Laplace C-S   Laplace Smooth+kappa")
+        for Tr, v in res.items():
+            print("  %.2f  %.4f  %.4e  %.4e  %+.4f  %s  %s" % (
+                Tr, v["alpha"], v["gamma_cs"], v["gamma_alpha"], v["kappa"],
+                "%.4e" % v["laplace_cs"] if v.get("laplace_cs") else "diverged",
+                "%.4e" % v["laplace_matched"] if v.get("laplace_matched") else "diverged"))
+        print("wall %.1f s" % (time.perf_counter() - t0))
+        if args.json:
+            with open(args.json, "w") as fh:
+                json.dump({str(k): v for k, v in res.items()}, fh, indent=1, default=float)
+        return
     Trs = [round(0.35 + 0.05 * k, 2) for k in range(9)]
     vrs = list(range(2, 25, 2))
     t0 = time.perf_counter()

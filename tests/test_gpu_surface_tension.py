@@ -68,6 +68,22 @@ def test_step_parity_with_kappa(kappa, relax, shape, bc):
     sim.close()
 
 
+@pytest.mark.parametrize("relax", ["unit", "two_phase"])
+def test_step_parity_with_kappa_and_guo_forcing(relax):
+    """With the Guo scheme (sigma = 0) the Li term's z is zero and the source alone
+    fills it. Plain C-S at T_r = 0.8, where Guo forcing is stable (Sec. III.A)."""
+    cs08 = (E.MODE_CS, 0.8, 0.5, 0.5, 0.0)
+    olat, sim = make_pair(40, 24, BC_PER, cs08, dict(RELAX[relax], kappa=0.4), forcing_li=False)
+    rho, ux, uy = _state(40, 24, BC_PER, olat.eos, 31)
+    f = olat.init_equilibrium(rho, ux, uy)
+    sim.init_equilibrium(rho, ux, uy)
+    f = olat.step(f, 8)
+    sim.step(8)
+    sim.sync()
+    assert normwise(sim.get_f().cpu().numpy(), f) < 4e-12
+    sim.close()
+
+
 @pytest.mark.parametrize("mode,width", [(0, 0), (0, 8), (1, 0), (2, 0)])
 def test_batch_with_mixed_kappa_bitwise_equals_single_lattices(mode, width):
     inst = [(4, 90, BC_PER, 0.8, 0.0), (70, 45, BC_PER, 0.6, 0.5), (33, 33, BC_PER, 0.5, -0.4),
@@ -244,3 +260,18 @@ def test_oscillating_droplet_period_and_fd_agreement_with_kappa():
     halfk = np.mean(np.diff(ck[:2])) if len(ck) < 3 else np.mean(np.diff(ck[:3]))
     r = halfk / half0 * np.sqrt(1 - 0.5)
     assert 1.0 <= r < 1.1, (half0, halfk)
+
+
+def test_weber_matching_keeps_the_cs_surface_tension_at_the_cs_width():
+    """Sec. V across T_r (sweeps.weber_matching): the Smooth C-S set to the C-S
+    interface width (a = 0.363, alpha tuned as in the stability study) has a lower
+    surface tension (Table DropImpactParameters at T_r = 0.5: 8.3e-3 against 8.9e-3);
+    kappa = 1 - gamma_CS / gamma_alpha restores it, checked on static droplets
+    (Laplace fits within 3 % of C-S at T_r = 0.5 and 0.6)."""
+    res = S.weber_matching((0.5, 0.6))
+    assert set(res) == {0.5, 0.6}
+    assert res[0.5]["gamma_alpha"] < 0.96 * res[0.5]["gamma_cs"]
+    for Tr, v in res.items():
+        assert v["kappa"] < 0
+        assert v["laplace_cs"] and v["laplace_matched"], (Tr, v)
+        assert abs(v["laplace_matched"] / v["laplace_cs"] - 1) < 0.03, (Tr, v)
