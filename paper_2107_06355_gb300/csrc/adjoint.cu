@@ -127,8 +127,9 @@ __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double r
   *gy_b = gy_bb;
 }
 
-// psi^2(rho) and its derivatives w.r.t. rho and the alpha-dependent constants (eos_dev.cuh)
-__device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, double* dc) {
+// psi^2(rho) and its derivatives w.r.t. rho and the alpha-dependent constants (eos_dev.cuh);
+// the C-S branch constants' derivatives only when bulk_slots (a uniform flag)
+__device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, bool bulk_slots, double* dc) {
   for (int k = 0; k < kA2; ++k) dc[k] = 0.0;
   const long long rb = dbits(rho);
   const bool vap = rb <= e.bits_rho_v, liq = rb >= e.bits_rho_l;
@@ -141,20 +142,20 @@ __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, doubl
     const bool use_v = (e.mode == 1) && vap;
     const double k1 = use_v ? e.k1_v : e.k1_l, k2 = use_v ? e.k2_v : e.k2_l;
     const double eta = e.b4 * rho, om = 1.0 - eta;
-    const double num = fma(eta, fma(eta, om, 1.0), 1.0);
-    const double r = fast_rcp(om);
-    const double r3 = r * r * r;
-    const double Z = num * r3;
-    const double dZ = e.b4 * (4.0 + eta * (4.0 - 2.0 * eta)) * r3 * r;
-    // psi^2 = rho (k1 Z + k2 rho + k3) + k4 (k4 of the vapour branch is 0); constant
-    // indices only, so dc stays in registers
-    const double rz = rho * Z, rr = rho * rho;
-    dc[a2_index(G_K1V)] = use_v ? rz : 0.0;
-    dc[a2_index(G_K2V)] = use_v ? rr : 0.0;
-    dc[a2_index(G_K1L)] = use_v ? 0.0 : rz;
-    dc[a2_index(G_K2L)] = use_v ? 0.0 : rr;
-    dc[a2_index(G_K4L)] = use_v ? 0.0 : 1.0;
-    return fma(k1, Z, fma(k2, rho, e.k3)) + rho * fma(k1, dZ, k2);
+    const double r = fast_rcp(om), r2 = r * r;
+    // psi^2 = rho (k1 Z + k2 rho + k3) + k4 (k4 of the vapour branch is 0), Z of Eq. CS;
+    // d(rho Z)/drho = Z + eta Z'(eta) = (1 + 4 eta + 4 eta^2 - 4 eta^3 + eta^4) / (1 - eta)^4
+    const double P = fma(eta, fma(eta, fma(eta, eta - 4.0, 4.0), 4.0), 1.0);
+    if (bulk_slots) {  // constant indices only, so dc stays in registers
+      const double Z = fma(eta, fma(eta, om, 1.0), 1.0) * (r2 * r);
+      const double rz = rho * Z, rr = rho * rho;
+      dc[a2_index(G_K1V)] = use_v ? rz : 0.0;
+      dc[a2_index(G_K2V)] = use_v ? rr : 0.0;
+      dc[a2_index(G_K1L)] = use_v ? 0.0 : rz;
+      dc[a2_index(G_K2L)] = use_v ? 0.0 : rr;
+      dc[a2_index(G_K4L)] = use_v ? 0.0 : 1.0;
+    }
+    return fma(k1 * (r2 * r2), P, fma(2.0 * k2, rho, e.k3));
   }
   const double s = e.psi2_scale;
   double dp;
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     const double rho = a.mom[node];
     const double psi = a.psi[node];
     double dc[kA2];
-    const double dpsi2 = psi2_grad(a.eos, rho, dc);
+    const double dpsi2 = psi2_grad(a.eos, rho, (g.slots & slot_bits(G_K1V, G_K4L)) != 0u, dc);
     const double psi2_b = 0.5 * psi_b * fast_rcp(psi);  // psi = sqrt(psi^2) > 0 (checked by the step)
     const double rho_b = g.bar[node] + psi2_b * dpsi2;
     const long long rb = dbits(rho);
