@@ -120,8 +120,8 @@ typedef struct pplbm_relax {
      over the Shan-Chen stencil (wall ghosts as for the force). The coexistence
      densities (Eq. VaporLiqEq) are unchanged and the surface tension of Eq.
      IntegralSurfaceTension scales by (1 - kappa). 0 = off (the step is then
-     bitwise the plain one); finite and < 1, else PPLBM_ERR_ARG. Not covered by
-     the adjoint (PPLBM_ERR_STATE there). */
+     bitwise the plain one); finite and < 1, else PPLBM_ERR_ARG. The adjoint
+     (unit relaxation times) differentiates through it. */
   double kappa;
 } pplbm_relax;
 

@@ -11,7 +11,10 @@ a, T of the vapour and liquid branches with the liquid shift Delta P), which are
 inputs here; their dependence on a parameter (alpha, a_v or a_l) is taken from the
 numpy oracle by central differences with Richardson extrapolation.
 
-Only the unit-relaxation-time set (Lambda = I, Sec. III.A) is restated.
+Only the unit-relaxation-time set (Lambda = I, Sec. III.A) is restated, with the
+optional surface-tension source of ``oracle/lbm.py`` (``Relax.kappa``; the technique
+the paper's Sec. V names, Li & Luo 2013): with Lambda = I its moment vector is
+C = [0, 1.5 tr Q, -1.5 tr Q, 0, 0, 0, 0, -(Q_xx - Q_yy), -Q_xy].
 """
 from __future__ import annotations
 
@@ -107,6 +110,27 @@ def step(f, lat: L.Lattice, c):
         sx = sx + _WSC[i] * nb * cx
         sy = sy + _WSC[i] * nb * cy
     Fx, Fy = -G * psi * sx, -G * psi * sy
+    kappa = lat.relax.kappa
+    if kappa != 0.0:
+        # Q_ab = kappa (G/2) psi(x) sum_i w_i [psi(x + c_i) - psi(x)] c_ia c_ib (same ghosts)
+        qxx = torch.zeros_like(psi)
+        qyy = torch.zeros_like(psi)
+        qxy = torch.zeros_like(psi)
+        for i in range(1, 9):
+            cx, cy = int(L.C[i, 0]), int(L.C[i, 1])
+            nb = _roll(psi, -cy, -cx)
+            if walls:
+                rows = torch.arange(ny).reshape(ny, 1).expand_as(psi)
+                if cy == 1:
+                    nb = torch.where(rows == ny - 1, torch.full_like(nb, lat.psi_ghost_top), nb)
+                elif cy == -1:
+                    nb = torch.where(rows == 0, torch.full_like(nb, lat.psi_ghost_bottom), nb)
+            d = nb - psi
+            qxx = qxx + _WSC[i] * d * cx * cx
+            qyy = qyy + _WSC[i] * d * cy * cy
+            qxy = qxy + _WSC[i] * d * cx * cy
+        kq = kappa * G / 2.0 * psi
+        qxx, qyy, qxy = kq * qxx, kq * qyy, kq * qxy
     jx = torch.einsum("i,iyx->yx", _C[:, 0], f)
     jy = torch.einsum("i,iyx->yx", _C[:, 1], f)
     ux = (jx + Fx / 2.0) / rho
@@ -123,6 +147,9 @@ def step(f, lat: L.Lattice, c):
                      -6.0 * uF - 12.0 * sigma * F2 / (psi**2 * 0.5), Fx, -Fx, Fy, -Fy,
                      2.0 * (ux * Fx - uy * Fy), ux * Fy + uy * Fx])
     mstar = m - (m - meq) + 0.5 * S          # Lambda = I
+    if kappa != 0.0:
+        z = torch.zeros_like(rho)
+        mstar = mstar + torch.stack([z, 1.5 * (qxx + qyy), -1.5 * (qxx + qyy), z, z, z, z, -(qxx - qyy), -qxy])
     fstar = torch.einsum("ik,kyx->iyx", _MINV, mstar)
     out = []
     for i in range(9):

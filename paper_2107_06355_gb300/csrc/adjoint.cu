@@ -12,7 +12,9 @@
 //      adjoint;
 //   A2 (per node): psi_bar(y) += sum_c W_c (c_x gx_bar(y - c) + c_y gy_bar(y - c)),
 //      the transpose of the psi stencil written as a gather (W = 4 axis, 1
-//      diagonal; neighbours beyond a wall are ghosts with no adjoint); then
+//      diagonal; neighbours beyond a wall are ghosts with no adjoint), and with the
+//      surface-tension source the transposes of its stencil sums t, sd, xd
+//      (step_device.cuh; symmetric stencils, so the same sums of their adjoints); then
 //      through psi = sqrt(psi^2(rho; constants)) to rho_bar and the constants'
 //      adjoints; lambda^t_i = rho_bar + c_i . j_bar.
 // Constant adjoints are reduced per block and summed in a fixed order
@@ -34,6 +36,10 @@ namespace pplbm {
 namespace {
 
 constexpr int kTX = 32, kTY = 8, kNT = kTX * kTY;
+// adjoint workspace: kBarPlanes adjoint planes, two 9-plane lambda buffers, per-block partials
+constexpr int kBarPlanes = 9;
+constexpr int kLamOffset = kBarPlanes;            // in planes of n values
+constexpr int kPartialOffset = kBarPlanes + 18;
 // gradient slots: the constants of the shaped branches (which alpha moves), the
 // Li-term scale, then the bulk C-S constants the parameters a_vap and a_liq move
 enum { G_PMAX = 0, G_B1, G_IA1, G_A2, G_B2, G_PMIN, G_B3, G_IA3, G_ZZ, G_K1V, G_K2V, G_K1L, G_K2L, G_K4L, kNGrad };
@@ -46,7 +52,8 @@ struct AdjArgs {
   StepArgs a;            // forward arguments of step t (psi, mom filled by K1 on f^t)
   const double* lam1;    // lambda^{t+1}, 9 planes
   double* lam0;          // lambda^t, 9 planes
-  double* bar;           // 6 planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar
+  double* bar;           // kBarPlanes planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar,
+                         // and the surface-tension sums' t_bar, sd_bar, xd_bar
   double* partial1;      // per A1 block: zz-scale adjoint
   double* partial2;      // per A2 block: kA2 constant adjoints (slot order without G_ZZ)
   int accumulate;        // add this step's block sums to the partials (a rollout) instead of storing them
@@ -56,11 +63,13 @@ struct AdjArgs {
 // bits of the slots [k0, k1] of a group
 __host__ __device__ constexpr unsigned slot_bits(int k0, int k1) { return ((2u << k1) - 1u) & ~((1u << k0) - 1u); }
 
-// reverse mode of collide_reduced<kUnitTau> (see its comments for the forward)
+// reverse mode of collide_reduced<kUnitTau> (see its comments for the forward). The
+// surface-tension source only adds to zz, axp, ayp and Pxy, so the adjoints of those
+// four (zq_b) are all it needs; they are returned when zq_b is not null.
 __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double rho, double jx, double jy, double psi0,
                                                      double gx, double gy, const double* mu, double* rho_b,
                                                      double* jx_b, double* jy_b, double* psi_b, double* gx_b,
-                                                     double* gy_b, double* zs_b) {
+                                                     double* gy_b, double* zs_b, double* zq_b = nullptr) {
   // forward recompute
   const double cH = a.half_force * psi0;
   const double hx = cH * gx, hy = cH * gy;
@@ -120,6 +129,12 @@ __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double r
   gx_bb += hx_b * cH;
   gy_bb += hy_b * cH;
   *psi_b = cH_b * a.half_force;
+  if (zq_b) {
+    zq_b[0] = zz_b;
+    zq_b[1] = axp_b;
+    zq_b[2] = ayp_b;
+    zq_b[3] = Pxy_b;
+  }
   *rho_b = r_b;
   *jx_b = jx_bb;
   *jy_b = jy_bb;
@@ -198,6 +213,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
+template <bool ST>
 __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
   __shared__ double sp[(kTY + 2) * (kTX + 2)];
   __shared__ double red[kNT];
@@ -239,9 +255,23 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
     mu[7] = down ? L1[5 * N + node] : L1[7 * N + rs + xw];
     mu[8] = down ? L1[6 * N + node] : L1[8 * N + rs + xe];
     double rb, jxb, jyb, pb, gxb, gyb;
+    double zq_b[4];
     collide_unit_reverse(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, mu, &rb, &jxb, &jyb, &pb,
-                         &gxb, &gyb, &zs_b);
+                         &gxb, &gyb, &zs_b, ST ? zq_b : nullptr);
     double* B = g.bar;
+    if (ST) {
+      // forward: zz += k t, axp -= k sd, ayp += k sd, Pxy -= k xd, k = kappa_q psi(x)
+      const SurfQ sq = surface_q(a, p0, sp[c + 1], sp[c - 1], sp[c + sw], sp[c - sw], sp[c + sw + 1],
+                                 sp[c + sw - 1], sp[c - sw - 1], sp[c - sw + 1]);
+      const double dsd = zq_b[2] - zq_b[1];
+      const double k_b = fma(zq_b[0], sq.t, fma(dsd, sq.sd, -zq_b[3] * sq.xd));
+      const double t_b = zq_b[0] * sq.k;
+      // own node: k = kappa_q psi(x), and t carries -psi(x)
+      pb += fma(k_b, a.kappa_q, -t_b);
+      B[6 * N + node] = t_b;
+      B[7 * N + node] = dsd * sq.k;
+      B[8 * N + node] = -zq_b[3] * sq.k;
+    }
     B[node] = rb;
     B[N + node] = jxb;
     B[2 * N + node] = jyb;
@@ -256,36 +286,33 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
   }
 }
 
-// gx_bar, gy_bar tile with a one-node halo (zero beyond a wall: ghosts carry no adjoint)
-__device__ __forceinline__ void load_gbar_tile(const AdjArgs& g, double* sx, double* sy, int x0, int y0) {
+// tiles of adjoint planes p0 .. p0 + NP - 1 with a one-node halo (zero beyond a wall:
+// ghosts carry no adjoint); tile j at s + j * (kTY + 2) * (kTX + 2)
+template <int NP>
+__device__ __forceinline__ void load_bar_tiles(const AdjArgs& g, int p0, double* s, int x0, int y0) {
   const StepArgs& a = g.a;
-  const int sw = kTX + 2;
-  for (int k = threadIdx.y * kTX + threadIdx.x; k < (kTY + 2) * sw; k += kNT) {
+  const int sw = kTX + 2, ts = (kTY + 2) * sw;
+  for (int k = threadIdx.y * kTX + threadIdx.x; k < ts; k += kNT) {
     const int ty = k / sw, tx = k - ty * sw;
     const int gx = wrap_index(x0 + tx - 1, a.nx);
     int gy = y0 + ty - 1;
-    double vx = 0.0, vy = 0.0;
-    if (a.walls) {
-      if (gy >= 0 && gy < a.ny) {
-        vx = g.bar[4 * a.n + (int64_t)gy * a.nx + gx];
-        vy = g.bar[5 * a.n + (int64_t)gy * a.nx + gx];
-      }
-    } else {
-      gy = wrap_index(gy, a.ny);
-      vx = g.bar[4 * a.n + (int64_t)gy * a.nx + gx];
-      vy = g.bar[5 * a.n + (int64_t)gy * a.nx + gx];
-    }
-    sx[k] = vx;
-    sy[k] = vy;
+    const bool in = !a.walls || (gy >= 0 && gy < a.ny);
+    if (!a.walls) gy = wrap_index(gy, a.ny);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s[j * ts + k] = in ? g.bar[(p0 + j) * a.n + (int64_t)gy * a.nx + gx] : 0.0;
   }
 }
 
+template <bool ST>
 __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
-  __shared__ double sx[(kTY + 2) * (kTX + 2)], sy[(kTY + 2) * (kTX + 2)];
+  constexpr int ts = (kTY + 2) * (kTX + 2);
+  __shared__ double tiles[(ST ? 5 : 2) * ts];  // gx_bar, gy_bar (and t_bar, sd_bar, xd_bar)
   __shared__ double red[kNT];
+  double* sx = tiles;
+  double* sy = tiles + ts;
   const StepArgs& a = g.a;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  load_gbar_tile(g, sx, sy, x0, y0);
+  load_bar_tiles<ST ? 5 : 2>(g, 4, tiles, x0, y0);
   __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   double dcsum[kA2];
@@ -300,7 +327,18 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
                       (sx[c - sw - 1] + sy[c - sw - 1]) - (sx[c + sw + 1] + sy[c + sw + 1]) +
                       (sx[c + sw - 1] - sy[c + sw - 1]) - (sx[c - sw + 1] - sy[c - sw + 1]);
     const int64_t N = a.n, node = (int64_t)y * a.nx + x;
-    const double psi_b = g.bar[3 * N + node] + pg;
+    double psi_b = g.bar[3 * N + node] + pg;
+    if constexpr (ST) {
+      // transposes of t = (axis sum)/6 + (diagonal sum)/12 - psi(x), sd = (pE + pW) - (pN + pS),
+      // xd = (pNE + pSW) - (pNW + pSE) at the neighbours (the -psi(x) term is A1's)
+      const double* st = tiles + 2 * ts;
+      const double* sd = tiles + 3 * ts;
+      const double* sq = tiles + 4 * ts;
+      const double ta = (st[c + 1] + st[c - 1]) + (st[c + sw] + st[c - sw]);
+      const double tg = (st[c + sw + 1] + st[c - sw - 1]) + (st[c + sw - 1] + st[c - sw + 1]);
+      psi_b += fma(1.0 / 6.0, ta, fma(1.0 / 12.0, tg, ((sd[c + 1] + sd[c - 1]) - (sd[c + sw] + sd[c - sw])) +
+                                                      ((sq[c + sw + 1] + sq[c - sw - 1]) - (sq[c + sw - 1] + sq[c - sw + 1]))));
+    }
     const double rho = a.mom[node];
     const double psi = a.psi[node];
     double dc[kA2];
@@ -392,7 +430,7 @@ namespace {
 size_t adj_bytes(const pplbm_lattice* l) {
   const size_t n = (size_t)l->nx * l->ny;
   const size_t nb = (size_t)((l->nx + kTX - 1) / kTX) * ((l->ny + kTY - 1) / kTY);
-  return sizeof(double) * (6 * n + 18 * n + nb * kNGrad + 64);
+  return sizeof(double) * (kPartialOffset * n + nb * kNGrad + 64);
 }
 
 // one adjoint step given the forward arguments of step t whose psi and moment
@@ -405,13 +443,18 @@ pplbm_status adjoint_core(pplbm_ctx* c, const StepArgs& a, const double* lam1, d
   g.lam0 = lam0;
   g.bar = ws;
   const int nb = nblocks(a);
-  g.partial1 = ws + 24 * c->n;
+  g.partial1 = ws + kPartialOffset * c->n;
   g.partial2 = g.partial1 + nb;
   g.accumulate = accumulate ? 1 : 0;
   g.slots = c->adj_slots;
   const dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY), block(kTX, kTY);
-  k_adj_collide<<<grid, block, 0, c->stream>>>(g);
-  k_adj_rho_psi<<<grid, block, 0, c->stream>>>(g);
+  if (a.kappa_q != 0.0) {  // with the surface-tension source
+    k_adj_collide<true><<<grid, block, 0, c->stream>>>(g);
+    k_adj_rho_psi<true><<<grid, block, 0, c->stream>>>(g);
+  } else {
+    k_adj_collide<false><<<grid, block, 0, c->stream>>>(g);
+    k_adj_rho_psi<false><<<grid, block, 0, c->stream>>>(g);
+  }
   if (reduce) k_adj_reduce<<<kNGrad, 256, 0, c->stream>>>(g.partial1, g.partial2, nb, grad);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -450,14 +493,10 @@ size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice) {
   return adj_bytes(lattice);
 }
 
-// the adjoint differentiates collide_reduced<kUnitTau> without the surface-tension source
+// the adjoint differentiates collide_reduced<kUnitTau> (with or without the surface-tension source)
 static pplbm_status adjoint_supported(pplbm_ctx* c) {
   if (c->args.kind != kUnitTau) {
     c->msg = "the adjoint covers unit relaxation times only";
-    return PPLBM_ERR_STATE;
-  }
-  if (c->args.kappa_q != 0.0) {
-    c->msg = "the adjoint does not cover the surface-tension source (kappa != 0)";
     return PPLBM_ERR_STATE;
   }
   return PPLBM_OK;
@@ -497,7 +536,7 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
   if (c->sticky) return c->sticky;
   const int64_t stride = 9 * c->n;
   double* ws = (double*)adj_workspace;
-  double* lamA = ws + 6 * c->n;       // lambda ping-pong inside the adjoint workspace
+  double* lamA = ws + kLamOffset * c->n;  // lambda ping-pong inside the adjoint workspace
   double* lamB = lamA + stride;
   cudaStream_t s = c->stream;
   if (cudaMemcpyAsync(lamA, lambda_N, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
@@ -506,7 +545,7 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
   double* nxt = lamB;
   // per-block constant adjoints are summed over the whole rollout, then reduced once
   const size_t nb = (size_t)nblocks(c->args);
-  double* partials = ws + 24 * c->n;
+  double* partials = ws + kPartialOffset * c->n;
   if (cudaMemsetAsync(partials, 0, sizeof(double) * nb * kNGrad, s) != cudaSuccess) return PPLBM_ERR_CUDA;
   if (nsteps > 0) {
     const int64_t nseg = (nsteps + interval - 1) / interval;
@@ -590,13 +629,13 @@ pplbm_status pplbm_backward_stored(pplbm_ctx* c, int64_t nsteps, const double* f
   if (c->sticky) return c->sticky;
   const int64_t n = c->n, stride = 9 * n;
   double* ws = (double*)adj_workspace;
-  double* cur = ws + 6 * n;
+  double* cur = ws + kLamOffset * n;
   double* nxt = cur + stride;
   cudaStream_t s = c->stream;
   if (cudaMemcpyAsync(cur, lambda_N, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
     return PPLBM_ERR_CUDA;
   const size_t nb = (size_t)nblocks(c->args);
-  double* partials = ws + 24 * n;
+  double* partials = ws + kPartialOffset * n;
   if (cudaMemsetAsync(partials, 0, sizeof(double) * nb * kNGrad, s) != cudaSuccess) return PPLBM_ERR_CUDA;
   for (int64_t t = nsteps - 1; t >= 0; --t) {
     StepArgs a = c->args;

@@ -41,10 +41,13 @@ def _gpu_alpha_grad(grad, spec_eos, relax, which=0):
     return float(sum(g * d for g, d in zip(grad, dc)))
 
 
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
 @pytest.mark.parametrize("shape,bc", [((40, 18), BC_PER), ((37, 22), BC_WALLS)], ids=["periodic", "walls"])
-def test_adjoint_step_matches_oracle_autograd(shape, bc):
+def test_adjoint_step_matches_oracle_autograd(shape, bc, kappa):
+    """One adjoint step against reverse mode through the oracle's torch restatement;
+    kappa != 0 includes the surface-tension source (its stencil sums' transposes)."""
     nx, ny = shape
-    olat, sim = make_pair(nx, ny, bc, CASE, {})
+    olat, sim = make_pair(nx, ny, bc, CASE, {"kappa": kappa})
     f = _state(olat, nx, ny, bc)
     lam1 = np.random.default_rng(11).standard_normal((9, ny, nx))
     # oracle: reverse mode through the torch restatement
@@ -75,9 +78,10 @@ def test_adjoint_step_matches_oracle_autograd(shape, bc):
         assert g_gpu == pytest.approx(g_cpu, rel=1e-6), wrt
 
 
-def test_small_rollout_matches_oracle_reference_adjoint():
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
+def test_small_rollout_matches_oracle_reference_adjoint(kappa):
     nx, ny, nsteps = 24, 24, 30
-    olat, _ = make_pair(nx, ny, BC_PER, CASE, {})
+    olat, _ = make_pair(nx, ny, BC_PER, CASE, {"kappa": kappa})
     e = olat.eos
     rho0 = I.droplet(nx, ny, 6.0, e.rho_v, e.rho_l, W=5.0)
     # oracle reference adjoint
@@ -91,8 +95,8 @@ def test_small_rollout_matches_oracle_reference_adjoint():
     dc_cpu = A.constants_derivative(*CASE[:4], CASE[4])
     galpha_cpu = sum(float(c[k].grad) * dc_cpu[k] for k in A.CONST_NAMES)
     # GPU rollout through the autograd Function
-    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775), P.Relax(),
-                          nsteps, interval=7)
+    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775),
+                          P.Relax(kappa=kappa), nsteps, interval=7)
     rho0_t = torch.tensor(rho0, device="cuda", requires_grad=True)
     alpha = torch.tensor(0.775, dtype=torch.float64, requires_grad=True)
     rhoN = AD.rollout(rho0_t, alpha, spec)
@@ -247,7 +251,8 @@ def test_slot_mask_skips_only_the_deselected_gradients():
     assert L.lib().pplbm_adjoint_set_slots(sim.ctx, 1 << L.NGRAD) == L.PPLBM_ERR_ARG
 
 
-def test_stored_rollout_equals_checkpointed_rollout_bitwise():
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
+def test_stored_rollout_equals_checkpointed_rollout_bitwise(kappa):
     """pplbm_forward_stored / pplbm_backward_stored keep every step's psi and
     moments instead of recomputing them: the gradients are bitwise those of the
     sqrt(N)-checkpointed pair (the Python rollout picks the stored mode when the
@@ -258,7 +263,7 @@ def test_stored_rollout_equals_checkpointed_rollout_bitwise():
     rho0 = I.perturbed(I.droplet(nx, ny, 10.0, d["rho_v"], d["rho_l"], W=6.0), 0.002, 21)
     out = []
     for interval in (0, 6):
-        spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), nsteps, interval=interval)
+        spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(kappa=kappa), nsteps, interval=interval)
         assert spec.stored() == (interval == 0)
         r0 = torch.tensor(rho0, device="cuda", requires_grad=True)
         alpha = torch.tensor(0.775, dtype=torch.float64, requires_grad=True)

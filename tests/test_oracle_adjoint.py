@@ -1,7 +1,7 @@
 """Pins for the oracle's reference adjoint (CPU only): the torch restatement of
 the step equals the numpy oracle step, and its reverse-mode gradients agree with
 central finite differences of the numpy oracle (w.r.t. the initial field and the
-shaping parameter alpha)."""
+shaping parameter alpha), also with the surface-tension control on (kappa)."""
 import numpy as np
 import pytest
 
@@ -17,10 +17,10 @@ PER = L.BC_PERIODIC_X | L.BC_PERIODIC_Y
 WALLS = L.BC_PERIODIC_X | L.BC_WALL_BOTTOM | L.BC_WALL_TOP
 
 
-def lattice(nx, ny, bc, alpha=CASE[4]):
+def lattice(nx, ny, bc, alpha=CASE[4], kappa=0.0):
     e = E.make_eos(CASE[0], CASE[1], CASE[2], CASE[3], alpha)
     e.solve_eps(n=40000)
-    return L.Lattice(nx, ny, bc, e, L.Relax(sigma=e.sigma()))
+    return L.Lattice(nx, ny, bc, e, L.Relax(sigma=e.sigma(), kappa=kappa))
 
 
 def initial(lat, nx, ny, bc):
@@ -33,9 +33,10 @@ def initial(lat, nx, ny, bc):
     return lat.init_equilibrium(rho, ux, uy)
 
 
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
 @pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
-def test_torch_step_equals_numpy_oracle(bc):
-    lat = lattice(12, 10, bc)
+def test_torch_step_equals_numpy_oracle(bc, kappa):
+    lat = lattice(12, 10, bc, kappa=kappa)
     f = initial(lat, 12, 10, bc)
     c = A.constants_as_tensors(lat.eos, requires_grad=False)
     g = torch.tensor(f)
@@ -45,10 +46,11 @@ def test_torch_step_equals_numpy_oracle(bc):
     assert np.max(np.abs(g.numpy() - f)) < 1e-14 * np.max(np.abs(f))
 
 
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
 @pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
-def test_gradient_wrt_initial_field_matches_finite_differences(bc):
+def test_gradient_wrt_initial_field_matches_finite_differences(bc, kappa):
     nx, ny, steps = 10, 12, 5
-    lat = lattice(nx, ny, bc)
+    lat = lattice(nx, ny, bc, kappa=kappa)
     e = lat.eos
     f0 = initial(lat, nx, ny, bc)
     c = A.constants_as_tensors(e, requires_grad=False)
