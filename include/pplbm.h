@@ -228,16 +228,18 @@ pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux
  * all 1 (other sets return PPLBM_ERR_STATE). Gradients flow to the state and to
  * the EOS constants that the shaping parameters move (Sec. III.D):
  * grad[PPLBM_NGRAD] = dL/d{p_max, b1, 1/a1^2, a2, b2, p_min, b3, 1/a3^2, z,
- *                          k1_v, k2_v, k1_l, k2_l, k4_l},
+ *                          k1_v, k2_v, k1_l, k2_l, k4_l, kappa},
  * with a2, b2 the cubic's coefficients, z = sigma G^2/432 the Li term's scale
  * (Eq. LiFS), and k1 = (2/G) R T, k2 = -(2/G) a, k4 = (2/G) Delta P the constants of
  * psi^2 = rho (k1 Z(rho) + k2 rho - 2/(3G)) + k4 on the vapour (v) and liquid (l)
- * C-S branches (Eq. CS, Eq. InteractionPotential). pplbm_eos_constant_sensitivity
+ * C-S branches (Eq. CS, Eq. InteractionPotential), and kappa the surface-tension
+ * control, pplbm_relax.kappa; its slot is computed also at kappa = 0, through the
+ * source's kernels with a zero scale. pplbm_eos_constant_sensitivity
  * gives their derivatives with respect to alpha, a_vap or a_liq, so dL/dtheta =
  * sum_k grad[k] dc[k]. At fixed T_r the branch boundaries (rho_v, rho_l, rho_max,
  * rho_min) do not depend on these parameters, so the chain is exact. All pointers
  * are device memory unless noted. */
-#define PPLBM_NGRAD 14
+#define PPLBM_NGRAD 15
 
 /* Bytes of the adjoint workspace (adjoint planes, lambda ping-pong, per-block partials). */
 size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice);
@@ -283,12 +285,13 @@ pplbm_status pplbm_adjoint_set_slots(pplbm_ctx* ctx, uint32_t mask);
 /* rho0_bar = sum_i w_i lambda_0[i]: the gradient w.r.t. the initial density of
  * f^0 = f^eq(rho0, u = 0) (Sec. III.A). */
 pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* ctx, const double* lambda_0, double* rho0_bar);
-/* Host only: the values of the PPLBM_NGRAD constants (z left 0). */
+/* Host only: the values of the PPLBM_NGRAD constants (z and kappa left 0). */
 pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* eos, double c[PPLBM_NGRAD]);
 /* Host only: dc/dtheta of the PPLBM_NGRAD constants for theta = alpha (which = 0),
  * a_vap (1) or a_liq (2), including z through sigma(theta) when relax->sigma_auto,
  * by central differences of pplbm_eos_setup at steps h and h/2 combined by
- * Richardson extrapolation (error O(h^4)). PPLBM_ERR_ARG for another `which`. */
+ * Richardson extrapolation (error O(h^4)); for theta = kappa (3) exactly the unit
+ * vector of its slot. PPLBM_ERR_ARG for another `which`. */
 pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* params, double G, const pplbm_relax* relax,
                                             int32_t which, double h, double dc[PPLBM_NGRAD]);
 

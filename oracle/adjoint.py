@@ -110,8 +110,10 @@ def step(f, lat: L.Lattice, c):
         sx = sx + _WSC[i] * nb * cx
         sy = sy + _WSC[i] * nb * cy
     Fx, Fy = -G * psi * sx, -G * psi * sy
-    kappa = lat.relax.kappa
-    if kappa != 0.0:
+    # kappa: a tensor in c (to differentiate by it) or the lattice's Relax.kappa
+    kappa = c["kappa"] if "kappa" in c else lat.relax.kappa
+    with_st = torch.is_tensor(kappa) or kappa != 0.0
+    if with_st:
         # Q_ab = kappa (G/2) psi(x) sum_i w_i [psi(x + c_i) - psi(x)] c_ia c_ib (same ghosts)
         qxx = torch.zeros_like(psi)
         qyy = torch.zeros_like(psi)
@@ -147,7 +149,7 @@ def step(f, lat: L.Lattice, c):
                      -6.0 * uF - 12.0 * sigma * F2 / (psi**2 * 0.5), Fx, -Fx, Fy, -Fy,
                      2.0 * (ux * Fx - uy * Fy), ux * Fy + uy * Fx])
     mstar = m - (m - meq) + 0.5 * S          # Lambda = I
-    if kappa != 0.0:
+    if with_st:
         z = torch.zeros_like(rho)
         mstar = mstar + torch.stack([z, 1.5 * (qxx + qyy), -1.5 * (qxx + qyy), z, z, z, z, -(qxx - qyy), -qxy])
     fstar = torch.einsum("ik,kyx->iyx", _MINV, mstar)

@@ -79,11 +79,12 @@ class pplbm_batch_plan(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
-NGRAD = 14
+NGRAD = 15
 GRAD_NAMES = ("p_max", "b1", "inv_a1sq", "a2", "b2", "p_min", "b3", "inv_a3sq", "zz_scale",
-              "k1_v", "k2_v", "k1_l", "k2_l", "k4_l")
-# parameters pplbm_eos_constant_sensitivity differentiates by (its `which`)
-SENS_PARAMS = {"alpha": 0, "a_vap": 1, "a_liq": 2}
+              "k1_v", "k2_v", "k1_l", "k2_l", "k4_l", "kappa")
+# parameters pplbm_eos_constant_sensitivity differentiates by (its `which`); kappa
+# belongs to the relaxation set (Relax.kappa), the others to the EOS
+SENS_PARAMS = {"alpha": 0, "a_vap": 1, "a_liq": 2, "kappa": 3}
 
 PLAN_LAUNCHES = 0
 PLAN_GRAPH = 1

@@ -8,7 +8,8 @@ output rho^N. Backward: pplbm_backward_stored, or pplbm_backward_checkpointed
 dL/d(EOS constants); the initial-density gradient is
 sum_i w_i dL/df^0_i and the parameter gradient (alpha, a_vap or a_liq, chosen by
 RolloutSpec.param) chains the constants' gradients with their derivatives
-(pplbm_eos_constant_sensitivity). Argument marshalling only: every step runs in
+(pplbm_eos_constant_sensitivity); for kappa, the surface-tension control, it is
+the kappa slot itself. Argument marshalling only: every step runs in
 the library's kernels.
 """
 from __future__ import annotations
@@ -31,7 +32,7 @@ class RolloutSpec:
     nsteps: int
     interval: int = 0       # > 0: checkpoints every `interval` steps; 0: automatic (see `stored`)
     G: float = -1.0
-    param: str = "alpha"    # "alpha", "a_vap" or "a_liq"
+    param: str = "alpha"    # "alpha", "a_vap", "a_liq" (EOS) or "kappa" (Relax)
     memory_fraction: float = 0.25  # automatic mode: share of free device memory the stored fields may take
 
     def k(self):
@@ -50,10 +51,11 @@ class RolloutSpec:
 
 
 def param_sensitivity(spec: RolloutSpec, value: float, h: float = 1e-4):
-    """d(EOS constants)/d(spec.param) at spec.param = value, PPLBM_NGRAD values (host)."""
+    """d(gradient constants)/d(spec.param) at spec.param = value, PPLBM_NGRAD values (host)."""
     dc = (C.c_double * L.NGRAD)()
-    p = _with_param(spec, value).c()
-    r = spec.relax.c()
+    eos, relax = _with_param(spec, value)
+    p = eos.c()
+    r = relax.c()
     L.check(L.lib().pplbm_eos_constant_sensitivity(C.byref(p), spec.G, C.byref(r), L.SENS_PARAMS[spec.param], h,
                                                    dc))
     return list(dc)
@@ -64,16 +66,20 @@ def alpha_sensitivity(spec: RolloutSpec, alpha: float, h: float = 1e-4):
     return param_sensitivity(replace(spec, param="alpha"), alpha, h)
 
 
-def _with_param(spec: RolloutSpec, value: float) -> EOSParams:
+def _with_param(spec: RolloutSpec, value: float):
+    """(EOSParams, Relax) with spec.param set to value."""
     if spec.param not in L.SENS_PARAMS:
         raise ValueError(f"unknown parameter {spec.param!r}")
-    return replace(spec.eos, **{spec.param: value})
+    if spec.param == "kappa":
+        return spec.eos, replace(spec.relax, kappa=value)
+    return replace(spec.eos, **{spec.param: value}), spec.relax
 
 
 def _rollout_forward(spec: RolloutSpec, rho0, value: float):
     import torch
 
-    sim = Simulation(spec.nx, spec.ny, spec.bc, _with_param(spec, value), spec.relax, G=spec.G)
+    eos, relax = _with_param(spec, value)
+    sim = Simulation(spec.nx, spec.ny, spec.bc, eos, relax, G=spec.G)
     sim.init_equilibrium(rho0)
     if spec.stored():
         # ckpt holds every step's psi and moments

@@ -41,11 +41,15 @@ constexpr int kBarPlanes = 9;
 constexpr int kLamOffset = kBarPlanes;            // in planes of n values
 constexpr int kPartialOffset = kBarPlanes + 18;
 // gradient slots: the constants of the shaped branches (which alpha moves), the
-// Li-term scale, then the bulk C-S constants the parameters a_vap and a_liq move
-enum { G_PMAX = 0, G_B1, G_IA1, G_A2, G_B2, G_PMIN, G_B3, G_IA3, G_ZZ, G_K1V, G_K2V, G_K1L, G_K2L, G_K4L, kNGrad };
+// Li-term scale, the bulk C-S constants the parameters a_vap and a_liq move, and the
+// surface-tension control's kappa
+enum {
+  G_PMAX = 0, G_B1, G_IA1, G_A2, G_B2, G_PMIN, G_B3, G_IA3, G_ZZ, G_K1V, G_K2V, G_K1L, G_K2L, G_K4L, G_KAPPA, kNGrad
+};
 static_assert(kNGrad == PPLBM_NGRAD, "gradient slot count");
-// A2 reduces every slot but G_ZZ (A1's); its local index of slot k
-constexpr int kA2 = kNGrad - 1;
+// A1 reduces G_ZZ and G_KAPPA (two values per block), A2 every other slot; A2's
+// local index of slot k (k != G_ZZ, k < G_KAPPA)
+constexpr int kA2 = kNGrad - 2;
 __host__ __device__ constexpr int a2_index(int k) { return k < G_ZZ ? k : k - 1; }
 
 struct AdjArgs {
@@ -54,8 +58,8 @@ struct AdjArgs {
   double* lam0;          // lambda^t, 9 planes
   double* bar;           // kBarPlanes planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar,
                          // and the surface-tension sums' t_bar, sd_bar, xd_bar
-  double* partial1;      // per A1 block: zz-scale adjoint
-  double* partial2;      // per A2 block: kA2 constant adjoints (slot order without G_ZZ)
+  double* partial1;      // per A1 block: the zz-scale and kappa adjoints
+  double* partial2;      // per A2 block: kA2 constant adjoints (slot order without G_ZZ, G_KAPPA)
   int accumulate;        // add this step's block sums to the partials (a rollout) instead of storing them
   unsigned slots;        // bit k set: gradient slot k is accumulated (others stay 0)
 };
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
   load_psi_tile(a, sp, x0, y0, kTX, kTY, threadIdx.y * kTX + threadIdx.x, kNT);
   __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  double zs_b = 0.0;
+  double zs_b = 0.0, kap_b = 0.0;
   if (x < a.nx && y < a.ny) {
     const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
     const double p0 = sp[c];
@@ -266,8 +270,9 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
       const double dsd = zq_b[2] - zq_b[1];
       const double k_b = fma(zq_b[0], sq.t, fma(dsd, sq.sd, -zq_b[3] * sq.xd));
       const double t_b = zq_b[0] * sq.k;
-      // own node: k = kappa_q psi(x), and t carries -psi(x)
+      // own node: k = kappa_q psi(x), and t carries -psi(x); kappa_q = kappa G / 24
       pb += fma(k_b, a.kappa_q, -t_b);
+      kap_b = k_b * p0 * (a.G / 24.0);
       B[6 * N + node] = t_b;
       B[7 * N + node] = dsd * sq.k;
       B[8 * N + node] = -zq_b[3] * sq.k;
@@ -279,10 +284,13 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
     B[4 * N + node] = gxb;
     B[5 * N + node] = gyb;
   }
-  const double s = (g.slots >> G_ZZ) & 1u ? block_sum(zs_b, red) : 0.0;  // grid-uniform test
+  // grid-uniform tests
+  const double s = (g.slots >> G_ZZ) & 1u ? block_sum(zs_b, red) : 0.0;
+  const double sk = ST && ((g.slots >> G_KAPPA) & 1u) ? block_sum(kap_b, red) : 0.0;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double* dst = g.partial1 + blockIdx.y * gridDim.x + blockIdx.x;
-    *dst = g.accumulate ? *dst + s : s;
+    double* dst = g.partial1 + 2 * (blockIdx.y * gridDim.x + blockIdx.x);
+    dst[0] = g.accumulate ? dst[0] + s : s;
+    dst[1] = g.accumulate ? dst[1] + sk : sk;
   }
 }
 
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(256) k_adj_reduce(const double* partial1, cons
   const int k = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += 256)
-    acc += k == G_ZZ ? partial1[b] : partial2[(int64_t)b * kA2 + a2_index(k)];
+    acc += k == G_ZZ ? partial1[2 * b] : k == G_KAPPA ? partial1[2 * b + 1] : partial2[(int64_t)b * kA2 + a2_index(k)];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -444,11 +452,11 @@ pplbm_status adjoint_core(pplbm_ctx* c, const StepArgs& a, const double* lam1, d
   g.bar = ws;
   const int nb = nblocks(a);
   g.partial1 = ws + kPartialOffset * c->n;
-  g.partial2 = g.partial1 + nb;
+  g.partial2 = g.partial1 + 2 * nb;
   g.accumulate = accumulate ? 1 : 0;
   g.slots = c->adj_slots;
   const dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY), block(kTX, kTY);
-  if (a.kappa_q != 0.0) {  // with the surface-tension source
+  if (a.kappa_q != 0.0 || ((g.slots >> G_KAPPA) & 1u)) {  // with the surface-tension source (kappa_q may be 0)
     k_adj_collide<true><<<grid, block, 0, c->stream>>>(g);
     k_adj_rho_psi<true><<<grid, block, 0, c->stream>>>(g);
   } else {
@@ -592,7 +600,7 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
       }
     }
   }
-  k_adj_reduce<<<kNGrad, 256, 0, s>>>(partials, partials + nb, (int)nb, grad);
+  k_adj_reduce<<<kNGrad, 256, 0, s>>>(partials, partials + 2 * nb, (int)nb, grad);
   if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   if (cudaMemcpyAsync(lambda_0, cur, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
     return PPLBM_ERR_CUDA;
@@ -644,7 +652,7 @@ pplbm_status pplbm_backward_stored(pplbm_ctx* c, int64_t nsteps, const double* f
     if (pplbm_status st = adjoint_core(c, a, cur, nxt, grad, ws, true, false)) return st;
     std::swap(cur, nxt);
   }
-  k_adj_reduce<<<kNGrad, 256, 0, s>>>(partials, partials + nb, (int)nb, grad);
+  k_adj_reduce<<<kNGrad, 256, 0, s>>>(partials, partials + 2 * nb, (int)nb, grad);
   if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   if (cudaMemcpyAsync(lambda_0, cur, sizeof(double) * stride, cudaMemcpyDefault, s) != cudaSuccess)
     return PPLBM_ERR_CUDA;
@@ -667,14 +675,18 @@ pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* d, double c[PPLBM
   if (!d || !c) return PPLBM_ERR_ARG;
   const EosConst e = make_eos_const(*d);
   const double vals[PPLBM_NGRAD] = {e.p_max, e.b1, e.inv_a1sq, e.a2, e.b2, e.p_min, e.b3,
-                                    e.inv_a3sq, 0.0, e.k1_v, e.k2_v, e.k1_l, e.k2_l, e.k4_l};
+                                    e.inv_a3sq, 0.0, e.k1_v, e.k2_v, e.k1_l, e.k2_l, e.k4_l, 0.0};
   std::memcpy(c, vals, sizeof(vals));
   return PPLBM_OK;
 }
 
 pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* p, double G, const pplbm_relax* relax,
                                             int32_t which, double h, double dc[PPLBM_NGRAD]) {
-  if (!p || !relax || !dc || which < 0 || which > 2 || !(h > 0.0)) return PPLBM_ERR_ARG;
+  if (!p || !relax || !dc || which < 0 || which > 3 || !(h > 0.0)) return PPLBM_ERR_ARG;
+  if (which == 3) {  // kappa is its own slot
+    for (int k = 0; k < PPLBM_NGRAD; ++k) dc[k] = k == G_KAPPA ? 1.0 : 0.0;
+    return PPLBM_OK;
+  }
   auto at = [&](double v, double* out) -> pplbm_status {
     pplbm_eos_params q = *p;
     (which == 0 ? q.alpha : which == 1 ? q.a_vap : q.a_liq) = v;

@@ -52,6 +52,7 @@ def test_adjoint_step_matches_oracle_autograd(shape, bc, kappa):
     lam1 = np.random.default_rng(11).standard_normal((9, ny, nx))
     # oracle: reverse mode through the torch restatement
     c = A.constants_as_tensors(olat.eos)
+    c["kappa"] = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
     x = torch.tensor(f, requires_grad=True)
     (A.step(x, olat, c) * torch.tensor(lam1)).sum().backward()
     dc_cpu = A.constants_derivative(*CASE[:4], CASE[4])
@@ -67,6 +68,9 @@ def test_adjoint_step_matches_oracle_autograd(shape, bc, kappa):
     assert L.lib().pplbm_adjoint_step(sim.ctx, p(fd), p(l1), p(l0), p(grad), p(ws), nbytes) == 0
     torch.cuda.synchronize()
     assert normwise(l0.cpu().numpy(), x.grad.numpy()) < 1e-12
+    # dL/dkappa: its own slot (computed at kappa = 0 too, the default slots including it)
+    assert float(c["kappa"].grad) != 0.0
+    assert float(grad[L.GRAD_NAMES.index("kappa")]) == pytest.approx(float(c["kappa"].grad), rel=1e-9)
     galpha_gpu = _gpu_alpha_grad(grad.tolist(), sim.eos_params, sim.relax)
     assert galpha_gpu == pytest.approx(galpha_cpu, rel=1e-6)
     # the branch parameters: the GPU's k1, k2, k4 slots against the oracle's a, T, Delta P
@@ -272,3 +276,34 @@ def test_stored_rollout_equals_checkpointed_rollout_bitwise(kappa):
         out.append((rhoN.detach().cpu(), r0.grad.cpu(), float(alpha.grad)))
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.4])
+def test_rollout_gradient_wrt_kappa_matches_finite_differences(kappa):
+    """dL/dkappa of a checkpointed rollout (the surface-tension control, its own
+    gradient slot) against central differences of the forward rollout: a 48^2
+    droplet (T_r = 0.5, Smooth C-S), 300 steps, loss = droplet-shape mismatch (the
+    oracle's reverse mode on the same case gives 0.64268440237 at kappa = 0.4, the
+    GPU adjoint 0.64268440234)."""
+    nx = ny = 48
+    eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
+    d = P.eos_setup(eosp)
+    rho0 = I.perturbed(I.droplet(nx, ny, 12.0, d["rho_v"], d["rho_l"], W=6.0), 0.002, 5)
+    spec = AD.RolloutSpec(nx, ny, P.BC_PERIODIC, eosp, P.Relax(), 300, interval=20, param="kappa")
+
+    def loss(rhoN):
+        return A.droplet_loss(rhoN, d["rho_v"], d["rho_l"], 12.0)
+
+    r0 = torch.tensor(rho0, device="cuda", requires_grad=True)
+    k = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    loss(AD.rollout(r0, k, spec)).backward()
+    h = 1e-4
+    with torch.no_grad():
+        # float64: a float32 theta would round kappa +- h by ~1e-8, 1e-4 of the step
+        lp = float(loss(AD.rollout(torch.tensor(rho0, device="cuda"), torch.tensor(kappa + h, dtype=torch.float64),
+                                   spec)))
+        lm = float(loss(AD.rollout(torch.tensor(rho0, device="cuda"), torch.tensor(kappa - h, dtype=torch.float64),
+                                   spec)))
+    fd = (lp - lm) / (2 * h)
+    assert abs(fd) > 1e-8
+    assert float(k.grad) == pytest.approx(fd, rel=1e-6)

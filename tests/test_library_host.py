@@ -144,7 +144,7 @@ def test_one_call_setups_reject_missing_fields_without_touching_the_gpu(lib):
 def test_constant_sensitivity_of_the_bulk_branches_has_closed_forms(lib):
     """k2 = -(2/G) a and k1 = (2/G) R T with T = T_r T_c(a), T_c proportional to a
     (Eq. CS, Sec. III.D): dk2/da = -2/G, dk1/da = k1/a on the branch the parameter
-    owns and 0 on the other; alpha moves no bulk constant."""
+    owns and 0 on the other; alpha moves no bulk constant; kappa only its own slot."""
     G = -1.0
     eos = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
     relax = P.Relax().c()
@@ -171,8 +171,12 @@ def test_constant_sensitivity_of_the_bulk_branches_has_closed_forms(lib):
         assert abs(sens["alpha"][idx[k]]) < 1e-9
     # Delta P = p_sat(a_v) - p_sat(a_l): both parameters move the liquid shift
     assert abs(sens["a_vap"][idx["k4_l"]]) > 0 and abs(sens["a_liq"][idx["k4_l"]]) > 0
+    # kappa (the surface-tension control) is its own slot: the unit vector, and no EOS constant moves
+    assert sens["kappa"] == [1.0 if k == idx["kappa"] else 0.0 for k in range(L.NGRAD)]
+    for name in ("alpha", "a_vap", "a_liq"):
+        assert sens[name][idx["kappa"]] == 0.0
     dc = (C.c_double * L.NGRAD)()
-    assert lib.pplbm_eos_constant_sensitivity(C.byref(p), G, C.byref(relax), 3, 1e-4, dc) == L.PPLBM_ERR_ARG
+    assert lib.pplbm_eos_constant_sensitivity(C.byref(p), G, C.byref(relax), 4, 1e-4, dc) == L.PPLBM_ERR_ARG
 
 
 def _declarations():
