@@ -442,7 +442,9 @@ def adjoint_cost(torch, steps=2000, interval=45):
     lib = L.lib()
     alpha_slots = (1 << 9) - 1   # the shaped-branch constants and the Li-term scale: all alpha moves
     out = {}
-    for label, mask in (("alpha", alpha_slots), ("all_slots", (1 << L.NGRAD) - 1)):
+    # every EOS constant and the Li-term scale (the kappa slot would run the surface-tension kernels)
+    eos_slots = (1 << L.GRAD_NAMES.index("kappa")) - 1
+    for label, mask in (("alpha", alpha_slots), ("all_slots", eos_slots)):
         L.check(lib.pplbm_adjoint_set_slots(sim.ctx, mask), sim.ctx)
         res = []
         for _ in range(2):  # second round is timed
