@@ -126,6 +126,9 @@ def test_planar_interface_evolves_identically_at_unit_tau():
 
 
 def _droplet_dp_r(e, kappa, R, n=64):
+    """dp R of a static droplet (dp = p_EOS(centre) - p_EOS(corner), R equimolar);
+    e None: the T_r = 0.6 Smooth C-S (so spawned workers build it themselves)."""
+    e = _eos06() if e is None else e
     lat = L.Lattice(n, n, PER, e, L.Relax(sigma=e.sigma(), kappa=kappa))
     f = lat.init_equilibrium(I.droplet(n, n, R, e.rho_v, e.rho_l, W=8.0))
     prev = f.sum(0)
@@ -142,10 +145,16 @@ def _droplet_dp_r(e, kappa, R, n=64):
 
 
 def test_laplace_law_surface_tension_scales_by_one_minus_kappa():
-    e = _eos06()
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+
     kappa = 0.5
+    jobs = [(k, R) for R in (10, 14) for k in (0.0, kappa)]
+    # the four droplets are independent: side by side in spawned processes
+    with ProcessPoolExecutor(max_workers=4, mp_context=multiprocessing.get_context("spawn")) as ex:
+        dpr = dict(zip(jobs, ex.map(_droplet_dp_r, [None] * 4, [k for k, _ in jobs], [R for _, R in jobs])))
     for R in (10, 14):
-        ratio = _droplet_dp_r(e, kappa, R) / _droplet_dp_r(e, 0.0, R)
+        ratio = dpr[(kappa, R)] / dpr[(0.0, R)]
         assert abs(ratio / (1 - kappa) - 1) < 0.03, (R, ratio)
 
 
