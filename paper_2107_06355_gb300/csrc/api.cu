@@ -64,24 +64,6 @@ bool valid_lattice(const pplbm_lattice* l) {
   return walls == (PPLBM_BC_WALL_BOTTOM | PPLBM_BC_WALL_TOP);
 }
 
-// Collision kind from the relaxation set; -1 if invalid.
-int relax_kind(const pplbm_relax* r) {
-  if (!r || r->reserved != 0) return -1;
-  if (!std::isfinite(r->kappa) || !(r->kappa < 1.0)) return -1;
-  if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
-  if (r->kind == PPLBM_RELAX_TWO_PHASE) {
-    if (!(r->tau_l > 0.5) || !(r->visc_ratio > 0.0)) return -1;
-    return kShearTau;
-  }
-  if (r->kind != PPLBM_RELAX_MRT) return -1;
-  const double t[6] = {r->tau_rho, r->tau_e, r->tau_zeta, r->tau_j, r->tau_q, r->tau_nu};
-  for (double v : t)
-    if (!(v > 0.5) || !std::isfinite(v)) return -1;
-  if (r->tau_rho == 1.0 && r->tau_e == 1.0 && r->tau_zeta == 1.0 && r->tau_j == 1.0 && r->tau_q == 1.0)
-    return r->tau_nu == 1.0 ? kUnitTau : kShearTau;
-  return kFullMrt;
-}
-
 pplbm_status check_sticky(pplbm_ctx* c) {
   if (c->sticky != PPLBM_OK) return c->sticky;
   return PPLBM_OK;
@@ -158,7 +140,7 @@ const char* pplbm_status_string(pplbm_status s) {
 
 size_t pplbm_workspace_bytes(const pplbm_lattice* lattice, const pplbm_relax* relax) {
   if (!valid_lattice(lattice)) return 0;
-  const int kind = relax_kind(relax);
+  const int kind = collision_kind(relax);
   if (kind < 0) return 0;
   const size_t n = (size_t)lattice->nx * lattice->ny;
   return sizeof(double) * n * (9 + 9 + 1 + (size_t)moment_planes(kind));
@@ -170,7 +152,7 @@ pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const p
   if (!out) return PPLBM_ERR_ARG;
   *out = nullptr;
   if (!valid_lattice(lattice) || !eos || !workspace) return PPLBM_ERR_ARG;
-  const int kind = relax_kind(relax);
+  const int kind = collision_kind(relax);
   if (kind < 0) return PPLBM_ERR_ARG;
   if (workspace_bytes < pplbm_workspace_bytes(lattice, relax)) return PPLBM_ERR_ARG;
   if (((uintptr_t)workspace & 15u) != 0) return PPLBM_ERR_ARG;
@@ -226,29 +208,7 @@ pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const p
   a.half_force = -G / 24.0;
   a.psi_ghost_bottom = d.psi_l;  // liquid below the bottom wall (Sec. IV)
   a.psi_ghost_top = d.psi_v;     // vapour above the top wall
-  const double sigma = relax->forcing == PPLBM_FORCING_GUO ? 0.0
-                       : relax->sigma_auto               ? -d.eps / (16.0 * G)
-                                                         : relax->sigma;
-  if (kind == kShearTau) {
-    if (relax->kind == PPLBM_RELAX_TWO_PHASE) {
-      // tau = tau_l (rho - rho_v)/(rho_l - rho_v) + tau_v (rho - rho_l)/(rho_v - rho_l)
-      const double tv = 0.5 + relax->visc_ratio * (relax->tau_l - 0.5);
-      a.tau_b = (relax->tau_l - tv) / (d.rho_l - d.rho_v);
-      a.tau_a = relax->tau_l - a.tau_b * d.rho_l;
-    } else {
-      a.tau_a = relax->tau_nu;
-      a.tau_b = 0.0;
-    }
-  }
-  a.zz_scale = sigma * G * G / 432.0;
-  a.kappa_q = relax->kappa * G / 24.0;
-  if (kind == kFullMrt) {
-    const double t[9] = {relax->tau_rho, relax->tau_e, relax->tau_zeta, relax->tau_j, relax->tau_q,
-                         relax->tau_j,   relax->tau_q, relax->tau_nu,   relax->tau_nu};
-    for (int k = 0; k < 9; ++k) a.omega[k] = 1.0 / t[k];
-    a.li_e = 12.0 * sigma / (relax->tau_e - 0.5);
-    a.li_z = 12.0 * sigma / (relax->tau_zeta - 0.5);
-  }
+  set_collision_args(a, kind, *relax, d, G);
   *out = c;
   return PPLBM_OK;
 }

@@ -300,21 +300,6 @@ int ilog2(int v) {
   return r;
 }
 
-// collision kind and validity, as pplbm_create
-int kind_of(const pplbm_relax* r) {
-  if (!r || r->reserved != 0) return -1;
-  if (!std::isfinite(r->kappa) || !(r->kappa < 1.0)) return -1;
-  if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
-  if (r->kind == PPLBM_RELAX_TWO_PHASE) return (r->tau_l > 0.5 && r->visc_ratio > 0.0) ? kShearTau : -1;
-  if (r->kind != PPLBM_RELAX_MRT) return -1;
-  const double t[6] = {r->tau_rho, r->tau_e, r->tau_zeta, r->tau_j, r->tau_q, r->tau_nu};
-  for (double v : t)
-    if (!(v > 0.5) || !std::isfinite(v)) return -1;
-  if (r->tau_rho == 1.0 && r->tau_e == 1.0 && r->tau_zeta == 1.0 && r->tau_j == 1.0 && r->tau_q == 1.0)
-    return r->tau_nu == 1.0 ? kUnitTau : kShearTau;
-  return kFullMrt;
-}
-
 bool lattice_ok(const pplbm_lattice* l) {
   if (!l || l->nx < 1 || l->ny < 1 || l->reserved != 0) return false;
   if (9 * (int64_t)l->nx * l->ny >= ((int64_t)1 << 31)) return false;
@@ -555,9 +540,9 @@ extern "C" {
 size_t pplbm_batch_workspace_bytes(int32_t n, const pplbm_lattice* lattices, const pplbm_relax* relax) {
   if (n < 1 || !lattices || !relax) return 0;
   size_t total = 0;
-  const int k0 = kind_of(&relax[0]);
+  const int k0 = collision_kind(&relax[0]);
   for (int i = 0; i < n; ++i) {
-    const int k = kind_of(&relax[i]);
+    const int k = collision_kind(&relax[i]);
     if (k < 0 || k != k0 || !lattice_ok(&lattices[i])) return 0;
     total += inst_doubles(lattices[i], k);
   }
@@ -575,7 +560,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   pplbm_batch* b = new (std::nothrow) pplbm_batch();
   if (!b) return PPLBM_ERR_ARG;
   b->n = n;
-  b->kind = kind_of(&relax[0]);
+  b->kind = collision_kind(&relax[0]);
   b->st = false;
   for (int i = 0; i < n; ++i) b->st = b->st || relax[i].kappa != 0.0;
   b->lat.assign(lattices, lattices + n);
@@ -654,25 +639,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
     a.half_force = -G / 24.0;
     a.psi_ghost_bottom = d.psi_l;
     a.psi_ghost_top = d.psi_v;
-    const double sigma = r.forcing == PPLBM_FORCING_GUO ? 0.0 : r.sigma_auto ? -d.eps / (16.0 * G) : r.sigma;
-    if (b->kind == kShearTau) {
-      if (r.kind == PPLBM_RELAX_TWO_PHASE) {
-        const double tv = 0.5 + r.visc_ratio * (r.tau_l - 0.5);
-        a.tau_b = (r.tau_l - tv) / (d.rho_l - d.rho_v);
-        a.tau_a = r.tau_l - a.tau_b * d.rho_l;
-      } else {
-        a.tau_a = r.tau_nu;
-        a.tau_b = 0.0;
-      }
-    }
-    a.zz_scale = sigma * G * G / 432.0;
-    a.kappa_q = r.kappa * G / 24.0;
-    if (b->kind == kFullMrt) {
-      const double t[9] = {r.tau_rho, r.tau_e, r.tau_zeta, r.tau_j, r.tau_q, r.tau_j, r.tau_q, r.tau_nu, r.tau_nu};
-      for (int k = 0; k < 9; ++k) a.omega[k] = 1.0 / t[k];
-      a.li_e = 12.0 * sigma / (r.tau_e - 0.5);
-      a.li_z = 12.0 * sigma / (r.tau_zeta - 0.5);
-    }
+    set_collision_args(a, b->kind, r, d, G);
     b->bufA[i] = w;
     b->bufB[i] = w + 9 * nn;
     BatchInst& I = b->host_inst[i];

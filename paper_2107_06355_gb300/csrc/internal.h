@@ -48,6 +48,14 @@ struct StepArgs {
   double kappa_q;
 };
 
+// Collision kind of a relaxation set (kUnitTau, kShearTau, kFullMrt), -1 if the set
+// is invalid (reserved word, forcing, kappa finite and < 1, relaxation times > 1/2)
+// (collision_args.cpp).
+int collision_kind(const pplbm_relax* r);
+// The collision fields of a (tau_a, tau_b, zz_scale, kappa_q, omega, li_e, li_z) for
+// the relaxation set r of collision kind `kind`, the EOS d and the interaction G.
+void set_collision_args(StepArgs& a, int kind, const pplbm_relax& r, const pplbm_eos_derived& d, double G);
+
 // Launchers (step_kernels.cu); all asynchronous on `stream`.
 void launch_rho_psi(const StepArgs& a, void* stream);
 void launch_collide(const StepArgs& a, void* stream);

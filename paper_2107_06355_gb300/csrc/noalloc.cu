@@ -43,21 +43,6 @@ pplbm_status noalloc_fail(const char** message, pplbm_status s, const char* text
   return s;
 }
 
-// collision kind of a relaxation set (same rules as pplbm_create); -1 if invalid
-int noalloc_kind(const pplbm_relax* r) {
-  if (!r || r->reserved != 0) return -1;
-  if (!std::isfinite(r->kappa) || !(r->kappa < 1.0)) return -1;
-  if (r->forcing != PPLBM_FORCING_GUO && r->forcing != PPLBM_FORCING_LI) return -1;
-  if (r->kind == PPLBM_RELAX_TWO_PHASE) return (r->tau_l > 0.5 && r->visc_ratio > 0.0) ? kShearTau : -1;
-  if (r->kind != PPLBM_RELAX_MRT) return -1;
-  const double t[6] = {r->tau_rho, r->tau_e, r->tau_zeta, r->tau_j, r->tau_q, r->tau_nu};
-  for (double v : t)
-    if (!(v > 0.5) || !std::isfinite(v)) return -1;
-  if (r->tau_rho == 1.0 && r->tau_e == 1.0 && r->tau_zeta == 1.0 && r->tau_j == 1.0 && r->tau_q == 1.0)
-    return r->tau_nu == 1.0 ? kUnitTau : kShearTau;
-  return kFullMrt;
-}
-
 }  // namespace
 }  // namespace pplbm
 
@@ -67,7 +52,7 @@ extern "C" pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const p
                                            const pplbm_relax* relax, const double* f_in, double* f_out,
                                            void* stream, const char** message) {
   if (message) *message = "";
-  const int kind = noalloc_kind(relax);
+  const int kind = collision_kind(relax);
   if (!lattice || !eos || !f_in || !f_out || f_in == f_out || kind < 0 || lattice->nx < 1 || lattice->ny < 1 ||
       lattice->reserved != 0 || !(eos->G < 0.0) || (eos->mode != PPLBM_EOS_CS && eos->mode != PPLBM_EOS_SMOOTH))
     return noalloc_fail(message, PPLBM_ERR_ARG, kMsgArgs);
@@ -112,29 +97,7 @@ extern "C" pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const p
   a.half_force = -eos->G / 24.0;
   a.psi_ghost_bottom = eos->psi_l;
   a.psi_ghost_top = eos->psi_v;
-  const double G = eos->G;
-  const double sigma = relax->forcing == PPLBM_FORCING_GUO ? 0.0
-                       : relax->sigma_auto               ? -eos->eps / (16.0 * G)
-                                                         : relax->sigma;
-  if (kind == kShearTau) {
-    if (relax->kind == PPLBM_RELAX_TWO_PHASE) {
-      const double tv = 0.5 + relax->visc_ratio * (relax->tau_l - 0.5);
-      a.tau_b = (relax->tau_l - tv) / (eos->rho_l - eos->rho_v);
-      a.tau_a = relax->tau_l - a.tau_b * eos->rho_l;
-    } else {
-      a.tau_a = relax->tau_nu;
-      a.tau_b = 0.0;
-    }
-  }
-  a.zz_scale = sigma * G * G / 432.0;
-  a.kappa_q = relax->kappa * G / 24.0;
-  if (kind == kFullMrt) {
-    const double t[9] = {relax->tau_rho, relax->tau_e, relax->tau_zeta, relax->tau_j, relax->tau_q,
-                         relax->tau_j,   relax->tau_q, relax->tau_nu,   relax->tau_nu};
-    for (int k = 0; k < 9; ++k) a.omega[k] = 1.0 / t[k];
-    a.li_e = 12.0 * sigma / (relax->tau_e - 0.5);
-    a.li_z = 12.0 * sigma / (relax->tau_zeta - 0.5);
-  }
+  set_collision_args(a, kind, *relax, *eos, eos->G);
 
   // the error word keeps the previous call's value: clear it first
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return noalloc_fail(message, PPLBM_ERR_CUDA, kMsgCuda);
