@@ -231,5 +231,10 @@ def test_surface_tension_kappa_is_validated_at_set_up(lib):
             assert (lib.pplbm_workspace_bytes(C.byref(lat), C.byref(r)) > 0) == ok, (kind, kappa)
             arr = (L.pplbm_relax * 1)(r)
             assert (lib.pplbm_batch_workspace_bytes(1, (L.pplbm_lattice * 1)(lat), arr) > 0) == ok, (kind, kappa)
+    # two-phase relaxation needs finite tau_l > 1/2 and visc_ratio > 0
+    for tau_l, vr, ok in ((0.7, 5.0, True), (0.5, 5.0, False), (float("inf"), 5.0, False), (0.7, 0.0, False),
+                          (0.7, float("inf"), False)):
+        r = P.Relax(kind=L.RELAX_TWO_PHASE, tau_l=tau_l, visc_ratio=vr).c()
+        assert (lib.pplbm_workspace_bytes(C.byref(lat), C.byref(r)) > 0) == ok, (tau_l, vr)
     assert C.sizeof(L.pplbm_relax) == 8 + 8 * 9 + 8 + 8
     assert L.pplbm_relax.kappa.offset == C.sizeof(L.pplbm_relax) - 8
