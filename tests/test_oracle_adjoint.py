@@ -134,3 +134,31 @@ def test_gradient_wrt_branch_parameters_matches_finite_differences(wrt):
     fd = (Lv(base[wrt] + h) - Lv(base[wrt] - h)) / (2 * h)
     assert ad != 0.0
     assert ad == pytest.approx(fd, rel=1e-5)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.4])
+@pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
+def test_gradient_wrt_kappa_matches_finite_differences(bc, kappa):
+    """dL/dkappa of the surface-tension control through the torch restatement
+    (kappa as a tensor in the constants) against central differences of the numpy
+    oracle over 5 steps, L = sum rho^2 (a loss of moderate size, so the differences
+    are not lost to rounding)."""
+    nx, ny, steps = 12, 10, 5
+    lat = lattice(nx, ny, bc, kappa=kappa)
+    e = lat.eos
+    f0 = initial(lat, nx, ny, bc)
+    c = A.constants_as_tensors(e, requires_grad=False)
+    c["kappa"] = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    g = torch.tensor(f0)
+    for _ in range(steps):
+        g = A.step(g, lat, c)
+    (g.sum(0) ** 2).sum().backward()
+    h = 1e-5
+
+    def Lnp(k):
+        rho = L.Lattice(nx, ny, bc, e, L.Relax(sigma=e.sigma(), kappa=k)).step(f0, steps).sum(0)
+        return float((rho ** 2).sum())
+
+    fd = (Lnp(kappa + h) - Lnp(kappa - h)) / (2 * h)
+    assert abs(fd) > 1e-8
+    assert float(c["kappa"].grad) == pytest.approx(fd, rel=1e-6)
