@@ -88,6 +88,12 @@ def _roll(a, dy, dx):
     return torch.roll(a, shifts=(dy, dx), dims=(-2, -1))
 
 
+def _surface_tension_source(qxx, qyy, qxy, z):
+    """The surface-tension source's moment vector with Lambda = I (Li & Luo 2013):
+    [0, 1.5 tr Q, -1.5 tr Q, 0, 0, 0, 0, -(Q_xx - Q_yy), -Q_xy]; z a zero plane."""
+    return torch.stack([z, 1.5 * (qxx + qyy), -1.5 * (qxx + qyy), z, z, z, z, -(qxx - qyy), -qxy])
+
+
 def step(f, lat: L.Lattice, c):
     """One step, f of shape (9, ny, nx) (torch float64); c: dict of constant tensors."""
     eos = lat.eos
@@ -151,7 +157,7 @@ def step(f, lat: L.Lattice, c):
     mstar = m - (m - meq) + 0.5 * S          # Lambda = I
     if with_st:
         z = torch.zeros_like(rho)
-        mstar = mstar + torch.stack([z, 1.5 * (qxx + qyy), -1.5 * (qxx + qyy), z, z, z, z, -(qxx - qyy), -qxy])
+        mstar = mstar + _surface_tension_source(qxx, qyy, qxy, z)
     fstar = torch.einsum("ik,kyx->iyx", _MINV, mstar)
     out = []
     for i in range(9):

@@ -250,3 +250,21 @@ def test_fd_surface_tension_term_sign(monkeypatch):
 
     monkeypatch.setattr(F.FDSolver, "__init__", init)
     assert some_pin_fails(TS.test_droplet_response_to_kappa_matches_fd)
+
+
+def test_torch_restatement_surface_tension_row8_sign(monkeypatch):
+    """The oracle adjoint's torch restatement with +Q_xy in row 8 of the surface-tension
+    source: it no longer equals the numpy oracle's step."""
+    pytest.importorskip("torch")
+    from oracle import adjoint as A
+    import test_oracle_adjoint as TA
+
+    orig = A._surface_tension_source
+
+    def src(qxx, qyy, qxy, z):
+        c = orig(qxx, qyy, qxy, z)
+        return c.index_copy(0, A.torch.tensor([8]), -c[8:9])
+
+    monkeypatch.setattr(A, "_surface_tension_source", src)
+    assert some_pin_fails(lambda: TA.test_torch_step_equals_numpy_oracle(TA.PER, 0.6),
+                          lambda: TA.test_torch_step_equals_numpy_oracle(TA.WALLS, 0.6))
