@@ -268,3 +268,33 @@ def test_torch_restatement_surface_tension_row8_sign(monkeypatch):
     monkeypatch.setattr(A, "_surface_tension_source", src)
     assert some_pin_fails(lambda: TA.test_torch_step_equals_numpy_oracle(TA.PER, 0.6),
                           lambda: TA.test_torch_step_equals_numpy_oracle(TA.WALLS, 0.6))
+
+
+def test_peng_theta_weights_swapped(monkeypatch):
+    """Eq. PengTheta with r_theta weighting the vapour slope and 1 - r_theta the liquid's."""
+    import test_oracle_peng as TP
+
+    def theta(self, rho_m):
+        rv, rl = self.rho_v, self.rho_l
+        self.theta = (self.r_theta / ((rv - rho_m) * (rv - rl)) * self.dpdrho_v
+                      + (1.0 - self.r_theta) / ((rl - rho_m) * (rl - rv)) * self.dpdrho_l)
+
+    monkeypatch.setattr(E.EOS, "_peng_theta", theta)
+    assert some_pin_fails(TP.test_peng_theta_gives_the_weighted_branch_its_slope)
+
+
+def test_fd_two_phase_relaxation_times_swapped(monkeypatch):
+    """The FD scheme's tau_nu(rho) of Eq. RelaxationTime with tau_l at rho_v and tau_v at rho_l."""
+    from oracle import fd as F
+
+    def tau_nu(self, rho):
+        if self.tau_l is None:
+            return self.tau_nu, 0.0
+        e = self.eos
+        tau_v = 0.5 + self.visc_ratio * (self.tau_l - 0.5)
+        tau = tau_v * (rho - e.rho_v) / (e.rho_l - e.rho_v) + self.tau_l * (rho - e.rho_l) / (e.rho_v - e.rho_l)
+        return tau, (tau_v - self.tau_l) / (e.rho_l - e.rho_v)
+
+    monkeypatch.setattr(F.FDSolver, "_tau_nu", tau_nu)
+    assert some_pin_fails(lambda: TF.test_fd_two_phase_viscosity_shear_waves_decay_at_each_phase_rate("liquid"),
+                          lambda: TF.test_fd_two_phase_viscosity_shear_waves_decay_at_each_phase_rate("vapour"))
