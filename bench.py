@@ -1,17 +1,28 @@
 """Benchmark of the pseudopotential D2Q9 LBM step on GB300.
 
-Default workload (one bench step = one LBM time step of all four lattices):
-four 512 x 512 periodic static droplets, radii 32, 48, 64, 96, reduced
-temperature 0.6, Smooth C-S EOS (a_l = 0.387, a_v = 2, alpha = 0.834),
-all relaxation times 1, Li forcing with sigma from the mechanical-stability
-condition; initial tanh profiles of width 8. The four lattices' buffers
-(f in/out, psi, moments: ~180 MB per step) exceed the 126 MB L2, so the state
-streams from HBM every step (no explicit flush).
+Headline workload (one bench step = one LBM time step of every lattice): the
+batched sweep of 64 independent lattices, seed 210706355 -- even k a planar
+interface 4 x L, odd k a static droplet L x L with R = L/4, L uniform in
+64..1024, reduced temperature 0.35 + 0.6 k/63 -- Smooth C-S EOS (a_l = 0.363,
+a_v = 2, alpha = 0.775), all relaxation times 1, Li forcing with sigma from the
+mechanical-stability condition, periodic, tanh initial profiles of width 8:
+12,946,797 node updates per step. The state (two f buffers, psi, moments:
+about 2.4 GB) is far larger than the 126 MB L2, so every step streams it from
+HBM; there is no explicit flush.
 
-Prints one JSON line: MLUPS (million lattice-node updates per second) over all
-ranks, the roofline of the dominant kernel, an end-to-end figure through the
-host-buffer C-ABI call, clocks sampled during the timed region and the oracle
-timed on the host cores (rank 0 only).
+Timing: W untimed warm-up steps, then blocks of exactly K steps, each bracketed
+by a barrier and a device synchronisation and timed with CUDA events on the
+batch's stream, repeated until at least 1.5 s and 5 blocks have run (nvidia-smi
+samples the clocks meanwhile); `value` is from the median block, the max over
+ranks. Each pass's launches are bracketed by their own CUDA events inside the
+same blocks, which gives the dominant kernel's live launch duration for the
+roofline. Its peak is the FP64 issue rate measured here by pplbm_fp64_peak.
+
+Also reported: the 2048 x 1024 droplet impact (walls, two-phase tau, T_r = 0.35,
+Re = 300) as a single lattice; per-plan times of the 64-lattice batch over 1,000
+steps; batched against serial per-instance launches; the adjoint's cost; EOS
+variants; the FD solver; an end-to-end figure through the host-buffer C-ABI
+call; and the CPU oracle on one core and on all host cores (rank 0 only).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -29,31 +40,44 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-RADII = (32, 48, 64, 96)
-NX = NY = 512
-TR, A_L, A_V, ALPHA = 0.6, 0.387, 2.0, 0.834
-METRIC = "D2Q9 pseudopotential MLUPS (4 x 512^2 static droplets, T_r=0.6, Smooth C-S, FP64)"
-WORKLOAD = "static droplets 512x512 periodic, R in {32,48,64,96}, T_r=0.6, Smooth C-S (a_l=0.387, a_v=2, alpha=0.834), tau=1, Li forcing"
+# the 64-lattice sweep's EOS (every instance; T_r from the spec)
+SWEEP_EOS = dict(a_l=0.363, a_v=2.0, alpha=0.775)
+METRIC = "D2Q9 pseudopotential MLUPS (64-lattice batched sweep, FP64)"
+WORKLOAD = ("batched sweep: 64 independent D2Q9 lattices, seed 210706355: even k planar 4 x L, odd k droplet "
+            "L x L (R = L/4), L ~ U{64..1024}, T_r = 0.35 + 0.6 k/63; Smooth C-S (a_l=0.363, a_v=2, alpha=0.775), "
+            "tau=1, Li forcing, periodic, tanh profiles W=8")
 E2E_INNER = 100  # LBM steps per end-to-end call
+MIN_TIMED_S = 1.5
+MIN_BLOCKS = 5
 
-# FP64 instructions of one node update per kernel (unit relaxation times, Li forcing,
-# bulk nodes), counted from the kernels' arithmetic; ncu's FP64-pipe cycles agree.
-FP64_OPS_PER_NODE = {"rho_psi": 33, "collide": 51}
+# FP64 instructions of one node update per kernel, from the kernels' arithmetic on
+# bulk nodes (unit relaxation times, Li forcing): density/psi pass 33 (moments 14,
+# C-S branch 14, sqrt 5), collision pass 51 (force 8, velocity and second moments
+# 16, reciprocal 4, Li term 3, reconstruction 20). ncu's sm__inst_executed_pipe_fp64
+# on the sweep agrees within a few percent (interface nodes take the shaped branches).
+FP64_PER_NODE = {"rho_psi": 33, "collide": 51}
+# the two-phase relaxation (rows 7, 8 relax with 1/tau(rho)), walls: the impact lattice;
+# pass 1 adds the two stress moments (6), pass 2 tau(rho) and its reciprocal (4), the
+# rows 7, 8 equilibria and sources (9) and their relaxation (7), less Pi_xy's 2
+FP64_PER_NODE_SHEAR = {"rho_psi": 39, "collide": 69}
+# algorithmic bytes per node of each pass as built (moments handed from pass 1 to
+# pass 2): pass 1 reads 9 f and writes psi + 3 moments (5 with tau(rho)); pass 2
+# reads the moments and the psi tile and writes 9 f
 BYTES_PER_NODE = {"rho_psi": 72 + 32, "collide": 24 + 8 + 72}
+BYTES_PER_NODE_SHEAR = {"rho_psi": 72 + 48, "collide": 40 + 8 + 72}
+# the scope table's algorithmic count for the pull design: 72 + 8 (pass 1) and
+# 72 + 8 + 72 (pass 2) bytes per node
+BYTES_PER_NODE_SCOPE = 232
 # FP64 instructions of one MacCormack step per grid point: predictor 113, corrector
 # 119, two EOS passes of 27 (the kernels' arithmetic; ncu's sm__inst_executed_pipe_fp64
-# on the 2048 x 1024 grid, profiles/k_fd_update_k_fd_eos_2048x1024.md)
+# agrees on the 2048 x 1024 grid)
 FD_FP64_PER_POINT = 113 + 119 + 2 * 27
-# FP64 instructions per node of the two-phase (tau(rho), walls) batched passes of the
-# impact sweep (ncu sm__inst_executed_pipe_fp64, profiles/k_batch_shear_tau_impact_sweep.md)
-IMPACT_FP64_PER_NODE = 42.0 + 67.5
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
-# batched pass on this workload, averaged over three launches of an ncu capture of
-# `bench.py --profile-batch` (profiles/k_batch_collide_k_batch_rho_psi_droplets512.md).
-# They hold for the kernel sources whose digest is recorded with them; once those
-# sources change, traffic is reported as null until the capture is repeated.
-TRAFFIC = {"sources": "31b781817864a4b6", "rho_psi": 75548160 + 2560768, "collide": 33602987 + 13737131}
+# batched pass on the headline workload, from an ncu capture, with the digest of the
+# kernel sources they were taken on; once those sources change, traffic is
+# reported as null until the capture is repeated.
+TRAFFIC = {"sources": None, "rho_psi": None, "collide": None}
 KERNEL_SOURCES = ("batch.cu", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
 
 
@@ -71,10 +95,10 @@ def kernel_sources_digest():
     return h.hexdigest()[:16]
 
 
-def step_traffic():
+def pass_traffic(name):
     if TRAFFIC["sources"] is None or TRAFFIC["sources"] != kernel_sources_digest():
         return None
-    return TRAFFIC["rho_psi"] + TRAFFIC["collide"]
+    return TRAFFIC[name]
 
 
 def load_peaks():
@@ -87,16 +111,16 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, tag="main"):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}_{tag}.csv")
 
     def start(self):
         try:
@@ -108,13 +132,13 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -123,6 +147,7 @@ class ClockSampler:
             try:
                 sm.append(float(parts[1]))
                 smax.append(float(parts[2]))
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[5:9]):
@@ -133,6 +158,7 @@ class ClockSampler:
         except OSError:
             pass
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_median": float(np.median(power)) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
@@ -148,184 +174,37 @@ def build_lib():
     build.build()
 
 
-def make_droplets(torch, stream):
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+# ---- workloads -------------------------------------------------------------------
+
+def sweep_specs(n=64):
     import lbm_inputs as I
-    import paper_2107_06355_gb300 as P
 
-    eos = P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA)
-    relax = P.Relax()
-    sims, rho0s = [], []
-    for R in RADII:
-        s = P.Simulation(NX, NY, P.BC_PERIODIC, eos, relax, stream=stream)
-        d = s.derived()
-        rho0 = I.droplet(NX, NY, R, d["rho_v"], d["rho_l"], W=8.0)
-        s.init_equilibrium(rho0)
-        sims.append(s)
-        rho0s.append(rho0)
-    return sims, rho0s
+    specs = I.batch_specs(n)
+    for s in specs:
+        s.update(SWEEP_EOS)
+    return specs
 
 
-def time_oracle_sample(max_seconds=20.0):
-    """The oracle (numpy, as it stands) on one 512^2 droplet lattice of the workload."""
-    import lbm_inputs as I
-    from oracle import eos as E
-    from oracle import lbm as L
-
-    e = E.make_eos(E.MODE_SMOOTH, TR, A_L, A_V, ALPHA)
-    lat = L.Lattice(NX, NY, L.BC_PERIODIC_X | L.BC_PERIODIC_Y, e, L.Relax(sigma=e.sigma()))
-    f = lat.init_equilibrium(I.droplet(NX, NY, RADII[1], e.rho_v, e.rho_l, W=8.0))
-    f = lat.step(f, 1)
-    n, t0 = 0, time.perf_counter()
-    while True:
-        f = lat.step(f, 1)
-        n += 1
-        dt = time.perf_counter() - t0
-        if dt > max_seconds or n >= 200:
-            break
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    threads = _numpy_threads()
-    return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": threads, "host_cores": cores,
-            "kind": "oracle",
-            "sample": f"{n} LBM steps of one 512x512 droplet lattice (R=48) of the workload, {dt:.1f} s"}
-
-
-def _numpy_threads():
-    try:
-        from threadpoolctl import threadpool_info
-        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
-    except Exception:
-        return 1
-
-
-def profile_case():
-    """One 2048 x 1024 periodic droplet lattice (R = 100) of the workload's EOS, 3 steps:
-    369 MB of workspace (larger than L2), 3 launches of each step kernel."""
-    import torch
-    import lbm_inputs as I
-    import paper_2107_06355_gb300 as P
-
-    build_lib()
-    s = P.Simulation(2048, 1024, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA), P.Relax())
-    d = s.derived()
-    s.init_equilibrium(I.droplet(2048, 1024, 100, d["rho_v"], d["rho_l"], W=8.0))
-    s.step(3)
-    s.sync()
-    torch.cuda.synchronize()
-    print("profile case done")
-
-
-def profile_batch(kappa=0.0):
-    """The benchmark's four 512 x 512 droplets in one batch, launches plan, 3 steps:
-    3 launches of each batched pass over 1,048,576 nodes (184 MB of state, > L2);
-    kappa != 0 runs them with the surface-tension control."""
-    import torch
-    import lbm_inputs as I
-    import paper_2107_06355_gb300 as P
-
-    build_lib()
-    specs = [dict(kind="droplet", nx=NX, ny=NY, R=R, Tr=TR) for R in RADII]
-    b, _, _, _ = make_batch(P, I, specs, torch.cuda.current_stream(), kappa=kappa)
-    b.set_plan(P.PLAN_LAUNCHES, 0)
-    b.step(3)
-    b.sync()
-    torch.cuda.synchronize()
-    print("profile batch done")
-
-
-def profile_fd():
-    """The finite-difference solver on the 2048 x 1024 droplet grid of fd_throughput,
-    3 steps: 3 launches of each of its two kernels per half-step pair."""
-    import torch
-    import lbm_inputs as I
-    import paper_2107_06355_gb300 as P
-
-    build_lib()
-    eos = P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA)
-    d = P.eos_setup(eos)
-    fd = P.FDSolver(2048, 1024, eos, dx=1.0)
-    rho = I.droplet(2048, 1024, 100, d["rho_v"], d["rho_l"], W=8.0)
-    fd.set_state(rho, np.zeros_like(rho), np.zeros_like(rho))
-    fd.step(3, 0.4)
-    torch.cuda.synchronize()
-    print("profile fd done")
-
-
-def profile_adjoint():
-    """Checkpointed forward and reverse pass on a 1024 x 1024 droplet (T_r = 0.5,
-    tau = 1), 12 steps with interval 4, gradient slots of alpha: 12 launches of each
-    adjoint kernel on 75 MB states (> L2 with the adjoint planes)."""
-    import ctypes as C
-    import torch
-    import lbm_inputs as I
-    import paper_2107_06355_gb300 as P
-    from paper_2107_06355_gb300 import _lib as L
-
-    build_lib()
-    nx = ny = 1024
-    steps, interval = 12, 4
-    sim = P.Simulation(nx, ny, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775), P.Relax())
-    d = sim.derived()
-    sim.init_equilibrium(I.droplet(nx, ny, 192.0, d["rho_v"], d["rho_l"], W=7.0))
-    dev = sim.device
-    ckpt = torch.empty((steps // interval, 9, ny, nx), dtype=torch.float64, device=dev)
-    seg = torch.empty((interval, 9, ny, nx), dtype=torch.float64, device=dev)
-    lam = torch.ones((9, ny, nx), dtype=torch.float64, device=dev)
-    lam0 = torch.empty_like(lam)
-    grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
-    nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
-    ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
-    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
-    L.check(L.lib().pplbm_adjoint_set_slots(sim.ctx, (1 << 9) - 1), sim.ctx)  # alpha's slots, as in adjoint_cost
-    L.check(L.lib().pplbm_forward_checkpointed(sim.ctx, steps, interval, p(ckpt)), sim.ctx)
-    L.check(L.lib().pplbm_backward_checkpointed(sim.ctx, steps, interval, p(ckpt), p(seg), p(lam), p(lam0), p(grad),
-                                                p(ws), nb), sim.ctx)
-    torch.cuda.synchronize()
-    sim.close()
-    print("profile adjoint done")
-
-
-def run_reference(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return
-    timed = []
-    for k in range(args.warmup + args.steps):
-        r = time_oracle_sample(max_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
-        if k >= args.warmup:
-            timed.append(r)
-    last = timed[-1]
-    val = sum(r["value"] for r in timed) / len(timed)   # mean rate over the timed samples
-    nodes = NX * NY * len(RADII)
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": nodes / (val * 1e6) * 1e3,   # one step of the whole 4-lattice workload at this rate
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
-            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def serial_sims(torch, stream):
-    sims, rho0s = make_droplets(torch, stream)
-    return sims, rho0s
+def initial_density(I, s, rho_v, rho_l):
+    if s["kind"] == "planar":
+        return I.planar(s["nx"], s["ny"], rho_v, rho_l, W=8.0)
+    return I.droplet(s["nx"], s["ny"], s["R"], rho_v, rho_l, W=8.0)
 
 
 def make_batch(P, I, specs, stream, kappa=0.0):
-    """A Batch over `specs` (dicts with nx, ny, Tr, kind, R) with tanh initial fields;
-    kappa: the surface-tension control of every instance (0 = off)."""
-    eos = [P.EOSParams(P.EOS_SMOOTH, s["Tr"], s.get("a_l", A_L), s.get("a_v", A_V), s.get("alpha", ALPHA))
-           for s in specs]
+    """A Batch over `specs` (dicts with nx, ny, Tr, kind, R, a_l, a_v, alpha) with
+    tanh initial fields; kappa: the surface-tension control of every instance."""
+    eos = [P.EOSParams(P.EOS_SMOOTH, s["Tr"], s["a_l"], s["a_v"], s["alpha"]) for s in specs]
     relax = [P.Relax(kappa=kappa) for _ in specs]
     b = P.Batch([(s["nx"], s["ny"], P.BC_PERIODIC) for s in specs], eos, relax, stream=stream)
     inits = []
     for k, s in enumerate(specs):
         d = b.derived(k)
-        if s["kind"] == "planar":
-            rho = I.planar(s["nx"], s["ny"], d["rho_v"], d["rho_l"], W=8.0)
-        else:
-            rho = I.droplet(s["nx"], s["ny"], s["R"], d["rho_v"], d["rho_l"], W=8.0)
+        rho = initial_density(I, s, d["rho_v"], d["rho_l"])
         b.init_equilibrium(k, rho)
         inits.append(rho)
     return b, eos, relax, inits
@@ -341,28 +220,137 @@ def time_device(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def sweep_comparison(torch, stream, steps):
-    """64-lattice sweep (seed 210706355): batched engine vs one context per lattice,
-    the latter as per-instance CUDA graphs (the baseline) and as plain launches."""
+def timed_blocks(torch, stream, fn, barrier, min_seconds=MIN_TIMED_S, min_blocks=MIN_BLOCKS, max_blocks=2000,
+                 after=None):
+    """Runs fn() in blocks, each bracketed by barrier() and timed with CUDA events on
+    `stream`, until min_seconds of device time and min_blocks blocks; block times in ms.
+    after(), if given, runs after each block's closing barrier (outside the timing)."""
+    times = []
+    while len(times) < max_blocks and (len(times) < min_blocks or sum(times) < 1e3 * min_seconds):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+        if after is not None:
+            after()
+    return times
+
+
+# ---- FP64 issue-rate peak ---------------------------------------------------------
+
+def measure_fp64_peak(torch, local, seconds=0.6, repeats=3):
+    """pplbm_fp64_peak: 8 independent FMA chains per thread, 8 blocks of 256 per SM,
+    sized to run `seconds`; best of `repeats`, with the clocks sampled meanwhile."""
+    import ctypes as C
+    from paper_2107_06355_gb300 import _lib as L
+
+    lib = L.lib()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = (C.c_double * 3)()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(lib.pplbm_fp64_peak(8, 4000, C.c_void_p(sink.data_ptr()), out, stream))  # warm-up and calibration
+    iters = max(1000, int(4000 * seconds / max(out[1] * 1e-3, 1e-6)))
+    clocks = ClockSampler(local, "fp64")
+    clocks.start()
+    rates, ms = [], []
+    for _ in range(repeats):
+        L.check(lib.pplbm_fp64_peak(8, iters, C.c_void_p(sink.data_ptr()), out, stream))
+        rates.append(out[0])
+        ms.append(out[1])
+    clk = clocks.stop()
+    best = max(rates)
+    return {"value": best / 1e12, "unit": "TFLOP/s (1 per FP64 FMA instruction per thread)",
+            "median": float(np.median(rates)) / 1e12,
+            "launch_ms": ms, "blocks": int(out[2]), "iters": iters, "clocks": clk,
+            "how": "pplbm_fp64_peak: 8 independent FP64 FMA chains per thread, 256 threads x 8 blocks per SM, "
+                   "CUDA events, best of 3"}
+
+
+# ---- the 2048 x 1024 droplet impact (single lattice) ---------------------------------
+
+def impact_2048(torch, stream, barrier, steps=1000):
+    """Droplet impact on a liquid film: 2048 x 1024, periodic x, walls in y, Smooth C-S
+    at T_r = 0.35 (a_l = 0.363, a_v = 2, alpha = 0.838), two-phase tau(rho) with
+    tau_l = 0.6 and v_r = 1, R = 100, film 102, V_d = 0.05 (Re = V_d 2R / nu_l = 300),
+    tanh width 6. One context (two launches per step, per-kernel CUDA events)."""
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
 
-    specs = I.batch_specs()
-    for s in specs:
-        s["a_l"], s["a_v"], s["alpha"] = 0.363, 2.0, 0.775
+    nx, ny = 2048, 1024
+    eos = P.EOSParams(P.EOS_SMOOTH, 0.35, 0.363, 2.0, 0.838)
+    sim = P.Simulation(nx, ny, P.BC_WALLS_Y, eos, P.Relax(kind=P.RELAX_TWO_PHASE, tau_l=0.6, visc_ratio=1.0),
+                       stream=stream)
+    d = sim.derived()
+    sim.init_equilibrium(*I.impact(nx, ny, 100, 102, d["rho_v"], d["rho_l"], 0.05, W=6.0))
+    m0 = sim.guard()[0]
+    sim.step(20)
+    sim.sync()
+    sim.enable_kernel_timing(3 * steps)
+    times = timed_blocks(torch, stream, lambda: sim.step(steps), barrier, min_seconds=1.0, min_blocks=3,
+                         max_blocks=3)
+    (k_ms, k_n) = sim.kernel_times()
+    sim.enable_kernel_timing(0)
+    m1, umax, bad, _ = sim.guard()
+    sim.close()
+    if bad or not abs(m1 - m0) < 1e-10 * m0:
+        raise RuntimeError("impact lattice diverged or lost mass")
+    med = float(np.median(times))
+    nodes = nx * ny
+    _, sm_max, _ = load_peaks()
+    per = {k: k_ms[i] / max(1, k_n[i]) for i, k in enumerate(("rho_psi", "collide"))}
+    out = {"config": "2048x1024 droplet impact on a film, walls in y, Smooth C-S T_r=0.35 (a_l=0.363, a_v=2, "
+                     "alpha=0.838), tau(rho) tau_l=0.6 v_r=1, R=100, film 102, V_d=0.05 (Re=300)",
+           "steps_per_block": steps, "blocks_ms": times, "ms_per_step": med / steps,
+           "mlups": nodes * steps / (med / 1e3) / 1e6, "kernel_ms": per, "max_u": umax,
+           "mass_drift": abs(m1 - m0) / m0}
+    hbm_gbs, _, peak_src = load_peaks()
+    step_s = med / steps / 1e3
+    out["roofline_hbm"] = {
+        "scope_bytes_per_node": BYTES_PER_NODE_SCOPE,
+        "achieved_scope": BYTES_PER_NODE_SCOPE * nodes / step_s / 1e9,
+        "frac_scope": BYTES_PER_NODE_SCOPE * nodes / step_s / 1e9 / hbm_gbs,
+        "built_bytes_per_node": sum(BYTES_PER_NODE_SHEAR.values()),
+        "frac_built": sum(BYTES_PER_NODE_SHEAR.values()) * nodes / step_s / 1e9 / hbm_gbs,
+        "peak": hbm_gbs, "unit": "GB/s", "peak_source": peak_src}
+    out["fp64_per_node"] = FP64_PER_NODE_SHEAR
+    return out
+
+
+# ---- batch plans and batched vs serial ----------------------------------------------
+
+def plan_times(torch, stream, batch, P, steps=1000):
+    """Per-plan ms per step of the batch over `steps` steps each (state restored)."""
+    out = {}
+    saved = [batch.get_f(k).clone() for k in range(batch.n)]
+    for name, mode in (("launches", P.PLAN_LAUNCHES), ("graph", P.PLAN_GRAPH), ("persistent", P.PLAN_PERSISTENT)):
+        batch.set_plan(mode, 0)
+        batch.step(4)
+        ms = time_device(torch, stream, lambda: batch.step(steps))
+        out[name] = ms / steps
+    for k in range(batch.n):
+        batch.set_f(k, saved[k])
+    return out
+
+
+def serial_comparison(torch, stream, specs, batch_ms_per_step, steps=200):
+    """The same lattices as one context each: per-instance CUDA graphs of two steps
+    replayed one instance after another (the baseline), and plain launches."""
+    import ctypes as C
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import _lib as L
+
     nodes = sum(s["nx"] * s["ny"] for s in specs)
-    b, eos, relax, inits = make_batch(P, I, specs, stream)
-    plan = b.autotune(trial_steps=4)
-    b.step(2)
-    ms_b = time_device(torch, stream, lambda: b.step(steps))
-    b.sync()
-    b.close()
-    del b
-    torch.cuda.empty_cache()
     sims = []
-    for k, s in enumerate(specs):
-        sim = P.Simulation(s["nx"], s["ny"], P.BC_PERIODIC, eos[k], relax[k], stream=stream)
-        sim.init_equilibrium(inits[k])
+    for s in specs:
+        sim = P.Simulation(s["nx"], s["ny"], P.BC_PERIODIC,
+                           P.EOSParams(P.EOS_SMOOTH, s["Tr"], s["a_l"], s["a_v"], s["alpha"]), P.Relax(),
+                           stream=stream)
+        d = sim.derived()
+        sim.init_equilibrium(initial_density(I, s, d["rho_v"], d["rho_l"]))
         sims.append(sim)
 
     def serial():
@@ -373,12 +361,6 @@ def sweep_comparison(torch, stream, steps):
     for sim in sims:
         sim.step(2)
     ms_s = time_device(torch, stream, serial)
-
-    # the baseline the batch is measured against: per-instance CUDA graphs of two
-    # steps (pplbm_step only enqueues kernels), replayed one instance after another
-    import ctypes as C
-    from paper_2107_06355_gb300 import _lib as L
-
     for sim in sims:
         sim.sync()
     cs = torch.cuda.Stream()
@@ -404,17 +386,19 @@ def sweep_comparison(torch, stream, steps):
     for sim in sims:
         sim.sync()
         sim.close()
-    mode = {0: "launches", 1: "graph", 2: "persistent"}[plan["mode"]]
-    return {"instances": len(specs), "nodes": nodes, "steps": steps, "plan": mode,
-            "tile_width": plan["tile_width"] or "per-instance",
-            "batched_instance_steps_per_s": len(specs) * steps / (ms_b / 1e3),
-            "serial_instance_steps_per_s": len(specs) * steps / (ms_g / 1e3),
-            "batched_mlups": nodes * steps / (ms_b / 1e3) / 1e6,
-            "serial_mlups": nodes * steps / (ms_g / 1e3) / 1e6,
-            "serial_baseline": "64 per-instance CUDA graphs of 2 steps, replayed serially",
-            "speedup": ms_g / ms_b,
+    serial_ms = ms_g / steps
+    return {"instances": len(specs), "nodes": nodes, "steps": steps,
+            "serial_baseline": "per-instance CUDA graphs of 2 steps, replayed serially",
+            "batched_ms_per_step": batch_ms_per_step, "serial_ms_per_step": serial_ms,
+            "batched_instance_steps_per_s": len(specs) / (batch_ms_per_step / 1e3),
+            "serial_instance_steps_per_s": len(specs) / (serial_ms / 1e3),
+            "batched_mlups": nodes / (batch_ms_per_step / 1e3) / 1e6,
+            "serial_mlups": nodes / (serial_ms / 1e3) / 1e6,
+            "speedup": serial_ms / batch_ms_per_step,
             "serial_plain_launches_mlups": nodes * steps / (ms_s / 1e3) / 1e6}
 
+
+# ---- other spec and next-row figures ------------------------------------------
 
 def adjoint_cost(torch, steps=2000, interval=45):
     """Adjoint configuration (256 x 256 droplet, R = 48, T_r = 0.5, tau = 1): time of a
@@ -438,11 +422,10 @@ def adjoint_cost(torch, steps=2000, interval=45):
     grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
     nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
     ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
-    p = lambda t: C.c_void_p(t.data_ptr())
+    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
     lib = L.lib()
     alpha_slots = (1 << 9) - 1   # the shaped-branch constants and the Li-term scale: all alpha moves
     out = {}
-    # every EOS constant and the Li-term scale (the kappa slot would run the surface-tension kernels)
     eos_slots = (1 << L.GRAD_NAMES.index("kappa")) - 1
     for label, mask in (("alpha", alpha_slots), ("all_slots", eos_slots)):
         L.check(lib.pplbm_adjoint_set_slots(sim.ctx, mask), sim.ctx)
@@ -458,8 +441,6 @@ def adjoint_cost(torch, steps=2000, interval=45):
                                                                               nb), sim.ctx))
             res = (t_f, t_b)
         out[label] = res
-    # the same rollout with every step's psi and moments kept (4 planes x 2,000 steps =
-    # 4.2 GB): no recomputation in the reverse pass
     L.check(lib.pplbm_adjoint_set_slots(sim.ctx, alpha_slots), sim.ctx)
     fields = torch.empty((steps, 4, ny, nx), dtype=torch.float64, device=dev)
     res = []
@@ -486,16 +467,15 @@ def adjoint_cost(torch, steps=2000, interval=45):
 
 
 def eos_variant_throughput(torch, steps=1000):
-    """The bench workload (4 x 512^2 droplets, tau = 1) with each EOS the kernels
-    support (T_r = 0.6; the two Guo-forced EOS at 0.7), and the Smooth C-S with the
-    surface-tension control, batched graph plan: MLUPS per variant."""
+    """Four 512 x 512 periodic static droplets (R = 32, 48, 64, 96; tau = 1) with each
+    EOS the kernels support (T_r = 0.6; the two Guo-forced EOS at 0.7), and the Smooth
+    C-S with the surface-tension control, batched graph plan: MLUPS per variant."""
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
 
     variants = {
         "cs_a0.387_li": (P.EOSParams(P.EOS_CS, 0.6, 0.387, 0.387, 0.5), P.Relax()),
         "smooth_alpha0.834_li": (P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax()),
-        # the same with the surface-tension control (Sec. V's technique): its cost per step
         "smooth_alpha0.834_li_kappa0.5": (P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834), P.Relax(kappa=0.5)),
         # Peng + Guo droplets diverge below T_r ~ 0.65 (the paper's minimum for that method)
         "peng_r0.45_Tr0.7_guo": (P.EOSParams(P.EOS_PENG, 0.7, 0.387, 0.387, 0.5, r_theta=0.45),
@@ -506,28 +486,27 @@ def eos_variant_throughput(torch, steps=1000):
     }
     out = {}
     for name, (eos, relax) in variants.items():
-        b = P.Batch([(NX, NY, P.BC_PERIODIC)] * 4, [eos] * 4, [relax] * 4)
+        b = P.Batch([(512, 512, P.BC_PERIODIC)] * 4, [eos] * 4, [relax] * 4)
         d = b.derived(0)
-        for k, R in enumerate(RADII):
-            b.init_equilibrium(k, I.droplet(NX, NY, R, d["rho_v"], d["rho_l"], W=8.0))
+        for k, R in enumerate((32, 48, 64, 96)):
+            b.init_equilibrium(k, I.droplet(512, 512, R, d["rho_v"], d["rho_l"], W=8.0))
         b.set_plan(P.PLAN_GRAPH, 0)
         b.step(20)
         ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
         try:
             b.sync()
-            out[name] = 4 * NX * NY * steps / (ms / 1e3) / 1e6
+            out[name] = 4 * 512 * 512 * steps / (ms / 1e3) / 1e6
         except P.PPLBMError as e:
             out[name] = f"diverged ({e})"
         b.close()
     return out
 
 
-def impact_sweep_throughput(torch, steps=2000):
+def impact_sweep_throughput(torch, fp64_peak, steps=2000):
     """A slice of the stability study (Sec. IV.D) on the batched engine: droplet
     impact at Re = 300 on (600, 250) lattices with walls, C-S a = 0.363, Li forcing,
     two-phase tau(rho), T_r in {0.45, ..., 0.75} x v_r in {2, ..., 10}: 35 instances,
-    5.25 M nodes, graph plan with divergence isolation. Every run is stable here, so
-    all nodes count."""
+    5.25 M nodes, graph plan with divergence isolation."""
     b, n_inst = impact_sweep_batch()
     b.step(20)
     ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
@@ -537,19 +516,18 @@ def impact_sweep_throughput(torch, steps=2000):
     nodes = 600 * 250 * n_inst
     mlups = nodes * steps / (ms / 1e3) / 1e6 if stable == n_inst else None
     out = {"instances": n_inst, "stable": stable, "nodes": nodes, "steps": steps, "mlups": mlups}
-    if mlups is not None and IMPACT_FP64_PER_NODE is not None:
-        _, sm_max, _ = load_peaks()
-        peak = 2 * 152 * sm_max * 1e6
-        achieved = IMPACT_FP64_PER_NODE * mlups * 1e6
-        out["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                           "frac": achieved / peak, "fp64_per_node": IMPACT_FP64_PER_NODE}
+    if mlups is not None:
+        per = sum(FP64_PER_NODE_SHEAR.values())
+        achieved = per * mlups * 1e6
+        out["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                           "frac": achieved / 1e12 / fp64_peak, "fp64_per_node": per}
     return out
 
 
 def impact_sweep_batch():
     """The impact-sweep batch, initialised, on the graph plan: (Batch, instances)."""
+    import lbm_inputs as I
     import paper_2107_06355_gb300 as P
-    from paper_2107_06355_gb300 import sweeps as SW
 
     # initial interface widths: the planar C-S (a = 0.363) widths at each T_r
     width = {0.45: 6.0, 0.50: 7.0, 0.55: 7.0, 0.60: 9.0, 0.65: 9.0, 0.70: 10.0, 0.75: 11.0}
@@ -566,28 +544,12 @@ def impact_sweep_batch():
     b.set_isolation(True)
     for i in range(len(lats)):
         d = b.derived(i)
-        b.init_equilibrium(i, *SW._impact_profile(600, 250, 50, 25, d["rho_v"], d["rho_l"], 0.1, Ws[i]))
+        b.init_equilibrium(i, *I.impact(600, 250, 50, 25, d["rho_v"], d["rho_l"], 0.1, W=Ws[i]))
     b.set_plan(P.PLAN_GRAPH, 0)
     return b, len(lats)
 
 
-def profile_impact():
-    """The impact-sweep batch (35 lattices 600 x 250, two-phase tau, walls), launches
-    plan, 3 steps: 3 launches of each two-phase batched pass over 5.25 M nodes."""
-    import torch
-    import paper_2107_06355_gb300 as P
-
-    build_lib()
-    b, _ = impact_sweep_batch()
-    b.set_plan(P.PLAN_LAUNCHES, 0)
-    b.step(3)
-    b.sync()
-    torch.cuda.synchronize()
-    b.close()
-    print("profile impact done")
-
-
-def fd_throughput(torch, steps=200):
+def fd_throughput(torch, fp64_peak, steps=200):
     """The finite-difference solver (App. A) on a 2048 x 1024 periodic droplet grid
     (dx = 1, Smooth C-S at T_r = 0.6): grid-point updates per second. dt = 0.4: with
     the paper's 0.8 dx^2 the static droplet diverges in this scheme (CPU oracle too)."""
@@ -595,7 +557,7 @@ def fd_throughput(torch, steps=200):
     import paper_2107_06355_gb300 as P
 
     nx, ny = 2048, 1024
-    eos = P.EOSParams(P.EOS_SMOOTH, TR, A_L, A_V, ALPHA)
+    eos = P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834)
     d = P.eos_setup(eos)
     fd = P.FDSolver(nx, ny, eos, dx=1.0)
     rho = I.droplet(nx, ny, 100, d["rho_v"], d["rho_l"], W=8.0)
@@ -607,46 +569,250 @@ def fd_throughput(torch, steps=200):
     r = fd.get_state()[0]
     ok = bool(torch.isfinite(r).all())
     fd.close()
-    _, sm_max, _ = load_peaks()
-    peak = 2 * 152 * sm_max * 1e6
     achieved = FD_FP64_PER_POINT * nx * ny * steps / (ms / 1e3)
     return {"grid": f"{nx}x{ny}, dx=1, dt=0.4", "mlups": nx * ny * steps / (ms / 1e3) / 1e6,
             "ms_per_step": ms / steps, "finite": ok, "launches_per_step": 4,
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "fp64_per_point_step": FD_FP64_PER_POINT,
-                         "peak_source": f"2 FP64 instr/clk/SM x 152 SMs x {sm_max:.0f} MHz"}}
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / 1e12 / fp64_peak, "fp64_per_point_step": FD_FP64_PER_POINT}}
 
+
+# ---- the oracle on the host cores ---------------------------------------------------
+
+def _oracle_worker(conn, specs, threads_env):
+    """Spawned process: builds the oracle lattices of `specs` (untimed), then on each
+    'step' message advances every one of them by one step and replies with the seconds
+    it took."""
+    os.environ.update(threads_env)
+    sys.path.insert(0, ROOT)
+    import lbm_inputs as I
+    from oracle import eos as E
+    from oracle import lbm as L
+    import warnings
+
+    warnings.simplefilter("ignore")
+    lats, fs = [], []
+    for s in specs:
+        e = E.make_eos(E.MODE_SMOOTH, s["Tr"], s["a_l"], s["a_v"], s["alpha"])
+        lat = L.Lattice(s["nx"], s["ny"], L.BC_PERIODIC_X | L.BC_PERIODIC_Y, e, L.Relax(sigma=e.sigma()))
+        lats.append(lat)
+        fs.append(lat.init_equilibrium(initial_density(I, s, e.rho_v, e.rho_l)))
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg == "stop":
+            break
+        t0 = time.perf_counter()
+        for k, lat in enumerate(lats):
+            fs[k] = lat.step(fs[k], 1)
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+class OraclePool:
+    """The oracle (plain numpy, as it stands) advancing the instances of `specs` in
+    `workers` spawned processes, one numpy thread each, instances assigned largest
+    first to the least-loaded process. step() advances every instance by one LBM step
+    and returns the wall time of the slowest process."""
+
+    def __init__(self, specs, workers):
+        import multiprocessing as mp
+
+        from paper_2107_06355_gb300.replicas import shard_instances
+
+        ctx = mp.get_context("spawn")
+        sizes = [s["nx"] * s["ny"] for s in specs]
+        shards = [sh for sh in shard_instances(sizes, max(1, min(workers, len(specs)))) if sh]
+        env = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        self.nodes = sum(sizes)
+        self.conns, self.procs = [], []
+        for sh in shards:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, [specs[i] for i in sh], env), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    @property
+    def workers(self):
+        return len(self.procs)
+
+    def step(self):
+        for c in self.conns:
+            c.send("step")
+        return max(c.recv() for c in self.conns)
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def cpu_baseline(specs, max_seconds=20.0):
+    """The oracle on the host cores: (1) one process on a bounded sample of the
+    workload (the instances every 8th, from index 1), (2) every instance across all
+    host cores, a few steps. MLUPS each."""
+    cores = host_cores()
+    sample = [specs[k] for k in range(1, len(specs), 8)]
+    one = OraclePool(sample, 1)
+    t, n = 0.0, 0
+    while t < 0.5 * max_seconds and n < 50:
+        t += one.step()
+        n += 1
+    one.close()
+    single = one.nodes * n / t / 1e6
+    pool = OraclePool(specs, cores)
+    t2, n2 = 0.0, 0
+    while t2 < 0.25 * max_seconds and n2 < 20:
+        t2 += pool.step()
+        n2 += 1
+    pool.close()
+    all_cores = pool.nodes * n2 / t2 / 1e6
+    return {"value": all_cores, "unit": "MLUPS", "cores": pool.workers, "kind": "oracle",
+            "sample": f"all {len(specs)} instances of the workload ({pool.nodes} nodes), {n2} steps, "
+                      f"{pool.workers} processes x 1 thread, {t2:.1f} s",
+            "single_core": {"value": single, "unit": "MLUPS", "cores": 1,
+                            "sample": f"{len(sample)} instances (every 8th; {one.nodes} nodes), {n} steps, "
+                                      f"{t:.1f} s"},
+            "host_cores": cores}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each bench step is one LBM step of the whole
+    64-lattice workload, spread over the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    specs = sweep_specs()
+    pool = OraclePool(specs, host_cores())
+    for _ in range(args.warmup):
+        pool.step()
+    t = sum(pool.step() for _ in range(args.steps))
+    pool.close()
+    val = pool.nodes * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nodes_per_step": pool.nodes},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": pool.workers, "kind": "oracle",
+                             "sample": f"{args.steps} steps of all 64 instances, {pool.workers} processes"},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- small cases for ncu captures -----------------------------------------------------
+
+def profile_sweep(n=16):
+    """The first `n` lattices of the 64-lattice sweep (the bench's EOS and tiles),
+    launches plan, 3 steps: 3 launches of each batched pass."""
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    specs = sweep_specs()[:n]
+    b, _, _, _ = make_batch(P, I, specs, torch.cuda.current_stream())
+    b.set_plan(P.PLAN_LAUNCHES, 0)
+    b.step(3)
+    b.sync()
+    torch.cuda.synchronize()
+    print(f"profile sweep done: {len(specs)} lattices, {sum(s['nx'] * s['ny'] for s in specs)} nodes")
+
+
+def profile_impact_single():
+    """The 2048 x 1024 impact lattice of impact_2048, 3 steps."""
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    sim = P.Simulation(2048, 1024, P.BC_WALLS_Y, P.EOSParams(P.EOS_SMOOTH, 0.35, 0.363, 2.0, 0.838),
+                       P.Relax(kind=P.RELAX_TWO_PHASE, tau_l=0.6, visc_ratio=1.0))
+    d = sim.derived()
+    sim.init_equilibrium(*I.impact(2048, 1024, 100, 102, d["rho_v"], d["rho_l"], 0.05, W=6.0))
+    sim.step(3)
+    sim.sync()
+    torch.cuda.synchronize()
+    sim.close()
+    print("profile impact done")
+
+
+def profile_fd():
+    """The finite-difference solver on the 2048 x 1024 droplet grid, 3 steps."""
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+
+    build_lib()
+    eos = P.EOSParams(P.EOS_SMOOTH, 0.6, 0.387, 2.0, 0.834)
+    d = P.eos_setup(eos)
+    fd = P.FDSolver(2048, 1024, eos, dx=1.0)
+    rho = I.droplet(2048, 1024, 100, d["rho_v"], d["rho_l"], W=8.0)
+    fd.set_state(rho, np.zeros_like(rho), np.zeros_like(rho))
+    fd.step(3, 0.4)
+    torch.cuda.synchronize()
+    print("profile fd done")
+
+
+def profile_adjoint():
+    """Checkpointed forward and reverse pass on a 1024 x 1024 droplet (T_r = 0.5,
+    tau = 1), 12 steps with interval 4, gradient slots of alpha."""
+    import ctypes as C
+    import torch
+    import lbm_inputs as I
+    import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300 import _lib as L
+
+    build_lib()
+    nx = ny = 1024
+    steps, interval = 12, 4
+    sim = P.Simulation(nx, ny, P.BC_PERIODIC, P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775), P.Relax())
+    d = sim.derived()
+    sim.init_equilibrium(I.droplet(nx, ny, 192.0, d["rho_v"], d["rho_l"], W=7.0))
+    dev = sim.device
+    ckpt = torch.empty((steps // interval, 9, ny, nx), dtype=torch.float64, device=dev)
+    seg = torch.empty((interval, 9, ny, nx), dtype=torch.float64, device=dev)
+    lam = torch.ones((9, ny, nx), dtype=torch.float64, device=dev)
+    lam0 = torch.empty_like(lam)
+    grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
+    nb = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
+    ws = torch.empty(nb // 8 + 1, dtype=torch.float64, device=dev)
+    p = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    L.check(L.lib().pplbm_adjoint_set_slots(sim.ctx, (1 << 9) - 1), sim.ctx)
+    L.check(L.lib().pplbm_forward_checkpointed(sim.ctx, steps, interval, p(ckpt)), sim.ctx)
+    L.check(L.lib().pplbm_backward_checkpointed(sim.ctx, steps, interval, p(ckpt), p(seg), p(lam), p(lam0), p(grad),
+                                                p(ws), nb), sim.ctx)
+    torch.cuda.synchronize()
+    sim.close()
+    print("profile adjoint done")
+
+
+# ---- main ---------------------------------------------------------------------------
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=12000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline line only (no extra keys)")
     ap.add_argument("--plan", default="auto", choices=["auto", "launches", "graph", "persistent"],
                     help="batched-engine plan for the timed run (auto: autotuned)")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run one 2048x1024 droplet lattice for 3 steps (a small case for ncu captures) and exit")
+    ap.add_argument("--profile-sweep", type=int, default=None, metavar="N",
+                    help="3 steps of the first N lattices of the sweep (a small case for ncu) and exit")
+    ap.add_argument("--profile-impact", action="store_true", help="3 steps of the 2048x1024 impact (for ncu)")
     ap.add_argument("--profile-adjoint", action="store_true", help="checkpointed adjoint on 1024 x 1024 (for ncu)")
-    ap.add_argument("--profile-impact", action="store_true", help="3 steps of the impact-sweep batch (for ncu)")
     ap.add_argument("--profile-fd", action="store_true", help="3 steps of the FD solver on 2048 x 1024 (for ncu)")
-    ap.add_argument("--profile-batch", action="store_true",
-                    help="run the four 512x512 droplets through the batched engine (launches plan) for 3 steps and exit")
-    ap.add_argument("--profile-kappa", type=float, default=None,
-                    help="as --profile-batch, with the surface-tension control at this kappa")
     args = ap.parse_args()
-    if args.profile_case:
-        return profile_case()
-    if args.profile_batch:
-        return profile_batch()
-    if args.profile_kappa is not None:
-        return profile_batch(args.profile_kappa)
+    if args.profile_sweep is not None:
+        return profile_sweep(args.profile_sweep)
+    if args.profile_impact:
+        return profile_impact_single()
     if args.profile_fd:
         return profile_fd()
-    if args.profile_impact:
-        return profile_impact()
     if args.profile_adjoint:
         return profile_adjoint()
     if args.warmup < 3:
@@ -657,6 +823,7 @@ def main():
     import torch
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
+    from paper_2107_06355_gb300.replicas import max_over_ranks
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -669,141 +836,154 @@ def main():
         torch.distributed.barrier()
         build_lib()  # no-op after rank 0 (up to date)
 
-    stream = torch.cuda.current_stream()
-    specs = [dict(kind="droplet", nx=NX, ny=NY, R=R, Tr=TR) for R in RADII]
-    batch, _, _, rho0s = make_batch(P, I, specs, stream)
-    nodes = NX * NY * len(specs)
-    if args.plan == "auto":
-        plan = batch.autotune(trial_steps=20)
-    else:
-        batch.set_plan({"launches": P.PLAN_LAUNCHES, "graph": P.PLAN_GRAPH, "persistent": P.PLAN_PERSISTENT}[args.plan], 0)
-        plan = batch.plan()
-    batch.step(args.warmup)
-    torch.cuda.synchronize()
-    batch.enable_timing(4)
-
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    stream = torch.cuda.current_stream()
+    fp64 = measure_fp64_peak(torch, local)
+    specs = sweep_specs()
+    nodes = sum(s["nx"] * s["ny"] for s in specs)
+    batch, _, _, rho0s = make_batch(P, I, specs, stream)
+    if args.plan == "auto":
+        plan = batch.autotune(trial_steps=20)
+    else:
+        batch.set_plan({"launches": P.PLAN_LAUNCHES, "graph": P.PLAN_GRAPH,
+                        "persistent": P.PLAN_PERSISTENT}[args.plan], 0)
+        plan = batch.plan()
+    mode = {0: "launches", 1: "graph", 2: "persistent"}[plan["mode"]]
+    per_pass = plan["mode"] != P.PLAN_PERSISTENT
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    if per_pass:
+        batch.enable_pass_timing(args.steps)
+    batch.enable_timing(1)
+    acc = {"pass_ms": [0.0, 0.0], "pass_n": [0, 0], "call_ms": 0.0, "call_steps": 0}
+
+    def collect():  # after each block: the per-pass and per-call CUDA-event sums
+        ms_, n_ = batch.times()
+        acc["call_ms"] += ms_
+        acc["call_steps"] += n_
+        if per_pass:
+            (a0, a1), (n0, n1) = batch.pass_times()
+            acc["pass_ms"][0] += a0
+            acc["pass_ms"][1] += a1
+            acc["pass_n"][0] += n0
+            acc["pass_n"][1] += n1
+
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    batch.step(args.steps)
-    e1.record(stream)
-    barrier()
+    blocks = timed_blocks(torch, stream, lambda: batch.step(args.steps), barrier, after=collect)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    call_ms, call_steps = batch.times()
     batch.enable_timing(0)
-    from paper_2107_06355_gb300.replicas import max_over_ranks
-
-    ms = max_over_ranks(ms, device="cuda")  # each rank runs its own replica; slowest rank sets the time
+    if per_pass:
+        batch.enable_pass_timing(0)
+    call_ms, call_steps = acc["call_ms"], acc["call_steps"]
+    pass_ms, pass_n = acc["pass_ms"], acc["pass_n"]
+    med_ms = max_over_ranks(float(np.median(blocks)), device="cuda")  # each rank runs its own replica
     batch.sync()
-
-    # the same four lattices stepped one context at a time (two launches per lattice per step)
-    sims, _ = serial_sims(torch, stream)
-    for s in sims:
-        s.step(args.warmup)
-    serial_steps = min(args.steps, 2000)
-    for s in sims:
-        s.enable_kernel_timing(serial_steps)
-
-    def serial():
-        for _ in range(serial_steps):
-            for s in sims:
-                s.step(1)
-
-    ms_serial = time_device(torch, stream, serial)
-    k_ms, k_n = [0.0, 0.0], [0, 0]
-    for s in sims:
-        t, n = s.kernel_times()
-        s.enable_kernel_timing(0)
-        for i in range(2):
-            k_ms[i] += t[i]
-            k_n[i] += n[i]
-
-    # end to end through the batch's host-to-host call: the four host densities in
-    # (pinned), f = f_eq, E2E_INNER steps with the tuned plan, the four densities out
-    pin_in = [torch.from_numpy(np.ascontiguousarray(r)).pin_memory() for r in rho0s]
-    pin_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in specs]
-
-    def e2e_call():
-        batch.run_host(pin_in, E2E_INNER, pin_out)
-
-    e2e_call()
-    e2e_steps = 5
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_call()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_mlups = nodes * E2E_INNER / e2e_s / 1e6 * ws
-    if not all(bool(torch.isfinite(po).all()) for po in pin_out):
-        raise RuntimeError("end-to-end densities are not finite")
-    for s in sims:
-        m, umax, bad = s.guard()
-        if bad:
-            raise RuntimeError("benchmark state diverged")
-        s.close()
+    g = batch.guard()
+    if (g[:, 2] > 0).any():
+        raise RuntimeError("benchmark state diverged")
 
     hbm_gbs, sm_max, peak_src = load_peaks()
-    ms_per_step = ms / args.steps
-    mlups = nodes * args.steps / (ms / 1e3) / 1e6 * ws
-    fp64_peak = 2 * 152 * sm_max * 1e6  # FP64 instructions/s: 2 per SM per clock
-    ops_per_node = FP64_OPS_PER_NODE["rho_psi"] + FP64_OPS_PER_NODE["collide"]
-    bytes_per_node = BYTES_PER_NODE["rho_psi"] + BYTES_PER_NODE["collide"]
-    step_s = call_ms / max(1, call_steps) / 1e3
-    achieved = ops_per_node * nodes / step_s
-    mode = {0: "launches", 1: "graph", 2: "persistent"}[plan["mode"]]
-    launches_per_step = 0 if plan["mode"] == 2 else 2
+    ms_per_step = med_ms / args.steps
+    step_s = ms_per_step / 1e3
+    mlups = nodes * args.steps / (med_ms / 1e3) / 1e6 * ws
+    fp64_peak = fp64["value"]  # T FP64 instructions/s, measured above
+    if per_pass:
+        kern = {"rho_psi": pass_ms[0] / max(1, pass_n[0]), "collide": pass_ms[1] / max(1, pass_n[1])}
+        dom = max(kern, key=kern.get)
+        dom_s = kern[dom] / 1e3
+        dom_name = {"rho_psi": "k_batch_rho_psi", "collide": "k_batch_collide"}[dom]
+        dom_flops = FP64_PER_NODE[dom] * nodes
+        dom_bytes = BYTES_PER_NODE[dom] * nodes
+        share = kern[dom] / (kern["rho_psi"] + kern["collide"])
+    else:
+        kern = {"persistent": call_ms / max(1, call_steps)}
+        dom, dom_name, share = "persistent", "k_batch_persistent", 1.0
+        dom_s = call_ms / max(1, call_steps) / 1e3
+        dom_flops = sum(FP64_PER_NODE.values()) * nodes
+        dom_bytes = sum(BYTES_PER_NODE.values()) * nodes
+    achieved = dom_flops / dom_s / 1e12
+    launches_per_block = 2 * args.steps if per_pass else 1
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattices": len(specs), "nx": NX, "ny": NY, "nodes_per_step": nodes,
-                   "engine": f"batched ({mode}, tiles {plan['tile_width'] or 'per-instance'})",
-                   "parallelism": f"replicas{ws}", "l2": "state > L2 (about 180 MB per step), no flush"},
-        "roofline": {"bound": "alu", "kernel": f"batched step: density/psi + collision passes ({mode})",
-                     "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": step_traffic(),
-                     "traffic_unit": "DRAM bytes per step (both passes; ncu, same kernel sources)",
-                     "flop_convention": "1 per FP64 add/mul/fma instruction; 84 per node update",
-                     "peak_source": f"2 FP64 instr/clk/SM x 152 SMs x {sm_max:.0f} MHz",
-                     "launch_ms": step_s * 1e3},
-        "roofline_hbm": {"achieved": bytes_per_node * nodes / step_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
-                         "frac": bytes_per_node * nodes / step_s / 1e9 / hbm_gbs,
-                         "bytes_per_node": bytes_per_node, "peak_source": peak_src},
+        "config": {"workload": WORKLOAD, "lattices": len(specs), "nodes_per_step": nodes,
+                   "engine": f"batched ({mode}{', per-pass CUDA events' if per_pass else ''}, tiles "
+                             f"{plan['tile_width'] or 'per-instance'})",
+                   "parallelism": f"replicas{ws}",
+                   "timing": f"median of {len(blocks)} blocks of {args.steps} steps ({sum(blocks) / 1e3:.2f} s)",
+                   "l2": "state about 2.4 GB >> 126 MB L2, no flush"},
+        "blocks_ms": blocks,
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": pass_traffic(dom) if per_pass else None,
+                     "traffic_unit": "DRAM bytes per launch (ncu capture, same kernel sources)",
+                     "flop_convention": "1 per FP64 add/mul/fma instruction (per thread); "
+                                        f"{FP64_PER_NODE.get(dom, sum(FP64_PER_NODE.values()))} per node",
+                     "peak_source": "measured: pplbm_fp64_peak in this run (fp64_peak_measured)",
+                     "launch_ms": dom_s * 1e3, "share_of_step": share},
+        "kernel_ms": kern,
+        "fp64_peak_measured": fp64,
+        "roofline_hbm": {
+            "dominant_kernel": {"achieved": dom_bytes / dom_s / 1e9, "frac": dom_bytes / dom_s / 1e9 / hbm_gbs,
+                                "bytes_per_node": BYTES_PER_NODE.get(dom, sum(BYTES_PER_NODE.values()))},
+            "step_scope": {"bytes_per_node": BYTES_PER_NODE_SCOPE,
+                           "achieved": BYTES_PER_NODE_SCOPE * nodes / step_s / 1e9,
+                           "frac": BYTES_PER_NODE_SCOPE * nodes / step_s / 1e9 / hbm_gbs},
+            "step_built": {"bytes_per_node": sum(BYTES_PER_NODE.values()),
+                           "achieved": sum(BYTES_PER_NODE.values()) * nodes / step_s / 1e9,
+                           "frac": sum(BYTES_PER_NODE.values()) * nodes / step_s / 1e9 / hbm_gbs},
+            "peak": hbm_gbs, "unit": "GB/s", "peak_source": peak_src},
+        "fp64_roofline_step": {"fp64_per_node": sum(FP64_PER_NODE.values()),
+                               "achieved": sum(FP64_PER_NODE.values()) * nodes / step_s / 1e12,
+                               "frac": sum(FP64_PER_NODE.values()) * nodes / step_s / 1e12 / fp64_peak},
         "autotune_ms_per_step": {"launches": plan["ms_launches"], "graph": plan["ms_graph"],
                                  "persistent": plan["ms_persistent"]},
-        "serial_contexts": {"mlups": nodes * serial_steps / (ms_serial / 1e3) / 1e6, "steps": serial_steps,
-                            "kernel_ms": {"rho_psi": k_ms[0] / max(1, k_n[0]),
-                                          "collide": k_ms[1] / max(1, k_n[1])}},
-        "e2e": {"value": e2e_mlups, "unit": "MLUPS",
-                "h2d_bytes_per_step": 8 * NX * NY * len(specs) // E2E_INNER,
-                "d2h_bytes_per_step": 8 * NX * NY * len(specs) // E2E_INNER,
-                "steps_per_call": E2E_INNER, "h2d_bytes_per_call": 8 * NX * NY * len(specs),
-                "d2h_bytes_per_call": 8 * NX * NY * len(specs),
-                "call": f"pplbm_batch_run_host: H2D of the four rho0 (pinned), f=f_eq, {E2E_INNER} steps "
-                        "(tuned plan), D2H of the four rho"},
-        "gpu_launches": launches_per_step * args.steps + (1 if plan["mode"] == 2 else 0),
+        "gpu_launches": launches_per_block * len(blocks),
         "clocks": clk,
     }
-    if rank == 0 and ws == 1 and not args.no_sweep:
-        line["batch_sweep"] = sweep_comparison(torch, stream, 100)
+
+    # end to end through the batch's host-to-host call: the 64 host densities in
+    # (pinned), f = f_eq, E2E_INNER steps with the tuned plan, the 64 densities out
+    pin_in = [torch.from_numpy(np.ascontiguousarray(r)).pin_memory() for r in rho0s]
+    pin_out = [torch.empty(r.shape, dtype=torch.float64).pin_memory() for r in rho0s]
+    batch.run_host(pin_in, E2E_INNER, pin_out)
+    e2e_calls = 3
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_calls):
+        batch.run_host(pin_in, E2E_INNER, pin_out)
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_calls)
+    if not all(bool(torch.isfinite(po).all()) for po in pin_out):
+        raise RuntimeError("end-to-end densities are not finite")
+    line["e2e"] = {"value": nodes * E2E_INNER / e2e_s / 1e6 * ws, "unit": "MLUPS",
+                   "h2d_bytes_per_step": 8 * nodes // E2E_INNER, "d2h_bytes_per_step": 8 * nodes // E2E_INNER,
+                   "steps_per_call": E2E_INNER, "h2d_bytes_per_call": 8 * nodes, "d2h_bytes_per_call": 8 * nodes,
+                   "call": f"pplbm_batch_run_host: H2D of the 64 rho0 (pinned), f=f_eq, {E2E_INNER} steps "
+                           "(tuned plan), D2H of the 64 rho"}
+
+    if rank == 0 and ws == 1 and not args.no_extras:
+        line["plans_ms_per_step"] = plan_times(torch, stream, batch, P, steps=1000)
+        line["batched_vs_serial"] = serial_comparison(torch, stream, specs, ms_per_step)
+        batch.close()
+        torch.cuda.empty_cache()
+        line["impact_2048x1024"] = impact_2048(torch, stream, barrier)
         line["adjoint"] = adjoint_cost(torch)
         line["eos_variants_mlups"] = eos_variant_throughput(torch)
-        line["fd_solver"] = fd_throughput(torch)
-        line["impact_sweep"] = impact_sweep_throughput(torch)
+        line["fd_solver"] = fd_throughput(torch, fp64_peak)
+        line["impact_sweep"] = impact_sweep_throughput(torch, fp64_peak)
+    else:
+        batch.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = time_oracle_sample()
+        line["cpu_baseline"] = cpu_baseline(specs)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 

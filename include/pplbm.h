@@ -160,8 +160,9 @@ typedef struct pplbm_ctx pplbm_ctx;
 pplbm_status pplbm_eos_setup(const pplbm_eos_params* params, double G, pplbm_eos_derived* out);
 
 /* Bytes of caller-owned device workspace a lattice needs with the given
- * relaxation set: two distribution buffers (9 planes each), psi (1 plane) and the
- * moments the collision pass reads (3, 5 or 9 planes). 0 on invalid input. */
+ * relaxation set: two distribution buffers (9 planes each), psi (1 plane), the
+ * moments the collision pass reads (3, 5 or 9 planes) and the guard's density
+ * snapshot (1 plane). 0 on invalid input. */
 size_t pplbm_workspace_bytes(const pplbm_lattice* lattice, const pplbm_relax* relax);
 
 /* Creates a context for one lattice. `workspace` is device memory of at least
@@ -206,13 +207,24 @@ pplbm_status pplbm_set_f(pplbm_ctx* ctx, const double* f);
  * of steps issued so far (steps_done may be NULL). */
 pplbm_status pplbm_sync(pplbm_ctx* ctx, int64_t* steps_done);
 
-/* Per-step guard (Sec. III.A convergence check and mass): writes to host
- * out[0] = total mass sum(rho), out[1] = max |j|/rho with j = sum_i f_i c_i (the
- * momentum before the half-force shift of Eq. Momentum; the fluid velocity is in
- * pplbm_get_fields and pplbm_batch_guard), out[2] = number of nodes with a
- * non-finite or non-positive density. Deterministic two-pass reduction.
- * Synchronises the stream. */
-pplbm_status pplbm_guard(pplbm_ctx* ctx, double out[3]);
+/* Per-M-step guard (Sec. III.A: the convergence criterion of the planar tests, the
+ * paragraph after Eq. PlanarIntDensity; mass; the stability test of the dynamic
+ * runs, Sec. IV). First runs the density/psi pass over the current state (as the
+ * next step would; the psi and moment planes are rebuilt by every step anyway),
+ * then writes to the host array out[4]:
+ *   out[0] = mass sum(rho) over the nodes with a finite, positive density;
+ *   out[1] = max |u| with u = (j + F/2)/rho the fluid velocity of Eq. Momentum (F the
+ *            Shan-Chen force of the collision pass: same stencil, wrap and wall
+ *            ghosts), the same quantity pplbm_batch_guard reports;
+ *   out[2] = number of nodes with a non-finite or non-positive density (excluded
+ *            from the other three);
+ *   out[3] = sum |rho - rho'| / sum rho, rho' the density at the previous
+ *            pplbm_guard call (a snapshot plane in the workspace): called every
+ *            100 steps this is the paper's residual, converged below 1e-6. -1 on the
+ *            first call and after pplbm_init_equilibrium / pplbm_set_f.
+ * Deterministic (fixed partition, fixed-order reduction). Synchronises the stream.
+ * Returns PPLBM_ERR_DIVERGED (sticky) when out[2] > 0. */
+pplbm_status pplbm_guard(pplbm_ctx* ctx, double out[4]);
 
 /* The EOS block the context uses. */
 pplbm_status pplbm_get_derived(const pplbm_ctx* ctx, pplbm_eos_derived* out);
@@ -407,6 +419,17 @@ pplbm_status pplbm_batch_get_derived(const pplbm_batch* b, int32_t i, pplbm_eos_
  * steps since the previous call, then resets. */
 pplbm_status pplbm_batch_enable_timing(pplbm_batch* b, int64_t capacity);
 pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps);
+/* Per-pass timing aid (for the roofline of each kernel). With capacity > 0, every
+ * step is issued as two plain launches (the graph plan's replay is set aside while
+ * this is on), each bracketed by a CUDA event pair on the batch's stream; events for
+ * `capacity` steps are created here (more on demand). PPLBM_ERR_STATE under the
+ * persistent plan, whose passes share one launch. capacity = 0 turns it off. The
+ * autotuner times every plan without these events and turns them off if it keeps
+ * the persistent plan. pplbm_batch_pass_times synchronises and returns, since the
+ * previous call, the summed milliseconds and launch counts of the density/psi pass
+ * (index 0) and of the collision pass (index 1), then resets them. */
+pplbm_status pplbm_batch_enable_pass_timing(pplbm_batch* b, int64_t capacity);
+pplbm_status pplbm_batch_pass_times(pplbm_batch* b, double ms[2], int64_t launches[2]);
 /* Failure-detection self-test of the persistent kernel's bounded grid barrier:
  * launches one step in which one block leaves without arriving, with waits
  * limited to spin_limit sleeps of ~100 ns; returns PPLBM_ERR_TIMEOUT when the
@@ -455,6 +478,19 @@ void pplbm_batch_destroy(pplbm_batch* b);
  * Asynchronous on `stream`. */
 pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed, double* out, void* stream);
 
+/* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the
+ * step's per-node arithmetic is double precision throughout, Sec. II; on this GPU
+ * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)
+ * blocks of 256 threads; each thread runs `iters` rounds of 8 independent FP64
+ * fused multiply-adds. Times the launch with CUDA events on `stream` and
+ * synchronises it. Writes to host out[3]: out[0] = FP64 FMA instructions per
+ * second (counted per thread, as the step's per-node instruction counts are),
+ * out[1] = the launch's milliseconds, out[2] = blocks launched. `sink` is one
+ * device double the kernel may write (it never does for these inputs; it keeps
+ * the chains from being optimised away). PPLBM_ERR_ARG for blocks_per_sm outside
+ * [1, 64], iters < 1 or NULL pointers. */
+pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, long long iters, double* sink, double* out, void* stream);
+
 /* Kernel timing, a profiling aid. With capacity > 0, pplbm_step records a CUDA
  * event pair around every launch of the two step kernels on the context's
  * stream; events for `capacity` launches of each kernel are created here, outside
@@ -471,14 +507,16 @@ pplbm_status pplbm_kernel_times(pplbm_ctx* ctx, double ms[2], int64_t launches[2
  * as code inside a host framework that owns all device memory through its own
  * pool or budget, or code on a latency-critical stream where cudaMalloc/cudaFree
  * would synchronise the device. There is no context: the caller passes the
- * lattice, an EOS block from pplbm_eos_setup (host only), the relaxation set and
- * two distinct device buffers of 9*nx*ny values (plane-major); psi and the
+ * lattice, an EOS block from pplbm_eos_setup (host only; any PPLBM_EOS_* mode),
+ * the relaxation set and two non-overlapping device buffers of 9*nx*ny values
+ * (plane-major; overlapping ranges return PPLBM_ERR_ARG); psi and the
  * moment planes live in a static device array inside the library, so
  * nx*ny <= 65536 (larger lattices return PPLBM_ERR_ARG with a message saying so).
  *  - The array (5.2 MB) is held by every GPU that loads the library until the
  *    process exits. Its address is looked up once per device, by the first call
  *    made while that device is current; make that first call before any stream
- *    capture.
+ *    capture. The address is kept for the life of the process: after a
+ *    cudaDeviceReset() on that device this entry point must not be called.
  *  - Every call uses the same array: calls that overlap on the GPU (other
  *    streams, other threads) race and give undefined results. The error word in
  *    it is cleared at the start of each call.

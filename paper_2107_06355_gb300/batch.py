@@ -114,6 +114,17 @@ class Batch:
         self._check(L.lib().pplbm_batch_times(self.b, C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
+    def enable_pass_timing(self, capacity=4096):
+        """CUDA events around each pass of every step (capacity 0 turns it off)."""
+        self._check(L.lib().pplbm_batch_enable_pass_timing(self.b, int(capacity)))
+
+    def pass_times(self):
+        """((ms density/psi pass, ms collision pass), (launches, launches)) since the last call."""
+        ms = (C.c_double * 2)()
+        n = (C.c_int64 * 2)()
+        self._check(L.lib().pplbm_batch_pass_times(self.b, ms, n))
+        return (ms[0], ms[1]), (n[0], n[1])
+
     def set_isolation(self, on=True):
         """Let diverged instances be reported individually instead of stopping the batch."""
         self._check(L.lib().pplbm_batch_set_isolation(self.b, 1 if on else 0))
@@ -148,8 +159,9 @@ class Batch:
         self._check(L.lib().pplbm_batch_run_host(self.b, src, int(nsteps), dst))
 
     def guard(self):
-        """(n, 4) array per instance: mass, max |j|/rho, bad-node count, residual
-        against the previous guard call (-1 when there is none); synchronises."""
+        """(n, 4) array per instance: mass, max |u| with u = (j + F/2)/rho, bad-node
+        count, residual against the previous guard call (-1 when there is none);
+        synchronises."""
         import numpy as np
 
         out = np.empty(4 * self.n, dtype=np.float64)

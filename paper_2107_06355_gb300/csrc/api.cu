@@ -143,7 +143,7 @@ size_t pplbm_workspace_bytes(const pplbm_lattice* lattice, const pplbm_relax* re
   const int kind = collision_kind(relax);
   if (kind < 0) return 0;
   const size_t n = (size_t)lattice->nx * lattice->ny;
-  return sizeof(double) * n * (9 + 9 + 1 + (size_t)moment_planes(kind));
+  return sizeof(double) * n * (9 + 9 + 1 + (size_t)moment_planes(kind) + 1);
 }
 
 pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const pplbm_eos_params* eos,
@@ -172,9 +172,11 @@ pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const p
   c->fB = w + 9 * c->n;
   c->psi = w + 18 * c->n;
   c->mom = w + 19 * c->n;
+  c->snap = w + (19 + c->nmom) * c->n;
+  c->snap_valid = false;
   c->stream = (cudaStream_t)stream;
   c->sticky = PPLBM_OK;
-  const size_t partial_bytes = sizeof(double) * 3 * guard_blocks();
+  const size_t partial_bytes = sizeof(double) * 4 * guard_blocks();
   const size_t block_bytes = 256 + partial_bytes + 256;
   cudaError_t e = cudaMalloc(&c->dev_block, block_bytes);
   if (e != cudaSuccess) {
@@ -228,6 +230,7 @@ pplbm_status pplbm_init_equilibrium(pplbm_ctx* c, const double* rho0, const doub
   launch_init_eq(c->args, c->fA, r, u, v, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   c->steps = 0;
+  c->snap_valid = false;
   return poll_error(c);
 }
 
@@ -283,6 +286,7 @@ pplbm_status pplbm_set_f(pplbm_ctx* c, const double* f) {
   if (pplbm_status s = check_sticky(c)) return s;
   CUDA_TRY(c, cudaMemcpyAsync(c->fA, f, sizeof(double) * 9 * c->n, cudaMemcpyDefault, c->stream));
   if (!is_device_ptr(f)) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->snap_valid = false;
   return PPLBM_OK;
 }
 
@@ -293,12 +297,17 @@ pplbm_status pplbm_sync(pplbm_ctx* c, int64_t* steps_done) {
   return s;
 }
 
-pplbm_status pplbm_guard(pplbm_ctx* c, double out[3]) {
+pplbm_status pplbm_guard(pplbm_ctx* c, double out[4]) {
   if (!c || !out) return fail(c, PPLBM_ERR_ARG, "out is NULL");
-  launch_guard(c->args, c->fA, c->d_partials, c->d_guard, c->stream);
+  if (pplbm_status s = check_sticky(c)) return s;
+  StepArgs a = c->args;
+  a.f_in = c->fA;
+  a.f_out = c->fB;
+  launch_guard(a, c->snap, c->snap_valid ? 1 : 0, c->d_partials, c->d_guard, c->stream);
   CUDA_TRY(c, cudaGetLastError());
-  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_guard, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_guard, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   const pplbm_status s = poll_error(c);
+  c->snap_valid = true;
   if (s == PPLBM_OK && out[2] > 0) {
     c->sticky = PPLBM_ERR_DIVERGED;
     c->msg = "non-finite or non-positive density in the state";

@@ -153,40 +153,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* 
 }
 
 // Guard, pass 1: one block per 256-node work item of the density pass; per block
-// (mass, max |u|, bad count, sum |rho - rho'|), reduced in a fixed tree order.
-// Runs after a density pass over the current state, so rho, j and psi are those
-// the next step starts from; u = (j + F/2)/rho is the fluid velocity of Eq.
-// Momentum, with the Shan-Chen force evaluated as in the collision pass (same
-// stencil, periodic wrap, wall ghost values). Refreshes the snapshot rho'.
-constexpr int kGuardQ = 4;
-
-__device__ __forceinline__ void block_reduce4(double v[kGuardQ], double (*s)[kThreads]) {
-  for (int q = 0; q < kGuardQ; ++q) s[q][threadIdx.x] = v[q];
-  __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + w];
-      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
-      s[2][threadIdx.x] += s[2][threadIdx.x + w];
-      s[3][threadIdx.x] += s[3][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-}
-
-// psi at (x + dx, y + dy) for 0 <= x < nx, 0 <= y < ny, |dx|, |dy| <= 1
-__device__ __forceinline__ double psi_near(const StepArgs& a, int x, int y, int dx, int dy) {
-  const int gx = wrap_index(x + dx, a.nx);
-  int gy = y + dy;
-  if (a.walls) {
-    if (gy < 0) return a.psi_ghost_bottom;
-    if (gy >= a.ny) return a.psi_ghost_top;
-  } else {
-    gy = wrap_index(gy, a.ny);
-  }
-  return a.psi[(int64_t)gy * a.nx + gx];
-}
-
+// (mass, max |u|, bad count, sum |rho - rho'|), reduced in a fixed tree order
+// (guard_node, the same terms as the single-lattice guard). Runs after a density
+// pass over the current state, so rho, j and psi are those the next step starts
+// from. Refreshes the snapshot rho'.
 __global__ void __launch_bounds__(kThreads) k_batch_guard_partial(const BatchInst* inst, const int* owner, int parity,
                                                                   const int* snap_valid, double* partials) {
   __shared__ double s[kGuardQ][kThreads];
@@ -194,29 +164,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_guard_partial(const BatchIns
   const int id = owner[w];
   const BatchInst& I = inst[id];
   const StepArgs& a = I.a[parity];
-  const int64_t n = a.n;
   const int64_t i = (int64_t)(w - I.k1_start) * kThreads + threadIdx.x;
   double v[kGuardQ] = {0.0, 0.0, 0.0, 0.0};
-  if (i < n) {
-    const double rho = a.mom[i];
-    if (!(rho > 0.0 && rho < 1e300)) {
-      v[2] = 1.0;
-    } else {
-      const int y = (int)(i / a.nx), x = (int)(i - (int64_t)y * a.nx);
-      const double pE = psi_near(a, x, y, 1, 0), pW = psi_near(a, x, y, -1, 0);
-      const double pN = psi_near(a, x, y, 0, 1), pS = psi_near(a, x, y, 0, -1);
-      const double d1 = psi_near(a, x, y, 1, 1) - psi_near(a, x, y, -1, -1);
-      const double d2 = psi_near(a, x, y, 1, -1) - psi_near(a, x, y, -1, 1);
-      const double gx = 4.0 * (pE - pW) + (d1 + d2), gy = 4.0 * (pN - pS) + (d1 - d2);
-      const double cH = a.half_force * a.psi[i];
-      const double ux = (a.mom[n + i] + cH * gx) / rho, uy = (a.mom[2 * n + i] + cH * gy) / rho;
-      v[0] = rho;
-      v[1] = sqrt(ux * ux + uy * uy);
-      if (snap_valid[id]) v[3] = fabs(rho - I.snap[i]);
-    }
-    I.snap[i] = rho;
-  }
-  block_reduce4(v, s);
+  if (i < a.n) guard_node(a, i, I.snap, snap_valid[id] != 0, v);
+  guard_block_reduce<kThreads>(v, s);
   if (threadIdx.x < kGuardQ) partials[kGuardQ * (int64_t)w + threadIdx.x] = s[threadIdx.x][0];
 }
 
@@ -235,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_guard_final(const BatchInst*
     v[2] += p[2];
     v[3] += p[3];
   }
-  block_reduce4(v, s);
+  guard_block_reduce<kThreads>(v, s);
   if (threadIdx.x == 0) {
     out[kGuardQ * id + 0] = s[0][0];
     out[kGuardQ * id + 1] = s[1][0];
@@ -283,6 +234,24 @@ void launch_pair(int kind, bool st, const BatchInst* inst, const int* o1, int n1
     launch_pair_t<true>(kind, inst, o1, n1, o2, n2, parity, s);
   else
     launch_pair_t<false>(kind, inst, o1, n1, o2, n2, parity, s);
+}
+
+// the collision pass alone, over every instance
+void launch_collision_pass(int kind, bool st, const BatchInst* inst, const int* o2, int n2, int parity,
+                           cudaStream_t s) {
+#define PPLBM_K2(K)                                                                   \
+  do {                                                                                \
+    if (st)                                                                           \
+      k_batch_collide<K, true><<<n2, kThreads, 0, s>>>(inst, o2, parity);             \
+    else                                                                              \
+      k_batch_collide<K, false><<<n2, kThreads, 0, s>>>(inst, o2, parity);            \
+  } while (0)
+  switch (kind) {
+    case kUnitTau: PPLBM_K2(kUnitTau); break;
+    case kShearTau: PPLBM_K2(kShearTau); break;
+    default: PPLBM_K2(kFullMrt); break;
+  }
+#undef PPLBM_K2
 }
 
 // the density/psi pass alone, over every instance (refreshes psi and the moments)
@@ -373,6 +342,11 @@ struct pplbm_batch {
   std::vector<cudaEvent_t> ev;
   size_t ev_used;
   int64_t timed_steps;
+  // per-pass timing: event pairs around every launch of each pass (0: density/psi,
+  // 1: collision); while on, every step is issued as two plain launches
+  bool pass_timing;
+  std::vector<cudaEvent_t> pev[2];
+  size_t pev_used[2];
 };
 
 namespace {
@@ -512,8 +486,39 @@ pplbm_status launch_persistent(pplbm_batch* b, int64_t nsteps, cudaStream_t s, u
   return PPLBM_OK;
 }
 
+pplbm_status grow_pass_events(pplbm_batch* b, int k, size_t need) {
+  while (b->pev[k].size() < need) {
+    cudaEvent_t e;
+    BTRY(b, cudaEventCreate(&e));
+    b->pev[k].push_back(e);
+  }
+  return PPLBM_OK;
+}
+
+// one step as two plain launches, each bracketed by an event pair
+pplbm_status issue_timed_step(pplbm_batch* b, cudaStream_t s) {
+  for (int k = 0; k < 2; ++k) {
+    if (pplbm_status st = grow_pass_events(b, k, b->pev_used[k] + 2)) return st;
+    BTRY(b, cudaEventRecord(b->pev[k][b->pev_used[k]], s));
+    if (k == 0)
+      launch_density_pass(b->kind, b->d_inst, b->d_owner1, b->n1, b->parity, s);
+    else
+      launch_collision_pass(b->kind, b->st, b->d_inst, b->d_owner2, b->n2, b->parity, s);
+    BTRY(b, cudaEventRecord(b->pev[k][b->pev_used[k] + 1], s));
+    b->pev_used[k] += 2;
+  }
+  b->parity ^= 1;
+  return PPLBM_OK;
+}
+
 pplbm_status issue_steps(pplbm_batch* b, int64_t nsteps, cudaStream_t s) {
   int64_t k = 0;
+  if (b->pass_timing) {
+    for (; k < nsteps; ++k)
+      if (pplbm_status st = issue_timed_step(b, s)) return st;
+    BTRY(b, cudaGetLastError());
+    return PPLBM_OK;
+  }
   if (b->plan.mode == PPLBM_PLAN_PERSISTENT && nsteps > 0) {
     if (pplbm_status st = launch_persistent(b, nsteps, s, kSpinLimit, -1)) return st;
     b->parity = (int)((b->parity + nsteps) & 1);
@@ -777,6 +782,8 @@ pplbm_status pplbm_batch_set_f(pplbm_batch* b, int32_t i, const double* f) {
 
 pplbm_status pplbm_batch_set_plan(pplbm_batch* b, int32_t mode, int32_t tile_width) {
   if (!b) return PPLBM_ERR_ARG;
+  if (b->pass_timing && mode == PPLBM_PLAN_PERSISTENT)
+    return bfail(b, PPLBM_ERR_STATE, "per-pass timing is on: the persistent plan has one launch");
   BTRY(b, cudaStreamSynchronize(b->stream));
   return apply_plan(b, mode, tile_width);
 }
@@ -802,6 +809,8 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
     cudaMemcpyAsync(backup + off, a.f_in, sizeof(double) * 9 * a.n, cudaMemcpyDeviceToDevice, b->stream);
     off += 9 * (size_t)a.n;
   }
+  const bool pass_timing = b->pass_timing;  // the trials time whole steps, each plan as it runs
+  b->pass_timing = false;
   const int modes[3] = {PPLBM_PLAN_LAUNCHES, PPLBM_PLAN_GRAPH, PPLBM_PLAN_PERSISTENT};
   const int widths[2] = {0, 32};
   double best = 1e300;
@@ -848,6 +857,7 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
   }
   cudaStreamSynchronize(b->stream);
   cudaFree(backup);
+  b->pass_timing = pass_timing && best_mode != PPLBM_PLAN_PERSISTENT;
   if (st != PPLBM_OK) return st;
   if (pplbm_status s = poll(b)) return s;
   const double keep_l = b->plan.ms_launches, keep_g = b->plan.ms_graph, keep_p = b->plan.ms_persistent;
@@ -902,6 +912,35 @@ pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps) {
   return PPLBM_OK;
 }
 
+pplbm_status pplbm_batch_enable_pass_timing(pplbm_batch* b, int64_t capacity) {
+  if (!b || capacity < 0) return PPLBM_ERR_ARG;
+  if (capacity > 0 && b->plan.mode == PPLBM_PLAN_PERSISTENT)
+    return bfail(b, PPLBM_ERR_STATE, "per-pass timing needs the launches or graph plan (the persistent plan has one launch)");
+  b->pass_timing = capacity > 0;
+  for (int k = 0; k < 2; ++k) {
+    if (pplbm_status st = grow_pass_events(b, k, 2 * (size_t)capacity)) return st;
+    b->pev_used[k] = 0;
+  }
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_batch_pass_times(pplbm_batch* b, double ms[2], int64_t launches[2]) {
+  if (!b || !ms || !launches) return PPLBM_ERR_ARG;
+  BTRY(b, cudaStreamSynchronize(b->stream));
+  for (int k = 0; k < 2; ++k) {
+    double acc = 0.0;
+    for (size_t i = 0; i + 1 < b->pev_used[k]; i += 2) {
+      float t = 0.f;
+      BTRY(b, cudaEventElapsedTime(&t, b->pev[k][i], b->pev[k][i + 1]));
+      acc += t;
+    }
+    ms[k] = acc;
+    launches[k] = (int64_t)(b->pev_used[k] / 2);
+    b->pev_used[k] = 0;
+  }
+  return PPLBM_OK;
+}
+
 pplbm_status pplbm_batch_barrier_selftest(pplbm_batch* b, uint32_t spin_limit) {
   if (!b || spin_limit < 1) return PPLBM_ERR_ARG;
   if (b->sticky) return b->sticky;
@@ -949,6 +988,8 @@ void pplbm_batch_destroy(pplbm_batch* b) {
   if (!b) return;
   destroy_graphs(b);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k)
+    for (cudaEvent_t e : b->pev[k]) cudaEventDestroy(e);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   if (b->dev_block) cudaFree(b->dev_block);
   delete b;

@@ -21,8 +21,10 @@ struct pplbm_ctx {
   double* fB;  // next f(t+1); scratch between steps (host staging)
   double* psi;
   double* mom;
+  double* snap;     // density at the previous pplbm_guard call (workspace plane)
+  bool snap_valid;  // snap holds a density of this state's history
   cudaStream_t stream;
-  void* dev_block;  // owned: error word + guard partials + guard output
+  void* dev_block;  // owned: error word + guard partials + guard output (4 values)
   int* d_err;
   double* d_partials;
   double* d_guard;

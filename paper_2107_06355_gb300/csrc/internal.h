@@ -62,8 +62,12 @@ void launch_collide(const StepArgs& a, void* stream);
 void launch_fields(const StepArgs& a, double* rho, double* ux, double* uy, double* psi_out, void* stream);
 void launch_init_eq(const StepArgs& a, double* f, const double* rho0, const double* ux0, const double* uy0,
                     void* stream);
-// deterministic guard reduction over f: partials has room for guard_blocks()*3 doubles; out gets 3
+// Guard of the state a.f_in: a density pass (psi and the moment planes), then a
+// deterministic reduction of the guard terms (step_device.cuh, guard_node) into
+// out[kGuardQ]: mass, max |u|, bad-node count, residual against the density in snap
+// (-1 unless snap_valid); snap is refreshed. partials has room for
+// guard_blocks() * kGuardQ doubles.
 int guard_blocks();
-void launch_guard(const StepArgs& a, const double* f, double* partials, double* out, void* stream);
+void launch_guard(const StepArgs& a, double* snap, int snap_valid, double* partials, double* out, void* stream);
 
 }  // namespace pplbm

@@ -10,7 +10,9 @@
 // The array is file-scope `static __device__`, so every GPU that loads the library
 // holds it (5.2 MB) until the process exits. Host code cannot use its name as a
 // device address; the address is taken once per device with cudaGetSymbolAddress
-// on the first call made while that device is current.
+// on the first call made while that device is current, and kept for the life of
+// the process (a cudaDeviceReset() ends the context that address belongs to, so
+// the entry point must not be called after one).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -34,6 +36,7 @@ std::atomic<double*> g_scratch_addr[kMaxDevices];
 
 const char* kMsgTooLarge = "pplbm_step_noalloc: nx*ny exceeds the static scratch limit of 65536 nodes";
 const char* kMsgArgs = "pplbm_step_noalloc: invalid lattice, relaxation set, EOS block or buffer";
+const char* kMsgOverlap = "pplbm_step_noalloc: f_in and f_out overlap (they must be distinct 9*nx*ny buffers)";
 const char* kMsgSymbol = "pplbm_step_noalloc: cudaGetSymbolAddress of the static scratch failed";
 const char* kMsgCuda = "pplbm_step_noalloc: a CUDA call failed";
 const char* kMsgDiverged = "pplbm_step_noalloc: non-finite or non-positive density, or psi^2 <= 0";
@@ -53,8 +56,8 @@ extern "C" pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const p
                                            void* stream, const char** message) {
   if (message) *message = "";
   const int kind = collision_kind(relax);
-  if (!lattice || !eos || !f_in || !f_out || f_in == f_out || kind < 0 || lattice->nx < 1 || lattice->ny < 1 ||
-      lattice->reserved != 0 || !(eos->G < 0.0) || (eos->mode != PPLBM_EOS_CS && eos->mode != PPLBM_EOS_SMOOTH))
+  if (!lattice || !eos || !f_in || !f_out || kind < 0 || lattice->nx < 1 || lattice->ny < 1 ||
+      lattice->reserved != 0 || !(eos->G < 0.0) || eos->mode < PPLBM_EOS_CS || eos->mode > PPLBM_EOS_SMOOTH_MOD)
     return noalloc_fail(message, PPLBM_ERR_ARG, kMsgArgs);
   const uint32_t bc = lattice->bc, walls_bits = bc & (PPLBM_BC_WALL_BOTTOM | PPLBM_BC_WALL_TOP);
   const bool per_y = (bc & PPLBM_BC_PERIODIC_Y) != 0;
@@ -63,6 +66,9 @@ extern "C" pplbm_status pplbm_step_noalloc(const pplbm_lattice* lattice, const p
     return noalloc_fail(message, PPLBM_ERR_ARG, kMsgArgs);
   const int64_t n = (int64_t)lattice->nx * lattice->ny;
   if (n > kNoAllocMaxNodes) return noalloc_fail(message, PPLBM_ERR_ARG, kMsgTooLarge);
+  // f_in and f_out are two separate buffers, as in the context path: reject any overlap
+  const uintptr_t in0 = (uintptr_t)f_in, out0 = (uintptr_t)f_out, bytes = (uintptr_t)(9 * n) * sizeof(double);
+  if (in0 < out0 + bytes && out0 < in0 + bytes) return noalloc_fail(message, PPLBM_ERR_ARG, kMsgOverlap);
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)

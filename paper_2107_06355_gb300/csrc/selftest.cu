@@ -44,3 +44,61 @@ extern "C" pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed
   if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   return PPLBM_OK;
 }
+
+// FP64 issue-rate probe: every thread runs kChains independent fused multiply-add
+// chains (x <- x * b + c, |b| < 1 keeps them bounded), so the FP64 pipe is the only
+// limit; the sum of the chains goes to `sink` so that none of the work is dead.
+namespace pplbm {
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kPeakThreads = 256;
+
+__global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(long long iters, double b, double c, double* sink) {
+  double x[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += x[k];
+  if (s == 12345.678) sink[0] = s;  // never true for these chains; keeps them live
+}
+
+}  // namespace
+}  // namespace pplbm
+
+extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, long long iters, double* sink, double* out,
+                                        void* stream) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out) return PPLBM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PPLBM_ERR_CUDA;
+  const int blocks = sms * blocks_per_sm;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PPLBM_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PPLBM_ERR_CUDA;
+  }
+  pplbm_status st = PPLBM_OK;
+  float ms = 0.f;
+  cudaEventRecord(e0, s);
+  pplbm::k_fp64_peak<<<blocks, pplbm::kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink);
+  cudaEventRecord(e1, s);
+  if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f))
+    st = PPLBM_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PPLBM_OK) return st;
+  const double instr = (double)blocks * pplbm::kPeakThreads * (double)iters * pplbm::kChains;
+  out[0] = instr / (ms * 1e-3);  // FP64 FMA instructions (one per thread) per second
+  out[1] = ms;
+  out[2] = (double)blocks;
+  return PPLBM_OK;
+}

@@ -338,4 +338,67 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   }
 }
 
+// ---- per-M-step guard (Sec. III.A convergence check, mass, stability) --------------
+
+constexpr int kGuardQ = 4;  // mass, max |u|, bad-node count, sum |rho - rho'|
+
+// psi at (x + dx, y + dy) for 0 <= x < nx, 0 <= y < ny, |dx|, |dy| <= 1
+__device__ __forceinline__ double psi_near(const StepArgs& a, int x, int y, int dx, int dy) {
+  const int gx = wrap_index(x + dx, a.nx);
+  int gy = y + dy;
+  if (a.walls) {
+    if (gy < 0) return a.psi_ghost_bottom;
+    if (gy >= a.ny) return a.psi_ghost_top;
+  } else {
+    gy = wrap_index(gy, a.ny);
+  }
+  return a.psi[(int64_t)gy * a.nx + gx];
+}
+
+// Guard terms of node i, read from the psi and moment planes a density pass has just
+// written for the current state: adds rho to v[0], raises v[1] to |u| with
+// u = (j + F/2)/rho the fluid velocity of Eq. Momentum (F of Eq. ShanChenForce, wall
+// ghosts as in the collision pass), and, when snap_valid, adds |rho - rho'| to v[3]
+// with rho' = snap[i] the density of the previous guard call (the numerator of the
+// Sec. III.A criterion). A non-finite or non-positive density adds 1 to v[2] and
+// nothing else. Refreshes snap[i] = rho. IEEE division and sqrt: not on the hot path.
+__device__ __forceinline__ void guard_node(const StepArgs& a, int64_t i, double* snap, bool snap_valid,
+                                           double v[kGuardQ]) {
+  const int64_t n = a.n;
+  const double rho = a.mom[i];
+  if (!(rho > 0.0 && rho < 1e300)) {
+    v[2] += 1.0;
+  } else {
+    const int y = (int)(i / a.nx), x = (int)(i - (int64_t)y * a.nx);
+    const double pE = psi_near(a, x, y, 1, 0), pW = psi_near(a, x, y, -1, 0);
+    const double pN = psi_near(a, x, y, 0, 1), pS = psi_near(a, x, y, 0, -1);
+    const double d1 = psi_near(a, x, y, 1, 1) - psi_near(a, x, y, -1, -1);
+    const double d2 = psi_near(a, x, y, 1, -1) - psi_near(a, x, y, -1, 1);
+    const double gx = 4.0 * (pE - pW) + (d1 + d2), gy = 4.0 * (pN - pS) + (d1 - d2);
+    const double cH = a.half_force * a.psi[i];
+    const double ux = (a.mom[n + i] + cH * gx) / rho, uy = (a.mom[2 * n + i] + cH * gy) / rho;
+    v[0] += rho;
+    v[1] = fmax(v[1], sqrt(ux * ux + uy * uy));
+    if (snap_valid) v[3] += fabs(rho - snap[i]);
+  }
+  snap[i] = rho;
+}
+
+// Fixed-order tree reduction of the guard terms over a block of `nthreads` (a power
+// of two); s[q][0] holds the block's result.
+template <int kNThreads>
+__device__ __forceinline__ void guard_block_reduce(const double v[kGuardQ], double (*s)[kNThreads]) {
+  for (int q = 0; q < kGuardQ; ++q) s[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = kNThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + w];
+      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
+      s[2][threadIdx.x] += s[2][threadIdx.x + w];
+      s[3][threadIdx.x] += s[3][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace pplbm

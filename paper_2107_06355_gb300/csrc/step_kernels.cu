@@ -64,74 +64,38 @@ __global__ void k_init_eq(int64_t n, double* f, const double* rho0, const double
   }
 }
 
-// guard: per-block partial (mass, max |j|/rho, bad count), then one block reduces
+// guard: a density pass over the current state, then per-block partials of the
+// guard terms (guard_node) over a fixed grid-stride partition, then one block
+// reduces them in a fixed order: deterministic
 constexpr int kGuardBlocks = 304;
 constexpr int kGuardThreads = 256;
 
-__global__ void __launch_bounds__(kGuardThreads) k_guard_partial(const double* f, int64_t n, double* partials) {
-  double mass = 0.0, umax = 0.0, bad = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)kGuardThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kGuardThreads) {
-    double rho = 0.0, jx = 0.0, jy = 0.0;
-    const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const double v = f[k * n + i];
-      rho += v;
-      jx += cx[k] * v;
-      jy += cy[k] * v;
-    }
-    if (!(rho > 0.0 && rho < 1e300)) {
-      bad += 1.0;
-    } else {
-      mass += rho;
-      umax = fmax(umax, sqrt(jx * jx + jy * jy) / rho);
-    }
-  }
-  __shared__ double s[3][kGuardThreads];
-  s[0][threadIdx.x] = mass;
-  s[1][threadIdx.x] = umax;
-  s[2][threadIdx.x] = bad;
-  __syncthreads();
-  for (int w = kGuardThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + w];
-      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
-      s[2][threadIdx.x] += s[2][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x + 0] = s[0][0];
-    partials[3 * blockIdx.x + 1] = s[1][0];
-    partials[3 * blockIdx.x + 2] = s[2][0];
-  }
+__global__ void __launch_bounds__(kGuardThreads) k_guard_partial(const StepArgs a, double* snap, int snap_valid,
+                                                                 double* partials) {
+  __shared__ double s[kGuardQ][kGuardThreads];
+  double v[kGuardQ] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kGuardThreads + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kGuardThreads)
+    guard_node(a, i, snap, snap_valid != 0, v);
+  guard_block_reduce<kGuardThreads>(v, s);
+  if (threadIdx.x < kGuardQ) partials[kGuardQ * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
 }
 
-__global__ void __launch_bounds__(kGuardThreads) k_guard_final(const double* partials, int nblocks, double* out) {
-  __shared__ double s[3][kGuardThreads];
-  double a = 0.0, b = 0.0, c = 0.0;
+__global__ void __launch_bounds__(kGuardThreads) k_guard_final(const double* partials, int nblocks, int snap_valid,
+                                                               double* out) {
+  __shared__ double s[kGuardQ][kGuardThreads];
+  double v[kGuardQ] = {0.0, 0.0, 0.0, 0.0};
   for (int k = threadIdx.x; k < nblocks; k += kGuardThreads) {
-    a += partials[3 * k];
-    b = fmax(b, partials[3 * k + 1]);
-    c += partials[3 * k + 2];
+    v[0] += partials[kGuardQ * k];
+    v[1] = fmax(v[1], partials[kGuardQ * k + 1]);
+    v[2] += partials[kGuardQ * k + 2];
+    v[3] += partials[kGuardQ * k + 3];
   }
-  s[0][threadIdx.x] = a;
-  s[1][threadIdx.x] = b;
-  s[2][threadIdx.x] = c;
-  __syncthreads();
-  for (int w = kGuardThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + w];
-      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
-      s[2][threadIdx.x] += s[2][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
+  guard_block_reduce<kGuardThreads>(v, s);
   if (threadIdx.x == 0) {
     out[0] = s[0][0];
     out[1] = s[1][0];
     out[2] = s[2][0];
+    out[3] = snap_valid ? s[3][0] / s[0][0] : -1.0;
   }
 }
 
@@ -185,10 +149,11 @@ void launch_init_eq(const StepArgs& a, double* f, const double* rho0, const doub
 
 int guard_blocks() { return kGuardBlocks; }
 
-void launch_guard(const StepArgs& a, const double* f, double* partials, double* out, void* stream) {
+void launch_guard(const StepArgs& a, double* snap, int snap_valid, double* partials, double* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  k_guard_partial<<<kGuardBlocks, kGuardThreads, 0, s>>>(f, a.n, partials);
-  k_guard_final<<<1, kGuardThreads, 0, s>>>(partials, kGuardBlocks, out);
+  launch_rho_psi(a, stream);
+  k_guard_partial<<<kGuardBlocks, kGuardThreads, 0, s>>>(a, snap, snap_valid, partials);
+  k_guard_final<<<1, kGuardThreads, 0, s>>>(partials, kGuardBlocks, snap_valid, out);
 }
 
 }  // namespace pplbm

@@ -157,10 +157,12 @@ class Simulation:
         self.torch.cuda.current_stream(self.device).synchronize()
 
     def guard(self):
-        """(mass, max |j|/rho, bad-node count); synchronises."""
-        out = (C.c_double * 3)()
+        """(mass, max |u| with u = (j + F/2)/rho, bad-node count, residual
+        sum |rho - rho'| / sum rho against the previous guard call, -1 if none);
+        synchronises."""
+        out = (C.c_double * 4)()
         self._check(L.lib().pplbm_guard(self.ctx, out))
-        return out[0], out[1], int(out[2])
+        return out[0], out[1], int(out[2]), out[3]
 
     def enable_kernel_timing(self, capacity=4096):
         """Record per-launch device times of the two step kernels (capacity 0 disables)."""

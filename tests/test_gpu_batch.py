@@ -274,3 +274,65 @@ def test_one_call_batch_init_equals_create_then_init():
         assert torch.equal(f, ref.get_f(k))
     L.lib().pplbm_batch_destroy(b)
     ref.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pass_timing_counts_launches_and_keeps_results(mode):
+    """pplbm_batch_enable_pass_timing brackets each pass with CUDA events; the steps it
+    issues are the same arithmetic (bitwise) and every launch is counted."""
+    b, sims = _build({})
+    for s in sims:
+        s.close()
+    ref, _ = _build({})
+    b.set_plan(mode, 0)
+    ref.set_plan(mode, 0)
+    b.enable_pass_timing(3)
+    b.step(7)
+    (m0, m1), (n0, n1) = b.pass_times()
+    assert (n0, n1) == (7, 7) and m0 > 0 and m1 > 0
+    b.step(2)
+    assert b.pass_times()[1] == (2, 2)
+    with pytest.raises(P.PPLBMError):
+        b.set_plan(2, 0)   # the persistent plan has a single launch
+    b.enable_pass_timing(0)
+    ref.step(9)
+    for k in range(b.n):
+        assert torch.equal(b.get_f(k), ref.get_f(k))
+    b.close()
+    ref.close()
+
+
+def test_sweep_64_lattices_full_length_stable():
+    """The 64-lattice sweep the benchmark times (seed 210706355, T_r 0.35..0.95, Smooth
+    C-S a_l = 0.363, a_v = 2, alpha = 0.775, tau = 1, Li forcing), run for its full
+    20,000 steps: no non-physical node, mass conserved to round-off, speeds bounded, and
+    the small instances still equal to the oracle's state stepped alongside for the
+    first 200 steps (the large ones are covered by bitwise equality with the single-
+    lattice path, itself checked against the oracle)."""
+    specs = I.batch_specs()
+    eos = [P.EOSParams(P.EOS_SMOOTH, s["Tr"], 0.363, 2.0, 0.775) for s in specs]
+    b = P.Batch([(s["nx"], s["ny"], BC_PER) for s in specs], eos, [P.Relax() for _ in specs])
+    inits = []
+    for k, s in enumerate(specs):
+        d = b.derived(k)
+        rho = (I.planar(s["nx"], s["ny"], d["rho_v"], d["rho_l"], W=8.0) if s["kind"] == "planar"
+               else I.droplet(s["nx"], s["ny"], s["R"], d["rho_v"], d["rho_l"], W=8.0))
+        b.init_equilibrium(k, rho)
+        inits.append(rho)
+    b.autotune(trial_steps=4)
+    g0 = b.guard()
+    small = [k for k, s in enumerate(specs) if s["nx"] * s["ny"] <= 1200][:3]
+    oracles = {}
+    for k in small:
+        s = specs[k]
+        olat, _ = make_pair(s["nx"], s["ny"], BC_PER, (E.MODE_SMOOTH, s["Tr"], 0.363, 2.0, 0.775), {})
+        oracles[k] = (olat, olat.step(olat.init_equilibrium(inits[k]), 200))
+    b.step(200)
+    for k, (olat, f) in oracles.items():
+        assert normwise(b.get_f(k).cpu().numpy(), f) < 1e-10, k
+    b.step(20000 - 200)
+    g = b.guard()
+    assert (g[:, 2] == 0).all()
+    np.testing.assert_allclose(g[:, 0], g0[:, 0], rtol=1e-10)
+    assert (g[:, 1] < 0.3).all()
+    b.close()

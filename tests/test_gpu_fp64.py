@@ -20,3 +20,24 @@ def test_fast_rcp_and_sqrt_within_a_few_ulp():
     ulp = 2.0**-52
     assert err_rcp <= 2 * ulp, err_rcp
     assert err_sqrt <= 2 * ulp, err_sqrt
+
+
+def test_fp64_peak_probe_reports_a_rate_consistent_with_its_own_timing():
+    """pplbm_fp64_peak (the denominator of the step's FP64 roofline): the rate equals
+    the instructions it issues over the launch time it reports, and stays within the
+    nominal issue rate of the part (2 FP64 FMA per clock per SM at the maximum clock)
+    with some margin for clock reporting."""
+    from paper_2107_06355_gb300 import _lib as L
+
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = (C.c_double * 3)()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.lib().pplbm_fp64_peak(4, 20000, C.c_void_p(sink.data_ptr()), out, stream) == 0
+    rate, ms, blocks = out[0], out[1], int(out[2])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert blocks == 4 * sms
+    assert rate == pytest.approx(blocks * 256 * 20000 * 8 / (ms * 1e-3), rel=1e-12)
+    assert 0.05e12 < rate < 1.2 * 2 * sms * 2.1e9
+    assert sink.item() == 0.0
+    for bad in ((0, 10), (65, 10), (4, 0)):
+        assert L.lib().pplbm_fp64_peak(bad[0], bad[1], C.c_void_p(sink.data_ptr()), out, stream) == L.PPLBM_ERR_ARG

@@ -122,9 +122,9 @@ def test_mass_conservation_and_guard():
     olat, sim = make_pair(96, 40, BC_WALLS, SMOOTH05, {"kind": 1, "tau_l": 0.7, "visc_ratio": 2.0})
     rho, ux, uy = I.impact(96, 40, 8, 6, olat.eos.rho_v, olat.eos.rho_l, 0.03, W=7.0)
     sim.init_equilibrium(rho, ux, uy)
-    m0, _, bad0 = sim.guard()
+    m0, _, bad0, _ = sim.guard()
     sim.step(300)
-    m1, umax, bad1 = sim.guard()
+    m1, umax, bad1, _ = sim.guard()
     assert bad0 == 0 and bad1 == 0
     assert abs(m1 - m0) < 1e-12 * m0
     assert abs(m0 - olat.init_equilibrium(rho, ux, uy).sum()) < 1e-12 * m0
@@ -251,7 +251,7 @@ def test_impact_2048x1024_100000_steps_stable_and_conserves_mass():
     m0 = sim.guard()[0]
     for _ in range(10):
         sim.step(10000)
-        m, _, bad = sim.guard()
+        m, _, bad, _ = sim.guard()
         assert bad == 0
         assert abs(m - m0) < 1e-10 * m0
     rho = sim.fields()[0].cpu().numpy()

@@ -94,9 +94,9 @@ def test_workspace_bytes_and_lattice_validation(lib):
     full = P.Relax(tau_e=0.8).c()
     lat = L.pplbm_lattice(256, 4, L.BC_PERIODIC, 0)
     n = 256 * 4
-    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(relax)) == 8 * n * (19 + 3)
-    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(two)) == 8 * n * (19 + 5)
-    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(full)) == 8 * n * (19 + 9)
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(relax)) == 8 * n * (20 + 3)
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(two)) == 8 * n * (20 + 5)
+    assert lib.pplbm_workspace_bytes(C.byref(lat), C.byref(full)) == 8 * n * (20 + 9)
     for bad in [L.pplbm_lattice(0, 4, L.BC_PERIODIC, 0), L.pplbm_lattice(4, 0, L.BC_PERIODIC, 0),
                 L.pplbm_lattice(4, 4, L.BC_PERIODIC_Y, 0),                       # x not periodic
                 L.pplbm_lattice(4, 4, L.BC_PERIODIC_X | L.BC_WALL_BOTTOM, 0),    # one wall only
@@ -238,3 +238,33 @@ def test_surface_tension_kappa_is_validated_at_set_up(lib):
         assert (lib.pplbm_workspace_bytes(C.byref(lat), C.byref(r)) > 0) == ok, (tau_l, vr)
     assert C.sizeof(L.pplbm_relax) == 8 + 8 * 9 + 8 + 8
     assert L.pplbm_relax.kappa.offset == C.sizeof(L.pplbm_relax) - 8
+
+
+def test_noalloc_step_rejects_overlapping_buffers_before_any_cuda_call(lib):
+    """pplbm_step_noalloc checks its arguments on the host first: overlapping f_in /
+    f_out ranges (an offset view into one buffer) are refused with their own message,
+    before the device is touched (no GPU here; the pointers are never dereferenced)."""
+    eos = L.pplbm_eos_derived()
+    p = P.EOSParams().c()
+    assert lib.pplbm_eos_setup(C.byref(p), -1.0, C.byref(eos)) == L.PPLBM_OK
+    lat = L.pplbm_lattice(16, 8, L.BC_PERIODIC, 0)
+    relax = P.Relax().c()
+    n = 16 * 8
+    base = 1 << 40
+    msg = C.c_char_p()
+    for off in (8, 8 * n, 8 * (9 * n - 1)):   # partial overlaps, in bytes
+        st = lib.pplbm_step_noalloc(C.byref(lat), C.byref(eos), C.byref(relax), C.c_void_p(base),
+                                    C.c_void_p(base + off), None, C.byref(msg))
+        assert st == L.PPLBM_ERR_ARG
+        assert b"overlap" in msg.value
+        st = lib.pplbm_step_noalloc(C.byref(lat), C.byref(eos), C.byref(relax), C.c_void_p(base + off),
+                                    C.c_void_p(base), None, C.byref(msg))
+        assert st == L.PPLBM_ERR_ARG and b"overlap" in msg.value
+    st = lib.pplbm_step_noalloc(C.byref(lat), C.byref(eos), C.byref(relax), C.c_void_p(base), C.c_void_p(base),
+                                None, C.byref(msg))
+    assert st == L.PPLBM_ERR_ARG and b"overlap" in msg.value
+    # too large a lattice is refused by its own message, also before any CUDA call
+    big = L.pplbm_lattice(257, 256, L.BC_PERIODIC, 0)
+    st = lib.pplbm_step_noalloc(C.byref(big), C.byref(eos), C.byref(relax), C.c_void_p(base),
+                                C.c_void_p(base + 8 * 9 * 257 * 256), None, C.byref(msg))
+    assert st == L.PPLBM_ERR_ARG and b"65536" in msg.value

@@ -2,7 +2,8 @@
 (a host framework owning all device memory, or a stream that must not be
 synchronised by cudaMalloc/cudaFree). Its psi and moment planes live in a static
 device array, so it must give the same distributions as the context-based step
-(pplbm_create / pplbm_step), call after call. This file is collected last so that
+(pplbm_create / pplbm_step), call after call, for every EOS and relaxation kind
+(and the oracle's). This file is collected last so that
 a run stopping at the first failure has already run every other test."""
 import ctypes as C
 
@@ -28,15 +29,25 @@ def _noalloc(L, sim, f_in, f_out):
     return st, (msg.value or b"").decode()
 
 
-@pytest.mark.parametrize("relax", [{}, {"kind": 1, "tau_l": 0.6, "visc_ratio": 3.0},
-                                   {"tau_e": 0.8, "tau_zeta": 1.1, "tau_q": 1.2, "tau_nu": 0.7}],
-                         ids=["unit", "two_phase", "full_mrt"])
-def test_noalloc_step_matches_context_step_twice(relax):
+CASES = {
+    "unit": ((E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), {}, True),
+    "two_phase": ((E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), {"kind": 1, "tau_l": 0.6, "visc_ratio": 3.0}, True),
+    "full_mrt": ((E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), {"tau_e": 0.8, "tau_zeta": 1.1, "tau_q": 1.2, "tau_nu": 0.7},
+                 True),
+    # the two EOS built for Guo forcing (Sec. IV.C, Eqs. PengEOS, PengTheta)
+    "peng06": ((E.MODE_PENG, 0.6, 0.387, 0.387, 0.0, 0.45), {}, False),
+    "modsmooth06": ((E.MODE_SMOOTH_MOD, 0.6, 0.387, 2.0, 0.446), {}, False),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES), ids=list(CASES))
+def test_noalloc_step_matches_context_step_twice(case):
     from paper_2107_06355_gb300 import _lib as L
 
-    olat, sim = make_pair(70, 27, BC_WALLS, (E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), relax)
+    eos_case, relax, li = CASES[case]
+    olat, sim = make_pair(70, 27, BC_WALLS, eos_case, relax, forcing_li=li)
     e = olat.eos
-    rho, ux, uy = I.impact(70, 27, 5, 5, e.rho_v, e.rho_l, 0.03, W=5.0)
+    rho, ux, uy = I.impact(70, 27, 5, 5, e.rho_v, e.rho_l, 0.01 if not li else 0.03, W=8.0 if not li else 5.0)
     sim.init_equilibrium(rho, ux, uy)
     f0 = sim.get_f()
     a = torch.empty_like(f0)
@@ -50,6 +61,9 @@ def test_noalloc_step_matches_context_step_twice(relax):
     ref = sim.get_f()
     torch.cuda.synchronize()
     assert normwise(b.cpu().numpy(), ref.cpu().numpy()) < 1e-12
+    # and the oracle's two steps from the same state
+    f_or = olat.step(olat.init_equilibrium(rho, ux, uy), 2)
+    assert normwise(b.cpu().numpy(), f_or) < 3e-12
     # one step from f0 also matches
     sim.set_f(f0)
     sim.step(1)
