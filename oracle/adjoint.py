@@ -11,10 +11,14 @@ a, T of the vapour and liquid branches with the liquid shift Delta P), which are
 inputs here; their dependence on a parameter (alpha, a_v or a_l) is taken from the
 numpy oracle by central differences with Richardson extrapolation.
 
-Only the unit-relaxation-time set (Lambda = I, Sec. III.A) is restated, with the
-optional surface-tension source of ``oracle/lbm.py`` (``Relax.kappa``; the technique
-the paper's Sec. V names, Li & Luo 2013): with Lambda = I its moment vector is
-C = [0, 1.5 tr Q, -1.5 tr Q, 0, 0, 0, 0, -(Q_xx - Q_yy), -Q_xy].
+Two relaxation sets are restated: unit relaxation times (Lambda = I, Sec. III.A)
+and the two-phase set of the dynamic runs (Sec. IV): Lambda = diag(1, ..., 1,
+1/tau, 1/tau) with tau(rho) linear between tau_v at rho_v and tau_l at rho_l
+(Eq. RelaxationTime), so that autograd also differentiates through tau(rho). Both
+carry the optional surface-tension source of ``oracle/lbm.py`` (``Relax.kappa``;
+the technique the paper's Sec. V names, Li & Luo 2013), whose moment vector is
+C = [0, 1.5 l_e tr Q, -1.5 l_zeta tr Q, 0, 0, 0, 0, -l_nu (Q_xx - Q_yy), -l_nu Q_xy]
+with l the diagonal of Lambda.
 """
 from __future__ import annotations
 
@@ -88,10 +92,29 @@ def _roll(a, dy, dx):
     return torch.roll(a, shifts=(dy, dx), dims=(-2, -1))
 
 
-def _surface_tension_source(qxx, qyy, qxy, z):
-    """The surface-tension source's moment vector with Lambda = I (Li & Luo 2013):
-    [0, 1.5 tr Q, -1.5 tr Q, 0, 0, 0, 0, -(Q_xx - Q_yy), -Q_xy]; z a zero plane."""
-    return torch.stack([z, 1.5 * (qxx + qyy), -1.5 * (qxx + qyy), z, z, z, z, -(qxx - qyy), -qxy])
+def _surface_tension_source(qxx, qyy, qxy, z, lam):
+    """The surface-tension source's moment vector (Li & Luo 2013):
+    [0, 1.5 l_1 tr Q, -1.5 l_2 tr Q, 0, 0, 0, 0, -l_7 (Q_xx - Q_yy), -l_8 Q_xy], l = lam the
+    diagonal of Lambda (l_1 = l_2 = 1 in both restated sets); z a zero plane."""
+    return torch.stack([z, 1.5 * lam[1] * (qxx + qyy), -1.5 * lam[2] * (qxx + qyy), z, z, z, z,
+                        -lam[7] * (qxx - qyy), -lam[8] * qxy])
+
+
+def relaxation_diagonal(lat: L.Lattice, rho):
+    """Diagonal of Lambda per node, shape (9,) + rho.shape: all ones for unit relaxation
+    times (Sec. III.A); for the two-phase set (Sec. IV) rows 7, 8 are 1/tau(rho) with
+    tau(rho) = tau_l (rho - rho_v)/(rho_l - rho_v) + tau_v (rho - rho_l)/(rho_v - rho_l),
+    tau_v = 1/2 + v_r (tau_l - 1/2) (Eq. RelaxationTime). Other sets are not restated."""
+    r = lat.relax
+    one = torch.ones_like(rho)
+    if r.kind == L.RELAX_TWO_PHASE:
+        e = lat.eos
+        tau_v = 0.5 + r.visc_ratio * (r.tau_l - 0.5)
+        tau = r.tau_l * (rho - e.rho_v) / (e.rho_l - e.rho_v) + tau_v * (rho - e.rho_l) / (e.rho_v - e.rho_l)
+        return torch.stack([one] * 7 + [1.0 / tau, 1.0 / tau])
+    if r.kind == L.RELAX_MRT and all(t == 1.0 for t in (r.tau_rho, r.tau_e, r.tau_zeta, r.tau_j, r.tau_q, r.tau_nu)):
+        return torch.stack([one] * 9)
+    raise ValueError("the torch restatement covers unit relaxation times and the two-phase set only")
 
 
 def step(f, lat: L.Lattice, c):
@@ -154,10 +177,11 @@ def step(f, lat: L.Lattice, c):
     S = torch.stack([torch.zeros_like(rho), 6.0 * uF + 12.0 * sigma * F2 / (psi**2 * 0.5),
                      -6.0 * uF - 12.0 * sigma * F2 / (psi**2 * 0.5), Fx, -Fx, Fy, -Fy,
                      2.0 * (ux * Fx - uy * Fy), ux * Fy + uy * Fx])
-    mstar = m - (m - meq) + 0.5 * S          # Lambda = I
+    lam = relaxation_diagonal(lat, rho)
+    mstar = m - lam * (m - meq) + (1.0 - lam / 2.0) * S
     if with_st:
         z = torch.zeros_like(rho)
-        mstar = mstar + _surface_tension_source(qxx, qyy, qxy, z)
+        mstar = mstar + _surface_tension_source(qxx, qyy, qxy, z, lam)
     fstar = torch.einsum("ik,kyx->iyx", _MINV, mstar)
     out = []
     for i in range(9):

@@ -150,6 +150,14 @@ def maxwell(a, b, R, T):
 # ---------------------------------------------------------------------------
 # Shaped EOS (Sec. III.D) and plain C-S as one piecewise object
 # ---------------------------------------------------------------------------
+def _radicand(d, asq):
+    """1 - d^2 / a^2 of the ellipse constants (Sec. III.D). With r = h / (p' d) the
+    ratio of the ellipse's rise h to the tangent's, a^2 = d^2 (1 - r)^2 / (1 - 2 r), so
+    the radicand is r^2 / (1 - r)^2 >= 0; near r = 0 (the lower end of the p_max
+    bracket) the subtraction can round to -1 ulp, which is clamped to 0."""
+    return max(0.0, 1.0 - d**2 / asq)
+
+
 @dataclass
 class EOS:
     """A coexistence EOS at one reduced temperature.
@@ -211,14 +219,14 @@ class EOS:
         d = self.rho_l - self.rho_min
         k = (self.p_sat - self.p_min) * d / self.dpdrho_l - d**2
         self.a3sq = -(k**2) / (2.0 * k + d**2)
-        self.b3 = (self.p_sat - self.p_min) / (1.0 - math.sqrt(1.0 - d**2 / self.a3sq))
+        self.b3 = (self.p_sat - self.p_min) / (1.0 - math.sqrt(_radicand(d, self.a3sq)))
 
     def _region1(self, p_max):
         d = self.rho_max - self.rho_v
         k = (p_max - self.p_sat) * d / self.dpdrho_v - d**2
         self.p_max = p_max
         self.a1sq = -(k**2) / (2.0 * k + d**2)
-        self.b1 = (p_max - self.p_sat) / (1.0 - math.sqrt(1.0 - d**2 / self.a1sq))
+        self.b1 = (p_max - self.p_sat) / (1.0 - math.sqrt(_radicand(d, self.a1sq)))
 
     def _solve_p_max(self):
         """p_max such that the shaped EOS satisfies Eq. MaxwellRule at rho_v, rho_l."""

@@ -162,3 +162,83 @@ def test_gradient_wrt_kappa_matches_finite_differences(bc, kappa):
     fd = (Lnp(kappa + h) - Lnp(kappa - h)) / (2 * h)
     assert abs(fd) > 1e-8
     assert float(c["kappa"].grad) == pytest.approx(fd, rel=1e-6)
+
+
+# ---- the two-phase relaxation of the dynamic runs (Sec. IV, Eq. RelaxationTime) ----
+
+def lattice_two_phase(nx, ny, bc, alpha=CASE[4], kappa=0.0, tau_l=0.6, visc_ratio=3.0):
+    e = E.make_eos(CASE[0], CASE[1], CASE[2], CASE[3], alpha)
+    e.solve_eps(n=40000)
+    return L.Lattice(nx, ny, bc, e, L.Relax(kind=L.RELAX_TWO_PHASE, tau_l=tau_l, visc_ratio=visc_ratio,
+                                            sigma=e.sigma(), kappa=kappa))
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.6])
+@pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
+def test_two_phase_torch_step_equals_numpy_oracle(bc, kappa):
+    """The restatement with Lambda = diag(1, ..., 1, 1/tau(rho), 1/tau(rho)) equals the
+    numpy oracle's step (whose tau(rho) end points are pinned in test_oracle_lbm)."""
+    lat = lattice_two_phase(12, 10, bc, kappa=kappa)
+    f = initial(lat, 12, 10, bc)
+    c = A.constants_as_tensors(lat.eos, requires_grad=False)
+    g = torch.tensor(f)
+    for _ in range(4):
+        f = lat.step(f, 1)
+        g = A.step(g, lat, c)
+    assert np.max(np.abs(g.numpy() - f)) < 1e-14 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("bc", [PER, WALLS], ids=["periodic", "walls"])
+def test_two_phase_gradient_wrt_initial_field_matches_finite_differences(bc):
+    """Reverse mode through tau(rho) as well: the derivative of the droplet loss after 5
+    steps along a random direction equals central differences (h = 1e-6) of the numpy
+    oracle."""
+    nx, ny, steps = 10, 12, 5
+    lat = lattice_two_phase(nx, ny, bc)
+    e = lat.eos
+    f0 = initial(lat, nx, ny, bc)
+    c = A.constants_as_tensors(e, requires_grad=False)
+    x = torch.tensor(f0, requires_grad=True)
+    g = x
+    for _ in range(steps):
+        g = A.step(g, lat, c)
+    loss = A.droplet_loss(g.sum(0), e.rho_v, e.rho_l, 2.5)
+    loss.backward()
+    v = np.random.default_rng(4).standard_normal(f0.shape) * f0
+    h = 1e-6
+
+    def Lnp(f):
+        rho = lat.step(f, steps).sum(0)
+        return float(A.droplet_loss(torch.tensor(rho), e.rho_v, e.rho_l, 2.5))
+
+    fd = (Lnp(f0 + h * v) - Lnp(f0 - h * v)) / (2 * h)
+    ad = float((x.grad.numpy() * v).sum())
+    assert ad == pytest.approx(fd, rel=1e-6)
+
+
+def test_two_phase_gradient_wrt_alpha_matches_finite_differences():
+    """dL/dalpha through the constants with the two-phase relaxation, walls: autograd
+    of the restatement chained with constants_derivative against central differences
+    of the numpy oracle rebuilt at alpha +- h."""
+    nx, ny, steps = 12, 12, 6
+    alpha = CASE[4]
+    lat = lattice_two_phase(nx, ny, WALLS, alpha)
+    e = lat.eos
+    rho0, ux0, uy0 = I.impact(nx, ny, 3, 4, e.rho_v, e.rho_l, 0.01, W=6.0)
+    c = A.constants_as_tensors(e)
+    g = A.step(torch.tensor(lat.init_equilibrium(rho0, ux0, uy0)), lat, c)
+    for _ in range(steps - 1):
+        g = A.step(g, lat, c)
+    A.droplet_loss(g.sum(0), e.rho_v, e.rho_l, 3.0).backward()
+    dc = A.constants_derivative(*CASE[:4], alpha)
+    ad = sum(float(c[k].grad) * dc[k] for k in A.CONST_NAMES)
+    h = 1e-5
+
+    def Lnp(a):
+        la = lattice_two_phase(nx, ny, WALLS, a)
+        # the same initial field (the Maxwell densities do not depend on alpha)
+        rho = la.step(la.init_equilibrium(rho0, ux0, uy0), steps).sum(0)
+        return float(A.droplet_loss(torch.tensor(rho), e.rho_v, e.rho_l, 3.0))
+
+    fd = (Lnp(alpha + h) - Lnp(alpha - h)) / (2 * h)
+    assert ad == pytest.approx(fd, rel=1e-6)

@@ -261,8 +261,8 @@ def test_torch_restatement_surface_tension_row8_sign(monkeypatch):
 
     orig = A._surface_tension_source
 
-    def src(qxx, qyy, qxy, z):
-        c = orig(qxx, qyy, qxy, z)
+    def src(qxx, qyy, qxy, z, lam):
+        c = orig(qxx, qyy, qxy, z, lam)
         return c.index_copy(0, A.torch.tensor([8]), -c[8:9])
 
     monkeypatch.setattr(A, "_surface_tension_source", src)
@@ -298,3 +298,21 @@ def test_fd_two_phase_relaxation_times_swapped(monkeypatch):
     monkeypatch.setattr(F.FDSolver, "_tau_nu", tau_nu)
     assert some_pin_fails(lambda: TF.test_fd_two_phase_viscosity_shear_waves_decay_at_each_phase_rate("liquid"),
                           lambda: TF.test_fd_two_phase_viscosity_shear_waves_decay_at_each_phase_rate("vapour"))
+
+
+def test_torch_restatement_two_phase_rate_inverted(monkeypatch):
+    """The torch restatement relaxing rows 7, 8 with tau(rho) instead of 1/tau(rho)
+    (Eq. RelaxationTime misread): it no longer equals the numpy oracle's step."""
+    pytest.importorskip("torch")
+    from oracle import adjoint as A
+    import test_oracle_adjoint as TA
+
+    orig = A.relaxation_diagonal
+
+    def diag(lat, rho):
+        lam = orig(lat, rho)
+        return A.torch.cat([lam[:7], 1.0 / lam[7:]])
+
+    monkeypatch.setattr(A, "relaxation_diagonal", diag)
+    assert some_pin_fails(lambda: TA.test_two_phase_torch_step_equals_numpy_oracle(TA.PER, 0.0),
+                          lambda: TA.test_two_phase_torch_step_equals_numpy_oracle(TA.WALLS, 0.0))
