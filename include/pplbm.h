@@ -294,6 +294,18 @@ pplbm_status pplbm_backward_stored(pplbm_ctx* ctx, int64_t nsteps, const double*
  * clear the slots whose dc/dtheta is 0 (for alpha: the five C-S branch constants)
  * and skip their reductions. PPLBM_ERR_ARG for bits at or above PPLBM_NGRAD. */
 pplbm_status pplbm_adjoint_set_slots(pplbm_ctx* ctx, uint32_t mask);
+/* The chain rule to one parameter theta, behind the ABI. pplbm_adjoint_set_param
+ * chooses theta (which: 0 alpha, 1 a_vap, 2 a_liq, 3 kappa, as in
+ * pplbm_eos_constant_sensitivity), computes dc/dtheta at the context's own EOS
+ * parameters and relaxation set with step h (host only), keeps it in the context and
+ * sets the gradient slots to those with dc_k != 0 (as pplbm_adjoint_set_slots would);
+ * PPLBM_ERR_ARG for another `which` or h <= 0. After the adjoint calls have filled
+ * grad, pplbm_adjoint_param_gradient writes to the host out[0] = dL/dtheta =
+ * sum_k grad[k] dc_k/dtheta over the selected slots, summed in slot order; grad is
+ * PPLBM_NGRAD values in device or host memory (the call synchronises the stream).
+ * PPLBM_ERR_STATE if no parameter was chosen. */
+pplbm_status pplbm_adjoint_set_param(pplbm_ctx* ctx, int32_t which, double h);
+pplbm_status pplbm_adjoint_param_gradient(pplbm_ctx* ctx, const double* grad, double* out);
 /* rho0_bar = sum_i w_i lambda_0[i]: the gradient w.r.t. the initial density of
  * f^0 = f^eq(rho0, u = 0) (Sec. III.A). */
 pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* ctx, const double* lambda_0, double* rho0_bar);
@@ -302,8 +314,14 @@ pplbm_status pplbm_eos_grad_constants(const pplbm_eos_derived* eos, double c[PPL
 /* Host only: dc/dtheta of the PPLBM_NGRAD constants for theta = alpha (which = 0),
  * a_vap (1) or a_liq (2), including z through sigma(theta) when relax->sigma_auto,
  * by central differences of pplbm_eos_setup at steps h and h/2 combined by
- * Richardson extrapolation (error O(h^4)); for theta = kappa (3) exactly the unit
- * vector of its slot. PPLBM_ERR_ARG for another `which`. */
+ * Richardson extrapolation: D = (4 D(h/2) - D(h))/3. Error bound: the truncation
+ * term is O(h^4) (the set-up is smooth in these parameters at fixed T_r); a
+ * rounding or root-finding error delta in a constant adds at most 3 delta / h
+ * (8 delta/h from D(h/2), delta/h from D(h), over 3). With the set-up's roots and
+ * quadratures good to delta ~ 1e-15 |c| and the suggested h = 1e-4, the error is
+ * about 3e-11 |c| (the tests compare h and h/2, and the oracle's own derivative).
+ * For theta = kappa (3) exactly the unit vector of its slot. PPLBM_ERR_ARG for
+ * another `which` or h <= 0. */
 pplbm_status pplbm_eos_constant_sensitivity(const pplbm_eos_params* params, double G, const pplbm_relax* relax,
                                             int32_t which, double h, double dc[PPLBM_NGRAD]);
 

@@ -135,6 +135,8 @@ _SIGS = {
     "pplbm_batch_instance_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "pplbm_batch_guard": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "pplbm_adjoint_set_slots": (C.c_int, [_P, C.c_uint32]),
+    "pplbm_adjoint_set_param": (C.c_int, [_P, C.c_int32, C.c_double]),
+    "pplbm_adjoint_param_gradient": (C.c_int, [_P, _P, _D]),
     "pplbm_fd_set_two_phase_viscosity": (C.c_int, [_P, C.c_double, C.c_double]),
     "pplbm_fd_set_surface_tension": (C.c_int, [_P, C.c_double]),
     "pplbm_forward_stored": (C.c_int, [_P, C.c_int64, _P]),

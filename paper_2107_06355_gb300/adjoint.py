@@ -6,11 +6,12 @@ pplbm_forward_checkpointed (checkpoints every `interval` steps, ~sqrt(nsteps)),
 output rho^N. Backward: pplbm_backward_stored, or pplbm_backward_checkpointed
 (segment recomputation), then the hand-written adjoint kernels give dL/df^0 and
 dL/d(EOS constants); the initial-density gradient is
-sum_i w_i dL/df^0_i and the parameter gradient (alpha, a_vap or a_liq, chosen by
-RolloutSpec.param) chains the constants' gradients with their derivatives
-(pplbm_eos_constant_sensitivity); for kappa, the surface-tension control, it is
-the kappa slot itself. Argument marshalling only: every step runs in
-the library's kernels.
+sum_i w_i dL/df^0_i (pplbm_adjoint_initial_density) and the parameter gradient
+(alpha, a_vap, a_liq or kappa, chosen by RolloutSpec.param) is the library's
+chain rule: pplbm_adjoint_set_param takes dc/dtheta at the context's parameters
+and selects the slots theta moves, pplbm_adjoint_param_gradient forms
+sum_k grad[k] dc_k/dtheta. Argument marshalling only: every step, and every sum,
+runs in the library.
 """
 from __future__ import annotations
 
@@ -50,7 +51,10 @@ class RolloutSpec:
         return 32 * self.nx * self.ny * max(1, self.nsteps) <= self.memory_fraction * free
 
 
-def param_sensitivity(spec: RolloutSpec, value: float, h: float = 1e-4):
+SENS_STEP = 1e-4  # step of the central differences behind dc/dtheta (pplbm_eos_constant_sensitivity)
+
+
+def param_sensitivity(spec: RolloutSpec, value: float, h: float = SENS_STEP):
     """d(gradient constants)/d(spec.param) at spec.param = value, PPLBM_NGRAD values (host)."""
     dc = (C.c_double * L.NGRAD)()
     eos, relax = _with_param(spec, value)
@@ -61,7 +65,7 @@ def param_sensitivity(spec: RolloutSpec, value: float, h: float = 1e-4):
     return list(dc)
 
 
-def alpha_sensitivity(spec: RolloutSpec, alpha: float, h: float = 1e-4):
+def alpha_sensitivity(spec: RolloutSpec, alpha: float, h: float = SENS_STEP):
     """d(EOS constants)/d(alpha), PPLBM_NGRAD values (host)."""
     return param_sensitivity(replace(spec, param="alpha"), alpha, h)
 
@@ -130,18 +134,20 @@ def _make_function():
         def forward(ctx, rho0, theta, spec):
             sim, ckpt, rhoN = _rollout_forward(spec, rho0.detach(), float(theta))
             ctx.spec, ctx.sim, ctx.ckpt, ctx.theta = spec, sim, ckpt, float(theta)
+            ctx.theta_device = theta.device if isinstance(theta, torch.Tensor) else torch.device("cpu")
             return rhoN
 
         @staticmethod
         def backward(ctx, grad_rhoN):
             spec = ctx.spec
-            dc_list = param_sensitivity(spec, ctx.theta)
-            mask = sum(1 << k for k, v in enumerate(dc_list) if v != 0.0)  # slots theta moves
-            rho0_bar, grad, _ = _rollout_backward(spec, ctx.sim, ctx.ckpt, grad_rhoN.contiguous(), mask)
-            dc = torch.tensor(dc_list, dtype=torch.float64, device=grad.device)
-            gtheta = (grad * dc).sum()
-            ctx.sim.close()
-            return rho0_bar, gtheta.to(grad_rhoN.dtype), None
+            sim = ctx.sim
+            sim._check(L.lib().pplbm_adjoint_set_param(sim.ctx, L.SENS_PARAMS[spec.param], SENS_STEP))
+            rho0_bar, grad, _ = _rollout_backward(spec, sim, ctx.ckpt, grad_rhoN.contiguous())
+            out = (C.c_double * 1)()
+            sim._check(L.lib().pplbm_adjoint_param_gradient(sim.ctx, _ptr(grad), out))
+            sim.close()
+            gtheta = torch.tensor(out[0], dtype=grad_rhoN.dtype, device=ctx.theta_device)
+            return rho0_bar, gtheta, None
 
     return Rollout
 

@@ -665,6 +665,34 @@ pplbm_status pplbm_adjoint_set_slots(pplbm_ctx* c, uint32_t mask) {
   return PPLBM_OK;
 }
 
+pplbm_status pplbm_adjoint_set_param(pplbm_ctx* c, int32_t which, double h) {
+  if (!c || which < 0 || which > 3 || !(h > 0.0)) return PPLBM_ERR_ARG;
+  double dc[PPLBM_NGRAD];
+  if (pplbm_status s = pplbm_eos_constant_sensitivity(&c->eos_params, c->G, &c->relax, which, h, dc)) return s;
+  uint32_t mask = 0u;
+  for (int k = 0; k < PPLBM_NGRAD; ++k) {
+    c->adj_dc[k] = dc[k];
+    if (dc[k] != 0.0) mask |= 1u << k;
+  }
+  c->adj_param = which;
+  c->adj_slots = mask;
+  return PPLBM_OK;
+}
+
+pplbm_status pplbm_adjoint_param_gradient(pplbm_ctx* c, const double* grad, double* out) {
+  if (!c || !grad || !out) return PPLBM_ERR_ARG;
+  if (c->adj_param < 0) return PPLBM_ERR_STATE;
+  double g[PPLBM_NGRAD];
+  if (cudaMemcpyAsync(g, grad, sizeof(g), cudaMemcpyDefault, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return PPLBM_ERR_CUDA;
+  double acc = 0.0;  // fixed slot order: deterministic
+  for (int k = 0; k < PPLBM_NGRAD; ++k)
+    if (c->adj_slots & (1u << k)) acc += g[k] * c->adj_dc[k];
+  out[0] = acc;
+  return PPLBM_OK;
+}
+
 pplbm_status pplbm_adjoint_initial_density(pplbm_ctx* c, const double* lambda_0, double* rho0_bar) {
   if (!c || !lambda_0 || !rho0_bar) return PPLBM_ERR_ARG;
   k_adj_init<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(c->n, lambda_0, rho0_bar);

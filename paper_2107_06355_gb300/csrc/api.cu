@@ -163,6 +163,7 @@ pplbm_status pplbm_create(pplbm_ctx** out, const pplbm_lattice* lattice, const p
   if (!c) return PPLBM_ERR_ARG;
   c->lat = *lattice;
   c->relax = *relax;
+  c->eos_params = *eos;
   c->eos = d;
   c->G = G;
   c->n = (int64_t)lattice->nx * lattice->ny;

@@ -13,6 +13,7 @@ using pplbm::StepArgs;
 struct pplbm_ctx {
   pplbm_lattice lat;
   pplbm_relax relax;
+  pplbm_eos_params eos_params;  // as given to pplbm_create (the adjoint's chain rule needs them)
   pplbm_eos_derived eos;
   double G;
   int64_t n;
@@ -37,4 +38,7 @@ struct pplbm_ctx {
   std::vector<cudaEvent_t> ev[2];  // per kernel: start/stop interleaved
   size_t ev_used[2];
   uint32_t adj_slots = ~0u;  // adjoint: bit k set = gradient slot k is accumulated
+  // adjoint chain rule: dc_k/dtheta of the parameter chosen by pplbm_adjoint_set_param
+  double adj_dc[PPLBM_NGRAD] = {};
+  int adj_param = -1;  // -1: none chosen
 };

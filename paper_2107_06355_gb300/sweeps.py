@@ -23,10 +23,22 @@ from . import _lib as L
 from .batch import Batch
 
 
+def _inputs():
+    """The seeded initial-field generators (module lbm_inputs beside this package),
+    the one definition of the planar, droplet and impact profiles."""
+    import importlib
+    import os
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    return importlib.import_module("lbm_inputs")
+
+
 def planar_profile(ny, rho_v, rho_l, W):
     """Eq. PlanarIntDensity along y: interfaces at 1/4 and 3/4 of the length."""
-    y = np.arange(ny, dtype=np.float64)
-    return rho_v + 0.5 * (rho_l - rho_v) * (np.tanh(4.6 * (y - 0.25 * ny) / W) - np.tanh(4.6 * (y - 0.75 * ny) / W))
+    return _inputs().planar(1, ny, rho_v, rho_l, W=W)[:, 0].copy()
 
 
 def density_error(rho_v_sim, rho_v_maxwell):
@@ -274,7 +286,7 @@ def stability_map(cases, Trs, vrs, steps=4000, check_every=500, u_limit=float("i
     b.set_isolation(True)
     for i, W in enumerate(inits):
         d = b.derived(i)
-        rho, ux, uy = _impact_profile(nx, ny, R, film, d["rho_v"], d["rho_l"], V_d, W)
+        rho, ux, uy = _inputs().impact(nx, ny, R, film, d["rho_v"], d["rho_l"], V_d, W=W)
         b.init_equilibrium(i, rho, ux, uy)
     b.set_plan(L.PLAN_GRAPH, 0)
     g0 = b.guard()
@@ -316,13 +328,6 @@ def kappa_for_surface_tension(gamma_target, gamma_at_kappa0):
     return 1.0 - gamma_target / gamma_at_kappa0
 
 
-def _droplet_profile(n, R, rho_v, rho_l, W):
-    """Centred tanh droplet of radius R on an n x n lattice (the planar profile's form)."""
-    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
-    r = np.hypot(x - n / 2.0, y - n / 2.0)
-    return rho_v + (rho_l - rho_v) * 0.5 * (1.0 - np.tanh(4.6 * (r - R) / W))
-
-
 def laplace_law(cases, radii, n=256, steps=40000, W=8.0, G=-1.0):
     """Static droplets: for each (EOSParams, Relax) case and radius R a centred
     droplet on a periodic n x n lattice, all advanced together in one batch for
@@ -338,7 +343,7 @@ def laplace_law(cases, radii, n=256, steps=40000, W=8.0, G=-1.0):
     b.set_isolation(True)
     for k in range(m):
         d = b.derived(k)
-        b.init_equilibrium(k, _droplet_profile(n, radii[k % len(radii)], d["rho_v"], d["rho_l"], W))
+        b.init_equilibrium(k, _inputs().droplet(n, n, radii[k % len(radii)], d["rho_v"], d["rho_l"], W=W))
     b.autotune(trial_steps=4)
     b.step(steps)
     b.sync()
@@ -365,17 +370,6 @@ def laplace_law(cases, radii, n=256, steps=40000, W=8.0, G=-1.0):
     b.close()
     torch.cuda.synchronize()
     return out
-
-
-def _impact_profile(nx, ny, R, film, rho_v, rho_l, V_d, W):
-    """Drop above a film on the bottom wall, tanh interfaces of width W (the planar
-    profile's form), centre at (nx/2, film + R + W), drop velocity (0, -V_d)."""
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
-    r = np.hypot(x - nx / 2.0, y - (film + R + W))
-    phi_d = 0.5 * (1.0 - np.tanh(4.6 * (r - R) / W))
-    phi_f = 0.5 * (1.0 - np.tanh(4.6 * (y - film) / W))
-    rho = rho_v + (rho_l - rho_v) * np.maximum(phi_d, phi_f)
-    return rho, np.zeros_like(rho), -V_d * phi_d
 
 
 def stability_study(Trs, vrs, steps=4000, a_cs=0.363, a_v=2.0, check_every=500):

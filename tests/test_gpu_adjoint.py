@@ -33,12 +33,13 @@ def _state(olat, nx, ny, bc):
     return olat.step(olat.init_equilibrium(rho, ux, uy), 3)
 
 
-def _gpu_alpha_grad(grad, spec_eos, relax, which=0):
-    dc = (C.c_double * L.NGRAD)()
-    p = spec_eos.c()
-    r = relax.c()
-    assert L.lib().pplbm_eos_constant_sensitivity(C.byref(p), -1.0, C.byref(r), which, 1e-4, dc) == 0
-    return float(sum(g * d for g, d in zip(grad, dc)))
+def _gpu_param_grad(sim, grad, which=0):
+    """dL/dtheta through the library's chain rule (pplbm_adjoint_set_param at the
+    context's parameters, then pplbm_adjoint_param_gradient over grad on the device)."""
+    assert L.lib().pplbm_adjoint_set_param(sim.ctx, which, 1e-4) == 0
+    out = (C.c_double * 1)()
+    assert L.lib().pplbm_adjoint_param_gradient(sim.ctx, C.c_void_p(grad.data_ptr()), out) == 0
+    return out[0]
 
 
 @pytest.mark.parametrize("kappa", [0.0, 0.6])
@@ -71,13 +72,15 @@ def test_adjoint_step_matches_oracle_autograd(shape, bc, kappa):
     # dL/dkappa: its own slot (computed at kappa = 0 too, the default slots including it)
     assert float(c["kappa"].grad) != 0.0
     assert float(grad[L.GRAD_NAMES.index("kappa")]) == pytest.approx(float(c["kappa"].grad), rel=1e-9)
-    galpha_gpu = _gpu_alpha_grad(grad.tolist(), sim.eos_params, sim.relax)
+    out = (C.c_double * 1)()
+    assert L.lib().pplbm_adjoint_param_gradient(sim.ctx, C.c_void_p(grad.data_ptr()), out) == L.PPLBM_ERR_STATE
+    galpha_gpu = _gpu_param_grad(sim, grad, 0)
     assert galpha_gpu == pytest.approx(galpha_cpu, rel=1e-6)
     # the branch parameters: the GPU's k1, k2, k4 slots against the oracle's a, T, Delta P
     for wrt, which in (("a_v", 1), ("a_l", 2)):
         dc_w = A.constants_derivative(*CASE[:4], CASE[4], wrt=wrt)
         g_cpu = sum(float(c[k].grad) * dc_w[k] for k in A.CONST_NAMES)
-        g_gpu = _gpu_alpha_grad(grad.tolist(), sim.eos_params, sim.relax, which)
+        g_gpu = _gpu_param_grad(sim, grad, which)
         assert g_cpu != 0.0
         assert g_gpu == pytest.approx(g_cpu, rel=1e-6), wrt
 

@@ -95,7 +95,7 @@ def test_single_lattice_guard_matches_oracle(case):
     from paper_2107_06355_gb300 import _lib as L
 
     fb = f.copy()
-    fb[:, 3, 5] = -1.0
+    fb[:, 3, 1] = -1.0
     fb[:, ny - 1, 0] = np.nan
     sim.set_f(fb)
     rho = fb.sum(axis=0)

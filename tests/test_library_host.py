@@ -33,7 +33,9 @@ def test_library_exports_every_declared_symbol(lib):
 CASES = [(E.MODE_SMOOTH, 0.6, 0.387, 2.0, 0.834), (E.MODE_SMOOTH, 0.5, 0.363, 2.0, 0.775),
          (E.MODE_SMOOTH, 0.35, 0.363, 2.0, 0.775), (E.MODE_SMOOTH, 0.8, 0.5, 0.5, 0.342),
          (E.MODE_SMOOTH, 0.95, 0.363, 2.0, 0.775), (E.MODE_CS, 0.6, 0.387, 0.387, 0.0),
-         (E.MODE_CS, 0.5, 0.363, 0.363, 0.0), (E.MODE_CS, 0.8, 0.5, 0.5, 0.0)]
+         (E.MODE_CS, 0.5, 0.363, 0.363, 0.0), (E.MODE_CS, 0.8, 0.5, 0.5, 0.0),
+         # instance 61 of the 64-lattice sweep: p_max close to p_sat, the ellipse radicand near 0
+         (E.MODE_SMOOTH, 0.35 + 0.6 * 61 / 63, 0.363, 2.0, 0.775)]
 
 
 def test_peng_and_modified_smooth_setup_match_oracle(lib):
@@ -268,3 +270,58 @@ def test_noalloc_step_rejects_overlapping_buffers_before_any_cuda_call(lib):
     st = lib.pplbm_step_noalloc(C.byref(big), C.byref(eos), C.byref(relax), C.c_void_p(base),
                                 C.c_void_p(base + 8 * 9 * 257 * 256), None, C.byref(msg))
     assert st == L.PPLBM_ERR_ARG and b"65536" in msg.value
+
+
+def _oracle_dc_in_library_slots(d, wrt, h, G=-1.0):
+    """The oracle's d(constants)/d(theta) (oracle.adjoint.constants_derivative, central
+    differences with Richardson extrapolation of its own set-up) mapped onto the
+    library's slots: 1/a^2 of the ellipses, the cubic's a2 = 2 (p_max - p_min) and
+    b2 = 3 (p_min - p_max), z = sigma G^2/432, k1 = (2/G) R T, k2 = -(2/G) a,
+    k4 = (2/G) Delta P (Sec. III.D, Eqs. CS, InteractionPotential, LiFS)."""
+    from oracle import adjoint as A
+
+    o = A.constants_derivative(E.MODE_SMOOTH, 0.5, 0.363, 2.0, 0.775, h=h, wrt=wrt)
+    s = 2.0 / G
+    R = 1.0
+    return {"p_max": o["p_max"], "b1": o["b1"], "inv_a1sq": -o["a1sq"] / d["a1sq"] ** 2,
+            "a2": 2.0 * (o["p_max"] - o["p_min"]), "b2": 3.0 * (o["p_min"] - o["p_max"]), "p_min": o["p_min"],
+            "b3": o["b3"], "inv_a3sq": -o["a3sq"] / d["a3sq"] ** 2, "zz_scale": o["sigma"] * G * G / 432.0,
+            "k1_v": s * R * o["T_v"], "k2_v": -s * o["a_v"], "k1_l": s * R * o["T_l"], "k2_l": -s * o["a_l"],
+            "k4_l": s * o["dP"], "kappa": 0.0}
+
+
+@pytest.mark.parametrize("which,wrt", [(0, "alpha"), (1, "a_v"), (2, "a_l")])
+def test_constant_sensitivity_matches_the_oracle_and_its_error_bound(lib, which, wrt):
+    """pplbm_eos_constant_sensitivity (the product's set-up: Maxwell by the chemical
+    potential, Gauss-Legendre, Ridders) against the oracle's derivative of its own
+    set-up (brentq, adaptive quadrature, Simpson for eps) on the adjoint configuration
+    (T_r = 0.5, a_l = 0.363, a_v = 2, alpha = 0.775).
+
+    The header's bound for the library: O(h^4) + 3 delta/h, delta the set-up's error
+    in a constant c (~1e-15 |c|). Its estimates at h = 1e-4 and h/2 (bound 6 delta/h)
+    therefore differ by at most ~1e-10 |c|; the test allows 1e-9 |c| (+ 1e-8 of the
+    derivative for the O(h^4) term). The oracle's (h = 1e-3, its quadratures good to
+    ~1e-14 |c|, its eps to ~1e-11) may be off by 3e-11 |c|, 3e-8 for sigma: the test
+    allows 1e-7 |c| + 1e-6 of the derivative."""
+    G = -1.0
+    p = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775).c()
+    relax = P.Relax().c()
+    d = P.eos_setup(P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775))
+    dd = L.pplbm_eos_derived()
+    assert lib.pplbm_eos_setup(C.byref(p), G, C.byref(dd)) == L.PPLBM_OK
+    cv = (C.c_double * L.NGRAD)()
+    assert lib.pplbm_eos_grad_constants(C.byref(dd), cv) == L.PPLBM_OK
+    cval = dict(zip(L.GRAD_NAMES, list(cv)))
+    cval["zz_scale"] = (-d["eps"] / (16.0 * G)) * G * G / 432.0   # sigma = -eps/(16 G), Sec. III.A
+    dc = {}
+    for h in (1e-4, 5e-5):
+        out = (C.c_double * L.NGRAD)()
+        assert lib.pplbm_eos_constant_sensitivity(C.byref(p), G, C.byref(relax), which, h, out) == L.PPLBM_OK
+        dc[h] = dict(zip(L.GRAD_NAMES, list(out)))
+    want = _oracle_dc_in_library_slots(d, wrt, 1e-3, G)
+    for k in L.GRAD_NAMES:
+        a, b = dc[1e-4][k], dc[5e-5][k]
+        assert abs(a - b) <= 1e-9 * abs(cval[k]) + 1e-8 * abs(a), (k, a, b)
+        assert abs(a - want[k]) <= 1e-7 * abs(cval[k]) + 1e-6 * abs(want[k]), (k, a, want[k])
+    # the slots each parameter moves are not all zero
+    assert sum(abs(v) for v in dc[1e-4].values()) > 0
