@@ -251,13 +251,13 @@ def measure_fp64_peak(torch, local, seconds=0.6, repeats=3):
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
     out = (C.c_double * 3)()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    L.check(lib.pplbm_fp64_peak(8, 4000, C.c_void_p(sink.data_ptr()), out, stream))  # warm-up and calibration
+    L.check(lib.pplbm_fp64_peak(8, 8, 0, 4000, C.c_void_p(sink.data_ptr()), out, stream))  # warm-up, calibration
     iters = max(1000, int(4000 * seconds / max(out[1] * 1e-3, 1e-6)))
     clocks = ClockSampler(local, "fp64")
     clocks.start()
     rates, ms = [], []
     for _ in range(repeats):
-        L.check(lib.pplbm_fp64_peak(8, iters, C.c_void_p(sink.data_ptr()), out, stream))
+        L.check(lib.pplbm_fp64_peak(8, 8, 0, iters, C.c_void_p(sink.data_ptr()), out, stream))
         rates.append(out[0])
         ms.append(out[1])
     clk = clocks.stop()
@@ -267,6 +267,35 @@ def measure_fp64_peak(torch, local, seconds=0.6, repeats=3):
             "launch_ms": ms, "blocks": int(out[2]), "iters": iters, "clocks": clk,
             "how": "pplbm_fp64_peak: 8 independent FP64 FMA chains per thread, 256 threads x 8 blocks per SM, "
                    "CUDA events, best of 3"}
+
+
+def fp64_probe_sweep(torch, local):
+    """pplbm_fp64_peak over chain counts, occupancies and operations (each launch
+    ~0.1-0.2 s at the running clock, sampled by nvidia-smi): whether any issue pattern
+    beats the rate the bench uses as its peak. One JSON line."""
+    import ctypes as C
+    from paper_2107_06355_gb300 import _lib as L
+
+    lib = L.lib()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = (C.c_double * 3)()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    variants = [(8, 8, 0), (4, 8, 0), (2, 8, 0), (1, 8, 0), (8, 1, 0), (8, 2, 0), (8, 4, 0), (8, 16, 0),
+                (4, 32, 0), (8, 8, 1), (8, 8, 2)]
+    L.check(lib.pplbm_fp64_peak(8, 8, 0, 4000, C.c_void_p(sink.data_ptr()), out, stream))
+    clocks = ClockSampler(local, "sweep")
+    clocks.start()
+    rows = []
+    for bpsm, ch, op in variants:
+        iters = max(1000, int(160000 * 8 / (bpsm * ch)))
+        L.check(lib.pplbm_fp64_peak(bpsm, ch, op, iters, C.c_void_p(sink.data_ptr()), out, stream))
+        rows.append({"blocks_per_sm": bpsm, "chains": ch, "op": ("fma", "add", "mul")[op], "rate": out[0] / 1e12,
+                     "ms": out[1]})
+    clk = clocks.stop()
+    mhz = clk["sm_mhz"] or 2070.0
+    for r in rows:
+        r["per_sm_clk"] = r["rate"] * 1e12 / (152 * mhz * 1e6)
+    print(json.dumps({"fp64_probe_sweep": rows, "clocks": clk, "unit": "T FP64 instr/s"}), flush=True)
 
 
 # ---- the 2048 x 1024 droplet impact (single lattice) ---------------------------------
@@ -806,7 +835,13 @@ def main():
     ap.add_argument("--profile-impact", action="store_true", help="3 steps of the 2048x1024 impact (for ncu)")
     ap.add_argument("--profile-adjoint", action="store_true", help="checkpointed adjoint on 1024 x 1024 (for ncu)")
     ap.add_argument("--profile-fd", action="store_true", help="3 steps of the FD solver on 2048 x 1024 (for ncu)")
+    ap.add_argument("--fp64-probe-sweep", action="store_true",
+                    help="the FP64 issue-rate probe over chains, occupancy and operation, then exit")
     args = ap.parse_args()
+    if args.fp64_probe_sweep:
+        import torch
+        build_lib()
+        return fp64_probe_sweep(torch, dist_env()[2])
     if args.profile_sweep is not None:
         return profile_sweep(args.profile_sweep)
     if args.profile_impact:

@@ -235,9 +235,11 @@ pplbm_status pplbm_get_derived(const pplbm_ctx* ctx, pplbm_eos_derived* out);
 pplbm_status pplbm_run_host(pplbm_ctx* ctx, const double* rho0, const double* ux0, const double* uy0,
                             int64_t nsteps, double* rho_out);
 
-/* ---- Adjoint (reverse-mode gradients), unit relaxation times (Sec. III.A) -----
+/* ---- Adjoint (reverse-mode gradients) -----------------------------------------
  * A hand-written adjoint of pplbm_step for contexts whose relaxation times are
- * all 1 (other sets return PPLBM_ERR_STATE). Gradients flow to the state and to
+ * all 1 (Sec. III.A) or the two-phase set of the dynamic runs (Sec. IV: rows 7, 8
+ * relax with 1/tau(rho), Eq. RelaxationTime, differentiated through tau(rho) too);
+ * the general six-time MRT set returns PPLBM_ERR_STATE. Gradients flow to the state and to
  * the EOS constants that the shaping parameters move (Sec. III.D):
  * grad[PPLBM_NGRAD] = dL/d{p_max, b1, 1/a1^2, a2, b2, p_min, b3, 1/a3^2, z,
  *                          k1_v, k2_v, k1_l, k2_l, k4_l, kappa},
@@ -279,10 +281,12 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* ctx, int64_t nsteps, int64_t
 pplbm_status pplbm_adjoint_segment(pplbm_ctx* ctx, const double* f_start, int64_t nsteps, double* states,
                                    const double* lambda_end, double* lambda_start, double* grad,
                                    void* adj_workspace, size_t adj_workspace_bytes);
-/* Rollouts whose fields fit in device memory (4 planes per step: psi, rho, jx, jy;
- * 2,000 steps of a 256^2 lattice take 4.2 GB): pplbm_forward_stored advances nsteps
+/* Rollouts whose fields fit in device memory (P planes per step: psi and the moment
+ * planes, P = 4 with unit relaxation times -- psi, rho, jx, jy -- and P = 6 with the
+ * two-phase set, which adds the stress moments of rows 7, 8; 2,000 steps of a 256^2
+ * lattice with P = 4 take 4.2 GB): pplbm_forward_stored advances nsteps
  * like pplbm_step, its density passes writing psi and the moments of f^t into
- * fields + 4*nx*ny*t (nsteps slots, device); pplbm_backward_stored then runs the
+ * fields + P*nx*ny*t (nsteps slots, device); pplbm_backward_stored then runs the
  * adjoint steps t = nsteps-1 ... 0 from those slots, with no recomputation and no
  * density pass of its own. Results are bitwise those of the checkpointed pair. */
 pplbm_status pplbm_forward_stored(pplbm_ctx* ctx, int64_t nsteps, double* fields);
@@ -499,15 +503,17 @@ pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed, double* o
 /* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the
  * step's per-node arithmetic is double precision throughout, Sec. II; on this GPU
  * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)
- * blocks of 256 threads; each thread runs `iters` rounds of 8 independent FP64
- * fused multiply-adds. Times the launch with CUDA events on `stream` and
- * synchronises it. Writes to host out[3]: out[0] = FP64 FMA instructions per
- * second (counted per thread, as the step's per-node instruction counts are),
- * out[1] = the launch's milliseconds, out[2] = blocks launched. `sink` is one
- * device double the kernel may write (it never does for these inputs; it keeps
- * the chains from being optimised away). PPLBM_ERR_ARG for blocks_per_sm outside
- * [1, 64], iters < 1 or NULL pointers. */
-pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, long long iters, double* sink, double* out, void* stream);
+ * blocks of 256 threads; each thread runs `iters` rounds of `chains` (1, 2, 4, 8,
+ * 16 or 32) independent chains of one FP64 operation: op 0 fused multiply-add,
+ * 1 add, 2 multiply. Times the launch with CUDA events on `stream` and
+ * synchronises it. Writes to host out[3]: out[0] = FP64 instructions per second
+ * (counted per thread, as the step's per-node instruction counts are), out[1] =
+ * the launch's milliseconds, out[2] = blocks launched. `sink` is one device double
+ * the kernel may write (it never does for these inputs; it keeps the chains from
+ * being optimised away). PPLBM_ERR_ARG for blocks_per_sm outside [1, 64], another
+ * chain count or op, iters < 1 or NULL pointers. */
+pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, int32_t op, long long iters, double* sink,
+                             double* out, void* stream);
 
 /* Kernel timing, a profiling aid. With capacity > 0, pplbm_step records a CUDA
  * event pair around every launch of the two step kernels on the context's

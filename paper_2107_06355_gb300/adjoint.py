@@ -39,16 +39,21 @@ class RolloutSpec:
     def k(self):
         return self.interval if self.interval > 0 else max(1, math.ceil(math.sqrt(self.nsteps)))
 
+    def field_planes(self):
+        """Planes a stored step keeps: psi and the moment planes (4 with unit relaxation
+        times, 6 with the two-phase set)."""
+        return 6 if self.relax.kind == L.RELAX_TWO_PHASE else 4
+
     def stored(self):
         """Keep every step's psi and moments (no recomputation) when the interval is
-        automatic and 4 nx ny nsteps doubles fit in memory_fraction of the free device
-        memory; otherwise sqrt(N) checkpointing with recomputation."""
+        automatic and field_planes() nx ny nsteps doubles fit in memory_fraction of the
+        free device memory; otherwise sqrt(N) checkpointing with recomputation."""
         if self.interval > 0:
             return False
         import torch
 
         free, _ = torch.cuda.mem_get_info()
-        return 32 * self.nx * self.ny * max(1, self.nsteps) <= self.memory_fraction * free
+        return 8 * self.field_planes() * self.nx * self.ny * max(1, self.nsteps) <= self.memory_fraction * free
 
 
 SENS_STEP = 1e-4  # step of the central differences behind dc/dtheta (pplbm_eos_constant_sensitivity)
@@ -87,8 +92,10 @@ def _rollout_forward(spec: RolloutSpec, rho0, value: float):
     sim.init_equilibrium(rho0)
     if spec.stored():
         # ckpt holds every step's psi and moments
-        ckpt = torch.empty((max(1, spec.nsteps), 4, spec.ny, spec.nx), dtype=torch.float64, device=sim.device)
+        ckpt = torch.empty((max(1, spec.nsteps), spec.field_planes(), spec.ny, spec.nx), dtype=torch.float64,
+                           device=sim.device)
         sim._check(L.lib().pplbm_forward_stored(sim.ctx, spec.nsteps, _ptr(ckpt)))
+        sim._stored = True
     else:
         K = spec.k()
         nseg = max(1, -(-spec.nsteps // K))
@@ -110,7 +117,7 @@ def _rollout_backward(spec: RolloutSpec, sim: Simulation, ckpt, grad_rhoN, slots
     grad = torch.zeros(L.NGRAD, dtype=torch.float64, device=dev)
     nbytes = L.lib().pplbm_adjoint_workspace_bytes(C.byref(sim.lattice))
     ws = torch.empty(nbytes // 8 + 1, dtype=torch.float64, device=dev)
-    if ckpt.shape[1] == 4:   # stored fields of every step
+    if getattr(sim, "_stored", False):   # stored fields of every step
         sim._check(L.lib().pplbm_backward_stored(sim.ctx, spec.nsteps, _ptr(ckpt), _ptr(lamN), _ptr(lam0),
                                                  _ptr(grad), _ptr(ws), nbytes))
     else:

@@ -1,4 +1,5 @@
-// Hand-written adjoint of the step (unit relaxation times), sqrt(N) checkpointed
+// Hand-written adjoint of the step (unit relaxation times, or the two-phase set of
+// Sec. IV whose rows 7, 8 relax with 1/tau(rho), Eq. RelaxationTime), sqrt(N) checkpointed
 // rollouts, and the EOS-constant sensitivities that chain the gradient to the
 // shaping parameter alpha (Sec. III.D).
 //
@@ -16,7 +17,8 @@
 //      surface-tension source the transposes of its stencil sums t, sd, xd
 //      (step_device.cuh; symmetric stencils, so the same sums of their adjoints); then
 //      through psi = sqrt(psi^2(rho; constants)) to rho_bar and the constants'
-//      adjoints; lambda^t_i = rho_bar + c_i . j_bar.
+//      adjoints; lambda^t_i = rho_bar + c_i . j_bar (+ the rows 7, 8 of Eq. MatrixMRT
+//      times the stress moments' adjoints with the two-phase set).
 // Constant adjoints are reduced per block and summed in a fixed order
 // (deterministic); over a checkpointed rollout each block's sums accumulate
 // across the steps and are reduced once at the end. Blocks with no node on a
@@ -37,7 +39,7 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8, kNT = kTX * kTY;
 // adjoint workspace: kBarPlanes adjoint planes, two 9-plane lambda buffers, per-block partials
-constexpr int kBarPlanes = 9;
+constexpr int kBarPlanes = 11;
 constexpr int kLamOffset = kBarPlanes;            // in planes of n values
 constexpr int kPartialOffset = kBarPlanes + 18;
 // gradient slots: the constants of the shaped branches (which alpha moves), the
@@ -57,7 +59,8 @@ struct AdjArgs {
   const double* lam1;    // lambda^{t+1}, 9 planes
   double* lam0;          // lambda^t, 9 planes
   double* bar;           // kBarPlanes planes: rho_bar, jx_bar, jy_bar, psi_bar (own), gx_bar, gy_bar,
-                         // and the surface-tension sums' t_bar, sd_bar, xd_bar
+                         // the surface-tension sums' t_bar, sd_bar, xd_bar, and (two-phase set)
+                         // the stress moments' m7_bar, m8_bar
   double* partial1;      // per A1 block: the zz-scale and kappa adjoints
   double* partial2;      // per A2 block: kA2 constant adjoints (slot order without G_ZZ, G_KAPPA)
   int accumulate;        // add this step's block sums to the partials (a rollout) instead of storing them
@@ -146,6 +149,116 @@ __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double r
   *gy_b = gy_bb;
 }
 
+// reverse mode of collide_reduced<kShearTau> (see its comments for the forward): rows
+// 7, 8 relax with omega = 1/tau(rho), tau = tau_a + tau_b rho, as
+//   m7* = (Pi_xx - Pi_yy) + (1 - omega) A7,  A7 = m7 - ux (jx - hx) + uy (jy - hy),
+//   m8* = Pi_xy + (1 - omega) A8,           A8 = m8 - ux jy + uy hx,
+// so the adjoint reaches rho also through omega, and m7, m8 (the density pass's stress
+// moments) directly. With the surface-tension source (sq not null: zz += k t,
+// m7* -= 4 omega k sd, m8* -= omega k xd) it returns st_b = {k_b, t_b, sd_b, xd_b}.
+__device__ __forceinline__ void collide_shear_reverse(const StepArgs& a, double rho, double jx, double jy, double m7,
+                                                      double m8, double psi0, double gx, double gy, const double* mu,
+                                                      const SurfQ* sq, double* rho_b, double* jx_b, double* jy_b,
+                                                      double* m7_b, double* m8_b, double* psi_b, double* gx_b,
+                                                      double* gy_b, double* zs_b, double* st_b) {
+  // forward recompute
+  const double cH = a.half_force * psi0;
+  const double hx = cH * gx, hy = cH * gy;
+  const double inv = fast_rcp(rho);
+  const double Jx = jx + hx, Jy = jy + hy;
+  const double ux = Jx * inv, uy = Jy * inv;
+  const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
+  const double g2 = fma(gx, gx, gy * gy);
+  const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
+  const double omc = 1.0 - om;
+  const double Kx = jx - hx, Ky = jy - hy;
+  const double A7 = fma(-ux, Kx, fma(uy, Ky, m7));
+  const double A8 = fma(-ux, jy, fma(uy, hx, m8));
+  // reverse: population-space reconstruction
+  const double dp_b = mu[5] + mu[7], ps_b = (mu[5] - mu[7]) * (1.0 / 12.0);
+  const double dm_b = mu[6] + mu[8], pd_b = (mu[6] - mu[8]) * (1.0 / 12.0);
+  const double Dq_b = dp_b + dm_b;
+  const double Pxy_b = 0.25 * (dp_b - dm_b);
+  double zz_b = Dq_b;
+  double r_b = Dq_b * (1.0 / 36.0);
+  double tr_b = Dq_b * (1.0 / 12.0);
+  const double axp_b = mu[1] + mu[3], ayp_b = mu[2] + mu[4];
+  double Px_b = (mu[1] - mu[3]) * (1.0 / 3.0) + (ps_b - pd_b);
+  double Py_b = (mu[2] - mu[4]) * (1.0 / 3.0) + (ps_b + pd_b);
+  // axp, ayp = T4 +- m7*/4, T4 = Q + tr/4
+  const double T4_b = axp_b + ayp_b;
+  const double m7s_b = 0.25 * (axp_b - ayp_b);
+  tr_b += 0.25 * T4_b;
+  const double B0_b = (4.0 / 9.0) * mu[0] + T4_b * (1.0 / 9.0);
+  zz_b += T4_b - 8.0 * mu[0];
+  r_b += B0_b;
+  tr_b += -1.5 * B0_b;
+  // rows 7, 8 (and the source's terms)
+  const double A8_b = Pxy_b * omc, A7_b = m7s_b * omc;
+  double om_b = -(Pxy_b * A8 + m7s_b * A7);  // through omc = 1 - omega
+  if (sq) {
+    const double w = fma(4.0 * sq->sd, m7s_b, sq->xd * Pxy_b);
+    st_b[0] = fma(zz_b, sq->t, -om * w);  // k_b
+    st_b[1] = zz_b * sq->k;               // t_b
+    st_b[2] = -4.0 * om * sq->k * m7s_b;  // sd_b
+    st_b[3] = -om * sq->k * Pxy_b;        // xd_b
+    om_b -= sq->k * w;
+  }
+  r_b += -om_b * om * om * a.tau_b;  // d omega / d rho = -tau_b omega^2
+  const double Pxx_b = m7s_b + tr_b, Pyy_b = tr_b - m7s_b;
+  // A8 = m8 - ux jy + uy hx
+  double ux_b = -A8_b * jy, uy_b = A8_b * hx, hx_b = A8_b * uy;
+  double jx_bb = 0.0, jy_bb = -A8_b * ux;
+  // A7 = m7 - ux (jx - hx) + uy (jy - hy)
+  ux_b -= A7_b * Kx;
+  uy_b += A7_b * Ky;
+  jx_bb -= A7_b * ux;
+  hx_b += A7_b * ux;
+  jy_bb += A7_b * uy;
+  double hy_b = -A7_b * uy;
+  // Pi_xy = ux Py + uy hx
+  ux_b += Pxy_b * Py;
+  Py_b += Pxy_b * ux;
+  uy_b += Pxy_b * hx;
+  hx_b += Pxy_b * uy;
+  // Pi_xx = ux (Px + hx), Pi_yy = uy (Py + hy)
+  ux_b += Pxx_b * (Px + hx);
+  Px_b += Pxx_b * ux;
+  hx_b += Pxx_b * ux;
+  uy_b += Pyy_b * (Py + hy);
+  Py_b += Pyy_b * uy;
+  hy_b += Pyy_b * uy;
+  // Px = jx + 2 hx, Py = jy + 2 hy
+  jx_bb += Px_b;
+  hx_b += 2.0 * Px_b;
+  jy_bb += Py_b;
+  hy_b += 2.0 * Py_b;
+  // ux = Jx inv, uy = Jy inv
+  const double Jx_b = ux_b * inv, Jy_b = uy_b * inv;
+  const double inv_b = ux_b * Jx + uy_b * Jy;
+  jx_bb += Jx_b;
+  hx_b += Jx_b;
+  jy_bb += Jy_b;
+  hy_b += Jy_b;
+  r_b += -inv_b * inv * inv;
+  // zz = zs g2
+  const double zs = a.zz_scale;
+  double gx_bb = 2.0 * zs * gx * zz_b, gy_bb = 2.0 * zs * gy * zz_b;
+  *zs_b = zz_b * g2;
+  // hx = cH gx, hy = cH gy, cH = hf psi0
+  const double cH_b = hx_b * gx + hy_b * gy;
+  gx_bb += hx_b * cH;
+  gy_bb += hy_b * cH;
+  *psi_b = cH_b * a.half_force;
+  *rho_b = r_b;
+  *jx_b = jx_bb;
+  *jy_b = jy_bb;
+  *m7_b = A7_b;
+  *m8_b = A8_b;
+  *gx_b = gx_bb;
+  *gy_b = gy_bb;
+}
+
 // psi^2(rho) and its derivatives w.r.t. rho and the alpha-dependent constants (eos_dev.cuh);
 // the C-S branch constants' derivatives only when bulk_slots (a uniform flag)
 __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, bool bulk_slots, double* dc) {
@@ -217,7 +330,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
-template <bool ST>
+template <int KIND, bool ST>
 __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
   __shared__ double sp[(kTY + 2) * (kTX + 2)];
   __shared__ double red[kNT];
@@ -259,23 +372,39 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
     mu[7] = down ? L1[5 * N + node] : L1[7 * N + rs + xw];
     mu[8] = down ? L1[6 * N + node] : L1[8 * N + rs + xe];
     double rb, jxb, jyb, pb, gxb, gyb;
-    double zq_b[4];
-    collide_unit_reverse(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, mu, &rb, &jxb, &jyb, &pb,
-                         &gxb, &gyb, &zs_b, ST ? zq_b : nullptr);
+    double st_b[4] = {0.0, 0.0, 0.0, 0.0};  // the source's k_b, t_b, sd_b, xd_b
+    SurfQ sq = {0.0, 0.0, 0.0, 0.0};
+    if (ST)
+      sq = surface_q(a, p0, sp[c + 1], sp[c - 1], sp[c + sw], sp[c - sw], sp[c + sw + 1], sp[c + sw - 1],
+                     sp[c - sw - 1], sp[c - sw + 1]);
     double* B = g.bar;
+    if (KIND == kShearTau) {
+      double m7b, m8b;
+      collide_shear_reverse(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node], a.mom[3 * N + node],
+                            a.mom[4 * N + node], p0, gx, gy, mu, ST ? &sq : nullptr, &rb, &jxb, &jyb, &m7b, &m8b, &pb,
+                            &gxb, &gyb, &zs_b, st_b);
+      B[9 * N + node] = m7b;
+      B[10 * N + node] = m8b;
+    } else {
+      double zq_b[4];
+      collide_unit_reverse(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, mu, &rb, &jxb, &jyb,
+                           &pb, &gxb, &gyb, &zs_b, ST ? zq_b : nullptr);
+      if (ST) {
+        // forward: zz += k t, axp -= k sd, ayp += k sd, Pxy -= k xd, k = kappa_q psi(x)
+        const double dsd = zq_b[2] - zq_b[1];
+        st_b[0] = fma(zq_b[0], sq.t, fma(dsd, sq.sd, -zq_b[3] * sq.xd));
+        st_b[1] = zq_b[0] * sq.k;
+        st_b[2] = dsd * sq.k;
+        st_b[3] = -zq_b[3] * sq.k;
+      }
+    }
     if (ST) {
-      // forward: zz += k t, axp -= k sd, ayp += k sd, Pxy -= k xd, k = kappa_q psi(x)
-      const SurfQ sq = surface_q(a, p0, sp[c + 1], sp[c - 1], sp[c + sw], sp[c - sw], sp[c + sw + 1],
-                                 sp[c + sw - 1], sp[c - sw - 1], sp[c - sw + 1]);
-      const double dsd = zq_b[2] - zq_b[1];
-      const double k_b = fma(zq_b[0], sq.t, fma(dsd, sq.sd, -zq_b[3] * sq.xd));
-      const double t_b = zq_b[0] * sq.k;
       // own node: k = kappa_q psi(x), and t carries -psi(x); kappa_q = kappa G / 24
-      pb += fma(k_b, a.kappa_q, -t_b);
-      kap_b = k_b * p0 * (a.G / 24.0);
-      B[6 * N + node] = t_b;
-      B[7 * N + node] = dsd * sq.k;
-      B[8 * N + node] = -zq_b[3] * sq.k;
+      pb += fma(st_b[0], a.kappa_q, -st_b[1]);
+      kap_b = st_b[0] * p0 * (a.G / 24.0);
+      B[6 * N + node] = st_b[1];
+      B[7 * N + node] = st_b[2];
+      B[8 * N + node] = st_b[3];
     }
     B[node] = rb;
     B[N + node] = jxb;
@@ -311,7 +440,7 @@ __device__ __forceinline__ void load_bar_tiles(const AdjArgs& g, int p0, double*
   }
 }
 
-template <bool ST>
+template <int KIND, bool ST>
 __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
   constexpr int ts = (kTY + 2) * (kTX + 2);
   __shared__ double tiles[(ST ? 5 : 2) * ts];  // gx_bar, gy_bar (and t_bar, sd_bar, xd_bar)
@@ -369,16 +498,19 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     if (liq_side)
       for (int k = a2_index(G_K1L); k <= a2_index(G_K4L); ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
+    // the stress moments of the two-phase set: rows 7, 8 of Eq. MatrixMRT
+    const double m7b = KIND == kShearTau ? g.bar[9 * N + node] : 0.0;
+    const double m8b = KIND == kShearTau ? g.bar[10 * N + node] : 0.0;
     double* L0 = g.lam0;
     L0[node] = rho_b;
-    L0[N + node] = rho_b + jxb;
-    L0[2 * N + node] = rho_b + jyb;
-    L0[3 * N + node] = rho_b - jxb;
-    L0[4 * N + node] = rho_b - jyb;
-    L0[5 * N + node] = rho_b + jxb + jyb;
-    L0[6 * N + node] = rho_b - jxb + jyb;
-    L0[7 * N + node] = rho_b - jxb - jyb;
-    L0[8 * N + node] = rho_b + jxb - jyb;
+    L0[N + node] = rho_b + jxb + m7b;
+    L0[2 * N + node] = rho_b + jyb - m7b;
+    L0[3 * N + node] = rho_b - jxb + m7b;
+    L0[4 * N + node] = rho_b - jyb - m7b;
+    L0[5 * N + node] = rho_b + jxb + jyb + m8b;
+    L0[6 * N + node] = rho_b - jxb + jyb - m8b;
+    L0[7 * N + node] = rho_b - jxb - jyb + m8b;
+    L0[8 * N + node] = rho_b + jxb - jyb - m8b;
   }
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   double* dst = g.partial2 + (int64_t)blk * kA2;
@@ -456,12 +588,21 @@ pplbm_status adjoint_core(pplbm_ctx* c, const StepArgs& a, const double* lam1, d
   g.accumulate = accumulate ? 1 : 0;
   g.slots = c->adj_slots;
   const dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY), block(kTX, kTY);
-  if (a.kappa_q != 0.0 || ((g.slots >> G_KAPPA) & 1u)) {  // with the surface-tension source (kappa_q may be 0)
-    k_adj_collide<true><<<grid, block, 0, c->stream>>>(g);
-    k_adj_rho_psi<true><<<grid, block, 0, c->stream>>>(g);
+  const bool st = a.kappa_q != 0.0 || ((g.slots >> G_KAPPA) & 1u);  // with the source (kappa_q may be 0)
+  if (a.kind == kShearTau) {
+    if (st) {
+      k_adj_collide<kShearTau, true><<<grid, block, 0, c->stream>>>(g);
+      k_adj_rho_psi<kShearTau, true><<<grid, block, 0, c->stream>>>(g);
+    } else {
+      k_adj_collide<kShearTau, false><<<grid, block, 0, c->stream>>>(g);
+      k_adj_rho_psi<kShearTau, false><<<grid, block, 0, c->stream>>>(g);
+    }
+  } else if (st) {
+    k_adj_collide<kUnitTau, true><<<grid, block, 0, c->stream>>>(g);
+    k_adj_rho_psi<kUnitTau, true><<<grid, block, 0, c->stream>>>(g);
   } else {
-    k_adj_collide<false><<<grid, block, 0, c->stream>>>(g);
-    k_adj_rho_psi<false><<<grid, block, 0, c->stream>>>(g);
+    k_adj_collide<kUnitTau, false><<<grid, block, 0, c->stream>>>(g);
+    k_adj_rho_psi<kUnitTau, false><<<grid, block, 0, c->stream>>>(g);
   }
   if (reduce) k_adj_reduce<<<kNGrad, 256, 0, c->stream>>>(g.partial1, g.partial2, nb, grad);
   const cudaError_t e = cudaGetLastError();
@@ -501,14 +642,18 @@ size_t pplbm_adjoint_workspace_bytes(const pplbm_lattice* lattice) {
   return adj_bytes(lattice);
 }
 
-// the adjoint differentiates collide_reduced<kUnitTau> (with or without the surface-tension source)
+// the adjoint differentiates collide_reduced<kUnitTau> and <kShearTau> (with or without
+// the surface-tension source); the general six-time MRT set is not covered
 static pplbm_status adjoint_supported(pplbm_ctx* c) {
-  if (c->args.kind != kUnitTau) {
-    c->msg = "the adjoint covers unit relaxation times only";
+  if (c->args.kind != kUnitTau && c->args.kind != kShearTau) {
+    c->msg = "the adjoint covers unit relaxation times and the two-phase set only";
     return PPLBM_ERR_STATE;
   }
   return PPLBM_OK;
 }
+
+// planes kept per step by the stored and segment modes: psi and the moment planes
+static int field_planes(const pplbm_ctx* c) { return 1 + moment_planes(c->args.kind); }
 
 pplbm_status pplbm_adjoint_step(pplbm_ctx* c, const double* f_t, const double* lambda_next, double* lambda_t,
                                 double* grad, void* adj_workspace, size_t adj_workspace_bytes) {
@@ -561,7 +706,8 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
     // buffers plus psi and the three moments of every state of the segment: the
     // recomputation keeps what its density passes produce and the adjoint steps
     // reuse it. Shorter intervals store the states themselves.
-    const bool keep_fields = 9 * interval >= 18 + 4 * interval;
+    const int fp = field_planes(c);
+    const bool keep_fields = 9 * interval >= 18 + fp * interval;
     const int64_t n = c->n;
     for (int64_t j = nseg - 1; j >= 0; --j) {
       const int64_t t0 = j * interval, t1 = std::min(nsteps, t0 + interval);
@@ -570,12 +716,12 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
         return PPLBM_ERR_CUDA;
       if (keep_fields) {
         double* fb[2] = {segment, segment + stride};
-        double* fields = segment + 2 * stride;  // per state: psi, rho, jx, jy
+        double* fields = segment + 2 * stride;  // per state: psi and the moment planes
         for (int64_t t = t0; t < t1; ++t) {
           StepArgs a = c->args;
           a.f_in = fb[(t - t0) & 1];
           a.f_out = fb[(t - t0 + 1) & 1];
-          a.psi = fields + (t - t0) * 4 * n;
+          a.psi = fields + (t - t0) * fp * n;
           a.mom = a.psi + n;
           launch_rho_psi(a, s);
           if (t + 1 < t1) launch_collide(a, s);
@@ -583,7 +729,7 @@ pplbm_status pplbm_backward_checkpointed(pplbm_ctx* c, int64_t nsteps, int64_t i
         if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
         for (int64_t t = t1 - 1; t >= t0; --t) {
           StepArgs a = c->args;
-          a.psi = fields + (t - t0) * 4 * n;
+          a.psi = fields + (t - t0) * fp * n;
           a.mom = a.psi + n;
           if (pplbm_status st = adjoint_core(c, a, cur, nxt, grad, ws, true, false)) return st;
           std::swap(cur, nxt);
@@ -618,7 +764,7 @@ pplbm_status pplbm_forward_stored(pplbm_ctx* c, int64_t nsteps, double* fields) 
     StepArgs a = c->args;
     a.f_in = c->fA;
     a.f_out = c->fB;
-    a.psi = fields + t * 4 * n;
+    a.psi = fields + t * field_planes(c) * n;
     a.mom = a.psi + n;
     launch_rho_psi(a, c->stream);
     launch_collide(a, c->stream);
@@ -647,7 +793,7 @@ pplbm_status pplbm_backward_stored(pplbm_ctx* c, int64_t nsteps, const double* f
   if (cudaMemsetAsync(partials, 0, sizeof(double) * nb * kNGrad, s) != cudaSuccess) return PPLBM_ERR_CUDA;
   for (int64_t t = nsteps - 1; t >= 0; --t) {
     StepArgs a = c->args;
-    a.psi = const_cast<double*>(fields) + t * 4 * n;
+    a.psi = const_cast<double*>(fields) + t * field_planes(c) * n;
     a.mom = a.psi + n;
     if (pplbm_status st = adjoint_core(c, a, cur, nxt, grad, ws, true, false)) return st;
     std::swap(cur, nxt);

@@ -45,35 +45,51 @@ extern "C" pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed
   return PPLBM_OK;
 }
 
-// FP64 issue-rate probe: every thread runs kChains independent fused multiply-add
-// chains (x <- x * b + c, |b| < 1 keeps them bounded), so the FP64 pipe is the only
-// limit; the sum of the chains goes to `sink` so that none of the work is dead.
+// FP64 issue-rate probe: every thread runs CH independent chains of one FP64
+// operation (OP 0: x <- x * b + c, 1: x <- x + c, 2: x <- x * b; |b| < 1 keeps the
+// chains bounded), so the FP64 pipe is the only limit; the sum of the chains goes to
+// `sink` so that none of the work is dead.
 namespace pplbm {
 namespace {
 
-constexpr int kChains = 8;
 constexpr int kPeakThreads = 256;
 
+template <int CH, int OP>
 __global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(long long iters, double b, double c, double* sink) {
-  double x[kChains];
+  double x[CH];
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+  for (int k = 0; k < CH; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
   for (long long it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], b, c);
+    for (int k = 0; k < CH; ++k) x[k] = OP == 0 ? fma(x[k], b, c) : OP == 1 ? x[k] + c : x[k] * b;
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) s += x[k];
+  for (int k = 0; k < CH; ++k) s += x[k];
   if (s == 12345.678) sink[0] = s;  // never true for these chains; keeps them live
+}
+
+template <int OP>
+bool launch_peak(int chains, int blocks, long long iters, double* sink, cudaStream_t s) {
+  switch (chains) {
+    case 1: k_fp64_peak<1, OP><<<blocks, kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink); return true;
+    case 2: k_fp64_peak<2, OP><<<blocks, kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink); return true;
+    case 4: k_fp64_peak<4, OP><<<blocks, kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink); return true;
+    case 8: k_fp64_peak<8, OP><<<blocks, kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink); return true;
+    case 16: k_fp64_peak<16, OP><<<blocks, kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink); return true;
+    case 32: k_fp64_peak<32, OP><<<blocks, kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink); return true;
+  }
+  return false;
 }
 
 }  // namespace
 }  // namespace pplbm
 
-extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, long long iters, double* sink, double* out,
-                                        void* stream) {
-  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out) return PPLBM_ERR_ARG;
+extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, int32_t op, long long iters,
+                                        double* sink, double* out, void* stream) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out || op < 0 || op > 2 ||
+      !(chains == 1 || chains == 2 || chains == 4 || chains == 8 || chains == 16 || chains == 32))
+    return PPLBM_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -88,7 +104,9 @@ extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, long long iters, 
   pplbm_status st = PPLBM_OK;
   float ms = 0.f;
   cudaEventRecord(e0, s);
-  pplbm::k_fp64_peak<<<blocks, pplbm::kPeakThreads, 0, s>>>(iters, 0.999999, 1e-7, sink);
+  if (op == 0) pplbm::launch_peak<0>(chains, blocks, iters, sink, s);
+  else if (op == 1) pplbm::launch_peak<1>(chains, blocks, iters, sink, s);
+  else pplbm::launch_peak<2>(chains, blocks, iters, sink, s);
   cudaEventRecord(e1, s);
   if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
       cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f))
@@ -96,8 +114,8 @@ extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, long long iters, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != PPLBM_OK) return st;
-  const double instr = (double)blocks * pplbm::kPeakThreads * (double)iters * pplbm::kChains;
-  out[0] = instr / (ms * 1e-3);  // FP64 FMA instructions (one per thread) per second
+  const double instr = (double)blocks * pplbm::kPeakThreads * (double)iters * chains;
+  out[0] = instr / (ms * 1e-3);  // FP64 instructions (one per thread) per second
   out[1] = ms;
   out[2] = (double)blocks;
   return PPLBM_OK;

@@ -33,11 +33,22 @@ __device__ __forceinline__ void rho_psi_node(const StepArgs& a, const double* __
   const int64_t N = a.n;
   const double f0 = f[i], f1 = f[N + i], f2 = f[2 * N + i], f3 = f[3 * N + i], f4 = f[4 * N + i];
   const double f5 = f[5 * N + i], f6 = f[6 * N + i], f7 = f[7 * N + i], f8 = f[8 * N + i];
-  const double sxp = f1 + f5 + f8;  // populations with c_x = +1
-  const double sxm = f3 + f6 + f7;  // c_x = -1
-  const double rho = (f0 + f2 + f4) + (sxp + sxm);
-  const double jx = sxp - sxm;
-  const double jy = (f2 + f5 + f6) - (f4 + f7 + f8);
+  double rho, jx, jy, a13 = 0.0, a24 = 0.0, a57 = 0.0, a68 = 0.0;
+  if (KIND == kShearTau) {
+    // rows 7, 8 of Eq. MatrixMRT share their pair sums with rho: 18 additions for
+    // rho, j and both stress moments (20 when formed separately)
+    a13 = f1 + f3, a24 = f2 + f4, a57 = f5 + f7, a68 = f6 + f8;
+    rho = f0 + ((a13 + a24) + (a57 + a68));
+    const double p = f5 - f7, q = f6 - f8;
+    jx = (f1 - f3) + (p - q);
+    jy = (f2 - f4) + (p + q);
+  } else {
+    const double sxp = f1 + f5 + f8;  // populations with c_x = +1
+    const double sxm = f3 + f6 + f7;  // c_x = -1
+    rho = (f0 + f2 + f4) + (sxp + sxm);
+    jx = sxp - sxm;
+    jy = (f2 + f5 + f6) - (f4 + f7 + f8);
+  }
   const double psi2 = eos_psi2_dev(a.eos, rho);
   // 0 < rho < 1e300 and 0 < psi^2 < inf, tested on the bit patterns (integer pipe)
   const long long rb = dbits(rho), pb = dbits(psi2);
@@ -48,8 +59,8 @@ __device__ __forceinline__ void rho_psi_node(const StepArgs& a, const double* __
   m[N + i] = jx;
   m[2 * N + i] = jy;
   if (KIND == kShearTau) {
-    m[3 * N + i] = (f1 + f3) - (f2 + f4);  // row 7 of Eq. MatrixMRT
-    m[4 * N + i] = (f5 + f7) - (f6 + f8);  // row 8
+    m[3 * N + i] = a13 - a24;  // row 7 of Eq. MatrixMRT
+    m[4 * N + i] = a57 - a68;  // row 8
   } else if (KIND == kFullMrt) {
     const double ax = f1 + f2 + f3 + f4, dg = f5 + f6 + f7 + f8;
     m[3 * N + i] = -4.0 * f0 - ax + 2.0 * dg;                    // row 1 (e)
@@ -123,7 +134,8 @@ __device__ __forceinline__ SurfQ surface_q(const StepArgs& a, double p0, double 
 //   Pi_xx = rho ux^2 + ux Fx = ux (P_x + h_x),  Pi_yy = uy (P_y + h_y),
 //   Pi_xy = rho ux uy + (ux Fy + uy Fx)/2 = ux P_y + uy h_x.
 // These are rows 1, 7, 8 of m* = m_eq + S/2 (Eqs. LiFS, GFS with tau = 1);
-// kShearTau relaxes rows 7, 8 with omega = 1/tau instead. Then
+// kShearTau relaxes rows 7, 8 with omega = 1/tau(rho) instead (Eq. RelaxationTime).
+// Then
 //   f*_i = w_i [rho + 3 c_i.P + 4.5 (c_i c_i - I/3) : Pi] + z_i,
 // z_i = zz (-8, 1, 1, 1, 1, 1, 1, 1, 1) being M^-1 applied to the Li sigma terms
 // +-12 sigma |F|^2 / psi^2 of rows 1 and 2 (tau_e = tau_zeta = 1), zz = sigma |F|^2 / (3 psi^2).
@@ -159,15 +171,17 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
       Pxy = fma(-sq.k, sq.xd, Pxy);  // m_8* -= Q_xy
     }
   } else {
-    // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S, with m_eq + S/2 = Pi above
+    // rows 7, 8: m* = m - omega (m - m_eq) + (1 - omega/2) S. With m_eq + S/2 the
+    // unit-tau values Pi_xx - Pi_yy and Pi_xy above, this is
+    //   m* = (m_eq + S/2) + (1 - omega) (m + S - m_eq - S/2),
+    // and the brackets reduce to m7 - ux (jx - hx) + uy (jy - hy) and m8 - ux jy + uy hx.
     const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
+    const double omc = 1.0 - om;
     const double m7 = a.mom[3 * a.n + node], m8 = a.mom[4 * a.n + node];
-    const double Jx = jx + hx, Jy = jy + hy;
-    const double meq7 = fma(ux, Jx, -uy * Jy), meq8 = ux * Jy;
-    const double s7 = 4.0 * fma(ux, hx, -uy * hy), s8 = 2.0 * fma(ux, hy, uy * hx);
-    const double hw = fma(-0.5, om, 1.0);
-    double m7s = fma(hw, s7, fma(-om, m7 - meq7, m7));
-    Pxy = fma(hw, s8, fma(-om, m8 - meq8, m8));
+    const double A7 = fma(-ux, jx - hx, fma(uy, jy - hy, m7));
+    const double A8 = fma(-ux, jy, fma(uy, hx, m8));
+    double m7s = fma(omc, A7, Pxx - Pyy);
+    Pxy = fma(omc, A8, Pxy_eq);
     if (ST) {
       const double ok = om * sq.k;
       m7s = fma(-4.0 * ok, sq.sd, m7s);  // -omega (Q_xx - Q_yy)

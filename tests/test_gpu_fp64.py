@@ -32,12 +32,13 @@ def test_fp64_peak_probe_reports_a_rate_consistent_with_its_own_timing():
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
     out = (C.c_double * 3)()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    assert L.lib().pplbm_fp64_peak(4, 20000, C.c_void_p(sink.data_ptr()), out, stream) == 0
-    rate, ms, blocks = out[0], out[1], int(out[2])
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert blocks == 4 * sms
-    assert rate == pytest.approx(blocks * 256 * 20000 * 8 / (ms * 1e-3), rel=1e-12)
-    assert 0.05e12 < rate < 1.2 * 2 * sms * 2.1e9
+    for chains, op in ((8, 0), (1, 0), (32, 0), (8, 1), (8, 2)):
+        assert L.lib().pplbm_fp64_peak(4, chains, op, 20000, C.c_void_p(sink.data_ptr()), out, stream) == 0
+        rate, ms, blocks = out[0], out[1], int(out[2])
+        assert blocks == 4 * sms
+        assert rate == pytest.approx(blocks * 256 * 20000 * chains / (ms * 1e-3), rel=1e-12)
+        assert 0.05e12 < rate < 1.2 * 2 * sms * 2.1e9
     assert sink.item() == 0.0
-    for bad in ((0, 10), (65, 10), (4, 0)):
-        assert L.lib().pplbm_fp64_peak(bad[0], bad[1], C.c_void_p(sink.data_ptr()), out, stream) == L.PPLBM_ERR_ARG
+    for bad in ((0, 8, 0, 10), (65, 8, 0, 10), (4, 8, 0, 0), (4, 3, 0, 10), (4, 8, 3, 10)):
+        assert L.lib().pplbm_fp64_peak(*bad, C.c_void_p(sink.data_ptr()), out, stream) == L.PPLBM_ERR_ARG
