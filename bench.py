@@ -52,14 +52,14 @@ MIN_BLOCKS = 5
 
 # FP64 instructions of one node update per kernel, from the kernels' arithmetic on
 # bulk nodes (unit relaxation times, Li forcing): density/psi pass 33 (moments 14,
-# C-S branch 14, sqrt 5), collision pass 51 (force 8, velocity and second moments
-# 16, reciprocal 4, Li term 3, reconstruction 20). ncu's sm__inst_executed_pipe_fp64
-# on the sweep agrees within a few percent (interface nodes take the shaped branches).
-FP64_PER_NODE = {"rho_psi": 33, "collide": 51}
-# the two-phase relaxation (rows 7, 8 relax with 1/tau(rho)), walls: the impact lattice;
-# pass 1 adds the two stress moments (6), pass 2 tau(rho) and its reciprocal (4), the
-# rows 7, 8 equilibria and sources (9) and their relaxation (7), less Pi_xy's 2
-FP64_PER_NODE_SHEAR = {"rho_psi": 39, "collide": 69}
+# C-S branch 13, sqrt 5, one compare folded), collision pass 50 (force 8, velocity
+# and second moments 18, Li term 3, reconstruction 20, reciprocal 3 ...). These are
+# the fallback; the roofline uses the counts ncu measured on the workload (COUNTS).
+FP64_PER_NODE = {"rho_psi": 33, "collide": 50}
+# the two-phase relaxation (rows 7, 8 relax with 1/tau(rho)), walls: pass 1 adds the
+# two stress moments with shared pair sums (+4), pass 2 tau(rho), its reciprocal and
+# the rows 7, 8 corrections (+14)
+FP64_PER_NODE_SHEAR = {"rho_psi": 37, "collide": 64}
 # algorithmic bytes per node of each pass as built (moments handed from pass 1 to
 # pass 2): pass 1 reads 9 f and writes psi + 3 moments (5 with tau(rho)); pass 2
 # reads the moments and the psi tile and writes 9 f
@@ -73,16 +73,20 @@ BYTES_PER_NODE_SCOPE = 232
 # agrees on the 2048 x 1024 grid)
 FD_FP64_PER_POINT = 113 + 119 + 2 * 27
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
-# batched pass on the headline workload, from an ncu capture, with the digest of the
-# kernel sources they were taken on; once those sources change, traffic is
-# reported as null until the capture is repeated.
-TRAFFIC = {"sources": None, "rho_psi": None, "collide": None}
-KERNEL_SOURCES = ("batch.cu", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
+# Per launch of each batched pass on the headline workload (all 64 lattices), from
+# one ncu capture per kernel (--metrics dram__bytes_read.sum, dram__bytes_write.sum
+# and the thread-level DFMA/DADD/DMUL counts; bench.py --profile-sweep 64): DRAM
+# bytes and FP64 instructions per node. They hold for the device code whose digest
+# is recorded with them; once it changes, traffic is null and the source counts
+# above are used until the capture is repeated.
+COUNTS = {"sources": None,
+          "rho_psi": {"dram_bytes": 1316121856, "fp64_per_node": 31.69},
+          "collide": {"dram_bytes": 1287597312, "fp64_per_node": 50.00}}
+KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
 
 
 def kernel_sources_digest():
-    """sha256 (first 16 hex digits) over the sources the batched step kernels are
+    """sha256 (first 16 hex digits) over the device code the batched step kernels are
     compiled from, in a fixed order, each preceded by its file name."""
     import hashlib
 
@@ -95,10 +99,19 @@ def kernel_sources_digest():
     return h.hexdigest()[:16]
 
 
+def counts_valid():
+    return COUNTS["sources"] is not None and COUNTS["sources"] == kernel_sources_digest()
+
+
 def pass_traffic(name):
-    if TRAFFIC["sources"] is None or TRAFFIC["sources"] != kernel_sources_digest():
-        return None
-    return TRAFFIC[name]
+    return COUNTS[name]["dram_bytes"] if counts_valid() else None
+
+
+def pass_fp64(name):
+    """(FP64 instructions per node, where the figure comes from)."""
+    if counts_valid():
+        return COUNTS[name]["fp64_per_node"], "ncu on this workload (thread-level DFMA + DADD + DMUL per node)"
+    return FP64_PER_NODE[name], "the kernel's arithmetic on bulk nodes"
 
 
 def load_peaks():
@@ -882,7 +895,7 @@ def main():
     nodes = sum(s["nx"] * s["ny"] for s in specs)
     batch, _, _, rho0s = make_batch(P, I, specs, stream)
     if args.plan == "auto":
-        plan = batch.autotune(trial_steps=20)
+        plan = batch.autotune(trial_steps=100)
     else:
         batch.set_plan({"launches": P.PLAN_LAUNCHES, "graph": P.PLAN_GRAPH,
                         "persistent": P.PLAN_PERSISTENT}[args.plan], 0)
@@ -927,19 +940,21 @@ def main():
     step_s = ms_per_step / 1e3
     mlups = nodes * args.steps / (med_ms / 1e3) / 1e6 * ws
     fp64_peak = fp64["value"]  # T FP64 instructions/s, measured above
+    fp64_node = {k: pass_fp64(k)[0] for k in ("rho_psi", "collide")}
+    fp64_src = pass_fp64("collide")[1]
     if per_pass:
         kern = {"rho_psi": pass_ms[0] / max(1, pass_n[0]), "collide": pass_ms[1] / max(1, pass_n[1])}
         dom = max(kern, key=kern.get)
         dom_s = kern[dom] / 1e3
         dom_name = {"rho_psi": "k_batch_rho_psi", "collide": "k_batch_collide"}[dom]
-        dom_flops = FP64_PER_NODE[dom] * nodes
+        dom_flops = fp64_node[dom] * nodes
         dom_bytes = BYTES_PER_NODE[dom] * nodes
         share = kern[dom] / (kern["rho_psi"] + kern["collide"])
     else:
         kern = {"persistent": call_ms / max(1, call_steps)}
         dom, dom_name, share = "persistent", "k_batch_persistent", 1.0
         dom_s = call_ms / max(1, call_steps) / 1e3
-        dom_flops = sum(FP64_PER_NODE.values()) * nodes
+        dom_flops = sum(fp64_node.values()) * nodes
         dom_bytes = sum(BYTES_PER_NODE.values()) * nodes
     achieved = dom_flops / dom_s / 1e12
     launches_per_block = 2 * args.steps if per_pass else 1
@@ -959,7 +974,7 @@ def main():
                      "traffic": pass_traffic(dom) if per_pass else None,
                      "traffic_unit": "DRAM bytes per launch (ncu capture, same kernel sources)",
                      "flop_convention": "1 per FP64 add/mul/fma instruction (per thread); "
-                                        f"{FP64_PER_NODE.get(dom, sum(FP64_PER_NODE.values()))} per node",
+                                        f"{fp64_node.get(dom, sum(fp64_node.values()))} per node ({fp64_src})",
                      "peak_source": "measured: pplbm_fp64_peak in this run (fp64_peak_measured)",
                      "launch_ms": dom_s * 1e3, "share_of_step": share},
         "kernel_ms": kern,
@@ -974,9 +989,9 @@ def main():
                            "achieved": sum(BYTES_PER_NODE.values()) * nodes / step_s / 1e9,
                            "frac": sum(BYTES_PER_NODE.values()) * nodes / step_s / 1e9 / hbm_gbs},
             "peak": hbm_gbs, "unit": "GB/s", "peak_source": peak_src},
-        "fp64_roofline_step": {"fp64_per_node": sum(FP64_PER_NODE.values()),
-                               "achieved": sum(FP64_PER_NODE.values()) * nodes / step_s / 1e12,
-                               "frac": sum(FP64_PER_NODE.values()) * nodes / step_s / 1e12 / fp64_peak},
+        "fp64_roofline_step": {"fp64_per_node": sum(fp64_node.values()),
+                               "achieved": sum(fp64_node.values()) * nodes / step_s / 1e12,
+                               "frac": sum(fp64_node.values()) * nodes / step_s / 1e12 / fp64_peak},
         "autotune_ms_per_step": {"launches": plan["ms_launches"], "graph": plan["ms_graph"],
                                  "persistent": plan["ms_persistent"]},
         "gpu_launches": launches_per_block * len(blocks),

@@ -442,14 +442,17 @@ pplbm_status pplbm_batch_get_derived(const pplbm_batch* b, int32_t i, pplbm_eos_
 pplbm_status pplbm_batch_enable_timing(pplbm_batch* b, int64_t capacity);
 pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps);
 /* Per-pass timing aid (for the roofline of each kernel). With capacity > 0, every
- * step is issued as two plain launches (the graph plan's replay is set aside while
- * this is on), each bracketed by a CUDA event pair on the batch's stream; events for
- * `capacity` steps are created here (more on demand). PPLBM_ERR_STATE under the
- * persistent plan, whose passes share one launch. capacity = 0 turns it off. The
- * autotuner times every plan without these events and turns them off if it keeps
- * the persistent plan. pplbm_batch_pass_times synchronises and returns, since the
- * previous call, the summed milliseconds and launch counts of the density/psi pass
- * (index 0) and of the collision pass (index 1), then resets them. */
+ * launch of either pass is bracketed by CUDA events on the batch's stream: under the
+ * launches plan as two plain launches per step (events for `capacity` steps are
+ * created here, more on demand); under the graph plan by event-record nodes inside
+ * ceil(capacity/2) two-step graphs per parity built here, each replayed at most once
+ * between two pplbm_batch_pass_times calls (steps beyond them run as timed plain
+ * launches). PPLBM_ERR_STATE under the persistent plan, whose passes share one
+ * launch. capacity = 0 turns it off. The autotuner times every plan without these
+ * events and turns them off if it keeps the persistent plan. pplbm_batch_pass_times
+ * synchronises and returns, since the previous call, the summed milliseconds and
+ * launch counts of the density/psi pass (index 0) and of the collision pass (index
+ * 1), then resets them. */
 pplbm_status pplbm_batch_enable_pass_timing(pplbm_batch* b, int64_t capacity);
 pplbm_status pplbm_batch_pass_times(pplbm_batch* b, double ms[2], int64_t launches[2]);
 /* Failure-detection self-test of the persistent kernel's bounded grid barrier:
