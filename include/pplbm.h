@@ -430,8 +430,10 @@ pplbm_status pplbm_batch_set_f(pplbm_batch* b, int32_t i, const double* f);
 pplbm_status pplbm_batch_set_plan(pplbm_batch* b, int32_t mode, int32_t tile_width);
 pplbm_status pplbm_batch_get_plan(const pplbm_batch* b, pplbm_batch_plan* out);
 /* Times trial_steps (>= 2) steps of each mode with per-instance and width-32 tiles
- * on the current state, keeps the fastest plan and restores the state (it
- * allocates a temporary copy of every instance's distributions). Synchronises. */
+ * on the current state, in three interleaved rounds keeping each candidate's best
+ * time, keeps the fastest plan and restores the state (it allocates a temporary copy
+ * of every instance's distributions). The plan's ms_* fields get each mode's best
+ * per-step time. Synchronises. */
 pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_batch_plan* chosen);
 /* Synchronises; sticky device error (PPLBM_ERR_DIVERGED / PPLBM_ERR_TIMEOUT) and steps issued. */
 pplbm_status pplbm_batch_sync(pplbm_batch* b, int64_t* steps_done);

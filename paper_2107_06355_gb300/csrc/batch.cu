@@ -648,37 +648,44 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
   b->pass_timing = false;
   const int modes[3] = {PPLBM_PLAN_LAUNCHES, PPLBM_PLAN_GRAPH, PPLBM_PLAN_PERSISTENT};
   const int widths[2] = {0, 32};
-  double best = 1e300;
-  int best_mode = PPLBM_PLAN_LAUNCHES, best_w = 0;
+  // three interleaved rounds over the six candidates; each keeps its best time, so a
+  // transient (a clock change, another process) does not decide the plan
+  double per[3][2];
+  for (auto& r : per) r[0] = r[1] = 1e300;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   pplbm_status st = PPLBM_OK;
-  for (int m : modes) {
-    for (int wd : widths) {
-      if ((st = apply_plan(b, m, wd)) != PPLBM_OK) break;
-      if ((st = issue_steps(b, 2, b->stream)) != PPLBM_OK) break;  // warm-up
-      cudaEventRecord(e0, b->stream);
-      if ((st = issue_steps(b, trial_steps, b->stream)) != PPLBM_OK) break;
-      cudaEventRecord(e1, b->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        st = bfail(b, PPLBM_ERR_CUDA, "autotune timing failed");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double per = ms / trial_steps;
-      if (m == PPLBM_PLAN_LAUNCHES) b->plan.ms_launches = per;
-      if (m == PPLBM_PLAN_GRAPH) b->plan.ms_graph = per;
-      if (m == PPLBM_PLAN_PERSISTENT) b->plan.ms_persistent = per;
-      if (per < best) {
-        best = per;
-        best_mode = m;
-        best_w = wd;
+  for (int round = 0; round < 3 && st == PPLBM_OK; ++round) {
+    for (int mi = 0; mi < 3 && st == PPLBM_OK; ++mi) {
+      for (int wi = 0; wi < 2; ++wi) {
+        if ((st = apply_plan(b, modes[mi], widths[wi])) != PPLBM_OK) break;
+        if ((st = issue_steps(b, 2, b->stream)) != PPLBM_OK) break;  // warm-up
+        cudaEventRecord(e0, b->stream);
+        if ((st = issue_steps(b, trial_steps, b->stream)) != PPLBM_OK) break;
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          st = bfail(b, PPLBM_ERR_CUDA, "autotune timing failed");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        per[mi][wi] = std::min(per[mi][wi], ms / trial_steps);
       }
     }
-    if (st != PPLBM_OK) break;
   }
+  double best = 1e300;
+  int best_mode = PPLBM_PLAN_LAUNCHES, best_w = 0;
+  for (int mi = 0; mi < 3; ++mi)
+    for (int wi = 0; wi < 2; ++wi)
+      if (per[mi][wi] < best) {
+        best = per[mi][wi];
+        best_mode = modes[mi];
+        best_w = widths[wi];
+      }
+  b->plan.ms_launches = std::min(per[0][0], per[0][1]);
+  b->plan.ms_graph = std::min(per[1][0], per[1][1]);
+  b->plan.ms_persistent = std::min(per[2][0], per[2][1]);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // restore the state into buffer parity0

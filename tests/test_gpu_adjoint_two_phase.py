@@ -174,7 +174,8 @@ def test_two_phase_stored_and_checkpointed_rollouts_are_bitwise_equal():
     eosp = P.EOSParams(P.EOS_SMOOTH, 0.5, 0.363, 2.0, 0.775)
     relax = P.Relax(kind=P.RELAX_TWO_PHASE, tau_l=0.6, visc_ratio=3.0, kappa=0.3)
     d = P.eos_setup(eosp)
-    rho0 = I.perturbed(I.droplet(nx, ny, 10.0, d["rho_v"], d["rho_l"], W=6.0), 0.002, 31)
+    # a drop above a film on the bottom wall (the walled set-up of Sec. IV), perturbed
+    rho0 = I.perturbed(I.impact(nx, ny, 7.0, 6, d["rho_v"], d["rho_l"], 0.0, W=6.0)[0], 0.002, 31)
     out = []
     for interval in (0, 1, 3, 6):
         spec = AD.RolloutSpec(nx, ny, P.BC_WALLS_Y, eosp, relax, nsteps, interval=interval)
