@@ -670,7 +670,7 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        per[mi][wi] = std::min(per[mi][wi], ms / trial_steps);
+        per[mi][wi] = std::min(per[mi][wi], (double)ms / trial_steps);
       }
     }
   }
