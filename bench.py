@@ -904,32 +904,44 @@ def main():
     per_pass = plan["mode"] != P.PLAN_PERSISTENT
     batch.step(args.warmup)
     torch.cuda.synchronize()
-    if per_pass:
-        batch.enable_pass_timing(args.steps)
     batch.enable_timing(1)
     acc = {"pass_ms": [0.0, 0.0], "pass_n": [0, 0], "call_ms": 0.0, "call_steps": 0}
+    state = {"timed": False}
 
-    def collect():  # after each block: the per-pass and per-call CUDA-event sums
+    def collect():
+        """After each block: the per-call (and per-pass) CUDA-event sums; then switch the
+        per-pass events on or off for the next block (outside the block's timing)."""
         ms_, n_ = batch.times()
         acc["call_ms"] += ms_
         acc["call_steps"] += n_
-        if per_pass:
+        if state["timed"]:
             (a0, a1), (n0, n1) = batch.pass_times()
             acc["pass_ms"][0] += a0
             acc["pass_ms"][1] += a1
             acc["pass_n"][0] += n0
             acc["pass_n"][1] += n1
+        if per_pass:
+            state["timed"] = not state["timed"]
+            batch.enable_pass_timing(args.steps if state["timed"] else 0)
+        kinds.append(state["timed"])
 
+    # Blocks alternate: plain (the plan as tuned: `value`) and instrumented (event
+    # records around each pass: the kernels' launch durations for the roofline).
+    kinds = [False]
     clocks = ClockSampler(local)
     clocks.start()
-    blocks = timed_blocks(torch, stream, lambda: batch.step(args.steps), barrier, after=collect)
+    blocks = timed_blocks(torch, stream, lambda: batch.step(args.steps), barrier, min_blocks=2 * MIN_BLOCKS,
+                          after=collect)
     clk = clocks.stop()
     batch.enable_timing(0)
     if per_pass:
         batch.enable_pass_timing(0)
+    kinds = kinds[:len(blocks)]
+    plain = [t for t, k in zip(blocks, kinds) if not k]
+    instrumented = [t for t, k in zip(blocks, kinds) if k]
     call_ms, call_steps = acc["call_ms"], acc["call_steps"]
     pass_ms, pass_n = acc["pass_ms"], acc["pass_n"]
-    med_ms = max_over_ranks(float(np.median(blocks)), device="cuda")  # each rank runs its own replica
+    med_ms = max_over_ranks(float(np.median(plain)), device="cuda")  # each rank runs its own replica
     batch.sync()
     g = batch.guard()
     if (g[:, 2] > 0).any():
@@ -963,12 +975,14 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattices": len(specs), "nodes_per_step": nodes,
-                   "engine": f"batched ({mode}{', per-pass CUDA events' if per_pass else ''}, tiles "
-                             f"{plan['tile_width'] or 'per-instance'})",
+                   "engine": f"batched ({mode}, tiles {plan['tile_width'] or 'per-instance'})",
                    "parallelism": f"replicas{ws}",
-                   "timing": f"median of {len(blocks)} blocks of {args.steps} steps ({sum(blocks) / 1e3:.2f} s)",
+                   "timing": f"{len(blocks)} blocks of {args.steps} steps ({sum(blocks) / 1e3:.2f} s), alternating plain "
+                             f"blocks (value: median of {len(plain)}) and blocks with per-pass CUDA events (kernel "
+                             f"durations: {len(instrumented)})",
                    "l2": "state about 2.4 GB >> 126 MB L2, no flush"},
-        "blocks_ms": blocks,
+        "blocks_ms": plain,
+        "blocks_ms_instrumented": instrumented,
         "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "traffic": pass_traffic(dom) if per_pass else None,
