@@ -505,6 +505,15 @@ void pplbm_batch_destroy(pplbm_batch* b);
  * Asynchronous on `stream`. */
 pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed, double* out, void* stream);
 
+/* Self-test of the integer-pipe addition the density pass uses for sums of positive
+ * populations (a software IEEE 754 round-to-nearest-even add, bitwise equal to the
+ * FP64 pipe's). Evaluates n seeded pairs of positive normal doubles (independent
+ * exponents, exponent gaps 0..63, half-way ties, rounding carries) and writes to the
+ * device array out[5]: out[0] = the number of results that differ from the FP64
+ * add in any bit, out[1..4] = the first such pair and the two results (bit patterns).
+ * Asynchronous on `stream`. */
+pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out, void* stream);
+
 /* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the
  * step's per-node arithmetic is double precision throughout, Sec. II; on this GPU
  * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)

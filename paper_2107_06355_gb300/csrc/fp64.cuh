@@ -12,7 +12,8 @@
 // Comparisons of non-negative doubles are done on their bit patterns as signed
 // 64-bit integers, which orders them like the doubles and runs on the integer
 // pipe. A negative or NaN operand compares as out of range, which the callers
-// treat as an error.
+// treat as an error. add_pos_int moves additions of positive doubles to the integer
+// pipe, bit for bit equal to the FP64 pipe's.
 #pragma once
 
 #include <cstdint>
@@ -49,5 +50,51 @@ __device__ __forceinline__ double fast_sqrt(double x) {
 }
 
 __device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
+
+// Sum of two positive normal doubles on the integer pipe, correctly rounded
+// (round to nearest, ties to even: IEEE 754-2008, 4.3.1), so bitwise equal to the
+// FP64 pipe's x + y. The FP64 pipe is the step kernels' bottleneck while the integer
+// pipe is nearly idle and runs beside it, so additions moved here shorten the pass.
+// Textbook method (e.g. Muller et al., Handbook of Floating-Point Arithmetic, ch. 7):
+// align the smaller significand with three extra bits (guard, round and a sticky bit
+// that ORs everything shifted out), add, renormalise by at most one place, round.
+// Both operands must be positive and normal with a normal sum (callers check their
+// inputs with all_positive_normal); pplbm_int_add_selftest compares it with the FP64
+// add bit for bit.
+__device__ __forceinline__ double add_pos_int(double x, double y) {
+  typedef unsigned long long u64;
+  const u64 a = (u64)__double_as_longlong(x), b = (u64)__double_as_longlong(y);
+  const u64 hi = a > b ? a : b, lo = a > b ? b : a;  // positive doubles order like their bits
+  const int eh = (int)(hi >> 52);
+  const int d = min(eh - (int)(lo >> 52), 63);
+  const u64 H = 1ull << 52, M = H - 1;
+  const u64 mh = ((hi & M) | H) << 3;  // significands with 3 extra bits, < 2^56
+  const u64 ml = ((lo & M) | H) << 3;
+  const u64 sh = ml >> d;
+  u64 m = mh + (sh | (u64)((sh << d) != ml));  // the sticky bit: anything shifted out
+  const u64 ov = m >> 56;                         // 1 if the sum carried into bit 56
+  m = (m >> ov) | (m & ov);
+  const u64 low = m & 7;                          // guard, round, sticky
+  m >>= 3;
+  m += (low > 4) | ((low == 4) & (m & 1));        // ties to even
+  // a carry out of the significand (m == 2^53) moves into the exponent field
+  return __longlong_as_double((long long)((((u64)(eh + (int)ov)) << 52) + (m - H)));
+}
+
+// True if every value is a positive normal double below 2^1000 (so add_pos_int
+// applies to them and to sums of a few of them): the sign bits ORed, and the smallest
+// and largest high words against that range.
+template <int K>
+__device__ __forceinline__ bool all_positive_normal(const double (&v)[K]) {
+  unsigned int orh = 0, mn = 0xFFFFFFFFu, mx = 0u;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const unsigned int h = (unsigned int)__double2hiint(v[k]);
+    orh |= h;
+    mn = min(mn, h);
+    mx = max(mx, h);
+  }
+  return !(orh >> 31) && mn >= 0x00100000u && mx < 0x7EF00000u;
+}
 
 }  // namespace pplbm

@@ -33,6 +33,37 @@ __global__ void k_fp64_selftest(long long n, unsigned long long seed, unsigned l
   atomicMax(&out[1], (unsigned long long)__double_as_longlong(es));
 }
 
+// add_pos_int against the FP64 pipe's x + y, bit for bit. Four kinds of pairs:
+// independent exponents around 1; exponent gaps 0..63; low bits of the smaller
+// operand forced to a half-way pattern (ties, both parities); the larger operand's
+// significand all ones (rounding carries into the exponent).
+__global__ void k_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out) {
+  typedef unsigned long long u64;
+  const u64 M = (1ull << 52) - 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const u64 h = splitmix64(seed ^ (u64)i), g = splitmix64(h);
+    const int kind = (int)(h & 3);
+    const u64 ea = 1023 - 40 + ((h >> 2) & 63);
+    u64 eb = 1023 - 40 + ((g >> 2) & 63);
+    u64 ma = (h >> 8) & M, mb = (g >> 8) & M;
+    if (kind == 1 || kind == 2) eb = ea - ((g >> 58) & 63);
+    if (kind == 2) {
+      const int d = (int)(ea - eb);
+      if (d >= 1 && d <= 52) mb = (mb & ~((1ull << d) - 1)) | (1ull << (d - 1));  // half an ulp of a, exactly
+    }
+    if (kind == 3) ma = M;
+    const u64 a = (ea << 52) | ma, b = (eb << 52) | mb;
+    const double x = __longlong_as_double((long long)a), y = __longlong_as_double((long long)b);
+    const u64 got = (u64)__double_as_longlong(add_pos_int(x, y)), want = (u64)__double_as_longlong(x + y);
+    if (got != want && atomicAdd(&out[0], 1ull) == 0ull) {
+      out[1] = a;
+      out[2] = b;
+      out[3] = got;
+      out[4] = want;
+    }
+  }
+}
+
 }  // namespace
 }  // namespace pplbm
 
@@ -118,5 +149,15 @@ extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, i
   out[0] = instr / (ms * 1e-3);  // FP64 instructions (one per thread) per second
   out[1] = ms;
   out[2] = (double)blocks;
+  return PPLBM_OK;
+}
+
+extern "C" pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out,
+                                               void* stream) {
+  if (n < 1 || !out) return PPLBM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(out, 0, 5 * sizeof(unsigned long long), s) != cudaSuccess) return PPLBM_ERR_CUDA;
+  pplbm::k_int_add_selftest<<<1216, 256, 0, s>>>(n, seed, out);
+  if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   return PPLBM_OK;
 }

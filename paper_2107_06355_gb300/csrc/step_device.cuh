@@ -34,14 +34,31 @@ __device__ __forceinline__ void rho_psi_node(const StepArgs& a, const double* __
   const double f0 = f[i], f1 = f[N + i], f2 = f[2 * N + i], f3 = f[3 * N + i], f4 = f[4 * N + i];
   const double f5 = f[5 * N + i], f6 = f[6 * N + i], f7 = f[7 * N + i], f8 = f[8 * N + i];
   double rho, jx, jy, a13 = 0.0, a24 = 0.0, a57 = 0.0, a68 = 0.0;
+  // The sums of positive populations run on the integer pipe (add_pos_int, bitwise
+  // the FP64 add) when all nine are positive normal doubles, which leaves the FP64
+  // pipe, the pass's bottleneck, the differences and the EOS; otherwise the same sums
+  // in the same order on the FP64 pipe. Either way the results are identical.
+  const double fv[9] = {f0, f1, f2, f3, f4, f5, f6, f7, f8};
+  const bool ip = KIND != kFullMrt && all_positive_normal(fv);
   if (KIND == kShearTau) {
     // rows 7, 8 of Eq. MatrixMRT share their pair sums with rho: 18 additions for
     // rho, j and both stress moments (20 when formed separately)
-    a13 = f1 + f3, a24 = f2 + f4, a57 = f5 + f7, a68 = f6 + f8;
-    rho = f0 + ((a13 + a24) + (a57 + a68));
+    if (ip) {
+      a13 = add_pos_int(f1, f3), a24 = add_pos_int(f2, f4), a57 = add_pos_int(f5, f7), a68 = add_pos_int(f6, f8);
+      rho = add_pos_int(f0, add_pos_int(add_pos_int(a13, a24), add_pos_int(a57, a68)));
+    } else {
+      a13 = f1 + f3, a24 = f2 + f4, a57 = f5 + f7, a68 = f6 + f8;
+      rho = f0 + ((a13 + a24) + (a57 + a68));
+    }
     const double p = f5 - f7, q = f6 - f8;
     jx = (f1 - f3) + (p - q);
     jy = (f2 - f4) + (p + q);
+  } else if (ip) {
+    const double sxp = add_pos_int(add_pos_int(f1, f5), f8);  // populations with c_x = +1
+    const double sxm = add_pos_int(add_pos_int(f3, f6), f7);  // c_x = -1
+    rho = add_pos_int(add_pos_int(add_pos_int(f0, f2), f4), add_pos_int(sxp, sxm));
+    jx = sxp - sxm;
+    jy = add_pos_int(add_pos_int(f2, f5), f6) - add_pos_int(add_pos_int(f4, f7), f8);
   } else {
     const double sxp = f1 + f5 + f8;  // populations with c_x = +1
     const double sxm = f3 + f6 + f7;  // c_x = -1

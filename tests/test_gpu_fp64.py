@@ -42,3 +42,18 @@ def test_fp64_peak_probe_reports_a_rate_consistent_with_its_own_timing():
     assert sink.item() == 0.0
     for bad in ((0, 8, 0, 10), (65, 8, 0, 10), (4, 8, 0, 0), (4, 3, 0, 10), (4, 8, 3, 10)):
         assert L.lib().pplbm_fp64_peak(*bad, C.c_void_p(sink.data_ptr()), out, stream) == L.PPLBM_ERR_ARG
+
+
+def test_integer_pipe_addition_is_bitwise_the_fp64_add():
+    """add_pos_int (the density pass's sums of positive populations on the integer
+    pipe) against the FP64 pipe's x + y on 2^30 seeded pairs: random exponents,
+    exponent gaps 0..63, exact ties and rounding carries; no bit may differ."""
+    from paper_2107_06355_gb300 import _lib as L
+
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
+    st = L.lib().pplbm_int_add_selftest(1 << 30, 20260, C.c_void_p(out.data_ptr()),
+                                        C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    bad = out.tolist()
+    assert bad[0] == 0, [hex(v & (2**64 - 1)) for v in bad]
