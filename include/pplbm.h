@@ -505,13 +505,14 @@ void pplbm_batch_destroy(pplbm_batch* b);
  * Asynchronous on `stream`. */
 pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed, double* out, void* stream);
 
-/* Self-test of the integer-pipe addition the density pass uses for sums of positive
- * populations (a software IEEE 754 round-to-nearest-even add, bitwise equal to the
- * FP64 pipe's). Evaluates n seeded pairs of positive normal doubles (independent
- * exponents, exponent gaps 0..63, half-way ties, rounding carries) and writes to the
- * device array out[5]: out[0] = the number of results that differ from the FP64
- * add in any bit, out[1..4] = the first such pair and the two results (bit patterns).
- * Asynchronous on `stream`. */
+/* Self-test of the integer-pipe additions the step kernels use to unload the FP64
+ * pipe (software IEEE 754 round-to-nearest-even adds, bitwise equal to the FP64
+ * pipe's): the positive-operand sum of the density pass and the signed add of the
+ * collision pass. Evaluates n seeded pairs (independent exponents, exponent gaps
+ * 0..63, half-way ties, rounding carries; for the signed add every sign combination
+ * and operands 0..7 ulp apart) and writes to the device array out[5]: out[0] = the
+ * number of results that differ from the FP64 add in any bit, out[1..4] = the first
+ * such pair and the two results (bit patterns). Asynchronous on `stream`. */
 pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out, void* stream);
 
 /* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the

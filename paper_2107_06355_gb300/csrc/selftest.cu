@@ -33,10 +33,12 @@ __global__ void k_fp64_selftest(long long n, unsigned long long seed, unsigned l
   atomicMax(&out[1], (unsigned long long)__double_as_longlong(es));
 }
 
-// add_pos_int against the FP64 pipe's x + y, bit for bit. Four kinds of pairs:
-// independent exponents around 1; exponent gaps 0..63; low bits of the smaller
+// add_pos_int and add_int against the FP64 pipe's x + y, bit for bit. Four kinds of
+// pairs: independent exponents around 1; exponent gaps 0..63; low bits of the smaller
 // operand forced to a half-way pattern (ties, both parities); the larger operand's
-// significand all ones (rounding carries into the exponent).
+// significand all ones (rounding carries into the exponent). add_int also sees every
+// sign combination and, in the last kind, operands 0..7 ulp apart (exact and near
+// cancellation).
 __global__ void k_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out) {
   typedef unsigned long long u64;
   const u64 M = (1ull << 52) - 1;
@@ -54,12 +56,26 @@ __global__ void k_int_add_selftest(long long n, unsigned long long seed, unsigne
     if (kind == 3) ma = M;
     const u64 a = (ea << 52) | ma, b = (eb << 52) | mb;
     const double x = __longlong_as_double((long long)a), y = __longlong_as_double((long long)b);
-    const u64 got = (u64)__double_as_longlong(add_pos_int(x, y)), want = (u64)__double_as_longlong(x + y);
+    const u64 want = (u64)__double_as_longlong(x + y);
+    const u64 got = (u64)__double_as_longlong(add_pos_int(x, y));
     if (got != want && atomicAdd(&out[0], 1ull) == 0ull) {
       out[1] = a;
       out[2] = b;
       out[3] = got;
       out[4] = want;
+    }
+    // add_int on the same magnitudes with every sign combination, and on a pair that
+    // cancels exactly or up to the last bits (x + (-x), x + (-(x + k ulp)))
+    const u64 sa = (g >> 60) & 1, sb = (g >> 61) & 1;
+    const u64 a2 = a | (sa << 63), b2 = (kind == 3 ? (a + ((g >> 56) & 7)) : b) | (sb << 63);
+    const double x2 = __longlong_as_double((long long)a2), y2 = __longlong_as_double((long long)b2);
+    const u64 want2 = (u64)__double_as_longlong(x2 + y2);
+    const u64 got2 = (u64)__double_as_longlong(add_int(x2, y2));
+    if (got2 != want2 && atomicAdd(&out[0], 1ull) == 0ull) {
+      out[1] = a2;
+      out[2] = b2;
+      out[3] = got2;
+      out[4] = want2;
     }
   }
 }

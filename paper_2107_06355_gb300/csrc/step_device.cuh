@@ -163,15 +163,17 @@ template <int KIND, bool ST = false>
 __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node, double rho, double jx, double jy,
                                                 double psi0, double gx, double gy, const SurfQ& sq, Post& out,
                                                 double* ux_o, double* uy_o) {
+  // Additions run on the integer pipe (add_int, bitwise the FP64 add): the FP64
+  // pipe, this pass's bottleneck, keeps the products and fused multiply-adds.
   const double cH = a.half_force * psi0;  // h = cH g, cH = -G psi / 24
   const double hx = cH * gx, hy = cH * gy;
   const double inv_rho = fast_rcp(rho);
-  const double ux = (jx + hx) * inv_rho, uy = (jy + hy) * inv_rho;
+  const double ux = add_int(jx, hx) * inv_rho, uy = add_int(jy, hy) * inv_rho;
   *ux_o = ux;
   *uy_o = uy;
   const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
-  const double Pxx = ux * (Px + hx), Pyy = uy * (Py + hy);
-  const double tr = Pxx + Pyy;
+  const double Pxx = ux * add_int(Px, hx), Pyy = uy * add_int(Py, hy);
+  const double tr = add_int(Pxx, Pyy);
   const double Pxy_eq = fma(ux, Py, uy * hx);
   double zz = a.zz_scale * fma(gx, gx, gy * gy);
   if (ST) zz = fma(sq.k, sq.t, zz);  // + tr Q / 24
@@ -193,11 +195,11 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
     //   m* = (m_eq + S/2) + (1 - omega) (m + S - m_eq - S/2),
     // and the brackets reduce to m7 - ux (jx - hx) + uy (jy - hy) and m8 - ux jy + uy hx.
     const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
-    const double omc = 1.0 - om;
+    const double omc = add_int(1.0, -om);
     const double m7 = a.mom[3 * a.n + node], m8 = a.mom[4 * a.n + node];
-    const double A7 = fma(-ux, jx - hx, fma(uy, jy - hy, m7));
+    const double A7 = fma(-ux, add_int(jx, -hx), fma(uy, add_int(jy, -hy), m7));
     const double A8 = fma(-ux, jy, fma(uy, hx, m8));
-    double m7s = fma(omc, A7, Pxx - Pyy);
+    double m7s = fma(omc, A7, add_int(Pxx, -Pyy));
     Pxy = fma(omc, A8, Pxy_eq);
     if (ST) {
       const double ok = om * sq.k;
@@ -215,7 +217,7 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
   out.f[4] = fma(-Py, 1.0 / 3.0, ayp);
   const double Dq = fma(fma(3.0, tr, rho), 1.0 / 36.0, zz);
   const double dp = fma(0.25, Pxy, Dq), dm = fma(-0.25, Pxy, Dq);
-  const double ps = Px + Py, pd = Py - Px;
+  const double ps = add_int(Px, Py), pd = add_int(Py, -Px);
   out.f[5] = fma(ps, 1.0 / 12.0, dp);
   out.f[7] = fma(-ps, 1.0 / 12.0, dp);
   out.f[6] = fma(pd, 1.0 / 12.0, dm);
@@ -305,10 +307,11 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   const double p0 = sp[c];
   const double pE = sp[c + 1], pW = sp[c - 1], pN = sp[c + sw], pS = sp[c - sw];
   const double pNE = sp[c + sw + 1], pNW = sp[c + sw - 1], pSW = sp[c - sw - 1], pSE = sp[c - sw + 1];
-  // 12 * sum_i w(|c_i|^2) psi(x + c_i) c_i  (w = 1/3 axis, 1/12 diagonal)
-  const double d1 = pNE - pSW, d2 = pSE - pNW;
-  const double gx = fma(4.0, pE - pW, d1 + d2);
-  const double gy = fma(4.0, pN - pS, d1 - d2);
+  // 12 * sum_i w(|c_i|^2) psi(x + c_i) c_i  (w = 1/3 axis, 1/12 diagonal); the
+  // differences on the integer pipe (add_int: bitwise the FP64 add)
+  const double d1 = add_int(pNE, -pSW), d2 = add_int(pSE, -pNW);
+  const double gx = fma(4.0, add_int(pE, -pW), add_int(d1, d2));
+  const double gy = fma(4.0, add_int(pN, -pS), add_int(d1, -d2));
   const int64_t N = a.n;
   const int64_t node = (int64_t)y * a.nx + x;
   Post o;
