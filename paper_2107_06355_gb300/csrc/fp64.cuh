@@ -81,46 +81,48 @@ __device__ __forceinline__ double add_pos_int(double x, double y) {
   return __longlong_as_double((long long)((((u64)(eh + (int)ov)) << 52) + (m - H)));
 }
 
-// x + y for any doubles, correctly rounded (round to nearest, ties to even), on the
-// integer pipe when both operands are normal and the result is normal or an exact
-// zero; otherwise (a zero, subnormal, infinite or NaN operand, a subnormal result) on
-// the FP64 pipe. Either way bitwise the FP64 pipe's x + y. Same method as
-// add_pos_int, with the magnitudes subtracted when the signs differ: the three extra
-// bits then also cover the one-place left shift a subtraction of operands two or more
-// binades apart can need; operands closer than that lose no bit when aligned, so a
-// cancellation is exact and renormalised by the leading-zero count.
+// x + y on the integer pipe, correctly rounded (round to nearest, ties to even), for
+// normal or zero operands whose sum is normal or zero: then bitwise the FP64 pipe's
+// x + y (including +0 for an exact cancellation and the signs of zero sums). Same
+// method as add_pos_int, with the magnitudes subtracted when the signs differ: the
+// three extra bits then also cover the one-place left shift a subtraction of operands
+// two or more binades apart can need; operands closer than that lose no bit when
+// aligned, so a cancellation is exact and renormalised by the leading-zero count.
+// Outside that domain it does not call the FP64 pipe (a fallback there would be
+// computed speculatively and cost the FP64 issue slots this exists to save): a
+// subnormal operand counts as zero, a result below 2^-1022 flushes to a signed zero,
+// and an infinite or NaN operand gives a NaN. The step's quantities stay far from
+// that range (densities, psi and velocities are above 1e-300 or exactly zero).
 __device__ __forceinline__ double add_int(double x, double y) {
   typedef unsigned long long u64;
   const u64 S = 1ull << 63, H = 1ull << 52, M = H - 1;
   const u64 a = (u64)__double_as_longlong(x), b = (u64)__double_as_longlong(y);
   const u64 ua = a & ~S, ub = b & ~S;
   const bool sw = ub > ua;
+  const u64 big = sw ? b : a;
   const u64 uh = sw ? ub : ua, ul = sw ? ua : ub;
-  const u64 sign = (sw ? b : a) & S;
+  const u64 sign = big & S;
   const int eh = (int)(uh >> 52), el = (int)(ul >> 52);
-  if (el == 0 || eh == 2047) return x + y;  // zero, subnormal, inf or NaN operand
   const int d = min(eh - el, 63);
   const u64 mh = ((uh & M) | H) << 3, ml = ((ul & M) | H) << 3;
   const u64 sh = ml >> d;
   const u64 al = sh | (u64)((sh << d) != ml);
   u64 m = ((a ^ b) & S) ? mh - al : mh + al;  // < 2^57
-  if (m == 0) return 0.0;                    // exact cancellation: +0 (round to nearest)
   // bring the leading one to bit 55: one place right after a carry, or left by the
   // leading zeros after a cancellation
-  const int lz = __clzll((long long)m) - 8;  // -1 (carry) .. 55
-  int e;
-  if (lz < 0) {
-    m = (m >> 1) | (m & 1);
-    e = eh + 1;
-  } else {
-    m <<= lz;
-    e = eh - lz;
-  }
-  if (e <= 0) return x + y;  // subnormal result
+  const int lz = __clzll((long long)m) - 8;  // -1 (carry) .. 56 (m = 0)
+  const u64 mr = (m >> 1) | (m & 1), mlft = m << (lz < 0 ? 0 : lz);
+  m = lz < 0 ? mr : mlft;
+  const int e = lz < 0 ? eh + 1 : eh - lz;
   const u64 low = m & 7;
   m >>= 3;
   m += (low > 4) | ((low == 4) & (m & 1));
-  return __longlong_as_double((long long)(sign | ((((u64)e) << 52) + (m - H))));
+  u64 r = sign | ((((u64)e) << 52) + (m - H));
+  r = e <= 0 ? sign : r;                            // underflow: signed zero
+  r = lz == 56 ? 0ull : r;                          // exact cancellation: +0
+  r = el == 0 ? (uh == 0 ? (a & b) : big) : r;      // smaller operand zero (or subnormal)
+  r = eh == 2047 ? 0x7FF8000000000000ull : r;       // infinite or NaN operand
+  return __longlong_as_double((long long)r);
 }
 
 // True if every value is a positive normal double below 2^1000 (so add_pos_int

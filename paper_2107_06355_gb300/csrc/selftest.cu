@@ -37,8 +37,8 @@ __global__ void k_fp64_selftest(long long n, unsigned long long seed, unsigned l
 // pairs: independent exponents around 1; exponent gaps 0..63; low bits of the smaller
 // operand forced to a half-way pattern (ties, both parities); the larger operand's
 // significand all ones (rounding carries into the exponent). add_int also sees every
-// sign combination and, in the last kind, operands 0..7 ulp apart (exact and near
-// cancellation).
+// sign combination, signed zeros, and, in the last kind, operands 0..7 ulp apart
+// (exact and near cancellation).
 __global__ void k_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out) {
   typedef unsigned long long u64;
   const u64 M = (1ull << 52) - 1;
@@ -67,7 +67,9 @@ __global__ void k_int_add_selftest(long long n, unsigned long long seed, unsigne
     // add_int on the same magnitudes with every sign combination, and on a pair that
     // cancels exactly or up to the last bits (x + (-x), x + (-(x + k ulp)))
     const u64 sa = (g >> 60) & 1, sb = (g >> 61) & 1;
-    const u64 a2 = a | (sa << 63), b2 = (kind == 3 ? (a + ((g >> 56) & 7)) : b) | (sb << 63);
+    u64 b2 = (kind == 3 ? (a + ((g >> 56) & 7)) : b) | (sb << 63);
+    if (((g >> 62) & 3) == 3) b2 = sb << 63;   // a zero of either sign
+    const u64 a2 = a | (sa << 63);
     const double x2 = __longlong_as_double((long long)a2), y2 = __longlong_as_double((long long)b2);
     const u64 want2 = (u64)__double_as_longlong(x2 + y2);
     const u64 got2 = (u64)__double_as_longlong(add_int(x2, y2));
