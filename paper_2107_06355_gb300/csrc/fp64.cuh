@@ -51,6 +51,20 @@ __device__ __forceinline__ double fast_sqrt(double x) {
 
 __device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
 
+// Bit patterns in and out through an opaque move, so that the optimiser does not
+// recognise the integer masks below as FP64 operations (an AND with ~sign is fabs, an
+// XOR of the sign is a negation) and move them back onto the FP64 pipe.
+__device__ __forceinline__ unsigned long long opaque_bits(double x) {
+  unsigned long long r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double opaque_double(unsigned long long r) {
+  double x;
+  asm("mov.b64 %0, %1;" : "=d"(x) : "l"(r));
+  return x;
+}
+
 // Sum of two positive normal doubles on the integer pipe, correctly rounded
 // (round to nearest, ties to even: IEEE 754-2008, 4.3.1), so bitwise equal to the
 // FP64 pipe's x + y. The FP64 pipe is the step kernels' bottleneck while the integer
@@ -63,7 +77,7 @@ __device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong
 // add bit for bit.
 __device__ __forceinline__ double add_pos_int(double x, double y) {
   typedef unsigned long long u64;
-  const u64 a = (u64)__double_as_longlong(x), b = (u64)__double_as_longlong(y);
+  const u64 a = opaque_bits(x), b = opaque_bits(y);
   const u64 hi = a > b ? a : b, lo = a > b ? b : a;  // positive doubles order like their bits
   const int eh = (int)(hi >> 52);
   const int d = min(eh - (int)(lo >> 52), 63);
@@ -78,25 +92,25 @@ __device__ __forceinline__ double add_pos_int(double x, double y) {
   m >>= 3;
   m += (low > 4) | ((low == 4) & (m & 1));        // ties to even
   // a carry out of the significand (m == 2^53) moves into the exponent field
-  return __longlong_as_double((long long)((((u64)(eh + (int)ov)) << 52) + (m - H)));
+  return opaque_double((((u64)(eh + (int)ov)) << 52) + (m - H));
 }
 
-// x + y on the integer pipe, correctly rounded (round to nearest, ties to even), for
-// normal or zero operands whose sum is normal or zero: then bitwise the FP64 pipe's
-// x + y (including +0 for an exact cancellation and the signs of zero sums). Same
-// method as add_pos_int, with the magnitudes subtracted when the signs differ: the
-// three extra bits then also cover the one-place left shift a subtraction of operands
-// two or more binades apart can need; operands closer than that lose no bit when
-// aligned, so a cancellation is exact and renormalised by the leading-zero count.
-// Outside that domain it does not call the FP64 pipe (a fallback there would be
-// computed speculatively and cost the FP64 issue slots this exists to save): a
-// subnormal operand counts as zero, a result below 2^-1022 flushes to a signed zero,
-// and an infinite or NaN operand gives a NaN. The step's quantities stay far from
-// that range (densities, psi and velocities are above 1e-300 or exactly zero).
-__device__ __forceinline__ double add_int(double x, double y) {
+// The sum of the doubles with bit patterns a and b on the integer pipe, correctly
+// rounded (round to nearest, ties to even), for normal or zero operands whose sum is
+// normal or zero: then bitwise the FP64 pipe's sum (including +0 for an exact
+// cancellation and the signs of zero sums). Same method as add_pos_int, with the
+// magnitudes subtracted when the signs differ: the three extra bits then also cover
+// the one-place left shift a subtraction of operands two or more binades apart can
+// need; operands closer than that lose no bit when aligned, so a cancellation is exact
+// and renormalised by the leading-zero count. Outside that domain it does not call
+// the FP64 pipe (a fallback there would be computed speculatively and cost the FP64
+// issue slots this exists to save): a subnormal operand counts as zero, a result below
+// 2^-1022 flushes to a signed zero, and an infinite or NaN operand gives a NaN. The
+// step's quantities stay far from that range (densities, psi and velocities are above
+// 1e-300 or exactly zero).
+__device__ __forceinline__ double add_bits_int(unsigned long long a, unsigned long long b) {
   typedef unsigned long long u64;
   const u64 S = 1ull << 63, H = 1ull << 52, M = H - 1;
-  const u64 a = (u64)__double_as_longlong(x), b = (u64)__double_as_longlong(y);
   const u64 ua = a & ~S, ub = b & ~S;
   const bool sw = ub > ua;
   const u64 big = sw ? b : a;
@@ -118,11 +132,17 @@ __device__ __forceinline__ double add_int(double x, double y) {
   m >>= 3;
   m += (low > 4) | ((low == 4) & (m & 1));
   u64 r = sign | ((((u64)e) << 52) + (m - H));
-  r = e <= 0 ? sign : r;                            // underflow: signed zero
-  r = lz == 56 ? 0ull : r;                          // exact cancellation: +0
-  r = el == 0 ? (uh == 0 ? (a & b) : big) : r;      // smaller operand zero (or subnormal)
-  r = eh == 2047 ? 0x7FF8000000000000ull : r;       // infinite or NaN operand
-  return __longlong_as_double((long long)r);
+  r = e <= 0 ? sign : r;                        // underflow: signed zero
+  r = lz == 56 ? 0ull : r;                      // exact cancellation: +0
+  r = el == 0 ? (uh == 0 ? (a & b) : big) : r;  // smaller operand zero (or subnormal)
+  r = eh == 2047 ? 0x7FF8000000000000ull : r;   // infinite or NaN operand
+  return opaque_double(r);
+}
+
+// x + y and x - y on the integer pipe (add_bits_int; the sign of y flipped in its bits)
+__device__ __forceinline__ double add_int(double x, double y) { return add_bits_int(opaque_bits(x), opaque_bits(y)); }
+__device__ __forceinline__ double sub_int(double x, double y) {
+  return add_bits_int(opaque_bits(x), opaque_bits(y) ^ (1ull << 63));
 }
 
 // True if every value is a positive normal double below 2^1000 (so add_pos_int

@@ -73,6 +73,14 @@ __global__ void k_int_add_selftest(long long n, unsigned long long seed, unsigne
     const double x2 = __longlong_as_double((long long)a2), y2 = __longlong_as_double((long long)b2);
     const u64 want2 = (u64)__double_as_longlong(x2 + y2);
     const u64 got2 = (u64)__double_as_longlong(add_int(x2, y2));
+    // and the subtraction x2 - (-y2), the same sum through sub_int
+    const u64 got3 = (u64)__double_as_longlong(sub_int(x2, -y2));
+    if (got3 != want2 && atomicAdd(&out[0], 1ull) == 0ull) {
+      out[1] = a2;
+      out[2] = b2 ^ (1ull << 63);
+      out[3] = got3;
+      out[4] = want2;
+    }
     if (got2 != want2 && atomicAdd(&out[0], 1ull) == 0ull) {
       out[1] = a2;
       out[2] = b2;

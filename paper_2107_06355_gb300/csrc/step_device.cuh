@@ -195,11 +195,11 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
     //   m* = (m_eq + S/2) + (1 - omega) (m + S - m_eq - S/2),
     // and the brackets reduce to m7 - ux (jx - hx) + uy (jy - hy) and m8 - ux jy + uy hx.
     const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
-    const double omc = add_int(1.0, -om);
+    const double omc = sub_int(1.0, om);
     const double m7 = a.mom[3 * a.n + node], m8 = a.mom[4 * a.n + node];
-    const double A7 = fma(-ux, add_int(jx, -hx), fma(uy, add_int(jy, -hy), m7));
+    const double A7 = fma(-ux, sub_int(jx, hx), fma(uy, sub_int(jy, hy), m7));
     const double A8 = fma(-ux, jy, fma(uy, hx, m8));
-    double m7s = fma(omc, A7, add_int(Pxx, -Pyy));
+    double m7s = fma(omc, A7, sub_int(Pxx, Pyy));
     Pxy = fma(omc, A8, Pxy_eq);
     if (ST) {
       const double ok = om * sq.k;
@@ -217,7 +217,7 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
   out.f[4] = fma(-Py, 1.0 / 3.0, ayp);
   const double Dq = fma(fma(3.0, tr, rho), 1.0 / 36.0, zz);
   const double dp = fma(0.25, Pxy, Dq), dm = fma(-0.25, Pxy, Dq);
-  const double ps = add_int(Px, Py), pd = add_int(Py, -Px);
+  const double ps = add_int(Px, Py), pd = sub_int(Py, Px);
   out.f[5] = fma(ps, 1.0 / 12.0, dp);
   out.f[7] = fma(-ps, 1.0 / 12.0, dp);
   out.f[6] = fma(pd, 1.0 / 12.0, dm);
@@ -309,9 +309,9 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   const double pNE = sp[c + sw + 1], pNW = sp[c + sw - 1], pSW = sp[c - sw - 1], pSE = sp[c - sw + 1];
   // 12 * sum_i w(|c_i|^2) psi(x + c_i) c_i  (w = 1/3 axis, 1/12 diagonal); the
   // differences on the integer pipe (add_int: bitwise the FP64 add)
-  const double d1 = add_int(pNE, -pSW), d2 = add_int(pSE, -pNW);
-  const double gx = fma(4.0, add_int(pE, -pW), add_int(d1, d2));
-  const double gy = fma(4.0, add_int(pN, -pS), add_int(d1, -d2));
+  const double d1 = sub_int(pNE, pSW), d2 = sub_int(pSE, pNW);
+  const double gx = fma(4.0, sub_int(pE, pW), add_int(d1, d2));
+  const double gy = fma(4.0, sub_int(pN, pS), sub_int(d1, d2));
   const int64_t N = a.n;
   const int64_t node = (int64_t)y * a.nx + x;
   Post o;
