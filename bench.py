@@ -51,15 +51,23 @@ MIN_TIMED_S = 1.5
 MIN_BLOCKS = 5
 
 # FP64 instructions of one node update per kernel, from the kernels' arithmetic on
-# bulk nodes (unit relaxation times, Li forcing): density/psi pass 33 (moments 14,
-# C-S branch 13, sqrt 5, one compare folded), collision pass 50 (force 8, velocity
-# and second moments 18, Li term 3, reconstruction 20, reciprocal 3 ...). These are
-# the fallback; the roofline uses the counts ncu measured on the workload (COUNTS).
-FP64_PER_NODE = {"rho_psi": 33, "collide": 50}
+# bulk nodes (unit relaxation times, Li forcing), counting what runs on the FP64 pipe:
+# the density pass 21 (moments 2 differences, C-S branch 13, sqrt 5, one compare
+# folded; its 12 sums of positive populations run on the integer pipe), the collision
+# pass 37 (11 products, 26 fused multiply-adds; its 13 additions run on the integer
+# pipe). These are the fallback; the roofline uses the counts ncu measured on the
+# workload (COUNTS).
+FP64_PER_NODE = {"rho_psi": 21, "collide": 37}
+# integer-pipe (ALU) instructions per node of the same passes (ncu; fallback figures)
+ALU_PER_NODE = {"rho_psi": 629, "collide": 1199}
+# ALU pipe issue rate: 64 thread instructions per SM per clock (ncu's
+# sm__pipe_alu_cycles_active scale: 82.7 % active at 16.6e12 instructions/s)
+ALU_PER_SM_CLK = 64
 # the two-phase relaxation (rows 7, 8 relax with 1/tau(rho)), walls: pass 1 adds the
-# two stress moments with shared pair sums (+4), pass 2 tau(rho), its reciprocal and
-# the rows 7, 8 corrections (+14)
-FP64_PER_NODE_SHEAR = {"rho_psi": 37, "collide": 64}
+# two stress moments with shared pair sums (its 8 positive sums on the integer pipe),
+# pass 2 tau(rho), its reciprocal and the rows 7, 8 corrections (its 17 additions on
+# the integer pipe)
+FP64_PER_NODE_SHEAR = {"rho_psi": 29, "collide": 47}
 # algorithmic bytes per node of each pass as built (moments handed from pass 1 to
 # pass 2): pass 1 reads 9 f and writes psi + 3 moments (5 with tau(rho)); pass 2
 # reads the moments and the psi tile and writes 9 f
@@ -74,14 +82,15 @@ BYTES_PER_NODE_SCOPE = 232
 FD_FP64_PER_POINT = 113 + 119 + 2 * 27
 
 # Per launch of each batched pass on the headline workload (all 64 lattices), from
-# one ncu capture per kernel (--metrics dram__bytes_read.sum, dram__bytes_write.sum
-# and the thread-level DFMA/DADD/DMUL counts; bench.py --profile-sweep 64): DRAM
-# bytes and FP64 instructions per node. They hold for the device code whose digest
-# is recorded with them; once it changes, traffic is null and the source counts
-# above are used until the capture is repeated.
-COUNTS = {"sources": "8d708b8c492084bf",
-          "rho_psi": {"dram_bytes": 1316156160, "fp64_per_node": 31.687},
-          "collide": {"dram_bytes": 1288777472, "fp64_per_node": 50.000}}
+# one ncu capture per kernel (--metrics dram__bytes_read.sum, dram__bytes_write.sum,
+# the thread-level DFMA/DADD/DMUL counts and sm__inst_executed_pipe_alu.sum;
+# bench.py --profile-sweep 64): DRAM bytes per launch, FP64 and ALU instructions per
+# node. They hold for the device code whose digest is recorded with them; once it
+# changes, traffic is null and the source counts above are used until the capture is
+# repeated.
+COUNTS = {"sources": "b0b1ffbeb1915797",
+          "rho_psi": {"dram_bytes": 1319260928, "fp64_per_node": 19.687, "alu_per_node": 629.3},
+          "collide": {"dram_bytes": 1289154048, "fp64_per_node": 37.000, "alu_per_node": 1199.3}}
 KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
 
 
@@ -112,6 +121,10 @@ def pass_fp64(name):
     if counts_valid():
         return COUNTS[name]["fp64_per_node"], "ncu on this workload (thread-level DFMA + DADD + DMUL per node)"
     return FP64_PER_NODE[name], "the kernel's arithmetic on bulk nodes"
+
+
+def pass_alu(name):
+    return COUNTS[name]["alu_per_node"] if counts_valid() else ALU_PER_NODE[name]
 
 
 def load_peaks():
@@ -1000,6 +1013,13 @@ def main():
                      "peak_source": "measured: pplbm_fp64_peak in this run (fp64_peak_measured)",
                      "launch_ms": dom_s * 1e3, "share_of_step": share},
         "kernel_ms": kern,
+        "int_pipe": {"kernel": dom_name, "alu_per_node": pass_alu(dom) if per_pass else None,
+                     "achieved": (pass_alu(dom) * nodes / dom_s / 1e12) if per_pass else None,
+                     "peak": ALU_PER_SM_CLK * 152 * (clk.get("sm_mhz") or sm_max) * 1e6 / 1e12,
+                     "unit": "T integer instr/s",
+                     "frac": (pass_alu(dom) * nodes / dom_s / (ALU_PER_SM_CLK * 152 * (clk.get("sm_mhz") or sm_max)
+                                                                * 1e6)) if per_pass else None,
+                     "note": "the pass's additions run on the integer pipe (bitwise the FP64 add), beside the FP64 pipe"},
         "fp64_peak_measured": fp64,
         "roofline_hbm": {
             "dominant_kernel": {"achieved": dom_bytes / dom_s / 1e9, "frac": dom_bytes / dom_s / 1e9 / hbm_gbs,
