@@ -307,7 +307,7 @@ def fp64_probe_sweep(torch, local):
     out = (C.c_double * 3)()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     variants = [(8, 8, 0), (4, 8, 0), (2, 8, 0), (1, 8, 0), (8, 1, 0), (8, 2, 0), (8, 4, 0), (8, 16, 0),
-                (4, 32, 0), (8, 8, 1), (8, 8, 2)]
+                (4, 32, 0), (8, 8, 1), (8, 8, 2), (8, 8, 3), (8, 8, 4), (8, 4, 3), (8, 4, 4)]
     L.check(lib.pplbm_fp64_peak(8, 8, 0, 4000, C.c_void_p(sink.data_ptr()), out, stream))
     clocks = ClockSampler(local, "sweep")
     clocks.start()
@@ -315,8 +315,9 @@ def fp64_probe_sweep(torch, local):
     for bpsm, ch, op in variants:
         iters = max(1000, int(160000 * 8 / (bpsm * ch)))
         L.check(lib.pplbm_fp64_peak(bpsm, ch, op, iters, C.c_void_p(sink.data_ptr()), out, stream))
-        rows.append({"blocks_per_sm": bpsm, "chains": ch, "op": ("fma", "add", "mul")[op], "rate": out[0] / 1e12,
-                     "ms": out[1]})
+        rows.append({"blocks_per_sm": bpsm, "chains": ch,
+                     "op": ("fma", "add", "mul", "integer-pipe add", "fma + integer-pipe add")[op],
+                     "rate": out[0] / 1e12, "ms": out[1]})
     clk = clocks.stop()
     mhz = clk["sm_mhz"] or 2070.0
     for r in rows:

@@ -520,10 +520,13 @@ pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsign
  * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)
  * blocks of 256 threads; each thread runs `iters` rounds of `chains` (1, 2, 4, 8,
  * 16 or 32) independent chains of one FP64 operation: op 0 fused multiply-add,
- * 1 add, 2 multiply. Times the launch with CUDA events on `stream` and
- * synchronises it. Writes to host out[3]: out[0] = FP64 instructions per second
- * (counted per thread, as the step's per-node instruction counts are), out[1] =
- * the launch's milliseconds, out[2] = blocks launched. `sink` is one device double
+ * 1 add, 2 multiply; op 3 runs chains of the integer-pipe addition the step kernels
+ * use instead, op 4 one FMA and one integer-pipe addition per chain and round (the
+ * same time as op 0 means the two pipes overlap). Times the launch with CUDA events
+ * on `stream` and synchronises it. Writes to host out[3]: out[0] = FP64
+ * instructions per second (op 3: integer-pipe additions per second; counted per
+ * thread, as the step's per-node instruction counts are), out[1] = the launch's
+ * milliseconds, out[2] = blocks launched. `sink` is one device double
  * the kernel may write (it never does for these inputs; it keeps the chains from
  * being optimised away). PPLBM_ERR_ARG for blocks_per_sm outside [1, 64], another
  * chain count or op, iters < 1 or NULL pointers. */

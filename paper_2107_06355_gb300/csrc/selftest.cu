@@ -104,8 +104,10 @@ extern "C" pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed
 
 // FP64 issue-rate probe: every thread runs CH independent chains of one FP64
 // operation (OP 0: x <- x * b + c, 1: x <- x + c, 2: x <- x * b; |b| < 1 keeps the
-// chains bounded), so the FP64 pipe is the only limit; the sum of the chains goes to
-// `sink` so that none of the work is dead.
+// chains bounded), so the FP64 pipe is the only limit; OP 3 runs chains of the
+// integer-pipe addition add_pos_int instead (y <- y + c), and OP 4 both, one FMA and
+// one integer-pipe addition per chain and round (whether the two pipes overlap). The
+// sum of the chains goes to `sink` so that none of the work is dead.
 namespace pplbm {
 namespace {
 
@@ -113,16 +115,24 @@ constexpr int kPeakThreads = 256;
 
 template <int CH, int OP>
 __global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(long long iters, double b, double c, double* sink) {
-  double x[CH];
+  double x[CH], y[CH];
 #pragma unroll
-  for (int k = 0; k < CH; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+  for (int k = 0; k < CH; ++k) {
+    x[k] = (double)(threadIdx.x + k) * 1e-3;
+    y[k] = 1.0 + x[k];
+  }
   for (long long it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < CH; ++k) x[k] = OP == 0 ? fma(x[k], b, c) : OP == 1 ? x[k] + c : x[k] * b;
+    for (int k = 0; k < CH; ++k) {
+      if (OP == 0 || OP == 4) x[k] = fma(x[k], b, c);
+      if (OP == 1) x[k] = x[k] + c;
+      if (OP == 2) x[k] = x[k] * b;
+      if (OP == 3 || OP == 4) y[k] = add_pos_int(y[k], c);
+    }
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < CH; ++k) s += x[k];
+  for (int k = 0; k < CH; ++k) s += x[k] + y[k];
   if (s == 12345.678) sink[0] = s;  // never true for these chains; keeps them live
 }
 
@@ -144,7 +154,7 @@ bool launch_peak(int chains, int blocks, long long iters, double* sink, cudaStre
 
 extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, int32_t op, long long iters,
                                         double* sink, double* out, void* stream) {
-  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out || op < 0 || op > 2 ||
+  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out || op < 0 || op > 4 ||
       !(chains == 1 || chains == 2 || chains == 4 || chains == 8 || chains == 16 || chains == 32))
     return PPLBM_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -163,7 +173,9 @@ extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, i
   cudaEventRecord(e0, s);
   if (op == 0) pplbm::launch_peak<0>(chains, blocks, iters, sink, s);
   else if (op == 1) pplbm::launch_peak<1>(chains, blocks, iters, sink, s);
-  else pplbm::launch_peak<2>(chains, blocks, iters, sink, s);
+  else if (op == 2) pplbm::launch_peak<2>(chains, blocks, iters, sink, s);
+  else if (op == 3) pplbm::launch_peak<3>(chains, blocks, iters, sink, s);
+  else pplbm::launch_peak<4>(chains, blocks, iters, sink, s);
   cudaEventRecord(e1, s);
   if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
       cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f))
@@ -172,7 +184,7 @@ extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, i
   cudaEventDestroy(e1);
   if (st != PPLBM_OK) return st;
   const double instr = (double)blocks * pplbm::kPeakThreads * (double)iters * chains;
-  out[0] = instr / (ms * 1e-3);  // FP64 instructions (one per thread) per second
+  out[0] = instr / (ms * 1e-3);  // FP64 instructions (op 3: integer-pipe additions) per thread per second
   out[1] = ms;
   out[2] = (double)blocks;
   return PPLBM_OK;

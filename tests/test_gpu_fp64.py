@@ -40,7 +40,14 @@ def test_fp64_peak_probe_reports_a_rate_consistent_with_its_own_timing():
         assert rate == pytest.approx(blocks * 256 * 20000 * chains / (ms * 1e-3), rel=1e-12)
         assert 0.05e12 < rate < 1.2 * 2 * sms * 2.1e9
     assert sink.item() == 0.0
-    for bad in ((0, 8, 0, 10), (65, 8, 0, 10), (4, 8, 0, 0), (4, 3, 0, 10), (4, 8, 3, 10)):
+    # the integer-pipe additions run beside the FP64 FMAs: both together take no longer
+    # than the slower of the two alone (within 10 %)
+    t = {}
+    for op in (0, 3, 4):
+        assert L.lib().pplbm_fp64_peak(8, 8, op, 20000, C.c_void_p(sink.data_ptr()), out, stream) == 0
+        t[op] = out[1]
+    assert t[4] < 1.1 * max(t[0], t[3])
+    for bad in ((0, 8, 0, 10), (65, 8, 0, 10), (4, 8, 0, 0), (4, 3, 0, 10), (4, 8, 5, 10)):
         assert L.lib().pplbm_fp64_peak(*bad, C.c_void_p(sink.data_ptr()), out, stream) == L.PPLBM_ERR_ARG
 
 
