@@ -67,7 +67,7 @@ ALU_PER_SM_CLK = 64
 # two stress moments with shared pair sums (its 8 positive sums on the integer pipe),
 # pass 2 tau(rho), its reciprocal and the rows 7, 8 corrections (its 17 additions on
 # the integer pipe)
-FP64_PER_NODE_SHEAR = {"rho_psi": 29, "collide": 47}
+FP64_PER_NODE_SHEAR = {"rho_psi": 28, "collide": 48}  # ncu on the impact lattice: 27.84, 48.00
 # algorithmic bytes per node of each pass as built (moments handed from pass 1 to
 # pass 2): pass 1 reads 9 f and writes psi + 3 moments (5 with tau(rho)); pass 2
 # reads the moments and the psi tile and writes 9 f
