@@ -81,38 +81,38 @@ __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double r
   const double cH = a.half_force * psi0;
   const double hx = cH * gx, hy = cH * gy;
   const double inv = fast_rcp(rho);
-  const double Jx = jx + hx, Jy = jy + hy;
+  const double Jx = add_int(jx, hx), Jy = add_int(jy, hy);
   const double ux = Jx * inv, uy = Jy * inv;
   const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
   const double g2 = fma(gx, gx, gy * gy);
   // reverse
-  const double dp_b = mu[5] + mu[7], ps_b = (mu[5] - mu[7]) * (1.0 / 12.0);
-  const double dm_b = mu[6] + mu[8], pd_b = (mu[6] - mu[8]) * (1.0 / 12.0);
-  const double Dq_b = dp_b + dm_b;
-  const double Pxy_b = 0.25 * (dp_b - dm_b);
+  const double dp_b = add_int(mu[5], mu[7]), ps_b = sub_int(mu[5], mu[7]) * (1.0 / 12.0);
+  const double dm_b = add_int(mu[6], mu[8]), pd_b = sub_int(mu[6], mu[8]) * (1.0 / 12.0);
+  const double Dq_b = add_int(dp_b, dm_b);
+  const double Pxy_b = 0.25 * sub_int(dp_b, dm_b);
   const double D_b = Dq_b * (1.0 / 36.0);
   double zz_b = Dq_b;
   double r_b = D_b;
   double tr_b = 3.0 * D_b;
-  const double axp_b = mu[1] + mu[3], ayp_b = mu[2] + mu[4];
-  double Px_b = (mu[1] - mu[3]) * (1.0 / 3.0) + (ps_b - pd_b);
-  double Py_b = (mu[2] - mu[4]) * (1.0 / 3.0) + (ps_b + pd_b);
-  const double Q_b = axp_b + ayp_b;
+  const double axp_b = add_int(mu[1], mu[3]), ayp_b = add_int(mu[2], mu[4]);
+  double Px_b = fma(sub_int(mu[1], mu[3]), 1.0 / 3.0, sub_int(ps_b, pd_b));
+  double Py_b = fma(sub_int(mu[2], mu[4]), 1.0 / 3.0, add_int(ps_b, pd_b));
+  const double Q_b = add_int(axp_b, ayp_b);
   double Pxx_b = 0.5 * axp_b, Pyy_b = 0.5 * ayp_b;
   const double B0_b = (4.0 / 9.0) * mu[0] + Q_b * (1.0 / 9.0);
-  zz_b += Q_b - 8.0 * mu[0];
-  r_b += B0_b;
+  zz_b = add_int(zz_b, fma(-8.0, mu[0], Q_b));
+  r_b = add_int(r_b, B0_b);
   tr_b += -1.5 * B0_b;
-  Pxx_b += tr_b;
-  Pyy_b += tr_b;
+  Pxx_b = add_int(Pxx_b, tr_b);
+  Pyy_b = add_int(Pyy_b, tr_b);
   // Pxy = ux Py + uy hx
   double ux_b = Pxy_b * Py, uy_b = Pxy_b * hx, hx_b = Pxy_b * uy;
   Py_b += Pxy_b * ux;
   // Pxx = ux (Px + hx), Pyy = uy (Py + hy)
-  ux_b += Pxx_b * (Px + hx);
+  ux_b = fma(Pxx_b, add_int(Px, hx), ux_b);
   Px_b += Pxx_b * ux;
   hx_b += Pxx_b * ux;
-  uy_b += Pyy_b * (Py + hy);
+  uy_b = fma(Pyy_b, add_int(Py, hy), uy_b);
   Py_b += Pyy_b * uy;
   double hy_b = Pyy_b * uy;
   // Px = jx + 2 hx, Py = jy + 2 hy
@@ -122,10 +122,10 @@ __device__ __forceinline__ void collide_unit_reverse(const StepArgs& a, double r
   // ux = Jx inv, uy = Jy inv
   const double Jx_b = ux_b * inv, Jy_b = uy_b * inv;
   const double inv_b = ux_b * Jx + uy_b * Jy;
-  jx_bb += Jx_b;
-  hx_b += Jx_b;
-  jy_bb += Jy_b;
-  hy_b += Jy_b;
+  jx_bb = add_int(jx_bb, Jx_b);
+  hx_b = add_int(hx_b, Jx_b);
+  jy_bb = add_int(jy_bb, Jy_b);
+  hy_b = add_int(hy_b, Jy_b);
   r_b += -inv_b * inv * inv;
   // zz = zs g2
   const double zs = a.zz_scale;
@@ -165,33 +165,33 @@ __device__ __forceinline__ void collide_shear_reverse(const StepArgs& a, double 
   const double cH = a.half_force * psi0;
   const double hx = cH * gx, hy = cH * gy;
   const double inv = fast_rcp(rho);
-  const double Jx = jx + hx, Jy = jy + hy;
+  const double Jx = add_int(jx, hx), Jy = add_int(jy, hy);
   const double ux = Jx * inv, uy = Jy * inv;
   const double Px = fma(2.0, hx, jx), Py = fma(2.0, hy, jy);
   const double g2 = fma(gx, gx, gy * gy);
   const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
-  const double omc = 1.0 - om;
-  const double Kx = jx - hx, Ky = jy - hy;
+  const double omc = sub_int(1.0, om);
+  const double Kx = sub_int(jx, hx), Ky = sub_int(jy, hy);
   const double A7 = fma(-ux, Kx, fma(uy, Ky, m7));
   const double A8 = fma(-ux, jy, fma(uy, hx, m8));
   // reverse: population-space reconstruction
-  const double dp_b = mu[5] + mu[7], ps_b = (mu[5] - mu[7]) * (1.0 / 12.0);
-  const double dm_b = mu[6] + mu[8], pd_b = (mu[6] - mu[8]) * (1.0 / 12.0);
-  const double Dq_b = dp_b + dm_b;
-  const double Pxy_b = 0.25 * (dp_b - dm_b);
+  const double dp_b = add_int(mu[5], mu[7]), ps_b = sub_int(mu[5], mu[7]) * (1.0 / 12.0);
+  const double dm_b = add_int(mu[6], mu[8]), pd_b = sub_int(mu[6], mu[8]) * (1.0 / 12.0);
+  const double Dq_b = add_int(dp_b, dm_b);
+  const double Pxy_b = 0.25 * sub_int(dp_b, dm_b);
   double zz_b = Dq_b;
   double r_b = Dq_b * (1.0 / 36.0);
   double tr_b = Dq_b * (1.0 / 12.0);
-  const double axp_b = mu[1] + mu[3], ayp_b = mu[2] + mu[4];
-  double Px_b = (mu[1] - mu[3]) * (1.0 / 3.0) + (ps_b - pd_b);
-  double Py_b = (mu[2] - mu[4]) * (1.0 / 3.0) + (ps_b + pd_b);
+  const double axp_b = add_int(mu[1], mu[3]), ayp_b = add_int(mu[2], mu[4]);
+  double Px_b = fma(sub_int(mu[1], mu[3]), 1.0 / 3.0, sub_int(ps_b, pd_b));
+  double Py_b = fma(sub_int(mu[2], mu[4]), 1.0 / 3.0, add_int(ps_b, pd_b));
   // axp, ayp = T4 +- m7*/4, T4 = Q + tr/4
-  const double T4_b = axp_b + ayp_b;
-  const double m7s_b = 0.25 * (axp_b - ayp_b);
+  const double T4_b = add_int(axp_b, ayp_b);
+  const double m7s_b = 0.25 * sub_int(axp_b, ayp_b);
   tr_b += 0.25 * T4_b;
   const double B0_b = (4.0 / 9.0) * mu[0] + T4_b * (1.0 / 9.0);
-  zz_b += T4_b - 8.0 * mu[0];
-  r_b += B0_b;
+  zz_b = add_int(zz_b, fma(-8.0, mu[0], T4_b));
+  r_b = add_int(r_b, B0_b);
   tr_b += -1.5 * B0_b;
   // rows 7, 8 (and the source's terms)
   const double A8_b = Pxy_b * omc, A7_b = m7s_b * omc;
@@ -205,7 +205,7 @@ __device__ __forceinline__ void collide_shear_reverse(const StepArgs& a, double 
     om_b -= sq->k * w;
   }
   r_b += -om_b * om * om * a.tau_b;  // d omega / d rho = -tau_b omega^2
-  const double Pxx_b = m7s_b + tr_b, Pyy_b = tr_b - m7s_b;
+  const double Pxx_b = add_int(m7s_b, tr_b), Pyy_b = sub_int(tr_b, m7s_b);
   // A8 = m8 - ux jy + uy hx
   double ux_b = -A8_b * jy, uy_b = A8_b * hx, hx_b = A8_b * uy;
   double jx_bb = 0.0, jy_bb = -A8_b * ux;
@@ -222,24 +222,24 @@ __device__ __forceinline__ void collide_shear_reverse(const StepArgs& a, double 
   uy_b += Pxy_b * hx;
   hx_b += Pxy_b * uy;
   // Pi_xx = ux (Px + hx), Pi_yy = uy (Py + hy)
-  ux_b += Pxx_b * (Px + hx);
+  ux_b = fma(Pxx_b, add_int(Px, hx), ux_b);
   Px_b += Pxx_b * ux;
   hx_b += Pxx_b * ux;
-  uy_b += Pyy_b * (Py + hy);
+  uy_b = fma(Pyy_b, add_int(Py, hy), uy_b);
   Py_b += Pyy_b * uy;
   hy_b += Pyy_b * uy;
   // Px = jx + 2 hx, Py = jy + 2 hy
-  jx_bb += Px_b;
+  jx_bb = add_int(jx_bb, Px_b);
   hx_b += 2.0 * Px_b;
-  jy_bb += Py_b;
+  jy_bb = add_int(jy_bb, Py_b);
   hy_b += 2.0 * Py_b;
   // ux = Jx inv, uy = Jy inv
   const double Jx_b = ux_b * inv, Jy_b = uy_b * inv;
   const double inv_b = ux_b * Jx + uy_b * Jy;
-  jx_bb += Jx_b;
-  hx_b += Jx_b;
-  jy_bb += Jy_b;
-  hy_b += Jy_b;
+  jx_bb = add_int(jx_bb, Jx_b);
+  hx_b = add_int(hx_b, Jx_b);
+  jy_bb = add_int(jy_bb, Jy_b);
+  hy_b = add_int(hy_b, Jy_b);
   r_b += -inv_b * inv * inv;
   // zz = zs g2
   const double zs = a.zz_scale;
@@ -460,11 +460,12 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
   if (x < a.nx && y < a.ny) {
     const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
     // transpose of g = 12 sum_c w_c psi(x + c) c, gathered at this node y
-    const double pg = 4.0 * (sx[c - 1] - sx[c + 1]) + 4.0 * (sy[c - sw] - sy[c + sw]) +
-                      (sx[c - sw - 1] + sy[c - sw - 1]) - (sx[c + sw + 1] + sy[c + sw + 1]) +
-                      (sx[c + sw - 1] - sy[c + sw - 1]) - (sx[c - sw + 1] - sy[c - sw + 1]);
+    const double q1 = add_int(sx[c - sw - 1], sy[c - sw - 1]), q2 = add_int(sx[c + sw + 1], sy[c + sw + 1]);
+    const double q3 = sub_int(sx[c + sw - 1], sy[c + sw - 1]), q4 = sub_int(sx[c - sw + 1], sy[c - sw + 1]);
+    const double pg = fma(4.0, sub_int(sx[c - 1], sx[c + 1]),
+                          fma(4.0, sub_int(sy[c - sw], sy[c + sw]), add_int(sub_int(q1, q2), sub_int(q3, q4))));
     const int64_t N = a.n, node = (int64_t)y * a.nx + x;
-    double psi_b = g.bar[3 * N + node] + pg;
+    double psi_b = add_int(g.bar[3 * N + node], pg);
     if constexpr (ST) {
       // transposes of t = (axis sum)/6 + (diagonal sum)/12 - psi(x), sd = (pE + pW) - (pN + pS),
       // xd = (pNE + pSW) - (pNW + pSE) at the neighbours (the -psi(x) term is A1's)
@@ -498,19 +499,32 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
     if (liq_side)
       for (int k = a2_index(G_K1L); k <= a2_index(G_K4L); ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
-    // the stress moments of the two-phase set: rows 7, 8 of Eq. MatrixMRT
-    const double m7b = KIND == kShearTau ? g.bar[9 * N + node] : 0.0;
-    const double m8b = KIND == kShearTau ? g.bar[10 * N + node] : 0.0;
+    // lambda^t_i = rho_bar + c_i . j_bar (+ rows 7, 8 of Eq. MatrixMRT times the stress
+    // moments' adjoints with the two-phase set), the sums on the integer pipe
+    const double rp = add_int(rho_b, jxb), rm = sub_int(rho_b, jxb);
+    double l1 = rp, l2 = add_int(rho_b, jyb), l3 = rm, l4 = sub_int(rho_b, jyb);
+    double l5 = add_int(rp, jyb), l6 = add_int(rm, jyb), l7 = sub_int(rm, jyb), l8 = sub_int(rp, jyb);
+    if (KIND == kShearTau) {
+      const double m7b = g.bar[9 * N + node], m8b = g.bar[10 * N + node];
+      l1 = add_int(l1, m7b);
+      l2 = sub_int(l2, m7b);
+      l3 = add_int(l3, m7b);
+      l4 = sub_int(l4, m7b);
+      l5 = add_int(l5, m8b);
+      l6 = sub_int(l6, m8b);
+      l7 = add_int(l7, m8b);
+      l8 = sub_int(l8, m8b);
+    }
     double* L0 = g.lam0;
     L0[node] = rho_b;
-    L0[N + node] = rho_b + jxb + m7b;
-    L0[2 * N + node] = rho_b + jyb - m7b;
-    L0[3 * N + node] = rho_b - jxb + m7b;
-    L0[4 * N + node] = rho_b - jyb - m7b;
-    L0[5 * N + node] = rho_b + jxb + jyb + m8b;
-    L0[6 * N + node] = rho_b - jxb + jyb - m8b;
-    L0[7 * N + node] = rho_b - jxb - jyb + m8b;
-    L0[8 * N + node] = rho_b + jxb - jyb - m8b;
+    L0[N + node] = l1;
+    L0[2 * N + node] = l2;
+    L0[3 * N + node] = l3;
+    L0[4 * N + node] = l4;
+    L0[5 * N + node] = l5;
+    L0[6 * N + node] = l6;
+    L0[7 * N + node] = l7;
+    L0[8 * N + node] = l8;
   }
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   double* dst = g.partial2 + (int64_t)blk * kA2;
