@@ -500,20 +500,21 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
       for (int k = a2_index(G_K1L); k <= a2_index(G_K4L); ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
     // lambda^t_i = rho_bar + c_i . j_bar (+ rows 7, 8 of Eq. MatrixMRT times the stress
-    // moments' adjoints with the two-phase set), the sums on the integer pipe
-    const double rp = add_int(rho_b, jxb), rm = sub_int(rho_b, jxb);
-    double l1 = rp, l2 = add_int(rho_b, jyb), l3 = rm, l4 = sub_int(rho_b, jyb);
-    double l5 = add_int(rp, jyb), l6 = add_int(rm, jyb), l7 = sub_int(rm, jyb), l8 = sub_int(rp, jyb);
+    // moments' adjoints with the two-phase set). These sums stay on the FP64 pipe: with
+    // the stencil's on the integer pipe, this pass has more integer than FP64 work.
+    const double rp = rho_b + jxb, rm = rho_b - jxb;
+    double l1 = rp, l2 = rho_b + jyb, l3 = rm, l4 = rho_b - jyb;
+    double l5 = rp + jyb, l6 = rm + jyb, l7 = rm - jyb, l8 = rp - jyb;
     if (KIND == kShearTau) {
       const double m7b = g.bar[9 * N + node], m8b = g.bar[10 * N + node];
-      l1 = add_int(l1, m7b);
-      l2 = sub_int(l2, m7b);
-      l3 = add_int(l3, m7b);
-      l4 = sub_int(l4, m7b);
-      l5 = add_int(l5, m8b);
-      l6 = sub_int(l6, m8b);
-      l7 = add_int(l7, m8b);
-      l8 = sub_int(l8, m8b);
+      l1 += m7b;
+      l2 -= m7b;
+      l3 += m7b;
+      l4 -= m7b;
+      l5 += m8b;
+      l6 -= m8b;
+      l7 += m8b;
+      l8 -= m8b;
     }
     double* L0 = g.lam0;
     L0[node] = rho_b;
