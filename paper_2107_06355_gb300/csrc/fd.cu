@@ -30,6 +30,7 @@
 
 #include "../../include/pplbm.h"
 #include "eos_dev.cuh"
+#include "fp64.cuh"
 #include "internal.h"
 
 namespace pplbm {
@@ -135,34 +136,39 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   auto at = [&](const double* f, int dx, int dy) { return f[ry[dy + 2] + cx[dx + 2]]; };
   // one-sided first difference along x (axis 0) or y (axis 1): forward in the
   // predictor, backward in the corrector; true derivative = h D
+  // The stencil sums and differences run on the integer pipe (add_int / sub_int,
+  // bitwise the FP64 add), about as many as balance it against the FP64 pipe, which
+  // keeps the products, the fused multiply-adds and the final combinations.
   auto D1 = [&](const double* f, int axis) {
     const double c = at(f, 0, 0);
-    if (PRED) return axis == 0 ? at(f, 1, 0) - c : at(f, 0, 1) - c;
-    return axis == 0 ? c - at(f, -1, 0) : c - at(f, 0, -1);
+    if (PRED) return axis == 0 ? sub_int(at(f, 1, 0), c) : sub_int(at(f, 0, 1), c);
+    return axis == 0 ? sub_int(c, at(f, -1, 0)) : sub_int(c, at(f, 0, -1));
   };
   // central second differences: d_xx = h^2 Dxx, d_xy = (h^2/4) Dxy
-  auto Dxx = [&](const double* f) { return (at(f, 1, 0) + at(f, -1, 0)) - 2.0 * at(f, 0, 0); };
-  auto Dyy = [&](const double* f) { return (at(f, 0, 1) + at(f, 0, -1)) - 2.0 * at(f, 0, 0); };
-  auto Dxy = [&](const double* f) { return (at(f, 1, 1) - at(f, 1, -1)) - (at(f, -1, 1) - at(f, -1, -1)); };
+  auto Dxx = [&](const double* f) { return fma(-2.0, at(f, 0, 0), add_int(at(f, 1, 0), at(f, -1, 0))); };
+  auto Dyy = [&](const double* f) { return fma(-2.0, at(f, 0, 0), add_int(at(f, 0, 1), at(f, 0, -1))); };
+  auto Dxy = [&](const double* f) {
+    return sub_int(sub_int(at(f, 1, 1), at(f, 1, -1)), sub_int(at(f, -1, 1), at(f, -1, -1)));
+  };
   const double rho = at(a.rho, 0, 0), ux = at(a.ux, 0, 0), uy = at(a.uy, 0, 0);
   // mass: d_t rho = -(rho div u + u . grad rho)
   const double Dr0 = D1(a.rho, 0), Dr1 = D1(a.rho, 1);
   const double Du00 = D1(a.ux, 0), Du01 = D1(a.uy, 0);  // Du_ab: d_a u_b
   const double Du10 = D1(a.ux, 1), Du11 = D1(a.uy, 1);
-  const double Dv = Du00 + Du11, Sh = Du01 + Du10;
+  const double Dv = add_int(Du00, Du11), Sh = add_int(Du01, Du10);
   const double drho = -a.cA * fma(rho, Dv, fma(ux, Dr0, uy * Dr1));
   // psi: dpsi = (h/2) Pd, d_ab psi from Dxx, Dyy, Dxy, lap = h^2 Lc, and the
   // derivative of lap psi = (h^3/2) DL from the 5-point sums at +-1
   const double* ps = a.psi;
   const double psi = at(ps, 0, 0);
-  const double Pd0 = at(ps, 1, 0) - at(ps, -1, 0), Pd1 = at(ps, 0, 1) - at(ps, 0, -1);
+  const double Pd0 = sub_int(at(ps, 1, 0), at(ps, -1, 0)), Pd1 = sub_int(at(ps, 0, 1), at(ps, 0, -1));
   const double Pxx = Dxx(ps), Pyy = Dyy(ps), q = 0.25 * Dxy(ps);
-  const double Lc = Pxx + Pyy;
+  const double Lc = add_int(Pxx, Pyy);
   auto L5 = [&](int ox, int oy) {
-    return ((at(ps, ox + 1, oy) + at(ps, ox - 1, oy)) + (at(ps, ox, oy + 1) + at(ps, ox, oy - 1))) -
-           4.0 * at(ps, ox, oy);
+    return fma(-4.0, at(ps, ox, oy),
+               add_int(add_int(at(ps, ox + 1, oy), at(ps, ox - 1, oy)), add_int(at(ps, ox, oy + 1), at(ps, ox, oy - 1))));
   };
-  const double DL0 = L5(1, 0) - L5(-1, 0), DL1 = L5(0, 1) - L5(0, -1);
+  const double DL0 = sub_int(L5(1, 0), L5(-1, 0)), DL1 = sub_int(L5(0, 1), L5(0, -1));
   // d_b p'_ab (Eq. FDforce) = (h^3/2) [(G/6 - eps G/4) S_a + (G/12) Pd_a Lc + (G/4) psi DL_a],
   // S_a = sum_g Pd_g (d_a d_g psi in the same units)
   const double S0 = fma(Pd0, Pxx, q * Pd1), S1 = fma(Pd1, Pyy, q * Pd0);
