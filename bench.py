@@ -52,14 +52,13 @@ MIN_BLOCKS = 5
 
 # FP64 instructions of one node update per kernel, from the kernels' arithmetic on
 # bulk nodes (unit relaxation times, Li forcing), counting what runs on the FP64 pipe:
-# the density pass 21 (moments 2 differences, C-S branch 13, sqrt 5, one compare
-# folded; its 12 sums of positive populations run on the integer pipe), the collision
-# pass 37 (11 products, 26 fused multiply-adds; its 13 additions run on the integer
-# pipe). These are the fallback; the roofline uses the counts ncu measured on the
-# workload (COUNTS).
-FP64_PER_NODE = {"rho_psi": 21, "collide": 37}
+# the density pass 18 (C-S branch 13, sqrt 5; its moments are integer sums in one
+# fixed-point frame), the collision pass 35 (11 products, 24 fused multiply-adds; its
+# force stencil in fixed point and its 7 other additions on the integer pipe). These
+# are the fallback; the roofline uses the counts ncu measured on the workload (COUNTS).
+FP64_PER_NODE = {"rho_psi": 18, "collide": 35}
 # integer-pipe (ALU) instructions per node of the same passes (ncu; fallback figures)
-ALU_PER_NODE = {"rho_psi": 629, "collide": 1199}
+ALU_PER_NODE = {"rho_psi": 223, "collide": 855}
 # ALU pipe issue rate: 64 thread instructions per SM per clock (ncu's
 # sm__pipe_alu_cycles_active scale: 82.7 % active at 16.6e12 instructions/s)
 ALU_PER_SM_CLK = 64
@@ -76,10 +75,13 @@ BYTES_PER_NODE_SHEAR = {"rho_psi": 72 + 48, "collide": 40 + 8 + 72}
 # the scope table's algorithmic count for the pull design: 72 + 8 (pass 1) and
 # 72 + 8 + 72 (pass 2) bytes per node
 BYTES_PER_NODE_SCOPE = 232
-# FP64 instructions of one MacCormack step per grid point: predictor 113, corrector
-# 119, two EOS passes of 27 (the kernels' arithmetic; ncu's sm__inst_executed_pipe_fp64
-# agrees on the 2048 x 1024 grid)
-FD_FP64_PER_POINT = 113 + 119 + 2 * 27
+# FP64-pipe and integer-pipe (ALU) instructions of one MacCormack step per grid point
+# (ncu, sm__inst_executed_pipe_fp64 / _alu x 32 per point, one kernel per capture, the
+# 2048 x 1024 grid of fd_throughput): predictor 65.0 / 3,653, corrector 71.0 / 3,672,
+# two EOS passes of 24.9 / 11; the update kernels' stencil sums and differences run on
+# the integer pipe, which binds them (94 % / 86 % active against 54 % FP64)
+FD_FP64_PER_POINT = 65.0 + 71.0 + 2 * 24.9
+FD_ALU_PER_POINT = 3653 + 3672 + 2 * 11
 
 # Per launch of each batched pass on the headline workload (all 64 lattices), from
 # one ncu capture per kernel (--metrics dram__bytes_read.sum, dram__bytes_write.sum,
@@ -88,10 +90,11 @@ FD_FP64_PER_POINT = 113 + 119 + 2 * 27
 # node. They hold for the device code whose digest is recorded with them; once it
 # changes, traffic is null and the source counts above are used until the capture is
 # repeated.
-COUNTS = {"sources": "b0b1ffbeb1915797",
-          "rho_psi": {"dram_bytes": 1319260928, "fp64_per_node": 19.687, "alu_per_node": 629.3},
-          "collide": {"dram_bytes": 1289154048, "fp64_per_node": 37.000, "alu_per_node": 1199.3}}
-KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "internal.h")
+COUNTS = {"sources": "d3089a09f9570ef0",
+          "rho_psi": {"dram_bytes": 1316544000, "fp64_per_node": 17.777, "alu_per_node": 222.7},
+          "collide": {"dram_bytes": 1288622080, "fp64_per_node": 35.000, "alu_per_node": 855.4}}
+KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "fixsum.cuh",
+                  "internal.h")
 
 
 def kernel_sources_digest():
@@ -307,7 +310,8 @@ def fp64_probe_sweep(torch, local):
     out = (C.c_double * 3)()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     variants = [(8, 8, 0), (4, 8, 0), (2, 8, 0), (1, 8, 0), (8, 1, 0), (8, 2, 0), (8, 4, 0), (8, 16, 0),
-                (4, 32, 0), (8, 8, 1), (8, 8, 2), (8, 8, 3), (8, 8, 4), (8, 4, 3), (8, 4, 4)]
+                (4, 32, 0), (8, 8, 1), (8, 8, 2), (8, 8, 3), (8, 8, 4), (8, 4, 3), (8, 4, 4), (8, 8, 5),
+                (8, 8, 6), (4, 4, 5)]
     L.check(lib.pplbm_fp64_peak(8, 8, 0, 4000, C.c_void_p(sink.data_ptr()), out, stream))
     clocks = ClockSampler(local, "sweep")
     clocks.start()
@@ -316,7 +320,8 @@ def fp64_probe_sweep(torch, local):
         iters = max(1000, int(160000 * 8 / (bpsm * ch)))
         L.check(lib.pplbm_fp64_peak(bpsm, ch, op, iters, C.c_void_p(sink.data_ptr()), out, stream))
         rows.append({"blocks_per_sm": bpsm, "chains": ch,
-                     "op": ("fma", "add", "mul", "integer-pipe add", "fma + integer-pipe add")[op],
+                     "op": ("fma", "add", "mul", "integer-pipe add", "fma + integer-pipe add",
+                                "int64 -> f64 conversion", "f64 -> int64 conversion")[op],
                      "rate": out[0] / 1e12, "ms": out[1]})
     clk = clocks.stop()
     mhz = clk["sm_mhz"] or 2070.0
@@ -454,7 +459,7 @@ def serial_comparison(torch, stream, specs, batch_ms_per_step, steps=200):
             "serial_plain_launches_mlups": nodes * steps / (ms_s / 1e3) / 1e6}
 
 
-# ---- other spec and next-row figures ------------------------------------------
+# ---- figures of the batched engine, the adjoint, the EOS variants, FD and the sweeps ----
 
 def adjoint_cost(torch, steps=2000, interval=45):
     """Adjoint configuration (256 x 256 droplet, R = 48, T_r = 0.5, tau = 1): time of a
@@ -605,7 +610,7 @@ def impact_sweep_batch():
     return b, len(lats)
 
 
-def fd_throughput(torch, fp64_peak, steps=200):
+def fd_throughput(torch, fp64_peak, sm_mhz, steps=200):
     """The finite-difference solver (App. A) on a 2048 x 1024 periodic droplet grid
     (dx = 1, Smooth C-S at T_r = 0.6): grid-point updates per second. dt = 0.4: with
     the paper's 0.8 dx^2 the static droplet diverges in this scheme (CPU oracle too)."""
@@ -625,11 +630,17 @@ def fd_throughput(torch, fp64_peak, steps=200):
     r = fd.get_state()[0]
     ok = bool(torch.isfinite(r).all())
     fd.close()
-    achieved = FD_FP64_PER_POINT * nx * ny * steps / (ms / 1e3)
-    return {"grid": f"{nx}x{ny}, dx=1, dt=0.4", "mlups": nx * ny * steps / (ms / 1e3) / 1e6,
+    pts = nx * ny * steps / (ms / 1e3)
+    achieved = FD_FP64_PER_POINT * pts
+    alu = FD_ALU_PER_POINT * pts
+    alu_peak = ALU_PER_SM_CLK * 152 * sm_mhz * 1e6
+    return {"grid": f"{nx}x{ny}, dx=1, dt=0.4", "mlups": pts / 1e6,
             "ms_per_step": ms / steps, "finite": ok, "launches_per_step": 4,
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / 1e12 / fp64_peak, "fp64_per_point_step": FD_FP64_PER_POINT}}
+            "roofline": {"bound": "alu", "pipe": "integer (the update kernels' additions)",
+                         "achieved": alu / 1e12, "peak": alu_peak / 1e12, "unit": "T integer instr/s",
+                         "frac": alu / alu_peak, "alu_per_point_step": FD_ALU_PER_POINT},
+            "fp64_pipe": {"achieved": achieved / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                          "frac": achieved / 1e12 / fp64_peak, "fp64_per_point_step": FD_FP64_PER_POINT}}
 
 
 # ---- the oracle on the host cores ---------------------------------------------------
@@ -1069,7 +1080,7 @@ def main():
         line["impact_2048x1024"] = impact_2048(torch, stream, barrier)
         line["adjoint"] = adjoint_cost(torch)
         line["eos_variants_mlups"] = eos_variant_throughput(torch)
-        line["fd_solver"] = fd_throughput(torch, fp64_peak)
+        line["fd_solver"] = fd_throughput(torch, fp64_peak, clk.get("sm_mhz") or sm_max)
         line["impact_sweep"] = impact_sweep_throughput(torch, fp64_peak)
     else:
         batch.close()

@@ -515,6 +515,20 @@ pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed, double* o
  * such pair and the two results (bit patterns). Asynchronous on `stream`. */
 pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsigned long long* out, void* stream);
 
+/* The fixed-point sums of the step kernels, evaluated on caller data (a check of
+ * the device build against other builds of the same source): the density moments
+ * of Eqs. Density and Momentum and, for the two-phase set, rows 7 and 8 of Eq.
+ * MatrixMRT, and the Shan-Chen stencil sums of Eq. ShanChenForce. Each sum is exact
+ * in one 64-bit fixed-point frame anchored at its largest operand and rounded once
+ * to nearest. Device arrays: f (n x 9 populations, row-major), p (n x 8 psi values
+ * pE, pW, pN, pS, pNE, pNW, pSW, pSE), out (n x 8): rho, jx, jy, m7, m8, a flag,
+ * gx, gy. The flag is 1.0 when the nine populations are positive normal doubles
+ * below 2^1008 (the domain of the fixed-point moments); otherwise it is 0.0 and so
+ * are the five moments. gx, gy are NaN for an infinite, NaN or negative psi.
+ * PPLBM_ERR_ARG for n < 0, n > 2^31 * 255, or NULL pointers with n > 0.
+ * Asynchronous on `stream`. */
+pplbm_status pplbm_fixsum_eval(long long n, const double* f, const double* p, double* out, void* stream);
+
 /* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the
  * step's per-node arithmetic is double precision throughout, Sec. II; on this GPU
  * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)
@@ -522,9 +536,12 @@ pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsign
  * 16 or 32) independent chains of one FP64 operation: op 0 fused multiply-add,
  * 1 add, 2 multiply; op 3 runs chains of the integer-pipe addition the step kernels
  * use instead, op 4 one FMA and one integer-pipe addition per chain and round (the
- * same time as op 0 means the two pipes overlap). Times the launch with CUDA events
- * on `stream` and synchronises it. Writes to host out[3]: out[0] = FP64
- * instructions per second (op 3: integer-pipe additions per second; counted per
+ * same time as op 0 means the two pipes overlap); op 5 runs chains of 64-bit
+ * integer to double conversions (round to nearest), op 6 of double to 64-bit
+ * integer conversions (toward zero), each with a 64-bit integer add or XOR that
+ * feeds the result back. Times the launch with CUDA events on `stream` and
+ * synchronises it. Writes to host out[3]: out[0] = FP64 instructions per second
+ * (op 3: integer-pipe additions, ops 5, 6: conversions per second; counted per
  * thread, as the step's per-node instruction counts are), out[1] = the launch's
  * milliseconds, out[2] = blocks launched. `sink` is one device double
  * the kernel may write (it never does for these inputs; it keeps the chains from

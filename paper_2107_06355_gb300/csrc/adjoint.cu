@@ -343,9 +343,10 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
   if (x < a.nx && y < a.ny) {
     const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
     const double p0 = sp[c];
-    const double d1 = sp[c + sw + 1] - sp[c - sw - 1], d2 = sp[c - sw + 1] - sp[c + sw - 1];
-    const double gx = fma(4.0, sp[c + 1] - sp[c - 1], d1 + d2);
-    const double gy = fma(4.0, sp[c + sw] - sp[c - sw], d1 - d2);
+    // the forward collision pass's stencil sums (same arithmetic, same force)
+    double gx, gy;
+    fx::shan_chen_stencil(sp[c + 1], sp[c - 1], sp[c + sw], sp[c - sw], sp[c + sw + 1], sp[c + sw - 1],
+                          sp[c - sw - 1], sp[c - sw + 1], &gx, &gy);
     const int64_t N = a.n, node = (int64_t)y * a.nx + x;
     const int nx = a.nx, ny = a.ny;
     const int xe = (x + 1 == nx) ? 0 : x + 1, xw = (x == 0) ? nx - 1 : x - 1;

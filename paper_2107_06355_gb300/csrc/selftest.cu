@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pplbm.h"
+#include "fixsum.cuh"
 #include "fp64.cuh"
 
 namespace pplbm {
@@ -106,8 +107,10 @@ extern "C" pplbm_status pplbm_fp64_selftest(long long n, unsigned long long seed
 // operation (OP 0: x <- x * b + c, 1: x <- x + c, 2: x <- x * b; |b| < 1 keeps the
 // chains bounded), so the FP64 pipe is the only limit; OP 3 runs chains of the
 // integer-pipe addition add_pos_int instead (y <- y + c), and OP 4 both, one FMA and
-// one integer-pipe addition per chain and round (whether the two pipes overlap). The
-// sum of the chains goes to `sink` so that none of the work is dead.
+// one integer-pipe addition per chain and round (whether the two pipes overlap); OP 5
+// chains of 64-bit integer to double conversions, OP 6 of double to 64-bit integer
+// conversions (each with one integer operation feeding the result back). The sum of
+// the chains goes to `sink` so that none of the work is dead.
 namespace pplbm {
 namespace {
 
@@ -116,10 +119,16 @@ constexpr int kPeakThreads = 256;
 template <int CH, int OP>
 __global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(long long iters, double b, double c, double* sink) {
   double x[CH], y[CH];
+  unsigned long long z[CH];
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
     x[k] = (double)(threadIdx.x + k) * 1e-3;
     y[k] = 1.0 + x[k];
+    z[k] = 1000ull + threadIdx.x + k;
+  }
+  if (OP == 6) {
+#pragma unroll
+    for (int k = 0; k < CH; ++k) x[k] = 1e6 + x[k];  // values in [1e6, 1e6 + 1): conversions stay in range
   }
   for (long long it = 0; it < iters; ++it) {
 #pragma unroll
@@ -128,11 +137,13 @@ __global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(long long iters, dou
       if (OP == 1) x[k] = x[k] + c;
       if (OP == 2) x[k] = x[k] * b;
       if (OP == 3 || OP == 4) y[k] = add_pos_int(y[k], c);
+      if (OP == 5) z[k] += (unsigned long long)__double_as_longlong(__ll2double_rn((long long)z[k]));
+      if (OP == 6) x[k] = __longlong_as_double(__double_as_longlong(x[k]) ^ (__double2ll_rz(x[k]) & 1ll));
     }
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < CH; ++k) s += x[k] + y[k];
+  for (int k = 0; k < CH; ++k) s += x[k] + y[k] + (double)(z[k] & 1ull);
   if (s == 12345.678) sink[0] = s;  // never true for these chains; keeps them live
 }
 
@@ -154,7 +165,7 @@ bool launch_peak(int chains, int blocks, long long iters, double* sink, cudaStre
 
 extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, int32_t op, long long iters,
                                         double* sink, double* out, void* stream) {
-  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out || op < 0 || op > 4 ||
+  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !out || op < 0 || op > 6 ||
       !(chains == 1 || chains == 2 || chains == 4 || chains == 8 || chains == 16 || chains == 32))
     return PPLBM_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -175,7 +186,9 @@ extern "C" pplbm_status pplbm_fp64_peak(int32_t blocks_per_sm, int32_t chains, i
   else if (op == 1) pplbm::launch_peak<1>(chains, blocks, iters, sink, s);
   else if (op == 2) pplbm::launch_peak<2>(chains, blocks, iters, sink, s);
   else if (op == 3) pplbm::launch_peak<3>(chains, blocks, iters, sink, s);
-  else pplbm::launch_peak<4>(chains, blocks, iters, sink, s);
+  else if (op == 4) pplbm::launch_peak<4>(chains, blocks, iters, sink, s);
+  else if (op == 5) pplbm::launch_peak<5>(chains, blocks, iters, sink, s);
+  else pplbm::launch_peak<6>(chains, blocks, iters, sink, s);
   cudaEventRecord(e1, s);
   if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
       cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f))
@@ -198,4 +211,36 @@ extern "C" pplbm_status pplbm_int_add_selftest(long long n, unsigned long long s
   pplbm::k_int_add_selftest<<<1216, 256, 0, s>>>(n, seed, out);
   if (cudaGetLastError() != cudaSuccess) return PPLBM_ERR_CUDA;
   return PPLBM_OK;
+}
+
+// The fixed-point sums of fixsum.cuh on caller data, one thread per row.
+namespace pplbm {
+namespace {
+
+__global__ void k_fixsum_eval(long long n, const double* f, const double* p, double* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = f[9 * i + k];
+  double* o = out + 8 * i;
+  unsigned mx = 0;
+  double r[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const bool ok = fx::positive_normal_range(v, &mx);
+  if (ok) fx::density_moments<true>(v, fx::frame_top(mx), &r[0], &r[1], &r[2], &r[3], &r[4]);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) o[k] = r[k];
+  o[5] = ok ? 1.0 : 0.0;
+  const double* q = p + 8 * i;
+  fx::shan_chen_stencil(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], &o[6], &o[7]);
+}
+
+}  // namespace
+}  // namespace pplbm
+
+extern "C" pplbm_status pplbm_fixsum_eval(long long n, const double* f, const double* p, double* out, void* stream) {
+  if (n < 0 || n > 0x7FFFFFFFLL * 255 || (n > 0 && (!f || !p || !out))) return PPLBM_ERR_ARG;
+  if (n == 0) return PPLBM_OK;
+  pplbm::k_fixsum_eval<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, f, p, out);
+  return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
 }

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "eos_dev.cuh"
+#include "fixsum.cuh"
 #include "fp64.cuh"
 #include "internal.h"
 
@@ -33,32 +34,24 @@ __device__ __forceinline__ void rho_psi_node(const StepArgs& a, const double* __
   const int64_t N = a.n;
   const double f0 = f[i], f1 = f[N + i], f2 = f[2 * N + i], f3 = f[3 * N + i], f4 = f[4 * N + i];
   const double f5 = f[5 * N + i], f6 = f[6 * N + i], f7 = f[7 * N + i], f8 = f[8 * N + i];
-  double rho, jx, jy, a13 = 0.0, a24 = 0.0, a57 = 0.0, a68 = 0.0;
-  // The sums of positive populations run on the integer pipe (add_pos_int, bitwise
-  // the FP64 add) when all nine are positive normal doubles, which leaves the FP64
-  // pipe, the pass's bottleneck, the differences and the EOS; otherwise the same sums
-  // in the same order on the FP64 pipe. Either way the results are identical.
+  double rho, jx, jy, m7 = 0.0, m8 = 0.0;
+  // When all nine populations are positive normal doubles (every bulk and interface
+  // node of a physical state), the moments are exact integer sums in one fixed-point
+  // frame, each rounded once (fixsum.cuh): integer-pipe work only, leaving the FP64
+  // pipe, the pass's bottleneck, the EOS. Otherwise the same moments as IEEE sums.
   const double fv[9] = {f0, f1, f2, f3, f4, f5, f6, f7, f8};
-  const bool ip = KIND != kFullMrt && all_positive_normal(fv);
-  if (KIND == kShearTau) {
-    // rows 7, 8 of Eq. MatrixMRT share their pair sums with rho: 18 additions for
-    // rho, j and both stress moments (20 when formed separately)
-    if (ip) {
-      a13 = add_pos_int(f1, f3), a24 = add_pos_int(f2, f4), a57 = add_pos_int(f5, f7), a68 = add_pos_int(f6, f8);
-      rho = add_pos_int(f0, add_pos_int(add_pos_int(a13, a24), add_pos_int(a57, a68)));
-    } else {
-      a13 = f1 + f3, a24 = f2 + f4, a57 = f5 + f7, a68 = f6 + f8;
-      rho = f0 + ((a13 + a24) + (a57 + a68));
-    }
+  unsigned max_hi = 0;
+  if (KIND != kFullMrt && fx::positive_normal_range(fv, &max_hi)) {
+    fx::density_moments<KIND == kShearTau>(fv, fx::frame_top(max_hi), &rho, &jx, &jy, &m7, &m8);
+  } else if (KIND == kShearTau) {
+    // rows 7, 8 of Eq. MatrixMRT share their pair sums with rho
+    const double a13 = f1 + f3, a24 = f2 + f4, a57 = f5 + f7, a68 = f6 + f8;
+    rho = f0 + ((a13 + a24) + (a57 + a68));
     const double p = f5 - f7, q = f6 - f8;
     jx = (f1 - f3) + (p - q);
     jy = (f2 - f4) + (p + q);
-  } else if (ip) {
-    const double sxp = add_pos_int(add_pos_int(f1, f5), f8);  // populations with c_x = +1
-    const double sxm = add_pos_int(add_pos_int(f3, f6), f7);  // c_x = -1
-    rho = add_pos_int(add_pos_int(add_pos_int(f0, f2), f4), add_pos_int(sxp, sxm));
-    jx = sxp - sxm;
-    jy = add_pos_int(add_pos_int(f2, f5), f6) - add_pos_int(add_pos_int(f4, f7), f8);
+    m7 = a13 - a24;
+    m8 = a57 - a68;
   } else {
     const double sxp = f1 + f5 + f8;  // populations with c_x = +1
     const double sxm = f3 + f6 + f7;  // c_x = -1
@@ -76,8 +69,8 @@ __device__ __forceinline__ void rho_psi_node(const StepArgs& a, const double* __
   m[N + i] = jx;
   m[2 * N + i] = jy;
   if (KIND == kShearTau) {
-    m[3 * N + i] = a13 - a24;  // row 7 of Eq. MatrixMRT
-    m[4 * N + i] = a57 - a68;  // row 8
+    m[3 * N + i] = m7;  // row 7 of Eq. MatrixMRT
+    m[4 * N + i] = m8;  // row 8
   } else if (KIND == kFullMrt) {
     const double ax = f1 + f2 + f3 + f4, dg = f5 + f6 + f7 + f8;
     m[3 * N + i] = -4.0 * f0 - ax + 2.0 * dg;                    // row 1 (e)
@@ -307,11 +300,11 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   const double p0 = sp[c];
   const double pE = sp[c + 1], pW = sp[c - 1], pN = sp[c + sw], pS = sp[c - sw];
   const double pNE = sp[c + sw + 1], pNW = sp[c + sw - 1], pSW = sp[c - sw - 1], pSE = sp[c - sw + 1];
-  // 12 * sum_i w(|c_i|^2) psi(x + c_i) c_i  (w = 1/3 axis, 1/12 diagonal); the
-  // differences on the integer pipe (add_int: bitwise the FP64 add)
-  const double d1 = sub_int(pNE, pSW), d2 = sub_int(pSE, pNW);
-  const double gx = fma(4.0, sub_int(pE, pW), add_int(d1, d2));
-  const double gy = fma(4.0, sub_int(pN, pS), sub_int(d1, d2));
+  // 12 * sum_i w(|c_i|^2) psi(x + c_i) c_i  (w = 1/3 axis, 1/12 diagonal): exact
+  // integer sums in one fixed-point frame, rounded once (fixsum.cuh); psi > 0 is
+  // normal and finite wherever the density pass left the error word clear
+  double gx, gy;
+  fx::shan_chen_stencil(pE, pW, pN, pS, pNE, pNW, pSW, pSE, &gx, &gy);
   const int64_t N = a.n;
   const int64_t node = (int64_t)y * a.nx + x;
   Post o;
@@ -404,11 +397,11 @@ __device__ __forceinline__ void guard_node(const StepArgs& a, int64_t i, double*
     v[2] += 1.0;
   } else {
     const int y = (int)(i / a.nx), x = (int)(i - (int64_t)y * a.nx);
-    const double pE = psi_near(a, x, y, 1, 0), pW = psi_near(a, x, y, -1, 0);
-    const double pN = psi_near(a, x, y, 0, 1), pS = psi_near(a, x, y, 0, -1);
-    const double d1 = psi_near(a, x, y, 1, 1) - psi_near(a, x, y, -1, -1);
-    const double d2 = psi_near(a, x, y, 1, -1) - psi_near(a, x, y, -1, 1);
-    const double gx = 4.0 * (pE - pW) + (d1 + d2), gy = 4.0 * (pN - pS) + (d1 - d2);
+    // the collision pass's stencil sums (the same arithmetic, so the same force)
+    double gx, gy;
+    fx::shan_chen_stencil(psi_near(a, x, y, 1, 0), psi_near(a, x, y, -1, 0), psi_near(a, x, y, 0, 1),
+                          psi_near(a, x, y, 0, -1), psi_near(a, x, y, 1, 1), psi_near(a, x, y, -1, 1),
+                          psi_near(a, x, y, -1, -1), psi_near(a, x, y, 1, -1), &gx, &gy);
     const double cH = a.half_force * a.psi[i];
     const double ux = (a.mom[n + i] + cH * gx) / rho, uy = (a.mom[2 * n + i] + cH * gy) / rho;
     v[0] += rho;

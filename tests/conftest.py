@@ -2,6 +2,8 @@ import os
 import sys
 import warnings
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -15,3 +17,21 @@ warnings.filterwarnings("ignore", message=".*Extremely bad integrand.*")
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the compiled library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def fixsum_host(tmp_path_factory):
+    """Host build (g++) of the step kernels' fixed-point sums (csrc/fixsum.cuh) through
+    tests/native/fixsum_host.cpp: fx_density(n, f, out) and fx_stencil(n, p, out)."""
+    import ctypes as C
+    import subprocess
+
+    d = tmp_path_factory.mktemp("fixsum")
+    so = str(d / "libfixsum_host.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", so,
+                    os.path.join(ROOT, "tests", "native", "fixsum_host.cpp")], check=True)
+    lib = C.CDLL(so)
+    for name in ("fx_density", "fx_stencil"):
+        getattr(lib, name).argtypes = [C.c_longlong, C.c_void_p, C.c_void_p]
+        getattr(lib, name).restype = None
+    return lib

@@ -1,0 +1,31 @@
+// Host build of the fixed-point sums of csrc/fixsum.cuh (the same source the step
+// kernels compile), for the CPU tests: evaluates them on caller arrays.
+#include "../../paper_2107_06355_gb300/csrc/fixsum.cuh"
+
+using namespace pplbm::fx;
+
+extern "C" {
+
+// n nodes: f (n x 9 populations) -> out (n x 6): rho, jx, jy, m7, m8, valid (1 if the
+// nine are in the range of the fixed-point path)
+void fx_density(long long n, const double* f, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    double v[9];
+    for (int k = 0; k < 9; ++k) v[k] = f[9 * i + k];
+    unsigned mx = 0;
+    const bool ok = positive_normal_range(v, &mx);
+    double* o = out + 6 * i;
+    o[0] = o[1] = o[2] = o[3] = o[4] = 0.0;
+    o[5] = ok ? 1.0 : 0.0;
+    if (ok) density_moments<true>(v, frame_top(mx), &o[0], &o[1], &o[2], &o[3], &o[4]);
+  }
+}
+
+// n nodes: p (n x 8: pE, pW, pN, pS, pNE, pNW, pSW, pSE) -> out (n x 2): gx, gy
+void fx_stencil(long long n, const double* p, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    const double* q = p + 8 * i;
+    shan_chen_stencil(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], &out[2 * i], &out[2 * i + 1]);
+  }
+}
+}

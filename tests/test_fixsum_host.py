@@ -1,0 +1,161 @@
+"""The fixed-point sums of the step kernels (csrc/fixsum.cuh: the density moments
+of Eqs. Density and Momentum, the Shan-Chen stencil of Eq. ShanChenForce), built
+for the host from the same source, against exact rational sums of the same
+doubles (fractions.Fraction). The bound: within half an ulp of the result plus,
+for each operand, 2^-7 of the largest operand's ulp (the bits a smaller operand
+loses below the frame); sums of positive operands within 0.57 ulp; exact results
+(representable sums, exact cancellation) reproduced exactly."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def fx(fixsum_host):
+    return fixsum_host
+
+
+def density(lib, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros((f.shape[0], 6))
+    lib.fx_density(f.shape[0], f.ctypes.data, out.ctypes.data)
+    return out
+
+
+def stencil(lib, p):
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.zeros((p.shape[0], 2))
+    lib.fx_stencil(p.shape[0], p.ctypes.data, out.ctypes.data)
+    return out
+
+
+def ulp(x):
+    return math.ulp(abs(float(x))) if x != 0 else math.ulp(0.0)
+
+
+def check(res, exact, operands, nterms, what):
+    """|res - exact| <= ulp(res)/2 + nterms 2^-7 ulp(max operand)."""
+    big = max(abs(float(v)) for v in operands)
+    bound = Fraction(ulp(res)) / 2 + nterms * Fraction(ulp(big)) / 128
+    if exact != 0 and res != 0:
+        # the rounding's half ulp is of the exact value's binade: take the larger
+        bound = max(bound, Fraction(ulp(float(exact))) / 2 + nterms * Fraction(ulp(big)) / 128)
+    err = abs(Fraction(float(res)) - exact)
+    assert err <= bound, (what, float(res), float(exact), float(err / Fraction(ulp(big))))
+
+
+def population_sets(rng, n, spread):
+    """Nine populations per node: f_eq-like weights times a density in 10^[-6, 0] with
+    relative perturbations up to `spread` (an interface node), or independent exponents."""
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    rho = 10.0 ** rng.uniform(-6, 0, size=(n, 1))
+    f = w * rho * (1 + spread * rng.uniform(-1, 1, size=(n, 9)))
+    return f
+
+
+@pytest.mark.parametrize("spread", [0.0, 1e-12, 1e-3, 0.5, 0.99])
+def test_density_moments_within_the_bound_of_the_exact_sums(fx, spread):
+    rng = np.random.default_rng(20260 + int(spread * 1000))
+    f = population_sets(rng, 3000, spread)
+    out = density(fx, f)
+    assert np.all(out[:, 5] == 1.0)
+    for i in range(f.shape[0]):
+        q = [Fraction(float(v)) for v in f[i]]
+        rho = sum(q)
+        jx = q[1] + q[5] + q[8] - q[3] - q[6] - q[7]
+        jy = q[2] + q[5] + q[6] - q[4] - q[7] - q[8]
+        m7 = (q[1] + q[3]) - (q[2] + q[4])
+        m8 = (q[5] + q[7]) - (q[6] + q[8])
+        # rho: a sum of positive operands, within 0.57 ulp of itself
+        assert abs(Fraction(float(out[i, 0])) - rho) <= Fraction(ulp(out[i, 0])) * Fraction(57, 100), i
+        check(out[i, 1], jx, f[i], 6, "jx")
+        check(out[i, 2], jy, f[i], 6, "jy")
+        check(out[i, 3], m7, f[i], 4, "m7")
+        check(out[i, 4], m8, f[i], 4, "m8")
+
+
+def test_density_moments_independent_exponents_and_exact_cases(fx):
+    rng = np.random.default_rng(7)
+    # independent magnitudes over 2^-60 .. 2^20: terms far below the largest vanish into
+    # the frame's low bits, the bound still holds
+    f = np.ldexp(1 + rng.random((4000, 9)), rng.integers(-60, 21, size=(4000, 9)))
+    out = density(fx, f)
+    for i in range(f.shape[0]):
+        q = [Fraction(float(v)) for v in f[i]]
+        check(out[i, 0], sum(q), f[i], 9, "rho")
+        check(out[i, 1], q[1] + q[5] + q[8] - q[3] - q[6] - q[7], f[i], 6, "jx")
+    # exactly representable sums come out exact; a state at rest has j = 0 exactly
+    g = np.array([[4.0, 1.0, 1.0, 1.0, 1.0, 0.25, 0.25, 0.25, 0.25]]) * 2.0 ** -10
+    o = density(fx, g)[0]
+    assert o[0] == 9.0 * 2.0 ** -10 and o[1] == 0.0 and o[2] == 0.0 and o[3] == 0.0 and o[4] == 0.0
+    assert not math.copysign(1.0, o[1]) < 0  # +0, as an IEEE x - x
+    # mirror-symmetric populations (f1 = f3, f5 = f6, f8 = f7) cancel exactly in jx
+    h = population_sets(np.random.default_rng(3), 200, 0.3)
+    h[:, 3], h[:, 6], h[:, 7] = h[:, 1], h[:, 5], h[:, 8]
+    assert np.all(density(fx, h)[:, 1] == 0.0)
+    # ties: with the others multiples of 2^-40, + 2^-53 is exactly half an ulp and
+    # rounds to even, + 3 2^-53 rounds up to the even neighbour
+    t = np.full((2, 9), 2.0 ** -40)
+    t[:, 0] = 1.0
+    t[0, 1], t[1, 1] = 2.0 ** -53, 3 * 2.0 ** -53
+    o = density(fx, t)
+    assert o[0, 0] == 1.0 + 7 * 2.0 ** -40 and o[1, 0] == 1.0 + 7 * 2.0 ** -40 + 2.0 ** -51
+    # an operand far below the others still counts as a sticky unit: above the tie
+    t[0, 8] = 2.0 ** -300
+    assert density(fx, t)[0, 0] == 1.0 + 6 * 2.0 ** -40 + 2.0 ** -52
+
+
+def test_density_range_check_rejects_what_the_frame_cannot_hold(fx):
+    base = np.full((1, 9), 0.1)
+    for bad in (0.0, -0.1, 5e-324, 1e-310, 2.0 ** 1008, np.inf, np.nan):
+        f = base.copy()
+        f[0, 4] = bad
+        assert density(fx, f)[0, 5] == 0.0, bad
+    assert density(fx, base)[0, 5] == 1.0
+
+
+@pytest.mark.parametrize("ratio", [1.0, 0.9, 1e-2, 1e-5])
+def test_shan_chen_stencil_within_the_bound_of_the_exact_sums(fx, ratio):
+    """psi over a 3 x 3 stencil: smooth fields, and interfaces where psi drops by
+    `ratio` (liquid to vapour) across the stencil."""
+    rng = np.random.default_rng(int(1 / ratio) % 100003)
+    n = 4000
+    psi_l = 10.0 ** rng.uniform(-3, 1, size=(n, 1))
+    frac = rng.random((n, 8))
+    p = psi_l * (ratio + (1 - ratio) * frac)
+    out = stencil(fx, p)
+    for i in range(n):
+        q = [Fraction(float(v)) for v in p[i]]
+        E_, W, N, S, NE, NW, SW, SE = q
+        gx = 4 * (E_ - W) + (NE - SW) + (SE - NW)
+        gy = 4 * (N - S) + (NE - SW) - (SE - NW)
+        check(out[i, 0], gx, p[i], 12, "gx")
+        check(out[i, 1], gy, p[i], 12, "gy")
+
+
+def test_shan_chen_stencil_uniform_and_symmetric_fields_give_zero(fx):
+    p = np.full((3, 8), 0.37)
+    p[1] *= 1e-4
+    p[2] = [0.5, 0.5, 0.2, 0.2, 0.3, 0.3, 0.3, 0.3]   # E = W, N = S, NE = NW = SW = SE
+    out = stencil(fx, p)
+    assert np.all(out == 0.0) and not np.any(np.signbit(out))
+    # antisymmetry: swapping east and west (and the diagonals) negates gx exactly
+    rng = np.random.default_rng(11)
+    a = rng.uniform(0.01, 1.0, size=(500, 8))
+    b = a[:, [1, 0, 2, 3, 5, 4, 7, 6]]   # E<->W, NE<->NW, SW<->SE
+    oa, ob = stencil(fx, a), stencil(fx, b)
+    assert np.array_equal(oa[:, 0], -ob[:, 0]) and np.array_equal(oa[:, 1], ob[:, 1])
+
+
+def test_shan_chen_stencil_non_finite_or_negative_psi_gives_nan(fx):
+    for bad in (np.inf, np.nan, -0.2):
+        p = np.full((1, 8), 0.3)
+        p[0, 5] = bad
+        assert np.all(np.isnan(stencil(fx, p)))
+    # a zero psi counts as (at most) one unit of the frame's last bit
+    p = np.full((1, 8), 0.3)
+    p[0, 1] = 0.0
+    out = stencil(fx, p)[0]
+    assert abs(out[0] - 4 * 0.3) <= 2 * math.ulp(1.2) and abs(out[1]) <= math.ulp(0.3)

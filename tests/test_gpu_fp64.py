@@ -47,7 +47,7 @@ def test_fp64_peak_probe_reports_a_rate_consistent_with_its_own_timing():
         assert L.lib().pplbm_fp64_peak(8, 8, op, 20000, C.c_void_p(sink.data_ptr()), out, stream) == 0
         t[op] = out[1]
     assert t[4] < 1.1 * max(t[0], t[3])
-    for bad in ((0, 8, 0, 10), (65, 8, 0, 10), (4, 8, 0, 0), (4, 3, 0, 10), (4, 8, 5, 10)):
+    for bad in ((0, 8, 0, 10), (65, 8, 0, 10), (4, 8, 0, 0), (4, 3, 0, 10), (4, 8, 7, 10), (4, 8, -1, 10)):
         assert L.lib().pplbm_fp64_peak(*bad, C.c_void_p(sink.data_ptr()), out, stream) == L.PPLBM_ERR_ARG
 
 
@@ -64,3 +64,41 @@ def test_integer_pipe_addition_is_bitwise_the_fp64_add():
     torch.cuda.synchronize()
     bad = out.tolist()
     assert bad[0] == 0, [hex(v & (2**64 - 1)) for v in bad]
+
+
+def test_fixed_point_sums_device_build_equals_host_build(fixsum_host):
+    """The step kernels' fixed-point moments and stencil sums (fixsum.cuh) compiled for
+    sm_103a give bit for bit the results of the host build of the same source, which
+    test_fixsum_host.py checks against exact rational sums: 2^20 population sets
+    (interface-like and independent exponents, a few outside the range) and psi
+    stencils (smooth, across interfaces, with non-finite and negative entries)."""
+    import numpy as np
+
+    from paper_2107_06355_gb300 import _lib as L
+
+    rng = np.random.default_rng(2107)
+    n = 1 << 20
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = w * 10.0 ** rng.uniform(-6, 0, size=(n, 1)) * (1 + rng.uniform(-0.99, 0.99, size=(n, 9)))
+    k = n // 4
+    f[:k] = np.ldexp(1 + rng.random((k, 9)), rng.integers(-70, 30, size=(k, 9)))
+    f[k:k + 64, 3] = [0.0, -1e-3, np.inf, np.nan] * 16
+    p = 10.0 ** rng.uniform(-3, 1, size=(n, 1)) * (1e-3 + rng.random((n, 8)))
+    p[:1000, 2] = [np.inf, np.nan, -0.5, 0.0] * 250
+    host_d = np.zeros((n, 6))
+    host_s = np.zeros((n, 2))
+    fixsum_host.fx_density(n, f.ctypes.data, host_d.ctypes.data)
+    fixsum_host.fx_stencil(n, p.ctypes.data, host_s.ctypes.data)
+    fd, pd = torch.from_numpy(f).cuda(), torch.from_numpy(p).cuda()
+    out = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+    st = L.lib().pplbm_fixsum_eval(n, C.c_void_p(fd.data_ptr()), C.c_void_p(pd.data_ptr()),
+                                   C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    dev = out.cpu().numpy()
+    # bit patterns (NaN payloads included)
+    assert np.array_equal(dev[:, :6].view(np.int64), host_d.view(np.int64))
+    assert np.array_equal(dev[:, 6:].view(np.int64), host_s.view(np.int64))
+    assert dev[:, 5].sum() < n and dev[:, 5].sum() > n - 100
+    assert L.lib().pplbm_fixsum_eval(-1, None, None, None, None) == L.PPLBM_ERR_ARG
+    assert L.lib().pplbm_fixsum_eval(4, None, None, None, None) == L.PPLBM_ERR_ARG
+    assert L.lib().pplbm_fixsum_eval(0, None, None, None, None) == 0
