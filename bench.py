@@ -52,21 +52,22 @@ MIN_BLOCKS = 5
 
 # FP64 instructions of one node update per kernel, from the kernels' arithmetic on
 # bulk nodes (unit relaxation times, Li forcing), counting what runs on the FP64 pipe:
-# the density pass 18 (C-S branch 13, sqrt 5; its moments are integer sums in one
-# fixed-point frame), the collision pass 35 (11 products, 24 fused multiply-adds; its
-# force stencil in fixed point and its 7 other additions on the integer pipe). These
-# are the fallback; the roofline uses the counts ncu measured on the workload (COUNTS).
-FP64_PER_NODE = {"rho_psi": 18, "collide": 35}
+# the density pass 15 (the C-S branch 9 with v = 1/(1 - eta), sqrt 5; its moments are
+# integer sums in one fixed-point frame), the collision pass 19 (products, the
+# reciprocal and the Li term; its force stencil, the sums j + h, j + 2h, j + 3h and
+# the nine output populations are exact integer combinations in fixed-point frames).
+# These are the fallback; the roofline uses the counts ncu measured on the workload
+# (COUNTS).
+FP64_PER_NODE = {"rho_psi": 15, "collide": 19}
 # integer-pipe (ALU) instructions per node of the same passes (ncu; fallback figures)
-ALU_PER_NODE = {"rho_psi": 223, "collide": 855}
+ALU_PER_NODE = {"rho_psi": 223, "collide": 1053}
 # ALU pipe issue rate: 64 thread instructions per SM per clock (ncu's
 # sm__pipe_alu_cycles_active scale: 82.7 % active at 16.6e12 instructions/s)
 ALU_PER_SM_CLK = 64
 # the two-phase relaxation (rows 7, 8 relax with 1/tau(rho)), walls: pass 1 adds the
-# two stress moments with shared pair sums (its 8 positive sums on the integer pipe),
-# pass 2 tau(rho), its reciprocal and the rows 7, 8 corrections (its 17 additions on
-# the integer pipe)
-FP64_PER_NODE_SHEAR = {"rho_psi": 28, "collide": 48}  # ncu on the impact lattice: 27.84, 48.00
+# two stress moments to its fixed-point frame, pass 2 tau(rho), its reciprocal and the
+# rows 7, 8 corrections (two more terms of its output frame)
+FP64_PER_NODE_SHEAR = {"rho_psi": 14.4, "collide": 32}  # ncu on the impact lattice: 14.42, 32.00
 # algorithmic bytes per node of each pass as built (moments handed from pass 1 to
 # pass 2): pass 1 reads 9 f and writes psi + 3 moments (5 with tau(rho)); pass 2
 # reads the moments and the psi tile and writes 9 f
@@ -90,9 +91,9 @@ FD_ALU_PER_POINT = 3653 + 3672 + 2 * 11
 # node. They hold for the device code whose digest is recorded with them; once it
 # changes, traffic is null and the source counts above are used until the capture is
 # repeated.
-COUNTS = {"sources": "d3089a09f9570ef0",
-          "rho_psi": {"dram_bytes": 1316544000, "fp64_per_node": 17.777, "alu_per_node": 222.7},
-          "collide": {"dram_bytes": 1288622080, "fp64_per_node": 35.000, "alu_per_node": 855.4}}
+COUNTS = {"sources": "643302f55229de1a",
+          "rho_psi": {"dram_bytes": 1317146368, "fp64_per_node": 14.542, "alu_per_node": 222.7},
+          "collide": {"dram_bytes": 1289946368, "fp64_per_node": 19.000, "alu_per_node": 1052.6}}
 KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "fixsum.cuh",
                   "internal.h")
 
@@ -1003,6 +1004,29 @@ def main():
         dom_bytes = sum(BYTES_PER_NODE.values()) * nodes
     achieved = dom_flops / dom_s / 1e12
     launches_per_block = 2 * args.steps if per_pass else 1
+    # the dominant kernel against both arithmetic pipes: FP64 instructions against the
+    # measured FP64 issue rate, integer instructions against the ALU pipe's 64 per SM per
+    # clock at the sampled clock; `roofline` is the pipe closer to its limit (the bound)
+    mhz = clk.get("sm_mhz") or sm_max
+    alu_peak = ALU_PER_SM_CLK * 152 * mhz * 1e6 / 1e12
+    fp64_pipe = {"pipe": "fp64", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
+                 "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                 "flop_convention": "1 per FP64 add/mul/fma instruction (per thread); "
+                                    f"{fp64_node.get(dom, sum(fp64_node.values()))} per node ({fp64_src})",
+                 "peak_source": "measured: pplbm_fp64_peak in this run (fp64_peak_measured)"}
+    int_pipe = {"pipe": "integer", "kernel": dom_name, "alu_per_node": pass_alu(dom) if per_pass else None,
+                "achieved": (pass_alu(dom) * nodes / dom_s / 1e12) if per_pass else None,
+                "peak": alu_peak, "unit": "T integer instr/s",
+                "frac": (pass_alu(dom) * nodes / dom_s / 1e12 / alu_peak) if per_pass else None,
+                "peak_source": f"derived: 64 integer lanes per SM x 152 SMs x {mhz:.0f} MHz (sampled)",
+                "note": "the pass's sums run on the integer pipe (fixed-point frames and software IEEE adds)"}
+    if int_pipe["frac"] is not None and int_pipe["frac"] > fp64_pipe["frac"]:
+        roof, other = dict(int_pipe), fp64_pipe
+    else:
+        roof, other = dict(fp64_pipe), int_pipe
+    roof = {"bound": "alu", **roof, "traffic": pass_traffic(dom) if per_pass else None,
+            "traffic_unit": "DRAM bytes per launch (ncu capture, same kernel sources)",
+            "launch_ms": dom_s * 1e3, "share_of_step": share}
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1016,22 +1040,9 @@ def main():
                    "l2": "state about 2.4 GB >> 126 MB L2, no flush"},
         "blocks_ms": plain,
         "blocks_ms_instrumented": instrumented,
-        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "traffic": pass_traffic(dom) if per_pass else None,
-                     "traffic_unit": "DRAM bytes per launch (ncu capture, same kernel sources)",
-                     "flop_convention": "1 per FP64 add/mul/fma instruction (per thread); "
-                                        f"{fp64_node.get(dom, sum(fp64_node.values()))} per node ({fp64_src})",
-                     "peak_source": "measured: pplbm_fp64_peak in this run (fp64_peak_measured)",
-                     "launch_ms": dom_s * 1e3, "share_of_step": share},
+        "roofline": roof,
         "kernel_ms": kern,
-        "int_pipe": {"kernel": dom_name, "alu_per_node": pass_alu(dom) if per_pass else None,
-                     "achieved": (pass_alu(dom) * nodes / dom_s / 1e12) if per_pass else None,
-                     "peak": ALU_PER_SM_CLK * 152 * (clk.get("sm_mhz") or sm_max) * 1e6 / 1e12,
-                     "unit": "T integer instr/s",
-                     "frac": (pass_alu(dom) * nodes / dom_s / (ALU_PER_SM_CLK * 152 * (clk.get("sm_mhz") or sm_max)
-                                                                * 1e6)) if per_pass else None,
-                     "note": "the pass's additions run on the integer pipe (bitwise the FP64 add), beside the FP64 pipe"},
+        "other_pipe": other,
         "fp64_peak_measured": fp64,
         "roofline_hbm": {
             "dominant_kernel": {"achieved": dom_bytes / dom_s / 1e9, "frac": dom_bytes / dom_s / 1e9 / hbm_gbs,

@@ -529,6 +529,18 @@ pplbm_status pplbm_int_add_selftest(long long n, unsigned long long seed, unsign
  * Asynchronous on `stream`. */
 pplbm_status pplbm_fixsum_eval(long long n, const double* f, const double* p, double* out, void* stream);
 
+/* The fixed-point parts of the collision pass, evaluated on caller data (a check of
+ * the device build against other builds of the same source): per row, the nine
+ * post-collision populations of the reduced collision (Eqs. OperatorMRT, LiFS with
+ * Lambda = I; with shear != 0 also the rows 7, 8 corrections of the two-phase set,
+ * Eq. RelaxationTime) from q (n x 9: rho/36, Pi_xx/36, Pi_yy/36, Pi_xy/36, P_x/36,
+ * P_y/36, the Li term zz, and the rows 7, 8 corrections, read only when shear != 0),
+ * and the sums j + h, j + 2h, j + 3h, j - h of jh (n x 2: j, h). Device arrays;
+ * out (n x 13): the nine populations, then the four sums. PPLBM_ERR_ARG for n < 0,
+ * n > 2^31 * 255, or NULL pointers with n > 0. Asynchronous on `stream`. */
+pplbm_status pplbm_fixsum_collision_eval(long long n, int32_t shear, const double* q, const double* jh, double* out,
+                                         void* stream);
+
 /* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the
  * step's per-node arithmetic is double precision throughout, Sec. II; on this GPU
  * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)

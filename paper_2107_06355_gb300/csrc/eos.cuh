@@ -39,6 +39,10 @@ struct EosConst {
   double k1_v, k2_v, k4_v;
   double k1_l, k2_l, k4_l;
   double k3;
+  // 2 k1 of each branch, for the kernels' form of Eq. CS: with v = 1/(1 - eta),
+  // (1 + eta + eta^2 - eta^3)/(1 - eta)^3 = 2 v^3 - 2 v + 1, so that
+  // k1 num/(1 - eta)^3 = c1 (v (v^2 - 1) + 1/2), c1 = 2 k1
+  double c1_v, c1_l;
   // bit patterns of the branch densities (positive doubles order like their bits)
   long long bits_rho_v, bits_rho_max, bits_rho_min, bits_rho_l;
   double p_sat, theta, rho_m;  // Peng loop: p_sat + theta (rho - rho_v)(rho - rho_l)(rho - rho_m)

@@ -252,6 +252,8 @@ EosConst make_eos_const(const pplbm_eos_derived& d) {
   e.k2_l = -sc * e.a_l;
   e.k4_l = sc * e.dP;
   e.k3 = -sc / 3.0;
+  e.c1_v = 2.0 * e.k1_v;
+  e.c1_l = 2.0 * e.k1_l;
   std::memcpy(&e.bits_rho_v, &e.rho_v, 8);
   std::memcpy(&e.bits_rho_max, &e.rho_max, 8);
   std::memcpy(&e.bits_rho_min, &e.rho_min, 8);

@@ -174,6 +174,107 @@ PPLBM_FX void density_moments(const double (&f)[9], int eg, double* rho, double*
   }
 }
 
+// The term of a double of either sign (bit pattern b) in the frame with top exponent
+// eg, rounded to the nearest unit (halves away from zero) rather than truncated, so
+// that the terms' errors do not all lean one way; zero gives 0. Needs eg - e >= 1 for
+// the operand's biased exponent e (frames built with a headroom of at least 1).
+PPLBM_FX i64 sterm(u64 b, int eg) {
+  const int e = (int)((b >> 52) & 0x7FFu);
+  const int d = eg - e - 1;  // >= 0: one place more than the term, then round
+  const u64 l = (b << 11) | ((u64)(e != 0) << 63);
+  const u64 m = ((l >> (d < 63 ? d : 63)) + 1) >> 1;
+  const u64 neg = (u64)((i64)b >> 63);  // 0 or all ones
+  return (i64)((m ^ neg) - neg);
+}
+
+// high word of a double with its sign cleared: the magnitude's order
+PPLBM_FX unsigned mag_hi(u64 b) { return hi32(b) & 0x7FFFFFFFu; }
+
+// j + h, j + 2 h, j + 3 h and, when MINUS, j - h: exact in one frame, each rounded
+// once (for J = j + F/2 = rho u of Eq. Momentum, P = j + F, P + F/2 and j - F/2, with
+// h = F/2). Finite operands; the results of non-finite ones are unspecified.
+template <bool MINUS>
+PPLBM_FX void j_h_combos(double j, double h, double* jh, double* j2h, double* j3h, double* jmh) {
+  const u64 bj = bits_of(j), bh = bits_of(h);
+  const unsigned mj = mag_hi(bj), mh = mag_hi(bh);
+  const int eg = frame_top(mj > mh ? mj : mh);  // |j| + 3 |h| < 4 2^(64 - kG) = 2^62
+  const u64 tj = (u64)sterm(bj, eg), th = (u64)sterm(bh, eg);
+  const u64 s1 = tj + th, s2 = s1 + th;
+  *jh = double_of(round_frame_s((i64)s1, eg));
+  *j2h = double_of(round_frame_s((i64)s2, eg));
+  *j3h = double_of(round_frame_s((i64)(s2 + th), eg));
+  if (MINUS) *jmh = double_of(round_frame_s((i64)(tj - th), eg));
+}
+
+// headroom of the collision output frame: the largest combination below has
+// coefficients summing to 44 < 2^6, plus the sign
+constexpr int kGOut = 7;
+
+// Post-collision populations f*_0..8 of the reduced collision (Lambda = I, or with
+// rows 7, 8 relaxing at omega = 1/tau(rho) when SHEAR): with every input scaled by
+// 1/36 except zz,
+//   r = rho/36, xx = Pi_xx/36, yy = Pi_yy/36, xy = Pi_xy/36 (the unit-tau second
+//   moments u (P + F/2) and u_x P_y + u_y F_x/2), px = P_x/36, py = P_y/36 (P = j + F),
+//   zz = the Li term sigma |F|^2 / (3 psi^2), and for SHEAR p7 = (1 - omega) A7/36,
+//   p8 = (1 - omega) A8/36 (the rows 7, 8 corrections),
+// the populations w_i [rho + 3 c_i.P + 4.5 (c_i c_i - I/3) : Pi*] + zz (-8, 1, ..., 1)
+// are small-integer combinations:
+//   f1,3 = 4 r + 12 xx - 6 yy + 9 p7 + zz +- 12 px,  f2,4 = 4 r - 6 xx + 12 yy - 9 p7 + zz +- 12 py,
+//   f5,7 = B + 9 (xy + p8) +- 3 (px + py),            f6,8 = B - 9 (xy + p8) +- 3 (py - px),
+//   B = r + 3 (xx + yy) + zz,                         f0 = 4 (4 r - 6 (xx + yy) - 2 zz),
+// evaluated exactly in one frame over the seven (nine) inputs and each rounded once.
+// A non-finite input makes every population NaN.
+template <bool SHEAR>
+PPLBM_FX void reduced_populations(double r, double xx, double yy, double xy, double px, double py, double zz,
+                                  double p7, double p8, double (&f)[9]) {
+  const u64 br = bits_of(r), bxx = bits_of(xx), byy = bits_of(yy), bxy = bits_of(xy);
+  const u64 bpx = bits_of(px), bpy = bits_of(py), bz = bits_of(zz);
+  const u64 b7 = SHEAR ? bits_of(p7) : 0ull, b8 = SHEAR ? bits_of(p8) : 0ull;
+  unsigned mx = mag_hi(br);
+  mx = mx > mag_hi(bxx) ? mx : mag_hi(bxx);
+  mx = mx > mag_hi(byy) ? mx : mag_hi(byy);
+  mx = mx > mag_hi(bxy) ? mx : mag_hi(bxy);
+  mx = mx > mag_hi(bpx) ? mx : mag_hi(bpx);
+  mx = mx > mag_hi(bpy) ? mx : mag_hi(bpy);
+  mx = mx > mag_hi(bz) ? mx : mag_hi(bz);
+  if (SHEAR) {
+    mx = mx > mag_hi(b7) ? mx : mag_hi(b7);
+    mx = mx > mag_hi(b8) ? mx : mag_hi(b8);
+  }
+  const int eg = (int)(mx >> 20) + kGOut;
+  // unsigned arithmetic (wrapping); every final combination lies below 2^63 in magnitude
+  const u64 tr = (u64)sterm(br, eg), txx = (u64)sterm(bxx, eg), tyy = (u64)sterm(byy, eg);
+  const u64 txy = (u64)sterm(bxy, eg), tx = (u64)sterm(bpx, eg), ty = (u64)sterm(bpy, eg);
+  const u64 tz = (u64)sterm(bz, eg);
+  const u64 t7 = SHEAR ? (u64)sterm(b7, eg) : 0ull, t8 = SHEAR ? (u64)sterm(b8, eg) : 0ull;
+  const u64 T = txx + tyy;
+  const u64 C = 4 * tr + tz;
+  const u64 X = 12 * txx - 6 * tyy + 9 * t7;  // f1, f3 part
+  const u64 Y = 6 * T - X;                    // 12 yy - 6 xx - 9 p7: f2, f4 part
+  const u64 a1 = C + X, a2 = C + Y;
+  const u64 x12 = 12 * tx, y12 = 12 * ty;
+  const u64 B = tr + 3 * T + tz;
+  const u64 Q = 9 * (txy + t8);
+  const u64 S = 3 * (tx + ty), D = 3 * (ty - tx);
+  const u64 bq = B + Q, bm = B - Q;
+  u64 n[9];
+  n[1] = a1 + x12;
+  n[3] = a1 - x12;
+  n[2] = a2 + y12;
+  n[4] = a2 - y12;
+  n[5] = bq + S;
+  n[7] = bq - S;
+  n[6] = bm + D;
+  n[8] = bm - D;
+  n[0] = 4 * tr - 6 * T - 2 * tz;  // f0 / 4
+  const bool bad = mx >= 0x7FF00000u;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const u64 v = round_frame_s((i64)n[k], k == 0 ? eg + 2 : eg);
+    f[k] = double_of(bad ? 0x7FF8000000000000ull : v);
+  }
+}
+
 // True if all K values are positive normal doubles below 2^1008 (high words in
 // [0x00100000, 0x7EF00000): a negative value's high word is above the range); the
 // largest high word goes to *max_hi.

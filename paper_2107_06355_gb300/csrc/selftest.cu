@@ -244,3 +244,36 @@ extern "C" pplbm_status pplbm_fixsum_eval(long long n, const double* f, const do
   pplbm::k_fixsum_eval<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, f, p, out);
   return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
 }
+
+// The collision pass's fixed-point output stage and sums on caller data, one thread per row.
+namespace pplbm {
+namespace {
+
+template <bool SHEAR>
+__global__ void k_fixsum_collision_eval(long long n, const double* q, const double* jh, double* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* r = q + 9 * i;
+  double f[9];
+  fx::reduced_populations<SHEAR>(r[0], r[1], r[2], r[3], r[4], r[5], r[6], SHEAR ? r[7] : 0.0, SHEAR ? r[8] : 0.0, f);
+  double* o = out + 13 * i;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[k] = f[k];
+  fx::j_h_combos<true>(jh[2 * i], jh[2 * i + 1], &o[9], &o[10], &o[11], &o[12]);
+}
+
+}  // namespace
+}  // namespace pplbm
+
+extern "C" pplbm_status pplbm_fixsum_collision_eval(long long n, int32_t shear, const double* q, const double* jh,
+                                                    double* out, void* stream) {
+  if (n < 0 || n > 0x7FFFFFFFLL * 255 || (n > 0 && (!q || !jh || !out))) return PPLBM_ERR_ARG;
+  if (n == 0) return PPLBM_OK;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (shear)
+    pplbm::k_fixsum_collision_eval<true><<<blocks, 256, 0, s>>>(n, q, jh, out);
+  else
+    pplbm::k_fixsum_collision_eval<false><<<blocks, 256, 0, s>>>(n, q, jh, out);
+  return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
+}

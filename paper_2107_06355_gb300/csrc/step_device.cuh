@@ -217,6 +217,42 @@ __device__ __forceinline__ void collide_reduced(const StepArgs& a, int64_t node,
   out.f[8] = fma(-pd, 1.0 / 12.0, dm);
 }
 
+// The same collision (Lambda = I, or rows 7, 8 at omega = 1/tau(rho) for kShearTau),
+// without the surface-tension source, arranged so that the FP64 pipe does only the
+// products, the reciprocals and the Li term (19 FP64 instructions per node for unit
+// relaxation times, 32 for the two-phase set): the sums J = j + h, P = j + 2h,
+// P + h (and j - h) come from one fixed-point frame, and the nine populations are
+// exact small-integer combinations of the inputs scaled by 1/36 (fixsum.cuh), each
+// rounded once, instead of chains of FP64 fused multiply-adds.
+template <int KIND>
+__device__ __forceinline__ void collide_reduced_fx(const StepArgs& a, int64_t node, double rho, double jx, double jy,
+                                                   double psi0, double gx, double gy, Post& out) {
+  constexpr bool kShear = KIND == kShearTau;
+  const double cH = a.half_force * psi0;  // h = F/2 = cH g, cH = -G psi / 24
+  const double hx = cH * gx, hy = cH * gy;
+  double Jx, Px, Qx, Kx = 0.0, Jy, Py, Qy, Ky = 0.0;
+  fx::j_h_combos<kShear>(jx, hx, &Jx, &Px, &Qx, &Kx);
+  fx::j_h_combos<kShear>(jy, hy, &Jy, &Py, &Qy, &Ky);
+  const double inv36 = fast_rcp(36.0 * rho);
+  const double ux = Jx * inv36, uy = Jy * inv36;  // u / 36
+  const double xx = ux * Qx, yy = uy * Qy;        // Pi_xx / 36 = u_x (P_x + h_x) / 36
+  const double xy = fma(ux, Py, uy * hx);         // Pi_xy / 36
+  const double zz = a.zz_scale * fma(gx, gx, gy * gy);
+  constexpr double s36 = 1.0 / 36.0;
+  double p7 = 0.0, p8 = 0.0;
+  if (kShear) {
+    // rows 7, 8: m* = m_eq + S/2 + (1 - omega)(m + S/2 - m_eq), the brackets
+    // A7 = m7 - u_x (j_x - h_x) + u_y (j_y - h_y), A8 = m8 - u_x j_y + u_y h_x
+    const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
+    const double omc = 1.0 - om;
+    const double A7 = fma(-ux, Kx, fma(uy, Ky, a.mom[3 * a.n + node] * s36));
+    const double A8 = fma(-ux, jy, fma(uy, hx, a.mom[4 * a.n + node] * s36));
+    p7 = omc * A7;
+    p8 = omc * A8;
+  }
+  fx::reduced_populations<kShear>(rho * s36, xx, yy, xy, Px * s36, Py * s36, zz, p7, p8, out.f);
+}
+
 // General MRT collision in moment space (six relaxation times). With ST the
 // surface-tension source C_k = l_k D_k enters as the shift D of m_eq in rows 1, 2,
 // 7, 8 (+1.5 tr Q, -1.5 tr Q, -(Q_xx - Q_yy), -Q_xy), since m - l (m - m_eq - D) =
@@ -314,6 +350,11 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, int x, int y, co
   constexpr bool kST = ST && !FIELDS;
   if (KIND == kFullMrt) {
     collide_full<kST>(a, node, p0, gx, gy, sq, o, &rho, &ux, &uy);
+  } else if (!FIELDS && (!kST || a.kappa_q == 0.0)) {
+    // (a kernel built with the source runs lattices without it, kappa = 0, in a batch:
+    // they take the same arithmetic as in the kernel without the source)
+    rho = a.mom[node];
+    collide_reduced_fx<KIND>(a, node, rho, a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, o);
   } else {
     rho = a.mom[node];
     collide_reduced<KIND, kST>(a, node, rho, a.mom[N + node], a.mom[2 * N + node], p0, gx, gy, sq, o, &ux, &uy);

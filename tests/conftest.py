@@ -31,7 +31,9 @@ def fixsum_host(tmp_path_factory):
     subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", so,
                     os.path.join(ROOT, "tests", "native", "fixsum_host.cpp")], check=True)
     lib = C.CDLL(so)
-    for name in ("fx_density", "fx_stencil"):
+    for name in ("fx_density", "fx_stencil", "fx_j_h"):
         getattr(lib, name).argtypes = [C.c_longlong, C.c_void_p, C.c_void_p]
         getattr(lib, name).restype = None
+    lib.fx_populations.argtypes = [C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
+    lib.fx_populations.restype = None
     return lib

@@ -29,3 +29,26 @@ void fx_stencil(long long n, const double* p, double* out) {
   }
 }
 }
+
+extern "C" {
+
+// n rows of (j, h) -> out (n x 4): j + h, j + 2h, j + 3h, j - h
+void fx_j_h(long long n, const double* in, double* out) {
+  for (long long i = 0; i < n; ++i)
+    j_h_combos<true>(in[2 * i], in[2 * i + 1], &out[4 * i], &out[4 * i + 1], &out[4 * i + 2], &out[4 * i + 3]);
+}
+
+// n rows of (r, xx, yy, xy, px, py, zz, p7, p8) -> out (n x 9) populations; shear != 0
+// takes p7, p8 into account
+void fx_populations(long long n, int shear, const double* in, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    const double* q = in + 9 * i;
+    double f[9];
+    if (shear)
+      reduced_populations<true>(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], f);
+    else
+      reduced_populations<false>(q[0], q[1], q[2], q[3], q[4], q[5], q[6], 0.0, 0.0, f);
+    for (int k = 0; k < 9; ++k) out[9 * i + k] = f[k];
+  }
+}
+}

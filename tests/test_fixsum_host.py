@@ -159,3 +159,131 @@ def test_shan_chen_stencil_non_finite_or_negative_psi_gives_nan(fx):
     p[0, 1] = 0.0
     out = stencil(fx, p)[0]
     assert abs(out[0] - 4 * 0.3) <= 2 * math.ulp(1.2) and abs(out[1]) <= math.ulp(0.3)
+
+
+def j_h(lib, a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.zeros((a.shape[0], 4))
+    lib.fx_j_h(a.shape[0], a.ctypes.data, out.ctypes.data)
+    return out
+
+
+def populations(lib, q, shear):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros((q.shape[0], 9))
+    lib.fx_populations(q.shape[0], 1 if shear else 0, q.ctypes.data, out.ctypes.data)
+    return out
+
+
+def frame_bound(res, exact, operands, coef_sum, headroom):
+    """Half an ulp of the result plus half a frame unit per unit of coefficient (each
+    operand is rounded to its nearest frame unit), plus one unit of slack; a frame unit
+    is 2^-(11 - headroom) of the largest operand's ulp."""
+    big = max(abs(float(v)) for v in operands)
+    unit = Fraction(ulp(big)) / 2 ** (11 - headroom)
+    half = Fraction(ulp(float(res))) / 2
+    if exact != 0:
+        half = max(half, Fraction(ulp(float(exact))) / 2)
+    return half + (Fraction(coef_sum, 2) + 1) * unit
+
+
+def test_j_h_combinations_within_the_bound(fx):
+    rng = np.random.default_rng(5)
+    n = 4000
+    j = rng.normal(size=n) * 10.0 ** rng.uniform(-8, 0, size=n)
+    h = rng.normal(size=n) * 10.0 ** rng.uniform(-8, 0, size=n)
+    j[:50] = 0.0
+    h[50:100] = -0.0
+    out = j_h(fx, np.stack([j, h], axis=1))
+    for i in range(n):
+        J, H = Fraction(float(j[i])), Fraction(float(h[i]))
+        for k, (ex, cs) in enumerate(((J + H, 2), (J + 2 * H, 3), (J + 3 * H, 4), (J - H, 2))):
+            err = abs(Fraction(float(out[i, k])) - ex)
+            assert err <= frame_bound(out[i, k], ex, (j[i], h[i]), cs, 4), (i, k)
+    # exact cases: zero operands, and a state at rest
+    assert np.array_equal(out[:50, 0], h[:50]) and np.array_equal(out[50:100, 0], j[50:100])
+    assert np.array_equal(out[:50, 2], 3 * h[:50])
+
+
+W = [Fraction(4, 9)] + [Fraction(1, 9)] * 4 + [Fraction(1, 36)] * 4
+CX = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+CY = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+
+
+def populations_by_definition(q, shear):
+    """f*_i = w_i [rho + 3 c_i.P + 4.5 (c_i c_i - I/3) : Pi*] + zz (-8, 1, ..., 1), from the
+    unscaled quantities rho = 36 r, P = 36 p, Pi = 36 (xx, yy, xy); with the rows 7, 8
+    corrections Pi*_xx = Pi_xx + 18 p7 36 / 36, i.e. Pi*_xx - Pi*_yy = Pi_xx - Pi_yy + 36 p7
+    and Pi*_xy = Pi_xy + 36 p8 (the trace relaxes with unit rate)."""
+    r, xx, yy, xy, px, py, zz, p7, p8 = [Fraction(float(v)) for v in q]
+    if not shear:
+        p7 = p8 = Fraction(0)
+    rho, Px, Py = 36 * r, 36 * px, 36 * py
+    Pxx, Pyy, Pxy = 36 * xx + 18 * p7, 36 * yy - 18 * p7, 36 * (xy + p8)
+    f = []
+    for i in range(9):
+        cx, cy = CX[i], CY[i]
+        quad = (cx * cx - Fraction(1, 3)) * Pxx + (cy * cy - Fraction(1, 3)) * Pyy + 2 * cx * cy * Pxy
+        z = -8 * zz if i == 0 else zz
+        f.append(W[i] * (rho + 3 * (cx * Px + cy * Py) + Fraction(9, 2) * quad) + z)
+    return f
+
+
+COEF_SUM = [72, 44, 44, 44, 44, 32, 32, 32, 32]
+
+
+@pytest.mark.parametrize("shear", [False, True])
+@pytest.mark.parametrize("regime", ["bulk", "interface", "li_dominant"])
+def test_reduced_populations_equal_the_collision_definition(fx, shear, regime):
+    """The fixed-point output stage against the populations' definition (not against its
+    own coefficient table): bulk nodes (second moments and forcing small against rho),
+    interface nodes (all of similar size) and vapour nodes beside an interface where the
+    Li term exceeds rho."""
+    rng = np.random.default_rng({"bulk": 1, "interface": 2, "li_dominant": 3}[regime] + 10 * shear)
+    n = 2500
+    rho = 10.0 ** rng.uniform(-5, 0, size=n)
+    scale = {"bulk": 1e-4, "interface": 0.3, "li_dominant": 1.0}[regime]
+    q = np.empty((n, 9))
+    q[:, 0] = rho / 36
+    for k in range(1, 9):
+        q[:, k] = rng.normal(size=n) * rho * scale / 36
+    if regime == "li_dominant":
+        q[:, 6] = rho * 10.0 ** rng.uniform(1, 4, size=n)
+    out = populations(fx, q, shear)
+    for i in range(n):
+        ref = populations_by_definition(q[i], shear)
+        ops = q[i] if shear else q[i, :7]
+        for k in range(9):
+            assert abs(Fraction(float(out[i, k])) - ref[k]) <= frame_bound(out[i, k], ref[k], ops, COEF_SUM[k], 7), \
+                (i, k, float(out[i, k]), float(ref[k]))
+
+
+def test_reduced_populations_conserve_mass_and_keep_rest_exact(fx):
+    rng = np.random.default_rng(9)
+    # a node at rest with no force: the equilibrium weights times rho, exactly
+    r = 10.0 ** rng.uniform(-5, 0, size=200) / 36
+    q = np.zeros((200, 9))
+    q[:, 0] = r
+    out = populations(fx, q, False)
+    w = np.array([16, 4, 4, 4, 4, 1, 1, 1, 1], dtype=float)
+    assert np.array_equal(out, w * r[:, None])
+    # a mirror-symmetric node (P_x = 0, Pi_xy = 0) gives f1 = f3, f5 = f6, f7 = f8 exactly
+    q = rng.normal(size=(300, 9)) * 1e-3
+    q[:, 0] = np.abs(q[:, 0]) + 0.01
+    q[:, 3] = q[:, 4] = q[:, 8] = 0.0
+    out = populations(fx, q, True)
+    assert np.array_equal(out[:, 1], out[:, 3]) and np.array_equal(out[:, 5], out[:, 6])
+    assert np.array_equal(out[:, 7], out[:, 8])
+    # the sum of the nine populations is rho = 36 r to within the nine roundings
+    q = np.abs(rng.normal(size=(500, 9))) * 1e-2
+    q[:, 0] = 0.1 + q[:, 0]
+    out = populations(fx, q, True)
+    for i in range(500):
+        tot = sum(Fraction(float(v)) for v in out[i])
+        assert abs(tot - 36 * Fraction(float(q[i, 0]))) <= 12 * Fraction(ulp(36 * q[i, 0]))
+
+
+def test_reduced_populations_non_finite_input_gives_nan(fx):
+    q = np.full((3, 9), 0.01)
+    q[0, 6], q[1, 2], q[2, 8] = np.inf, np.nan, np.inf
+    assert np.all(np.isnan(populations(fx, q, True)))

@@ -102,3 +102,44 @@ def test_fixed_point_sums_device_build_equals_host_build(fixsum_host):
     assert L.lib().pplbm_fixsum_eval(-1, None, None, None, None) == L.PPLBM_ERR_ARG
     assert L.lib().pplbm_fixsum_eval(4, None, None, None, None) == L.PPLBM_ERR_ARG
     assert L.lib().pplbm_fixsum_eval(0, None, None, None, None) == 0
+
+
+@pytest.mark.parametrize("shear", [0, 1])
+def test_collision_fixed_point_device_build_equals_host_build(fixsum_host, shear):
+    """The collision pass's fixed-point output stage and j/h sums (fixsum.cuh) compiled
+    for sm_103a against the host build of the same source (checked in
+    test_fixsum_host.py against the populations' definition): bit for bit on 2^20 rows
+    in the bulk, interface and Li-dominated regimes, with zeros and non-finite inputs."""
+    import numpy as np
+
+    from paper_2107_06355_gb300 import _lib as L
+
+    rng = np.random.default_rng(36 + shear)
+    n = 1 << 20
+    rho = 10.0 ** rng.uniform(-5, 0, size=n)
+    scale = np.choose(rng.integers(0, 3, size=n), [1e-4, 0.3, 1.0])
+    q = rng.normal(size=(n, 9)) * (rho * scale / 36)[:, None]
+    q[:, 0] = rho / 36
+    q[::3, 6] = rho[::3] * 10.0 ** rng.uniform(1, 4, size=q[::3].shape[0])
+    q[:1000, 1:] = 0.0
+    q[1000:1010, 5] = np.inf
+    q[1010:1020, 7] = np.nan
+    jh = rng.normal(size=(n, 2)) * 10.0 ** rng.uniform(-8, 0, size=(n, 2))
+    jh[:500, 0] = 0.0
+    jh[500:1000, 1] = -0.0
+    host = np.zeros((n, 9))
+    sh = np.ascontiguousarray(q)
+    fixsum_host.fx_populations(n, shear, sh.ctypes.data, host.ctypes.data)
+    hj = np.zeros((n, 4))
+    fixsum_host.fx_j_h(n, jh.ctypes.data, hj.ctypes.data)
+    qd, jd = torch.from_numpy(q).cuda(), torch.from_numpy(jh).cuda()
+    out = torch.empty((n, 13), dtype=torch.float64, device="cuda")
+    st = L.lib().pplbm_fixsum_collision_eval(n, shear, C.c_void_p(qd.data_ptr()), C.c_void_p(jd.data_ptr()),
+                                             C.c_void_p(out.data_ptr()),
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    dev = out.cpu().numpy()
+    assert np.array_equal(dev[:, :9].view(np.int64), host.view(np.int64))
+    assert np.array_equal(dev[:, 9:].view(np.int64), hj.view(np.int64))
+    assert L.lib().pplbm_fixsum_collision_eval(-1, 0, None, None, None, None) == L.PPLBM_ERR_ARG
+    assert L.lib().pplbm_fixsum_collision_eval(2, 0, None, None, None, None) == L.PPLBM_ERR_ARG
