@@ -60,7 +60,7 @@ MIN_BLOCKS = 5
 # (COUNTS).
 FP64_PER_NODE = {"rho_psi": 15, "collide": 19}
 # integer-pipe (ALU) instructions per node of the same passes (ncu; fallback figures)
-ALU_PER_NODE = {"rho_psi": 223, "collide": 1053}
+ALU_PER_NODE = {"rho_psi": 223, "collide": 1015}
 # ALU pipe issue rate: 64 thread instructions per SM per clock (ncu's
 # sm__pipe_alu_cycles_active scale: 82.7 % active at 16.6e12 instructions/s)
 ALU_PER_SM_CLK = 64
@@ -78,11 +78,11 @@ BYTES_PER_NODE_SHEAR = {"rho_psi": 72 + 48, "collide": 40 + 8 + 72}
 BYTES_PER_NODE_SCOPE = 232
 # FP64-pipe and integer-pipe (ALU) instructions of one MacCormack step per grid point
 # (ncu, sm__inst_executed_pipe_fp64 / _alu x 32 per point, one kernel per capture, the
-# 2048 x 1024 grid of fd_throughput): predictor 65.0 / 3,653, corrector 71.0 / 3,672,
-# two EOS passes of 24.9 / 11; the update kernels' stencil sums and differences run on
-# the integer pipe, which binds them (94 % / 86 % active against 54 % FP64)
-FD_FP64_PER_POINT = 65.0 + 71.0 + 2 * 24.9
-FD_ALU_PER_POINT = 3653 + 3672 + 2 * 11
+# 2048 x 1024 grid of fd_throughput): predictor 54.0 / 1,948, corrector 60.0 / 1,960,
+# two EOS passes of 24.9 / 11; the update kernels' stencil differences are integer
+# combinations in fixed-point frames (76 % / 73 % ALU against 67 % / 71 % FP64 active)
+FD_FP64_PER_POINT = 54.0 + 60.0 + 2 * 24.9
+FD_ALU_PER_POINT = 1948 + 1960 + 2 * 11
 
 # Per launch of each batched pass on the headline workload (all 64 lattices), from
 # one ncu capture per kernel (--metrics dram__bytes_read.sum, dram__bytes_write.sum,
@@ -387,7 +387,8 @@ def plan_times(torch, stream, batch, P, steps=1000):
     """Per-plan ms per step of the batch over `steps` steps each (state restored)."""
     out = {}
     saved = [batch.get_f(k).clone() for k in range(batch.n)]
-    for name, mode in (("launches", P.PLAN_LAUNCHES), ("graph", P.PLAN_GRAPH), ("persistent", P.PLAN_PERSISTENT)):
+    for name, mode in (("launches", P.PLAN_LAUNCHES), ("graph", P.PLAN_GRAPH), ("persistent", P.PLAN_PERSISTENT),
+                       ("pipelined", P.PLAN_PIPELINED)):
         batch.set_plan(mode, 0)
         batch.step(4)
         ms = time_device(torch, stream, lambda: batch.step(steps))
@@ -637,7 +638,7 @@ def fd_throughput(torch, fp64_peak, sm_mhz, steps=200):
     alu_peak = ALU_PER_SM_CLK * 152 * sm_mhz * 1e6
     return {"grid": f"{nx}x{ny}, dx=1, dt=0.4", "mlups": pts / 1e6,
             "ms_per_step": ms / steps, "finite": ok, "launches_per_step": 4,
-            "roofline": {"bound": "alu", "pipe": "integer (the update kernels' additions)",
+            "roofline": {"bound": "alu", "pipe": "integer (the update kernels' stencil sums)",
                          "achieved": alu / 1e12, "peak": alu_peak / 1e12, "unit": "T integer instr/s",
                          "frac": alu / alu_peak, "alu_per_point_step": FD_ALU_PER_POINT},
             "fp64_pipe": {"achieved": achieved / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -772,9 +773,10 @@ def run_reference(args):
 
 # ---- small cases for ncu captures -----------------------------------------------------
 
-def profile_sweep(n=16):
+def profile_sweep(n=16, plan="launches"):
     """The first `n` lattices of the 64-lattice sweep (the bench's EOS and tiles),
-    launches plan, 3 steps: 3 launches of each batched pass."""
+    3 steps: under the launches plan 3 launches of each batched pass, under the
+    pipelined plan 7 launches of the mixed kernel (prologue, 5 mixed, epilogue)."""
     import torch
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
@@ -782,7 +784,7 @@ def profile_sweep(n=16):
     build_lib()
     specs = sweep_specs()[:n]
     b, _, _, _ = make_batch(P, I, specs, torch.cuda.current_stream())
-    b.set_plan(P.PLAN_LAUNCHES, 0)
+    b.set_plan(P.PLAN_PIPELINED if plan == "pipelined" else P.PLAN_LAUNCHES, 0)
     b.step(3)
     b.sync()
     torch.cuda.synchronize()
@@ -867,7 +869,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline line only (no extra keys)")
-    ap.add_argument("--plan", default="auto", choices=["auto", "launches", "graph", "persistent"],
+    ap.add_argument("--plan", default="auto", choices=["auto", "launches", "graph", "persistent", "pipelined"],
                     help="batched-engine plan for the timed run (auto: autotuned)")
     ap.add_argument("--profile-sweep", type=int, default=None, metavar="N",
                     help="3 steps of the first N lattices of the sweep (a small case for ncu) and exit")
@@ -882,7 +884,7 @@ def main():
         build_lib()
         return fp64_probe_sweep(torch, dist_env()[2])
     if args.profile_sweep is not None:
-        return profile_sweep(args.profile_sweep)
+        return profile_sweep(args.profile_sweep, "pipelined" if args.plan == "pipelined" else "launches")
     if args.profile_impact:
         return profile_impact_single()
     if args.profile_fd:
@@ -924,10 +926,11 @@ def main():
         plan = batch.autotune(trial_steps=100)
     else:
         batch.set_plan({"launches": P.PLAN_LAUNCHES, "graph": P.PLAN_GRAPH,
-                        "persistent": P.PLAN_PERSISTENT}[args.plan], 0)
+                        "persistent": P.PLAN_PERSISTENT, "pipelined": P.PLAN_PIPELINED}[args.plan], 0)
         plan = batch.plan()
-    mode = {0: "launches", 1: "graph", 2: "persistent"}[plan["mode"]]
-    per_pass = plan["mode"] != P.PLAN_PERSISTENT
+    mode = {0: "launches", 1: "graph", 2: "persistent", 3: "pipelined"}[plan["mode"]]
+    # per-pass kernel durations exist where each launch runs one pass
+    per_pass = plan["mode"] in (P.PLAN_LAUNCHES, P.PLAN_GRAPH)
     batch.step(args.warmup)
     torch.cuda.synchronize()
     batch.enable_timing(1)
@@ -997,13 +1000,20 @@ def main():
         dom_bytes = BYTES_PER_NODE[dom] * nodes
         share = kern[dom] / (kern["rho_psi"] + kern["collide"])
     else:
-        kern = {"persistent": call_ms / max(1, call_steps)}
-        dom, dom_name, share = "persistent", "k_batch_persistent", 1.0
+        # the plan's launches run both passes: the step's time against both passes'
+        # instruction counts
+        kern = {mode: call_ms / max(1, call_steps)}
+        dom, share = mode, 1.0
+        dom_name = {"persistent": "k_batch_persistent", "pipelined": "k_batch_mixed"}[mode]
         dom_s = call_ms / max(1, call_steps) / 1e3
         dom_flops = sum(fp64_node.values()) * nodes
         dom_bytes = sum(BYTES_PER_NODE.values()) * nodes
     achieved = dom_flops / dom_s / 1e12
-    launches_per_block = 2 * args.steps if per_pass else 1
+    # kernel launches per timed block: two per step; one cooperative launch per call
+    # (persistent); 2 steps + 1 (pipelined: prologue, two mixed launches per step less
+    # one, epilogue)
+    launches_per_block = {"launches": 2 * args.steps, "graph": 2 * args.steps, "persistent": 1,
+                          "pipelined": 2 * args.steps + 1}[mode]
     # the dominant kernel against both arithmetic pipes: FP64 instructions against the
     # measured FP64 issue rate, integer instructions against the ALU pipe's 64 per SM per
     # clock at the sampled clock; `roofline` is the pipe closer to its limit (the bound)
@@ -1014,13 +1024,14 @@ def main():
                  "flop_convention": "1 per FP64 add/mul/fma instruction (per thread); "
                                     f"{fp64_node.get(dom, sum(fp64_node.values()))} per node ({fp64_src})",
                  "peak_source": "measured: pplbm_fp64_peak in this run (fp64_peak_measured)"}
-    int_pipe = {"pipe": "integer", "kernel": dom_name, "alu_per_node": pass_alu(dom) if per_pass else None,
-                "achieved": (pass_alu(dom) * nodes / dom_s / 1e12) if per_pass else None,
+    alu_node = pass_alu(dom) if per_pass else sum(pass_alu(k) for k in ("rho_psi", "collide"))
+    int_pipe = {"pipe": "integer", "kernel": dom_name, "alu_per_node": alu_node,
+                "achieved": alu_node * nodes / dom_s / 1e12,
                 "peak": alu_peak, "unit": "T integer instr/s",
-                "frac": (pass_alu(dom) * nodes / dom_s / 1e12 / alu_peak) if per_pass else None,
+                "frac": alu_node * nodes / dom_s / 1e12 / alu_peak,
                 "peak_source": f"derived: 64 integer lanes per SM x 152 SMs x {mhz:.0f} MHz (sampled)",
                 "note": "the pass's sums run on the integer pipe (fixed-point frames and software IEEE adds)"}
-    if int_pipe["frac"] is not None and int_pipe["frac"] > fp64_pipe["frac"]:
+    if int_pipe["frac"] > fp64_pipe["frac"]:
         roof, other = dict(int_pipe), fp64_pipe
     else:
         roof, other = dict(fp64_pipe), int_pipe
@@ -1058,7 +1069,7 @@ def main():
                                "achieved": sum(fp64_node.values()) * nodes / step_s / 1e12,
                                "frac": sum(fp64_node.values()) * nodes / step_s / 1e12 / fp64_peak},
         "autotune_ms_per_step": {"launches": plan["ms_launches"], "graph": plan["ms_graph"],
-                                 "persistent": plan["ms_persistent"]},
+                                 "persistent": plan["ms_persistent"], "pipelined": plan["ms_pipelined"]},
         "gpu_launches": launches_per_block * len(blocks),
         "clocks": clk,
     }

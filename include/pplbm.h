@@ -386,6 +386,13 @@ typedef struct pplbm_batch pplbm_batch;
 #define PPLBM_PLAN_GRAPH 1       /* the same launches, two steps per replayed CUDA graph */
 #define PPLBM_PLAN_PERSISTENT 2  /* one cooperative launch per call; bounded grid barriers
                                     between the passes (PPLBM_ERR_TIMEOUT if a wait gives up) */
+#define PPLBM_PLAN_PIPELINED 3   /* the instances in two groups of about equal node counts, the
+                                    second half a step behind the first within a call: every
+                                    launch runs one group's density pass with the other's
+                                    collision pass (the FP64-bound and the integer-bound pass
+                                    share the SMs); 2 nsteps + 1 launches per call, two-step
+                                    CUDA graphs in between; every instance ends the call at the
+                                    same step */
 
 typedef struct pplbm_batch_plan {
   int32_t mode;        /* PPLBM_PLAN_* */
@@ -395,6 +402,7 @@ typedef struct pplbm_batch_plan {
   int32_t k2_tiles;    /* work items of the collision pass */
   double ms_launches, ms_graph, ms_persistent;  /* per-step times measured by the autotuner (0 if not) */
   double ms_chosen;
+  double ms_pipelined;                          /* the pipelined plan's, likewise */
 } pplbm_batch_plan;
 
 /* Workspace bytes for n instances: per instance two f buffers, psi, the moment
@@ -450,8 +458,9 @@ pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps);
  * ceil(capacity/2) two-step graphs per parity built here, each replayed at most once
  * between two pplbm_batch_pass_times calls (steps beyond them run as timed plain
  * launches). PPLBM_ERR_STATE under the persistent plan, whose passes share one
- * launch. capacity = 0 turns it off. The autotuner times every plan without these
- * events and turns them off if it keeps the persistent plan. pplbm_batch_pass_times
+ * launch, and under the pipelined plan, whose launches mix the passes. capacity = 0
+ * turns it off. The autotuner times every plan without these events and turns them
+ * off if it keeps the persistent or the pipelined plan. pplbm_batch_pass_times
  * synchronises and returns, since the previous call, the summed milliseconds and
  * launch counts of the density/psi pass (index 0) and of the collision pass (index
  * 1), then resets them. */

@@ -9,7 +9,7 @@ simulation class fails.
 from ._lib import (BC_PERIODIC, BC_PERIODIC_X, BC_PERIODIC_Y, BC_WALL_BOTTOM, BC_WALL_TOP, BC_WALLS_Y,  # noqa: F401
                    EOS_CS, EOS_SMOOTH, EOS_PENG, EOS_SMOOTH_MOD, FORCING_GUO, FORCING_LI, RELAX_MRT, RELAX_TWO_PHASE, PPLBMError,
                    lib)
-from ._lib import PLAN_GRAPH, PLAN_LAUNCHES, PLAN_PERSISTENT  # noqa: F401
+from ._lib import PLAN_GRAPH, PLAN_LAUNCHES, PLAN_PERSISTENT, PLAN_PIPELINED  # noqa: F401
 from .batch import Batch  # noqa: F401
 from .fd import FDSolver  # noqa: F401
 from .lattice import EOSParams, Relax, Simulation, eos_setup  # noqa: F401

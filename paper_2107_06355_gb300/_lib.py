@@ -73,7 +73,7 @@ class pplbm_eos_derived(C.Structure):
 class pplbm_batch_plan(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_width", C.c_int32), ("k1_blocks", C.c_int32), ("k2_tiles", C.c_int32),
                 ("ms_launches", C.c_double), ("ms_graph", C.c_double), ("ms_persistent", C.c_double),
-                ("ms_chosen", C.c_double)]
+                ("ms_chosen", C.c_double), ("ms_pipelined", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -89,6 +89,7 @@ SENS_PARAMS = {"alpha": 0, "a_vap": 1, "a_liq": 2, "kappa": 3}
 PLAN_LAUNCHES = 0
 PLAN_GRAPH = 1
 PLAN_PERSISTENT = 2
+PLAN_PIPELINED = 3
 
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
   __shared__ double red[kNT];
   const StepArgs& a = g.a;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  load_psi_tile(a, sp, x0, y0, kTX, kTY, threadIdx.y * kTX + threadIdx.x, kNT);
+  load_psi_tile(a, sp, x0, y0, kTX, kTY, threadIdx.x, threadIdx.y, threadIdx.y * kTX + threadIdx.x, kNT);
   __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   double zs_b = 0.0, kap_b = 0.0;

@@ -14,6 +14,13 @@
 //                   loop over work items with a grid barrier between the passes.
 //                   Every barrier wait is bounded: after the spin limit the block
 //                   sets the error word (PPLBM_ERR_TIMEOUT) and returns.
+//   PLAN_PIPELINED  the instances in two groups of about equal node counts, group B
+//                   half a step behind group A inside a call: each launch runs the
+//                   density pass of one group with the collision pass of the other
+//                   (work items interleaved), so that the FP64-bound and the
+//                   integer-bound pass share the SMs; a prologue (density pass of A)
+//                   and an epilogue (collision pass of B) bring every instance to the
+//                   same step at the end of the call; two-step CUDA graphs in between.
 // The per-node arithmetic is the single-lattice kernels' (step_device.cuh), so a
 // batched step is bitwise identical to stepping each lattice alone.
 #include <cuda_runtime.h>
@@ -106,6 +113,13 @@ struct pplbm_batch {
   int persistent_grid;
   pplbm_batch_plan plan;
   cudaGraphExec_t graph[2];  // graph[p]: two steps starting from parity p
+  // pipelined plan: item tables (instance | pass bit, index within the instance) of
+  // M1 = collision of A + density of B, M2 = density of A + collision of B, the
+  // prologue PA = density of A and the epilogue EB = collision of B; pgraph[p] replays
+  // M1, M2, M1, M2 from parity p
+  int2* d_mix[4];
+  int nmix[4];
+  cudaGraphExec_t pgraph[2];
   int64_t steps;
   pplbm_status sticky;
   std::string msg;
@@ -180,6 +194,45 @@ pplbm_status build_tables(pplbm_batch* b, int tile_width) {
     return bfail(b, PPLBM_ERR_ARG, "batch too large");
   b->n1 = (int)o1.size();
   b->n2 = (int)o2.size();
+  // pipelined plan: two groups by node count (largest instance first to the lighter
+  // group), then the four item tables
+  std::vector<int> order(b->n);
+  for (int i = 0; i < b->n; ++i) order[i] = i;
+  auto nodes = [&](int i) { return (int64_t)b->lat[i].nx * b->lat[i].ny; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nodes(x) > nodes(y); });
+  std::vector<int> group(b->n, 0);
+  int64_t load[2] = {0, 0};
+  for (int i : order) {
+    const int g = load[1] < load[0] ? 1 : 0;
+    group[i] = g;
+    load[g] += nodes(i);
+  }
+  std::vector<int2> k1[2], k2[2];
+  for (int i = 0; i < b->n; ++i) {
+    const BatchInst& I = b->host_inst[i];
+    const int nb = (int)((nodes(i) + kThreads - 1) / kThreads);
+    const int tiles = I.tiles_x * ((b->lat[i].ny + I.th - 1) / I.th);
+    for (int j = 0; j < nb; ++j) k1[group[i]].push_back(make_int2(i, j));
+    for (int t = 0; t < tiles; ++t) k2[group[i]].push_back(make_int2(i | (int)0x80000000u, t));
+  }
+  // evenly interleaved: item i of x sits at (i + 1/2)/|x| of the table, likewise for y
+  auto interleave = [](const std::vector<int2>& x, const std::vector<int2>& y) {
+    std::vector<int2> m;
+    m.reserve(x.size() + y.size());
+    size_t i = 0, j = 0;
+    while (i < x.size() || j < y.size()) {
+      const bool take_x = j == y.size() || (i < x.size() && (2 * i + 1) * y.size() <= (2 * j + 1) * x.size());
+      m.push_back(take_x ? x[i++] : y[j++]);
+    }
+    return m;
+  };
+  const std::vector<int2> mix[4] = {interleave(k2[0], k1[1]), interleave(k1[0], k2[1]), k1[0], k2[1]};
+  for (int k = 0; k < 4; ++k) {
+    b->nmix[k] = (int)mix[k].size();
+    if (!mix[k].empty())
+      BTRY(b, cudaMemcpyAsync(b->d_mix[k], mix[k].data(), sizeof(int2) * mix[k].size(), cudaMemcpyHostToDevice,
+                              b->stream));
+  }
   // owner tables live in a device block sized at create for the worst case (tw = 4 or 256)
   BTRY(b, cudaMemcpyAsync(b->d_inst, b->host_inst.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice,
                           b->stream));
@@ -190,11 +243,37 @@ pplbm_status build_tables(pplbm_batch* b, int tile_width) {
 }
 
 void destroy_graphs(pplbm_batch* b) {
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < 2; ++p) {
     if (b->graph[p]) {
       cudaGraphExecDestroy(b->graph[p]);
       b->graph[p] = nullptr;
     }
+    if (b->pgraph[p]) {
+      cudaGraphExecDestroy(b->pgraph[p]);
+      b->pgraph[p] = nullptr;
+    }
+  }
+}
+
+// pipelined plan: M1 (collision of A and density of B, both at parity p) and M2
+// (density of A at 1 - p, collision of B at p) advance both groups by one step
+void launch_mixed_step(pplbm_batch* b, int p, cudaStream_t s) {
+  launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[0], b->nmix[0], p, p, s);
+  launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[1], b->nmix[1], 1 - p, p, s);
+}
+
+pplbm_status build_pipelined_graphs(pplbm_batch* b) {
+  for (int p = 0; p < 2; ++p) {
+    cudaGraph_t g;
+    BTRY(b, cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+    launch_mixed_step(b, p, b->capture_stream);
+    launch_mixed_step(b, 1 - p, b->capture_stream);
+    BTRY(b, cudaStreamEndCapture(b->capture_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&b->pgraph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, PPLBM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  return PPLBM_OK;
 }
 
 pplbm_status build_graphs(pplbm_batch* b) {
@@ -256,7 +335,8 @@ pplbm_status build_timed_graphs(pplbm_batch* b, int64_t count) {
 }
 
 pplbm_status apply_plan(pplbm_batch* b, int mode, int tile_width) {
-  if (mode != PPLBM_PLAN_LAUNCHES && mode != PPLBM_PLAN_GRAPH && mode != PPLBM_PLAN_PERSISTENT)
+  if (mode != PPLBM_PLAN_LAUNCHES && mode != PPLBM_PLAN_GRAPH && mode != PPLBM_PLAN_PERSISTENT &&
+      mode != PPLBM_PLAN_PIPELINED)
     return bfail(b, PPLBM_ERR_ARG, "unknown plan mode %d", mode);
   if (tile_width != 0 && (tile_width < 4 || tile_width > 256 || (tile_width & (tile_width - 1))))
     return bfail(b, PPLBM_ERR_ARG, "tile width must be 0 or a power of two in [4, 256]");
@@ -265,6 +345,8 @@ pplbm_status apply_plan(pplbm_batch* b, int mode, int tile_width) {
   destroy_timed_graphs(b);
   if (mode == PPLBM_PLAN_GRAPH)
     if (pplbm_status s = build_graphs(b)) return s;
+  if (mode == PPLBM_PLAN_PIPELINED)
+    if (pplbm_status s = build_pipelined_graphs(b)) return s;
   if (mode == PPLBM_PLAN_GRAPH && b->pass_timing)
     if (pplbm_status s = build_timed_graphs(b, (b->pass_capacity + 1) / 2)) return s;
   b->plan.mode = mode;
@@ -354,6 +436,20 @@ pplbm_status issue_steps(pplbm_batch* b, int64_t nsteps, cudaStream_t s) {
     BTRY(b, cudaGetLastError());
     return PPLBM_OK;
   }
+  if (b->plan.mode == PPLBM_PLAN_PIPELINED && nsteps > 0) {
+    // prologue, then M1 M2 per step with the last M2 left out, then the epilogue
+    const int p0 = b->parity;
+    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[2], b->nmix[2], p0, p0, s);
+    int64_t j = 0;
+    for (; j + 2 <= nsteps - 1; j += 2) BTRY(b, cudaGraphLaunch(b->pgraph[(p0 + j) & 1], s));
+    for (; j < nsteps - 1; ++j) launch_mixed_step(b, (int)((p0 + j) & 1), s);
+    const int pl = (int)((p0 + nsteps - 1) & 1);
+    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[0], b->nmix[0], pl, pl, s);
+    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[3], b->nmix[3], pl, pl, s);
+    BTRY(b, cudaGetLastError());
+    b->parity = (int)((p0 + nsteps) & 1);
+    return PPLBM_OK;
+  }
   if (b->plan.mode == PPLBM_PLAN_PERSISTENT && nsteps > 0) {
     if (pplbm_status st = launch_persistent(b, nsteps, s, kSpinLimit, -1)) return st;
     b->parity = (int)((b->parity + nsteps) & 1);
@@ -434,7 +530,9 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   const size_t ierr_bytes = ((sizeof(int) * n + 255) / 256) * 256;
   const size_t gpart_bytes = ((sizeof(double) * kGuardQ * max1 + 255) / 256) * 256;
   const size_t gout_bytes = ((sizeof(double) * kGuardQ * n + 255) / 256) * 256;
-  const size_t block = inst_bytes + o1_bytes + o2_bytes + 256 + 256 + 2 * ierr_bytes + gpart_bytes + gout_bytes;
+  const size_t mix_bytes = ((sizeof(int2) * (max1 + max2) + 255) / 256) * 256;  // each pipelined table
+  const size_t block =
+      inst_bytes + o1_bytes + o2_bytes + 256 + 256 + 2 * ierr_bytes + gpart_bytes + gout_bytes + 4 * mix_bytes;
   if (cudaMalloc(&b->dev_block, block) != cudaSuccess) {
     delete b;
     return PPLBM_ERR_CUDA;
@@ -449,6 +547,9 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   b->d_snap_valid = (int*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + ierr_bytes);
   b->d_gpart = (double*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes);
   b->d_gout = (double*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes);
+  for (int k = 0; k < 4; ++k)
+    b->d_mix[k] = (int2*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes + gout_bytes +
+                          k * mix_bytes);
   b->diverged.assign(n, 0);
   if (cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(b->dev_block);
@@ -617,8 +718,8 @@ pplbm_status pplbm_batch_set_f(pplbm_batch* b, int32_t i, const double* f) {
 
 pplbm_status pplbm_batch_set_plan(pplbm_batch* b, int32_t mode, int32_t tile_width) {
   if (!b) return PPLBM_ERR_ARG;
-  if (b->pass_timing && mode == PPLBM_PLAN_PERSISTENT)
-    return bfail(b, PPLBM_ERR_STATE, "per-pass timing is on: the persistent plan has one launch");
+  if (b->pass_timing && (mode == PPLBM_PLAN_PERSISTENT || mode == PPLBM_PLAN_PIPELINED))
+    return bfail(b, PPLBM_ERR_STATE, "per-pass timing is on: the persistent and pipelined plans mix the passes");
   BTRY(b, cudaStreamSynchronize(b->stream));
   return apply_plan(b, mode, tile_width);
 }
@@ -646,18 +747,18 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
   }
   const bool pass_timing = b->pass_timing;  // the trials time whole steps, each plan as it runs
   b->pass_timing = false;
-  const int modes[3] = {PPLBM_PLAN_LAUNCHES, PPLBM_PLAN_GRAPH, PPLBM_PLAN_PERSISTENT};
+  const int modes[4] = {PPLBM_PLAN_LAUNCHES, PPLBM_PLAN_GRAPH, PPLBM_PLAN_PERSISTENT, PPLBM_PLAN_PIPELINED};
   const int widths[2] = {0, 32};
   // three interleaved rounds over the six candidates; each keeps its best time, so a
   // transient (a clock change, another process) does not decide the plan
-  double per[3][2];
+  double per[4][2];
   for (auto& r : per) r[0] = r[1] = 1e300;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   pplbm_status st = PPLBM_OK;
   for (int round = 0; round < 3 && st == PPLBM_OK; ++round) {
-    for (int mi = 0; mi < 3 && st == PPLBM_OK; ++mi) {
+    for (int mi = 0; mi < 4 && st == PPLBM_OK; ++mi) {
       for (int wi = 0; wi < 2; ++wi) {
         if ((st = apply_plan(b, modes[mi], widths[wi])) != PPLBM_OK) break;
         if ((st = issue_steps(b, 2, b->stream)) != PPLBM_OK) break;  // warm-up
@@ -676,7 +777,7 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
   }
   double best = 1e300;
   int best_mode = PPLBM_PLAN_LAUNCHES, best_w = 0;
-  for (int mi = 0; mi < 3; ++mi)
+  for (int mi = 0; mi < 4; ++mi)
     for (int wi = 0; wi < 2; ++wi)
       if (per[mi][wi] < best) {
         best = per[mi][wi];
@@ -686,6 +787,7 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
   b->plan.ms_launches = std::min(per[0][0], per[0][1]);
   b->plan.ms_graph = std::min(per[1][0], per[1][1]);
   b->plan.ms_persistent = std::min(per[2][0], per[2][1]);
+  b->plan.ms_pipelined = std::min(per[3][0], per[3][1]);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // restore the state into buffer parity0
@@ -699,14 +801,16 @@ pplbm_status pplbm_batch_autotune(pplbm_batch* b, int32_t trial_steps, pplbm_bat
   }
   cudaStreamSynchronize(b->stream);
   cudaFree(backup);
-  b->pass_timing = pass_timing && best_mode != PPLBM_PLAN_PERSISTENT;
+  b->pass_timing = pass_timing && best_mode != PPLBM_PLAN_PERSISTENT && best_mode != PPLBM_PLAN_PIPELINED;
   if (st != PPLBM_OK) return st;
   if (pplbm_status s = poll(b)) return s;
   const double keep_l = b->plan.ms_launches, keep_g = b->plan.ms_graph, keep_p = b->plan.ms_persistent;
+  const double keep_q = b->plan.ms_pipelined;
   if (pplbm_status s = apply_plan(b, best_mode, best_w)) return s;
   b->plan.ms_launches = keep_l;
   b->plan.ms_graph = keep_g;
   b->plan.ms_persistent = keep_p;
+  b->plan.ms_pipelined = keep_q;
   b->plan.ms_chosen = best;
   if (chosen) *chosen = b->plan;
   return PPLBM_OK;
@@ -756,8 +860,9 @@ pplbm_status pplbm_batch_times(pplbm_batch* b, double* ms, int64_t* steps) {
 
 pplbm_status pplbm_batch_enable_pass_timing(pplbm_batch* b, int64_t capacity) {
   if (!b || capacity < 0) return PPLBM_ERR_ARG;
-  if (capacity > 0 && b->plan.mode == PPLBM_PLAN_PERSISTENT)
-    return bfail(b, PPLBM_ERR_STATE, "per-pass timing needs the launches or graph plan (the persistent plan has one launch)");
+  if (capacity > 0 && (b->plan.mode == PPLBM_PLAN_PERSISTENT || b->plan.mode == PPLBM_PLAN_PIPELINED))
+    return bfail(b, PPLBM_ERR_STATE,
+                 "per-pass timing needs the launches or graph plan (the persistent and pipelined plans mix the passes)");
   BTRY(b, cudaStreamSynchronize(b->stream));
   b->pass_timing = capacity > 0;
   b->pass_capacity = capacity;

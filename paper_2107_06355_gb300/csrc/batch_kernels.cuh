@@ -65,35 +65,53 @@ __device__ __forceinline__ void stage_args(const BatchInst* __restrict__ inst, i
   __syncthreads();
 }
 
+// density/psi pass over block `local` (256 nodes) of instance id
 template <int KIND>
-__device__ __forceinline__ void batch_rho_psi_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
-                                                   int w, int parity, StepArgs* sa) {
-  const int id = owner[w];
+__device__ __forceinline__ void batch_rho_psi_local(const BatchInst* __restrict__ inst, int id, int local,
+                                                    int parity, StepArgs* sa) {
   stage_args(inst, id, parity, sa);
-  const int64_t i = (int64_t)(w - inst[id].k1_start) * kThreads + threadIdx.x;
+  const int64_t i = (int64_t)local * kThreads + threadIdx.x;
   if (i < sa->n) rho_psi_node<KIND>(*sa, sa->f_in, i);
   __syncthreads();
 }
 
-template <int KIND, bool ST>
-__device__ __forceinline__ void batch_collide_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
-                                                   int w, int parity, double* sp, StepArgs* sa) {
+template <int KIND>
+__device__ __forceinline__ void batch_rho_psi_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
+                                                   int w, int parity, StepArgs* sa) {
   const int id = owner[w];
-  stage_args(inst, id, parity, sa);
-  const StepArgs& a = *sa;
+  batch_rho_psi_local<KIND>(inst, id, w - inst[id].k1_start, parity, sa);
+}
+
+// collision pass over tile t of instance id; org: two shared ints for the tile
+// origin, which one thread computes per item
+template <int KIND, bool ST>
+__device__ __forceinline__ void batch_collide_local(const BatchInst* __restrict__ inst, int id, int t, int parity,
+                                                    double* sp, StepArgs* sa, int* org) {
   const BatchInst& I = inst[id];
-  const int tw = I.tw, th = I.th, log2tw = I.log2tw, tiles_x = I.tiles_x;
-  const int t = w - I.k2_start;
-  const int tyi = t / tiles_x;
-  const int x0 = (t - tyi * tiles_x) * tw, y0 = tyi * th;
-  load_psi_tile(a, sp, x0, y0, tw, th, threadIdx.x, kThreads);
-  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int tyi = t / I.tiles_x;
+    org[0] = (t - tyi * I.tiles_x) * I.tw;
+    org[1] = tyi * I.th;
+  }
+  stage_args(inst, id, parity, sa);  // ends with a barrier: org is visible
+  const StepArgs& a = *sa;
+  const int tw = I.tw, th = I.th, log2tw = I.log2tw;
+  const int x0 = org[0], y0 = org[1];
   const int lx = threadIdx.x & (tw - 1), ly = threadIdx.x >> log2tw;
+  load_psi_tile(a, sp, x0, y0, tw, th, lx, ly, threadIdx.x, kThreads);
+  __syncthreads();
   const int x = x0 + lx, y = y0 + ly;
   if (x < a.nx && y < a.ny)
     collide_node<KIND, false, ST>(a, x, y, sp, (ly + 1) * (tw + 2) + lx + 1, tw + 2, nullptr, nullptr, nullptr,
                                   nullptr);
   __syncthreads();
+}
+
+template <int KIND, bool ST>
+__device__ __forceinline__ void batch_collide_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
+                                                   int w, int parity, double* sp, StepArgs* sa, int* org) {
+  const int id = owner[w];
+  batch_collide_local<KIND, ST>(inst, id, w - inst[id].k2_start, parity, sp, sa, org);
 }
 
 template <int KIND>
@@ -104,11 +122,37 @@ __global__ void __launch_bounds__(kThreads) k_batch_rho_psi(const BatchInst* ins
 
 // ST: some instance has the surface-tension source (kappa != 0); for the others
 // kappa_q = 0 makes the source exactly zero, so their results do not change
+// Unit relaxation times: 5 resident blocks per SM (at most 48 registers); the
+// integer-bound collision pass issues faster with the extra warps than it loses to
+// the 8-20 bytes of spilled registers. The other kinds keep 4 (they would spill more).
+constexpr int collide_min_blocks(int kind) { return kind == kUnitTau ? 5 : 4; }
+
 template <int KIND, bool ST>
-__global__ void __launch_bounds__(kThreads) k_batch_collide(const BatchInst* inst, const int* owner, int parity) {
+__global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
+    k_batch_collide(const BatchInst* inst, const int* owner, int parity) {
   __shared__ double sp[kMaxTileSmem];
   __shared__ StepArgs sa;
-  batch_collide_item<KIND, ST>(inst, owner, blockIdx.x, parity, sp, &sa);
+  __shared__ int org[2];
+  batch_collide_item<KIND, ST>(inst, owner, blockIdx.x, parity, sp, &sa, org);
+}
+
+// Work items of both passes in one launch (the pipelined plan): item.x is the
+// instance, with the top bit set for a collision tile; item.y the item's index within
+// its instance. Density items read buffer p1, collision items p2. Lattices of one
+// group run their density pass while those of the other run their collision pass, so
+// the FP64 pipe (the density pass's bound) and the integer pipe (the collision pass's)
+// work at the same time on every SM.
+template <int KIND, bool ST>
+__global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
+    k_batch_mixed(const BatchInst* inst, const int2* items, int p1, int p2) {
+  __shared__ double sp[kMaxTileSmem];
+  __shared__ StepArgs sa;
+  __shared__ int org[2];
+  const int2 it = items[blockIdx.x];
+  if (it.x >= 0)
+    batch_rho_psi_local<KIND>(inst, it.x, it.y, p1, &sa);
+  else
+    batch_collide_local<KIND, ST>(inst, it.x & 0x7FFFFFFF, it.y, p2, sp, &sa, org);
 }
 
 template <int KIND, bool ST>
@@ -118,13 +162,14 @@ __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* 
                                                                int absent_block) {
   __shared__ double sp[kMaxTileSmem];
   __shared__ StepArgs sa;
+  __shared__ int org[2];
   // barrier self-test only: one block leaves without arriving, so the others' waits run out
   if ((int)blockIdx.x == absent_block) return;
   for (long long s = 0; s < nsteps; ++s) {
     const int parity = (int)((parity0 + s) & 1);
     for (int w = blockIdx.x; w < n1; w += gridDim.x) batch_rho_psi_item<KIND>(inst, owner1, w, parity, &sa);
     if (!grid_barrier(bar, err, spin_limit)) return;
-    for (int w = blockIdx.x; w < n2; w += gridDim.x) batch_collide_item<KIND, ST>(inst, owner2, w, parity, sp, &sa);
+    for (int w = blockIdx.x; w < n2; w += gridDim.x) batch_collide_item<KIND, ST>(inst, owner2, w, parity, sp, &sa, org);
     if (!grid_barrier(bar, err, spin_limit)) return;
   }
 }
@@ -211,6 +256,24 @@ void launch_pair(int kind, bool st, const BatchInst* inst, const int* o1, int n1
     launch_pair_t<true>(kind, inst, o1, n1, o2, n2, parity, s);
   else
     launch_pair_t<false>(kind, inst, o1, n1, o2, n2, parity, s);
+}
+
+// one launch of the mixed kernel over n items
+void launch_mixed(int kind, bool st, const BatchInst* inst, const int2* items, int n, int p1, int p2, cudaStream_t s) {
+  if (n <= 0) return;
+#define PPLBM_KM(K)                                                                   \
+  do {                                                                                \
+    if (st)                                                                           \
+      k_batch_mixed<K, true><<<n, kThreads, 0, s>>>(inst, items, p1, p2);             \
+    else                                                                              \
+      k_batch_mixed<K, false><<<n, kThreads, 0, s>>>(inst, items, p1, p2);            \
+  } while (0)
+  switch (kind) {
+    case kUnitTau: PPLBM_KM(kUnitTau); break;
+    case kShearTau: PPLBM_KM(kShearTau); break;
+    default: PPLBM_KM(kFullMrt); break;
+  }
+#undef PPLBM_KM
 }
 
 // the collision pass alone, over every instance

@@ -30,6 +30,7 @@
 
 #include "../../include/pplbm.h"
 #include "eos_dev.cuh"
+#include "fixsum.cuh"
 #include "fp64.cuh"
 #include "internal.h"
 
@@ -108,6 +109,90 @@ __global__ void k_fd_walls(const EosConst e, double* rho, double* ux, double* uy
   uy[at(t2)] = 0.0;
 }
 
+// Stencil differences as exact integer combinations in one fixed-point frame per
+// field (fixsum.cuh), each rounded once: integer-pipe work in place of chains of
+// software IEEE additions and FP64 fused multiply-adds.
+using fx::u64;
+
+// psi's raw differences at a point from the 13 values of its 5 x 5 cross and
+// diagonals: central first differences Pd, second differences Pxx, Pyy, the mixed
+// one q = Dxy / 4, the Laplacian Lc = Pxx + Pyy and the differences DL of the
+// 5-point Laplacians at +-1 (their coefficients sum to 14 at most: headroom 5 + sign).
+// A non-finite value makes them all NaN.
+struct PsiDiffs {
+  double Pd0, Pd1, Pxx, Pyy, q, Lc, DL0, DL1;
+};
+
+__device__ __forceinline__ PsiDiffs psi_diffs(double c, double e, double w, double n, double s, double ne, double nw,
+                                              double sw, double se, double ee, double ww, double nn, double ss) {
+  const double v[13] = {c, e, w, n, s, ne, nw, sw, se, ee, ww, nn, ss};
+  u64 b[13];
+  unsigned mx = 0;
+#pragma unroll
+  for (int k = 0; k < 13; ++k) {
+    b[k] = fx::bits_of(v[k]);
+    mx = max(mx, fx::mag_hi(b[k]));
+  }
+  const int eg = (int)(mx >> 20) + 6;
+  u64 t[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) t[k] = (u64)fx::sterm(b[k], eg);
+  const u64 tC = t[0], tE = t[1], tW = t[2], tN = t[3], tS = t[4], tNE = t[5], tNW = t[6], tSW = t[7], tSE = t[8];
+  const u64 pd0 = tE - tW, pd1 = tN - tS;
+  const u64 pxx = tE + tW - 2 * tC, pyy = tN + tS - 2 * tC;
+  const u64 dxy = (tNE - tSE) - (tNW - tSW);
+  const u64 dl0 = (t[9] - t[10]) + (tNE + tSE) - (tNW + tSW) - 4 * pd0;  // L5(1, 0) - L5(-1, 0)
+  const u64 dl1 = (t[11] - t[12]) + (tNE + tNW) - (tSE + tSW) - 4 * pd1;  // L5(0, 1) - L5(0, -1)
+  const bool bad = mx >= 0x7FF00000u;
+  auto out = [&](u64 x, int shift) {
+    return fx::double_of(bad ? 0x7FF8000000000000ull : fx::round_frame_s((fx::i64)x, eg + shift));
+  };
+  PsiDiffs r;
+  r.Pd0 = out(pd0, 0);
+  r.Pd1 = out(pd1, 0);
+  r.Pxx = out(pxx, 0);
+  r.Pyy = out(pyy, 0);
+  r.q = out(dxy, -2);
+  r.Lc = out(pxx + pyy, 0);
+  r.DL0 = out(dl0, 0);
+  r.DL1 = out(dl1, 0);
+  return r;
+}
+
+// a velocity component's raw differences from its 3 x 3 neighbourhood: the one-sided
+// first differences along x and y (forward in the predictor, backward in the
+// corrector) and the central Dxx, Dyy, Dxy (coefficients sum to 4: headroom 3 + sign)
+struct VelDiffs {
+  double D0, D1, xx, yy, xy;
+};
+
+template <bool PRED>
+__device__ __forceinline__ VelDiffs vel_diffs(double c, double e, double w, double n, double s, double ne, double nw,
+                                              double sw, double se) {
+  const double v[9] = {c, e, w, n, s, ne, nw, sw, se};
+  u64 b[9];
+  unsigned mx = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    b[k] = fx::bits_of(v[k]);
+    mx = max(mx, fx::mag_hi(b[k]));
+  }
+  const int eg = (int)(mx >> 20) + 4;
+  u64 t[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t[k] = (u64)fx::sterm(b[k], eg);
+  const u64 tC = t[0], tE = t[1], tW = t[2], tN = t[3], tS = t[4];
+  const bool bad = mx >= 0x7FF00000u;
+  auto out = [&](u64 x) { return fx::double_of(bad ? 0x7FF8000000000000ull : fx::round_frame_s((fx::i64)x, eg)); };
+  VelDiffs r;
+  r.D0 = out(PRED ? tE - tC : tC - tW);
+  r.D1 = out(PRED ? tN - tC : tC - tS);
+  r.xx = out(tE + tW - 2 * tC);
+  r.yy = out(tN + tS - 2 * tC);
+  r.xy = out((t[5] - t[8]) - (t[6] - t[7]));
+  return r;
+}
+
 // PRED: predictor (forward differences) or corrector (backward); VV: tau_nu(rho)
 // viscosities, a compile-time choice so the constant-viscosity kernel carries none
 // of their arithmetic
@@ -134,41 +219,36 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
     ry[k] = (int64_t)(a.walls ? y + k : wrap(y + k - 2, ny)) * nx;  // walls: padded rows, no wrap
   }
   auto at = [&](const double* f, int dx, int dy) { return f[ry[dy + 2] + cx[dx + 2]]; };
-  // one-sided first difference along x (axis 0) or y (axis 1): forward in the
-  // predictor, backward in the corrector; true derivative = h D
-  // The stencil sums and differences run on the integer pipe (add_int / sub_int,
-  // bitwise the FP64 add), about as many as balance it against the FP64 pipe, which
-  // keeps the products, the fused multiply-adds and the final combinations.
+  // one-sided first difference along x (axis 0) or y (axis 1) of rho and p: forward in
+  // the predictor, backward in the corrector; true derivative = h D (integer pipe,
+  // add_int: bitwise the FP64 add)
   auto D1 = [&](const double* f, int axis) {
     const double c = at(f, 0, 0);
     if (PRED) return axis == 0 ? sub_int(at(f, 1, 0), c) : sub_int(at(f, 0, 1), c);
     return axis == 0 ? sub_int(c, at(f, -1, 0)) : sub_int(c, at(f, 0, -1));
   };
-  // central second differences: d_xx = h^2 Dxx, d_xy = (h^2/4) Dxy
-  auto Dxx = [&](const double* f) { return fma(-2.0, at(f, 0, 0), add_int(at(f, 1, 0), at(f, -1, 0))); };
-  auto Dyy = [&](const double* f) { return fma(-2.0, at(f, 0, 0), add_int(at(f, 0, 1), at(f, 0, -1))); };
-  auto Dxy = [&](const double* f) {
-    return sub_int(sub_int(at(f, 1, 1), at(f, 1, -1)), sub_int(at(f, -1, 1), at(f, -1, -1)));
+  auto vel = [&](const double* f) {
+    return vel_diffs<PRED>(at(f, 0, 0), at(f, 1, 0), at(f, -1, 0), at(f, 0, 1), at(f, 0, -1), at(f, 1, 1),
+                           at(f, -1, 1), at(f, -1, -1), at(f, 1, -1));
   };
   const double rho = at(a.rho, 0, 0), ux = at(a.ux, 0, 0), uy = at(a.uy, 0, 0);
+  // velocity differences: Du_ab = d_a u_b (one-sided), second differences central
+  // (d_xx = h^2 Dxx, d_xy = (h^2/4) Dxy)
+  const VelDiffs vx = vel(a.ux), vy = vel(a.uy);
+  const double Du00 = vx.D0, Du01 = vy.D0, Du10 = vx.D1, Du11 = vy.D1;
   // mass: d_t rho = -(rho div u + u . grad rho)
   const double Dr0 = D1(a.rho, 0), Dr1 = D1(a.rho, 1);
-  const double Du00 = D1(a.ux, 0), Du01 = D1(a.uy, 0);  // Du_ab: d_a u_b
-  const double Du10 = D1(a.ux, 1), Du11 = D1(a.uy, 1);
   const double Dv = add_int(Du00, Du11), Sh = add_int(Du01, Du10);
   const double drho = -a.cA * fma(rho, Dv, fma(ux, Dr0, uy * Dr1));
-  // psi: dpsi = (h/2) Pd, d_ab psi from Dxx, Dyy, Dxy, lap = h^2 Lc, and the
+  // psi: dpsi = (h/2) Pd, d_ab psi from Pxx, Pyy, q = Dxy/4, lap = h^2 Lc, and the
   // derivative of lap psi = (h^3/2) DL from the 5-point sums at +-1
   const double* ps = a.psi;
   const double psi = at(ps, 0, 0);
-  const double Pd0 = sub_int(at(ps, 1, 0), at(ps, -1, 0)), Pd1 = sub_int(at(ps, 0, 1), at(ps, 0, -1));
-  const double Pxx = Dxx(ps), Pyy = Dyy(ps), q = 0.25 * Dxy(ps);
-  const double Lc = add_int(Pxx, Pyy);
-  auto L5 = [&](int ox, int oy) {
-    return fma(-4.0, at(ps, ox, oy),
-               add_int(add_int(at(ps, ox + 1, oy), at(ps, ox - 1, oy)), add_int(at(ps, ox, oy + 1), at(ps, ox, oy - 1))));
-  };
-  const double DL0 = sub_int(L5(1, 0), L5(-1, 0)), DL1 = sub_int(L5(0, 1), L5(0, -1));
+  const PsiDiffs pd = psi_diffs(psi, at(ps, 1, 0), at(ps, -1, 0), at(ps, 0, 1), at(ps, 0, -1), at(ps, 1, 1),
+                                at(ps, -1, 1), at(ps, -1, -1), at(ps, 1, -1), at(ps, 2, 0), at(ps, -2, 0),
+                                at(ps, 0, 2), at(ps, 0, -2));
+  const double Pd0 = pd.Pd0, Pd1 = pd.Pd1, Pxx = pd.Pxx, Pyy = pd.Pyy, q = pd.q, Lc = pd.Lc;
+  const double DL0 = pd.DL0, DL1 = pd.DL1;
   // d_b p'_ab (Eq. FDforce) = (h^3/2) [(G/6 - eps G/4) S_a + (G/12) Pd_a Lc + (G/4) psi DL_a],
   // S_a = sum_g Pd_g (d_a d_g psi in the same units)
   const double S0 = fma(Pd0, Pxx, q * Pd1), S1 = fma(Pd1, Pyy, q * Pd0);
@@ -177,8 +257,8 @@ __global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
   const double F1 = fma(a.kS, S1, fma(a.kL * Pd1, Lc, kDpsi * DL1));
   // d_b sigma'_ab (Eqs. FDstressTensor, FDviscosityDerivative) with one-sided grad rho, grad u
   // and central second derivatives of u
-  const double U0xx = Dxx(a.ux), U0yy = Dyy(a.ux), U1xx = Dxx(a.uy), U1yy = Dyy(a.uy);
-  const double U0xy = Dxy(a.ux), U1xy = Dxy(a.uy);
+  const double U0xx = vx.xx, U0yy = vx.yy, U1xx = vy.xx, U1yy = vy.yy;
+  const double U0xy = vx.xy, U1xy = vy.xy;
   double V0, V1;
   if (!VV) {
     V0 = fma(a.v1, fma(2.0 * Dr0, Du00, Dr1 * Sh),

@@ -87,25 +87,48 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// v mod n for v in [-n, 2n) by one conditional add or subtract (no division); other
+// values (a lattice narrower than a tile) through the remainder
+__device__ __forceinline__ int wrap_near(int v, int n) {
+  v += v < 0 ? n : 0;
+  v -= v >= n ? n : 0;
+  return (v >= 0 && v < n) ? v : wrap_index(v, n);
+}
+
+// psi at lattice column gx (any integer: periodic wrap) and row gy in [-1, ny]
+// (periodic, or the wall ghost values beyond the walls)
+__device__ __forceinline__ double psi_wrapped(const StepArgs& a, int gx, int gy) {
+  gx = wrap_near(gx, a.nx);
+  if (a.walls) {
+    if (gy < 0) return a.psi_ghost_bottom;
+    if (gy >= a.ny) return a.psi_ghost_top;
+  } else {
+    gy = wrap_near(gy, a.ny);
+  }
+  return a.psi[(int64_t)gy * a.nx + gx];
+}
+
 // psi of the tile [x0 - 1, x0 + tw] x [y0 - 1, y0 + th] into sp (row stride tw + 2):
-// periodic wrap in x; periodic in y, or the wall ghost values beyond the walls.
-__device__ __forceinline__ void load_psi_tile(const StepArgs& a, double* sp, int x0, int y0, int tw, int th,
-                                              int tid, int nthreads) {
+// periodic wrap in x; periodic in y, or the wall ghost values beyond the walls. The
+// block has tw * th threads: thread (lx, ly) loads its own node, then the 2 (tw + 2)
+// + 2 th halo values are shared out, rows first (no division by the tile width).
+__device__ __forceinline__ void load_psi_tile(const StepArgs& a, double* sp, int x0, int y0, int tw, int th, int lx,
+                                              int ly, int tid, int nthreads) {
   const int sw = tw + 2;
-  for (int k = tid; k < (th + 2) * sw; k += nthreads) {
-    const int ty = k / sw, tx = k - ty * sw;
-    const int gx = wrap_index(x0 + tx - 1, a.nx);
-    int gy = y0 + ty - 1;
-    double v;
-    if (a.walls) {
-      if (gy < 0) v = a.psi_ghost_bottom;
-      else if (gy >= a.ny) v = a.psi_ghost_top;
-      else v = a.psi[(int64_t)gy * a.nx + gx];
+  sp[(ly + 1) * sw + lx + 1] = psi_wrapped(a, x0 + lx, y0 + ly);
+  const int nh = 2 * sw + 2 * th;
+  for (int k = tid; k < nh; k += nthreads) {
+    int tx, ty;
+    if (k < 2 * sw) {
+      const bool top = k >= sw;
+      ty = top ? th + 1 : 0;
+      tx = top ? k - sw : k;
     } else {
-      gy = wrap_index(gy, a.ny);
-      v = a.psi[(int64_t)gy * a.nx + gx];
+      const int j = k - 2 * sw;
+      ty = 1 + (j >> 1);
+      tx = (j & 1) ? tw + 1 : 0;
     }
-    sp[k] = v;
+    sp[ty * sw + tx] = psi_wrapped(a, x0 + tx - 1, y0 + ty - 1);
   }
 }
 

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_collide(const StepArgs a, double* 
                                                       double* psi_o) {
   __shared__ double sp[(kTY + 2) * (kTX + 2)];
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  load_psi_tile(a, sp, x0, y0, kTX, kTY, threadIdx.y * kTX + threadIdx.x, kTX * kTY);
+  load_psi_tile(a, sp, x0, y0, kTX, kTY, threadIdx.x, threadIdx.y, threadIdx.y * kTX + threadIdx.x, kTX * kTY);
   __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;

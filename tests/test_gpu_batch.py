@@ -55,7 +55,7 @@ def _build(relax_kw):
 @pytest.mark.parametrize("relax_kw", [{}, {"kind": 1, "tau_l": 0.6, "visc_ratio": 2.0},
                                       {"tau_e": 0.8, "tau_zeta": 1.1, "tau_q": 1.2, "tau_nu": 0.9}],
                          ids=["unit", "two_phase", "full_mrt"])
-@pytest.mark.parametrize("mode,width", [(0, 0), (0, 4), (0, 32), (0, 256), (1, 0), (2, 0), (2, 8)])
+@pytest.mark.parametrize("mode,width", [(0, 0), (0, 4), (0, 32), (0, 256), (1, 0), (2, 0), (2, 8), (3, 0), (3, 32)])
 def test_batch_bitwise_equals_single_lattice(relax_kw, mode, width):
     b, sims = _build(relax_kw)
     b.set_plan(mode, width)
@@ -98,8 +98,9 @@ def test_autotune_keeps_state_and_reports_plan():
     b.step(3)
     before = [b.get_f(k).clone() for k in range(len(sims))]
     plan = b.autotune(trial_steps=6)
-    assert plan["mode"] in (0, 1, 2)
+    assert plan["mode"] in (0, 1, 2, 3)
     assert plan["ms_launches"] > 0 and plan["ms_graph"] > 0 and plan["ms_persistent"] > 0
+    assert plan["ms_pipelined"] > 0
     for k in range(len(sims)):
         assert torch.equal(b.get_f(k), before[k])
     # stepping after tuning still matches the single-lattice path
@@ -216,7 +217,7 @@ def test_batch_guard_matches_host_reduction():
     b.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_run_host_equals_init_step_fields(mode):
     """pplbm_batch_run_host (host in, nsteps, host out) gives the densities of
     init_equilibrium + step + get_fields, bit for bit, in every plan."""
@@ -294,6 +295,8 @@ def test_pass_timing_counts_launches_and_keeps_results(mode):
     assert b.pass_times()[1] == (2, 2)
     with pytest.raises(P.PPLBMError):
         b.set_plan(2, 0)   # the persistent plan has a single launch
+    with pytest.raises(P.PPLBMError):
+        b.set_plan(3, 0)   # the pipelined plan's launches mix the passes
     b.enable_pass_timing(0)
     ref.step(9)
     for k in range(b.n):

@@ -142,7 +142,7 @@ def _batch_case():
     return b, olats, inits
 
 
-@pytest.mark.parametrize("plan", [0, 1, 2], ids=["launches", "graph", "persistent"])
+@pytest.mark.parametrize("plan", [0, 1, 2, 3], ids=["launches", "graph", "persistent", "pipelined"])
 def test_batch_guard_matches_oracle(plan):
     b, olats, inits = _batch_case()
     b.set_plan(plan, 0)

@@ -84,7 +84,7 @@ def test_step_parity_with_kappa_and_guo_forcing(relax):
     sim.close()
 
 
-@pytest.mark.parametrize("mode,width", [(0, 0), (0, 8), (1, 0), (2, 0)])
+@pytest.mark.parametrize("mode,width", [(0, 0), (0, 8), (1, 0), (2, 0), (3, 0)])
 def test_batch_with_mixed_kappa_bitwise_equals_single_lattices(mode, width):
     inst = [(4, 90, BC_PER, 0.8, 0.0), (70, 45, BC_PER, 0.6, 0.5), (33, 33, BC_PER, 0.5, -0.4),
             (48, 40, BC_WALLS, 0.6, 0.3), (3, 5, BC_PER, 0.6, 0.0), (130, 9, BC_WALLS, 0.5, 0.0)]
