@@ -91,9 +91,9 @@ FD_ALU_PER_POINT = 1948 + 1960 + 2 * 11
 # node. They hold for the device code whose digest is recorded with them; once it
 # changes, traffic is null and the source counts above are used until the capture is
 # repeated.
-COUNTS = {"sources": "643302f55229de1a",
-          "rho_psi": {"dram_bytes": 1317146368, "fp64_per_node": 14.542, "alu_per_node": 222.7},
-          "collide": {"dram_bytes": 1289946368, "fp64_per_node": 19.000, "alu_per_node": 1052.6}}
+COUNTS = {"sources": "2cb174fe8ee956f9",
+          "rho_psi": {"dram_bytes": 1316795648, "fp64_per_node": 14.542, "alu_per_node": 222.7},
+          "collide": {"dram_bytes": 1298580992, "fp64_per_node": 19.000, "alu_per_node": 1018.1}}
 KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "fixsum.cuh",
                   "internal.h")
 
@@ -1045,9 +1045,12 @@ def main():
         "config": {"workload": WORKLOAD, "lattices": len(specs), "nodes_per_step": nodes,
                    "engine": f"batched ({mode}, tiles {plan['tile_width'] or 'per-instance'})",
                    "parallelism": f"replicas{ws}",
-                   "timing": f"{len(blocks)} blocks of {args.steps} steps ({sum(blocks) / 1e3:.2f} s), alternating plain "
-                             f"blocks (value: median of {len(plain)}) and blocks with per-pass CUDA events (kernel "
-                             f"durations: {len(instrumented)})",
+                   "timing": (f"{len(blocks)} blocks of {args.steps} steps ({sum(blocks) / 1e3:.2f} s), alternating "
+                              f"plain blocks (value: median of {len(plain)}) and blocks with per-pass CUDA events "
+                              f"(kernel durations: {len(instrumented)})") if per_pass else
+                             (f"{len(blocks)} blocks of {args.steps} steps ({sum(blocks) / 1e3:.2f} s), value: median "
+                              f"of the {len(plain)} blocks; the {mode} plan's launches run both passes, so the kernel "
+                              "duration is the call's CUDA-event time per step"),
                    "l2": "state about 2.4 GB >> 126 MB L2, no flush"},
         "blocks_ms": plain,
         "blocks_ms_instrumented": instrumented,
