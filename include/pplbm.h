@@ -550,6 +550,22 @@ pplbm_status pplbm_fixsum_eval(long long n, const double* f, const double* p, do
 pplbm_status pplbm_fixsum_collision_eval(long long n, int32_t shear, const double* q, const double* jh, double* out,
                                          void* stream);
 
+/* The reverse-mode counterparts of pplbm_fixsum_collision_eval's stages, and the
+ * fixed-point sums of the adjoint's density pass, on caller data: per row, from mu
+ * (n x 9, the adjoints of the nine post-collision populations) the adjoints of the
+ * populations' nine inputs (rho/36, Pi_xx/36, Pi_yy/36, Pi_xy/36, P_x/36, P_y/36, zz
+ * and, when shear != 0, the rows 7, 8 corrections; 0.0 otherwise); from a (n x 6: the
+ * adjoints of j + h, j + 2h, j + 3h, j - h, and partial adjoints of j and h) the
+ * adjoints of j and h; from gth (n x 13: a node's own psi adjoint, then gx_bar, gy_bar
+ * at its W, E / S, N / SW, NE, NW, SE neighbours as x, y pairs) the gathered psi
+ * adjoint (the transpose of the Shan-Chen stencil, Eq. ShanChenForce); from lam (n x
+ * 5: rho_bar, jx_bar, jy_bar, m7_bar, m8_bar) the nine lambda_i = rho_bar + c_i . j_bar
+ * (+ with shear the rows 7, 8 terms). Device arrays; out (n x 21): the nine, the two,
+ * the gathered adjoint, the nine lambdas. PPLBM_ERR_ARG for n < 0, n > 2^31 * 255, or
+ * NULL pointers with n > 0. Asynchronous on `stream`. */
+pplbm_status pplbm_fixsum_adjoint_eval(long long n, int32_t shear, const double* mu, const double* a,
+                                       const double* gth, const double* lam, double* out, void* stream);
+
 /* FP64 issue-rate probe, the denominator of the step's arithmetic roofline (the
  * step's per-node arithmetic is double precision throughout, Sec. II; on this GPU
  * the FP64 pipe, not memory, bounds it). Launches blocks_per_sm x (SM count)

@@ -117,6 +117,7 @@ _SIGS = {
     "pplbm_int_add_selftest": (C.c_int, [C.c_longlong, C.c_ulonglong, _P, _P]),
     "pplbm_fixsum_eval": (C.c_int, [C.c_longlong, _P, _P, _P, _P]),
     "pplbm_fixsum_collision_eval": (C.c_int, [C.c_longlong, C.c_int32, _P, _P, _P, _P]),
+    "pplbm_fixsum_adjoint_eval": (C.c_int, [C.c_longlong, C.c_int32, _P, _P, _P, _P, _P, _P]),
     "pplbm_batch_workspace_bytes": (C.c_size_t, [C.c_int32, C.POINTER(pplbm_lattice), C.POINTER(pplbm_relax)]),
     "pplbm_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(pplbm_lattice), C.POINTER(pplbm_eos_params),
                                      C.POINTER(pplbm_relax), C.c_double, _P, C.c_size_t, _P]),

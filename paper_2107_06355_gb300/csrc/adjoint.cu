@@ -259,6 +259,100 @@ __device__ __forceinline__ void collide_shear_reverse(const StepArgs& a, double 
   *gy_b = gy_bb;
 }
 
+// Reverse mode of collide_reduced_fx (step_device.cuh), the collision the forward pass
+// runs without the surface-tension source: unit relaxation times, or with SHEAR the
+// rows 7, 8 relaxing at omega = 1/tau(rho). Forward, with s = 1/36:
+//   h = cH g (cH = hf psi0); J, P, P + h (and K = j - h) from j_h_combos;
+//   u' = J / (36 rho); xx = u'_x (P_x + h_x), yy likewise, xy = u'_x P_y + u'_y h_x;
+//   zz = zs |g|^2; SHEAR: p7 = (1 - omega) A7, A7 = s m7 - u'_x K_x + u'_y K_y,
+//   p8 = (1 - omega) A8, A8 = s m8 - u'_x j_y + u'_y h_x;
+//   f* = reduced_populations(s rho, xx, yy, xy, s P_x, s P_y, zz, p7, p8).
+// The adjoints of the populations' inputs come from the transposed integer stage
+// (fx::reduced_populations_transpose), those of j and h from the transposed sums
+// (fx::j_h_combos_transpose); the products between them are FP64.
+// With SRC (a kernel built with the surface-tension source, run at kappa = 0, when the
+// kappa gradient is asked for) it also returns src = {zz adjoint, row-7 adjoint, mixed
+// moment adjoint, omega}: the source adds nothing at kappa = 0, and these give its
+// adjoints.
+template <bool SHEAR, bool SRC = false>
+__device__ __forceinline__ void collide_reduced_reverse(const StepArgs& a, double rho, double jx, double jy,
+                                                        double m7, double m8, double psi0, double gx, double gy,
+                                                        const double* mu, double* rho_b, double* jx_b, double* jy_b,
+                                                        double* m7_b, double* m8_b, double* psi_b, double* gx_b,
+                                                        double* gy_b, double* zs_b, double* src = nullptr) {
+  constexpr double s36 = 1.0 / 36.0;
+  // forward recompute
+  const double cH = a.half_force * psi0;
+  const double hx = cH * gx, hy = cH * gy;
+  double Jx, Px, Qx, Kx = 0.0, Jy, Py, Qy, Ky = 0.0;
+  fx::j_h_combos<SHEAR>(jx, hx, &Jx, &Px, &Qx, &Kx);
+  fx::j_h_combos<SHEAR>(jy, hy, &Jy, &Py, &Qy, &Ky);
+  const double inv36 = fast_rcp(36.0 * rho);
+  const double ux = Jx * inv36, uy = Jy * inv36;
+  const double g2 = fma(gx, gx, gy * gy);
+  // reverse: the populations' inputs
+  const double m[9] = {mu[0], mu[1], mu[2], mu[3], mu[4], mu[5], mu[6], mu[7], mu[8]};
+  double U[9];
+  fx::reduced_populations_transpose<SHEAR, SHEAR || SRC>(m, U);
+  if (SRC) {
+    // the adjoints of zz, of the row-7 moment m7* (the axis populations carry +-m7*/4:
+    // (mu1 + mu3 - mu2 - mu4)/4 = U7/36) and of the mixed moment Pi_xy*
+    // ((mu5 + mu7 - mu6 - mu8)/4 = U8/36)
+    src[0] = U[6];
+    src[1] = U[7] * s36;
+    src[2] = U[8] * s36;
+    src[3] = 0.0;
+  }
+  double r_b = U[0] * s36;
+  double Px_b = U[4] * s36, Py_b = U[5] * s36;
+  // xx = ux Qx, yy = uy Qy, xy = ux Py + uy hx
+  double ux_b = fma(U[3], Py, U[1] * Qx);
+  double uy_b = fma(U[3], hx, U[2] * Qy);
+  const double Qx_b = U[1] * ux, Qy_b = U[2] * uy;
+  Py_b = fma(U[3], ux, Py_b);
+  double hx_b = U[3] * uy, hy_b = 0.0;
+  double Kx_b = 0.0, Ky_b = 0.0, jy_0 = 0.0;
+  if (SHEAR) {
+    const double om = fast_rcp(fma(a.tau_b, rho, a.tau_a));
+    if (SRC) src[3] = om;
+    const double omc = 1.0 - om;
+    const double A7 = fma(-ux, Kx, fma(uy, Ky, m7 * s36));
+    const double A8 = fma(-ux, jy, fma(uy, hx, m8 * s36));
+    const double A7_b = U[7] * omc, A8_b = U[8] * omc;
+    const double om_b = -fma(U[7], A7, U[8] * A8);  // through omc = 1 - omega
+    r_b = fma(-om_b * om, om * a.tau_b, r_b);       // d omega / d rho = -tau_b omega^2
+    *m7_b = A7_b * s36;
+    *m8_b = A8_b * s36;
+    // A7 = s m7 - ux Kx + uy Ky, A8 = s m8 - ux jy + uy hx
+    ux_b = fma(-A7_b, Kx, fma(-A8_b, jy, ux_b));
+    uy_b = fma(A7_b, Ky, fma(A8_b, hx, uy_b));
+    Kx_b = -A7_b * ux;
+    Ky_b = A7_b * uy;
+    jy_0 = -A8_b * ux;
+    hx_b = fma(A8_b, uy, hx_b);
+  }
+  // u' = J inv36, inv36 = 1/(36 rho): d inv36 / d rho = -36 inv36^2
+  const double Jx_b = ux_b * inv36, Jy_b = uy_b * inv36;
+  const double inv_b = fma(ux_b, Jx, uy_b * Jy);
+  r_b = fma(-36.0 * inv_b * inv36, inv36, r_b);
+  // J = j + h, P = j + 2h, P + h = j + 3h, K = j - h
+  double jxb, hxb, jyb, hyb;
+  fx::j_h_combos_transpose<SHEAR>(Jx_b, Px_b, Qx_b, Kx_b, 0.0, hx_b, &jxb, &hxb);
+  fx::j_h_combos_transpose<SHEAR>(Jy_b, Py_b, Qy_b, Ky_b, jy_0, hy_b, &jyb, &hyb);
+  // zz = zs g2
+  const double zs = a.zz_scale;
+  const double zg = 2.0 * zs * U[6];
+  *zs_b = U[6] * g2;
+  // h = cH g, cH = hf psi0
+  const double cH_b = fma(hxb, gx, hyb * gy);
+  *gx_b = fma(hxb, cH, zg * gx);
+  *gy_b = fma(hyb, cH, zg * gy);
+  *psi_b = cH_b * a.half_force;
+  *rho_b = r_b;
+  *jx_b = jxb;
+  *jy_b = jyb;
+}
+
 // psi^2(rho) and its derivatives w.r.t. rho and the alpha-dependent constants (eos_dev.cuh);
 // the C-S branch constants' derivatives only when bulk_slots (a uniform flag)
 __device__ __forceinline__ double psi2_grad(const EosConst& e, double rho, bool bulk_slots, double* dc) {
@@ -379,7 +473,28 @@ __global__ void __launch_bounds__(kNT) k_adj_collide(const AdjArgs g) {
       sq = surface_q(a, p0, sp[c + 1], sp[c - 1], sp[c + sw], sp[c - sw], sp[c + sw + 1], sp[c + sw - 1],
                      sp[c - sw - 1], sp[c - sw + 1]);
     double* B = g.bar;
-    if (KIND == kShearTau) {
+    if (!ST || a.kappa_q == 0.0) {
+      // the forward ran collide_reduced_fx (no source, or kappa = 0 in a kernel with it)
+      double m7b = 0.0, m8b = 0.0, src[4] = {0.0, 0.0, 0.0, 0.0};
+      const bool shear = KIND == kShearTau;
+      collide_reduced_reverse<KIND == kShearTau, ST>(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node],
+                                                     shear ? a.mom[3 * N + node] : 0.0,
+                                                     shear ? a.mom[4 * N + node] : 0.0, p0, gx, gy, mu, &rb, &jxb,
+                                                     &jyb, &m7b, &m8b, &pb, &gxb, &gyb, &zs_b, src);
+      if (shear) {
+        B[9 * N + node] = m7b;
+        B[10 * N + node] = m8b;
+      }
+      if (ST) {
+        // the source's adjoints at k = kappa_q psi = 0 (forward: zz += k t; unit: the
+        // axis populations' m7*/4 parts -= +-k sd, Pxy -= k xd; two-phase: m7* -= 4 omega
+        // k sd, m8* -= omega k xd): only the k adjoint is non-zero
+        if (shear)
+          st_b[0] = fma(src[0], sq.t, -src[3] * fma(4.0 * sq.sd, src[1], sq.xd * src[2]));
+        else
+          st_b[0] = fma(src[0], sq.t, -fma(4.0 * src[1], sq.sd, src[2] * sq.xd));
+      }
+    } else if (KIND == kShearTau) {
       double m7b, m8b;
       collide_shear_reverse(a, a.mom[node], a.mom[N + node], a.mom[2 * N + node], a.mom[3 * N + node],
                             a.mom[4 * N + node], p0, gx, gy, mu, ST ? &sq : nullptr, &rb, &jxb, &jyb, &m7b, &m8b, &pb,
@@ -460,13 +575,13 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
   bool shaped = false, vap_side = false, liq_side = false;
   if (x < a.nx && y < a.ny) {
     const int c = (threadIdx.y + 1) * (kTX + 2) + threadIdx.x + 1, sw = kTX + 2;
-    // transpose of g = 12 sum_c w_c psi(x + c) c, gathered at this node y
-    const double q1 = add_int(sx[c - sw - 1], sy[c - sw - 1]), q2 = add_int(sx[c + sw + 1], sy[c + sw + 1]);
-    const double q3 = sub_int(sx[c + sw - 1], sy[c + sw - 1]), q4 = sub_int(sx[c - sw + 1], sy[c - sw + 1]);
-    const double pg = fma(4.0, sub_int(sx[c - 1], sx[c + 1]),
-                          fma(4.0, sub_int(sy[c - sw], sy[c + sw]), add_int(sub_int(q1, q2), sub_int(q3, q4))));
+    // transpose of g = 12 sum_c w_c psi(x + c) c, gathered at this node y, plus the
+    // node's own psi adjoint (one fixed-point frame, fixsum.cuh)
     const int64_t N = a.n, node = (int64_t)y * a.nx + x;
-    double psi_b = add_int(g.bar[3 * N + node], pg);
+    const double gv[13] = {g.bar[3 * N + node], sx[c - 1], sx[c + 1], sy[c - sw], sy[c + sw],
+                           sx[c - sw - 1], sy[c - sw - 1], sx[c + sw + 1], sy[c + sw + 1],
+                           sx[c + sw - 1], sy[c + sw - 1], sx[c - sw + 1], sy[c - sw + 1]};
+    double psi_b = fx::psi_adjoint_gather(gv);
     if constexpr (ST) {
       // transposes of t = (axis sum)/6 + (diagonal sum)/12 - psi(x), sd = (pE + pW) - (pN + pS),
       // xd = (pNE + pSW) - (pNW + pSE) at the neighbours (the -psi(x) term is A1's)
@@ -501,32 +616,14 @@ __global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
       for (int k = a2_index(G_K1L); k <= a2_index(G_K4L); ++k) dcsum[k] = psi2_b * dc[k];
     const double jxb = g.bar[N + node], jyb = g.bar[2 * N + node];
     // lambda^t_i = rho_bar + c_i . j_bar (+ rows 7, 8 of Eq. MatrixMRT times the stress
-    // moments' adjoints with the two-phase set). These sums stay on the FP64 pipe: with
-    // the stencil's on the integer pipe, this pass has more integer than FP64 work.
-    const double rp = rho_b + jxb, rm = rho_b - jxb;
-    double l1 = rp, l2 = rho_b + jyb, l3 = rm, l4 = rho_b - jyb;
-    double l5 = rp + jyb, l6 = rm + jyb, l7 = rm - jyb, l8 = rp - jyb;
-    if (KIND == kShearTau) {
-      const double m7b = g.bar[9 * N + node], m8b = g.bar[10 * N + node];
-      l1 += m7b;
-      l2 -= m7b;
-      l3 += m7b;
-      l4 -= m7b;
-      l5 += m8b;
-      l6 -= m8b;
-      l7 += m8b;
-      l8 -= m8b;
-    }
+    // moments' adjoints with the two-phase set), exact in one frame (fixsum.cuh)
+    constexpr bool kShear = KIND == kShearTau;
+    double l[9];
+    fx::lambda_assembly<kShear>(rho_b, jxb, jyb, kShear ? g.bar[9 * N + node] : 0.0,
+                                kShear ? g.bar[10 * N + node] : 0.0, l);
     double* L0 = g.lam0;
-    L0[node] = rho_b;
-    L0[N + node] = l1;
-    L0[2 * N + node] = l2;
-    L0[3 * N + node] = l3;
-    L0[4 * N + node] = l4;
-    L0[5 * N + node] = l5;
-    L0[6 * N + node] = l6;
-    L0[7 * N + node] = l7;
-    L0[8 * N + node] = l8;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) L0[k * N + node] = l[k];
   }
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   double* dst = g.partial2 + (int64_t)blk * kA2;

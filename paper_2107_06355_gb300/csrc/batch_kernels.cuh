@@ -65,26 +65,28 @@ __device__ __forceinline__ void stage_args(const BatchInst* __restrict__ inst, i
   __syncthreads();
 }
 
-// density/psi pass over block `local` (256 nodes) of instance id
-template <int KIND>
+// density/psi pass over block `local` (256 nodes) of instance id; REUSE: the block
+// takes another item afterwards (persistent kernel), so it waits until every thread is
+// done with the shared arguments
+template <int KIND, bool REUSE>
 __device__ __forceinline__ void batch_rho_psi_local(const BatchInst* __restrict__ inst, int id, int local,
                                                     int parity, StepArgs* sa) {
   stage_args(inst, id, parity, sa);
   const int64_t i = (int64_t)local * kThreads + threadIdx.x;
   if (i < sa->n) rho_psi_node<KIND>(*sa, sa->f_in, i);
-  __syncthreads();
+  if (REUSE) __syncthreads();
 }
 
-template <int KIND>
+template <int KIND, bool REUSE>
 __device__ __forceinline__ void batch_rho_psi_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
                                                    int w, int parity, StepArgs* sa) {
   const int id = owner[w];
-  batch_rho_psi_local<KIND>(inst, id, w - inst[id].k1_start, parity, sa);
+  batch_rho_psi_local<KIND, REUSE>(inst, id, w - inst[id].k1_start, parity, sa);
 }
 
 // collision pass over tile t of instance id; org: two shared ints for the tile
-// origin, which one thread computes per item
-template <int KIND, bool ST>
+// origin, which one thread computes per item; REUSE as for the density pass
+template <int KIND, bool ST, bool REUSE>
 __device__ __forceinline__ void batch_collide_local(const BatchInst* __restrict__ inst, int id, int t, int parity,
                                                     double* sp, StepArgs* sa, int* org) {
   const BatchInst& I = inst[id];
@@ -104,20 +106,20 @@ __device__ __forceinline__ void batch_collide_local(const BatchInst* __restrict_
   if (x < a.nx && y < a.ny)
     collide_node<KIND, false, ST>(a, x, y, sp, (ly + 1) * (tw + 2) + lx + 1, tw + 2, nullptr, nullptr, nullptr,
                                   nullptr);
-  __syncthreads();
+  if (REUSE) __syncthreads();
 }
 
-template <int KIND, bool ST>
+template <int KIND, bool ST, bool REUSE>
 __device__ __forceinline__ void batch_collide_item(const BatchInst* __restrict__ inst, const int* __restrict__ owner,
                                                    int w, int parity, double* sp, StepArgs* sa, int* org) {
   const int id = owner[w];
-  batch_collide_local<KIND, ST>(inst, id, w - inst[id].k2_start, parity, sp, sa, org);
+  batch_collide_local<KIND, ST, REUSE>(inst, id, w - inst[id].k2_start, parity, sp, sa, org);
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) k_batch_rho_psi(const BatchInst* inst, const int* owner, int parity) {
   __shared__ StepArgs sa;
-  batch_rho_psi_item<KIND>(inst, owner, blockIdx.x, parity, &sa);
+  batch_rho_psi_item<KIND, false>(inst, owner, blockIdx.x, parity, &sa);
 }
 
 // ST: some instance has the surface-tension source (kappa != 0); for the others
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
   __shared__ double sp[kMaxTileSmem];
   __shared__ StepArgs sa;
   __shared__ int org[2];
-  batch_collide_item<KIND, ST>(inst, owner, blockIdx.x, parity, sp, &sa, org);
+  batch_collide_item<KIND, ST, false>(inst, owner, blockIdx.x, parity, sp, &sa, org);
 }
 
 // Work items of both passes in one launch (the pipelined plan): item.x is the
@@ -150,9 +152,9 @@ __global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
   __shared__ int org[2];
   const int2 it = items[blockIdx.x];
   if (it.x >= 0)
-    batch_rho_psi_local<KIND>(inst, it.x, it.y, p1, &sa);
+    batch_rho_psi_local<KIND, false>(inst, it.x, it.y, p1, &sa);
   else
-    batch_collide_local<KIND, ST>(inst, it.x & 0x7FFFFFFF, it.y, p2, sp, &sa, org);
+    batch_collide_local<KIND, ST, false>(inst, it.x & 0x7FFFFFFF, it.y, p2, sp, &sa, org);
 }
 
 template <int KIND, bool ST>
@@ -167,9 +169,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* 
   if ((int)blockIdx.x == absent_block) return;
   for (long long s = 0; s < nsteps; ++s) {
     const int parity = (int)((parity0 + s) & 1);
-    for (int w = blockIdx.x; w < n1; w += gridDim.x) batch_rho_psi_item<KIND>(inst, owner1, w, parity, &sa);
+    for (int w = blockIdx.x; w < n1; w += gridDim.x) batch_rho_psi_item<KIND, true>(inst, owner1, w, parity, &sa);
     if (!grid_barrier(bar, err, spin_limit)) return;
-    for (int w = blockIdx.x; w < n2; w += gridDim.x) batch_collide_item<KIND, ST>(inst, owner2, w, parity, sp, &sa, org);
+    for (int w = blockIdx.x; w < n2; w += gridDim.x)
+      batch_collide_item<KIND, ST, true>(inst, owner2, w, parity, sp, &sa, org);
     if (!grid_barrier(bar, err, spin_limit)) return;
   }
 }

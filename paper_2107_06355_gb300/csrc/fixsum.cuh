@@ -275,6 +275,141 @@ PPLBM_FX void reduced_populations(double r, double xx, double yy, double xy, dou
   }
 }
 
+// The reverse mode of reduced_populations: given the adjoints mu_0..8 of the nine
+// populations, the adjoints of its inputs out = {r, xx, yy, xy, px, py, zz, p7, p8}
+// (the transpose of its small-integer combinations; p7, p8 only when SHEAR):
+//   r  = 16 mu0 + 4 (mu1 + mu2 + mu3 + mu4) + (mu5 + mu6 + mu7 + mu8)
+//   xx = -24 mu0 + 12 (mu1 + mu3) - 6 (mu2 + mu4) + 3 (mu5 + mu6 + mu7 + mu8)
+//   yy = -24 mu0 - 6 (mu1 + mu3) + 12 (mu2 + mu4) + 3 (mu5 + mu6 + mu7 + mu8)
+//   xy = p8 = 9 (mu5 + mu7 - mu6 - mu8)
+//   px = 12 (mu1 - mu3) + 3 (mu5 - mu7 - mu6 + mu8),  py = 12 (mu2 - mu4) + 3 (mu5 - mu7 + mu6 - mu8)
+//   zz = -8 mu0 + (mu1 + ... + mu8),                 p7 = 9 (mu1 + mu3 - mu2 - mu4),
+// exact in one frame over the nine adjoints (coefficients summing to 72 at most:
+// headroom 8) and each rounded once; p7, p8 are formed when ALL (default SHEAR) and
+// are 0.0 otherwise. A non-finite adjoint makes every output NaN.
+constexpr int kGTr = 8;
+
+template <bool SHEAR, bool ALL = SHEAR>
+PPLBM_FX void reduced_populations_transpose(const double (&mu)[9], double (&out)[9]) {
+  u64 b[9];
+  unsigned mx = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    b[k] = bits_of(mu[k]);
+    mx = mx > mag_hi(b[k]) ? mx : mag_hi(b[k]);
+  }
+  const int eg = (int)(mx >> 20) + kGTr;
+  u64 t[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t[k] = (u64)sterm(b[k], eg);
+  const u64 a13 = t[1] + t[3], a24 = t[2] + t[4], d13 = t[1] - t[3], d24 = t[2] - t[4];
+  const u64 s57 = t[5] + t[7], s68 = t[6] + t[8], d57 = t[5] - t[7], d68 = t[6] - t[8];
+  const u64 diag = s57 + s68;
+  u64 n[9];
+  n[0] = 16 * t[0] + 4 * (a13 + a24) + diag;
+  n[1] = 3 * diag - 24 * t[0] + 12 * a13 - 6 * a24;
+  n[2] = 3 * diag - 24 * t[0] - 6 * a13 + 12 * a24;
+  n[3] = 9 * (s57 - s68);
+  n[4] = 12 * d13 + 3 * (d57 - d68);
+  n[5] = 12 * d24 + 3 * (d57 + d68);
+  n[6] = a13 + a24 + diag - 8 * t[0];
+  n[7] = 9 * (a13 - a24);
+  n[8] = n[3];
+  const bool bad = mx >= 0x7FF00000u;
+  const int kout = ALL ? 9 : 7;  // ALL: p7, p8 too (the adjoints the source terms need)
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    if (k >= kout) {
+      out[k] = 0.0;
+      continue;
+    }
+    out[k] = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)n[k], eg));
+  }
+}
+
+// The reverse mode of j_h_combos: from the adjoints a1, a2, a3 of j + h, j + 2h, j + 3h,
+// a4 of j - h (when MINUS) and partial adjoints j0 of j and h0 of h, the adjoints
+//   jb = j0 + a1 + a2 + a3 (+ a4),  hb = h0 + a1 + 2 a2 + 3 a3 (- a4),
+// exact in one frame (coefficients summing to 8 at most: headroom 5) and rounded once.
+template <bool MINUS>
+PPLBM_FX void j_h_combos_transpose(double a1, double a2, double a3, double a4, double j0, double h0, double* jb,
+                                   double* hb) {
+  const double v[6] = {a1, a2, a3, MINUS ? a4 : 0.0, j0, h0};
+  u64 b[6];
+  unsigned mx = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    b[k] = bits_of(v[k]);
+    mx = mx > mag_hi(b[k]) ? mx : mag_hi(b[k]);
+  }
+  const int eg = (int)(mx >> 20) + 5;
+  u64 t[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) t[k] = (u64)sterm(b[k], eg);
+  const u64 s = t[0] + t[1] + t[2];
+  const bool bad = mx >= 0x7FF00000u;
+  *jb = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)(t[4] + s + t[3]), eg));
+  *hb = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)(t[5] + s + t[1] + 2 * t[2] - t[3]), eg));
+}
+
+// The adjoint's transpose of the Shan-Chen stencil at a node, plus the node's own
+// psi adjoint: with gx_bar (sx) and gy_bar (sy) at the neighbours,
+//   psi_bar = own + 4 (sxW - sxE) + 4 (syS - syN) + (sxSW + sySW) - (sxNE + syNE)
+//                 + (sxNW - syNW) - (sxSE - sySE),
+// exact in one frame (coefficients summing to 25: headroom 6) and rounded once. v
+// holds {own, sxW, sxE, syS, syN, sxSW, sySW, sxNE, syNE, sxNW, syNW, sxSE, sySE}; a
+// non-finite value gives NaN.
+PPLBM_FX double psi_adjoint_gather(const double (&v)[13]) {
+  u64 b[13];
+  unsigned mx = 0;
+#pragma unroll
+  for (int k = 0; k < 13; ++k) {
+    b[k] = bits_of(v[k]);
+    mx = mx > mag_hi(b[k]) ? mx : mag_hi(b[k]);
+  }
+  const int eg = (int)(mx >> 20) + 6;
+  u64 t[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) t[k] = (u64)sterm(b[k], eg);
+  const u64 s = t[0] + 4 * ((t[1] - t[2]) + (t[3] - t[4])) + (t[5] + t[6]) - (t[7] + t[8]) + (t[9] - t[10]) -
+                (t[11] - t[12]);
+  return double_of(mx >= 0x7FF00000u ? 0x7FF8000000000000ull : round_frame_s((i64)s, eg));
+}
+
+// The adjoint's lambda^t_i = rho_bar + c_i . j_bar (+ with SHEAR the rows 7, 8 of Eq.
+// MatrixMRT times the stress moments' adjoints m7_bar, m8_bar: +-1 on the axes,
+// +-1 on the diagonals), i = 1..8 (lambda_0 = rho_bar), exact in one frame
+// (coefficients summing to 4: headroom 4) and each rounded once.
+template <bool SHEAR>
+PPLBM_FX void lambda_assembly(double rb, double jxb, double jyb, double m7b, double m8b, double (&l)[9]) {
+  const double v[5] = {rb, jxb, jyb, SHEAR ? m7b : 0.0, SHEAR ? m8b : 0.0};
+  u64 b[5];
+  unsigned mx = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    b[k] = bits_of(v[k]);
+    mx = mx > mag_hi(b[k]) ? mx : mag_hi(b[k]);
+  }
+  const int eg = (int)(mx >> 20) + 4;
+  u64 t[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) t[k] = (u64)sterm(b[k], eg);
+  const u64 rp = t[0] + t[1], rm = t[0] - t[1];
+  u64 n[9];
+  n[1] = rp + t[3];
+  n[2] = t[0] + t[2] - t[3];
+  n[3] = rm + t[3];
+  n[4] = t[0] - t[2] - t[3];
+  n[5] = rp + t[2] + t[4];
+  n[6] = rm + t[2] - t[4];
+  n[7] = rm - t[2] + t[4];
+  n[8] = rp - t[2] - t[4];
+  const bool bad = mx >= 0x7FF00000u;
+  l[0] = rb;
+#pragma unroll
+  for (int k = 1; k < 9; ++k) l[k] = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)n[k], eg));
+}
+
 // True if all K values are positive normal doubles below 2^1008 (high words in
 // [0x00100000, 0x7EF00000): a negative value's high word is above the range); the
 // largest high word goes to *max_hi.

@@ -277,3 +277,48 @@ extern "C" pplbm_status pplbm_fixsum_collision_eval(long long n, int32_t shear, 
     pplbm::k_fixsum_collision_eval<false><<<blocks, 256, 0, s>>>(n, q, jh, out);
   return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
 }
+
+// The reverse-mode stages on caller data, one thread per row.
+namespace pplbm {
+namespace {
+
+template <bool SHEAR>
+__global__ void k_fixsum_adjoint_eval(long long n, const double* mu, const double* a, const double* gth,
+                                      const double* lam, double* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double m[9], u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = mu[9 * i + k];
+  fx::reduced_populations_transpose<SHEAR>(m, u);
+  double* o = out + 21 * i;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[k] = u[k];
+  const double* q = a + 6 * i;
+  fx::j_h_combos_transpose<true>(q[0], q[1], q[2], q[3], q[4], q[5], &o[9], &o[10]);
+  double gv[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) gv[k] = gth[13 * i + k];
+  o[11] = fx::psi_adjoint_gather(gv);
+  const double* r = lam + 5 * i;
+  double l[9];
+  fx::lambda_assembly<SHEAR>(r[0], r[1], r[2], r[3], r[4], l);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[12 + k] = l[k];
+}
+
+}  // namespace
+}  // namespace pplbm
+
+extern "C" pplbm_status pplbm_fixsum_adjoint_eval(long long n, int32_t shear, const double* mu, const double* a,
+                                                  const double* gth, const double* lam, double* out, void* stream) {
+  if (n < 0 || n > 0x7FFFFFFFLL * 255 || (n > 0 && (!mu || !a || !gth || !lam || !out))) return PPLBM_ERR_ARG;
+  if (n == 0) return PPLBM_OK;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (shear)
+    pplbm::k_fixsum_adjoint_eval<true><<<blocks, 256, 0, s>>>(n, mu, a, gth, lam, out);
+  else
+    pplbm::k_fixsum_adjoint_eval<false><<<blocks, 256, 0, s>>>(n, mu, a, gth, lam, out);
+  return cudaGetLastError() == cudaSuccess ? PPLBM_OK : PPLBM_ERR_CUDA;
+}

@@ -34,6 +34,12 @@ def fixsum_host(tmp_path_factory):
     for name in ("fx_density", "fx_stencil", "fx_j_h"):
         getattr(lib, name).argtypes = [C.c_longlong, C.c_void_p, C.c_void_p]
         getattr(lib, name).restype = None
-    lib.fx_populations.argtypes = [C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
-    lib.fx_populations.restype = None
+    for name in ("fx_populations", "fx_populations_transpose"):
+        getattr(lib, name).argtypes = [C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
+        getattr(lib, name).restype = None
+    for name in ("fx_j_h_transpose", "fx_psi_gather"):
+        getattr(lib, name).argtypes = [C.c_longlong, C.c_void_p, C.c_void_p]
+        getattr(lib, name).restype = None
+    lib.fx_lambda.argtypes = [C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
+    lib.fx_lambda.restype = None
     return lib

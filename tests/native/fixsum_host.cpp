@@ -52,3 +52,52 @@ void fx_populations(long long n, int shear, const double* in, double* out) {
   }
 }
 }
+
+extern "C" {
+
+// n rows of mu (9) -> out (n x 9): the adjoints of reduced_populations' inputs
+void fx_populations_transpose(long long n, int shear, const double* mu, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    double m[9], o[9];
+    for (int k = 0; k < 9; ++k) m[k] = mu[9 * i + k];
+    if (shear)
+      reduced_populations_transpose<true>(m, o);
+    else
+      reduced_populations_transpose<false>(m, o);
+    for (int k = 0; k < 9; ++k) out[9 * i + k] = o[k];
+  }
+}
+
+// n rows of (a1, a2, a3, a4, j0, h0) -> out (n x 2): jb, hb (with the j - h adjoint a4)
+void fx_j_h_transpose(long long n, const double* in, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    const double* q = in + 6 * i;
+    j_h_combos_transpose<true>(q[0], q[1], q[2], q[3], q[4], q[5], &out[2 * i], &out[2 * i + 1]);
+  }
+}
+}
+
+extern "C" {
+
+// n rows of 13 gather inputs -> out (n): psi_adjoint_gather
+void fx_psi_gather(long long n, const double* in, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    double v[13];
+    for (int k = 0; k < 13; ++k) v[k] = in[13 * i + k];
+    out[i] = psi_adjoint_gather(v);
+  }
+}
+
+// n rows of (rho_b, jx_b, jy_b, m7_b, m8_b) -> out (n x 9): lambda_assembly
+void fx_lambda(long long n, int shear, const double* in, double* out) {
+  for (long long i = 0; i < n; ++i) {
+    const double* q = in + 5 * i;
+    double l[9];
+    if (shear)
+      lambda_assembly<true>(q[0], q[1], q[2], q[3], q[4], l);
+    else
+      lambda_assembly<false>(q[0], q[1], q[2], q[3], q[4], l);
+    for (int k = 0; k < 9; ++k) out[9 * i + k] = l[k];
+  }
+}
+}

@@ -287,3 +287,111 @@ def test_reduced_populations_non_finite_input_gives_nan(fx):
     q = np.full((3, 9), 0.01)
     q[0, 6], q[1, 2], q[2, 8] = np.inf, np.nan, np.inf
     assert np.all(np.isnan(populations(fx, q, True)))
+
+
+def populations_transpose(lib, mu, shear):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = np.zeros((mu.shape[0], 9))
+    lib.fx_populations_transpose(mu.shape[0], 1 if shear else 0, mu.ctypes.data, out.ctypes.data)
+    return out
+
+
+def _unit(k):
+    q = np.zeros(9)
+    q[k] = 1.0
+    return q
+
+
+@pytest.mark.parametrize("shear", [False, True])
+def test_populations_transpose_is_the_adjoint_of_the_definition(fx, shear):
+    """The reverse-mode stage against the derivative of the populations' definition:
+    out_k = sum_i mu_i df_i/dq_k, with df_i/dq_k = f_i(e_k) (f is linear in the
+    scaled inputs), in exact rational arithmetic, within the frame's bound."""
+    jac = [populations_by_definition(_unit(k), shear) for k in range(9)]  # jac[k][i]
+    rng = np.random.default_rng(77 + shear)
+    n = 2000
+    mu = rng.normal(size=(n, 9)) * 10.0 ** rng.uniform(-6, 2, size=(n, 1))
+    mu[:200] *= 10.0 ** rng.uniform(-3, 0, size=(200, 9))   # adjoints of unequal size
+    mu[200:220, 4] = 0.0
+    out = populations_transpose(fx, mu, shear)
+    coef = [36, 72, 72, 36, 36, 36, 16, 36, 36]
+    for i in range(n):
+        m = [Fraction(float(v)) for v in mu[i]]
+        for k in range(9 if shear else 7):
+            ex = sum(m[j] * jac[k][j] for j in range(9))
+            assert abs(Fraction(float(out[i, k])) - ex) <= frame_bound(out[i, k], ex, mu[i], coef[k], 8), (i, k)
+    if not shear:
+        assert np.all(out[:, 7:] == 0.0)
+
+
+def test_populations_transpose_exact_cases(fx):
+    # equal adjoints on every population: d(sum f)/d(rho/36) = 36, the rest cancels
+    out = populations_transpose(fx, np.full((1, 9), 0.5), True)[0]
+    assert out[0] == 18.0 and np.all(out[1:6] == [0.0, 0.0, 0.0, 0.0, 0.0]) and out[6] == 0.0
+    assert out[7] == 0.0 and out[8] == 0.0
+    q = np.full((2, 9), 0.1)
+    q[1, 3] = np.nan
+    assert np.all(np.isnan(populations_transpose(fx, q, True)[1]))
+
+
+def test_j_h_transpose_within_the_bound(fx):
+    rng = np.random.default_rng(31)
+    n = 3000
+    a = rng.normal(size=(n, 6)) * 10.0 ** rng.uniform(-8, 1, size=(n, 6))
+    a[:100, 3] = 0.0
+    a[100:200, 4] = 0.0
+    out = np.zeros((n, 2))
+    fx.fx_j_h_transpose(n, np.ascontiguousarray(a).ctypes.data, out.ctypes.data)
+    for i in range(n):
+        a1, a2, a3, a4, j0, h0 = [Fraction(float(v)) for v in a[i]]
+        jb, hb = j0 + a1 + a2 + a3 + a4, h0 + a1 + 2 * a2 + 3 * a3 - a4
+        assert abs(Fraction(float(out[i, 0])) - jb) <= frame_bound(out[i, 0], jb, a[i], 5, 5)
+        assert abs(Fraction(float(out[i, 1])) - hb) <= frame_bound(out[i, 1], hb, a[i], 8, 5)
+
+
+def test_psi_adjoint_gather_is_the_stencil_transpose(fx):
+    """psi_bar(y) = own + sum_c W_c (c_x gx_bar(y - c) + c_y gy_bar(y - c)) with W = 4 on the
+    axes and 1 on the diagonals: the value each neighbour y - c's stencil took from y,
+    written out from the stencil's definition (gx = 4 (pE - pW) + ..., so node y enters
+    the gx of its west neighbour with +4 and of its east neighbour with -4, etc.)."""
+    rng = np.random.default_rng(41)
+    n = 3000
+    v = rng.normal(size=(n, 13)) * 10.0 ** rng.uniform(-6, 1, size=(n, 13))
+    v[:50, 0] = 0.0
+    out = np.zeros(n)
+    fx.fx_psi_gather(n, np.ascontiguousarray(v).ctypes.data, out.ctypes.data)
+    # neighbour offsets of the inputs (order: own, sxW, sxE, syS, syN, sxSW, sySW, sxNE,
+    # syNE, sxNW, syNW, sxSE, sySE) and the stencil weight of node y in that neighbour's
+    # g: for a neighbour at y - c the node sits at +c, with weight W_c c
+    W = {(1, 0): 4, (-1, 0): 4, (0, 1): 4, (0, -1): 4, (1, 1): 1, (-1, -1): 1, (1, -1): 1, (-1, 1): 1}
+    nb = [("x", (-1, 0)), ("x", (1, 0)), ("y", (0, -1)), ("y", (0, 1)), ("x", (-1, -1)), ("y", (-1, -1)),
+          ("x", (1, 1)), ("y", (1, 1)), ("x", (-1, 1)), ("y", (-1, 1)), ("x", (1, -1)), ("y", (1, -1))]
+    for i in range(n):
+        q = [Fraction(float(t)) for t in v[i]]
+        ex = q[0]
+        for k, (comp, (dx, dy)) in enumerate(nb):
+            cx, cy = -dx, -dy   # node y is at +c from the neighbour at y - c
+            w = W[(cx, cy)] * (cx if comp == "x" else cy)
+            ex += w * q[k + 1]
+        assert abs(Fraction(float(out[i])) - ex) <= frame_bound(out[i], ex, v[i], 25, 6), i
+
+
+@pytest.mark.parametrize("shear", [False, True])
+def test_lambda_assembly_matches_the_moment_rows(fx, shear):
+    """lambda_i = rho_bar + c_i . j_bar (+ M7_i m7_bar + M8_i m8_bar with rows 7, 8 of the
+    MRT matrix restricted to the populations, (c_x^2 - c_y^2) and c_x c_y), exact."""
+    rng = np.random.default_rng(43 + shear)
+    n = 3000
+    v = rng.normal(size=(n, 5)) * 10.0 ** rng.uniform(-6, 1, size=(n, 5))
+    out = np.zeros((n, 9))
+    fx.fx_lambda(n, 1 if shear else 0, np.ascontiguousarray(v).ctypes.data, out.ctypes.data)
+    assert np.array_equal(out[:, 0], v[:, 0])
+    for i in range(n):
+        r, jx, jy, m7, m8 = [Fraction(float(t)) for t in v[i]]
+        for k in range(1, 9):
+            cx, cy = CX[k], CY[k]
+            ex = r + cx * jx + cy * jy
+            if shear:
+                ex += (cx * cx - cy * cy) * m7 + cx * cy * m8
+            ops = v[i] if shear else v[i, :3]
+            assert abs(Fraction(float(out[i, k])) - ex) <= frame_bound(out[i, k], ex, ops, 4, 4), (i, k)

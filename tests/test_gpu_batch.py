@@ -339,3 +339,36 @@ def test_sweep_64_lattices_full_length_stable():
     np.testing.assert_allclose(g[:, 0], g0[:, 0], rtol=1e-10)
     assert (g[:, 1] < 0.3).all()
     b.close()
+
+
+@pytest.mark.parametrize("count", [1, 2, 3])
+def test_pipelined_plan_small_batches_bitwise(count):
+    """The pipelined plan with one instance (the second group empty: prologue, the
+    first group's passes in turn, an empty epilogue), two and three (groups of
+    unequal node counts), over call lengths 1, 2, 5: bitwise the single-lattice step,
+    and every instance at the same step after each call."""
+    inst = [(70, 45, BC_PER, 0.6, "droplet"), (48, 40, BC_WALLS, 0.6, "impact"), (4, 90, BC_PER, 0.8, "planar")]
+    inst = inst[:count]
+    eos = [P.EOSParams(P.EOS_SMOOTH, Tr, 0.363, 2.0, 0.775) for (_, _, _, Tr, _) in inst]
+    relax = [P.Relax() for _ in inst]
+    b = P.Batch([(nx, ny, bc) for (nx, ny, bc, _, _) in inst], eos, relax)
+    sims = []
+    for k, (nx, ny, bc, Tr, kind) in enumerate(inst):
+        s = P.Simulation(nx, ny, bc, eos[k], relax[k])
+        rho, ux, uy = _init_fields(kind, nx, ny, s.derived(), 300 + k)
+        s.init_equilibrium(rho, ux, uy)
+        b.init_equilibrium(k, rho, ux, uy)
+        sims.append(s)
+    b.set_plan(P.PLAN_PIPELINED, 0)
+    done = 0
+    for nsteps in (1, 2, 5):
+        b.step(nsteps)
+        done += nsteps
+        for s in sims:
+            s.step(nsteps)
+        assert b.sync() == done
+        for k, s in enumerate(sims):
+            assert torch.equal(b.get_f(k), s.get_f()), (count, k, nsteps)
+    b.close()
+    for s in sims:
+        s.close()

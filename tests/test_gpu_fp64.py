@@ -143,3 +143,50 @@ def test_collision_fixed_point_device_build_equals_host_build(fixsum_host, shear
     assert np.array_equal(dev[:, 9:].view(np.int64), hj.view(np.int64))
     assert L.lib().pplbm_fixsum_collision_eval(-1, 0, None, None, None, None) == L.PPLBM_ERR_ARG
     assert L.lib().pplbm_fixsum_collision_eval(2, 0, None, None, None, None) == L.PPLBM_ERR_ARG
+
+
+@pytest.mark.parametrize("shear", [0, 1])
+def test_adjoint_fixed_point_device_build_equals_host_build(fixsum_host, shear):
+    """The adjoint's fixed-point stages (fixsum.cuh: the transposed output stage and
+    sums of the collision pass, the psi gather and lambda assembly of the density pass)
+    compiled for sm_103a against the host build (checked in test_fixsum_host.py against
+    derivatives of the populations' definition, the stencil's transpose and the moment
+    rows): bit for bit on 2^20 rows, with zeros and non-finite inputs."""
+    import numpy as np
+
+    from paper_2107_06355_gb300 import _lib as L
+
+    rng = np.random.default_rng(90 + shear)
+    n = 1 << 20
+    mu = rng.normal(size=(n, 9)) * 10.0 ** rng.uniform(-6, 2, size=(n, 1))
+    mu[:5000] *= 10.0 ** rng.uniform(-3, 0, size=(5000, 9))
+    mu[5000:5100, 2] = 0.0
+    mu[5100:5110, 7] = np.nan
+    a = rng.normal(size=(n, 6)) * 10.0 ** rng.uniform(-8, 1, size=(n, 6))
+    a[:300, 3] = 0.0
+    a[300:310, 5] = np.inf
+    gth = rng.normal(size=(n, 13)) * 10.0 ** rng.uniform(-6, 1, size=(n, 13))
+    gth[:200, 0] = 0.0
+    gth[200:210, 7] = np.nan
+    lam = rng.normal(size=(n, 5)) * 10.0 ** rng.uniform(-6, 1, size=(n, 5))
+    lam[:100, 3:] = 0.0
+    host_u = np.zeros((n, 9))
+    host_j = np.zeros((n, 2))
+    host_g = np.zeros(n)
+    host_l = np.zeros((n, 9))
+    fixsum_host.fx_populations_transpose(n, shear, np.ascontiguousarray(mu).ctypes.data, host_u.ctypes.data)
+    fixsum_host.fx_j_h_transpose(n, np.ascontiguousarray(a).ctypes.data, host_j.ctypes.data)
+    fixsum_host.fx_psi_gather(n, np.ascontiguousarray(gth).ctypes.data, host_g.ctypes.data)
+    fixsum_host.fx_lambda(n, shear, np.ascontiguousarray(lam).ctypes.data, host_l.ctypes.data)
+    dev_in = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (mu, a, gth, lam)]
+    out = torch.empty((n, 21), dtype=torch.float64, device="cuda")
+    st = L.lib().pplbm_fixsum_adjoint_eval(n, shear, *[C.c_void_p(t.data_ptr()) for t in dev_in],
+                                           C.c_void_p(out.data_ptr()),
+                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    dev = out.cpu().numpy()
+    assert np.array_equal(dev[:, :9].view(np.int64), host_u.view(np.int64))
+    assert np.array_equal(dev[:, 9:11].view(np.int64), host_j.view(np.int64))
+    assert np.array_equal(dev[:, 11].view(np.int64), host_g.view(np.int64))
+    assert np.array_equal(dev[:, 12:].view(np.int64), host_l.view(np.int64))
+    assert L.lib().pplbm_fixsum_adjoint_eval(-1, 0, None, None, None, None, None, None) == L.PPLBM_ERR_ARG
