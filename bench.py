@@ -91,9 +91,9 @@ FD_ALU_PER_POINT = 1948 + 1960 + 2 * 11
 # node. They hold for the device code whose digest is recorded with them; once it
 # changes, traffic is null and the source counts above are used until the capture is
 # repeated.
-COUNTS = {"sources": "2cb174fe8ee956f9",
-          "rho_psi": {"dram_bytes": 1316795648, "fp64_per_node": 14.542, "alu_per_node": 222.7},
-          "collide": {"dram_bytes": 1298580992, "fp64_per_node": 19.000, "alu_per_node": 1018.1}}
+COUNTS = {"sources": "e6fc390a598ffce1",
+          "rho_psi": {"dram_bytes": 1317249024, "fp64_per_node": 14.542, "alu_per_node": 222.7},
+          "collide": {"dram_bytes": 1298248704, "fp64_per_node": 19.000, "alu_per_node": 1018.1}}
 KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "fixsum.cuh",
                   "internal.h")
 
@@ -553,7 +553,7 @@ def eos_variant_throughput(torch, steps=1000):
         d = b.derived(0)
         for k, R in enumerate((32, 48, 64, 96)):
             b.init_equilibrium(k, I.droplet(512, 512, R, d["rho_v"], d["rho_l"], W=8.0))
-        b.set_plan(P.PLAN_GRAPH, 0)
+        b.autotune(trial_steps=20)
         b.step(20)
         ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
         try:
@@ -569,8 +569,9 @@ def impact_sweep_throughput(torch, fp64_peak, steps=2000):
     """A slice of the stability study (Sec. IV.D) on the batched engine: droplet
     impact at Re = 300 on (600, 250) lattices with walls, C-S a = 0.363, Li forcing,
     two-phase tau(rho), T_r in {0.45, ..., 0.75} x v_r in {2, ..., 10}: 35 instances,
-    5.25 M nodes, graph plan with divergence isolation."""
+    5.25 M nodes, autotuned plan with divergence isolation."""
     b, n_inst = impact_sweep_batch()
+    plan = {0: "launches", 1: "graph", 2: "persistent", 3: "pipelined"}[b.plan()["mode"]]
     b.step(20)
     ms = time_device(torch, torch.cuda.current_stream(), lambda: b.step(steps))
     g = b.guard()
@@ -578,7 +579,7 @@ def impact_sweep_throughput(torch, fp64_peak, steps=2000):
     b.close()
     nodes = 600 * 250 * n_inst
     mlups = nodes * steps / (ms / 1e3) / 1e6 if stable == n_inst else None
-    out = {"instances": n_inst, "stable": stable, "nodes": nodes, "steps": steps, "mlups": mlups}
+    out = {"instances": n_inst, "stable": stable, "nodes": nodes, "steps": steps, "mlups": mlups, "plan": plan}
     if mlups is not None:
         per = sum(FP64_PER_NODE_SHEAR.values())
         achieved = per * mlups * 1e6
@@ -588,7 +589,7 @@ def impact_sweep_throughput(torch, fp64_peak, steps=2000):
 
 
 def impact_sweep_batch():
-    """The impact-sweep batch, initialised, on the graph plan: (Batch, instances)."""
+    """The impact-sweep batch, initialised, on the autotuned plan: (Batch, instances)."""
     import lbm_inputs as I
     import paper_2107_06355_gb300 as P
 
@@ -608,7 +609,7 @@ def impact_sweep_batch():
     for i in range(len(lats)):
         d = b.derived(i)
         b.init_equilibrium(i, *I.impact(600, 250, 50, 25, d["rho_v"], d["rho_l"], 0.1, W=Ws[i]))
-    b.set_plan(P.PLAN_GRAPH, 0)
+    b.autotune(trial_steps=20)
     return b, len(lats)
 
 

@@ -556,8 +556,10 @@ __device__ __forceinline__ void load_bar_tiles(const AdjArgs& g, int p0, double*
   }
 }
 
+// 4 resident blocks per SM (64 registers, 8-16 bytes spilled): at 71 registers and 3
+// blocks the pass's FP64 pipe waits on latency (125 against 109 us on 1024^2)
 template <int KIND, bool ST>
-__global__ void __launch_bounds__(kNT) k_adj_rho_psi(const AdjArgs g) {
+__global__ void __launch_bounds__(kNT, 4) k_adj_rho_psi(const AdjArgs g) {
   constexpr int ts = (kTY + 2) * (kTX + 2);
   __shared__ double tiles[(ST ? 5 : 2) * ts];  // gx_bar, gy_bar (and t_bar, sd_bar, xd_bar)
   __shared__ double red[kNT];
