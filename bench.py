@@ -78,11 +78,12 @@ BYTES_PER_NODE_SHEAR = {"rho_psi": 72 + 48, "collide": 40 + 8 + 72}
 BYTES_PER_NODE_SCOPE = 232
 # FP64-pipe and integer-pipe (ALU) instructions of one MacCormack step per grid point
 # (ncu, sm__inst_executed_pipe_fp64 / _alu x 32 per point, one kernel per capture, the
-# 2048 x 1024 grid of fd_throughput): predictor 54.0 / 1,948, corrector 60.0 / 1,960,
+# 2048 x 1024 grid of fd_throughput): predictor 54.0 / 1,947, corrector 60.0 / 1,963,
 # two EOS passes of 24.9 / 11; the update kernels' stencil differences are integer
-# combinations in fixed-point frames (76 % / 73 % ALU against 67 % / 71 % FP64 active)
+# combinations in fixed-point frames (at 3 blocks per SM: ALU 89 % / 86 %, FP64 79 % /
+# 84 % active)
 FD_FP64_PER_POINT = 54.0 + 60.0 + 2 * 24.9
-FD_ALU_PER_POINT = 1948 + 1960 + 2 * 11
+FD_ALU_PER_POINT = 1947 + 1963 + 2 * 11
 
 # Per launch of each batched pass on the headline workload (all 64 lattices), from
 # one ncu capture per kernel (--metrics dram__bytes_read.sum, dram__bytes_write.sum,

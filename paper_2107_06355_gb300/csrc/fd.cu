@@ -196,8 +196,10 @@ __device__ __forceinline__ VelDiffs vel_diffs(double c, double e, double w, doub
 // PRED: predictor (forward differences) or corrector (backward); VV: tau_nu(rho)
 // viscosities, a compile-time choice so the constant-viscosity kernel carries none
 // of their arithmetic
+// 3 resident blocks per SM (80 registers, 16-36 bytes spilled): the two arithmetic pipes
+// issue 10 % faster than at 2 blocks and 89-94 registers
 template <bool PRED, bool VV>
-__global__ void __launch_bounds__(256) k_fd_update(const FDArgs a) {
+__global__ void __launch_bounds__(256, 3) k_fd_update(const FDArgs a) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;

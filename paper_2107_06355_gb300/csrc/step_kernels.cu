@@ -32,8 +32,13 @@ __global__ void __launch_bounds__(256) k_rho_psi(const StepArgs a) {
   rho_psi_node<KIND>(a, a.f_in, i);
 }
 
+// 5 resident blocks per SM (48 registers, 8-16 bytes spilled) except the two-phase
+// kernel with the surface-tension source, which would spill 60 bytes: the
+// integer-bound pass issues faster with the extra warps
+constexpr int collide_blocks(int kind, bool st) { return (st && kind == kShearTau) ? 4 : 5; }
+
 template <int KIND, bool FIELDS, bool ST = false>
-__global__ void __launch_bounds__(kTX* kTY) k_collide(const StepArgs a, double* rho_o, double* ux_o, double* uy_o,
+__global__ void __launch_bounds__(kTX* kTY, collide_blocks(KIND, ST)) k_collide(const StepArgs a, double* rho_o, double* ux_o, double* uy_o,
                                                       double* psi_o) {
   __shared__ double sp[(kTY + 2) * (kTX + 2)];
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
