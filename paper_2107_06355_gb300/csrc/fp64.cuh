@@ -12,8 +12,11 @@
 // Comparisons of non-negative doubles are done on their bit patterns as signed
 // 64-bit integers, which orders them like the doubles and runs on the integer
 // pipe. A negative or NaN operand compares as out of range, which the callers
-// treat as an error. add_pos_int moves additions of positive doubles to the integer
-// pipe, bit for bit equal to the FP64 pipe's.
+// treat as an error. add_pos_int and add_int are software IEEE additions on the
+// integer pipe, bit for bit equal to the FP64 pipe's: add_int carries the sums the
+// fixed-point frames of fixsum.cuh do not (the surface-tension path, the adjoint's
+// remaining sums, the FD solver's one-sided differences); the issue-rate probe times
+// add_pos_int.
 #pragma once
 
 #include <cstdint>
@@ -67,14 +70,13 @@ __device__ __forceinline__ double opaque_double(unsigned long long r) {
 
 // Sum of two positive normal doubles on the integer pipe, correctly rounded
 // (round to nearest, ties to even: IEEE 754-2008, 4.3.1), so bitwise equal to the
-// FP64 pipe's x + y. The FP64 pipe is the step kernels' bottleneck while the integer
-// pipe is nearly idle and runs beside it, so additions moved here shorten the pass.
+// FP64 pipe's x + y. The integer pipe runs beside the narrow FP64 pipe, so an
+// addition moved here frees an FP64 issue slot.
 // Textbook method (e.g. Muller et al., Handbook of Floating-Point Arithmetic, ch. 7):
 // align the smaller significand with three extra bits (guard, round and a sticky bit
 // that ORs everything shifted out), add, renormalise by at most one place, round.
-// Both operands must be positive and normal with a normal sum (callers check their
-// inputs with all_positive_normal); pplbm_int_add_selftest compares it with the FP64
-// add bit for bit.
+// Both operands must be positive and normal with a normal sum;
+// pplbm_int_add_selftest compares it with the FP64 add bit for bit.
 __device__ __forceinline__ double add_pos_int(double x, double y) {
   typedef unsigned long long u64;
   const u64 a = opaque_bits(x), b = opaque_bits(y);
@@ -143,22 +145,6 @@ __device__ __forceinline__ double add_bits_int(unsigned long long a, unsigned lo
 __device__ __forceinline__ double add_int(double x, double y) { return add_bits_int(opaque_bits(x), opaque_bits(y)); }
 __device__ __forceinline__ double sub_int(double x, double y) {
   return add_bits_int(opaque_bits(x), opaque_bits(y) ^ (1ull << 63));
-}
-
-// True if every value is a positive normal double below 2^1000 (so add_pos_int
-// applies to them and to sums of a few of them): the sign bits ORed, and the smallest
-// and largest high words against that range.
-template <int K>
-__device__ __forceinline__ bool all_positive_normal(const double (&v)[K]) {
-  unsigned int orh = 0, mn = 0xFFFFFFFFu, mx = 0u;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const unsigned int h = (unsigned int)__double2hiint(v[k]);
-    orh |= h;
-    mn = min(mn, h);
-    mx = max(mx, h);
-  }
-  return !(orh >> 31) && mn >= 0x00100000u && mx < 0x7EF00000u;
 }
 
 }  // namespace pplbm
