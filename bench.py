@@ -60,7 +60,7 @@ MIN_BLOCKS = 5
 # (COUNTS).
 FP64_PER_NODE = {"rho_psi": 15, "collide": 19}
 # integer-pipe (ALU) instructions per node of the same passes (ncu; fallback figures)
-ALU_PER_NODE = {"rho_psi": 223, "collide": 1015}
+ALU_PER_NODE = {"rho_psi": 223, "collide": 1020}
 # ALU pipe issue rate: 64 thread instructions per SM per clock (ncu's
 # sm__pipe_alu_cycles_active scale: 82.7 % active at 16.6e12 instructions/s)
 ALU_PER_SM_CLK = 64
@@ -92,9 +92,9 @@ FD_ALU_PER_POINT = 1947 + 1963 + 2 * 11
 # node. They hold for the device code whose digest is recorded with them; once it
 # changes, traffic is null and the source counts above are used until the capture is
 # repeated.
-COUNTS = {"sources": "9859c1ca68236367",
-          "rho_psi": {"dram_bytes": 1316701952, "fp64_per_node": 14.542, "alu_per_node": 222.7},
-          "collide": {"dram_bytes": 1297908736, "fp64_per_node": 19.000, "alu_per_node": 1018.1}}
+COUNTS = {"sources": "bdd011740931cc36",
+          "rho_psi": {"dram_bytes": 1316528384, "fp64_per_node": 14.542, "alu_per_node": 222.7},
+          "collide": {"dram_bytes": 1302848768, "fp64_per_node": 19.000, "alu_per_node": 1020.1}}
 KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "fixsum.cuh",
                   "internal.h")
 

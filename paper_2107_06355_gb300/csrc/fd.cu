@@ -118,7 +118,8 @@ using fx::u64;
 // diagonals: central first differences Pd, second differences Pxx, Pyy, the mixed
 // one q = Dxy / 4, the Laplacian Lc = Pxx + Pyy and the differences DL of the
 // 5-point Laplacians at +-1 (their coefficients sum to 14 at most: headroom 5 + sign).
-// A non-finite value makes them all NaN.
+// A value out of the frames' range (non-finite, or at or above 2^1008) makes them all
+// NaN.
 struct PsiDiffs {
   double Pd0, Pd1, Pxx, Pyy, q, Lc, DL0, DL1;
 };
@@ -143,9 +144,9 @@ __device__ __forceinline__ PsiDiffs psi_diffs(double c, double e, double w, doub
   const u64 dxy = (tNE - tSE) - (tNW - tSW);
   const u64 dl0 = (t[9] - t[10]) + (tNE + tSE) - (tNW + tSW) - 4 * pd0;  // L5(1, 0) - L5(-1, 0)
   const u64 dl1 = (t[11] - t[12]) + (tNE + tNW) - (tSE + tSW) - 4 * pd1;  // L5(0, 1) - L5(0, -1)
-  const bool bad = mx >= 0x7FF00000u;
+  const bool bad = mx >= fx::kFrameMaxHi;
   auto out = [&](u64 x, int shift) {
-    return fx::double_of(bad ? 0x7FF8000000000000ull : fx::round_frame_s((fx::i64)x, eg + shift));
+    return fx::double_of(bad ? fx::kNaN : fx::round_frame_s((fx::i64)x, eg + shift));
   };
   PsiDiffs r;
   r.Pd0 = out(pd0, 0);
@@ -182,8 +183,8 @@ __device__ __forceinline__ VelDiffs vel_diffs(double c, double e, double w, doub
 #pragma unroll
   for (int k = 0; k < 9; ++k) t[k] = (u64)fx::sterm(b[k], eg);
   const u64 tC = t[0], tE = t[1], tW = t[2], tN = t[3], tS = t[4];
-  const bool bad = mx >= 0x7FF00000u;
-  auto out = [&](u64 x) { return fx::double_of(bad ? 0x7FF8000000000000ull : fx::round_frame_s((fx::i64)x, eg)); };
+  const bool bad = mx >= fx::kFrameMaxHi;
+  auto out = [&](u64 x) { return fx::double_of(bad ? fx::kNaN : fx::round_frame_s((fx::i64)x, eg)); };
   VelDiffs r;
   r.D0 = out(PRED ? tE - tC : tC - tW);
   r.D1 = out(PRED ? tN - tC : tC - tS);

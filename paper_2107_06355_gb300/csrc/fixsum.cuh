@@ -50,6 +50,12 @@ typedef long long i64;
 // factor 4 on four of them) cannot overflow 64 bits
 constexpr int kG = 4;
 
+// Frames take operands below 2^1008 (high word below 0x7EF00000, magnitudes): with
+// at most 8 bits of headroom no rounded result can then overflow the exponent. An
+// operand at or above it, or infinite or NaN, makes the frame's results NaN.
+constexpr unsigned kFrameMaxHi = 0x7EF00000u;
+constexpr unsigned long long kNaN = 0x7FF8000000000000ull;
+
 // bit pattern of a double and back, through an opaque move on the device so that
 // the optimiser keeps the integer work on the integer pipe
 PPLBM_FX u64 bits_of(double x) {
@@ -124,7 +130,8 @@ PPLBM_FX u64 round_frame_s(i64 s, int eg) {
 //   gy = 4 (pN - pS) + (pNE - pSW) - (pSE - pNW),
 // from the eight neighbours' psi (positive finite values below 2^1008; a zero or
 // subnormal operand counts as at most one unit of the frame's bit 0), each exact in
-// one frame and rounded once. An infinite, NaN or negative operand gives NaN.
+// one frame and rounded once. A negative operand, or one out of the frames' range,
+// gives NaN.
 PPLBM_FX void shan_chen_stencil(double pE, double pW, double pN, double pS, double pNE, double pNW, double pSW,
                                 double pSE, double* gx, double* gy) {
   const u64 bE = bits_of(pE), bW = bits_of(pW), bN = bits_of(pN), bS = bits_of(pS);
@@ -138,14 +145,14 @@ PPLBM_FX void shan_chen_stencil(double pE, double pW, double pN, double pS, doub
   mx = mx > hi32(bSW) ? mx : hi32(bSW);
   mx = mx > hi32(bSE) ? mx : hi32(bSE);
   const int eg = frame_top(mx);
-  const bool bad = mx >= 0x7FF00000u;
+  const bool bad = mx >= kFrameMaxHi;
   // |4 (pE - pW)| < 2^(66 - kG) and each diagonal difference < 2^(64 - kG): the sums
   // stay below 2^63
   const u64 d1 = term(bNE, eg) - term(bSW, eg);
   const u64 d2 = term(bSE, eg) - term(bNW, eg);
   const u64 ex = term<2>(bE, eg) - term<2>(bW, eg);
   const u64 ny = term<2>(bN, eg) - term<2>(bS, eg);
-  const u64 nan = 0x7FF8000000000000ull;
+  const u64 nan = kNaN;
   *gx = double_of(bad ? nan : round_frame_s((i64)(ex + d1 + d2), eg));
   *gy = double_of(bad ? nan : round_frame_s((i64)(ny + d1 - d2), eg));
 }
@@ -192,18 +199,20 @@ PPLBM_FX unsigned mag_hi(u64 b) { return hi32(b) & 0x7FFFFFFFu; }
 
 // j + h, j + 2 h, j + 3 h and, when MINUS, j - h: exact in one frame, each rounded
 // once (for J = j + F/2 = rho u of Eq. Momentum, P = j + F, P + F/2 and j - F/2, with
-// h = F/2). Finite operands; the results of non-finite ones are unspecified.
+// h = F/2). Operands out of the frames' range give NaN.
 template <bool MINUS>
 PPLBM_FX void j_h_combos(double j, double h, double* jh, double* j2h, double* j3h, double* jmh) {
   const u64 bj = bits_of(j), bh = bits_of(h);
   const unsigned mj = mag_hi(bj), mh = mag_hi(bh);
-  const int eg = frame_top(mj > mh ? mj : mh);  // |j| + 3 |h| < 4 2^(64 - kG) = 2^62
+  const unsigned mx = mj > mh ? mj : mh;
+  const int eg = frame_top(mx);  // |j| + 3 |h| < 4 2^(64 - kG) = 2^62
   const u64 tj = (u64)sterm(bj, eg), th = (u64)sterm(bh, eg);
   const u64 s1 = tj + th, s2 = s1 + th;
-  *jh = double_of(round_frame_s((i64)s1, eg));
-  *j2h = double_of(round_frame_s((i64)s2, eg));
-  *j3h = double_of(round_frame_s((i64)(s2 + th), eg));
-  if (MINUS) *jmh = double_of(round_frame_s((i64)(tj - th), eg));
+  const bool bad = mx >= kFrameMaxHi;
+  *jh = double_of(bad ? kNaN : round_frame_s((i64)s1, eg));
+  *j2h = double_of(bad ? kNaN : round_frame_s((i64)s2, eg));
+  *j3h = double_of(bad ? kNaN : round_frame_s((i64)(s2 + th), eg));
+  if (MINUS) *jmh = double_of(bad ? kNaN : round_frame_s((i64)(tj - th), eg));
 }
 
 // headroom of the collision output frame: the largest combination below has
@@ -223,7 +232,7 @@ constexpr int kGOut = 7;
 //   f5,7 = B + 9 (xy + p8) +- 3 (px + py),            f6,8 = B - 9 (xy + p8) +- 3 (py - px),
 //   B = r + 3 (xx + yy) + zz,                         f0 = 4 (4 r - 6 (xx + yy) - 2 zz),
 // evaluated exactly in one frame over the seven (nine) inputs and each rounded once.
-// A non-finite input makes every population NaN.
+// An input out of the frames' range makes every population NaN.
 template <bool SHEAR>
 PPLBM_FX void reduced_populations(double r, double xx, double yy, double xy, double px, double py, double zz,
                                   double p7, double p8, double (&f)[9]) {
@@ -267,11 +276,11 @@ PPLBM_FX void reduced_populations(double r, double xx, double yy, double xy, dou
   n[6] = bm + D;
   n[8] = bm - D;
   n[0] = 4 * tr - 6 * T - 2 * tz;  // f0 / 4
-  const bool bad = mx >= 0x7FF00000u;
+  const bool bad = mx >= kFrameMaxHi;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const u64 v = round_frame_s((i64)n[k], k == 0 ? eg + 2 : eg);
-    f[k] = double_of(bad ? 0x7FF8000000000000ull : v);
+    f[k] = double_of(bad ? kNaN : v);
   }
 }
 
@@ -286,7 +295,7 @@ PPLBM_FX void reduced_populations(double r, double xx, double yy, double xy, dou
 //   zz = -8 mu0 + (mu1 + ... + mu8),                 p7 = 9 (mu1 + mu3 - mu2 - mu4),
 // exact in one frame over the nine adjoints (coefficients summing to 72 at most:
 // headroom 8) and each rounded once; p7, p8 are formed when ALL (default SHEAR) and
-// are 0.0 otherwise. A non-finite adjoint makes every output NaN.
+// are 0.0 otherwise. An adjoint out of the frames' range makes every output NaN.
 constexpr int kGTr = 8;
 
 template <bool SHEAR, bool ALL = SHEAR>
@@ -315,7 +324,7 @@ PPLBM_FX void reduced_populations_transpose(const double (&mu)[9], double (&out)
   n[6] = a13 + a24 + diag - 8 * t[0];
   n[7] = 9 * (a13 - a24);
   n[8] = n[3];
-  const bool bad = mx >= 0x7FF00000u;
+  const bool bad = mx >= kFrameMaxHi;
   const int kout = ALL ? 9 : 7;  // ALL: p7, p8 too (the adjoints the source terms need)
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -323,7 +332,7 @@ PPLBM_FX void reduced_populations_transpose(const double (&mu)[9], double (&out)
       out[k] = 0.0;
       continue;
     }
-    out[k] = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)n[k], eg));
+    out[k] = double_of(bad ? kNaN : round_frame_s((i64)n[k], eg));
   }
 }
 
@@ -347,9 +356,9 @@ PPLBM_FX void j_h_combos_transpose(double a1, double a2, double a3, double a4, d
 #pragma unroll
   for (int k = 0; k < 6; ++k) t[k] = (u64)sterm(b[k], eg);
   const u64 s = t[0] + t[1] + t[2];
-  const bool bad = mx >= 0x7FF00000u;
-  *jb = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)(t[4] + s + t[3]), eg));
-  *hb = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)(t[5] + s + t[1] + 2 * t[2] - t[3]), eg));
+  const bool bad = mx >= kFrameMaxHi;
+  *jb = double_of(bad ? kNaN : round_frame_s((i64)(t[4] + s + t[3]), eg));
+  *hb = double_of(bad ? kNaN : round_frame_s((i64)(t[5] + s + t[1] + 2 * t[2] - t[3]), eg));
 }
 
 // The adjoint's transpose of the Shan-Chen stencil at a node, plus the node's own
@@ -358,7 +367,7 @@ PPLBM_FX void j_h_combos_transpose(double a1, double a2, double a3, double a4, d
 //                 + (sxNW - syNW) - (sxSE - sySE),
 // exact in one frame (coefficients summing to 25: headroom 6) and rounded once. v
 // holds {own, sxW, sxE, syS, syN, sxSW, sySW, sxNE, syNE, sxNW, syNW, sxSE, sySE}; a
-// non-finite value gives NaN.
+// value out of the frames' range gives NaN.
 PPLBM_FX double psi_adjoint_gather(const double (&v)[13]) {
   u64 b[13];
   unsigned mx = 0;
@@ -373,7 +382,7 @@ PPLBM_FX double psi_adjoint_gather(const double (&v)[13]) {
   for (int k = 0; k < 13; ++k) t[k] = (u64)sterm(b[k], eg);
   const u64 s = t[0] + 4 * ((t[1] - t[2]) + (t[3] - t[4])) + (t[5] + t[6]) - (t[7] + t[8]) + (t[9] - t[10]) -
                 (t[11] - t[12]);
-  return double_of(mx >= 0x7FF00000u ? 0x7FF8000000000000ull : round_frame_s((i64)s, eg));
+  return double_of(mx >= kFrameMaxHi ? kNaN : round_frame_s((i64)s, eg));
 }
 
 // The adjoint's lambda^t_i = rho_bar + c_i . j_bar (+ with SHEAR the rows 7, 8 of Eq.
@@ -404,10 +413,10 @@ PPLBM_FX void lambda_assembly(double rb, double jxb, double jyb, double m7b, dou
   n[6] = rm + t[2] - t[4];
   n[7] = rm - t[2] + t[4];
   n[8] = rp - t[2] - t[4];
-  const bool bad = mx >= 0x7FF00000u;
+  const bool bad = mx >= kFrameMaxHi;
   l[0] = rb;
 #pragma unroll
-  for (int k = 1; k < 9; ++k) l[k] = double_of(bad ? 0x7FF8000000000000ull : round_frame_s((i64)n[k], eg));
+  for (int k = 1; k < 9; ++k) l[k] = double_of(bad ? kNaN : round_frame_s((i64)n[k], eg));
 }
 
 // True if all K values are positive normal doubles below 2^1008 (high words in

@@ -395,3 +395,21 @@ def test_lambda_assembly_matches_the_moment_rows(fx, shear):
                 ex += (cx * cx - cy * cy) * m7 + cx * cy * m8
             ops = v[i] if shear else v[i, :3]
             assert abs(Fraction(float(out[i, k])) - ex) <= frame_bound(out[i, k], ex, ops, 4, 4), (i, k)
+
+
+def test_operands_beyond_the_frame_range_give_nan(fx):
+    """Every frame takes operands below 2^1008 (below it no rounded result can overflow
+    the exponent); an operand at or above it gives NaN, as a non-finite one does."""
+    big = 2.0 ** 1008
+    assert np.all(np.isnan(j_h(fx, np.array([[1.0, big], [big, 0.5], [np.inf, 1.0]]))))
+    assert np.all(np.isfinite(j_h(fx, np.array([[1.0, 2.0 ** 1007]]))))
+    q = np.full((2, 9), 0.01)
+    q[0, 6] = big
+    out = populations(fx, q, True)
+    assert np.all(np.isnan(out[0])) and np.all(np.isfinite(out[1]))
+    p = np.full((1, 8), 0.3)
+    p[0, 2] = big
+    assert np.all(np.isnan(stencil(fx, p)))
+    mu = np.full((1, 9), 0.2)
+    mu[0, 5] = -big
+    assert np.all(np.isnan(populations_transpose(fx, mu, True)[0, :9]))
