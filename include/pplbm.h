@@ -392,7 +392,8 @@ typedef struct pplbm_batch pplbm_batch;
                                     collision pass (the FP64-bound and the integer-bound pass
                                     share the SMs); 2 nsteps + 1 launches per call, two-step
                                     CUDA graphs in between; every instance ends the call at the
-                                    same step */
+                                    same step; each launch is a resident grid whose blocks take
+                                    the work items in order from a device counter */
 
 typedef struct pplbm_batch_plan {
   int32_t mode;        /* PPLBM_PLAN_* */

@@ -104,6 +104,7 @@ struct pplbm_batch {
   int n1, n2;
   GridBarrier* d_bar;
   int* d_err;                       // batch-wide word (grid-barrier timeout)
+  unsigned* d_queue;                // the mixed kernel's item counter and finished-block count
   int* d_ierr;                      // one word per instance (divergence)
   int* d_snap_valid;                // one word per instance: guard snapshot holds a density
   double* d_gpart;                  // guard partials, 4 per density-pass work item
@@ -113,12 +114,14 @@ struct pplbm_batch {
   int persistent_grid;
   pplbm_batch_plan plan;
   cudaGraphExec_t graph[2];  // graph[p]: two steps starting from parity p
-  // pipelined plan: item tables (instance | pass bit, index within the instance) of
-  // M1 = collision of A + density of B, M2 = density of A + collision of B, the
-  // prologue PA = density of A and the epilogue EB = collision of B; pgraph[p] replays
-  // M1, M2, M1, M2 from parity p
-  int2* d_mix[4];
+  // pipelined plan: item tables (instance | pass bit, then the density block or the
+  // collision tile's log2 width and origin) of M1 = collision of A + density of B, M2 =
+  // density of A + collision of B, the prologue PA = density of A and the epilogue EB =
+  // collision of B; pgraph[p] replays M1, M2, M1, M2 from parity p; mixed_grid = the
+  // mixed kernel's resident blocks
+  int4* d_mix[4];
   int nmix[4];
+  int mixed_grid;
   cudaGraphExec_t pgraph[2];
   int64_t steps;
   pplbm_status sticky;
@@ -207,17 +210,19 @@ pplbm_status build_tables(pplbm_batch* b, int tile_width) {
     group[i] = g;
     load[g] += nodes(i);
   }
-  std::vector<int2> k1[2], k2[2];
+  std::vector<int4> k1[2], k2[2];
   for (int i = 0; i < b->n; ++i) {
     const BatchInst& I = b->host_inst[i];
     const int nb = (int)((nodes(i) + kThreads - 1) / kThreads);
-    const int tiles = I.tiles_x * ((b->lat[i].ny + I.th - 1) / I.th);
-    for (int j = 0; j < nb; ++j) k1[group[i]].push_back(make_int2(i, j));
-    for (int t = 0; t < tiles; ++t) k2[group[i]].push_back(make_int2(i | (int)0x80000000u, t));
+    const int ty_n = (b->lat[i].ny + I.th - 1) / I.th;
+    for (int j = 0; j < nb; ++j) k1[group[i]].push_back(make_int4(i, j, 0, 0));
+    for (int ty = 0; ty < ty_n; ++ty)
+      for (int tx = 0; tx < I.tiles_x; ++tx)
+        k2[group[i]].push_back(make_int4(i | (int)0x80000000u, I.log2tw, tx * I.tw, ty * I.th));
   }
   // evenly interleaved: item i of x sits at (i + 1/2)/|x| of the table, likewise for y
-  auto interleave = [](const std::vector<int2>& x, const std::vector<int2>& y) {
-    std::vector<int2> m;
+  auto interleave = [](const std::vector<int4>& x, const std::vector<int4>& y) {
+    std::vector<int4> m;
     m.reserve(x.size() + y.size());
     size_t i = 0, j = 0;
     while (i < x.size() || j < y.size()) {
@@ -226,11 +231,11 @@ pplbm_status build_tables(pplbm_batch* b, int tile_width) {
     }
     return m;
   };
-  const std::vector<int2> mix[4] = {interleave(k2[0], k1[1]), interleave(k1[0], k2[1]), k1[0], k2[1]};
+  const std::vector<int4> mix[4] = {interleave(k2[0], k1[1]), interleave(k1[0], k2[1]), k1[0], k2[1]};
   for (int k = 0; k < 4; ++k) {
     b->nmix[k] = (int)mix[k].size();
     if (!mix[k].empty())
-      BTRY(b, cudaMemcpyAsync(b->d_mix[k], mix[k].data(), sizeof(int2) * mix[k].size(), cudaMemcpyHostToDevice,
+      BTRY(b, cudaMemcpyAsync(b->d_mix[k], mix[k].data(), sizeof(int4) * mix[k].size(), cudaMemcpyHostToDevice,
                               b->stream));
   }
   // owner tables live in a device block sized at create for the worst case (tw = 4 or 256)
@@ -258,8 +263,8 @@ void destroy_graphs(pplbm_batch* b) {
 // pipelined plan: M1 (collision of A and density of B, both at parity p) and M2
 // (density of A at 1 - p, collision of B at p) advance both groups by one step
 void launch_mixed_step(pplbm_batch* b, int p, cudaStream_t s) {
-  launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[0], b->nmix[0], p, p, s);
-  launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[1], b->nmix[1], 1 - p, p, s);
+  launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[0], b->nmix[0], b->mixed_grid, p, p, b->d_queue, s);
+  launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[1], b->nmix[1], b->mixed_grid, 1 - p, p, b->d_queue, s);
 }
 
 pplbm_status build_pipelined_graphs(pplbm_batch* b) {
@@ -439,13 +444,13 @@ pplbm_status issue_steps(pplbm_batch* b, int64_t nsteps, cudaStream_t s) {
   if (b->plan.mode == PPLBM_PLAN_PIPELINED && nsteps > 0) {
     // prologue, then M1 M2 per step with the last M2 left out, then the epilogue
     const int p0 = b->parity;
-    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[2], b->nmix[2], p0, p0, s);
+    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[2], b->nmix[2], b->mixed_grid, p0, p0, b->d_queue, s);
     int64_t j = 0;
     for (; j + 2 <= nsteps - 1; j += 2) BTRY(b, cudaGraphLaunch(b->pgraph[(p0 + j) & 1], s));
     for (; j < nsteps - 1; ++j) launch_mixed_step(b, (int)((p0 + j) & 1), s);
     const int pl = (int)((p0 + nsteps - 1) & 1);
-    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[0], b->nmix[0], pl, pl, s);
-    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[3], b->nmix[3], pl, pl, s);
+    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[0], b->nmix[0], b->mixed_grid, pl, pl, b->d_queue, s);
+    launch_mixed(b->kind, b->st, b->d_inst, b->d_mix[3], b->nmix[3], b->mixed_grid, pl, pl, b->d_queue, s);
     BTRY(b, cudaGetLastError());
     b->parity = (int)((p0 + nsteps) & 1);
     return PPLBM_OK;
@@ -530,9 +535,9 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   const size_t ierr_bytes = ((sizeof(int) * n + 255) / 256) * 256;
   const size_t gpart_bytes = ((sizeof(double) * kGuardQ * max1 + 255) / 256) * 256;
   const size_t gout_bytes = ((sizeof(double) * kGuardQ * n + 255) / 256) * 256;
-  const size_t mix_bytes = ((sizeof(int2) * (max1 + max2) + 255) / 256) * 256;  // each pipelined table
+  const size_t mix_bytes = ((sizeof(int4) * (max1 + max2) + 255) / 256) * 256;  // each pipelined table
   const size_t block =
-      inst_bytes + o1_bytes + o2_bytes + 256 + 256 + 2 * ierr_bytes + gpart_bytes + gout_bytes + 4 * mix_bytes;
+      inst_bytes + o1_bytes + o2_bytes + 256 + 256 + 2 * ierr_bytes + gpart_bytes + gout_bytes + 4 * mix_bytes + 256;
   if (cudaMalloc(&b->dev_block, block) != cudaSuccess) {
     delete b;
     return PPLBM_ERR_CUDA;
@@ -548,8 +553,10 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   b->d_gpart = (double*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes);
   b->d_gout = (double*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes);
   for (int k = 0; k < 4; ++k)
-    b->d_mix[k] = (int2*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes + gout_bytes +
+    b->d_mix[k] = (int4*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes + gout_bytes +
                           k * mix_bytes);
+  b->d_queue = (unsigned*)(p + inst_bytes + o1_bytes + o2_bytes + 512 + 2 * ierr_bytes + gpart_bytes + gout_bytes +
+                           4 * mix_bytes);
   b->diverged.assign(n, 0);
   if (cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(b->dev_block);
@@ -557,6 +564,7 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
     return PPLBM_ERR_CUDA;
   }
   cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned), b->stream);
   cudaMemsetAsync(b->d_ierr, 0, sizeof(int) * n, b->stream);
   cudaMemsetAsync(b->d_snap_valid, 0, sizeof(int) * n, b->stream);
   double* w = (double*)workspace;
@@ -599,6 +607,9 @@ pplbm_status pplbm_batch_create(pplbm_batch** out, int32_t n, const pplbm_lattic
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->persistent_grid = std::max(1, occ * sms);
+  occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mixed_kernel(b->kind, b->st), kThreads, 0);
+  b->mixed_grid = std::max(1, occ * sms);
   pplbm_status s = apply_plan(b, PPLBM_PLAN_LAUNCHES, 0);
   if (s != PPLBM_OK) {
     pplbm_batch_destroy(b);

@@ -138,24 +138,161 @@ __global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
   batch_collide_item<KIND, ST, false>(inst, owner, blockIdx.x, parity, sp, &sa, org);
 }
 
-// Work items of both passes in one launch (the pipelined plan): item.x is the
-// instance, with the top bit set for a collision tile; item.y the item's index within
-// its instance. Density items read buffer p1, collision items p2. Lattices of one
-// group run their density pass while those of the other run their collision pass, so
-// the FP64 pipe (the density pass's bound) and the integer pipe (the collision pass's)
-// work at the same time on every SM.
+// ---- the pipelined plan's mixed kernel ----------------------------------------------
+
+// 8- and 16-byte asynchronous copies global -> shared (cp.async, cached in L1); the
+// data is visible to the block after cp_async_wait_all and a barrier. Both addresses
+// are aligned to the copy size.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// A work item of the pipelined plan (int4): x = the instance, with the top bit set for
+// a collision tile; for a density item y = its 256-node block within the instance; for
+// a collision tile y = log2 of the tile width tw (tile height 256 / tw) and (z, w) the
+// tile's origin (x0, y0).
+__device__ __forceinline__ bool is_collision_item(const int4& h) { return h.x < 0; }
+
+// Starts the copy of the item's StepArgs (density items: parity p1, collision tiles:
+// p2) into dst.
+__device__ __forceinline__ void fetch_item_args(const BatchInst* __restrict__ inst, const int4& h, int p1, int p2,
+                                                StepArgs* dst) {
+  const int id = h.x & 0x7FFFFFFF;
+  const unsigned long long* src =
+      reinterpret_cast<const unsigned long long*>(&inst[id].a[is_collision_item(h) ? p2 : p1]);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / 8); k += kThreads) cp_async8(d + k, src + k);
+}
+
+// Starts the load of a collision tile's psi halo tile into sp (row stride tw + 2), as
+// load_psi_tile does: psi values by asynchronous copies, the wall ghost values by
+// plain stores.
+__device__ __forceinline__ void fetch_item_tile(const StepArgs& a, const int4& h, double* sp) {
+  const int log2tw = h.y, tw = 1 << log2tw, th = kThreads >> log2tw, sw = tw + 2;
+  const int x0 = h.z, y0 = h.w;
+  const int nh = 2 * sw + 2 * th;
+  for (int k = (int)threadIdx.x - kThreads; k < nh; k += kThreads) {
+    int tx, ty;
+    if (k < 0) {  // the thread's own node
+      tx = 1 + ((int)threadIdx.x & (tw - 1));
+      ty = 1 + ((int)threadIdx.x >> log2tw);
+    } else if (k < 2 * sw) {
+      const bool top = k >= sw;
+      ty = top ? th + 1 : 0;
+      tx = top ? k - sw : k;
+    } else {
+      const int j = k - 2 * sw;
+      ty = 1 + (j >> 1);
+      tx = (j & 1) ? tw + 1 : 0;
+    }
+    const int gx = wrap_near(x0 + tx - 1, a.nx);
+    int gy = y0 + ty - 1;
+    double* d = sp + ty * sw + tx;
+    if (a.walls && (gy < 0 || gy >= a.ny)) {
+      *d = gy < 0 ? a.psi_ghost_bottom : a.psi_ghost_top;
+    } else {
+      if (!a.walls) gy = wrap_near(gy, a.ny);
+      cp_async8(d, a.psi + (int64_t)gy * a.nx + gx);
+    }
+  }
+}
+
+// The item's pass from its staged arguments (and tile)
+template <int KIND, bool ST>
+__device__ __forceinline__ void run_item(const StepArgs& a, const int4& h, const double* sp) {
+  if (!is_collision_item(h)) {
+    const int64_t i = (int64_t)h.y * kThreads + threadIdx.x;
+    if (i < a.n) rho_psi_node<KIND>(a, a.f_in, i);
+    return;
+  }
+  const int log2tw = h.y, tw = 1 << log2tw;
+  const int lx = (int)threadIdx.x & (tw - 1), ly = (int)threadIdx.x >> log2tw;
+  const int x = h.z + lx, y = h.w + ly;
+  if (x < a.nx && y < a.ny)
+    collide_node<KIND, false, ST>(a, x, y, sp, (ly + 1) * (tw + 2) + lx + 1, tw + 2, nullptr,
+                                  nullptr, nullptr, nullptr);
+}
+
+// Work items of both passes in one launch (the pipelined plan): density items read
+// buffer p1, collision tiles p2. Lattices of one group run their density pass while
+// those of the other run their collision pass, so the FP64 pipe (the density pass's
+// bound) and the integer pipe (the collision pass's) work at the same time on every
+// SM. The grid is the resident block count G (at most n). Block b starts with item b;
+// later items come in table order from the queue counter queue[0] (item G + the
+// counter's old value), taken four items ahead: while a block computes item k it
+// copies in the psi tile of item k + 1, the arguments of item k + 2 and the header of
+// item k + 3 (rings of 2 tiles, 4 argument blocks, 4 headers and 4 table indices), so
+// that no item waits on its set-up loads. The last block to finish resets queue[0]
+// and the finished-block count queue[1] for the next launch.
 template <int KIND, bool ST>
 __global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
-    k_batch_mixed(const BatchInst* inst, const int2* items, int p1, int p2) {
-  __shared__ double sp[kMaxTileSmem];
-  __shared__ StepArgs sa;
-  __shared__ int org[2];
-  const int2 it = items[blockIdx.x];
-  if (it.x >= 0)
-    batch_rho_psi_local<KIND, false>(inst, it.x, it.y, p1, &sa);
-  else
-    batch_collide_local<KIND, ST, false>(inst, it.x & 0x7FFFFFFF, it.y, p2, sp, &sa, org);
+    k_batch_mixed(const BatchInst* inst, const int4* items, int n, int p1, int p2, unsigned* queue) {
+  __shared__ double sp[2][kMaxTileSmem];
+  __shared__ StepArgs sa[4];
+  __shared__ int4 hdr[4];
+  __shared__ int qi[4];  // table index of the ring slot's item; -1: none
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    const int t = G + (int)atomicAdd(&queue[0], 3u);
+    qi[0] = blockIdx.x;
+    qi[1] = t < n ? t : -1;
+    qi[2] = t + 1 < n ? t + 1 : -1;
+    qi[3] = t + 2 < n ? t + 2 : -1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && qi[threadIdx.x] >= 0) cp_async16(&hdr[threadIdx.x], items + qi[threadIdx.x]);
+  cp_async_wait_all();
+  __syncthreads();
+  fetch_item_args(inst, hdr[0], p1, p2, &sa[0]);
+  if (qi[1] >= 0) fetch_item_args(inst, hdr[1], p1, p2, &sa[1]);
+  cp_async_wait_all();
+  __syncthreads();
+  if (is_collision_item(hdr[0])) fetch_item_tile(sa[0], hdr[0], sp[0]);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int k = 0; qi[k & 3] >= 0; ++k) {
+    const int c = k & 3, c1 = (k + 1) & 3, c2 = (k + 2) & 3, c3 = (k + 3) & 3;
+    if (qi[c1] >= 0 && is_collision_item(hdr[c1])) fetch_item_tile(sa[c1], hdr[c1], sp[(k + 1) & 1]);
+    if (qi[c2] >= 0) fetch_item_args(inst, hdr[c2], p1, p2, &sa[c2]);
+    int next = -1;
+    if (threadIdx.x == 0) {
+      if (qi[c3] >= 0) cp_async16(&hdr[c3], items + qi[c3]);
+      const int t = G + (int)atomicAdd(&queue[0], 1u);
+      next = t < n ? t : -1;
+    }
+    run_item<KIND, ST>(sa[c], hdr[c], sp[k & 1]);
+    if (threadIdx.x == 0) qi[c] = next;  // slot c now names item k + 4
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&queue[1], 1u) == (unsigned)G - 1u) {
+      queue[0] = 0u;
+      queue[1] = 0u;
+      __threadfence();
+    }
+  }
 }
+
+template <bool ST>
+const void* mixed_kernel_t(int kind) {
+  switch (kind) {
+    case kUnitTau: return (const void*)k_batch_mixed<kUnitTau, ST>;
+    case kShearTau: return (const void*)k_batch_mixed<kShearTau, ST>;
+    default: return (const void*)k_batch_mixed<kFullMrt, ST>;
+  }
+}
+
+const void* mixed_kernel(int kind, bool st) { return st ? mixed_kernel_t<true>(kind) : mixed_kernel_t<false>(kind); }
 
 template <int KIND, bool ST>
 __global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchInst* inst, const int* owner1, int n1,
@@ -261,15 +398,18 @@ void launch_pair(int kind, bool st, const BatchInst* inst, const int* o1, int n1
     launch_pair_t<false>(kind, inst, o1, n1, o2, n2, parity, s);
 }
 
-// one launch of the mixed kernel over n items
-void launch_mixed(int kind, bool st, const BatchInst* inst, const int2* items, int n, int p1, int p2, cudaStream_t s) {
+// one launch of the mixed kernel over n items with `grid` blocks (at most n); queue:
+// the kernel's two counters, zero before the launch (and after it)
+void launch_mixed(int kind, bool st, const BatchInst* inst, const int4* items, int n, int grid, int p1, int p2,
+                  unsigned* queue, cudaStream_t s) {
   if (n <= 0) return;
+  grid = grid < n ? grid : n;
 #define PPLBM_KM(K)                                                                   \
   do {                                                                                \
     if (st)                                                                           \
-      k_batch_mixed<K, true><<<n, kThreads, 0, s>>>(inst, items, p1, p2);             \
+      k_batch_mixed<K, true><<<grid, kThreads, 0, s>>>(inst, items, n, p1, p2, queue);\
     else                                                                              \
-      k_batch_mixed<K, false><<<n, kThreads, 0, s>>>(inst, items, p1, p2);            \
+      k_batch_mixed<K, false><<<grid, kThreads, 0, s>>>(inst, items, n, p1, p2, queue);\
   } while (0)
   switch (kind) {
     case kUnitTau: PPLBM_KM(kUnitTau); break;
