@@ -94,7 +94,11 @@ FD_ALU_PER_POINT = 1947 + 1963 + 2 * 11
 # repeated.
 COUNTS = {"sources": "60b6838eb51b50f4",
           "rho_psi": {"dram_bytes": 1316732672, "fp64_per_node": 14.542, "alu_per_node": 222.7},
-          "collide": {"dram_bytes": 1302215936, "fp64_per_node": 19.000, "alu_per_node": 1020.1}}
+          "collide": {"dram_bytes": 1302215936, "fp64_per_node": 19.000, "alu_per_node": 1020.1},
+          # the pipelined plan's mixed kernel: one launch runs the density pass of one
+          # group and the collision pass of the other (half the nodes each); a step is
+          # two launches
+          "mixed": {"dram_bytes": 1410547968}}
 KERNEL_SOURCES = ("batch_kernels.cuh", "step_device.cuh", "eos_dev.cuh", "eos.cuh", "fp64.cuh", "fixsum.cuh",
                   "internal.h")
 
@@ -1037,8 +1041,14 @@ def main():
         roof, other = dict(int_pipe), fp64_pipe
     else:
         roof, other = dict(fp64_pipe), int_pipe
-    roof = {"bound": "alu", **roof, "traffic": pass_traffic(dom) if per_pass else None,
-            "traffic_unit": "DRAM bytes per launch (ncu capture, same kernel sources)",
+    if per_pass:
+        traffic, traffic_unit = pass_traffic(dom), "DRAM bytes per launch (ncu capture, same kernel sources)"
+    elif mode == "pipelined" and counts_valid():
+        traffic = 2 * COUNTS["mixed"]["dram_bytes"]
+        traffic_unit = "DRAM bytes per step: two mixed launches (ncu capture of one, same kernel sources)"
+    else:
+        traffic, traffic_unit = None, "DRAM bytes per step"
+    roof = {"bound": "alu", **roof, "traffic": traffic, "traffic_unit": traffic_unit,
             "launch_ms": dom_s * 1e3, "share_of_step": share}
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
