@@ -258,7 +258,10 @@ __global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
   if (is_collision_item(hdr[0])) fetch_item_tile(sa[0], hdr[0], sp[0]);
   cp_async_wait_all();
   __syncthreads();
-  for (int k = 0; qi[k & 3] >= 0; ++k) {
+  // qi[c] is rewritten during iteration k (thread 0, for item k + 4), so whether item
+  // k + 1 exists is read from its slot c1 before the iteration's barrier: slot c1 is
+  // not written during iteration k, and every thread reads the same value
+  for (int k = 0;; ++k) {
     const int c = k & 3, c1 = (k + 1) & 3, c2 = (k + 2) & 3, c3 = (k + 3) & 3;
     if (qi[c1] >= 0 && is_collision_item(hdr[c1])) fetch_item_tile(sa[c1], hdr[c1], sp[(k + 1) & 1]);
     if (qi[c2] >= 0) fetch_item_args(inst, hdr[c2], p1, p2, &sa[c2]);
@@ -270,8 +273,10 @@ __global__ void __launch_bounds__(kThreads, collide_min_blocks(KIND))
     }
     run_item<KIND, ST>(sa[c], hdr[c], sp[k & 1]);
     if (threadIdx.x == 0) qi[c] = next;  // slot c now names item k + 4
+    const bool more = qi[c1] >= 0;
     cp_async_wait_all();
     __syncthreads();
+    if (!more) break;
   }
   if (threadIdx.x == 0) {
     __threadfence();
